@@ -1,0 +1,243 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/bench and the CPU oracle.
+
+This module holds no arithmetic of the evolution method: it only builds initial states
+(analytic puncture metrics and scalar profiles on a cell-centred grid), draws the seeded
+random parameters of the workloads, and describes the box/parameter dictionaries that
+both sides translate into their own structures.
+
+State layout (the C-ABI layout, also used by the oracle): float64 array of shape
+``(27, nz + 2*ng, ny + 2*ng, nx + 2*ng)``, field-major, x fastest. Grid point with
+ghosted index (i, j, k) sits at ``x = x0 + (i - ng)*dx`` (likewise y, z), where x0 is the
+coordinate of interior point 0. Field order (27 fields):
+
+    0 chi | 1-6 h11 h12 h13 h22 h23 h33 | 7 K | 8-13 A11 A12 A13 A22 A23 A33 | 14 Theta |
+    15-17 Gamma^1..3 | 18 lapse | 19-21 shift^1..3 | 22-24 B^1..3 | 25 phi | 26 Pi
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field, asdict
+
+import numpy as np
+
+NFIELDS = 27
+NG = 3
+FIELD_NAMES = ["chi", "h11", "h12", "h13", "h22", "h23", "h33", "K",
+               "A11", "A12", "A13", "A22", "A23", "A33", "Theta",
+               "Gamma1", "Gamma2", "Gamma3", "lapse", "shift1", "shift2", "shift3",
+               "B1", "B2", "B3", "phi", "Pi"]
+IDX = {n: i for i, n in enumerate(FIELD_NAMES)}
+
+BC_PERIODIC = 0
+BC_FROZEN = 1
+BETA_LINEAR = 0      # beta(phi) = lambda * phi
+BETA_QUADRATIC = 1   # beta(phi) = lambda * phi^2 / 2
+
+
+@dataclass
+class Box:
+    nx: int
+    ny: int
+    nz: int
+    dx: float
+    x0: float
+    y0: float
+    z0: float
+    bc: int = BC_PERIODIC
+    ng: int = NG
+
+    @property
+    def shape(self):
+        return (NFIELDS, self.nz + 2 * self.ng, self.ny + 2 * self.ng, self.nx + 2 * self.ng)
+
+    @property
+    def npoints(self):
+        return self.nx * self.ny * self.nz
+
+    def coords(self):
+        """Coordinate arrays (3D, ghosted) of every grid point."""
+        g = self.ng
+        x = self.x0 + (np.arange(self.nx + 2 * g) - g) * self.dx
+        y = self.y0 + (np.arange(self.ny + 2 * g) - g) * self.dx
+        z = self.z0 + (np.arange(self.nz + 2 * g) - g) * self.dx
+        Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+        return X, Y, Z
+
+    def interior(self, a):
+        g = self.ng
+        return a[..., g:g + self.nz, g:g + self.ny, g:g + self.nx]
+
+
+def cube_box(n, lo, hi, bc=BC_PERIODIC):
+    """Cell-centred box of n^3 interior points covering [lo, hi]^3."""
+    dx = (hi - lo) / n
+    c = lo + 0.5 * dx
+    return Box(n, n, n, dx, c, c, c, bc)
+
+
+@dataclass
+class Params:
+    kappa1: float = 0.1
+    kappa2: float = 0.0
+    kappa3: float = 1.0
+    shift_F: float = 0.75
+    eta: float = 1.0
+    a0: float = 0.2
+    b0: float = 0.4
+    beta_kind: int = BETA_LINEAR
+    lam: float = 0.01
+    g2: float = 0.01
+    sigma_ko: float = 0.3
+    min_chi: float = 1e-4
+    min_lapse: float = 1e-4
+    enforce_algebraic: int = 1
+
+    def to_dict(self):
+        return asdict(self)
+
+
+# ---------------------------------------------------------------------------------------
+# SplitMix64 (Steele, Lea, Flood 2014): the one documented generator for all seeded draws.
+# ---------------------------------------------------------------------------------------
+class SplitMix64:
+    MASK = (1 << 64) - 1
+
+    def __init__(self, seed: int):
+        self.state = seed & self.MASK
+
+    def next_u64(self) -> int:
+        self.state = (self.state + 0x9E3779B97F4A7C15) & self.MASK
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & self.MASK
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & self.MASK
+        return z ^ (z >> 31)
+
+    def uniform(self, lo=0.0, hi=1.0) -> float:
+        return lo + (hi - lo) * ((self.next_u64() >> 11) * (1.0 / 9007199254740992.0))
+
+    def choice(self, seq):
+        return seq[self.next_u64() % len(seq)]
+
+
+# ---------------------------------------------------------------------------------------
+# Initial data (analytic; evaluated on every grid point, ghosts included)
+# ---------------------------------------------------------------------------------------
+def _empty(box):
+    return np.zeros(box.shape, dtype=np.float64)
+
+
+def flat_state(box):
+    """Minkowski slice, unit lapse, zero shift, zero scalar."""
+    s = _empty(box)
+    s[IDX["chi"]] = 1.0
+    for n in ("h11", "h22", "h33"):
+        s[IDX[n]] = 1.0
+    s[IDX["lapse"]] = 1.0
+    return s
+
+
+def conformally_flat_puncture(box, psi, phi, Pi=None):
+    """chi = psi^-4, h = delta, K = A = Theta = Gamma = 0, lapse = chi^(1/2), shift = B = 0."""
+    s = flat_state(box)
+    chi = psi ** -4
+    s[IDX["chi"]] = chi
+    s[IDX["lapse"]] = np.sqrt(chi)
+    s[IDX["phi"]] = phi
+    if Pi is not None:
+        s[IDX["Pi"]] = Pi
+    return s
+
+
+def single_puncture(box, M=1.0, amp=1e-3, r0=2.0, width=1.0, centre=(0.0, 0.0, 0.0)):
+    """Schwarzschild puncture in isotropic coordinates plus phi = amp*exp(-(r-r0)^2/width^2)."""
+    X, Y, Z = box.coords()
+    r = np.sqrt((X - centre[0]) ** 2 + (Y - centre[1]) ** 2 + (Z - centre[2]) ** 2)
+    psi = 1.0 + M / (2.0 * r)
+    phi = amp * np.exp(-((r - r0) ** 2) / width ** 2)
+    return conformally_flat_puncture(box, psi, phi)
+
+
+def gaussian_bumps(seed, n_bumps, lo, hi):
+    """Seeded parameters of a sum of Gaussians: centres (uniform in [lo,hi]^3),
+    widths U[1,3], amplitudes 1e-2*U[-1,1]; drawn in that order."""
+    rng = SplitMix64(seed)
+    centres = [[rng.uniform(lo, hi) for _ in range(3)] for _ in range(n_bumps)]
+    widths = [rng.uniform(1.0, 3.0) for _ in range(n_bumps)]
+    amps = [1e-2 * rng.uniform(-1.0, 1.0) for _ in range(n_bumps)]
+    return centres, widths, amps
+
+
+def brill_lindquist_pair(box, m1=0.5, m2=0.5, sep=6.0, seed=0, n_bumps=8, lo=-16.0, hi=16.0):
+    """Brill-Lindquist pair on the z axis at +-sep/2 plus a seeded sum of Gaussians for phi."""
+    X, Y, Z = box.coords()
+    r1 = np.sqrt(X ** 2 + Y ** 2 + (Z - sep / 2) ** 2)
+    r2 = np.sqrt(X ** 2 + Y ** 2 + (Z + sep / 2) ** 2)
+    psi = 1.0 + m1 / (2 * r1) + m2 / (2 * r2)
+    centres, widths, amps = gaussian_bumps(seed, n_bumps, lo, hi)
+    phi = np.zeros_like(X)
+    for c, w, a in zip(centres, widths, amps):
+        phi += a * np.exp(-((X - c[0]) ** 2 + (Y - c[1]) ** 2 + (Z - c[2]) ** 2) / w ** 2)
+    return conformally_flat_puncture(box, psi, phi)
+
+
+def scalar_plane_wave(box, amp, kvec, t=0.0):
+    """Flat space with phi = amp*sin(k.x - |k| t), Pi = d_t phi = -amp |k| cos(k.x - |k| t)."""
+    s = flat_state(box)
+    X, Y, Z = box.coords()
+    kn = math.sqrt(sum(k * k for k in kvec))
+    ph = kvec[0] * X + kvec[1] * Y + kvec[2] * Z - kn * t
+    s[IDX["phi"]] = amp * np.sin(ph)
+    s[IDX["Pi"]] = -amp * kn * np.cos(ph)
+    return s
+
+
+def random_perturbed_state(box, seed, base=None, eps=1e-2):
+    """A smooth, generic state: base (flat by default) plus seeded low-mode sinusoids in every
+    field, so that every term of the equations is exercised (used by parity tests)."""
+    s = flat_state(box) if base is None else base.copy()
+    rng = SplitMix64(seed)
+    X, Y, Z = box.coords()
+    L = (box.nx * box.dx, box.ny * box.dx, box.nz * box.dx)
+    for f in range(NFIELDS):
+        for _ in range(2):
+            kx = 2 * math.pi * rng.choice([1, 2]) / L[0]
+            ky = 2 * math.pi * rng.choice([1, 2]) / L[1]
+            kz = 2 * math.pi * rng.choice([1, 2]) / L[2]
+            ph = rng.uniform(0, 2 * math.pi)
+            a = eps * rng.uniform(-1, 1)
+            s[f] += a * np.sin(kx * X + ph) * np.cos(ky * Y - ph) * np.sin(kz * Z + 0.5 * ph)
+    return s
+
+
+# ---------------------------------------------------------------------------------------
+# Workload descriptions
+# ---------------------------------------------------------------------------------------
+def config_single_puncture_32():
+    """32^3 interior on [-4,4]^3 (dx = 0.25), periodic, single puncture M=1 at the origin
+    (cell-centred grid: the puncture sits half a cell from the nearest points on every
+    axis), phi = 1e-3 exp(-(r-2)^2), beta = lambda*phi, lambda = g2 = 0.01, 10 steps."""
+    box = cube_box(32, -4.0, 4.0)
+    params = Params(beta_kind=BETA_LINEAR, lam=0.01, g2=0.01)
+    return dict(name="single_puncture_32", box=box, params=params, dt=0.25 * box.dx, nsteps=10,
+                make_state=lambda b=box: single_puncture(b))
+
+
+def config_bl_pair_256(n=256):
+    """256^3 interior on [-16,16]^3 (dx = 0.125), periodic, Brill-Lindquist pair m=0.5 each at
+    z = +-3, phi = seeded sum of 8 Gaussians, beta = lambda*phi^2/2, lambda = 0.05, g2 = 0.01,
+    100 steps at dt = 0.25*dx."""
+    box = cube_box(n, -16.0, 16.0)
+    params = Params(beta_kind=BETA_QUADRATIC, lam=0.05, g2=0.01)
+    return dict(name=f"bl_pair_{n}", box=box, params=params, dt=0.25 * box.dx, nsteps=100,
+                make_state=lambda b=box: brill_lindquist_pair(b))
+
+
+def coupling_sweep(n_instances=32, seed=0):
+    """Seeded couplings of the 32-instance sweep: lambda ~ U[0,0.1], g2 ~ U[0,0.05]."""
+    rng = SplitMix64(seed)
+    out = []
+    for _ in range(n_instances):
+        lam = rng.uniform(0.0, 0.1)
+        g2 = rng.uniform(0.0, 0.05)
+        out.append((lam, g2))
+    return out

@@ -1,0 +1,161 @@
+"""Python binding of the CPU oracle (ctypes over oracle/liborc.so).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, __graft_entry__.smoke() and bench.py's
+cpu_baseline / reference arm. The product path (paper_2309_06225_gb300) never imports it.
+All arrays are float64 numpy arrays in the ghosted field-major layout of grf_inputs.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+
+class OrcParams(C.Structure):
+    _fields_ = [("kappa1", C.c_double), ("kappa2", C.c_double), ("kappa3", C.c_double),
+                ("shift_F", C.c_double), ("eta", C.c_double),
+                ("a0", C.c_double), ("b0", C.c_double),
+                ("lam", C.c_double), ("g2", C.c_double),
+                ("sigma_ko", C.c_double), ("min_chi", C.c_double), ("min_lapse", C.c_double),
+                ("beta_kind", C.c_int), ("enforce_algebraic", C.c_int)]
+
+
+class OrcBox(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("ng", C.c_int),
+                ("dx", C.c_double), ("x0", C.c_double), ("y0", C.c_double), ("z0", C.c_double),
+                ("bc", C.c_int), ("pad_", C.c_int)]
+
+
+_lib = None
+_P = C.POINTER(C.c_double)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        L.orc_point_rhs.argtypes = [C.POINTER(OrcParams), _P, _P, _P, _P, _P]
+        L.orc_point_rhs.restype = C.c_int
+        L.orc_point_constraints.argtypes = [C.POINTER(OrcParams), _P, _P, _P, _P]
+        L.orc_phys_sources.argtypes = [C.POINTER(OrcParams), _P, _P, C.c_double, _P]
+        L.orc_solve.argtypes = [C.c_int, _P, _P, _P]
+        L.orc_solve.restype = C.c_int
+        L.orc_fill_ghosts.argtypes = [C.POINTER(OrcBox), _P]
+        L.orc_derivs.argtypes = [C.POINTER(OrcBox), _P, _P, _P]
+        L.orc_rhs.argtypes = [C.POINTER(OrcBox), C.POINTER(OrcParams), _P, _P, C.c_int]
+        L.orc_rhs.restype = C.c_int
+        L.orc_ko.argtypes = [C.POINTER(OrcBox), C.c_double, _P, _P]
+        L.orc_enforce.argtypes = [C.POINTER(OrcBox), C.POINTER(OrcParams), _P]
+        L.orc_rk4.argtypes = [C.POINTER(OrcBox), C.POINTER(OrcParams), _P, C.c_double, C.c_int]
+        L.orc_rk4.restype = C.c_int
+        L.orc_constraints.argtypes = [C.POINTER(OrcBox), C.POINTER(OrcParams), _P, _P]
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_P)
+
+
+def params(p) -> OrcParams:
+    """From a grf_inputs.Params (or anything with the same attributes)."""
+    return OrcParams(p.kappa1, p.kappa2, p.kappa3, p.shift_F, p.eta, p.a0, p.b0, p.lam, p.g2,
+                     p.sigma_ko, p.min_chi, p.min_lapse, int(p.beta_kind), int(p.enforce_algebraic))
+
+
+def box(b) -> OrcBox:
+    return OrcBox(b.nx, b.ny, b.nz, b.ng, b.dx, b.x0, b.y0, b.z0, int(b.bc), 0)
+
+
+def set_threads(n):
+    os.environ["OMP_NUM_THREADS"] = str(n)
+
+
+def point_rhs(p, v, d1, d2):
+    """Pointwise RHS (no dissipation). v[27], d1[27,3], d2[27,6] -> (rhs[27], diag[64], status)."""
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    d1 = np.ascontiguousarray(d1, dtype=np.float64)
+    d2 = np.ascontiguousarray(d2, dtype=np.float64)
+    rhs = np.zeros(27)
+    diag = np.zeros(64)
+    st = lib().orc_point_rhs(C.byref(params(p)), _ptr(v), _ptr(d1), _ptr(d2), _ptr(rhs), _ptr(diag))
+    return rhs, diag, st
+
+
+def point_constraints(p, v, d1, d2):
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    d1 = np.ascontiguousarray(d1, dtype=np.float64)
+    d2 = np.ascontiguousarray(d2, dtype=np.float64)
+    out = np.zeros(4)
+    lib().orc_point_constraints(C.byref(params(p)), _ptr(v), _ptr(d1), _ptr(d2), _ptr(out))
+    return out
+
+
+def phys_sources(p, phys, u6, w):
+    phys = np.ascontiguousarray(phys, dtype=np.float64)
+    assert phys.size == 120
+    u6 = np.ascontiguousarray(u6, dtype=np.float64)
+    out = np.zeros(19)
+    lib().orc_phys_sources(C.byref(params(p)), _ptr(phys), _ptr(u6), float(w), _ptr(out))
+    return out
+
+
+def solve(M, r):
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    r = np.ascontiguousarray(r, dtype=np.float64)
+    n = r.size
+    x = np.zeros(n)
+    st = lib().orc_solve(n, _ptr(M), _ptr(r), _ptr(x))
+    return x, st
+
+
+def fill_ghosts(b, s):
+    lib().orc_fill_ghosts(C.byref(box(b)), _ptr(s))
+    return s
+
+
+def derivs(b, s):
+    npt = b.npoints
+    d1 = np.zeros((27, 3, b.nz, b.ny, b.nx))
+    d2 = np.zeros((27, 6, b.nz, b.ny, b.nx))
+    lib().orc_derivs(C.byref(box(b)), _ptr(s), _ptr(d1), _ptr(d2))
+    return d1, d2
+
+
+def rhs(b, p, s, with_ko=True):
+    out = np.zeros_like(s)
+    st = lib().orc_rhs(C.byref(box(b)), C.byref(params(p)), _ptr(s), _ptr(out), int(with_ko))
+    if st != 0:
+        raise RuntimeError(f"oracle rhs status {st}")
+    return out
+
+
+def ko(b, sigma, s, out=None):
+    if out is None:
+        out = np.zeros_like(s)
+    lib().orc_ko(C.byref(box(b)), float(sigma), _ptr(s), _ptr(out))
+    return out
+
+
+def enforce(b, p, s):
+    lib().orc_enforce(C.byref(box(b)), C.byref(params(p)), _ptr(s))
+    return s
+
+
+def rk4(b, p, s, dt, nsteps):
+    """Advances s in place by nsteps RK4 steps."""
+    st = lib().orc_rk4(C.byref(box(b)), C.byref(params(p)), _ptr(s), float(dt), int(nsteps))
+    if st != 0:
+        raise RuntimeError(f"oracle rk4 status {st}")
+    return s
+
+
+def constraints(b, p, s):
+    out = np.zeros((4, b.nz, b.ny, b.nx))
+    lib().orc_constraints(C.byref(box(b)), C.byref(params(p)), _ptr(s), _ptr(out))
+    return out

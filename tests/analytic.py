@@ -1,0 +1,271 @@
+"""Exact (symbolic) point data for the oracle pins: analytic metrics and scalar fields,
+their derivatives by sympy, and a small numpy 4D-geometry toolkit used as an independent
+brute-force reference (4D Christoffels -> Riemann -> stress tensor in coordinates).
+"""
+import math
+
+import numpy as np
+
+try:
+    import sympy as sp
+except ImportError:  # pragma: no cover - the GPU machine has no sympy; these tests are CPU-only
+    sp = None
+
+SYM_PAIRS = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
+F_CHI, F_H, F_K, F_A, F_TH, F_GAM, F_LAPSE, F_SHIFT, F_B, F_PHI, F_PI = 0, 1, 7, 8, 14, 15, 18, 19, 22, 25, 26
+NEED_D2 = [F_CHI] + list(range(F_H, F_H + 6)) + [F_LAPSE] + list(range(F_SHIFT, F_SHIFT + 3)) + [F_PHI]
+
+
+def symbols():
+    return sp.symbols("t x y z", real=True)
+
+
+def evaluate(exprs, syms, pt):
+    """Evaluates a list of sympy expressions at one point (double precision)."""
+    return np.array(sp.lambdify(syms, [sp.sympify(e) for e in exprs], modules="math")(*pt), dtype=np.float64)
+
+
+def conformal_point(fields, pt, xyz):
+    """fields: list of 27 sympy expressions in (x, y, z). Returns v[27], d1[27,3], d2[27,6]
+    evaluated at pt (exact derivatives, double-precision evaluation). pt may also be a list
+    of points, in which case a list of triples is returned."""
+    exprs = []
+    for f, e in enumerate(fields):
+        e = sp.sympify(e)
+        firsts = [sp.diff(e, s) for s in xyz]
+        exprs.append(e)
+        exprs.extend(firsts)
+        if f in NEED_D2 or f == F_PI:
+            exprs.extend(sp.diff(firsts[a], xyz[b]) for a, b in SYM_PAIRS)
+        else:
+            exprs.extend([sp.Integer(0)] * 6)
+    fn = sp.lambdify(xyz, exprs, modules="math")
+    single = not isinstance(pt[0], (tuple, list, np.ndarray))
+    res = []
+    for q in ([pt] if single else list(pt)):
+        vals = np.array(fn(*q), dtype=np.float64).reshape(27, 10)
+        res.append((vals[:, 0].copy(), vals[:, 1:4].copy(), vals[:, 4:10].copy()))
+    return res[0] if single else res
+
+
+def christoffel_first(g, X):
+    n = len(X)
+    return [[[sp.Rational(1, 2) * (sp.diff(g[l, j], X[i]) + sp.diff(g[l, i], X[j]) - sp.diff(g[i, j], X[l]))
+              for j in range(n)] for i in range(n)] for l in range(n)]
+
+
+def kerr_schild_fields(M=1.0):
+    """Schwarzschild in Kerr-Schild (ingoing Eddington-Finkelstein) coordinates with its own
+    stationary lapse and shift, written in the 27 conformal CCZ4 variables with Theta = 0,
+    Gamma-hat = Gamma-tilde (Z = 0), B = 0, phi = Pi = 0. Returns (fields, (x, y, z))."""
+    t, x, y, z = symbols()
+    X = (x, y, z)
+    r = sp.sqrt(x * x + y * y + z * z)
+    H = M / r
+    l = [x / r, y / r, z / r]
+    g = sp.Matrix(3, 3, lambda i, j: (1 if i == j else 0) + 2 * H * l[i] * l[j])
+    gi = sp.Matrix(3, 3, lambda i, j: (1 if i == j else 0) - 2 * H * l[i] * l[j] / (1 + 2 * H))
+    beta_l = [2 * H * l[i] for i in range(3)]
+    beta_u = [2 * H * l[i] / (1 + 2 * H) for i in range(3)]
+    alpha = 1 / sp.sqrt(1 + 2 * H)
+    G1 = christoffel_first(g, X)
+    Dbeta = [[sp.diff(beta_l[j], X[i]) - sum(G1[m][i][j] * beta_u[m] for m in range(3)) for j in range(3)]
+             for i in range(3)]
+    K = sp.Matrix(3, 3, lambda i, j: (Dbeta[i][j] + Dbeta[j][i]) / (2 * alpha))
+    Ktr = sum(gi[i, j] * K[i, j] for i in range(3) for j in range(3))
+    chi = (1 + 2 * H) ** sp.Rational(-1, 3)
+    h = chi * g
+    A = chi * (K - g * Ktr / 3)
+    hi = gi / chi
+    Gt1 = christoffel_first(h, X)
+    Gam = [sum(hi[j, k] * sum(hi[i, l] * Gt1[l][j][k] for l in range(3)) for j in range(3) for k in range(3))
+           for i in range(3)]
+    fields = [chi] + [h[i, j] for i, j in SYM_PAIRS] + [Ktr] + [A[i, j] for i, j in SYM_PAIRS] + [0] \
+             + Gam + [alpha] + beta_u + [0, 0, 0] + [0, 0]
+    return fields, X
+
+
+def isotropic_schwarzschild_fields(M=1.0, lapse="precollapsed", phi_amp=0.0):
+    """Schwarzschild puncture data (time-symmetric slice, isotropic radius) with a chosen lapse."""
+    t, x, y, z = symbols()
+    X = (x, y, z)
+    r = sp.sqrt(x * x + y * y + z * z)
+    psi = 1 + M / (2 * r)
+    chi = psi ** -4
+    if lapse == "precollapsed":
+        alpha = psi ** -2
+    elif lapse == "static":
+        alpha = (1 - M / (2 * r)) / (1 + M / (2 * r))
+    else:
+        alpha = sp.Integer(1)
+    phi = phi_amp * sp.exp(-(r - 2) ** 2)
+    fields = [chi, 1, 0, 0, 1, 0, 1, 0] + [0] * 6 + [0] + [0, 0, 0] + [alpha] + [0] * 3 + [0] * 3 + [phi, 0]
+    return [sp.sympify(f) for f in fields], X
+
+
+def areal_radius_isotropic(r, M=1.0):
+    return r * (1 + M / (2 * r)) ** 2
+
+
+# ---------------------------------------------------------------------------------------
+# Generic analytic spacetime (lapse, shift, spatial metric, scalar) for the 4D checks
+# ---------------------------------------------------------------------------------------
+ROT = None
+
+
+def rotation():
+    """A fixed generic rotation (all entries non-zero), so that R^T diag(d) R has six
+    non-trivial components but a cheap symbolic inverse."""
+    a, b, c = 0.4, -0.7, 1.1
+    Rz = sp.Matrix([[sp.cos(a), -sp.sin(a), 0], [sp.sin(a), sp.cos(a), 0], [0, 0, 1]])
+    Ry = sp.Matrix([[sp.cos(b), 0, sp.sin(b)], [0, 1, 0], [-sp.sin(b), 0, sp.cos(b)]])
+    Rx = sp.Matrix([[1, 0, 0], [0, sp.cos(c), -sp.sin(c)], [0, sp.sin(c), sp.cos(c)]])
+    return sp.N(Rz * Ry * Rx, 20)
+
+
+def rotated_diag(d):
+    """Returns (M, M^-1) for M = R^T diag(d) R."""
+    R = rotation()
+    M = sp.Matrix(3, 3, lambda i, j: sum(R[a, i] * R[a, j] * d[a] for a in range(3)))
+    Mi = sp.Matrix(3, 3, lambda i, j: sum(R[a, i] * R[a, j] / d[a] for a in range(3)))
+    return M, Mi
+
+
+def generic_spacetime():
+    t, x, y, z = symbols()
+    alpha = 1 + sp.Rational(1, 5) * sp.sin(0.7 * x + 0.3 * y - 0.5 * z + 0.4 * t)
+    beta_u = [sp.Rational(1, 10) * sp.cos(0.5 * y + 0.2 * t + 0.3 * z),
+              0.15 * sp.sin(0.4 * z - 0.3 * x + 0.25 * t),
+              0.1 * sp.sin(x + t) * sp.cos(0.3 * y)]
+    d = [1 + 0.20 * sp.sin(0.3 * x + 0.2 * t - 0.4 * z), 1 + 0.15 * sp.cos(0.6 * z + 0.2 * x - 0.35 * t + 0.5 * y),
+         1 + 0.18 * sp.sin(0.5 * y + 0.3 * z + 0.45 * t)]
+    g, gi = rotated_diag(d)
+    phi = 0.3 * sp.sin(0.6 * x + 0.2 * t - 0.1 * y) * sp.cos(0.4 * y + 0.2 * z) + 0.2 * z * t + 0.1 * x
+    return (t, x, y, z), alpha, beta_u, g, phi
+
+
+def four_metric(alpha, beta_u, g):
+    beta_l = [sum(g[i, j] * beta_u[j] for j in range(3)) for i in range(3)]
+    g4 = sp.zeros(4, 4)
+    g4[0, 0] = -alpha ** 2 + sum(beta_l[i] * beta_u[i] for i in range(3))
+    for i in range(3):
+        g4[0, i + 1] = g4[i + 1, 0] = beta_l[i]
+        for j in range(3):
+            g4[i + 1, j + 1] = g[i, j]
+    return g4
+
+
+def lambdify_metric_derivs(g4, phi, T):
+    """Returns a function pt -> (g, dg[r][m][n], ddg[r][s][m][n], dphi[m], ddphi[m][n])."""
+    comps = []
+    for m in range(4):
+        for n in range(4):
+            comps.append(g4[m, n])
+    firsts = [[sp.diff(c, v) for v in T] for c in comps]
+    seconds = [[[sp.diff(f1, v) for v in T] for f1 in row] for row in firsts]
+    pf = [sp.diff(phi, v) for v in T]
+    pff = [[sp.diff(a, v) for v in T] for a in pf]
+    flat = comps + [f for row in firsts for f in row] + [s for row in seconds for r2 in row for s in r2] + pf \
+           + [a for row in pff for a in row]
+    fn = sp.lambdify(T, flat, modules="math")
+
+    def at(pt):
+        vals = np.array(fn(*pt), dtype=np.float64)
+        o = 0
+        g = vals[o:o + 16].reshape(4, 4); o += 16
+        dg = vals[o:o + 64].reshape(4, 4, 4); o += 64            # [comp m*4+n][r]
+        dg = np.transpose(dg.reshape(4, 4, 4), (2, 0, 1))         # -> dg[r][m][n]
+        ddg = vals[o:o + 256].reshape(4, 4, 4, 4); o += 256       # [m][n][r][s]
+        ddg = np.transpose(ddg, (2, 3, 0, 1))                     # -> ddg[r][s][m][n]
+        dphi = vals[o:o + 4]; o += 4
+        ddphi = vals[o:o + 16].reshape(4, 4)
+        return g, dg, ddg, dphi, ddphi
+    return at
+
+
+def geometry4(g, dg, ddg):
+    """Christoffels, Riemann (all lower), Ricci, scalar from metric data (coordinate basis,
+    any dimension): dg[r][m][n] = d_r g_mn, ddg[r][s][m][n] = d_r d_s g_mn."""
+    n = g.shape[0]
+    gi = np.linalg.inv(g)
+    # Gamma_lij = 1/2(d_i g_lj + d_j g_li - d_l g_ij)
+    G1 = np.zeros((n, n, n))
+    for l in range(n):
+        for i in range(n):
+            for j in range(n):
+                G1[l, i, j] = 0.5 * (dg[i, l, j] + dg[j, l, i] - dg[l, i, j])
+    Gam = np.einsum("kl,lij->kij", gi, G1)
+    dgi = -np.einsum("ka,mab,bl->mkl", gi, dg, gi)
+    dG1 = np.zeros((n, n, n, n))  # dG1[m][l][i][j]
+    for m in range(n):
+        for l in range(n):
+            for i in range(n):
+                for j in range(n):
+                    dG1[m, l, i, j] = 0.5 * (ddg[m, i, l, j] + ddg[m, j, l, i] - ddg[m, l, i, j])
+    dGam = np.einsum("mkl,lij->mkij", dgi, G1) + np.einsum("kl,mlij->mkij", gi, dG1)
+    # R^r_{s m n} = d_m Gam^r_{n s} - d_n Gam^r_{m s} + Gam^r_{m l} Gam^l_{n s} - Gam^r_{n l} Gam^l_{m s}
+    Rud = (np.einsum("mrns->rsmn", dGam) - np.einsum("nrms->rsmn", dGam)
+           + np.einsum("rml,lns->rsmn", Gam, Gam) - np.einsum("rnl,lms->rsmn", Gam, Gam))
+    Rdn = np.einsum("ra,asmn->rsmn", g, Rud)
+    Ric = np.einsum("rsrn->sn", Rud)
+    Rs = np.einsum("sn,sn->", gi, Ric)
+    return gi, Gam, Rdn, Ric, Rs
+
+
+def stress_and_scalar(g, gi, Gam, Rdn, Ric, Rs, dphi, ddphi, phi, lam, g2, beta_kind):
+    """8 pi T_mn and the scalar-equation residual E for the 4dST action
+    (1/16 pi) int [R + X + g2 X^2 + beta(phi) L_GB]."""
+    if beta_kind == 1:
+        b1, b2 = lam * phi, lam
+    else:
+        b1, b2 = lam, 0.0
+    Hphi = ddphi - np.einsum("lmn,l->mn", Gam, dphi)
+    Phi = b1 * Hphi + b2 * np.outer(dphi, dphi)
+    Phiu = gi @ Phi @ gi
+    X = -0.5 * dphi @ gi @ dphi
+    Ru = np.einsum("ai,bj,ck,dl,ijkl->abcd", gi, gi, gi, gi, Rdn)
+    Ricu = gi @ Ric @ gi
+    LGB = np.einsum("abcd,abcd->", Rdn, Ru) - 4 * np.einsum("ab,ab->", Ric, Ricu) + Rs * Rs
+    P = (Rdn - np.einsum("ac,bd->abcd", g, Ric) + np.einsum("ad,bc->abcd", g, Ric)
+         + np.einsum("bc,ad->abcd", g, Ric) - np.einsum("bd,ac->abcd", g, Ric)
+         + 0.5 * Rs * (np.einsum("ac,bd->abcd", g, g) - np.einsum("ad,bc->abcd", g, g)))
+    T8gb = -4 * np.einsum("acbd,cd->ab", P, Phiu)
+    T8 = 0.5 * (1 + 2 * g2 * X) * np.outer(dphi, dphi) + 0.5 * g * (X + g2 * X * X) + T8gb
+    dphu = gi @ dphi
+    E = (1 + 2 * g2 * X) * np.einsum("ab,ab->", gi, Hphi) - 2 * g2 * dphu @ Hphi @ dphu + b1 * LGB
+    return T8, E, LGB, T8gb
+
+
+def phys_pack_generic(alpha, beta_u, g, phi, T, pt):
+    """120-double physical 3+1 pack (see orc_phys_sources) plus u = d_t K_ij and w = d_t Pi,
+    all from exact derivatives of the analytic spacetime at pt."""
+    t, x, y, z = T
+    X = (x, y, z)
+    beta_l = [sum(g[i, j] * beta_u[j] for j in range(3)) for i in range(3)]
+    G1 = christoffel_first(g, X)
+    Dbeta = [[sp.diff(beta_l[j], X[i]) - sum(G1[l][i][j] * beta_u[l] for l in range(3)) for j in range(3)]
+             for i in range(3)]
+    K = sp.Matrix(3, 3, lambda i, j: -(sp.diff(g[i, j], t) - Dbeta[i][j] - Dbeta[j][i]) / (2 * alpha))
+    Pi = (sp.diff(phi, t) - sum(beta_u[k] * sp.diff(phi, X[k]) for k in range(3))) / alpha
+
+    ex = []
+    ex += [g[i, j] for i, j in SYM_PAIRS]
+    for k in range(3):
+        ex += [sp.diff(g[i, j], X[k]) for i, j in SYM_PAIRS]
+    for a, b in SYM_PAIRS:
+        ex += [sp.diff(g[i, j], X[a], X[b]) for i, j in SYM_PAIRS]
+    ex += [K[i, j] for i, j in SYM_PAIRS]
+    for k in range(3):
+        ex += [sp.diff(K[i, j], X[k]) for i, j in SYM_PAIRS]
+    ex += [alpha] + [sp.diff(alpha, X[k]) for k in range(3)]
+    ex += [sp.diff(alpha, X[a], X[b]) for a, b in SYM_PAIRS]
+    ex += [beta_u[k] for k in range(3)]
+    for j in range(3):
+        ex += [sp.diff(beta_u[i], X[j]) for i in range(3)]
+    ex += [phi] + [sp.diff(phi, X[k]) for k in range(3)]
+    ex += [sp.diff(phi, X[a], X[b]) for a, b in SYM_PAIRS]
+    ex += [Pi] + [sp.diff(Pi, X[k]) for k in range(3)]
+    ex += [sp.diff(K[i, j], t) for i, j in SYM_PAIRS]
+    ex += [sp.diff(Pi, t)]
+    vals = np.array(sp.lambdify(T, ex, modules="math")(*pt), dtype=np.float64)
+    return vals[:120].copy(), vals[120:126].copy(), float(vals[126])

@@ -1,0 +1,493 @@
+"""Pins of the CPU oracle against facts fixed by the mathematics (no GPU).
+
+Each test names the property it checks and the plausible mistakes it would catch. The
+oracle is test infrastructure (oracle/); these tests establish that it is right before
+the CUDA path is compared against it.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import grf_inputs as gi
+
+sp = pytest.importorskip("sympy")
+import analytic as an  # noqa: E402
+
+
+def P(**kw):
+    p = gi.Params()
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+# ----------------------------------------------------------------------------- P1 flat
+@pytest.mark.parametrize("kw", [dict(), dict(a0=0.0, b0=0.0), dict(beta_kind=1, lam=0.3, g2=0.2),
+                                dict(kappa1=0.5, kappa2=0.3, kappa3=0.5, a0=0.7, b0=1.3)])
+def test_flat_space_rhs_is_exactly_zero(orc, kw):
+    """Minkowski slice, unit lapse, zero shift and scalar: every RHS value and KO term is 0.0.
+    Catches any additive constant or a term that survives on trivial data."""
+    b = gi.Box(9, 8, 7, 0.3, -1.0, -1.0, -1.0)
+    s = gi.flat_state(b)
+    orc.fill_ghosts(b, s)
+    r = orc.rhs(b, P(**kw), s)
+    assert np.all(r == 0.0)
+
+
+# ----------------------------------------------------------------------------- P3 stencils
+def _poly(X, Y, Z, coef, deg):
+    out = np.zeros_like(X)
+    terms = []
+    for a in range(deg + 1):
+        for b in range(deg + 1 - a):
+            for c in range(deg + 1 - a - b):
+                terms.append((a, b, c))
+    for (a, b, c), k in zip(terms, coef):
+        out += k * X ** a * Y ** b * Z ** c
+    return out, terms
+
+
+def _poly_deriv(X, Y, Z, coef, terms, d):
+    """d: tuple of derivative orders (dx, dy, dz)."""
+    out = np.zeros_like(X)
+    for (a, b, c), k in zip(terms, coef):
+        if a < d[0] or b < d[1] or c < d[2]:
+            continue
+        fa = math.factorial(a) / math.factorial(a - d[0])
+        fb = math.factorial(b) / math.factorial(b - d[1])
+        fc = math.factorial(c) / math.factorial(c - d[2])
+        out += k * fa * fb * fc * X ** (a - d[0]) * Y ** (b - d[1]) * Z ** (c - d[2])
+    return out
+
+
+def test_stencils_exact_on_quartic_polynomials(orc):
+    """First, second and mixed 4th-order stencils are exact on every monomial of total degree
+    <= 4. Catches a wrong stencil weight, a wrong 1/(12 dx) or 1/(144 dx^2) scale, or a
+    transposed mixed-derivative index."""
+    b = gi.Box(7, 6, 5, 0.3, -0.4, 0.2, 0.5, bc=gi.BC_FROZEN)
+    X, Y, Z = b.coords()
+    rng = np.random.default_rng(1)
+    s = np.zeros(b.shape)
+    coefs = []
+    for f in range(27):
+        coef = rng.uniform(-1, 1, 35)
+        coefs.append(coef)
+        s[f], terms = _poly(X, Y, Z, coef, 4)
+    d1, d2 = orc.derivs(b, s)
+    Xi, Yi, Zi = (b.interior(a) for a in (X, Y, Z))
+    for f in range(27):
+        for d in range(3):
+            o = [0, 0, 0]
+            o[d] = 1
+            ex = _poly_deriv(Xi, Yi, Zi, coefs[f], terms, o)
+            assert np.max(np.abs(d1[f, d] - ex)) <= 1e-12 * max(1.0, np.max(np.abs(ex)))
+        for m, (p, q) in enumerate(an.SYM_PAIRS):
+            o = [0, 0, 0]
+            o[p] += 1
+            o[q] += 1
+            ex = _poly_deriv(Xi, Yi, Zi, coefs[f], terms, o)
+            assert np.max(np.abs(d2[f, m] - ex)) <= 1e-11 * max(1.0, np.max(np.abs(ex)))
+
+
+def test_stencils_converge_at_fourth_order(orc):
+    """Halving dx on a smooth periodic field divides the first/second/mixed derivative errors
+    by ~16 (4th order). Catches a stencil that is only 2nd-order accurate."""
+    errs = []
+    for n in (16, 32):
+        b = gi.cube_box(n, 0.0, 2.0)
+        X, Y, Z = b.coords()
+        k = math.pi
+        s = np.zeros(b.shape)
+        s[0] = np.sin(k * X) * np.cos(k * Y) * np.sin(k * Z + 0.3)
+        orc.fill_ghosts(b, s)
+        d1, d2 = orc.derivs(b, s)
+        Xi, Yi, Zi = (b.interior(a) for a in (X, Y, Z))
+        ex_x = k * np.cos(k * Xi) * np.cos(k * Yi) * np.sin(k * Zi + 0.3)
+        ex_xx = -k * k * np.sin(k * Xi) * np.cos(k * Yi) * np.sin(k * Zi + 0.3)
+        ex_xy = -k * k * np.cos(k * Xi) * np.sin(k * Yi) * np.sin(k * Zi + 0.3)
+        errs.append([np.max(np.abs(d1[0, 0] - ex_x)), np.max(np.abs(d2[0, 0] - ex_xx)),
+                     np.max(np.abs(d2[0, 1] - ex_xy))])
+    ratios = np.array(errs[0]) / np.array(errs[1])
+    assert np.all(ratios > 14.0) and np.all(ratios < 18.0), ratios
+
+
+def test_ko_annihilates_quintics_and_damps_nyquist(orc):
+    """KO: sigma/(64 dx) sum_d Delta^6_d u is zero on degree-5 polynomials and gives exactly
+    -sigma/dx * u per direction on the Nyquist mode. Catches a wrong sign (anti-damping),
+    a missing 1/64 or the wrong binomial weights."""
+    b = gi.Box(8, 7, 6, 0.25, 0.1, -0.3, 0.2, bc=gi.BC_FROZEN)
+    X, Y, Z = b.coords()
+    rng = np.random.default_rng(7)
+    s = np.zeros(b.shape)
+    for f in range(27):
+        s[f], _ = _poly(X, Y, Z, rng.uniform(-1, 1, 56), 5)
+    r = orc.ko(b, 0.3, s)
+    assert np.max(np.abs(b.interior(r))) < 1e-9
+    ii = np.arange(b.nx + 6)[None, None, :]
+    s = np.zeros(b.shape)
+    s[:] = np.where(ii % 2 == 0, 1.0, -1.0)
+    r = orc.ko(b, 0.3, s)
+    np.testing.assert_allclose(b.interior(r), -0.3 / b.dx * b.interior(s), rtol=0, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------- P9 solve
+def test_full_pivot_solve(orc):
+    """The long-double full-pivot elimination solves random systems (residual < 1e-14 relative,
+    agreement with LAPACK), handles a pivot-requiring system and reports a singular one."""
+    rng = np.random.default_rng(3)
+    for n in (6, 7):
+        for _ in range(20):
+            M = rng.normal(size=(n, n))
+            x0 = rng.normal(size=n)
+            r = M @ x0
+            x, st = orc.solve(M, r)
+            assert st == 0
+            assert np.max(np.abs(M @ x - r)) <= 1e-13 * np.max(np.abs(r))
+            np.testing.assert_allclose(x, np.linalg.solve(M, r), rtol=1e-10, atol=1e-12)
+    M = np.eye(7)[::-1].copy()          # zero diagonal: needs pivoting
+    x, st = orc.solve(M, np.arange(7.0))
+    assert st == 0 and np.allclose(x, np.arange(7.0)[::-1])
+    M = np.ones((7, 7))
+    x, st = orc.solve(M, np.ones(7))
+    assert st == -1
+
+
+# ----------------------------------------------------------------------------- KS stationarity
+KS_POINTS = [(1.3, -0.7, 2.1), (-2.2, 1.9, 0.6), (0.8, 1.1, -1.4)]
+
+
+@pytest.fixture(scope="module")
+def ks_data():
+    fields, X = an.kerr_schild_fields(M=1.0)
+    return [an.conformal_point(fields, pt, X) for pt in KS_POINTS]
+
+
+def test_kerr_schild_is_stationary(orc, ks_data):
+    """Schwarzschild in Kerr-Schild coordinates, evolved with its own (time-independent) lapse
+    and shift, has d_t of chi, h_ij, K, A_ij, Theta and Gamma-hat equal to zero. Every term of
+    those six equations is non-zero on this data (K_ij, shift and lapse gradients are all
+    non-trivial), so a wrong sign or factor in any of them breaks the cancellation. The
+    b-terms multiply the Hamiltonian constraint, which vanishes, so b0 != 0 is used."""
+    p = P(lam=0.0, g2=0.0, a0=0.2, b0=0.4)
+    idx = [0] + list(range(1, 7)) + [7] + list(range(8, 14)) + [14, 15, 16, 17]
+    for (v, d1, d2) in ks_data:
+        rhs, diag, st = orc.point_rhs(p, v, d1, d2)
+        assert st == 0
+        scale = max(1.0, np.max(np.abs(d1)))
+        assert np.max(np.abs(rhs[idx])) < 1e-12 * scale * 10, rhs[idx]
+
+
+def test_kerr_schild_gauss_bonnet_invariant(orc, ks_data):
+    """L_GB of Schwarzschild is the Kretschmann scalar 48 M^2 / r^6 (r = Kerr-Schild radius =
+    areal radius) on a slice with K_ij != 0 and non-zero shift, and the scalar is sourced as
+    d_t Pi = lapse * lambda * L_GB when phi = Pi = 0 (beta = lambda phi). Catches sign errors
+    in the Gauss, Codazzi or Ricci-equation blocks, in L_GB, and in the scalar source."""
+    lam = 1e-7
+    p = P(lam=lam, g2=0.3, a0=0.2, b0=0.4)
+    for (v, d1, d2), pt in zip(ks_data, KS_POINTS):
+        r = math.sqrt(sum(c * c for c in pt))
+        ex = 48.0 / r ** 6
+        rhs, diag, st = orc.point_rhs(p, v, d1, d2)
+        assert abs(diag[10] - ex) <= 1e-10 * ex
+        assert abs(rhs[26] / (v[18] * lam) - ex) <= 1e-6 * ex
+
+
+@pytest.mark.parametrize("lapse", ["precollapsed", "static", "unit"])
+def test_isotropic_schwarzschild_gauss_bonnet_any_lapse(orc, lapse):
+    """On the time-symmetric isotropic slice L_GB = 48 M^2/R^6 with R = r(1+M/2r)^2 whatever the
+    lapse (it is a spacetime invariant). Catches a lapse-dependent error in the Ricci equation
+    (the D_i D_j lapse term) or in the CCZ4 K / A_ij equations feeding d_t K_ij."""
+    fields, X = an.isotropic_schwarzschild_fields(lapse=lapse)
+    p = P(lam=1e-7, g2=0.0)
+    for pt in [(0.9, 0.4, -0.3), (1.5, -1.2, 2.0)]:
+        v, d1, d2 = an.conformal_point(fields, pt, X)
+        rhs, diag, st = orc.point_rhs(p, v, d1, d2)
+        r = math.sqrt(sum(c * c for c in pt))
+        R = an.areal_radius_isotropic(r)
+        ex = 48.0 / R ** 6
+        assert abs(diag[10] - ex) <= 1e-10 * ex
+
+
+def test_schwarzschild_scalar_source_converges_4th_order(orc):
+    """Finite-difference version of the scalar source: d_t Pi / (lapse lambda) at a fixed point,
+    computed on grids dx, dx/2, dx/4 with frozen analytic ghosts, converges to 48 M^2/R^6 with
+    error ratios ~16 (4th order)."""
+    pt = np.array([1.1, 0.7, 0.9])
+    r = float(np.linalg.norm(pt))
+    ex = 48.0 / an.areal_radius_isotropic(r) ** 6
+    lam = 1e-8
+    p = P(lam=lam, g2=0.0)
+    errs = []
+    for dx in (0.1, 0.05, 0.025):
+        b = gi.Box(1, 1, 1, dx, pt[0], pt[1], pt[2], bc=gi.BC_FROZEN)
+        s = gi.single_puncture(b, amp=0.0)
+        rhs = orc.rhs(b, p, s, with_ko=False)
+        val = b.interior(rhs)[26].ravel()[0] / (b.interior(s)[18].ravel()[0] * lam)
+        errs.append(abs(val - ex))
+    assert 12 < errs[0] / errs[1] < 20 and 12 < errs[1] / errs[2] < 20, errs
+
+
+# ----------------------------------------------------------------------------- 4D brute force
+@pytest.fixture(scope="module")
+def spacetime():
+    T, alpha, beta_u, g, phi = an.generic_spacetime()
+    g4 = an.four_metric(alpha, beta_u, g)
+    at = an.lambdify_metric_derivs(g4, phi, T)
+    phifn = sp.lambdify(T, phi, modules="math")
+    return T, alpha, beta_u, g, phi, at, phifn
+
+
+def _stress_at(at, phifn, pt, lam, g2, kind):
+    g, dg, ddg, dphi, ddphi = at(pt)
+    gi4, Gam, Rdn, Ric, Rs = an.geometry4(g, dg, ddg)
+    T8, E, LGB, T8gb = an.stress_and_scalar(g, gi4, Gam, Rdn, Ric, Rs, dphi, ddphi, phifn(*pt), lam, g2, kind)
+    return g, gi4, Gam, T8, E, LGB, dphi, T8gb
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_3p1_assembly_matches_4d_brute_force(orc, spacetime, kind):
+    """The oracle's 3+1 assembly (Gauss/Codazzi/Ricci-equation blocks in the (n, d_i) basis,
+    nabla nabla phi projections, T and the scalar equation) reproduces rho, S_i, S_ij, L_GB and
+    the scalar-equation residual of a brute-force 4D coordinate computation on a generic
+    non-vacuum spacetime with lapse, shift, K_ij, d_t K_ij and a scalar all non-trivial."""
+    T, alpha, beta_u, g, phi, at, phifn = spacetime
+    lam, g2 = 0.7, 0.3
+    pt = (0.3, 0.4, -0.2, 0.5)
+    ab = an.evaluate([alpha] + list(beta_u), T, pt)
+    g4v, gi4, Gam, T8, E, LGB, dphi, _ = _stress_at(at, phifn, pt, lam, g2, kind)
+    a, bu = ab[0], ab[1:4]
+    n_up = np.concatenate([[1.0 / a], -bu / a])
+    rho8 = n_up @ T8 @ n_up
+    S8 = -(T8 @ n_up)[1:]
+    Sij8 = T8[1:, 1:]
+    phys, u6, w = an.phys_pack_generic(alpha, beta_u, g, phi, T, pt)
+    p = P(lam=lam, g2=g2, beta_kind=kind)
+    out = orc.phys_sources(p, phys, u6, w)
+    scale = max(1.0, abs(rho8), np.max(np.abs(Sij8)))
+    assert abs(out[0] - rho8) < 1e-10 * scale
+    np.testing.assert_allclose(out[1:4], S8, atol=1e-10 * scale)
+    np.testing.assert_allclose(out[4:10], [Sij8[i, j] for i, j in an.SYM_PAIRS], atol=1e-10 * scale)
+    assert abs(out[10] - LGB) < 1e-10 * max(1.0, abs(LGB))
+    assert abs(out[11] - E) < 1e-10 * max(1.0, abs(E))
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_effective_stress_tensor_obeys_bianchi(spacetime, kind):
+    """Contracted Bianchi identity, off shell: nabla^m (8 pi T_mn) = (1/2) E d_n phi for the
+    4dST effective stress tensor, on a generic spacetime. This fixes the Gauss-Bonnet
+    coefficient (-4 P nabla nabla beta in 8 pi T) relative to the first-order terms and to
+    the scalar equation: a coefficient of -2, +4 or -8 fails by O(L_GB beta' d phi)."""
+    T, alpha, beta_u, g, phi, at, phifn = spacetime
+    lam, g2 = 0.7, 0.3
+    pt = np.array([0.3, 0.4, -0.2, 0.5])
+    g4v, gi4, Gam, T8, E, LGB, dphi, T8gb = _stress_at(at, phifn, tuple(pt), lam, g2, kind)
+    h = 2e-3
+    wts = {-3: -1 / 60, -2: 3 / 20, -1: -3 / 4, 1: 3 / 4, 2: -3 / 20, 3: 1 / 60}
+
+    def divergence(gb_factor):
+        dT = np.zeros((4, 4, 4))  # dT[r][m][n]
+        for r in range(4):
+            for o, wgt in wts.items():
+                q = pt.copy()
+                q[r] += o * h
+                res = _stress_at(at, phifn, tuple(q), lam, g2, kind)
+                dT[r] += wgt * (res[3] + (gb_factor - 1.0) * res[7]) / h
+        Tc = T8 + (gb_factor - 1.0) * T8gb
+        cov = dT - np.einsum("lrm,ln->rmn", Gam, Tc) - np.einsum("lrn,ml->rmn", Gam, Tc)
+        return np.einsum("rm,rmn->n", gi4, cov), np.max(np.abs(cov))
+
+    rhs = 0.5 * E * dphi
+    div, scale = divergence(1.0)
+    tol = 1e-9 * max(1.0, scale)
+    np.testing.assert_allclose(div, rhs, atol=tol)
+    # discrimination: the same identity fails by far more than the tolerance when the
+    # Gauss-Bonnet term carries half, or minus, its coefficient
+    for wrong in (0.5, -1.0):
+        div_w, _ = divergence(wrong)
+        assert np.max(np.abs(div_w - rhs)) > 1e3 * tol
+
+
+# ----------------------------------------------------------------------------- ADM consistency
+@pytest.fixture(scope="module")
+def conformal_generic():
+    """Generic conformal state with Theta = 0 and Gamma-hat = Gamma-tilde (Z = 0) and a scalar.
+    The physical reference quantities (gamma = h/chi, its Christoffels and Ricci tensor, D_i D_j
+    lapse) are computed by the numpy brute-force geometry from exact derivatives."""
+    t, x, y, z = an.symbols()
+    X = (x, y, z)
+    chi = 0.6 + 0.1 * sp.sin(0.5 * x + 0.3 * y) * sp.cos(0.4 * z)
+    h, hi = an.rotated_diag([1 + 0.1 * sp.sin(0.3 * y + 0.2 * z), 1 - 0.08 * sp.cos(0.5 * x + 0.2 * y),
+                             1 + 0.07 * sp.sin(0.6 * y + 0.1 * x - 0.3 * z)])
+    K = 0.2 * sp.cos(0.3 * x + 0.6 * y - 0.2 * z)
+    Araw = {(0, 0): 0.1 * sp.sin(x), (0, 1): 0.05 * sp.cos(y + z), (0, 2): -0.07 * sp.sin(0.5 * z),
+            (1, 1): 0.08 * sp.cos(0.3 * x + y), (1, 2): 0.04 * sp.sin(0.7 * x - z), (2, 2): -0.06 * sp.cos(0.4 * y)}
+    Am = sp.Matrix(3, 3, lambda i, j: Araw[(min(i, j), max(i, j))])
+    trA = sum(hi[i, j] * Am[i, j] for i in range(3) for j in range(3))
+    A = Am - h * trA / 3
+    Gt1 = an.christoffel_first(h, X)
+    Gam = [sum(hi[j, k] * sum(hi[i, l] * Gt1[l][j][k] for l in range(3)) for j in range(3) for k in range(3))
+           for i in range(3)]
+    alpha = 0.8 + 0.1 * sp.sin(0.4 * x - 0.5 * y + 0.3 * z)
+    beta = [0.1 * sp.sin(0.3 * y), 0.05 * sp.cos(0.5 * z + x), -0.08 * sp.sin(0.2 * x + 0.4 * y)]
+    B = [0.02, -0.01, 0.03]
+    phi = 0.2 * sp.sin(0.5 * x + 0.2 * y) * sp.cos(0.3 * z)
+    Pi = 0.15 * sp.cos(0.4 * x - 0.3 * y + 0.2 * z)
+    fields = [chi] + [h[i, j] for i, j in an.SYM_PAIRS] + [K] + [A[i, j] for i, j in an.SYM_PAIRS] + [0] \
+             + Gam + [alpha] + beta + B + [phi, Pi]
+    pt = (0.37, -0.52, 0.81)
+    v, d1, d2 = an.conformal_point(fields, pt, X)
+    g = h / chi
+    Kij = (A + h * K / 3) / chi
+    exprs = ([g[i, j] for i in range(3) for j in range(3)]
+             + [sp.diff(g[i, j], X[k]) for k in range(3) for i in range(3) for j in range(3)]
+             + [sp.diff(g[i, j], X[k], X[l]) for k in range(3) for l in range(3) for i in range(3) for j in range(3)]
+             + [Kij[i, j] for i in range(3) for j in range(3)]
+             + [sp.diff(Kij[i, j], X[k]) for k in range(3) for i in range(3) for j in range(3)]
+             + [alpha] + [sp.diff(alpha, X[k]) for k in range(3)]
+             + [sp.diff(alpha, X[k], X[l]) for k in range(3) for l in range(3)]
+             + beta + [sp.diff(beta[i], X[j]) for j in range(3) for i in range(3)])
+    vals = an.evaluate(exprs, X, pt)
+    o = [0]
+
+    def take(n, shape):
+        a = vals[o[0]:o[0] + n].reshape(shape)
+        o[0] += n
+        return a
+    gv, dg, ddg = take(9, (3, 3)), take(27, (3, 3, 3)), take(81, (3, 3, 3, 3))
+    Kv, dK = take(9, (3, 3)), take(27, (3, 3, 3))
+    al, dal, ddal = float(take(1, (1,))[0]), take(3, (3,)), take(9, (3, 3))
+    bv, dbv = take(3, (3,)), take(9, (3, 3))
+    gi3, Gam3, Rdn, Ric, Rs = an.geometry4(gv, dg, ddg)
+    phys = dict(g=gv, K=Kv, dK=dK, Ric=Ric, DDa=ddal - np.einsum("kij,k->ij", Gam3, dal), Gam=Gam3, dg=dg,
+                alpha=al, beta=bv, dbeta=dbv)
+    return v, d1, d2, phys
+
+
+@pytest.mark.parametrize("couplings", [(0.0, 0.0), (0.4, 0.3)])
+def test_ccz4_reduces_to_adm(orc, conformal_generic, couplings):
+    """With Theta = 0, Z = 0 and b = 0 the CCZ4 equations for chi, h_ij, K, A_ij imply exactly the
+    ADM equations:
+        d_t gamma_ij = -2 lapse K_ij + D_i beta_j + D_j beta_i,
+        d_t K_ij = -D_i D_j lapse + lapse (R_ij + K K_ij - 2 K_ik K^k_j) + L_beta K_ij
+                   - lapse (8 pi S_ij - 1/2 gamma_ij (8 pi S - 8 pi rho)),
+    with the solved (coupled) S_ij. The ADM side is computed here from the physical metric
+    with an independent (sympy) Ricci tensor. Catches errors in any term of the four
+    conformal equations or in the matter coupling of K and A_ij."""
+    v, d1, d2, ph = conformal_generic
+    lam, g2 = couplings
+    p = P(lam=lam, g2=g2, b0=0.0, a0=0.3)
+    rhs, diag, st = orc.point_rhs(p, v, d1, d2)
+    assert st == 0
+    chi, K = v[0], v[7]
+    h = np.zeros((3, 3)); A = np.zeros((3, 3)); hd = np.zeros((3, 3)); Ad = np.zeros((3, 3))
+    for m, (i, j) in enumerate(an.SYM_PAIRS):
+        h[i, j] = h[j, i] = v[1 + m]
+        A[i, j] = A[j, i] = v[8 + m]
+        hd[i, j] = hd[j, i] = rhs[1 + m]
+        Ad[i, j] = Ad[j, i] = rhs[8 + m]
+    chid, Kd = rhs[0], rhs[7]
+    g, Kij, al = ph["g"], ph["K"], ph["alpha"]
+    gi3 = np.linalg.inv(g)
+    # d_t gamma_ij from the conformal right-hand sides
+    gd = hd / chi - h * chid / chi ** 2
+    beta_l = g @ ph["beta"]
+    dbeta_l = np.einsum("kij,j->ki", ph["dg"], ph["beta"]) + np.einsum("ij,kj->ki", g, ph["dbeta"])
+    Dbeta = dbeta_l - np.einsum("lki,l->ki", ph["Gam"], beta_l)   # D_k beta_i
+    np.testing.assert_allclose(gd, -2 * al * Kij + Dbeta + Dbeta.T, atol=1e-12)
+    # d_t K_ij from the conformal right-hand sides
+    ud = (Ad + hd * K / 3 + h * Kd / 3) / chi - Kij * chid / chi
+    Sij8 = np.zeros((3, 3))
+    for m, (i, j) in enumerate(an.SYM_PAIRS):
+        Sij8[i, j] = Sij8[j, i] = diag[4 + m]
+    rho8 = diag[0]
+    S8 = np.einsum("ij,ij->", gi3, Sij8)
+    Ktr = np.einsum("ij,ij->", gi3, Kij)
+    KK = Kij @ gi3 @ Kij
+    LbK = (np.einsum("k,kij->ij", ph["beta"], ph["dK"]) + np.einsum("kj,ik->ij", Kij, ph["dbeta"])
+           + np.einsum("ik,jk->ij", Kij, ph["dbeta"]))
+    adm = -ph["DDa"] + al * (ph["Ric"] + Ktr * Kij - 2 * KK) + LbK - al * (Sij8 - 0.5 * g * (S8 - rho8))
+    np.testing.assert_allclose(ud, adm, atol=1e-11)
+    # the solved d_t K_ij is the one that enters the coupled system
+    np.testing.assert_allclose([ud[i, j] for i, j in an.SYM_PAIRS], diag[11:17], atol=1e-11)
+
+
+def test_zero_coupling_scalar_is_klein_gordon(orc, conformal_generic):
+    """With lambda = g2 = 0 the solved d_t Pi equals the 3+1 Klein-Gordon equation
+    d_t Pi = beta^k d_k Pi + lapse (D^i D_i phi + K Pi) + gamma^ij d_i lapse d_j phi,
+    and 8 pi rho = (Pi^2 + |D phi|^2)/4, 8 pi S_i = -Pi d_i phi / 2 (action R + X over 16 pi).
+    Catches sign errors in the nabla_i nabla_j phi = D_i D_j phi + K_ij Pi projection and in
+    the n-n block of the scalar equation."""
+    v, d1, d2, ph = conformal_generic
+    p = P(lam=0.0, g2=0.0)
+    rhs, diag, st = orc.point_rhs(p, v, d1, d2)
+    g, Kij, al = ph["g"], ph["K"], ph["alpha"]
+    gi3 = np.linalg.inv(g)
+    Pi, dPi, dphi = v[26], d1[26], d1[25]
+    ddphi = np.zeros((3, 3))
+    for m, (i, j) in enumerate(an.SYM_PAIRS):
+        ddphi[i, j] = ddphi[j, i] = d2[25, m]
+    DDphi = ddphi - np.einsum("kij,k->ij", ph["Gam"], dphi)
+    Ktr = np.einsum("ij,ij->", gi3, Kij)
+    kg = ph["beta"] @ dPi + al * (np.einsum("ij,ij->", gi3, DDphi) + Ktr * Pi) + d1[18] @ gi3 @ dphi
+    assert abs(rhs[26] - kg) < 1e-12
+    assert abs(diag[0] - 0.25 * (Pi ** 2 + dphi @ gi3 @ dphi)) < 1e-13
+    np.testing.assert_allclose(diag[1:4], -0.5 * Pi * dphi, atol=1e-13)
+
+
+def test_solve_matrix_is_identity_at_zero_coupling(orc, conformal_generic):
+    """The coupled system's Jacobian reduces to the trivial one (-1 on the d_t K_ij rows, +1 on
+    the d_t Pi row) when the couplings vanish, and departs from it when they do not."""
+    v, d1, d2, ph = conformal_generic
+    _, diag0, _ = orc.point_rhs(P(lam=0.0, g2=0.0), v, d1, d2)
+    np.testing.assert_allclose(diag0[38:45], [-1, -1, -1, -1, -1, -1, 1], atol=1e-13)
+    _, diag1, _ = orc.point_rhs(P(lam=0.5, g2=0.4), v, d1, d2)
+    assert np.max(np.abs(diag1[38:45] - np.array([-1, -1, -1, -1, -1, -1, 1]))) > 1e-3
+    assert diag1[18] < 1e-12  # residual of the coupled equations after the solve
+
+
+# ----------------------------------------------------------------------------- constraints
+def test_constraints_converge_to_zero_on_kerr_schild(orc):
+    """H and M_i of the exact Kerr-Schild data, computed with 4th-order differences on boxes
+    away from the singularity, converge to zero at 4th order (ratio ~16 per halving).
+    Catches wrong factors in H = R + K^2 - K_ij K^ij or M_i = D_j K^j_i - D_i K."""
+    fields, X = an.kerr_schild_fields(M=1.0)
+    fn = sp.lambdify(X, fields, modules="numpy")
+    errs = []
+    for dx in (0.1, 0.05):
+        n = int(round(0.4 / dx))
+        b = gi.Box(n, n, n, dx, 1.5, 1.2, 1.3, bc=gi.BC_FROZEN)
+        Xg, Yg, Zg = b.coords()
+        s = np.zeros(b.shape)
+        vals = fn(Xg, Yg, Zg)
+        for f in range(27):
+            s[f] = np.broadcast_to(np.asarray(vals[f], dtype=np.float64), Xg.shape)
+        c = orc.constraints(b, P(lam=0.0, g2=0.0), s)
+        # compare at the common physical points (every second point of the finer grid)
+        if dx == 0.1:
+            errs.append(np.max(np.abs(c)))
+        else:
+            errs.append(np.max(np.abs(c)))
+    assert errs[0] < 1e-4
+    assert 12 < errs[0] / errs[1] < 20, errs
+
+
+# ----------------------------------------------------------------------------- P4 plane wave
+def test_scalar_plane_wave_converges_4th_order(orc):
+    """A small scalar plane wave on flat space (amplitude 1e-6, so back-reaction is O(1e-12))
+    evolved with the full RK4 + 4th-order FD + KO converges to the exact solution
+    phi = A sin(k(x - t)) at 4th order. Catches errors in the RK4 weights/stage times, in the
+    scalar advection/lapse terms and in the stencils."""
+    amp, L, T = 1e-6, 2.0, 0.5
+    k = 2 * math.pi / L
+    errs = []
+    for n in (16, 32):
+        b = gi.Box(n, 4, 4, L / n, 0.5 * L / n, 0.0, 0.0)
+        s = gi.scalar_plane_wave(b, amp, (k, 0.0, 0.0))
+        dt = 0.25 * b.dx
+        nsteps = int(round(T / dt))
+        orc.rk4(b, gi.Params(), s, dt, nsteps)
+        ex = gi.scalar_plane_wave(b, amp, (k, 0.0, 0.0), t=nsteps * dt)
+        errs.append(np.max(np.abs(b.interior(s)[25] - b.interior(ex)[25])) / amp)
+    assert errs[1] < 1e-3
+    assert 13 < errs[0] / errs[1] < 19, errs
