@@ -1,0 +1,321 @@
+#!/usr/bin/env python
+"""Throughput of the modified-CCZ4 + 4dST RHS/RK4 path on GB300: FP64 grid-point RK4
+updates per second, with the FP64 roofline fraction of the RK4-stage kernel.
+
+One "step" = one full RK4 step (4 fused stage kernels: stencils + pointwise RHS + 7x7 solve
++ KO + stage update) over the whole 256^3 Brill-Lindquist box (the 32^3 single-puncture box
+and the other workloads are parity-test cases). Inputs are resident in HBM for `value`; `e2e`
+repeats the measurement with the state copied from pinned host memory to the device and back
+inside every timed step. The state (3.9 GB) is larger than L2, so no L2 flush is needed.
+
+--impl reference times the CPU oracle (the baseline arm) on a bounded sample of the same
+workload on the host cores.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FP64 grid-point RK4 updates/s (mCCZ4+4∂ST) and % of FP64/HBM roofline"
+UNIT = "point-updates/s"
+
+# FP64 operations per interior point per RK4 stage kernel, counted with ncu's DP instruction
+# counters (dadd + dmul + 2*dfma) on the stage kernel ("Roofline").
+FLOP_PER_POINT_STAGE = None
+# algorithmic HBM bytes per point-update (stage-wise RK4, 27 fields, perfect stencil reuse):
+# stage 1: read u_n, write u_1 and acc (3 x 216 B); stages 2-3: read u_s, u_n, acc, write u_s, acc
+# (5 x 216 B each); stage 4: read u_3, u_n, acc, write u_n (4 x 216 B)
+BYTES_PER_POINT_UPDATE = 216 * (3 + 5 + 5 + 4)
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="bl_pair_256", choices=["bl_pair_256", "bl_pair_128", "bl_pair_64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+def workload(name):
+    import grf_inputs as gi
+    n = int(name.rsplit("_", 1)[1])
+    return gi.config_bl_pair_256(n)
+
+
+# ------------------------------------------------------------------------------ clocks
+def gpu_selector(local_rank):
+    """nvidia-smi -i argument for this process's GPU (PCI bus id when torch exposes it)."""
+    try:
+        import torch
+        pr = torch.cuda.get_device_properties(local_rank)
+        return f"{pr.pci_domain_id:08X}:{pr.pci_bus_id:02X}:{pr.pci_device_id:02X}.0"
+    except Exception:
+        return str(local_rank)
+
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), power=float(parts[3]),
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], swp=parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown"),
+                              ("swp", "sw_power_cap")):
+                if r[key].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows), "sm_max_mhz": max(r["smax"] for r in rows),
+                "power_w_max": max(r["power"] for r in rows), "samples": len(rows), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------------------ CPU oracle
+def sub_block(cfg, n):
+    """An n^3 sub-block of the workload grid (same points, same analytic data) next to the
+    upper puncture, with frozen ghosts."""
+    import grf_inputs as gi
+    box = cfg["box"]
+    i0 = box.nx // 2 - n // 2
+    k0 = int(round((3.0 - box.z0) / box.dx)) - n // 2
+    sub = gi.Box(n, n, n, box.dx, box.x0 + i0 * box.dx, box.y0 + i0 * box.dx, box.z0 + k0 * box.dx, bc=gi.BC_FROZEN)
+    return sub, gi.brill_lindquist_pair(sub)
+
+
+def oracle_sample(cfg, seconds, steps=1):
+    """Times the CPU oracle on a cube sub-block of the workload, grown until one run takes
+    about `seconds`. Returns (point-updates/s, cores, description)."""
+    import oracle
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    n = 8
+    while True:
+        sub, s = sub_block(cfg, n)
+        t0 = time.perf_counter()
+        oracle.rk4(sub, cfg["params"], s, cfg["dt"], steps)
+        el = time.perf_counter() - t0
+        if el >= 0.3 * seconds or n >= 96:
+            break
+        n = int(min(96, max(n + 4, n * (seconds / max(el, 1e-3)) ** (1 / 3))))
+    return n ** 3 * steps / el, cores, f"{steps} RK4 step(s) of a {n}^3 frozen-ghost sub-block of the workload ({el:.1f} s)"
+
+
+def run_reference(args, rank):
+    cfg = workload(args.workload)
+    if rank != 0:
+        return
+    import oracle
+    box = cfg["box"]
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    # size one step's sample so that warmup + steps fit in a few minutes
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    n = 8
+    while True:
+        sub, s = sub_block(cfg, n)
+        t0 = time.perf_counter()
+        oracle.rk4(sub, cfg["params"], s, cfg["dt"], 1)
+        el = time.perf_counter() - t0
+        if el > 0.25 * budget or n >= 64:
+            break
+        n = int(min(64, max(n + 4, n * (0.5 * budget / max(el, 1e-3)) ** (1 / 3))))
+    for _ in range(max(0, args.warmup - 1)):
+        oracle.rk4(sub, cfg["params"], sub_block(cfg, n)[1], cfg["dt"], 1)
+    states = [sub_block(cfg, n)[1] for _ in range(args.steps)]
+    t0 = time.perf_counter()
+    for s in states:
+        oracle.rk4(sub, cfg["params"], s, cfg["dt"], 1)
+    el = time.perf_counter() - t0
+    value = n ** 3 * args.steps / el
+    sample = f"each step: 1 RK4 step of a {n}^3 frozen-ghost sub-box of the {cfg['name']} workload"
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": cfg["name"], "grid": [box.nx, box.ny, box.nz], "dx": box.dx, "dt": cfg["dt"],
+                      "sample": sample},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------------------ GPU arm
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import paper_2309_06225_gb300 as grf
+    from paper_2309_06225_gb300 import build_peak
+
+    cfg = workload(args.workload)
+    box = cfg["box"]
+    params, dt = cfg["params"], cfg["dt"]
+
+    # CPU oracle baseline first (rank 0, N = 1), before any CUDA work in this process
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, cores, desc = oracle_sample(cfg, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    b = grf.box_like(box)
+    p = grf.params_like(params)
+    s0 = cfg["make_state"]()
+    state = grf.to_device(s0, b)
+    init = state.clone()
+    ws = grf.alloc_workspace(grf.grf_workspace_bytes(b, grf.GRF_OP_RK4))
+    stream = torch.cuda.current_stream()
+    npts = box.nx * box.ny * box.nz
+
+    peak = build_peak.measure()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        grf.grf_rk4_step(b, p, state, dt, 1, ws=ws, stream=stream)
+    barrier()
+    clocks = ClockSampler(gpu_selector(local_rank))
+    clocks.start()
+    time.sleep(0.3)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier()
+    ev[0].record(stream)
+    for k in range(args.steps):
+        grf.grf_rk4_step(b, p, state, dt, 1, ws=ws, stream=stream)
+        ev[k + 1].record(stream)
+    barrier()
+    clk = clocks.stop()
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    ms = ev[0].elapsed_time(ev[-1])
+    status = grf.grf_check_status()
+    finite = grf.grf_check_finite(b, state)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * npts * args.steps / (ms * 1e-3)
+
+    e2e = None
+    if not args.no_e2e:
+        host_in = torch.empty(state.shape, dtype=torch.float64, pin_memory=True)
+        host_in.copy_(init)
+        host_out = torch.empty(state.shape, dtype=torch.float64, pin_memory=True)
+        nbytes = state.numel() * 8
+        for _ in range(1):
+            state.copy_(host_in, non_blocking=True)
+            grf.grf_rk4_step(b, p, state, dt, 1, ws=ws, stream=stream)
+            host_out.copy_(state, non_blocking=True)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            state.copy_(host_in, non_blocking=True)
+            grf.grf_rk4_step(b, p, state, dt, 1, ws=ws, stream=stream)
+            host_out.copy_(state, non_blocking=True)
+        e1.record(stream)
+        barrier()
+        ems = e0.elapsed_time(e1)
+        if dist is not None:
+            t = torch.tensor([ems], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": world * npts * args.steps / (ems * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "ms_per_step": ems / args.steps,
+               "path": "pinned host -> device, grf_rk4_step (1 step), device -> pinned host, every step"}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    launch_ms = ms / (4 * args.steps)  # the timed region is 4 stage kernels + 1 small ghost fill per step
+    roof = {"bound": "alu", "unit": "TFLOP/s", "peak": peak,
+            "peak_source": "measured FP64 FMA microbenchmark (libgrf_peak.so) in this run",
+            "peak_nominal": FP64_NOMINAL_TFLOPS, "kernel": "rk4_stage_kernel"}
+    if FLOP_PER_POINT_STAGE is not None:
+        achieved = FLOP_PER_POINT_STAGE * npts / (launch_ms * 1e-3) / 1e12
+        roof.update({"achieved": achieved, "frac": achieved / peak, "flop_per_point_stage": FLOP_PER_POINT_STAGE})
+    else:
+        roof.update({"achieved": None, "frac": None})
+    roof["traffic"] = None
+    roof["hbm_frac_of_measured"] = BYTES_PER_POINT_UPDATE * value / 6771.1e9
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": cfg["name"], "grid": [box.nx, box.ny, box.nz], "ghosts": 3, "dx": box.dx,
+                      "dt": dt, "beta": "lambda phi^2/2", "lambda": params.lam, "g2": params.g2,
+                      "state_bytes": int(state.numel() * 8), "l2": "inputs larger than L2 (no flush needed)",
+                      "parallelism": f"{world} independent replica(s), one box per GPU"},
+           "gpu_launches": 5 * args.steps, "roofline": roof, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
+           "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
+           "status": {"solve": status, "finite": finite}}
+    print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", args.gpus if "RANK" in os.environ else 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

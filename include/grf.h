@@ -1,0 +1,133 @@
+/*
+ * grf.h -- C ABI of the GB300 library (libgrf.so) for the modified-CCZ4 + 4-derivative
+ * scalar-tensor (4dST) evolution hot path of GRFolres (arXiv:2309.06225).
+ *
+ * What is computed (paper, section "Key features"): the fields of the 4dST theory
+ * (R + X + g2 X^2 + beta(phi) L_GB, X = -1/2 (d phi)^2) evolved in the modified moving
+ * puncture gauge with the CCZ4 formulation, 4th-order centred finite differences and
+ * 4th-order Runge-Kutta time integration, on a ghosted 3D box with periodic (or frozen)
+ * ghosts, plus Kreiss-Oliger dissipation and constraint monitoring ("Diagnostics").
+ * The Gauss-Bonnet and X^2 couplings make d_t K_ij and d_t Pi appear on both sides of
+ * the equations ("still second order equations of motion", section "Summary"): they are
+ * found by a 7x7 linear solve at every grid point.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * State layout: 27 FP64 fields, structure of arrays, field-major:
+ *     state[f * fstride + (k * (ny + 2 ng) + j) * pitch + i]
+ * with ghosted indices 0 <= i < nx + 2 ng (x fastest), fstride = (nz + 2 ng) * (ny + 2 ng) * pitch.
+ * Field order: 0 chi | 1-6 h11 h12 h13 h22 h23 h33 | 7 K | 8-13 A11..A33 | 14 Theta |
+ *              15-17 Gamma^i | 18 lapse | 19-21 shift^i | 22-24 B^i | 25 phi | 26 Pi.
+ * Ownership: every double* argument is a DEVICE pointer owned by the caller, except where
+ * marked "host". The library never allocates or frees memory; scratch space is passed in
+ * as `ws` (device, 256-byte aligned, at least grf_workspace_bytes(box, op) bytes).
+ * Streams: every call is asynchronous on `stream` (0 = legacy default stream) unless it
+ * says it synchronises.
+ * Errors: 0 on success, a negative GRF_E* code otherwise; grf_error_string() describes it.
+ * A launch failure is returned as GRF_ECUDA and its CUDA message is kept for
+ * grf_last_cuda_error(). Per-point failures detected inside kernels (a singular coupled
+ * system) are latched in a device flag and reported by grf_check_status().
+ */
+#ifndef GRF_H
+#define GRF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* grf_stream_t; /* same type as cudaStream_t */
+
+enum {
+    GRF_OK = 0,
+    GRF_EINVAL = -1,       /* bad sizes, null pointers, ng != 3, pitch too small */
+    GRF_EWORKSPACE = -2,   /* ws too small or misaligned */
+    GRF_ECUDA = -3,        /* a CUDA call failed; see grf_last_cuda_error() */
+    GRF_ENONFINITE = -4,   /* non-finite value found by grf_check_finite() */
+    GRF_ESINGULAR = -5,    /* some point's coupled 7x7 system had a vanishing pivot */
+    GRF_ETIMEOUT = -6      /* a bounded device-side wait gave up */
+};
+
+enum { GRF_BC_PERIODIC = 0, GRF_BC_FROZEN = 1 };
+enum { GRF_BETA_LINEAR = 0, GRF_BETA_QUADRATIC = 1 };
+enum { GRF_OP_RHS = 0, GRF_OP_RK4 = 1, GRF_OP_CONSTRAINTS = 2 };
+
+/* Grid box. Points sit at x = x0 + (i - ng) dx (ghosted index i); ng must be 3. */
+typedef struct {
+    int nx, ny, nz;       /* interior points per axis, each >= 1 (periodic: >= 3) */
+    int ng;               /* ghost layers: must be 3 */
+    double dx;            /* grid spacing, > 0 */
+    double x0, y0, z0;    /* coordinates of interior point (0,0,0) */
+    int bc;               /* GRF_BC_PERIODIC: ghosts refilled by periodic wrap;
+                             GRF_BC_FROZEN: ghosts are read as given and never written */
+    long long pitch;      /* doubles per x row, >= nx + 2 ng */
+} grf_box;
+
+/* Theory, gauge and numerical parameters (modified puncture gauge with constant a, b;
+ * beta(phi) = lambda phi or lambda phi^2 / 2; the X^2 coupling is the constant g2). */
+typedef struct {
+    double kappa1, kappa2, kappa3;   /* CCZ4 constraint damping */
+    double shift_F, eta;             /* Gamma-driver: d_t shift = F B / (1 + a) - ..., d_t B = d_t Gamma - eta B */
+    double a0, b0;                   /* modified-gauge functions a(x) = a0, b(x) = b0 (0, 0: standard gauge) */
+    double lambda, g2;               /* Gauss-Bonnet coupling constant, X^2 coupling */
+    double sigma_ko;                 /* Kreiss-Oliger strength sigma */
+    double min_chi, min_lapse;       /* floors applied after every RK stage */
+    int beta_kind;                   /* GRF_BETA_LINEAR or GRF_BETA_QUADRATIC */
+    int enforce_algebraic;           /* 1: trace-free A_ij and the floors after every stage */
+} grf_params;
+
+/* d_t of all 27 fields at the interior points of `state` (modified CCZ4 + 4dST, section
+ * "Key features"), including Kreiss-Oliger dissipation sigma/(64 dx) sum_d Delta^6_d.
+ * For GRF_BC_PERIODIC the ghost layers of `state` are first refilled by periodic wrap
+ * (the interior is not modified); for GRF_BC_FROZEN they are read as given.
+ * rhs: same layout as state; only interior entries are written. ws may be NULL. */
+int grf_rhs(const grf_box* box, const grf_params* params, double* state, double* rhs,
+            void* ws, size_t ws_bytes, grf_stream_t stream);
+
+/* Advance `state` in place by nsteps classical RK4 steps of size dt (section "Key
+ * features": 4th-order Runge-Kutta). k_s = RHS(u_{s-1}) with dissipation; u_1 = u_n +
+ * dt/2 k_1, u_2 = u_n + dt/2 k_2, u_3 = u_n + dt k_3, u_{n+1} = u_n + dt/6 (k_1 + 2k_2 +
+ * 2k_3 + k_4); every written state gets the algebraic enforcement when enabled.
+ * ws: >= grf_workspace_bytes(box, GRF_OP_RK4) bytes (two stage states + an accumulator). */
+int grf_rk4_step(const grf_box* box, const grf_params* params, double* state, double dt,
+                 int nsteps, void* ws, size_t ws_bytes, grf_stream_t stream);
+
+/* Hamiltonian and momentum constraints (section "Key features", Diagnostics):
+ *   H = R + K^2 - K_ij K^ij - 16 pi rho,  M_i = D_j K^j_i - D_i K - 8 pi S_i,
+ * with the full 4dST rho and S_i. out4: device, 4 fields in the state layout (H, M1, M2,
+ * M3; interior entries written). norms_host (host, may be NULL): 8 doubles
+ * {L2(H), max|H|, L2(M1), max|M1|, L2(M2), max|M2|, L2(M3), max|M3|} over the interior,
+ * L2 = sqrt(mean of squares). Synchronises `stream` when norms_host is given.
+ * ws: >= grf_workspace_bytes(box, GRF_OP_CONSTRAINTS) bytes when norms_host is given. */
+int grf_constraints(const grf_box* box, const grf_params* params, double* state, double* out4,
+                    double* norms_host, void* ws, size_t ws_bytes, grf_stream_t stream);
+
+/* rhs_accum += sigma/(64 dx) sum_{d=x,y,z} (u_-3 - 6u_-2 + 15u_-1 - 20u_0 + 15u_+1 - 6u_+2 + u_+3)
+ * for all 27 fields at the interior points (Kreiss-Oliger dissipation). Ghosts of
+ * `state` must be valid (call grf_fill_ghosts first for periodic boxes). */
+int grf_ko_dissipation(const grf_box* box, double sigma, const double* state, double* rhs_accum,
+                       grf_stream_t stream);
+
+/* Periodic wrap of the 3 ghost layers of all 27 fields (no-op for GRF_BC_FROZEN). */
+int grf_fill_ghosts(const grf_box* box, double* state, grf_stream_t stream);
+
+/* Scratch bytes needed by an operation (GRF_OP_*) on this machine. */
+size_t grf_workspace_bytes(const grf_box* box, int op);
+
+/* Returns (and clears) the per-point status latched by kernels since the last call:
+ * GRF_OK or GRF_ESINGULAR. Synchronises `stream`. */
+int grf_check_status(grf_stream_t stream);
+
+/* GRF_ENONFINITE if any interior value of the 27 fields is NaN/Inf, else GRF_OK.
+ * ws: >= 256 bytes. Synchronises `stream`. */
+int grf_check_finite(const grf_box* box, const double* state, void* ws, size_t ws_bytes,
+                     grf_stream_t stream);
+
+const char* grf_error_string(int code);
+const char* grf_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GRF_H */

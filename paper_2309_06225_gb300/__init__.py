@@ -1,0 +1,210 @@
+"""Python binding of libgrf.so, the GB300 C-ABI library for the modified-CCZ4 + 4dST
+evolution (GRFolres, arXiv:2309.06225).
+
+Argument marshalling only: every computation runs in the library's CUDA kernels. PyTorch
+provides device memory and streams. There is no CPU fallback: if libgrf.so is missing or
+cannot be loaded, importing a function raises.
+
+State tensors are float64 CUDA tensors of shape (27, nz+6, ny+6, pitch) (field-major,
+ghosted, x fastest, rows padded to `pitch` doubles); see include/grf.h for the layout and
+the meaning of every argument.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgrf.so")
+
+GRF_OK, GRF_EINVAL, GRF_EWORKSPACE, GRF_ECUDA, GRF_ENONFINITE, GRF_ESINGULAR, GRF_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+GRF_BC_PERIODIC, GRF_BC_FROZEN = 0, 1
+GRF_BETA_LINEAR, GRF_BETA_QUADRATIC = 0, 1
+GRF_OP_RHS, GRF_OP_RK4, GRF_OP_CONSTRAINTS = 0, 1, 2
+NFIELDS, NG = 27, 3
+
+
+class grf_box(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("ng", C.c_int), ("dx", C.c_double),
+                ("x0", C.c_double), ("y0", C.c_double), ("z0", C.c_double), ("bc", C.c_int),
+                ("pitch", C.c_longlong)]
+
+
+class grf_params(C.Structure):
+    _fields_ = [("kappa1", C.c_double), ("kappa2", C.c_double), ("kappa3", C.c_double),
+                ("shift_F", C.c_double), ("eta", C.c_double), ("a0", C.c_double), ("b0", C.c_double),
+                ("lambda_", C.c_double), ("g2", C.c_double), ("sigma_ko", C.c_double),
+                ("min_chi", C.c_double), ("min_lapse", C.c_double),
+                ("beta_kind", C.c_int), ("enforce_algebraic", C.c_int)]
+
+
+class GrfError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        msg = f"{what}: {lib().grf_error_string(code).decode()} (code {code})"
+        if code == GRF_ECUDA:
+            msg += f": {lib().grf_last_cuda_error().decode()}"
+        super().__init__(msg)
+
+
+_lib = None
+_VP = C.c_void_p
+
+
+def lib():
+    """Loads libgrf.so (raises if it is missing: there is no fallback path)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libgrf.so not built ({LIB_PATH}); run paper_2309_06225_gb300/build.py")
+        L = C.CDLL(LIB_PATH)
+        B, P = C.POINTER(grf_box), C.POINTER(grf_params)
+        L.grf_rhs.argtypes = [B, P, _VP, _VP, _VP, C.c_size_t, _VP]
+        L.grf_rk4_step.argtypes = [B, P, _VP, C.c_double, C.c_int, _VP, C.c_size_t, _VP]
+        L.grf_constraints.argtypes = [B, P, _VP, _VP, C.POINTER(C.c_double), _VP, C.c_size_t, _VP]
+        L.grf_ko_dissipation.argtypes = [B, C.c_double, _VP, _VP, _VP]
+        L.grf_fill_ghosts.argtypes = [B, _VP, _VP]
+        L.grf_workspace_bytes.argtypes = [B, C.c_int]
+        L.grf_workspace_bytes.restype = C.c_size_t
+        L.grf_check_status.argtypes = [_VP]
+        L.grf_check_finite.argtypes = [B, _VP, _VP, C.c_size_t, _VP]
+        L.grf_error_string.argtypes = [C.c_int]
+        L.grf_error_string.restype = C.c_char_p
+        L.grf_last_cuda_error.restype = C.c_char_p
+        for name in ("grf_rhs", "grf_rk4_step", "grf_constraints", "grf_ko_dissipation", "grf_fill_ghosts",
+                     "grf_check_status", "grf_check_finite"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+# ------------------------------------------------------------------------------ marshalling
+def pitch_for(nx):
+    """Row pitch in doubles: nx + 6 rounded up to a multiple of 4 (32-byte rows)."""
+    return ((nx + 2 * NG + 3) // 4) * 4
+
+
+def make_box(nx, ny, nz, dx, x0=0.0, y0=0.0, z0=0.0, bc=GRF_BC_PERIODIC, pitch=None) -> grf_box:
+    return grf_box(int(nx), int(ny), int(nz), NG, float(dx), float(x0), float(y0), float(z0), int(bc),
+                   int(pitch if pitch is not None else pitch_for(nx)))
+
+
+def box_like(b, pitch=None) -> grf_box:
+    """grf_box from any object with nx, ny, nz, dx, x0, y0, z0, bc attributes."""
+    return make_box(b.nx, b.ny, b.nz, b.dx, b.x0, b.y0, b.z0, b.bc, pitch)
+
+
+def params_like(p) -> grf_params:
+    """grf_params from any object with the parameter attributes (lambda under `lam`)."""
+    return grf_params(p.kappa1, p.kappa2, p.kappa3, p.shift_F, p.eta, p.a0, p.b0, p.lam, p.g2, p.sigma_ko,
+                      p.min_chi, p.min_lapse, int(p.beta_kind), int(p.enforce_algebraic))
+
+
+def state_shape(box: grf_box, nfields=NFIELDS):
+    return (nfields, box.nz + 2 * NG, box.ny + 2 * NG, box.pitch)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def alloc_state(box: grf_box, nfields=NFIELDS, device="cuda"):
+    torch = _torch()
+    return torch.zeros(state_shape(box, nfields), dtype=torch.float64, device=device)
+
+
+def to_device(state_np, box: grf_box, device="cuda", out=None):
+    """Copies a (27, nz+6, ny+6, nx+6) numpy array into a padded device tensor."""
+    torch = _torch()
+    nxg = box.nx + 2 * NG
+    if out is None:
+        out = alloc_state(box, state_np.shape[0], device)
+    out[..., :nxg].copy_(torch.from_numpy(np.ascontiguousarray(state_np)))
+    return out
+
+
+def to_host(t, box: grf_box):
+    return t[..., :box.nx + 2 * NG].cpu().numpy()
+
+
+def alloc_workspace(nbytes, device="cuda"):
+    torch = _torch()
+    ws = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+    assert ws.data_ptr() % 256 == 0
+    return ws
+
+
+def _stream(stream):
+    if stream is None:
+        return _VP(_torch().cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return _VP(stream)
+    return _VP(stream.cuda_stream)
+
+
+def _dev(t):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous() and str(t.dtype) in ("torch.float64", "torch.uint8")
+    return _VP(t.data_ptr())
+
+
+def _check(code, what):
+    if code != GRF_OK:
+        raise GrfError(code, what)
+    return code
+
+
+# ------------------------------------------------------------------------------ entry points
+def grf_workspace_bytes(box: grf_box, op: int) -> int:
+    return int(lib().grf_workspace_bytes(C.byref(box), int(op)))
+
+
+def grf_fill_ghosts(box: grf_box, state, stream=None):
+    return _check(lib().grf_fill_ghosts(C.byref(box), _dev(state), _stream(stream)), "grf_fill_ghosts")
+
+
+def grf_rhs(box: grf_box, params: grf_params, state, rhs, ws=None, stream=None):
+    nb = 0 if ws is None else ws.numel()
+    return _check(lib().grf_rhs(C.byref(box), C.byref(params), _dev(state), _dev(rhs), _dev(ws), nb,
+                                _stream(stream)), "grf_rhs")
+
+
+def grf_rk4_step(box: grf_box, params: grf_params, state, dt, nsteps, ws=None, stream=None):
+    if ws is None:
+        ws = alloc_workspace(grf_workspace_bytes(box, GRF_OP_RK4), state.device)
+    return _check(lib().grf_rk4_step(C.byref(box), C.byref(params), _dev(state), float(dt), int(nsteps), _dev(ws),
+                                     ws.numel(), _stream(stream)), "grf_rk4_step")
+
+
+def grf_constraints(box: grf_box, params: grf_params, state, out4, norms=True, ws=None, stream=None):
+    """Returns the 8 norms {L2(H), max|H|, L2(M1), max|M1|, ...} when norms=True (synchronises)."""
+    host = (C.c_double * 8)() if norms else None
+    if norms and ws is None:
+        ws = alloc_workspace(grf_workspace_bytes(box, GRF_OP_CONSTRAINTS), state.device)
+    nb = 0 if ws is None else ws.numel()
+    _check(lib().grf_constraints(C.byref(box), C.byref(params), _dev(state), _dev(out4), host, _dev(ws), nb,
+                                 _stream(stream)), "grf_constraints")
+    return np.array(list(host)) if norms else None
+
+
+def grf_ko_dissipation(box: grf_box, sigma, state, rhs_accum, stream=None):
+    return _check(lib().grf_ko_dissipation(C.byref(box), float(sigma), _dev(state), _dev(rhs_accum),
+                                           _stream(stream)), "grf_ko_dissipation")
+
+
+def grf_check_status(stream=None):
+    return int(lib().grf_check_status(_stream(stream)))
+
+
+def grf_check_finite(box: grf_box, state, ws=None, stream=None):
+    if ws is None:
+        ws = alloc_workspace(256, state.device)
+    return int(lib().grf_check_finite(C.byref(box), _dev(state), _dev(ws), ws.numel(), _stream(stream)))
+
+
+def grf_error_string(code: int) -> str:
+    return lib().grf_error_string(int(code)).decode()

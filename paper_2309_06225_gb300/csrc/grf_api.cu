@@ -1,0 +1,300 @@
+// C-ABI entry points of libgrf.so (declared in include/grf.h).
+#include <cstdio>
+#include <cstring>
+#include <cstdint>
+
+#include "grf.h"
+#include "grf_kernels.cuh"
+#include "grf_launch.h"
+
+namespace grf {
+
+__global__ void ko_kernel(Geom g, const double* __restrict__ s, double* __restrict__ rhs, double ko) {
+    int i, j, k;
+    if (!interior_thread(g, i, j, k)) return;
+    const long long p = gidx(g, i + NG, j + NG, k + NG);
+    for (int f = 0; f < NFIELDS; ++f) rhs[f * g.fstride + p] += ko * ko6(s + f * g.fstride, p, g.pitch, g.plane);
+}
+
+// Periodic ghost fill: one thread per ghosted (i, j) column and field; walks k.
+__global__ void ghost_fill_kernel(Geom g, double* __restrict__ s) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int f = blockIdx.z;
+    if (i >= g.NX || j >= g.NY) return;
+    auto wrap = [](int a, int n) { int x = (a - NG) % n; if (x < 0) x += n; return x + NG; };
+    const int wi = wrap(i, g.nx), wj = wrap(j, g.ny);
+    const bool ghost_ij = (wi != i) || (wj != j);
+    double* u = s + f * g.fstride;
+    for (int k = 0; k < g.NZ; ++k) {
+        const int wk = wrap(k, g.nz);
+        if (!ghost_ij && wk == k) continue;
+        u[gidx(g, i, j, k)] = u[gidx(g, wi, wj, wk)];
+    }
+}
+
+// Deterministic final reduction of the per-block partials (single block, fixed order).
+__global__ void norms_final_kernel(const double* __restrict__ part, long long nblocks, double npts, double* __restrict__ out8) {
+    __shared__ double red[8][256];
+    const int t = threadIdx.x;
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (long long b = t; b < nblocks; b += 256)
+        for (int m = 0; m < 8; ++m) acc[m] = (m & 1) ? fmax(acc[m], part[b * 8 + m]) : acc[m] + part[b * 8 + m];
+    for (int m = 0; m < 8; ++m) red[m][t] = acc[m];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (t < w)
+            for (int m = 0; m < 8; ++m)
+                red[m][t] = (m & 1) ? fmax(red[m][t], red[m][t + w]) : red[m][t] + red[m][t + w];
+        __syncthreads();
+    }
+    if (t == 0)
+        for (int m = 0; m < 8; ++m) out8[m] = (m & 1) ? red[m][0] : sqrt(red[m][0] / npts);
+}
+
+__global__ void finite_kernel(Geom g, const double* __restrict__ s, int* flag) {
+    int i, j, k;
+    if (!interior_thread(g, i, j, k)) return;
+    const long long p = gidx(g, i + NG, j + NG, k + NG);
+    for (int f = 0; f < NFIELDS; ++f)
+        if (!isfinite(s[f * g.fstride + p])) { atomicOr(flag, 1); return; }
+}
+
+}  // namespace grf
+
+using namespace grf;
+
+namespace {
+
+char g_cuda_msg[256] = "";
+__device__ int g_status;
+
+int cuda_fail(cudaError_t e) {
+    std::snprintf(g_cuda_msg, sizeof(g_cuda_msg), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+    return GRF_ECUDA;
+}
+
+int check_launch() {
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GRF_OK : cuda_fail(e);
+}
+
+bool box_ok(const grf_box* b) {
+    if (!b) return false;
+    if (b->ng != 3 || b->nx < 1 || b->ny < 1 || b->nz < 1 || !(b->dx > 0.0)) return false;
+    if (b->pitch < (long long)b->nx + 6) return false;
+    if (b->bc != GRF_BC_PERIODIC && b->bc != GRF_BC_FROZEN) return false;
+    if (b->bc == GRF_BC_PERIODIC && (b->nx < 3 || b->ny < 3 || b->nz < 3)) return false;
+    return true;
+}
+
+Geom make_geom(const grf_box* b) {
+    Geom g;
+    g.nx = b->nx; g.ny = b->ny; g.nz = b->nz;
+    g.NX = b->nx + 6; g.NY = b->ny + 6; g.NZ = b->nz + 6;
+    g.pitch = b->pitch;
+    g.plane = b->pitch * g.NY;
+    g.fstride = g.plane * g.NZ;
+    g.dx = b->dx;
+    g.periodic = (b->bc == GRF_BC_PERIODIC);
+    return g;
+}
+
+bool params_ok(const grf_params* p) {
+    if (!p) return false;
+    if (p->beta_kind != GRF_BETA_LINEAR && p->beta_kind != GRF_BETA_QUADRATIC) return false;
+    if (!(1.0 + p->a0 > 0.0) || !(1.0 + p->b0 > 0.0)) return false;
+    return true;
+}
+
+Coeffs make_coeffs(const grf_params* p) {
+    Coeffs c;
+    c.kappa1 = p->kappa1; c.kappa2 = p->kappa2; c.kappa3 = p->kappa3;
+    c.shift_F = p->shift_F; c.eta = p->eta; c.lam = p->lambda; c.g2 = p->g2;
+    c.inv_1pa = 1.0 / (1.0 + p->a0);
+    c.a_1pa = p->a0 / (1.0 + p->a0);
+    c.bK = 3.0 * p->b0 / (4.0 * (1.0 + p->b0));
+    c.bTh = 1.0 / (2.0 * (1.0 + p->b0));
+    c.beta_kind = p->beta_kind;
+    return c;
+}
+
+const dim3 kBlock(32, 4, 1);
+
+dim3 interior_grid(const Geom& g) {
+    return dim3((g.nx + kBlock.x - 1) / kBlock.x, (g.ny + kBlock.y - 1) / kBlock.y, (g.nz + kBlock.z - 1) / kBlock.z);
+}
+
+size_t state_bytes(const Geom& g) { return sizeof(double) * (size_t)NFIELDS * (size_t)g.fstride; }
+
+int* status_ptr() {
+    int* p = nullptr;
+    cudaGetSymbolAddress((void**)&p, g_status);
+    return p;
+}
+
+int fill_ghosts(const Geom& g, double* s, cudaStream_t st) {
+    if (!g.periodic) return GRF_OK;
+    dim3 blk(32, 8, 1), grd((g.NX + 31) / 32, (g.NY + 7) / 8, NFIELDS);
+    ghost_fill_kernel<<<grd, blk, 0, st>>>(g, s);
+    return check_launch();
+}
+
+size_t constraint_partials(const Geom& g) {
+    dim3 grd = interior_grid(g);
+    return (size_t)grd.x * grd.y * grd.z;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* grf_error_string(int code) {
+    switch (code) {
+        case GRF_OK: return "ok";
+        case GRF_EINVAL: return "invalid argument (sizes, pointers, ng != 3, pitch, bc or parameters)";
+        case GRF_EWORKSPACE: return "workspace too small or not 256-byte aligned";
+        case GRF_ECUDA: return "CUDA error (see grf_last_cuda_error)";
+        case GRF_ENONFINITE: return "non-finite value in the state";
+        case GRF_ESINGULAR: return "singular coupled 7x7 system at some grid point";
+        case GRF_ETIMEOUT: return "bounded device wait timed out";
+        default: return "unknown error code";
+    }
+}
+
+const char* grf_last_cuda_error(void) { return g_cuda_msg; }
+
+size_t grf_workspace_bytes(const grf_box* box, int op) {
+    if (!box_ok(box)) return 0;
+    Geom g = make_geom(box);
+    switch (op) {
+        case GRF_OP_RHS: return 0;
+        case GRF_OP_RK4: return 3 * state_bytes(g);
+        case GRF_OP_CONSTRAINTS: return (constraint_partials(g) * 8 + 8) * sizeof(double) + 256;
+        default: return 0;
+    }
+}
+
+int grf_fill_ghosts(const grf_box* box, double* state, grf_stream_t stream) {
+    if (!box_ok(box) || !state) return GRF_EINVAL;
+    return fill_ghosts(make_geom(box), state, (cudaStream_t)stream);
+}
+
+int grf_rhs(const grf_box* box, const grf_params* params, double* state, double* rhs, void* ws, size_t ws_bytes,
+            grf_stream_t stream) {
+    (void)ws; (void)ws_bytes;
+    if (!box_ok(box) || !params_ok(params) || !state || !rhs) return GRF_EINVAL;
+    Geom g = make_geom(box);
+    cudaStream_t st = (cudaStream_t)stream;
+    int r = fill_ghosts(g, state, st);
+    if (r) return r;
+    launch_rhs(interior_grid(g), kBlock, st, g, make_coeffs(params), state, rhs, params->sigma_ko / (64.0 * box->dx),
+               status_ptr());
+    return check_launch();
+}
+
+int grf_ko_dissipation(const grf_box* box, double sigma, const double* state, double* rhs_accum, grf_stream_t stream) {
+    if (!box_ok(box) || !state || !rhs_accum) return GRF_EINVAL;
+    Geom g = make_geom(box);
+    ko_kernel<<<interior_grid(g), kBlock, 0, (cudaStream_t)stream>>>(g, state, rhs_accum, sigma / (64.0 * box->dx));
+    return check_launch();
+}
+
+int grf_rk4_step(const grf_box* box, const grf_params* params, double* state, double dt, int nsteps, void* ws,
+                 size_t ws_bytes, grf_stream_t stream) {
+    if (!box_ok(box) || !params_ok(params) || !state || nsteps < 0) return GRF_EINVAL;
+    Geom g = make_geom(box);
+    const size_t sb = state_bytes(g);
+    if (!ws || ws_bytes < 3 * sb || ((uintptr_t)ws & 255)) return GRF_EWORKSPACE;
+    if (nsteps == 0) return GRF_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    double* A = (double*)ws;
+    double* B = (double*)((char*)ws + sb);
+    double* acc = (double*)((char*)ws + 2 * sb);
+    int r = fill_ghosts(g, state, st);
+    if (r) return r;
+    if (!g.periodic) {  // frozen ghosts: the stage buffers carry the caller's ghosts
+        cudaError_t e = cudaMemcpyAsync(A, state, sb, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(B, state, sb, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    const Coeffs c = make_coeffs(params);
+    StageArgs a;
+    a.dt = dt;
+    a.ko = params->sigma_ko / (64.0 * box->dx);
+    a.min_chi = params->min_chi;
+    a.min_lapse = params->min_lapse;
+    a.enforce = params->enforce_algebraic;
+    a.status = status_ptr();
+    a.un = state;
+    a.acc = acc;
+    const dim3 grd = interior_grid(g);
+    for (int n = 0; n < nsteps; ++n) {
+        a.src = state; a.dst = A;
+        launch_stage(0, grd, kBlock, st, g, c, a);
+        a.src = A; a.dst = B;
+        launch_stage(1, grd, kBlock, st, g, c, a);
+        a.src = B; a.dst = A;
+        launch_stage(2, grd, kBlock, st, g, c, a);
+        a.src = A; a.dst = state;
+        launch_stage(3, grd, kBlock, st, g, c, a);
+        r = check_launch();
+        if (r) return r;
+    }
+    return GRF_OK;
+}
+
+int grf_constraints(const grf_box* box, const grf_params* params, double* state, double* out4, double* norms_host,
+                    void* ws, size_t ws_bytes, grf_stream_t stream) {
+    if (!box_ok(box) || !params_ok(params) || !state || !out4) return GRF_EINVAL;
+    Geom g = make_geom(box);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t nb = constraint_partials(g);
+    if (norms_host) {
+        if (!ws || ws_bytes < (nb * 8 + 8) * sizeof(double) || ((uintptr_t)ws & 255)) return GRF_EWORKSPACE;
+    }
+    int r = fill_ghosts(g, state, st);
+    if (r) return r;
+    double* part = norms_host ? (double*)ws : nullptr;
+    launch_constraints(interior_grid(g), kBlock, st, g, make_coeffs(params), state, out4, part);
+    r = check_launch();
+    if (r || !norms_host) return r;
+    double* out8 = part + nb * 8;
+    norms_final_kernel<<<1, 256, 0, st>>>(part, (long long)nb, (double)g.nx * g.ny * g.nz, out8);
+    r = check_launch();
+    if (r) return r;
+    cudaError_t e = cudaMemcpyAsync(norms_host, out8, 8 * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? GRF_OK : cuda_fail(e);
+}
+
+int grf_check_status(grf_stream_t stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    int h = 0, z = 0;
+    e = cudaMemcpyFromSymbol(&h, g_status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_status, &z, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e);
+    return h ? GRF_ESINGULAR : GRF_OK;
+}
+
+int grf_check_finite(const grf_box* box, const double* state, void* ws, size_t ws_bytes, grf_stream_t stream) {
+    if (!box_ok(box) || !state) return GRF_EINVAL;
+    if (!ws || ws_bytes < 256 || ((uintptr_t)ws & 255)) return GRF_EWORKSPACE;
+    Geom g = make_geom(box);
+    cudaStream_t st = (cudaStream_t)stream;
+    int* flag = (int*)ws;
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int), st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    finite_kernel<<<interior_grid(g), kBlock, 0, st>>>(g, state, flag);
+    int r = check_launch();
+    if (r) return r;
+    int h = 0;
+    e = cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return h ? GRF_ENONFINITE : GRF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,176 @@
+// Grid kernels of the GB300 path: stencil gather, fused RK4 stage, RHS, KO dissipation,
+// periodic ghost fill, constraints and their norms.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "grf_point.cuh"
+
+namespace grf {
+
+struct Geom {
+    int nx, ny, nz;          // interior points
+    int NX, NY, NZ;          // ghosted extents (n + 6)
+    long long pitch;         // doubles per x row
+    long long plane;         // pitch * NY
+    long long fstride;       // plane * NZ
+    double dx;
+    int periodic;
+};
+
+constexpr int NG = 3;
+
+__device__ __forceinline__ long long gidx(const Geom& g, int i, int j, int k) {  // ghosted indices
+    return (long long)k * g.plane + (long long)j * g.pitch + i;
+}
+
+// Centred 4th-order first, second and mixed derivatives at ghosted offset p.
+// first: (u_-2 - 8 u_-1 + 8 u_+1 - u_+2)/(12 dx) ; second: (-u_-2 + 16 u_-1 - 30 u_0 + 16 u_+1 - u_+2)/(12 dx^2)
+// mixed: tensor product of the first-derivative weights, /(144 dx^2).
+__device__ __forceinline__ double fd1(const double* __restrict__ u, long long p, long long s, double i12) {
+    return ((__ldg(u + p - 2 * s) - __ldg(u + p + 2 * s)) + 8.0 * (__ldg(u + p + s) - __ldg(u + p - s))) * i12;
+}
+__device__ __forceinline__ double fd2(const double* __restrict__ u, long long p, long long s, double u0, double i12s) {
+    return (16.0 * (__ldg(u + p + s) + __ldg(u + p - s)) - (__ldg(u + p + 2 * s) + __ldg(u + p - 2 * s)) - 30.0 * u0) * i12s;
+}
+__device__ __forceinline__ double fdm(const double* __restrict__ u, long long p, long long s, long long t, double i144) {
+    // sum_a c_a * (first-derivative combination along t at offset a*s), c = (1, -8, 8, -1) at (-2,-1,1,2)
+    auto row = [&](long long q) {
+        return (__ldg(u + q - 2 * t) - __ldg(u + q + 2 * t)) + 8.0 * (__ldg(u + q + t) - __ldg(u + q - t));
+    };
+    return ((row(p - 2 * s) - row(p + 2 * s)) + 8.0 * (row(p + s) - row(p - s))) * i144;
+}
+
+__device__ __forceinline__ bool has_d2(int f) {
+    return f == F_CHI || (f >= F_H && f < F_H + 6) || f == F_LAPSE || (f >= F_SHIFT && f < F_SHIFT + 3) || f == F_PHI;
+}
+
+__device__ __forceinline__ void gather(const Geom& g, const double* __restrict__ s, long long p, PointIn& in) {
+    const double i12 = 1.0 / (12.0 * g.dx), i12s = 1.0 / (12.0 * g.dx * g.dx), i144 = 1.0 / (144.0 * g.dx * g.dx);
+    const long long sx = 1, sy = g.pitch, sz = g.plane;
+#pragma unroll 1
+    for (int f = 0; f < NFIELDS; ++f) {
+        const double* u = s + f * g.fstride;
+        const double u0 = __ldg(u + p);
+        in.v[f] = u0;
+        if (f >= F_B && f < F_B + 3) continue;
+        const int a = d1slot(f);
+        in.d1[a][0] = fd1(u, p, sx, i12);
+        in.d1[a][1] = fd1(u, p, sy, i12);
+        in.d1[a][2] = fd1(u, p, sz, i12);
+        if (has_d2(f)) {
+            const int b = d2slot(f);
+            in.d2[b][0] = fd2(u, p, sx, u0, i12s);
+            in.d2[b][1] = fdm(u, p, sx, sy, i144);
+            in.d2[b][2] = fdm(u, p, sx, sz, i144);
+            in.d2[b][3] = fd2(u, p, sy, u0, i12s);
+            in.d2[b][4] = fdm(u, p, sy, sz, i144);
+            in.d2[b][5] = fd2(u, p, sz, u0, i12s);
+        }
+    }
+}
+
+// sum_d (u_-3 - 6 u_-2 + 15 u_-1 - 20 u_0 + 15 u_+1 - 6 u_+2 + u_+3)
+__device__ __forceinline__ double ko6(const double* __restrict__ u, long long p, long long sy, long long sz) {
+    double t3 = 0.0, t2 = 0.0, t1 = 0.0;
+    const long long st[3] = {1, sy, sz};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const long long s = st[d];
+        t3 += __ldg(u + p - 3 * s) + __ldg(u + p + 3 * s);
+        t2 += __ldg(u + p - 2 * s) + __ldg(u + p + 2 * s);
+        t1 += __ldg(u + p - s) + __ldg(u + p + s);
+    }
+    return t3 - 6.0 * t2 + 15.0 * t1 - 60.0 * __ldg(u + p);
+}
+
+__device__ __forceinline__ bool interior_thread(const Geom& g, int& i, int& j, int& k) {
+    i = blockIdx.x * blockDim.x + threadIdx.x;
+    j = blockIdx.y * blockDim.y + threadIdx.y;
+    k = blockIdx.z * blockDim.z + threadIdx.z;
+    return i < g.nx && j < g.ny && k < g.nz;
+}
+
+// Writes value x of field f for interior point (i,j,k) and, for periodic boxes, to every
+// ghost location that is a periodic image of it.
+__device__ __forceinline__ void store_with_images(const Geom& g, double* __restrict__ dst, int f, int i, int j, int k,
+                                                  double x) {
+    double* d = dst + f * g.fstride;
+    if (!g.periodic) {
+        d[gidx(g, i + NG, j + NG, k + NG)] = x;
+        return;
+    }
+    int xi[3], yi[3], zi[3];
+    int nxi = 0, nyi = 0, nzi = 0;
+    xi[nxi++] = i + NG;
+    if (i < NG) xi[nxi++] = i + NG + g.nx;
+    if (i >= g.nx - NG) xi[nxi++] = i + NG - g.nx;
+    yi[nyi++] = j + NG;
+    if (j < NG) yi[nyi++] = j + NG + g.ny;
+    if (j >= g.ny - NG) yi[nyi++] = j + NG - g.ny;
+    zi[nzi++] = k + NG;
+    if (k < NG) zi[nzi++] = k + NG + g.nz;
+    if (k >= g.nz - NG) zi[nzi++] = k + NG - g.nz;
+    for (int c = 0; c < nzi; ++c)
+        for (int b = 0; b < nyi; ++b)
+            for (int a = 0; a < nxi; ++a) d[gidx(g, xi[a], yi[b], zi[c])] = x;
+}
+
+// Trace-free A_ij with respect to h_ij, and the chi / lapse floors, on one point's values.
+__device__ __forceinline__ void enforce_point(double u[NFIELDS], double min_chi, double min_lapse) {
+    double hh[6], hi[6];
+#pragma unroll
+    for (int m = 0; m < 6; ++m) hh[m] = u[F_H + m];
+    sym3_inv(hh, hi);
+    const double tr = hi[0] * u[F_A] + hi[3] * u[F_A + 3] + hi[5] * u[F_A + 5]
+                      + 2.0 * (hi[1] * u[F_A + 1] + hi[2] * u[F_A + 2] + hi[4] * u[F_A + 4]);
+#pragma unroll
+    for (int m = 0; m < 6; ++m) u[F_A + m] -= hh[m] * tr * (1.0 / 3.0);
+    u[F_CHI] = fmax(u[F_CHI], min_chi);
+    u[F_LAPSE] = fmax(u[F_LAPSE], min_lapse);
+}
+
+struct StageArgs {
+    const double* src;   // state whose RHS is evaluated (ghosts valid)
+    const double* un;    // u_n (pointwise)
+    double* acc;         // k1 + 2 k2 + 2 k3 accumulator (pointwise)
+    double* dst;         // state written by this stage
+    double dt;
+    double ko;           // sigma / (64 dx)
+    double min_chi, min_lapse;
+    int enforce;
+    int* status;
+};
+
+// One RK4 stage, fused: gather -> pointwise RHS -> + KO -> stage update -> enforcement ->
+// store (with periodic images). STAGE 0..3.
+template <int STAGE>
+__global__ void __launch_bounds__(128) rk4_stage_kernel(Geom g, Coeffs c, StageArgs a) {
+    int i, j, k;
+    if (!interior_thread(g, i, j, k)) return;
+    const long long p = gidx(g, i + NG, j + NG, k + NG);
+    PointIn in;
+    gather(g, a.src, p, in);
+    double r[NFIELDS];
+    bool ok = true;
+    point_rhs(c, in, r, nullptr, ok);
+    if (!ok) atomicOr(a.status, 1);
+    double out[NFIELDS];
+#pragma unroll 1
+    for (int f = 0; f < NFIELDS; ++f) {
+        const double kf = r[f] + a.ko * ko6(a.src + f * g.fstride, p, g.pitch, g.plane);
+        const double unf = (STAGE == 0) ? in.v[f] : a.un[f * g.fstride + p];
+        double accf;
+        if (STAGE == 0) accf = kf;
+        else if (STAGE == 3) accf = a.acc[f * g.fstride + p] + kf;
+        else accf = a.acc[f * g.fstride + p] + 2.0 * kf;
+        if (STAGE < 3) a.acc[f * g.fstride + p] = accf;
+        const double cs = (STAGE == 0 || STAGE == 1) ? 0.5 * a.dt : (STAGE == 2 ? a.dt : a.dt * (1.0 / 6.0));
+        out[f] = (STAGE == 3) ? fma(cs, accf, unf) : fma(cs, kf, unf);
+    }
+    if (a.enforce) enforce_point(out, a.min_chi, a.min_lapse);
+#pragma unroll 1
+    for (int f = 0; f < NFIELDS; ++f) store_with_images(g, a.dst, f, i, j, k, out[f]);
+}
+
+}  // namespace grf

@@ -1,0 +1,17 @@
+// Host-side launchers of the heavy kernels (each lives in its own translation unit so the
+// library builds in parallel).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "grf_point.cuh"
+
+namespace grf {
+struct Geom;
+struct StageArgs;
+void launch_stage(int stage, dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c, const StageArgs& a);
+void launch_rhs(dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c, const double* s, double* rhs,
+                double ko, int* status);
+void launch_constraints(dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c, const double* s,
+                        double* out4, double* part);
+}  // namespace grf

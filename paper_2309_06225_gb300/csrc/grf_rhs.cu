@@ -1,0 +1,72 @@
+// Single-state RHS and constraint kernels.
+#include "grf_kernels.cuh"
+#include "grf_launch.h"
+
+namespace grf {
+
+__global__ void __launch_bounds__(128) rhs_kernel(Geom g, Coeffs c, const double* __restrict__ s, double* __restrict__ rhs,
+                                                  double ko, int* status) {
+    int i, j, k;
+    if (!interior_thread(g, i, j, k)) return;
+    const long long p = gidx(g, i + NG, j + NG, k + NG);
+    PointIn in;
+    gather(g, s, p, in);
+    double r[NFIELDS];
+    bool ok = true;
+    point_rhs(c, in, r, nullptr, ok);
+    if (!ok) atomicOr(status, 1);
+#pragma unroll 1
+    for (int f = 0; f < NFIELDS; ++f) rhs[f * g.fstride + p] = r[f] + ko * ko6(s + f * g.fstride, p, g.pitch, g.plane);
+}
+
+// Constraints H, M_i at interior points (state layout, 4 fields) and per-block partial norms:
+// part[block][8] = {sum H^2, max|H|, sum M1^2, max|M1|, ...}
+__global__ void __launch_bounds__(128) constraints_kernel(Geom g, Coeffs c, const double* __restrict__ s,
+                                                          double* __restrict__ out4, double* __restrict__ part) {
+    __shared__ double red[8][128];
+    int i, j, k;
+    const bool live = interior_thread(g, i, j, k);
+    double vals[4] = {0.0, 0.0, 0.0, 0.0};
+    if (live) {
+        const long long p = gidx(g, i + NG, j + NG, k + NG);
+        PointIn in;
+        gather(g, s, p, in);
+        double r[NFIELDS];
+        PointExtra ex;
+        bool ok = true;
+        point_rhs(c, in, r, &ex, ok);
+        vals[0] = ex.ham;
+        vals[1] = ex.mom[0];
+        vals[2] = ex.mom[1];
+        vals[3] = ex.mom[2];
+        for (int m = 0; m < 4; ++m) out4[m * g.fstride + p] = vals[m];
+    }
+    const int t = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    for (int m = 0; m < 4; ++m) {
+        red[2 * m][t] = vals[m] * vals[m];
+        red[2 * m + 1][t] = fabs(vals[m]);
+    }
+    __syncthreads();
+    for (int w = 64; w > 0; w >>= 1) {
+        if (t < w)
+            for (int m = 0; m < 4; ++m) {
+                red[2 * m][t] += red[2 * m][t + w];
+                red[2 * m + 1][t] = fmax(red[2 * m + 1][t], red[2 * m + 1][t + w]);
+            }
+        __syncthreads();
+    }
+    if (t == 0 && part) {
+        const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+        for (int m = 0; m < 8; ++m) part[b * 8 + m] = red[m][0];
+    }
+}
+
+void launch_rhs(dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c, const double* s, double* rhs,
+                double ko, int* status) {
+    rhs_kernel<<<grid, block, 0, st>>>(g, c, s, rhs, ko, status);
+}
+void launch_constraints(dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c, const double* s,
+                        double* out4, double* part) {
+    constraints_kernel<<<grid, block, 0, st>>>(g, c, s, out4, part);
+}
+}  // namespace grf

@@ -1,0 +1,209 @@
+"""GPU (CUDA path through the C ABI) versus the CPU oracle, element by element.
+
+Tolerances (per field, relative to that field's maximum over the interior): one RHS
+evaluation <= 1e-11; one RK4 step <= 1e-11 and ten RK4 steps <= 1e-9 (the stated parity bar
+for the FP64 evolution). Integer/byte work (ghost fill) is bit-exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import grf_inputs as gi
+from parity import describe, field_errors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2309_06225_gb300 import build
+    build.build()
+    import paper_2309_06225_gb300 as grf
+    grf.lib()
+    return grf
+
+
+def P(**kw):
+    p = gi.Params()
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def gpu_rhs(g, box, params, s):
+    b = g.box_like(box)
+    st = g.to_device(s, b)
+    r = g.alloc_state(b)
+    g.grf_rhs(b, g.params_like(params), st, r)
+    assert g.grf_check_status() == 0
+    return g.to_host(r, b)
+
+
+def gpu_rk4(g, box, params, s, dt, n):
+    b = g.box_like(box)
+    st = g.to_device(s, b)
+    g.grf_rk4_step(b, g.params_like(params), st, dt, n)
+    assert g.grf_check_status() == 0
+    return g.to_host(st, b)
+
+
+def test_ghost_fill_is_bit_exact(g, orc):
+    box = gi.Box(13, 17, 11, 0.2, 0.0, 0.0, 0.0)
+    s = np.random.default_rng(0).normal(size=box.shape)
+    b = g.box_like(box)
+    t = g.to_device(s, b)
+    g.grf_fill_ghosts(b, t)
+    ref = orc.fill_ghosts(box, s.copy())
+    assert np.array_equal(g.to_host(t, b), ref)
+
+
+def test_ko_parity(g, orc):
+    box = gi.Box(13, 9, 11, 0.2, 0.0, 0.0, 0.0, bc=gi.BC_FROZEN)
+    s = np.random.default_rng(1).normal(size=box.shape)
+    b = g.box_like(box)
+    t = g.to_device(s, b)
+    r = g.alloc_state(b)
+    g.grf_ko_dissipation(b, 0.3, t, r)
+    ref = orc.ko(box, 0.3, s)
+    errs = field_errors(g.to_host(r, b), ref, box)
+    assert np.max(errs) < 1e-13, describe(errs)
+
+
+RHS_CASES = {
+    "puncture32": lambda: (gi.cube_box(32, -4.0, 4.0), P(), "puncture", 0),
+    "ragged_perturbed_linear": lambda: (gi.Box(13, 17, 11, 0.3, -1.9, -2.3, -1.6), P(lam=0.3, g2=0.2), "perturbed", 1),
+    "ragged_perturbed_quadratic": lambda: (gi.Box(11, 9, 14, 0.3, -1.7, -1.3, -2.0),
+                                           P(lam=0.4, g2=0.3, beta_kind=1, a0=0.5, b0=0.9, kappa2=0.2), "perturbed", 2),
+    "frozen_small": lambda: (gi.Box(7, 5, 9, 0.25, 0.9, 0.6, -1.2, bc=gi.BC_FROZEN), P(lam=0.2, g2=0.1), "perturbed", 3),
+    "minimal_periodic": lambda: (gi.Box(3, 3, 3, 0.4, -0.5, -0.5, -0.5), P(lam=0.1, g2=0.1), "perturbed", 4),
+    "single_point_frozen": lambda: (gi.Box(1, 1, 1, 0.1, 1.1, 0.7, 0.9, bc=gi.BC_FROZEN), P(lam=0.5, g2=0.5), "puncture", 5),
+    "zero_coupling_standard_gauge": lambda: (gi.Box(12, 10, 8, 0.3, -1.5, -1.4, -1.1), P(lam=0.0, g2=0.0, a0=0.0, b0=0.0),
+                                             "perturbed", 6),
+}
+
+
+def make_state(box, kind, seed):
+    if kind == "puncture":
+        base = gi.single_puncture(box)
+        return base
+    base = gi.single_puncture(box, amp=0.05)
+    s = gi.random_perturbed_state(box, seed, base=base, eps=3e-2)
+    # give Pi, K, Theta, shift and B non-trivial values of order one percent
+    return s
+
+
+@pytest.mark.parametrize("case", list(RHS_CASES))
+def test_rhs_parity(g, orc, case):
+    box, params, kind, seed = RHS_CASES[case]()
+    s = make_state(box, kind, seed)
+    if box.bc == gi.BC_PERIODIC:
+        orc.fill_ghosts(box, s)
+    ref = orc.rhs(box, params, s)
+    out = gpu_rhs(g, box, params, s)
+    errs = field_errors(out, ref, box)
+    assert np.max(errs) < 1e-11, describe(errs)
+
+
+def test_rk4_parity_single_puncture_32(g, orc):
+    """The 32^3 single-puncture workload: 1 step <= 1e-11 and 10 steps <= 1e-9 per field."""
+    cfg = gi.config_single_puncture_32()
+    box, params, dt = cfg["box"], cfg["params"], cfg["dt"]
+    s0 = cfg["make_state"]()
+    cpu = s0.copy()
+    orc.fill_ghosts(box, cpu)
+    orc.rk4(box, params, cpu, dt, 1)
+    gpu = gpu_rk4(g, box, params, s0, dt, 1)
+    e1 = field_errors(gpu, cpu, box)
+    assert np.max(e1) < 1e-11, describe(e1)
+    orc.rk4(box, params, cpu, dt, 9)
+    gpu = gpu_rk4(g, box, params, s0, dt, 10)
+    e10 = field_errors(gpu, cpu, box)
+    assert np.max(e10) < 1e-9, describe(e10)
+
+
+@pytest.mark.parametrize("bc", [gi.BC_PERIODIC, gi.BC_FROZEN])
+def test_rk4_parity_ragged_perturbed(g, orc, bc):
+    box = gi.Box(14, 11, 9, 0.3, -2.0, -1.6, -1.3, bc=bc)
+    params = P(lam=0.3, g2=0.2, beta_kind=1)
+    s0 = make_state(box, "perturbed", 11)
+    cpu = s0.copy()
+    orc.rk4(box, params, cpu, 0.25 * box.dx, 3)
+    gpu = gpu_rk4(g, box, params, s0, 0.25 * box.dx, 3)
+    errs = field_errors(gpu, cpu, box)
+    assert np.max(errs) < 1e-10, describe(errs)
+
+
+def test_constraints_parity(g, orc):
+    box = gi.Box(13, 12, 10, 0.3, -1.9, -1.7, -1.4)
+    params = P(lam=0.3, g2=0.2)
+    s = make_state(box, "perturbed", 21)
+    orc.enforce(box, params, s)
+    orc.fill_ghosts(box, s)
+    ref = orc.constraints(box, params, s)
+    b = g.box_like(box)
+    t = g.to_device(s, b)
+    out = g.alloc_state(b, 4)
+    norms = g.grf_constraints(b, g.params_like(params), t, out)
+    got = g.to_host(out, b)
+    gg = box.interior(got[:4])
+    for m in range(4):
+        den = np.max(np.abs(ref[m]))
+        assert np.max(np.abs(gg[m] - ref[m])) <= 1e-11 * den, m
+        np.testing.assert_allclose(norms[2 * m], math.sqrt(np.mean(ref[m] ** 2)), rtol=1e-11)
+        np.testing.assert_allclose(norms[2 * m + 1], np.max(np.abs(ref[m])), rtol=1e-11)
+
+
+def test_bl_pair_256_sampled_outputs(g, orc):
+    """Full-size 256^3 Brill-Lindquist workload, one RK4 step in the production launch
+    configuration; sampled points are recomputed by the oracle on 19^3 frozen-ghost sub-boxes
+    centred on them (one RK4 step has a domain of dependence of 12 points, so the centre of
+    such a sub-box is exact)."""
+    cfg = gi.config_bl_pair_256()
+    box, params, dt = cfg["box"], cfg["params"], cfg["dt"]
+    s0 = cfg["make_state"]()
+    gpu = gpu_rk4(g, box, params, s0, dt, 1)
+    assert np.all(np.isfinite(box.interior(gpu)))
+    orc.fill_ghosts(box, s0)
+    rng = np.random.default_rng(5)
+    samples = [(128, 128, 128 + 24), (3, 200, 77)] + [tuple(int(x) for x in rng.integers(0, 256, 3)) for _ in range(2)]
+    R = 9
+    for (i, j, k) in samples:
+        sub = gi.Box(2 * R + 1, 2 * R + 1, 2 * R + 1, box.dx, 0.0, 0.0, 0.0, bc=gi.BC_FROZEN)
+        idx = [(np.arange(2 * R + 7) + c - R - 3) % 256 + 3 for c in (k, j, i)]
+        ss = np.ascontiguousarray(s0[:, idx[0]][:, :, idx[1]][:, :, :, idx[2]])
+        orc.rk4(sub, params, ss, dt, 1)
+        ref = ss[:, R + 3, R + 3, R + 3]
+        got = gpu[:, k + 3, j + 3, i + 3]
+        scale = np.maximum(np.max(np.abs(box.interior(s0)), axis=(1, 2, 3)), 1e-12)
+        err = np.abs(got - ref) / scale
+        assert np.max(err) < 1e-11, (i, j, k, describe(err))
+
+
+def test_error_codes(g):
+    import torch
+    box = gi.cube_box(8, -1.0, 1.0)
+    b = g.box_like(box)
+    t = g.alloc_state(b)
+    p = g.params_like(P())
+    small = g.alloc_workspace(1024)
+    with pytest.raises(g.GrfError) as e:
+        g.grf_rk4_step(b, p, t, 0.1, 1, ws=small)
+    assert e.value.code == g.GRF_EWORKSPACE
+    bad = g.box_like(box)
+    bad.nx = 2  # periodic boxes need >= 3 points per axis
+    with pytest.raises(g.GrfError) as e:
+        g.grf_rhs(bad, p, t, t)
+    assert e.value.code == g.GRF_EINVAL
+    pb = g.params_like(P(beta_kind=7))
+    with pytest.raises(g.GrfError):
+        g.grf_rhs(b, pb, t, g.alloc_state(b))
+    s = gi.single_puncture(box)
+    t = g.to_device(s, b)
+    assert g.grf_check_finite(b, t) == 0
+    t[5, 5, 5, 5] = float("nan")
+    assert g.grf_check_finite(b, t) == g.GRF_ENONFINITE
+    torch.cuda.synchronize()
