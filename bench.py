@@ -43,9 +43,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="bl_pair_256", choices=["bl_pair_256", "bl_pair_128", "bl_pair_64"])
+    ap.add_argument("--workload", default="bl_pair_256", choices=["bl_pair_256", "bl_pair_128", "bl_pair_96", "bl_pair_64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-peak", action="store_true", help="skip the FP64 microbenchmark")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     return ap.parse_args()
 
@@ -217,7 +218,7 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     npts = box.nx * box.ny * box.nz
 
-    peak = build_peak.measure()
+    peak = None if args.no_peak else build_peak.measure()
 
     def barrier():
         if dist is not None:
@@ -284,7 +285,7 @@ def run_ours(args, rank, world, local_rank):
     roof = {"bound": "alu", "unit": "TFLOP/s", "peak": peak,
             "peak_source": "measured FP64 FMA microbenchmark (libgrf_peak.so) in this run",
             "peak_nominal": FP64_NOMINAL_TFLOPS, "kernel": "rk4_stage_kernel"}
-    if FLOP_PER_POINT_STAGE is not None:
+    if FLOP_PER_POINT_STAGE is not None and peak:
         achieved = FLOP_PER_POINT_STAGE * npts / (launch_ms * 1e-3) / 1e12
         roof.update({"achieved": achieved, "frac": achieved / peak, "flop_per_point_stage": FLOP_PER_POINT_STAGE})
     else:

@@ -21,23 +21,25 @@ def build(force=False, verbose=False):
     return LIB
 
 
-def measure(device_blocks=None, threads=256, iters=20000):
-    """Measured FP64 FMA throughput in TFLOP/s on the current CUDA device."""
+def measure(threads=256, iters=20000):
+    """Measured FP64 FMA throughput in TFLOP/s on the current CUDA device: best over a small
+    sweep of resident blocks per SM."""
     import ctypes as C
 
     import torch
     L = C.CDLL(build())
     L.grf_peak_fp64.argtypes = [C.c_int, C.c_int, C.c_int, C.c_void_p, C.POINTER(C.c_float), C.c_void_p]
     nsm = torch.cuda.get_device_properties(0).multi_processor_count
-    blocks = device_blocks or nsm * 8
-    out = torch.empty(blocks * threads, dtype=torch.float64, device="cuda")
+    out = torch.empty(nsm * 16 * threads, dtype=torch.float64, device="cuda")
     ms = C.c_float()
     st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
     best = 0.0
-    for _ in range(5):
-        rc = L.grf_peak_fp64(blocks, threads, iters, C.c_void_p(out.data_ptr()), C.byref(ms), st)
-        assert rc == 0
-        best = max(best, 16.0 * iters * blocks * threads / (ms.value * 1e-3) / 1e12)
+    for per_sm in (2, 4, 8, 16):
+        blocks = nsm * per_sm
+        for _ in range(3):
+            rc = L.grf_peak_fp64(blocks, threads, iters, C.c_void_p(out.data_ptr()), C.byref(ms), st)
+            assert rc == 0
+            best = max(best, 16.0 * iters * blocks * threads / (ms.value * 1e-3) / 1e12)
     return best
 
 

@@ -80,7 +80,7 @@ RHS_CASES = {
                                            P(lam=0.4, g2=0.3, beta_kind=1, a0=0.5, b0=0.9, kappa2=0.2), "perturbed", 2),
     "frozen_small": lambda: (gi.Box(7, 5, 9, 0.25, 0.9, 0.6, -1.2, bc=gi.BC_FROZEN), P(lam=0.2, g2=0.1), "perturbed", 3),
     "minimal_periodic": lambda: (gi.Box(3, 3, 3, 0.4, -0.5, -0.5, -0.5), P(lam=0.1, g2=0.1), "perturbed", 4),
-    "single_point_frozen": lambda: (gi.Box(1, 1, 1, 0.1, 1.1, 0.7, 0.9, bc=gi.BC_FROZEN), P(lam=0.5, g2=0.5), "puncture", 5),
+    "single_point_frozen": lambda: (gi.Box(1, 1, 1, 0.3, 1.1, 0.7, 0.9, bc=gi.BC_FROZEN), P(lam=0.5, g2=0.5), "perturbed", 5),
     "zero_coupling_standard_gauge": lambda: (gi.Box(12, 10, 8, 0.3, -1.5, -1.4, -1.1), P(lam=0.0, g2=0.0, a0=0.0, b0=0.0),
                                              "perturbed", 6),
 }
@@ -104,7 +104,7 @@ def test_rhs_parity(g, orc, case):
         orc.fill_ghosts(box, s)
     ref = orc.rhs(box, params, s)
     out = gpu_rhs(g, box, params, s)
-    errs = field_errors(out, ref, box)
+    errs = field_errors(out, ref, box, state=s, sigma=params.sigma_ko)
     assert np.max(errs) < 1e-11, describe(errs)
 
 
@@ -178,7 +178,8 @@ def test_bl_pair_256_sampled_outputs(g, orc):
         orc.rk4(sub, params, ss, dt, 1)
         ref = ss[:, R + 3, R + 3, R + 3]
         got = gpu[:, k + 3, j + 3, i + 3]
-        scale = np.maximum(np.max(np.abs(box.interior(s0)), axis=(1, 2, 3)), 1e-12)
+        # per-field scale: the field's maximum over the whole box after the step
+        scale = np.maximum(np.max(np.abs(box.interior(gpu)), axis=(1, 2, 3)), 1e-12)
         err = np.abs(got - ref) / scale
         assert np.max(err) < 1e-11, (i, j, k, describe(err))
 
