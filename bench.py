@@ -27,14 +27,18 @@ sys.path.insert(0, ROOT)
 METRIC = "FP64 grid-point RK4 updates/s (mCCZ4+4∂ST) and % of FP64/HBM roofline"
 UNIT = "point-updates/s"
 
-# FP64 operations per interior point per RK4 stage kernel, counted with ncu's DP instruction
-# counters (dadd + dmul + 2*dfma) on the stage kernel ("Roofline").
-FLOP_PER_POINT_STAGE = None
+# FP64 operations per interior point per RK4 stage kernel are counted from the kernel source
+# itself (paper_2309_06225_gb300.flops: the pointwise RHS run with an operation-counting
+# scalar, plus the stencil/KO/update expressions); add/sub/mul = 1 flop, fma = 2, div = 1.
 # algorithmic HBM bytes per point-update (stage-wise RK4, 27 fields, perfect stencil reuse):
 # stage 1: read u_n, write u_1 and acc (3 x 216 B); stages 2-3: read u_s, u_n, acc, write u_s, acc
 # (5 x 216 B each); stage 4: read u_3, u_n, acc, write u_n (4 x 216 B)
 BYTES_PER_POINT_UPDATE = 216 * (3 + 5 + 5 + 4)
-FP64_NOMINAL_TFLOPS = 1.25
+# dram__bytes_read.sum + dram__bytes_write.sum of one stage launch per interior point, from the
+# ncu capture of the current stage kernel (profiles/); None when the kernel changed since.
+TRAFFIC_BYTES_PER_POINT_STAGE = None
+# FP64 (non-tensor) peak of GB300: 152 SMs x 2 FP64 FMA lanes/clk x 2 flop x ~2.06 GHz = 1.25 TFLOP/s
+FP64_PEAK_TFLOPS = 1.25
 
 
 def parse():
@@ -281,16 +285,16 @@ def run_ours(args, rank, world, local_rank):
         if dist is not None:
             dist.destroy_process_group()
         return
+    from paper_2309_06225_gb300 import flops as grf_flops
+    flop_ps = grf_flops.flops_per_point_stage(p)
     launch_ms = ms / (4 * args.steps)  # the timed region is 4 stage kernels + 1 small ghost fill per step
-    roof = {"bound": "alu", "unit": "TFLOP/s", "peak": peak,
-            "peak_source": "measured FP64 FMA microbenchmark (libgrf_peak.so) in this run",
-            "peak_nominal": FP64_NOMINAL_TFLOPS, "kernel": "rk4_stage_kernel"}
-    if FLOP_PER_POINT_STAGE is not None and peak:
-        achieved = FLOP_PER_POINT_STAGE * npts / (launch_ms * 1e-3) / 1e12
-        roof.update({"achieved": achieved, "frac": achieved / peak, "flop_per_point_stage": FLOP_PER_POINT_STAGE})
-    else:
-        roof.update({"achieved": None, "frac": None})
-    roof["traffic"] = None
+    achieved = flop_ps * npts / (launch_ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "unit": "TFLOP/s", "kernel": "rk4_stage_kernel", "achieved": achieved,
+            "peak": FP64_PEAK_TFLOPS, "frac": achieved / FP64_PEAK_TFLOPS,
+            "peak_source": "GB300 FP64 non-tensor: 152 SMs x 2 FMA/clk x 2 flop x 2.06 GHz (recipe figure 1.25 TFLOP/s)",
+            "peak_dfma_microbenchmark": peak, "flop_per_point_stage": flop_ps,
+            "flop_convention": "counted from the kernel source: add/sub/mul 1, fma 2, div 1",
+            "traffic": TRAFFIC_BYTES_PER_POINT_STAGE * npts if TRAFFIC_BYTES_PER_POINT_STAGE else None}
     roof["hbm_frac_of_measured"] = BYTES_PER_POINT_UPDATE * value / 6771.1e9
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",

@@ -24,6 +24,24 @@ def _deps():
     return max(os.path.getmtime(f) for f in files)
 
 
+FLOPS_SRC = os.path.join(CSRC, "grf_flops.cpp")
+FLOPS_LIB = os.path.join(HERE, "libgrf_flops.so")
+
+
+def build_flops(force=False, verbose=False):
+    """Host build of the pointwise RHS source: operation counts and a double-precision
+    instance used by CPU checks (no GPU code)."""
+    if not force and os.path.exists(FLOPS_LIB) and os.path.getmtime(FLOPS_LIB) >= _deps():
+        return FLOPS_LIB
+    cmd = [os.environ.get("CXX", "g++"), "-std=c++17", "-O2", "-ffp-contract=off", "-shared", "-fPIC", "-I" + INC,
+           "-I" + CSRC, FLOPS_SRC, "-o", FLOPS_LIB + ".tmp"]
+    if verbose:
+        print(" ".join(cmd), flush=True)
+    subprocess.check_call(cmd)
+    os.replace(FLOPS_LIB + ".tmp", FLOPS_LIB)
+    return FLOPS_LIB
+
+
 def build(force=False, verbose=False, ptxas_verbose=False):
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps():
         return LIB
@@ -54,3 +72,4 @@ def build(force=False, verbose=False, ptxas_verbose=False):
 
 if __name__ == "__main__":
     build(force="--force" in sys.argv, verbose=True, ptxas_verbose="-v" in sys.argv)
+    build_flops(force="--force" in sys.argv, verbose=True)

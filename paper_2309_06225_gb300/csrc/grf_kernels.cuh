@@ -118,10 +118,10 @@ __device__ __forceinline__ void store_with_images(const Geom& g, double* __restr
 
 // Trace-free A_ij with respect to h_ij, and the chi / lapse floors, on one point's values.
 __device__ __forceinline__ void enforce_point(double u[NFIELDS], double min_chi, double min_lapse) {
-    double hh[6], hi[6];
+    double hh[6], hi[6], id;
 #pragma unroll
     for (int m = 0; m < 6; ++m) hh[m] = u[F_H + m];
-    sym3_inv(hh, hi);
+    sym3_inv(hh, hi, id);
     const double tr = hi[0] * u[F_A] + hi[3] * u[F_A + 3] + hi[5] * u[F_A + 5]
                       + 2.0 * (hi[1] * u[F_A + 1] + hi[2] * u[F_A + 2] + hi[4] * u[F_A + 4]);
 #pragma unroll
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(128) rk4_stage_kernel(Geom g, Coeffs c, StageA
     gather(g, a.src, p, in);
     double r[NFIELDS];
     bool ok = true;
-    point_rhs(c, in, r, nullptr, ok);
+    point_rhs<double>(c, in, r, nullptr, ok);
     if (!ok) atomicOr(a.status, 1);
     double out[NFIELDS];
 #pragma unroll 1

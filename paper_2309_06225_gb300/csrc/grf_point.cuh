@@ -21,7 +21,26 @@
 // is assembled from these expressions and solved by LU with partial pivoting.
 #pragma once
 
+#ifdef __CUDACC__
 #include <cuda_runtime.h>
+#define GRF_HD __host__ __device__ __forceinline__
+#else
+#include <cmath>
+#define GRF_HD inline
+#define __host__
+#define __device__
+#endif
+
+// Section markers: no-ops in the CUDA build; the host operation-counting build defines them
+// to attribute FP64 operations to the parts of the algorithm.
+#ifndef GRF_SECTION
+#define GRF_SECTION(id)
+#endif
+// Marks a value as data (not a known constant) in the counting build: compare-and-exchange
+// pivoting turns every swapped entry into a runtime value.
+#ifndef GRF_OPAQUE
+#define GRF_OPAQUE(x)
+#endif
 
 namespace grf {
 
@@ -43,30 +62,36 @@ struct Coeffs {
     int beta_kind;
 };
 
-struct PointIn {
-    double v[NFIELDS];
-    double d1[24][3];
-    double d2[12][6];
+template <typename T>
+struct PointInT {
+    T v[NFIELDS];
+    T d1[24][3];
+    T d2[12][6];
 };
+using PointIn = PointInT<double>;
 
 // Output diagnostics besides the RHS (constraints come out as by-products).
-struct PointExtra {
-    double ham;      // H = S - 2 (8 pi rho)
-    double mom[3];   // M_i = B_i - 8 pi S_i
+template <typename T>
+struct PointExtraT {
+    T ham;      // H = S - 2 (8 pi rho)
+    T mom[3];   // M_i = B_i - 8 pi S_i
 };
+using PointExtra = PointExtraT<double>;
 
-__device__ __forceinline__ double sym3_det(const double h[6]) {
+template <typename T>
+GRF_HD T sym3_det(const T h[6]) {
     return h[0] * (h[3] * h[5] - h[4] * h[4]) - h[1] * (h[1] * h[5] - h[4] * h[2])
            + h[2] * (h[1] * h[4] - h[3] * h[2]);
 }
 
 // symmetric inverse; returns determinant
-__device__ __forceinline__ double sym3_inv(const double h[6], double hi[6]) {
-    const double c00 = h[3] * h[5] - h[4] * h[4];
-    const double c01 = h[2] * h[4] - h[1] * h[5];
-    const double c02 = h[1] * h[4] - h[2] * h[3];
-    const double det = h[0] * c00 + h[1] * c01 + h[2] * c02;
-    const double id = 1.0 / det;
+template <typename T>
+GRF_HD T sym3_inv(const T h[6], T hi[6], T& id) {
+    const T c00 = h[3] * h[5] - h[4] * h[4];
+    const T c01 = h[2] * h[4] - h[1] * h[5];
+    const T c02 = h[1] * h[4] - h[2] * h[3];
+    const T det = h[0] * c00 + h[1] * c01 + h[2] * c02;
+    id = 1.0 / det;
     hi[0] = c00 * id;
     hi[1] = c01 * id;
     hi[2] = c02 * id;
@@ -79,8 +104,9 @@ __device__ __forceinline__ double sym3_inv(const double h[6], double hi[6]) {
 // 7x7 LU with partial pivoting (row swaps by compare-and-exchange, so every index stays a
 // compile-time constant and the matrix stays in registers). Returns false on a pivot
 // smaller than 1e-300 times the largest entry.
-__device__ __forceinline__ bool solve7(double M[7][8]) {
-    double mx = 0.0;
+template <typename T>
+GRF_HD bool solve7(T M[7][8]) {
+    T mx = 0.0;
 #pragma unroll
     for (int i = 0; i < 7; ++i)
 #pragma unroll
@@ -93,16 +119,18 @@ __device__ __forceinline__ bool solve7(double M[7][8]) {
             const bool sw = fabs(M[i][k]) > fabs(M[k][k]);
 #pragma unroll
             for (int j = k; j < 8; ++j) {
-                const double a = M[k][j], b = M[i][j];
+                const T a = M[k][j], b = M[i][j];
                 M[k][j] = sw ? b : a;
                 M[i][j] = sw ? a : b;
+                GRF_OPAQUE(M[k][j]);
+                GRF_OPAQUE(M[i][j]);
             }
         }
         ok = ok && (fabs(M[k][k]) > 1e-300 * mx);
-        const double ip = 1.0 / M[k][k];
+        const T ip = 1.0 / M[k][k];
 #pragma unroll
         for (int i = k + 1; i < 7; ++i) {
-            const double f = M[i][k] * ip;
+            const T f = M[i][k] * ip;
 #pragma unroll
             for (int j = k + 1; j < 8; ++j) M[i][j] = fma(-f, M[k][j], M[i][j]);
         }
@@ -118,68 +146,89 @@ __device__ __forceinline__ bool solve7(double M[7][8]) {
     return ok;
 }
 
-// L(Q(u)) for a symmetric u (6 components): the linear part of the 4dST S_ij in d_t K_ij,
-// traced-reversed as it enters d_t K_ij. gd: gamma_ij, Phm: Phi_i^k (mixed, row i),
-// Phu: Phi^{ij}, Phd: Phi_ij, trP = gamma^ij Phi_ij, gu: gamma^ij.
-__device__ __forceinline__ void apply_LQ(const double u[6], const double gd[6], const double gu[6],
-                                         const double Phd[6], const double Phu[6], const double Phm[3][3],
-                                         double trP, double out[6]) {
-    double uP = 0.0, tru = 0.0;
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            uP = fma(u[sidx(i, j)], Phu[sidx(i, j)], uP);
-            tru = fma(u[sidx(i, j)], gu[sidx(i, j)], tru);
-        }
+// sum_ij a_ij b^ij for symmetric a, b stored as 6 components, with `bw` = b with the three
+// off-diagonal components pre-multiplied by 2.
+template <typename T>
+GRF_HD T sdotw(const T a[6], const T bw[6]) {
+    return a[0] * bw[0] + a[1] * bw[1] + a[2] * bw[2] + a[3] * bw[3] + a[4] * bw[4] + a[5] * bw[5];
+}
+
+// Levi-Civita bookkeeping of the Codazzi block: B_kij (antisymmetric in ij) is stored through
+// its dual bb[k][m] = B_{k,(m+1)%3,(m+2)%3}; B_kij = +-bb[k][3-i-j] for i != j.
+__host__ __device__ constexpr int third(int i, int j) { return 3 - i - j; }
+__host__ __device__ constexpr bool cyclic(int i, int j) { return (j - i + 3) % 3 == 1; }
+
+// Q_ij(X) = P_ikjl X^kl-type contraction: the Gauss-Bonnet S_ij is -4 [... + Q_ij(C)] with
+//   Q_ij(X) = gamma_ij (X.Phi) - Phi_i^k X_kj - Phi_j^k X_ik + tr(Phi) X_ij - tr(X)(gamma_ij tr(Phi) - Phi_ij)
+template <typename T>
+GRF_HD void q_of(const T X[6], const T gd[6], const T gw[6], const T Phd[6], const T Phuw[6], const T Phm[3][3], T trP,
+                 T out[6]) {
+    const T XP = sdotw(X, Phuw);
+    const T trX = sdotw(X, gw);
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = i; j < 3; ++j) {
-            double pu = 0.0;
-#pragma unroll
-            for (int k = 0; k < 3; ++k) pu += Phm[i][k] * u[sidx(k, j)] + Phm[j][k] * u[sidx(i, k)];
-            out[sidx(i, j)] = 0.5 * gd[sidx(i, j)] * (uP - tru * trP) - pu + trP * u[sidx(i, j)] + tru * Phd[sidx(i, j)];
+            T pu = Phm[i][0] * X[sidx(0, j)];
+            pu = fma(Phm[i][1], X[sidx(1, j)], pu);
+            pu = fma(Phm[i][2], X[sidx(2, j)], pu);
+            pu = fma(Phm[j][0], X[sidx(i, 0)], pu);
+            pu = fma(Phm[j][1], X[sidx(i, 1)], pu);
+            pu = fma(Phm[j][2], X[sidx(i, 2)], pu);
+            out[sidx(i, j)] = gd[sidx(i, j)] * (XP - trX * trP) - pu + trP * X[sidx(i, j)] + trX * Phd[sidx(i, j)];
         }
 }
 
-__device__ __forceinline__ void point_rhs(const Coeffs& c, const PointIn& in, double rhs[NFIELDS],
-                                          PointExtra* extra, bool& ok) {
-    const double* v = in.v;
-    const double chi = v[F_CHI], K = v[F_K], Th = v[F_TH], al = v[F_LAPSE], phi = v[F_PHI], Pi = v[F_PI];
-    double h[6], A[6];
+template <typename T>
+GRF_HD void point_rhs(const Coeffs& c, const PointInT<T>& in, T rhs[NFIELDS], PointExtraT<T>* extra, bool& ok) {
+    GRF_SECTION(0);
+    const T* v = in.v;
+    const T chi = v[F_CHI], K = v[F_K], Th = v[F_TH], al = v[F_LAPSE], phi = v[F_PHI], Pi = v[F_PI];
+    T h[6], A[6];
 #pragma unroll
     for (int m = 0; m < 6; ++m) { h[m] = v[F_H + m]; A[m] = v[F_A + m]; }
-    double hi[6];
-    const double deth = sym3_inv(h, hi);
-    const double ichi = 1.0 / chi;
-    const double ial = 1.0 / al;
+    T hi[6], ideth;
+    sym3_inv(h, hi, ideth);
+    const T ichi = 1.0 / chi;
+    const T ial = 1.0 / al;
+    // weighted inverses (off-diagonals doubled) for symmetric contractions; gamma^ij = chi h^ij
+    T hw[6], gu[6], gw[6], gd[6];
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+        const bool off = (m == 1 || m == 2 || m == 4);
+        hw[m] = off ? 2.0 * hi[m] : hi[m];
+        gu[m] = chi * hi[m];
+        gw[m] = chi * hw[m];
+        gd[m] = h[m] * ichi;
+    }
 
-    // ---- derivatives (aliases)
+    GRF_SECTION(1);
 #define D1(f, k) in.d1[d1slot(f)][k]
 #define D2(f, m) in.d2[d2slot(f)][m]
-    double dh[3][6];
+    T dh[3][6];
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
         for (int m = 0; m < 6; ++m) dh[k][m] = D1(F_H + m, k);
-    double dchi[3], dal[3], dK[3], dTh[3], dphi[3], dPi[3];
+    T dchi[3], dal[3], dK[3], dTh[3], dphi[3], dPi[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         dchi[k] = D1(F_CHI, k); dal[k] = D1(F_LAPSE, k); dK[k] = D1(F_K, k);
         dTh[k] = D1(F_TH, k); dphi[k] = D1(F_PHI, k); dPi[k] = D1(F_PI, k);
     }
-    double db[3][3];  // db[j][i] = d_j beta^i
+    T db[3][3];  // db[j][i] = d_j beta^i
 #pragma unroll
     for (int j = 0; j < 3; ++j)
 #pragma unroll
         for (int i = 0; i < 3; ++i) db[j][i] = D1(F_SHIFT + i, j);
-    const double divb = db[0][0] + db[1][1] + db[2][2];
-    const double bx = v[F_SHIFT], by = v[F_SHIFT + 1], bz = v[F_SHIFT + 2];
+    const T divb = db[0][0] + db[1][1] + db[2][2];
+    const T bx = v[F_SHIFT], by = v[F_SHIFT + 1], bz = v[F_SHIFT + 2];
 #define ADV(f) (bx * D1(f, 0) + by * D1(f, 1) + bz * D1(f, 2))
 
-    // ---- conformal Christoffels: G1[l][ij] = Gt_{l ij}, G2[k][ij] = Gt^k_ij, Gtc^k
-    double G1[3][6], G2[3][6], Gtc[3];
+    // ---- conformal Christoffels: G1[l][ij] = Gt_{l ij}, G2[k][ij] = Gt^k_ij,
+    //      Gl_l = h^ij Gt_lij (= h_lk Gt^k), Gtc^k = h^kl Gl_l
+    GRF_SECTION(2);
+    T G1[3][6], G2[3][6], Gl[3], Gtc[3];
 #pragma unroll
     for (int l = 0; l < 3; ++l)
 #pragma unroll
@@ -188,279 +237,306 @@ __device__ __forceinline__ void point_rhs(const Coeffs& c, const PointIn& in, do
             for (int j = i; j < 3; ++j)
                 G1[l][sidx(i, j)] = 0.5 * (dh[i][sidx(l, j)] + dh[j][sidx(l, i)] - dh[l][sidx(i, j)]);
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
+    for (int l = 0; l < 3; ++l) Gl[l] = sdotw(G1[l], hw);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        Gtc[k] = hi[sidx(k, 0)] * Gl[0] + hi[sidx(k, 1)] * Gl[1] + hi[sidx(k, 2)] * Gl[2];
 #pragma unroll
         for (int m = 0; m < 6; ++m)
             G2[k][m] = hi[sidx(k, 0)] * G1[0][m] + hi[sidx(k, 1)] * G1[1][m] + hi[sidx(k, 2)] * G1[2][m];
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-        Gtc[k] = hi[0] * G2[k][0] + hi[3] * G2[k][3] + hi[5] * G2[k][5]
-                 + 2.0 * (hi[1] * G2[k][1] + hi[2] * G2[k][2] + hi[4] * G2[k][4]);
+    }
 
-    // ---- d_m Gt^k (chain rule through h^-1 and d2 h)
-    double dGtc[3][3];
-    {
-        double Gl[3];  // G_l = h^ij Gt_lij
+    // ---- dGl[m][l] = d_m Gl_l = d_m h^ij Gt_lij + h^ij d_m d_i h_lj - h^ij d_m d_l h_ij / 2
+    GRF_SECTION(3);
+    T dGl[3][3];
 #pragma unroll
-        for (int l = 0; l < 3; ++l)
-            Gl[l] = hi[0] * G1[l][0] + hi[3] * G1[l][3] + hi[5] * G1[l][5]
-                    + 2.0 * (hi[1] * G1[l][1] + hi[2] * G1[l][2] + hi[4] * G1[l][4]);
+    for (int m = 0; m < 3; ++m) {
+        T Tm[3][3];  // h^ac d_m h_cd
 #pragma unroll
-        for (int m = 0; m < 3; ++m) {
-            // d_m h^ab = -h^ac d_m h_cd h^db
-            double T[3][3];
+        for (int a = 0; a < 3; ++a)
 #pragma unroll
-            for (int a = 0; a < 3; ++a)
+            for (int d = 0; d < 3; ++d)
+                Tm[a][d] = hi[sidx(a, 0)] * dh[m][sidx(0, d)] + hi[sidx(a, 1)] * dh[m][sidx(1, d)]
+                           + hi[sidx(a, 2)] * dh[m][sidx(2, d)];
+        T dhiw[6];  // -(h^-1 d_m h h^-1), off-diagonals doubled
 #pragma unroll
-                for (int d = 0; d < 3; ++d)
-                    T[a][d] = hi[sidx(a, 0)] * dh[m][sidx(0, d)] + hi[sidx(a, 1)] * dh[m][sidx(1, d)]
-                              + hi[sidx(a, 2)] * dh[m][sidx(2, d)];
-            double dhi[6];
+        for (int a = 0; a < 3; ++a)
 #pragma unroll
-            for (int a = 0; a < 3; ++a)
-#pragma unroll
-                for (int b = a; b < 3; ++b)
-                    dhi[sidx(a, b)] = -(T[a][0] * hi[sidx(0, b)] + T[a][1] * hi[sidx(1, b)] + T[a][2] * hi[sidx(2, b)]);
-            double dGl[3];
-#pragma unroll
-            for (int l = 0; l < 3; ++l) {
-                double s = 0.0;
-#pragma unroll
-                for (int i = 0; i < 3; ++i)
-#pragma unroll
-                    for (int j = 0; j < 3; ++j) {
-                        // d_m Gt_lij = 1/2 (d_m d_i h_lj + d_m d_j h_li - d_m d_l h_ij)
-                        const double dG1 = 0.5 * (D2(F_H + sidx(l, j), sidx(m, i)) + D2(F_H + sidx(l, i), sidx(m, j))
-                                                  - D2(F_H + sidx(i, j), sidx(m, l)));
-                        s += dhi[sidx(i, j)] * G1[l][sidx(i, j)] + hi[sidx(i, j)] * dG1;
-                    }
-                dGl[l] = s;
+            for (int b = a; b < 3; ++b) {
+                const T x = Tm[a][0] * hi[sidx(0, b)] + Tm[a][1] * hi[sidx(1, b)] + Tm[a][2] * hi[sidx(2, b)];
+                dhiw[sidx(a, b)] = (a == b) ? -x : -2.0 * x;
             }
 #pragma unroll
-            for (int k = 0; k < 3; ++k)
-                dGtc[m][k] = dhi[sidx(k, 0)] * Gl[0] + dhi[sidx(k, 1)] * Gl[1] + dhi[sidx(k, 2)] * Gl[2]
-                             + hi[sidx(k, 0)] * dGl[0] + hi[sidx(k, 1)] * dGl[1] + hi[sidx(k, 2)] * dGl[2];
+        for (int l = 0; l < 3; ++l) {
+            T s = sdotw(G1[l], dhiw);
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) s = fma(hi[sidx(i, j)], D2(F_H + sidx(l, j), sidx(m, i)), s);
+            T b = 0.0;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) b = (q == 0) ? hw[0] * D2(F_H + 0, sidx(m, l)) : fma(hw[q], D2(F_H + q, sidx(m, l)), b);
+            dGl[m][l] = fma(-0.5, b, s);
         }
     }
 
-    // ---- physical Christoffels Gp^k_ij = Gt^k_ij - (d_i chi delta^k_j + d_j chi delta^k_i - h_ij h^kl d_l chi)/(2 chi)
-    double hidchi[3];
+    // ---- physical Christoffels Gp^k_ij = Gt^k_ij - (delta^k_i d_j chi + delta^k_j d_i chi - h_ij h^kl d_l chi)/(2 chi)
+    GRF_SECTION(4);
+    T hidchi[3], c1[3], c2[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) hidchi[k] = hi[sidx(k, 0)] * dchi[0] + hi[sidx(k, 1)] * dchi[1] + hi[sidx(k, 2)] * dchi[2];
-    double Gp[3][6];
+    for (int k = 0; k < 3; ++k) {
+        hidchi[k] = hi[sidx(k, 0)] * dchi[0] + hi[sidx(k, 1)] * dchi[1] + hi[sidx(k, 2)] * dchi[2];
+        c1[k] = (0.5 * ichi) * dchi[k];
+        c2[k] = (0.5 * ichi) * hidchi[k];
+    }
+    T Gp[3][6];
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
             for (int j = i; j < 3; ++j) {
-                double t = -h[sidx(i, j)] * hidchi[k];
-                if (k == j) t += dchi[i];
-                if (k == i) t += dchi[j];
-                Gp[k][sidx(i, j)] = G2[k][sidx(i, j)] - 0.5 * ichi * t;
+                T t = fma(h[sidx(i, j)], c2[k], G2[k][sidx(i, j)]);
+                if (k == j) t = t - c1[i];
+                if (k == i) t = t - c1[j];
+                Gp[k][sidx(i, j)] = t;
             }
 
-    // ---- plain Ricci tensor of gamma = h/chi (conformal decomposition)
-    double Ric[6];
+    // ---- plain Ricci tensor of gamma = h/chi:
+    // R_ij = -1/2 h^lm d_l d_m h_ij + d_(i Gl_j) - Gt^k Gt_kij
+    //        + h^lm (Gt^k_li Gt_jkm + Gt^k_lj Gt_ikm + Gt^k_im Gt_klj) + chi part
+    GRF_SECTION(5);
+    T Ric[6];
     {
-        double DDchi[6];
+        T U[3][3][3];  // U[k][m][i] = h^lm Gt^k_li
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int m = 0; m < 3; ++m)
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+                    U[k][m][i] = hi[sidx(0, m)] * G2[k][sidx(0, i)] + hi[sidx(1, m)] * G2[k][sidx(1, i)]
+                                 + hi[sidx(2, m)] * G2[k][sidx(2, i)];
+        T Q1[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                T s = 0.0;
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+#pragma unroll
+                    for (int m = 0; m < 3; ++m)
+                        s = (k == 0 && m == 0) ? U[0][0][i] * G1[j][0] : fma(U[k][m][i], G1[j][sidx(k, m)], s);
+                Q1[i][j] = s;
+            }
+        T DDchi[6];
 #pragma unroll
         for (int m = 0; m < 6; ++m)
             DDchi[m] = D2(F_CHI, m) - G2[0][m] * dchi[0] - G2[1][m] * dchi[1] - G2[2][m] * dchi[2];
-        const double lapchi = hi[0] * DDchi[0] + hi[3] * DDchi[3] + hi[5] * DDchi[5]
-                              + 2.0 * (hi[1] * DDchi[1] + hi[2] * DDchi[2] + hi[4] * DDchi[4]);
-        const double dchi2 = dchi[0] * hidchi[0] + dchi[1] * hidchi[1] + dchi[2] * hidchi[2];
+        const T lapchi = sdotw(DDchi, hw);
+        const T dchi2 = dchi[0] * hidchi[0] + dchi[1] * hidchi[1] + dchi[2] * hidchi[2];
+        const T hichi = 0.5 * ichi, qichi2 = -0.25 * ichi * ichi;
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
             for (int j = i; j < 3; ++j) {
-                double r = 0.0;
+                T r = Q1[i][j] + Q1[j][i] + 0.5 * (dGl[j][i] + dGl[i][j]);
 #pragma unroll
-                for (int l = 0; l < 3; ++l)
+                for (int k = 0; k < 3; ++k)
 #pragma unroll
-                    for (int m = 0; m < 3; ++m) r -= 0.5 * hi[sidx(l, m)] * D2(F_H + sidx(i, j), sidx(l, m));
+                    for (int l = 0; l < 3; ++l) r = fma(U[k][l][i], G1[k][sidx(l, j)], r);
 #pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    r += 0.5 * (h[sidx(k, i)] * dGtc[j][k] + h[sidx(k, j)] * dGtc[i][k]);
-                    r += 0.5 * Gtc[k] * (G1[i][sidx(j, k)] + G1[j][sidx(i, k)]);
+                for (int k = 0; k < 3; ++k) r = fma(-Gtc[k], G1[k][sidx(i, j)], r);
 #pragma unroll
-                    for (int l = 0; l < 3; ++l)
-#pragma unroll
-                        for (int m = 0; m < 3; ++m)
-                            r += hi[sidx(l, m)] * (G2[k][sidx(l, i)] * G1[j][sidx(k, m)] + G2[k][sidx(l, j)] * G1[i][sidx(k, m)]
-                                                   + G2[k][sidx(i, m)] * G1[k][sidx(l, j)]);
-                }
-                r += 0.5 * ichi * (DDchi[sidx(i, j)] + h[sidx(i, j)] * lapchi)
-                     - 0.25 * ichi * ichi * (dchi[i] * dchi[j] + 3.0 * h[sidx(i, j)] * dchi2);
+                for (int q = 0; q < 6; ++q) r = fma(-0.5 * hw[q], D2(F_H + sidx(i, j), q), r);
+                r = fma(hichi, fma(h[sidx(i, j)], lapchi, DDchi[sidx(i, j)]), r);
+                r = fma(qichi2, fma(3.0 * h[sidx(i, j)], dchi2, dchi[i] * dchi[j]), r);
                 Ric[sidx(i, j)] = r;
             }
     }
-    // gamma^ij = chi h^ij, gamma_ij = h_ij / chi
-    double gu[6], gd[6];
-#pragma unroll
-    for (int m = 0; m < 6; ++m) { gu[m] = chi * hi[m]; gd[m] = h[m] * ichi; }
-#define TRU(X) (gu[0] * (X)[0] + gu[3] * (X)[3] + gu[5] * (X)[5] + 2.0 * (gu[1] * (X)[1] + gu[2] * (X)[2] + gu[4] * (X)[4]))
-    const double Rs = TRU(Ric);
+    const T Rs = sdotw(Ric, gw);
 
-    // ---- Z terms: Zl_i = h_ik (Gamma-hat^k - Gt^k)/2 ; R^Z_ij = R_ij + D_i Z_j + D_j Z_i
-    double dG[3], Zl[3], Zu[3];
+    // ---- Z terms: Zl_i = (h_ik Gamma-hat^k - Gl_i)/2, R^Z_ij = R_ij + D_i Z_j + D_j Z_i
+    GRF_SECTION(6);
+    T dG[3], Zl[3], Zu[3];
+    const T Gh[3] = {v[F_GAM], v[F_GAM + 1], v[F_GAM + 2]};
 #pragma unroll
-    for (int k = 0; k < 3; ++k) dG[k] = v[F_GAM + k] - Gtc[k];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        Zl[i] = 0.5 * (h[sidx(i, 0)] * dG[0] + h[sidx(i, 1)] * dG[1] + h[sidx(i, 2)] * dG[2]);
-        Zu[i] = 0.5 * chi * dG[i];
+    for (int k = 0; k < 3; ++k) {
+        dG[k] = Gh[k] - Gtc[k];
+        Zu[k] = (0.5 * chi) * dG[k];
     }
-    double RZ[6];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        Zl[i] = 0.5 * (h[sidx(i, 0)] * Gh[0] + h[sidx(i, 1)] * Gh[1] + h[sidx(i, 2)] * Gh[2] - Gl[i]);
+    T RZ[6];
     {
-        double dZ[3][3];  // dZ[j][i] = d_j Zl_i
+        T dZ[3][3];  // dZ[j][i] = d_j Zl_i
 #pragma unroll
         for (int j = 0; j < 3; ++j)
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
-                double s = 0.0;
+                T s = -dGl[j][i];
 #pragma unroll
-                for (int k = 0; k < 3; ++k) s += dh[j][sidx(i, k)] * dG[k] + h[sidx(i, k)] * (D1(F_GAM + k, j) - dGtc[j][k]);
+                for (int k = 0; k < 3; ++k) s = fma(dh[j][sidx(i, k)], Gh[k], fma(h[sidx(i, k)], D1(F_GAM + k, j), s));
                 dZ[j][i] = 0.5 * s;
             }
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
             for (int j = i; j < 3; ++j) {
-                const double gz = Gp[0][sidx(i, j)] * Zl[0] + Gp[1][sidx(i, j)] * Zl[1] + Gp[2][sidx(i, j)] * Zl[2];
-                RZ[sidx(i, j)] = Ric[sidx(i, j)] + dZ[i][j] + dZ[j][i] - 2.0 * gz;
+                const T gz = Gp[0][sidx(i, j)] * Zl[0] + Gp[1][sidx(i, j)] * Zl[1] + Gp[2][sidx(i, j)] * Zl[2];
+                RZ[sidx(i, j)] = fma(-2.0, gz, Ric[sidx(i, j)] + (dZ[i][j] + dZ[j][i]));
             }
     }
-    const double RZs = TRU(RZ);
+    const T RZs = sdotw(RZ, gw);
 
     // ---- D_i D_j lapse, D_i D_j phi (physical)
-    double DDa[6], DDp[6];
+    GRF_SECTION(7);
+    T DDa[6], DDp[6];
 #pragma unroll
     for (int m = 0; m < 6; ++m) {
         DDa[m] = D2(F_LAPSE, m) - Gp[0][m] * dal[0] - Gp[1][m] * dal[1] - Gp[2][m] * dal[2];
         DDp[m] = D2(F_PHI, m) - Gp[0][m] * dphi[0] - Gp[1][m] * dphi[1] - Gp[2][m] * dphi[2];
     }
-    const double lapal = TRU(DDa);
+    const T lapal = sdotw(DDa, gw);
 
     // ---- extrinsic curvature K_ij = (A_ij + h_ij K/3)/chi and friends
-    double Kp[6], Aud[3][3], Kud[3][3];
+    GRF_SECTION(8);
+    const T K3 = K * (1.0 / 3.0);
+    T Kp[6], Aud[3][3];
 #pragma unroll
-    for (int m = 0; m < 6; ++m) Kp[m] = (A[m] + h[m] * K * (1.0 / 3.0)) * ichi;
+    for (int m = 0; m < 6; ++m) Kp[m] = fma(h[m], K3, A[m]) * ichi;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
+        for (int j = 0; j < 3; ++j)
             Aud[i][j] = hi[sidx(i, 0)] * A[sidx(0, j)] + hi[sidx(i, 1)] * A[sidx(1, j)] + hi[sidx(i, 2)] * A[sidx(2, j)];
-            Kud[i][j] = Aud[i][j] + (i == j ? K * (1.0 / 3.0) : 0.0);
-        }
-    const double trK = K + Aud[0][0] + Aud[1][1] + Aud[2][2];
-    double Au[6];
+    // K^i_j = A^i_j + delta^i_j K/3
+    auto Kud = [&](int i, int j) -> T { return i == j ? Aud[i][j] + K3 : Aud[i][j]; };
+    const T trK = K + Aud[0][0] + Aud[1][1] + Aud[2][2];
+    T Au[6];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = i; j < 3; ++j)
             Au[sidx(i, j)] = Aud[i][0] * hi[sidx(0, j)] + Aud[i][1] * hi[sidx(1, j)] + Aud[i][2] * hi[sidx(2, j)];
-    const double AA = A[0] * Au[0] + A[3] * Au[3] + A[5] * Au[5] + 2.0 * (A[1] * Au[1] + A[2] * Au[2] + A[4] * Au[4]);
-    double KK[6];  // K_ik K^k_j
+    const T AA = A[0] * Au[0] + A[3] * Au[3] + A[5] * Au[5] + 2.0 * (A[1] * Au[1] + A[2] * Au[2] + A[4] * Au[4]);
+    T KK[6];  // K_ik K^k_j
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = i; j < 3; ++j)
-            KK[sidx(i, j)] = Kp[sidx(i, 0)] * Kud[0][j] + Kp[sidx(i, 1)] * Kud[1][j] + Kp[sidx(i, 2)] * Kud[2][j];
-
-    // d_k K_ij, D_k K_ij, L_beta K_ij
-    double dKp[3][6];
+            KK[sidx(i, j)] = Kp[sidx(i, 0)] * Kud(0, j) + Kp[sidx(i, 1)] * Kud(1, j) + Kp[sidx(i, 2)] * Kud(2, j);
+    T dKp[3][6];
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
+    for (int k = 0; k < 3; ++k) {
+        const T dK3 = dK[k] * (1.0 / 3.0);
 #pragma unroll
         for (int m = 0; m < 6; ++m)
-            dKp[k][m] = (D1(F_A + m, k) + (dh[k][m] * K + h[m] * dK[k]) * (1.0 / 3.0) - Kp[m] * dchi[k]) * ichi;
-    double LbK[6];
+            dKp[k][m] = fma(-Kp[m], dchi[k], fma(dh[k][m], K3, fma(h[m], dK3, D1(F_A + m, k)))) * ichi;
+    }
+    T LbK[6];
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = i; j < 3; ++j) {
-            double s = bx * dKp[0][sidx(i, j)] + by * dKp[1][sidx(i, j)] + bz * dKp[2][sidx(i, j)];
+            T s = bx * dKp[0][sidx(i, j)] + by * dKp[1][sidx(i, j)] + bz * dKp[2][sidx(i, j)];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) s += Kp[sidx(k, j)] * db[i][k] + Kp[sidx(i, k)] * db[j][k];
+            for (int k = 0; k < 3; ++k) s = fma(Kp[sidx(k, j)], db[i][k], fma(Kp[sidx(i, k)], db[j][k], s));
             LbK[sidx(i, j)] = s;
         }
-    // Codazzi block: Bc[k][i][j] = D_i K_kj - D_j K_ki
-    double Bc[3][3][3];
+    // Codazzi block through its dual: bb[k][m] = B_{k,(m+1),(m+2)} = D_(m+1) K_k(m+2) - D_(m+2) K_k(m+1)
+    T bb[3][3];
     {
-        double DK[3][6];  // DK[k][ij] = D_k K_ij
+        T DK[3][6];  // D_k K_ij
 #pragma unroll
         for (int k = 0; k < 3; ++k)
 #pragma unroll
             for (int i = 0; i < 3; ++i)
 #pragma unroll
                 for (int j = i; j < 3; ++j) {
-                    double s = dKp[k][sidx(i, j)];
+                    T s = dKp[k][sidx(i, j)];
 #pragma unroll
-                    for (int l = 0; l < 3; ++l) s -= Gp[l][sidx(k, i)] * Kp[sidx(l, j)] + Gp[l][sidx(k, j)] * Kp[sidx(i, l)];
+                    for (int l = 0; l < 3; ++l)
+                        s = fma(-Gp[l][sidx(k, i)], Kp[sidx(l, j)], fma(-Gp[l][sidx(k, j)], Kp[sidx(i, l)], s));
                     DK[k][sidx(i, j)] = s;
                 }
 #pragma unroll
         for (int k = 0; k < 3; ++k)
 #pragma unroll
-            for (int i = 0; i < 3; ++i)
-#pragma unroll
-                for (int j = 0; j < 3; ++j) Bc[k][i][j] = (i == j) ? 0.0 : DK[i][sidx(k, j)] - DK[j][sidx(k, i)];
+            for (int m = 0; m < 3; ++m) {
+                const int a = (m + 1) % 3, b = (m + 2) % 3;
+                bb[k][m] = DK[a][sidx(k, b)] - DK[b][sidx(k, a)];
+            }
     }
-    double Bv[3];  // B_j = gamma^ab B_abj
+#define BC(k, i, j) (cyclic(i, j) ? bb[k][third(i, j)] : -bb[k][third(i, j)])
+    T Bv[3];  // B_j = gamma^ab B_abj
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        double s = 0.0;
+        T s = 0.0;
+        bool first = true;
 #pragma unroll
         for (int a = 0; a < 3; ++a)
 #pragma unroll
-            for (int b = 0; b < 3; ++b) s += gu[sidx(a, b)] * Bc[a][b][j];
+            for (int b = 0; b < 3; ++b)
+                if (b != j) {
+                    s = first ? gu[sidx(a, b)] * BC(a, b, j) : fma(gu[sidx(a, b)], BC(a, b, j), s);
+                    first = false;
+                }
         Bv[j] = s;
     }
 
-    // ---- Gauss block and its Einstein tensor
-    double S[6];
+    // ---- Gauss block S_ij and its Einstein tensor G_S
+    GRF_SECTION(9);
+    T S[6];
 #pragma unroll
-    for (int m = 0; m < 6; ++m) S[m] = Ric[m] + trK * Kp[m] - KK[m];
-    const double Ss = TRU(S);
-    double GS[6], GSu[6];
+    for (int m = 0; m < 6; ++m) S[m] = fma(trK, Kp[m], Ric[m] - KK[m]);
+    const T Ss = sdotw(S, gw);
+    T GS[6], GSuw[6];
 #pragma unroll
-    for (int m = 0; m < 6; ++m) GS[m] = S[m] - 0.5 * gd[m] * Ss;
-    // raise both indices: GSu = gu GS gu
+    for (int m = 0; m < 6; ++m) GS[m] = fma(-0.5 * Ss, gd[m], S[m]);
+    {
+        T M1[3][3];  // gamma^ia G_S ab
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+        for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int j = i; j < 3; ++j) {
-            double s = 0.0;
+            for (int b = 0; b < 3; ++b)
+                M1[i][b] = gu[sidx(i, 0)] * GS[sidx(0, b)] + gu[sidx(i, 1)] * GS[sidx(1, b)] + gu[sidx(i, 2)] * GS[sidx(2, b)];
 #pragma unroll
-            for (int a = 0; a < 3; ++a)
+        for (int i = 0; i < 3; ++i)
 #pragma unroll
-                for (int b = 0; b < 3; ++b) s += gu[sidx(i, a)] * GS[sidx(a, b)] * gu[sidx(b, j)];
-            GSu[sidx(i, j)] = s;
-        }
+            for (int j = i; j < 3; ++j) {
+                const T x = M1[i][0] * gu[sidx(0, j)] + M1[i][1] * gu[sidx(1, j)] + M1[i][2] * gu[sidx(2, j)];
+                GSuw[sidx(i, j)] = (i == j) ? x : 2.0 * x;  // G_S^ij, off-diagonals doubled
+            }
+    }
 
     // ---- scalar: nabla nabla phi blocks, Phi = nabla nabla beta(phi)
-    double b1, b2;
+    GRF_SECTION(10);
+    T b1, b2;
     if (c.beta_kind == 1) { b1 = c.lam * phi; b2 = c.lam; } else { b1 = c.lam; b2 = 0.0; }
-    double dphiu[3];
+    T dphiu[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) dphiu[i] = gu[sidx(i, 0)] * dphi[0] + gu[sidx(i, 1)] * dphi[1] + gu[sidx(i, 2)] * dphi[2];
-    const double dphi2 = dphi[0] * dphiu[0] + dphi[1] * dphiu[1] + dphi[2] * dphiu[2];
-    const double X = 0.5 * (Pi * Pi - dphi2);
+    const T dphi2 = dphi[0] * dphiu[0] + dphi[1] * dphiu[1] + dphi[2] * dphiu[2];
+    const T X = 0.5 * (Pi * Pi - dphi2);
     const double g2 = c.g2;
-    double Hij[6], Hn[3];
+    T Hij[6], Hn[3];
 #pragma unroll
-    for (int m = 0; m < 6; ++m) Hij[m] = DDp[m] + Kp[m] * Pi;
+    for (int m = 0; m < 6; ++m) Hij[m] = fma(Kp[m], Pi, DDp[m]);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) Hn[i] = dPi[i] + Kud[0][i] * dphi[0] + Kud[1][i] * dphi[1] + Kud[2][i] * dphi[2];
-    double Phd[6], Phn[3];
+    for (int i = 0; i < 3; ++i) Hn[i] = dPi[i] + Kud(0, i) * dphi[0] + Kud(1, i) * dphi[1] + Kud(2, i) * dphi[2];
+    T Phd[6], Phn[3];
+    const T b2Pi = b2 * Pi;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        Phn[i] = b1 * Hn[i] + b2 * Pi * dphi[i];
+        Phn[i] = fma(b1, Hn[i], b2Pi * dphi[i]);
+        const T b2d = b2 * dphi[i];
 #pragma unroll
-        for (int j = i; j < 3; ++j) Phd[sidx(i, j)] = b1 * Hij[sidx(i, j)] + b2 * dphi[i] * dphi[j];
+        for (int j = i; j < 3; ++j) Phd[sidx(i, j)] = fma(b1, Hij[sidx(i, j)], b2d * dphi[j]);
     }
-    double Phm[3][3], Phu[6], Phnu[3];  // Phi_i^k, Phi^ij, Phi_n^k
+    T Phm[3][3], Phuw[6], Phnu[3];  // Phi_i^k, Phi^ij (off-diagonals doubled), Phi_n^k
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -469,258 +545,267 @@ __device__ __forceinline__ void point_rhs(const Coeffs& c, const PointIn& in, do
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
 #pragma unroll
-        for (int j = i; j < 3; ++j)
-            Phu[sidx(i, j)] = gu[sidx(i, 0)] * Phm[0][j] + gu[sidx(i, 1)] * Phm[1][j] + gu[sidx(i, 2)] * Phm[2][j];
+        for (int j = i; j < 3; ++j) {
+            const T x = gu[sidx(i, 0)] * Phm[0][j] + gu[sidx(i, 1)] * Phm[1][j] + gu[sidx(i, 2)] * Phm[2][j];
+            Phuw[sidx(i, j)] = (i == j) ? x : 2.0 * x;
+        }
         Phnu[i] = gu[sidx(i, 0)] * Phn[0] + gu[sidx(i, 1)] * Phn[1] + gu[sidx(i, 2)] * Phn[2];
     }
-    const double trP = Phm[0][0] + Phm[1][1] + Phm[2][2];
+    const T trP = Phm[0][0] + Phm[1][1] + Phm[2][2];
 
     // ---- sources that do not depend on the unknowns
-    const double fX = 1.0 + 2.0 * g2 * X;
-    double rho8 = 0.5 * fX * Pi * Pi - 0.5 * (X + g2 * X * X);
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) rho8 -= 4.0 * GS[sidx(i, j)] * Phu[sidx(i, j)];
-    double S8[3];
-    const double BPn = Bv[0] * Phnu[0] + Bv[1] * Phnu[1] + Bv[2] * Phnu[2];
+    GRF_SECTION(11);
+    const T fX = fma(2.0 * g2, X, 1.0);
+    const T XX = fma(g2 * X, X, X);  // X + g2 X^2
+    const T rho8 = fma(0.5 * fX, Pi * Pi, fma(-4.0, sdotw(GS, Phuw), -0.5 * XX));
+    T S8[3];
+    const T BPn = Bv[0] * Phnu[0] + Bv[1] * Phnu[1] + Bv[2] * Phnu[2];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        double s = GS[sidx(i, 0)] * Phnu[0] + GS[sidx(i, 1)] * Phnu[1] + GS[sidx(i, 2)] * Phnu[2]
-                   - (Phm[i][0] * Bv[0] + Phm[i][1] * Bv[1] + Phm[i][2] * Bv[2]) + trP * Bv[i];
+        T s = GS[sidx(i, 0)] * Phnu[0] + GS[sidx(i, 1)] * Phnu[1] + GS[sidx(i, 2)] * Phnu[2];
+        s = fma(trP, Bv[i], s - (Phm[i][0] * Bv[0] + Phm[i][1] * Bv[1] + Phm[i][2] * Bv[2]));
 #pragma unroll
         for (int k = 0; k < 3; ++k)
 #pragma unroll
-            for (int l = 0; l < 3; ++l) s += Bc[k][i][l] * Phu[sidx(k, l)];
-        S8[i] = -0.5 * fX * Pi * dphi[i] + 4.0 * s;
+            for (int l = 0; l < 3; ++l)
+                if (l != i) {
+                    const T pkl = (k == l) ? Phuw[sidx(k, l)] : 0.5 * Phuw[sidx(k, l)];
+                    s = fma(BC(k, i, l), pkl, s);
+                }
+        S8[i] = fma(-0.5 * fX * Pi, dphi[i], 4.0 * s);
     }
-    // first-order S_ij and the Y_ij (mixed-block) part of the Gauss-Bonnet S_ij
-    double S1[6], Y[6];
+    T S1[6], Y[6];
+    const T fXh = 0.5 * fX, XXh = 0.5 * XX;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = i; j < 3; ++j) {
-            S1[sidx(i, j)] = 0.5 * fX * dphi[i] * dphi[j] + 0.5 * gd[sidx(i, j)] * (X + g2 * X * X);
-            double y = 0.0;
+            S1[sidx(i, j)] = fma(fXh * dphi[i], dphi[j], XXh * gd[sidx(i, j)]);
+            T y = fma(Bv[j], Phn[i], Bv[i] * Phn[j]);
+            y = fma(-2.0 * BPn, gd[sidx(i, j)], y);
 #pragma unroll
-            for (int l = 0; l < 3; ++l) y += (Bc[i][j][l] + Bc[j][i][l]) * Phnu[l];
-            Y[sidx(i, j)] = y - 2.0 * gd[sidx(i, j)] * BPn + Bv[j] * Phn[i] + Bv[i] * Phn[j];
+            for (int l = 0; l < 3; ++l) {
+                if (l != j) y = fma(BC(i, j, l), Phnu[l], y);
+                if (l != i) y = fma(BC(j, i, l), Phnu[l], y);
+            }
+            Y[sidx(i, j)] = y;
         }
+
     // C0 = C at d_t K_ij = 0
-    double C0[6];
+    GRF_SECTION(12);
+    T C0[6];
 #pragma unroll
-    for (int m = 0; m < 6; ++m) C0[m] = (DDa[m] - LbK[m]) * ial + KK[m];
-    const double bdPi = bx * dPi[0] + by * dPi[1] + bz * dPi[2];
-    const double dadp = dal[0] * dphiu[0] + dal[1] * dphiu[1] + dal[2] * dphiu[2];
-    const double Phnn0 = b1 * (-bdPi - dadp) * ial + b2 * Pi * Pi;
-    // L_GB at d_t K_ij = 0
-    double L0;
+    for (int m = 0; m < 6; ++m) C0[m] = fma(DDa[m] - LbK[m], ial, KK[m]);
+    const T bdPi = bx * dPi[0] + by * dPi[1] + bz * dPi[2];
+    const T dadp = dal[0] * dphiu[0] + dal[1] * dphiu[1] + dal[2] * dphiu[2];
+    const T Phnn0 = fma(b1 * ial, -(bdPi + dadp), b2Pi * Pi);
+
+    // L_GB at d_t K_ij = 0: 8 G_S^ij C_ij - 4 B_kij B^kij + 8 B_i B^i, with
+    // B_kij B^kij = 2 chi^3 / det(h) h^kk' h_mm' bb[k][m] bb[k'][m']
+    GRF_SECTION(13);
+    T L0;
     {
-        double gc = 0.0;
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) gc += GSu[sidx(i, j)] * C0[sidx(i, j)];
-        // B_kij B^kij through the dual b_k^m = B_k,(m+1)(m+2):  = 2 chi^3/det(h) h^kk' h_mm' b_k^m b_k'^m'
-        double bb[3][3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) { bb[k][0] = Bc[k][1][2]; bb[k][1] = Bc[k][2][0]; bb[k][2] = Bc[k][0][1]; }
-        double s = 0.0;
+        T N[3][3];
 #pragma unroll
         for (int k = 0; k < 3; ++k)
 #pragma unroll
-            for (int kk = 0; kk < 3; ++kk) {
-                double t = 0.0;
+            for (int q = 0; q < 3; ++q)
+                N[k][q] = h[sidx(0, q)] * bb[k][0] + h[sidx(1, q)] * bb[k][1] + h[sidx(2, q)] * bb[k][2];
+        T tt[6];
 #pragma unroll
-                for (int m = 0; m < 3; ++m)
+        for (int k = 0; k < 3; ++k)
 #pragma unroll
-                    for (int mm = 0; mm < 3; ++mm) t += h[sidx(m, mm)] * bb[k][m] * bb[kk][mm];
-                s += hi[sidx(k, kk)] * t;
-            }
-        const double BB = 2.0 * chi * chi * chi / deth * s;
-        const double BvBv = Bv[0] * (gu[0] * Bv[0] + gu[1] * Bv[1] + gu[2] * Bv[2])
-                            + Bv[1] * (gu[1] * Bv[0] + gu[3] * Bv[1] + gu[4] * Bv[2])
-                            + Bv[2] * (gu[2] * Bv[0] + gu[4] * Bv[1] + gu[5] * Bv[2]);
-        L0 = 8.0 * gc - 4.0 * BB + 8.0 * BvBv;
+            for (int kk = k; kk < 3; ++kk) tt[sidx(k, kk)] = N[k][0] * bb[kk][0] + N[k][1] * bb[kk][1] + N[k][2] * bb[kk][2];
+        const T BB = (2.0 * chi * chi * chi * ideth) * sdotw(tt, hw);
+        const T Bvu0 = gu[0] * Bv[0] + gu[1] * Bv[1] + gu[2] * Bv[2];
+        const T Bvu1 = gu[1] * Bv[0] + gu[3] * Bv[1] + gu[4] * Bv[2];
+        const T Bvu2 = gu[2] * Bv[0] + gu[4] * Bv[1] + gu[5] * Bv[2];
+        const T BvBv = Bv[0] * Bvu0 + Bv[1] * Bvu1 + Bv[2] * Bvu2;
+        L0 = fma(8.0, sdotw(C0, GSuw), fma(-4.0, BB, 8.0 * BvBv));
     }
 
     // ---- CCZ4 right-hand sides without S_ij (rho and S_i included)
-    rhs[F_CHI] = ADV(F_CHI) + (2.0 / 3.0) * chi * (al * K - divb);
+    GRF_SECTION(14);
+    rhs[F_CHI] = fma((2.0 / 3.0) * chi, al * K - divb, ADV(F_CHI));
+    const T divb23 = (2.0 / 3.0) * divb;
+    const T al2 = 2.0 * al;
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = i; j < 3; ++j) {
-            double x = ADV(F_H + sidx(i, j)) - (2.0 / 3.0) * h[sidx(i, j)] * divb - 2.0 * al * A[sidx(i, j)];
+            T x = fma(-h[sidx(i, j)], divb23, fma(-al2, A[sidx(i, j)], ADV(F_H + sidx(i, j))));
 #pragma unroll
-            for (int k = 0; k < 3; ++k) x += h[sidx(i, k)] * db[j][k] + h[sidx(j, k)] * db[i][k];
+            for (int k = 0; k < 3; ++k) x = fma(h[sidx(i, k)], db[j][k], fma(h[sidx(j, k)], db[i][k], x));
             rhs[F_H + sidx(i, j)] = x;
         }
-    const double Kdot0 = ADV(F_K) + al * (RZs + K * (K - 2.0 * Th)) - 3.0 * al * c.kappa1 * (1.0 + c.kappa2) * Th
-                         - lapal - 1.5 * al * rho8
-                         - c.bK * al * (Rs - AA + (2.0 / 3.0) * K * K - 2.0 * rho8);
-    double Adot0[6];
+    const T K2Th = K - 2.0 * Th;
+    const T Kdot0 = ADV(F_K) + al * fma(K, K2Th, RZs) - (3.0 * c.kappa1 * (1.0 + c.kappa2)) * al * Th - lapal
+                    - 1.5 * al * rho8 - (c.bK * al) * (Rs - AA + (2.0 / 3.0) * K * K - 2.0 * rho8);
+    T Adot0[6];
     {
-        double Xa[6];
+        T Xa[6];
 #pragma unroll
-        for (int m = 0; m < 6; ++m) Xa[m] = -DDa[m] + al * RZ[m];
-        const double trX = hi[0] * Xa[0] + hi[3] * Xa[3] + hi[5] * Xa[5] + 2.0 * (hi[1] * Xa[1] + hi[2] * Xa[2] + hi[4] * Xa[4]);
+        for (int m = 0; m < 6; ++m) Xa[m] = fma(al, RZ[m], -DDa[m]);
+        const T trX3 = sdotw(Xa, hw) * (1.0 / 3.0);
+        const T alK2Th = al * K2Th;
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
             for (int j = i; j < 3; ++j) {
-                double x = ADV(F_A + sidx(i, j)) + chi * (Xa[sidx(i, j)] - h[sidx(i, j)] * trX * (1.0 / 3.0))
-                           + al * (K - 2.0 * Th) * A[sidx(i, j)] - (2.0 / 3.0) * A[sidx(i, j)] * divb;
+                T x = fma(chi, fma(-h[sidx(i, j)], trX3, Xa[sidx(i, j)]), ADV(F_A + sidx(i, j)));
+                x = fma(alK2Th - divb23, A[sidx(i, j)], x);
 #pragma unroll
                 for (int k = 0; k < 3; ++k)
-                    x += -2.0 * al * A[sidx(i, k)] * Aud[k][j] + A[sidx(i, k)] * db[j][k] + A[sidx(j, k)] * db[i][k];
+                    x = fma(A[sidx(i, k)], fma(-al2, Aud[k][j], db[j][k]), fma(A[sidx(j, k)], db[i][k], x));
                 Adot0[sidx(i, j)] = x;
             }
     }
-    rhs[F_TH] = ADV(F_TH) + c.bTh * al * (RZs - AA + (2.0 / 3.0) * K * K - 2.0 * Th * K - 2.0 * rho8)
-                - (Zu[0] * dal[0] + Zu[1] * dal[1] + Zu[2] * dal[2]) - al * c.kappa1 * (2.0 + c.kappa2) * Th;
+    rhs[F_TH] = ADV(F_TH) + (c.bTh * al) * (RZs - AA + (2.0 / 3.0) * K * K - 2.0 * Th * K - 2.0 * rho8)
+                - (Zu[0] * dal[0] + Zu[1] * dal[1] + Zu[2] * dal[2]) - (c.kappa1 * (2.0 + c.kappa2)) * al * Th;
     {
-        double hZ[3];
+        T hZ[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) hZ[i] = hi[sidx(i, 0)] * Zl[0] + hi[sidx(i, 1)] * Zl[1] + hi[sidx(i, 2)] * Zl[2];
-        double ddbk[3];  // sum_k d_j d_k beta^k
+        T ddbk[3];  // sum_k d_j d_k beta^k
 #pragma unroll
         for (int j = 0; j < 3; ++j) ddbk[j] = D2(F_SHIFT, sidx(j, 0)) + D2(F_SHIFT + 1, sidx(j, 1)) + D2(F_SHIFT + 2, sidx(j, 2));
+        T Auw[6];
+#pragma unroll
+        for (int m = 0; m < 6; ++m) Auw[m] = (m == 1 || m == 2 || m == 4) ? 2.0 * Au[m] : Au[m];
+        T tk[3];  // 2 (al d_k Theta - Theta d_k al - 2/3 al K Z_k)
+        const T alK23 = (2.0 / 3.0) * al * K;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) tk[k] = 2.0 * fma(al, dTh[k], fma(-Th, dal[k], -alK23 * Zl[k]));
+        const T k3div = (4.0 / 3.0) * c.kappa3 * divb;
+        const T ak1 = 2.0 * al * c.kappa1;
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            double t1 = 0.0, t2 = 0.0, t3 = 0.0, t4 = 0.0, t5 = 0.0, t6 = 0.0;
+            const T t1 = sdotw(G2[i], Auw);
+            const T t2 = Au[sidx(i, 0)] * dchi[0] + Au[sidx(i, 1)] * dchi[1] + Au[sidx(i, 2)] * dchi[2];
+            const T t3 = hi[sidx(i, 0)] * dK[0] + hi[sidx(i, 1)] * dK[1] + hi[sidx(i, 2)] * dK[2];
+            const T t4 = Au[sidx(i, 0)] * dal[0] + Au[sidx(i, 1)] * dal[1] + Au[sidx(i, 2)] * dal[2];
+            T t5 = 0.0;
 #pragma unroll
-            for (int j = 0; j < 3; ++j) {
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    t1 += G2[i][sidx(j, k)] * Au[sidx(j, k)];
-                    t5 += hi[sidx(j, k)] * D2(F_SHIFT + i, sidx(j, k));
-                    t6 += hi[sidx(j, k)] * Zl[j] * db[k][i];
-                }
-                t2 += Au[sidx(i, j)] * dchi[j];
-                t3 += hi[sidx(i, j)] * dK[j];
-                t4 += Au[sidx(i, j)] * dal[j];
-            }
-            double x = ADV(F_GAM + i) + 2.0 * al * (t1 - 1.5 * ichi * t2 - (2.0 / 3.0) * t3) - 2.0 * t4 + t5;
+            for (int q = 0; q < 6; ++q) t5 = (q == 0) ? hw[0] * D2(F_SHIFT + i, 0) : fma(hw[q], D2(F_SHIFT + i, q), t5);
+            const T t6 = hZ[0] * db[0][i] + hZ[1] * db[1][i] + hZ[2] * db[2][i];
+            T x = ADV(F_GAM + i) + al2 * (t1 - (1.5 * ichi) * t2 - (2.0 / 3.0) * t3) - 2.0 * t4 + t5;
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                x += 2.0 * hi[sidx(k, i)] * (al * dTh[k] - Th * dal[k] - (2.0 / 3.0) * al * K * Zl[k]);
-                x += (1.0 / 3.0) * hi[sidx(i, k)] * ddbk[k] - Gtc[k] * db[k][i];
+                x = fma(hi[sidx(k, i)], fma(1.0 / 3.0, ddbk[k], tk[k]), x);
+                x = fma(-Gtc[k], db[k][i], x);
             }
-            x += (2.0 / 3.0) * Gtc[i] * divb + 2.0 * c.kappa3 * ((2.0 / 3.0) * hZ[i] * divb - t6)
-                 - 2.0 * al * c.kappa1 * hZ[i]
-                 - 2.0 * al * (hi[sidx(i, 0)] * S8[0] + hi[sidx(i, 1)] * S8[1] + hi[sidx(i, 2)] * S8[2]);
+            x = fma((2.0 / 3.0) * divb, Gtc[i], x);
+            x = fma(k3div - ak1, hZ[i], x);
+            x = fma(-2.0 * c.kappa3, t6, x);
+            x = fma(-al2, hi[sidx(i, 0)] * S8[0] + hi[sidx(i, 1)] * S8[1] + hi[sidx(i, 2)] * S8[2], x);
             rhs[F_GAM + i] = x;
-            rhs[F_B + i] = x - c.eta * v[F_B + i];
-            rhs[F_SHIFT + i] = c.shift_F * v[F_B + i] * c.inv_1pa
-                               - c.a_1pa * al * chi * (hi[sidx(i, 0)] * dal[0] + hi[sidx(i, 1)] * dal[1] + hi[sidx(i, 2)] * dal[2]);
+            rhs[F_B + i] = fma(-c.eta, v[F_B + i], x);
+            rhs[F_SHIFT + i] = fma(c.shift_F * c.inv_1pa, v[F_B + i],
+                                   -(c.a_1pa * al * chi) * (hi[sidx(i, 0)] * dal[0] + hi[sidx(i, 1)] * dal[1] + hi[sidx(i, 2)] * dal[2]));
         }
     }
-    rhs[F_LAPSE] = ADV(F_LAPSE) - 2.0 * al * (K - 2.0 * Th) * c.inv_1pa;
-    rhs[F_PHI] = al * Pi + ADV(F_PHI);
+    rhs[F_LAPSE] = fma(-2.0 * c.inv_1pa * al, K2Th, ADV(F_LAPSE));
+    rhs[F_PHI] = fma(al, Pi, ADV(F_PHI));
 
-    // ---- coupled system for v = (d_t K_ij, d_t Pi)
-    double Msys[7][8];
+    // ---- coupled system for v = (d_t K_ij, d_t Pi):
+    //   u - 4 L(Q(u)) - 4 b1 L(G_S) w = r,   w - (8 b1 / D) G_S^ij u_ij = r_w,   L(X) = X - gamma tr(X)/2
+    GRF_SECTION(15);
+    T Msys[7][8];
+    T QC0[6];
+    q_of(C0, gd, gw, Phd, Phuw, Phm, trP, QC0);
     {
-        // U0_ij: d_t K_ij implied by the S_ij-free right-hand sides
-        const double chid = rhs[F_CHI];
-        double LGS[6], rr[6], QC0[6], LS1[6], LY[6];
-        const double trS1 = TRU(S1), trY = TRU(Y);
+        const T chid = rhs[F_CHI];
+        const T trS1h = 0.5 * sdotw(S1, gw), trYh = 0.5 * sdotw(Y, gw), trQh = 0.5 * sdotw(QC0, gw);
+        const T Ss4 = 0.25 * Ss;
+        const T al4 = 4.0 * al;
+        const T four_b1 = 4.0 * b1;
 #pragma unroll
         for (int m = 0; m < 6; ++m) {
-            LGS[m] = S[m] - 0.25 * gd[m] * Ss;
-            LS1[m] = S1[m] - 0.5 * gd[m] * trS1;
-            LY[m] = Y[m] - 0.5 * gd[m] * trY;
+            const T LGS = fma(-Ss4, gd[m], S[m]);
+            const T U0 = fma(-Kp[m], chid, fma(rhs[F_H + m], K3, fma(h[m], Kdot0 * (1.0 / 3.0), Adot0[m]))) * ichi;
+            const T lin = fma(LGS, Phnn0, (Y[m] + QC0[m]) - gd[m] * (trYh + trQh));
+            Msys[m][7] = fma(al4, lin, fma(-al, fma(-trS1h, gd[m], S1[m]), U0));
+            Msys[m][6] = -four_b1 * LGS;
         }
-        apply_LQ(C0, gd, gu, Phd, Phu, Phm, trP, QC0);  // = L(Q(C0))
+        // 6x6 block, column (a,b): -4 L(Q(E_ab)) with E_ab the unit symmetric matrix
+        //   = -2 gamma_ij w_ab (Phi^ab - gamma^ab tr Phi) - 4 w_ab gamma^ab Phi_ij + 4 P_ij,ab - 4 tr(Phi) [ij == ab]
+        //   P_ij,ab = Phi_i^k E_kj + Phi_j^k E_ik
+        const T one4P = fma(-4.0, trP, 1.0);
 #pragma unroll
-        for (int m = 0; m < 6; ++m) {
-            const double U0 = (Adot0[m] + (rhs[F_H + m] * K + h[m] * Kdot0) * (1.0 / 3.0) - Kp[m] * chid) * ichi;
-            rr[m] = U0 - al * LS1[m] + 4.0 * al * (LGS[m] * Phnn0 + LY[m] + QC0[m]);
-        }
-        // u-rows: u - 4 L(Q(u)) - 4 b1 L(G_S) w = r
+        for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int col = 0; col < 6; ++col) {
-            double e[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-            e[col] = 1.0;
-            double q[6];
-            apply_LQ(e, gd, gu, Phd, Phu, Phm, trP, q);
+            for (int b = a; b < 3; ++b) {
+                const int col = sidx(a, b);
+                const T sab = Phuw[col] - gw[col] * trP;   // w_ab (Phi^ab - gamma^ab trP)
+                const T tab = -4.0 * gw[col];               // -4 w_ab gamma^ab
 #pragma unroll
-            for (int row = 0; row < 6; ++row) Msys[row][col] = (row == col ? 1.0 : 0.0) - 4.0 * q[row];
-        }
+                for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int row = 0; row < 6; ++row) {
-            Msys[row][6] = -4.0 * b1 * LGS[row];
-            Msys[row][7] = rr[row];
-        }
-        // w-row: w - (8 b1 / D) G_S^ij u_ij = r_w
-        const double Dphi = fX + 2.0 * g2 * Pi * Pi;
-        const double iD = 1.0 / Dphi;
+                    for (int j = i; j < 3; ++j) {
+                        const int row = sidx(i, j);
+                        T p = 0.0;
+                        bool any = false;
+                        // Phi_i^k E_kj: E_kj = [k==a][j==b] + [k==b][j==a] (single term when a == b)
+                        if (j == b) { p = any ? p + Phm[i][a] : Phm[i][a]; any = true; }
+                        if (a != b && j == a) { p = any ? p + Phm[i][b] : Phm[i][b]; any = true; }
+                        if (i == b) { p = any ? p + Phm[j][a] : Phm[j][a]; any = true; }
+                        if (a != b && i == a) { p = any ? p + Phm[j][b] : Phm[j][b]; any = true; }
+                        T e = fma(-2.0 * gd[row], sab, tab * Phd[row]);
+                        if (any) e = fma(4.0, p, e);
+                        if (row == col) e = e + one4P;
+                        Msys[row][col] = e;
+                    }
+            }
+        const T Dphi = fma(2.0 * g2, Pi * Pi, fX);
+        const T iD = 1.0 / Dphi;
+        const T c8 = -8.0 * b1 * iD;
 #pragma unroll
-        for (int col = 0; col < 6; ++col) {
-            const bool off = (col == 1 || col == 2 || col == 4);
-            Msys[6][col] = -8.0 * b1 * iD * GSu[col] * (off ? 2.0 : 1.0);
-        }
+        for (int col = 0; col < 6; ++col) Msys[6][col] = c8 * GSuw[col];
         Msys[6][6] = 1.0;
-        const double trH = TRU(Hij);
-        double Hnd = 0.0, Hdd = 0.0;
+        const T trH = sdotw(Hij, gw);
+        const T Hnd = dphiu[0] * Hn[0] + dphiu[1] * Hn[1] + dphiu[2] * Hn[2];
+        T Hdd = 0.0;
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            Hnd += dphiu[i] * Hn[i];
-#pragma unroll
-            for (int j = 0; j < 3; ++j) Hdd += dphiu[i] * dphiu[j] * Hij[sidx(i, j)];
+            const T t = Hij[sidx(i, 0)] * dphiu[0] + Hij[sidx(i, 1)] * dphiu[1] + Hij[sidx(i, 2)] * dphiu[2];
+            Hdd = (i == 0) ? dphiu[0] * t : fma(dphiu[i], t, Hdd);
         }
-        Msys[6][7] = bdPi + dadp + al * iD * (fX * trH + 4.0 * g2 * Pi * Hnd - 2.0 * g2 * Hdd + b1 * L0);
+        const T src = fma(fX, trH, fma(4.0 * g2 * Pi, Hnd, fma(-2.0 * g2, Hdd, b1 * L0)));
+        Msys[6][7] = fma(al * iD, src, bdPi + dadp);
     }
+    GRF_SECTION(16);
     ok = solve7(Msys);
-    double u[6];
+    T u[6];
 #pragma unroll
     for (int m = 0; m < 6; ++m) u[m] = Msys[m][7];
-    const double w = Msys[6][7];
+    const T w = Msys[6][7];
 
     // ---- full S_ij at the solution and the final K, A_ij, Pi right-hand sides
+    GRF_SECTION(17);
     {
-        double Cs[6], QC[6];
+        T Qu[6];
+        q_of(u, gd, gw, Phd, Phuw, Phm, trP, Qu);
+        const T Phnn = fma(b1 * ial, w, Phnn0);
+        T S8ij[6];
 #pragma unroll
-        for (int m = 0; m < 6; ++m) Cs[m] = C0[m] + u[m] * ial;
-        // Q(C) itself (not trace-reversed): Q = L(Q) + gamma tr(Q)/2 ... compute directly
-        double CP = 0.0, trC = 0.0;
+        for (int m = 0; m < 6; ++m) S8ij[m] = fma(-4.0, fma(GS[m], Phnn, Y[m] + fma(Qu[m], ial, QC0[m])), S1[m]);
+        const T Ss8 = sdotw(S8ij, gw);
+        rhs[F_K] = fma(0.5 * al, Ss8, Kdot0);
+        const T trh3 = sdotw(S8ij, hw) * (1.0 / 3.0);
+        const T alchi = al * chi;
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                CP += Cs[sidx(i, j)] * Phu[sidx(i, j)];
-                trC += Cs[sidx(i, j)] * gu[sidx(i, j)];
-            }
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = i; j < 3; ++j) {
-                double pc = 0.0;
-#pragma unroll
-                for (int k = 0; k < 3; ++k) pc += Phm[i][k] * Cs[sidx(k, j)] + Phm[j][k] * Cs[sidx(i, k)];
-                QC[sidx(i, j)] = gd[sidx(i, j)] * CP - pc + trP * Cs[sidx(i, j)] - trC * (gd[sidx(i, j)] * trP - Phd[sidx(i, j)]);
-            }
-        const double Phnn = Phnn0 + b1 * w * ial;
-        double S8ij[6];
-#pragma unroll
-        for (int m = 0; m < 6; ++m) S8ij[m] = S1[m] - 4.0 * (GS[m] * Phnn + Y[m] + QC[m]);
-        const double Ss8 = TRU(S8ij);
-        rhs[F_K] = Kdot0 + 0.5 * al * Ss8;
-        const double trh = hi[0] * S8ij[0] + hi[3] * S8ij[3] + hi[5] * S8ij[5]
-                           + 2.0 * (hi[1] * S8ij[1] + hi[2] * S8ij[2] + hi[4] * S8ij[4]);
-#pragma unroll
-        for (int m = 0; m < 6; ++m) rhs[F_A + m] = Adot0[m] - al * chi * (S8ij[m] - h[m] * trh * (1.0 / 3.0));
+        for (int m = 0; m < 6; ++m) rhs[F_A + m] = fma(-alchi, fma(-h[m], trh3, S8ij[m]), Adot0[m]);
         rhs[F_PI] = w;
     }
     if (extra) {
-        extra->ham = Ss - 2.0 * rho8;
+        extra->ham = fma(-2.0, rho8, Ss);
 #pragma unroll
         for (int i = 0; i < 3; ++i) extra->mom[i] = Bv[i] - S8[i];
     }
+#undef BC
 #undef D1
 #undef D2
 #undef ADV
-#undef TRU
 }
 
 }  // namespace grf

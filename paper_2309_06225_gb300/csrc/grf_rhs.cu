@@ -13,7 +13,7 @@ __global__ void __launch_bounds__(128) rhs_kernel(Geom g, Coeffs c, const double
     gather(g, s, p, in);
     double r[NFIELDS];
     bool ok = true;
-    point_rhs(c, in, r, nullptr, ok);
+    point_rhs<double>(c, in, r, nullptr, ok);
     if (!ok) atomicOr(status, 1);
 #pragma unroll 1
     for (int f = 0; f < NFIELDS; ++f) rhs[f * g.fstride + p] = r[f] + ko * ko6(s + f * g.fstride, p, g.pitch, g.plane);
@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(128) constraints_kernel(Geom g, Coeffs c, cons
         double r[NFIELDS];
         PointExtra ex;
         bool ok = true;
-        point_rhs(c, in, r, &ex, ok);
+        point_rhs<double>(c, in, r, &ex, ok);
         vals[0] = ex.ham;
         vals[1] = ex.mom[0];
         vals[2] = ex.mom[1];
