@@ -36,7 +36,7 @@ UNIT = "point-updates/s"
 BYTES_PER_POINT_UPDATE = 216 * (3 + 5 + 5 + 4)
 # dram__bytes_read.sum + dram__bytes_write.sum of one stage launch per interior point, from the
 # ncu capture of the current stage kernel (profiles/); None when the kernel changed since.
-TRAFFIC_BYTES_PER_POINT_STAGE = None
+TRAFFIC_BYTES_PER_POINT_STAGE = 6886  # mean of stage 0 and 1, 96^3 capture (profiles/rk4_stage_kernel_bl_pair_96.md)
 # FP64 (non-tensor) peak of GB300: 152 SMs x 2 FP64 FMA lanes/clk x 2 flop x ~2.06 GHz = 1.25 TFLOP/s
 FP64_PEAK_TFLOPS = 1.25
 
@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="bl_pair_256", choices=["bl_pair_256", "bl_pair_128", "bl_pair_96", "bl_pair_64"])
+    ap.add_argument("--workload", default="bl_pair_256", choices=["bl_pair_256", "bl_pair_128", "bl_pair_96", "bl_pair_64", "amr_boxes_96", "coupling_sweep_32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-peak", action="store_true", help="skip the FP64 microbenchmark")
@@ -59,6 +59,116 @@ def workload(name):
     import grf_inputs as gi
     n = int(name.rsplit("_", 1)[1])
     return gi.config_bl_pair_256(n)
+
+
+def batched_workload(name):
+    """(boxes, params list, params index per box, dt per box, initial states) of a batched
+    workload: 96 uneven AMR-like boxes with frozen ghosts (single-puncture data, dt = dx/4 per
+    box), or the 32-instance coupling sweep of periodic 64^3 boxes (dt = dx/4)."""
+    import grf_inputs as gi
+    if name == "amr_boxes_96":
+        boxes = gi.amr_like_boxes()
+        params = [gi.Params(beta_kind=gi.BETA_LINEAR, lam=0.01, g2=0.01)]
+        pidx = [0] * len(boxes)
+    else:
+        boxes, params = gi.coupling_sweep_boxes()
+        pidx = list(range(len(boxes)))
+    dts = [0.25 * b.dx for b in boxes]
+    return boxes, params, pidx, dts
+
+
+def run_batched(args, rank, world, local_rank):
+    import torch
+    import grf_inputs as gi
+    import paper_2309_06225_gb300 as grf
+    from paper_2309_06225_gb300 import autotune
+    from paper_2309_06225_gb300 import flops as grf_flops
+
+    torch.cuda.set_device(local_rank)
+    boxes, params, pidx, dts = batched_workload(args.workload)
+    gb = [grf.box_like(b) for b in boxes]
+    gp = grf.params_array([grf.params_like(p) for p in params])
+    init = [grf.to_device(gi.single_puncture(b), b2) for b, b2 in zip(boxes, gb)]
+    states = [t.clone() for t in init]
+    npts = sum(b.npoints for b in boxes)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        cfg, timings = autotune.tune(gb, states, pidx, dts, gp, stream=stream)
+        items = grf.batch_items(gb, states, pidx, dts)
+        ws = grf.alloc_workspace(grf.grf_batched_workspace_bytes(items, cfg))
+        grf.grf_batched_rk4(items, gp, args.warmup, cfg, ws=ws, stream=stream)
+        torch.cuda.synchronize()
+        clocks = ClockSampler(gpu_selector(local_rank))
+        clocks.start()
+        time.sleep(0.3)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        grf.grf_batched_rk4(items, gp, args.steps, cfg, ws=ws, stream=stream, sync_status=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        ms = e0.elapsed_time(e1)
+        status = grf.grf_check_status()
+        # the plain single-box path on the same boxes: one grf_rk4_step call per box and step
+        wss = {}
+        for b2 in gb:
+            key = (b2.nx, b2.ny, b2.nz, b2.pitch)
+            if key not in wss:
+                wss[key] = grf.alloc_workspace(grf.grf_workspace_bytes(b2, grf.GRF_OP_RK4))
+        single = [t.clone() for t in init]
+        for b2, t, pi, dt in zip(gb, single, pidx, dts):
+            grf.grf_rk4_step(b2, gp[pi], t, dt, 1, ws=wss[(b2.nx, b2.ny, b2.nz, b2.pitch)], stream=stream)
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(args.steps):
+            for b2, t, pi, dt in zip(gb, single, pidx, dts):
+                grf.grf_rk4_step(b2, gp[pi], t, dt, 1, ws=wss[(b2.nx, b2.ny, b2.nz, b2.pitch)], stream=stream)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        ms_single = s0.elapsed_time(s1)
+        # e2e: every step, all box states from pinned host to device and back
+        host = [torch.empty(t.shape, dtype=torch.float64, pin_memory=True) for t in init]
+        for h, t in zip(host, init):
+            h.copy_(t)
+        hout = [torch.empty(t.shape, dtype=torch.float64, pin_memory=True) for t in init]
+        nbytes = sum(t.numel() * 8 for t in init)
+        torch.cuda.synchronize()
+        x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        x0.record(stream)
+        for _ in range(args.steps):
+            for h, t in zip(host, states):
+                t.copy_(h, non_blocking=True)
+            grf.grf_batched_rk4(items, gp, 1, cfg, ws=ws, stream=stream, sync_status=False)
+            for h, t in zip(hout, states):
+                h.copy_(t, non_blocking=True)
+        x1.record(stream)
+        torch.cuda.synchronize()
+        ems = x0.elapsed_time(x1)
+    value = npts * args.steps / (ms * 1e-3)
+    flop_ps = sum(grf_flops.flops_per_point_stage(gp[pi]) * b.npoints for b, pi in zip(boxes, pidx)) / npts
+    achieved = flop_ps * npts * 4 * args.steps / (ms * 1e-3) / 1e12
+    variant = {grf.GRF_BATCH_GRAPH: "graph", grf.GRF_BATCH_PERSISTENT: "persistent"}.get(cfg.variant, "stream")
+    kernel = "batch_persistent_kernel" if cfg.variant == grf.GRF_BATCH_PERSISTENT else "batch_stage_kernel"
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "boxes": len(boxes), "points": npts,
+                      "shapes": autotune.signature(gb), "variant": variant,
+                      "tile": [cfg.tile_x, cfg.tile_y, cfg.tile_z], "autotune_ms_per_step": timings,
+                      "l2": "inputs larger than L2 (no flush needed)"},
+           "gpu_launches": (1 if cfg.variant == grf.GRF_BATCH_PERSISTENT else 4 * args.steps),
+           "roofline": {"bound": "alu", "unit": "TFLOP/s", "kernel": kernel, "achieved": achieved,
+                        "peak": FP64_PEAK_TFLOPS, "frac": achieved / FP64_PEAK_TFLOPS, "flop_per_point_stage": flop_ps,
+                        "traffic": None},
+           "single_box_path": {"value": npts * args.steps / (ms_single * 1e-3), "ms_per_step": ms_single / args.steps,
+                               "launches_per_step": len(boxes) * 5,
+                               "batched_speedup": ms_single / ms},
+           "clocks": clk, "status": {"solve": status},
+           "e2e": {"value": npts * args.steps / (ems * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                   "d2h_bytes_per_step": nbytes, "ms_per_step": ems / args.steps},
+           "cpu_baseline": None}
+    print(json.dumps(out), flush=True)
 
 
 # ------------------------------------------------------------------------------ clocks
@@ -318,6 +428,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.workload in ("amr_boxes_96", "coupling_sweep_32"):
+        run_batched(args, rank, world, local_rank)
         return
     run_ours(args, rank, world, local_rank)
 

@@ -241,3 +241,34 @@ def coupling_sweep(n_instances=32, seed=0):
         g2 = rng.uniform(0.0, 0.05)
         out.append((lam, g2))
     return out
+
+
+def amr_like_boxes(n_boxes=96, seed=0, edges=(16, 24, 32, 48, 64), levels=5, centre_range=4.0):
+    """Seeded set of uneven AMR-like boxes: edge n drawn from `edges`, a cube or a 2:1 slab
+    (n, n, n/2) with the short axis drawn, refinement level l in 0..levels-1 (dx = 2^-l), centre
+    uniform in [-centre_range, centre_range]^3. Lower corners sit on multiples of dx, points at
+    (k + 1/2) dx, ghosts frozen (filled from the analytic data). Draw order per box: edge,
+    shape, short axis, level, centre (x, y, z)."""
+    rng = SplitMix64(seed)
+    boxes = []
+    for _ in range(n_boxes):
+        n = rng.choice(list(edges))
+        slab = rng.next_u64() % 2 == 1
+        axis = rng.next_u64() % 3
+        level = rng.next_u64() % levels
+        c = [rng.uniform(-centre_range, centre_range) for _ in range(3)]
+        dims = [n, n, n]
+        if slab:
+            dims[axis] = n // 2
+        dx = 2.0 ** (-level)
+        x0 = [math.floor((c[a] - 0.5 * dims[a] * dx) / dx) * dx + 0.5 * dx for a in range(3)]
+        boxes.append(Box(dims[0], dims[1], dims[2], dx, x0[0], x0[1], x0[2], bc=BC_FROZEN))
+    return boxes
+
+
+def coupling_sweep_boxes(n_instances=32, n=64, lo=-8.0, hi=8.0, seed=0):
+    """n_instances periodic n^3 boxes on [lo, hi]^3 with the single-puncture data and seeded
+    couplings (lambda ~ U[0, 0.1], g2 ~ U[0, 0.05]). Returns (boxes, params list)."""
+    boxes = [cube_box(n, lo, hi) for _ in range(n_instances)]
+    params = [Params(beta_kind=BETA_LINEAR, lam=lam, g2=g2) for lam, g2 in coupling_sweep(n_instances, seed)]
+    return boxes, params

@@ -124,6 +124,45 @@ int grf_check_status(grf_stream_t stream);
 int grf_check_finite(const grf_box* box, const double* state, void* ws, size_t ws_bytes,
                      grf_stream_t stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Batched evolution of many independent boxes (uneven AMR-like box sets, coupling sweeps).
+ * The paper evolves boxes of a block-structured AMR hierarchy ("Adaptive Mesh Refinement",
+ * section "Key features"); this call advances a set of independent boxes, each with its own
+ * geometry, boundary type, couplings and time step, by nsteps RK4 steps, with all boxes'
+ * points in one flattened work list of (box, tile) items.
+ * ------------------------------------------------------------------------------------- */
+enum { GRF_BATCH_GRAPH = 1, GRF_BATCH_PERSISTENT = 2, GRF_BATCH_STREAM = 3 };
+
+typedef struct {
+    grf_box box;          /* this box's geometry and boundary type */
+    double* state;        /* device: this box's state (layout above), advanced in place */
+    int params_index;     /* index of this box's entry in the params array */
+    double dt;            /* this box's time step */
+} grf_batch_item;
+
+typedef struct {
+    int variant;          /* GRF_BATCH_GRAPH: the 4 x nsteps stage launches as one CUDA graph (kernel-node
+                             chain, cached and replayed when the same batch is stepped again);
+                             GRF_BATCH_PERSISTENT: one cooperative launch of co-resident blocks looping
+                             over the work list, grid barriers between stages;
+                             GRF_BATCH_STREAM: the stage launches issued directly */
+    int tile_x, tile_y, tile_z;        /* threads per block / points per tile; product in [32, 128] */
+    int blocks_per_sm;                 /* persistent: resident blocks per SM (0: as many as fit) */
+    long long barrier_timeout_cycles;  /* persistent: spin limit of one grid barrier (0: 2e10 cycles);
+                                          on expiry the call reports GRF_ETIMEOUT, no block hangs */
+} grf_batch_config;
+
+/* Scratch bytes for grf_batched_rk4: descriptors, tile list and three state-sized buffers per
+ * box. 0 if an item or the configuration is invalid. */
+size_t grf_batched_workspace_bytes(const grf_batch_item* items, int nitems, const grf_batch_config* cfg);
+
+/* Advance every box by nsteps RK4 steps (same scheme as grf_rk4_step, per box). items, params
+ * and cfg are host arrays read during the call. status_host (host, may be NULL): when given,
+ * the call synchronises `stream` and returns GRF_ETIMEOUT / GRF_ESINGULAR if a barrier timed
+ * out or a coupled system was singular. */
+int grf_batched_rk4(const grf_batch_item* items, int nitems, const grf_params* params, int nparams, int nsteps,
+                    const grf_batch_config* cfg, void* ws, size_t ws_bytes, int* status_host, grf_stream_t stream);
+
 const char* grf_error_string(int code);
 const char* grf_last_cuda_error(void);
 

@@ -40,6 +40,18 @@ class grf_params(C.Structure):
                 ("beta_kind", C.c_int), ("enforce_algebraic", C.c_int)]
 
 
+GRF_BATCH_GRAPH, GRF_BATCH_PERSISTENT, GRF_BATCH_STREAM = 1, 2, 3
+
+
+class grf_batch_item(C.Structure):
+    _fields_ = [("box", grf_box), ("state", C.c_void_p), ("params_index", C.c_int), ("dt", C.c_double)]
+
+
+class grf_batch_config(C.Structure):
+    _fields_ = [("variant", C.c_int), ("tile_x", C.c_int), ("tile_y", C.c_int), ("tile_z", C.c_int),
+                ("blocks_per_sm", C.c_int), ("barrier_timeout_cycles", C.c_longlong)]
+
+
 class GrfError(RuntimeError):
     def __init__(self, code, what):
         self.code = code
@@ -70,6 +82,11 @@ def lib():
         L.grf_workspace_bytes.restype = C.c_size_t
         L.grf_check_status.argtypes = [_VP]
         L.grf_check_finite.argtypes = [B, _VP, _VP, C.c_size_t, _VP]
+        BI, BC = C.POINTER(grf_batch_item), C.POINTER(grf_batch_config)
+        L.grf_batched_workspace_bytes.argtypes = [BI, C.c_int, BC]
+        L.grf_batched_workspace_bytes.restype = C.c_size_t
+        L.grf_batched_rk4.argtypes = [BI, C.c_int, P, C.c_int, C.c_int, BC, _VP, C.c_size_t, C.POINTER(C.c_int), _VP]
+        L.grf_batched_rk4.restype = C.c_int
         L.grf_error_string.argtypes = [C.c_int]
         L.grf_error_string.restype = C.c_char_p
         L.grf_last_cuda_error.restype = C.c_char_p
@@ -208,3 +225,40 @@ def grf_check_finite(box: grf_box, state, ws=None, stream=None):
 
 def grf_error_string(code: int) -> str:
     return lib().grf_error_string(int(code)).decode()
+
+
+# ------------------------------------------------------------------------------ batched boxes
+def batch_config(variant=GRF_BATCH_GRAPH, tile=(32, 4, 1), blocks_per_sm=0, barrier_timeout_cycles=0):
+    return grf_batch_config(int(variant), int(tile[0]), int(tile[1]), int(tile[2]), int(blocks_per_sm),
+                            int(barrier_timeout_cycles))
+
+
+def batch_items(boxes, states, params_index, dts):
+    """ctypes array of grf_batch_item from parallel lists (boxes: grf_box, states: device tensors)."""
+    arr = (grf_batch_item * len(boxes))()
+    for i, (b, t, pi, dt) in enumerate(zip(boxes, states, params_index, dts)):
+        assert t.is_cuda and t.is_contiguous()
+        arr[i] = grf_batch_item(b, C.c_void_p(t.data_ptr()), int(pi), float(dt))
+    return arr
+
+
+def params_array(params):
+    arr = (grf_params * len(params))()
+    for i, p in enumerate(params):
+        arr[i] = p
+    return arr
+
+
+def grf_batched_workspace_bytes(items, cfg) -> int:
+    return int(lib().grf_batched_workspace_bytes(items, len(items), C.byref(cfg)))
+
+
+def grf_batched_rk4(items, params, nsteps, cfg, ws=None, stream=None, sync_status=True):
+    """Advances every box of `items` (batch_items) by nsteps RK4 steps; params: grf_params array."""
+    if ws is None:
+        ws = alloc_workspace(grf_batched_workspace_bytes(items, cfg))
+    st = C.c_int(0)
+    code = lib().grf_batched_rk4(items, len(items), params, len(params), int(nsteps), C.byref(cfg), _dev(ws),
+                                 ws.numel(), C.byref(st) if sync_status else None, _stream(stream))
+    return _check(code, "grf_batched_rk4")
+

@@ -9,6 +9,8 @@
 
 namespace grf {
 
+char g_cuda_msg[256] = "";
+
 __global__ void ko_kernel(Geom g, const double* __restrict__ s, double* __restrict__ rhs, double ko) {
     int i, j, k;
     if (!interior_thread(g, i, j, k)) return;
@@ -60,19 +62,20 @@ __global__ void finite_kernel(Geom g, const double* __restrict__ s, int* flag) {
         if (!isfinite(s[f * g.fstride + p])) { atomicOr(flag, 1); return; }
 }
 
+
+int record_cuda_error(cudaError_t e) {
+    std::snprintf(g_cuda_msg, sizeof(g_cuda_msg), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+    return GRF_ECUDA;
+}
 }  // namespace grf
 
 using namespace grf;
 
 namespace {
 
-char g_cuda_msg[256] = "";
 __device__ int g_status;
 
-int cuda_fail(cudaError_t e) {
-    std::snprintf(g_cuda_msg, sizeof(g_cuda_msg), "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
-    return GRF_ECUDA;
-}
+int cuda_fail(cudaError_t e) { return grf::record_cuda_error(e); }
 
 int check_launch() {
     cudaError_t e = cudaGetLastError();

@@ -1,0 +1,434 @@
+// Batched RK4 over many boxes (uneven AMR-like boxes, coupling sweeps): a flattened work list
+// of (box, tile) items, each box with its own geometry, couplings and time step.
+//
+// Variants (grf_batch_config.variant):
+//   GRF_BATCH_GRAPH       the per-stage launches over the whole work list as one CUDA graph
+//                         (a chain of kernel nodes built with the graph API, cached and replayed);
+//   GRF_BATCH_PERSISTENT  one cooperative launch of co-resident blocks that loop over the work
+//                         list for every stage and step, separated by grid barriers whose spin
+//                         is bounded (a barrier that times out latches GRF_ETIMEOUT and every
+//                         block returns);
+//   GRF_BATCH_STREAM      the per-stage launches without a graph.
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "grf.h"
+#include "grf_kernels.cuh"
+#include "grf_launch.h"
+
+namespace grf {
+
+struct BoxDesc {
+    Geom g;
+    Coeffs c;
+    double* un;
+    double* A;
+    double* B;
+    double* acc;
+    double dt, ko, min_chi, min_lapse;
+    int enforce;
+    int pad_;
+};
+
+struct TileDesc {
+    int box, i0, j0, k0;
+};
+
+template <int STAGE>
+__device__ __forceinline__ void batch_tile(const BoxDesc* __restrict__ boxes, const TileDesc& td, int* status) {
+    const BoxDesc& d = boxes[td.box];
+    const int i = td.i0 + threadIdx.x, j = td.j0 + threadIdx.y, k = td.k0 + threadIdx.z;
+    if (i >= d.g.nx || j >= d.g.ny || k >= d.g.nz) return;
+    StageArgs a;
+    a.un = d.un;
+    a.acc = d.acc;
+    a.dt = d.dt;
+    a.ko = d.ko;
+    a.min_chi = d.min_chi;
+    a.min_lapse = d.min_lapse;
+    a.enforce = d.enforce;
+    a.status = status;
+    a.src = (STAGE == 0) ? d.un : (STAGE == 1 ? d.A : (STAGE == 2 ? d.B : d.A));
+    a.dst = (STAGE == 0) ? d.A : (STAGE == 1 ? d.B : (STAGE == 2 ? d.A : d.un));
+    stage_point<STAGE>(d.g, d.c, a, i, j, k);
+}
+
+template <int STAGE>
+__global__ void __launch_bounds__(128) batch_stage_kernel(const BoxDesc* __restrict__ boxes,
+                                                          const TileDesc* __restrict__ tiles, int ntiles, int* status) {
+    const int t = blockIdx.x;
+    if (t >= ntiles) return;
+    const TileDesc td = tiles[t];
+    batch_tile<STAGE>(boxes, td, status);
+}
+
+// Grid-wide barrier for a cooperative launch. Thread 0 of each block arrives on a counter;
+// the last arrival resets it and bumps the generation. Waiting is bounded by `timeout`
+// clock cycles: on expiry the status word gets bit 2 and false is returned (the caller
+// returns from the kernel), so a barrier can never hang the device.
+__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, long long timeout, int* status) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) {
+        int ok = 1;
+        volatile unsigned* gen = bar + 1;
+        const unsigned g0 = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(bar, 1u) + 1u;
+        if (arrived == nblocks) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*gen == g0) {
+                if (clock64() - t0 > timeout) {
+                    atomicOr(status, 2);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(256);
+            }
+        }
+        __threadfence();
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+__global__ void __launch_bounds__(128) batch_persistent_kernel(const BoxDesc* __restrict__ boxes,
+                                                               const TileDesc* __restrict__ tiles, int ntiles,
+                                                               int nsteps, unsigned* bar, int* status,
+                                                               long long timeout) {
+    for (int n = 0; n < nsteps; ++n) {
+#pragma unroll 1
+        for (int s = 0; s < 4; ++s) {
+            for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+                const TileDesc td = tiles[t];
+                switch (s) {
+                    case 0: batch_tile<0>(boxes, td, status); break;
+                    case 1: batch_tile<1>(boxes, td, status); break;
+                    case 2: batch_tile<2>(boxes, td, status); break;
+                    default: batch_tile<3>(boxes, td, status); break;
+                }
+            }
+            if (!grid_barrier(bar, gridDim.x, timeout, status)) return;
+        }
+    }
+}
+
+__global__ void batch_ghost_fill_kernel(const BoxDesc* __restrict__ boxes, int box) {
+    const BoxDesc& d = boxes[box];
+    const Geom& g = d.g;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int f = blockIdx.z;
+    if (i >= g.NX || j >= g.NY) return;
+    auto wrap = [](int a, int n) { int x = (a - NG) % n; if (x < 0) x += n; return x + NG; };
+    const int wi = wrap(i, g.nx), wj = wrap(j, g.ny);
+    const bool ghost_ij = (wi != i) || (wj != j);
+    double* u = d.un + f * g.fstride;
+    for (int k = 0; k < g.NZ; ++k) {
+        const int wk = wrap(k, g.nz);
+        if (!ghost_ij && wk == k) continue;
+        u[gidx(g, i, j, k)] = u[gidx(g, wi, wj, wk)];
+    }
+}
+
+}  // namespace grf
+
+using namespace grf;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+bool item_ok(const grf_batch_item& it) {
+    const grf_box* b = &it.box;
+    if (b->ng != 3 || b->nx < 1 || b->ny < 1 || b->nz < 1 || !(b->dx > 0.0)) return false;
+    if (b->pitch < (long long)b->nx + 6) return false;
+    if (b->bc != GRF_BC_PERIODIC && b->bc != GRF_BC_FROZEN) return false;
+    if (b->bc == GRF_BC_PERIODIC && (b->nx < 3 || b->ny < 3 || b->nz < 3)) return false;
+    return it.state != nullptr;
+}
+
+bool cfg_ok(const grf_batch_config* c) {
+    if (!c) return false;
+    if (c->tile_x < 1 || c->tile_y < 1 || c->tile_z < 1) return false;
+    const long long n = (long long)c->tile_x * c->tile_y * c->tile_z;
+    if (n > 128 || n < 32) return false;
+    return c->variant >= GRF_BATCH_GRAPH && c->variant <= GRF_BATCH_STREAM;
+}
+
+Geom geom_of(const grf_box* b) {
+    Geom g;
+    g.nx = b->nx; g.ny = b->ny; g.nz = b->nz;
+    g.NX = b->nx + 6; g.NY = b->ny + 6; g.NZ = b->nz + 6;
+    g.pitch = b->pitch;
+    g.plane = b->pitch * g.NY;
+    g.fstride = g.plane * g.NZ;
+    g.dx = b->dx;
+    g.periodic = (b->bc == GRF_BC_PERIODIC);
+    return g;
+}
+
+size_t state_bytes_of(const Geom& g) { return sizeof(double) * (size_t)NFIELDS * (size_t)g.fstride; }
+
+long long tiles_of(const grf_box* b, const grf_batch_config* c) {
+    return (long long)((b->nx + c->tile_x - 1) / c->tile_x) * ((b->ny + c->tile_y - 1) / c->tile_y) *
+           ((b->nz + c->tile_z - 1) / c->tile_z);
+}
+
+struct Layout {
+    size_t ctrl, boxes, tiles, bufs, total;
+    long long ntiles;
+};
+
+Layout layout(const grf_batch_item* items, int n, const grf_batch_config* c) {
+    Layout L;
+    L.ntiles = 0;
+    size_t bufs = 0;
+    for (int i = 0; i < n; ++i) {
+        L.ntiles += tiles_of(&items[i].box, c);
+        bufs += 3 * align_up(state_bytes_of(geom_of(&items[i].box)));
+    }
+    L.ctrl = 0;
+    L.boxes = kAlign;
+    L.tiles = L.boxes + align_up(sizeof(BoxDesc) * (size_t)n);
+    L.bufs = L.tiles + align_up(sizeof(TileDesc) * (size_t)L.ntiles);
+    L.total = L.bufs + bufs;
+    return L;
+}
+
+// one cached executable graph (re-used when the same batch is stepped again)
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t stream = nullptr;
+    const void* ws = nullptr;
+    int nsteps = -1;
+    long long ntiles = -1;
+    int tx = 0, ty = 0, tz = 0;
+    std::vector<char> key;
+};
+GraphCache g_graph;
+
+int cuda_err(cudaError_t e) { return grf::record_cuda_error(e); }
+
+bool debug_on() {
+    static const bool on = std::getenv("GRF_DEBUG_BATCH") != nullptr;
+    return on;
+}
+#define DBG(...)                                              \
+    do {                                                      \
+        if (debug_on()) {                                     \
+            std::fprintf(stderr, "[grf_batched_rk4] " __VA_ARGS__); \
+            std::fprintf(stderr, "\n");                       \
+            std::fflush(stderr);                              \
+        }                                                     \
+    } while (0)
+
+// The 4 x nsteps stage launches as an explicitly built graph: a chain of kernel nodes.
+cudaError_t build_stage_graph(int nsteps, long long ntiles, dim3 block, const BoxDesc* boxes, const TileDesc* tiles,
+                              int* status, cudaGraphExec_t* exec) {
+    const void* funcs[4] = {(const void*)batch_stage_kernel<0>, (const void*)batch_stage_kernel<1>,
+                            (const void*)batch_stage_kernel<2>, (const void*)batch_stage_kernel<3>};
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaGraphCreate(&graph, 0);
+    if (e != cudaSuccess) return e;
+    int nt = (int)ntiles;
+    void* args[4] = {(void*)&boxes, (void*)&tiles, (void*)&nt, (void*)&status};
+    cudaGraphNode_t prev = nullptr;
+    for (int n = 0; n < nsteps && e == cudaSuccess; ++n)
+        for (int s = 0; s < 4 && e == cudaSuccess; ++s) {
+            cudaKernelNodeParams kp;
+            std::memset(&kp, 0, sizeof(kp));
+            kp.func = (void*)funcs[s];
+            kp.gridDim = dim3((unsigned)ntiles);
+            kp.blockDim = block;
+            kp.sharedMemBytes = 0;
+            kp.kernelParams = args;
+            kp.extra = nullptr;
+            cudaGraphNode_t node = nullptr;
+            e = cudaGraphAddKernelNode(&node, graph, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
+            prev = node;
+        }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    return e;
+}
+
+void launch_stages(int nsteps, long long ntiles, dim3 block, cudaStream_t st, const BoxDesc* boxes,
+                   const TileDesc* tiles, int* status) {
+    const dim3 grid((unsigned)ntiles);
+    for (int n = 0; n < nsteps; ++n) {
+        batch_stage_kernel<0><<<grid, block, 0, st>>>(boxes, tiles, (int)ntiles, status);
+        batch_stage_kernel<1><<<grid, block, 0, st>>>(boxes, tiles, (int)ntiles, status);
+        batch_stage_kernel<2><<<grid, block, 0, st>>>(boxes, tiles, (int)ntiles, status);
+        batch_stage_kernel<3><<<grid, block, 0, st>>>(boxes, tiles, (int)ntiles, status);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t grf_batched_workspace_bytes(const grf_batch_item* items, int nitems, const grf_batch_config* cfg) {
+    if (!items || nitems < 1 || !cfg_ok(cfg)) return 0;
+    for (int i = 0; i < nitems; ++i)
+        if (!item_ok(items[i])) return 0;
+    return layout(items, nitems, cfg).total;
+}
+
+int grf_batched_rk4(const grf_batch_item* items, int nitems, const grf_params* params, int nparams, int nsteps,
+                    const grf_batch_config* cfg, void* ws, size_t ws_bytes, int* status_host, grf_stream_t stream) {
+    if (!items || nitems < 1 || !params || nparams < 1 || nsteps < 0 || !cfg_ok(cfg)) return GRF_EINVAL;
+    for (int i = 0; i < nitems; ++i) {
+        if (!item_ok(items[i])) return GRF_EINVAL;
+        const int pi = items[i].params_index;
+        if (pi < 0 || pi >= nparams) return GRF_EINVAL;
+        const grf_params* p = &params[pi];
+        if (p->beta_kind != GRF_BETA_LINEAR && p->beta_kind != GRF_BETA_QUADRATIC) return GRF_EINVAL;
+        if (!(1.0 + p->a0 > 0.0) || !(1.0 + p->b0 > 0.0)) return GRF_EINVAL;
+    }
+    const Layout L = layout(items, nitems, cfg);
+    DBG("entry: %d boxes, %lld tiles, ws %zu of %zu bytes, variant %d, tile %dx%dx%d", nitems, L.ntiles, ws_bytes,
+        L.total, cfg->variant, cfg->tile_x, cfg->tile_y, cfg->tile_z);
+    if (L.ntiles > 0x7fffffffLL) return GRF_EINVAL;
+    if (!ws || ws_bytes < L.total || ((uintptr_t)ws & (kAlign - 1))) return GRF_EWORKSPACE;
+    if (nsteps == 0) return GRF_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    char* base = (char*)ws;
+    unsigned* bar = (unsigned*)(base + L.ctrl);
+    int* status = (int*)(base + L.ctrl + 64);
+    BoxDesc* dboxes = (BoxDesc*)(base + L.boxes);
+    TileDesc* dtiles = (TileDesc*)(base + L.tiles);
+
+    // descriptors (host side), then one upload
+    std::vector<BoxDesc> hb(nitems);
+    std::vector<TileDesc> ht;
+    ht.reserve((size_t)L.ntiles);
+    size_t off = L.bufs;
+    for (int b = 0; b < nitems; ++b) {
+        const grf_batch_item& it = items[b];
+        const grf_params* p = &params[it.params_index];
+        BoxDesc& d = hb[b];
+        std::memset(&d, 0, sizeof(d));
+        d.g = geom_of(&it.box);
+        d.c.kappa1 = p->kappa1; d.c.kappa2 = p->kappa2; d.c.kappa3 = p->kappa3;
+        d.c.shift_F = p->shift_F; d.c.eta = p->eta; d.c.lam = p->lambda; d.c.g2 = p->g2;
+        d.c.inv_1pa = 1.0 / (1.0 + p->a0); d.c.a_1pa = p->a0 / (1.0 + p->a0);
+        d.c.bK = 3.0 * p->b0 / (4.0 * (1.0 + p->b0)); d.c.bTh = 1.0 / (2.0 * (1.0 + p->b0));
+        d.c.beta_kind = p->beta_kind;
+        const size_t sb = align_up(state_bytes_of(d.g));
+        d.un = it.state;
+        d.A = (double*)(base + off);
+        d.B = (double*)(base + off + sb);
+        d.acc = (double*)(base + off + 2 * sb);
+        off += 3 * sb;
+        d.dt = it.dt;
+        d.ko = p->sigma_ko / (64.0 * it.box.dx);
+        d.min_chi = p->min_chi;
+        d.min_lapse = p->min_lapse;
+        d.enforce = p->enforce_algebraic;
+        for (int k = 0; k < it.box.nz; k += cfg->tile_z)
+            for (int j = 0; j < it.box.ny; j += cfg->tile_y)
+                for (int i = 0; i < it.box.nx; i += cfg->tile_x) ht.push_back(TileDesc{b, i, j, k});
+    }
+    cudaError_t e = cudaMemcpyAsync(dboxes, hb.data(), sizeof(BoxDesc) * nitems, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dtiles, ht.data(), sizeof(TileDesc) * ht.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base, 0, kAlign, st);
+    if (e != cudaSuccess) return cuda_err(e);
+    // ghosts: periodic boxes refill theirs; frozen boxes hand theirs to the stage buffers
+    for (int b = 0; b < nitems; ++b) {
+        const Geom& g = hb[b].g;
+        if (g.periodic) {
+            dim3 blk(32, 8, 1), grd((g.NX + 31) / 32, (g.NY + 7) / 8, NFIELDS);
+            batch_ghost_fill_kernel<<<grd, blk, 0, st>>>(dboxes, b);
+        } else {
+            const size_t sb = state_bytes_of(g);
+            e = cudaMemcpyAsync(hb[b].A, hb[b].un, sb, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(hb[b].B, hb[b].un, sb, cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess) return cuda_err(e);
+        }
+    }
+    e = cudaGetLastError();
+    DBG("descriptors uploaded, ghosts prepared (%s)", cudaGetErrorName(e));
+    if (e != cudaSuccess) return cuda_err(e);
+    // load the stage kernels before any graph work
+    for (const void* f : {(const void*)batch_stage_kernel<0>, (const void*)batch_stage_kernel<1>,
+                          (const void*)batch_stage_kernel<2>, (const void*)batch_stage_kernel<3>,
+                          (const void*)batch_persistent_kernel}) {
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, f);
+        if (e != cudaSuccess) return cuda_err(e);
+    }
+    DBG("kernels loaded");
+
+    const dim3 block(cfg->tile_x, cfg->tile_y, cfg->tile_z);
+    int variant = cfg->variant;
+
+    if (variant == GRF_BATCH_STREAM) {
+        launch_stages(nsteps, L.ntiles, block, st, dboxes, dtiles, status);
+        e = cudaGetLastError();
+        DBG("stream: launched (%s)", cudaGetErrorName(e));
+    } else if (variant == GRF_BATCH_GRAPH) {
+        // key: everything the graph's launches depend on
+        std::vector<char> key(sizeof(BoxDesc) * nitems);
+        std::memcpy(key.data(), hb.data(), key.size());
+        const bool hit = g_graph.exec && g_graph.stream == st && g_graph.ws == ws && g_graph.nsteps == nsteps &&
+                         g_graph.ntiles == L.ntiles && g_graph.tx == cfg->tile_x && g_graph.ty == cfg->tile_y &&
+                         g_graph.tz == cfg->tile_z && g_graph.key == key;
+        DBG("graph: cache %s", hit ? "hit" : "miss");
+        if (!hit) {
+            if (g_graph.exec) {  // an executable graph still in flight is freed when it completes
+                cudaGraphExecDestroy(g_graph.exec);
+                g_graph.exec = nullptr;
+            }
+            e = build_stage_graph(nsteps, L.ntiles, block, dboxes, dtiles, status, &g_graph.exec);
+            DBG("graph: built (%s)", cudaGetErrorName(e));
+            if (e != cudaSuccess) { g_graph.exec = nullptr; return cuda_err(e); }
+            g_graph.stream = st; g_graph.ws = ws; g_graph.nsteps = nsteps; g_graph.ntiles = L.ntiles;
+            g_graph.tx = cfg->tile_x; g_graph.ty = cfg->tile_y; g_graph.tz = cfg->tile_z; g_graph.key = key;
+        }
+        e = cudaGraphLaunch(g_graph.exec, st);
+        DBG("graph: launched (%s)", cudaGetErrorName(e));
+    } else {  // persistent cooperative launch
+        int dev = 0, nsm = 0, per_sm = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        const int nthreads = cfg->tile_x * cfg->tile_y * cfg->tile_z;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_persistent_kernel, nthreads, 0);
+        if (e != cudaSuccess) return cuda_err(e);
+        if (per_sm < 1) return GRF_EINVAL;
+        if (cfg->blocks_per_sm > 0 && cfg->blocks_per_sm < per_sm) per_sm = cfg->blocks_per_sm;
+        long long nb = (long long)per_sm * nsm;
+        if (nb > L.ntiles) nb = L.ntiles;
+        const long long timeout = cfg->barrier_timeout_cycles > 0 ? cfg->barrier_timeout_cycles : 20000000000LL;
+        int nt = (int)L.ntiles;
+        const BoxDesc* pb = dboxes;
+        const TileDesc* pt = dtiles;
+        void* args[] = {(void*)&pb, (void*)&pt, (void*)&nt, (void*)&nsteps, (void*)&bar, (void*)&status,
+                        (void*)&timeout};
+        DBG("persistent: %lld blocks (%d per SM x %d SMs)", nb, per_sm, nsm);
+        e = cudaLaunchCooperativeKernel((const void*)batch_persistent_kernel, dim3((unsigned)nb), block, args, 0, st);
+        DBG("persistent: launched (%s)", cudaGetErrorName(e));
+    }
+    if (e != cudaSuccess) return cuda_err(e);
+    if (status_host) {
+        DBG("waiting for status");
+        e = cudaMemcpyAsync(status_host, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_err(e);
+        if (*status_host & 2) return GRF_ETIMEOUT;
+        if (*status_host & 1) return GRF_ESINGULAR;
+    }
+    return GRF_OK;
+}
+
+}  // extern "C"

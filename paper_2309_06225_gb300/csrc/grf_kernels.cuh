@@ -142,12 +142,10 @@ struct StageArgs {
     int* status;
 };
 
-// One RK4 stage, fused: gather -> pointwise RHS -> + KO -> stage update -> enforcement ->
-// store (with periodic images). STAGE 0..3.
+// One RK4 stage at one interior point, fused: gather -> pointwise RHS -> + KO -> stage update
+// -> enforcement -> store (with periodic images). STAGE 0..3.
 template <int STAGE>
-__global__ void __launch_bounds__(128) rk4_stage_kernel(Geom g, Coeffs c, StageArgs a) {
-    int i, j, k;
-    if (!interior_thread(g, i, j, k)) return;
+__device__ __forceinline__ void stage_point(const Geom& g, const Coeffs& c, const StageArgs& a, int i, int j, int k) {
     const long long p = gidx(g, i + NG, j + NG, k + NG);
     PointIn in;
     gather(g, a.src, p, in);
@@ -171,6 +169,13 @@ __global__ void __launch_bounds__(128) rk4_stage_kernel(Geom g, Coeffs c, StageA
     if (a.enforce) enforce_point(out, a.min_chi, a.min_lapse);
 #pragma unroll 1
     for (int f = 0; f < NFIELDS; ++f) store_with_images(g, a.dst, f, i, j, k, out[f]);
+}
+
+template <int STAGE>
+__global__ void __launch_bounds__(128) rk4_stage_kernel(Geom g, Coeffs c, StageArgs a) {
+    int i, j, k;
+    if (!interior_thread(g, i, j, k)) return;
+    stage_point<STAGE>(g, c, a, i, j, k);
 }
 
 }  // namespace grf

@@ -14,4 +14,6 @@ void launch_rhs(dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coe
                 double ko, int* status);
 void launch_constraints(dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c, const double* s,
                         double* out4, double* part);
+// Records a CUDA error for grf_last_cuda_error() and returns GRF_ECUDA.
+int record_cuda_error(cudaError_t e);
 }  // namespace grf
