@@ -46,7 +46,8 @@ enum {
     GRF_ECUDA = -3,        /* a CUDA call failed; see grf_last_cuda_error() */
     GRF_ENONFINITE = -4,   /* non-finite value found by grf_check_finite() */
     GRF_ESINGULAR = -5,    /* some point's coupled 7x7 system had a vanishing pivot */
-    GRF_ETIMEOUT = -6      /* a bounded device-side wait gave up */
+    GRF_ETIMEOUT = -6,     /* a bounded device-side wait gave up */
+    GRF_ETOOLARGE = -7     /* box too large for the fixed scratch of grf_rk4_step_noalloc */
 };
 
 enum { GRF_BC_PERIODIC = 0, GRF_BC_FROZEN = 1 };
@@ -162,6 +163,27 @@ size_t grf_batched_workspace_bytes(const grf_batch_item* items, int nitems, cons
  * out or a coupled system was singular. */
 int grf_batched_rk4(const grf_batch_item* items, int nitems, const grf_params* params, int nparams, int nsteps,
                     const grf_batch_config* cfg, void* ws, size_t ws_bytes, int* status_host, grf_stream_t stream);
+
+/* ---------------------------------------------------------------------------------------
+ * No-allocation variant (the paper has no counterpart: this is a library convenience).
+ * Some callers cannot call cudaMalloc: code that runs inside an already-captured CUDA
+ * graph region, host frameworks that hand out device pointers but own all allocation, or
+ * embedded/real-time callers that forbid allocation after start-up. For them this entry point
+ * runs the same RK4 step as grf_rk4_step with its scratch (two stage states and the RK4
+ * accumulator) in a fixed file-scope device array of GRF_NOALLOC_SCRATCH_BYTES bytes that every
+ * GPU loading the library holds until the process exits. It calls no cudaMalloc, cudaFree or
+ * allocating library routine.
+ *   - Limit: 3 x state bytes <= GRF_NOALLOC_SCRATCH_BYTES (48 MiB: e.g. a 32^3 box, 12.5 MB per
+ *     state); larger boxes are rejected with GRF_ETOOLARGE before any work.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ *     with that device current) and caches it; make that first call before any stream capture.
+ *   - All calls share the array, which keeps the last call's contents; nothing in it needs to
+ *     start at zero (every value is written before it is read). Calls that overlap on the GPU
+ *     (other streams, other host threads) race on the array: serialise them.
+ * Arguments, layout and errors otherwise as grf_rk4_step. */
+#define GRF_NOALLOC_SCRATCH_BYTES (48u * 1024u * 1024u)
+int grf_rk4_step_noalloc(const grf_box* box, const grf_params* params, double* state, double dt, int nsteps,
+                         grf_stream_t stream);
 
 const char* grf_error_string(int code);
 const char* grf_last_cuda_error(void);

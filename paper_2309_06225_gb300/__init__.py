@@ -20,6 +20,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgrf.so")
 
 GRF_OK, GRF_EINVAL, GRF_EWORKSPACE, GRF_ECUDA, GRF_ENONFINITE, GRF_ESINGULAR, GRF_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+GRF_ETOOLARGE = -7
+GRF_NOALLOC_SCRATCH_BYTES = 48 * 1024 * 1024
 GRF_BC_PERIODIC, GRF_BC_FROZEN = 0, 1
 GRF_BETA_LINEAR, GRF_BETA_QUADRATIC = 0, 1
 GRF_OP_RHS, GRF_OP_RK4, GRF_OP_CONSTRAINTS = 0, 1, 2
@@ -87,6 +89,8 @@ def lib():
         L.grf_batched_workspace_bytes.restype = C.c_size_t
         L.grf_batched_rk4.argtypes = [BI, C.c_int, P, C.c_int, C.c_int, BC, _VP, C.c_size_t, C.POINTER(C.c_int), _VP]
         L.grf_batched_rk4.restype = C.c_int
+        L.grf_rk4_step_noalloc.argtypes = [B, P, _VP, C.c_double, C.c_int, _VP]
+        L.grf_rk4_step_noalloc.restype = C.c_int
         L.grf_error_string.argtypes = [C.c_int]
         L.grf_error_string.restype = C.c_char_p
         L.grf_last_cuda_error.restype = C.c_char_p
@@ -262,3 +266,10 @@ def grf_batched_rk4(items, params, nsteps, cfg, ws=None, stream=None, sync_statu
                                  ws.numel(), C.byref(st) if sync_status else None, _stream(stream))
     return _check(code, "grf_batched_rk4")
 
+
+def grf_rk4_step_noalloc(box: grf_box, params: grf_params, state, dt, nsteps, stream=None):
+    """grf_rk4_step without a workspace: for callers that cannot allocate device memory (the
+    scratch is a fixed 48 MiB device array inside the library; boxes whose three stage states
+    exceed it are rejected with GRF_ETOOLARGE). See include/grf.h."""
+    return _check(lib().grf_rk4_step_noalloc(C.byref(box), C.byref(params), _dev(state), float(dt), int(nsteps),
+                                             _stream(stream)), "grf_rk4_step_noalloc")

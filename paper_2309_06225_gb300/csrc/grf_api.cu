@@ -161,6 +161,7 @@ const char* grf_error_string(int code) {
         case GRF_ENONFINITE: return "non-finite value in the state";
         case GRF_ESINGULAR: return "singular coupled 7x7 system at some grid point";
         case GRF_ETIMEOUT: return "bounded device wait timed out";
+        case GRF_ETOOLARGE: return "box too large for the fixed scratch of grf_rk4_step_noalloc (3 states > GRF_NOALLOC_SCRATCH_BYTES)";
         default: return "unknown error code";
     }
 }
