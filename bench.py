@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="bl_pair_256", choices=["bl_pair_256", "bl_pair_128", "bl_pair_96", "bl_pair_64", "amr_boxes_96", "coupling_sweep_32"])
+    ap.add_argument("--workload", default="bl_pair_256", choices=["bl_pair_256", "bl_pair_128", "bl_pair_96", "bl_pair_64", "amr_boxes_96", "coupling_sweep_32", "sphere_signal_96"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-peak", action="store_true", help="skip the FP64 microbenchmark")
@@ -75,6 +75,64 @@ def batched_workload(name):
         pidx = list(range(len(boxes)))
     dts = [0.25 * b.dx for b in boxes]
     return boxes, params, pidx, dts
+
+
+def run_tangent(args, rank, world, local_rank):
+    """The differentiated evolution: 96^3 single-puncture box on [-9.6, 9.6]^3 (dx = 0.2,
+    periodic), sphere signal at r = 6 with its derivatives in (lambda, g2, A), against the plain
+    RK4 step on the same box."""
+    import numpy as np
+    import torch
+    import grf_inputs as gi
+    import paper_2309_06225_gb300 as grf
+
+    torch.cuda.set_device(local_rank)
+    box = gi.cube_box(96, -9.6, 9.6)
+    params = gi.Params(lam=0.01, g2=0.01)
+    amp = 1e-3
+    b = grf.box_like(box)
+    p = grf.params_like(params)
+    dt = 0.25 * box.dx
+    s0 = gi.single_puncture(box, amp=amp)
+    dphi = np.zeros(box.shape)
+    dphi[25] = gi.single_puncture(box, amp=1.0)[25]
+    state = grf.to_device(s0, b)
+    tang = grf.alloc_state(b, 81)
+    tang.view(3, -1)[2].copy_(grf.to_device(dphi, b).reshape(-1))
+    loss = torch.zeros(4, dtype=torch.float64, device="cuda")
+    ws = grf.alloc_workspace(grf.grf_tlm_workspace_bytes(b))
+    sph = grf.grf_sphere(6.0, 0.0, 0.0, 0.0)
+    seeds = [1.0, 0.0, 0.0, 1.0, 0.0, 0.0]
+    grf.grf_tlm_rk4(b, p, seeds, state, tang, dt, max(1, args.warmup), sph, loss, ws=ws)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    grf.grf_tlm_rk4(b, p, seeds, state, tang, dt, args.steps, sph, loss, ws=ws, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_t = e0.elapsed_time(e1)
+    prim = grf.to_device(s0, b)
+    pws = grf.alloc_workspace(grf.grf_workspace_bytes(b, grf.GRF_OP_RK4))
+    grf.grf_rk4_step(b, p, prim, dt, max(1, args.warmup), ws=pws)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    grf.grf_rk4_step(b, p, prim, dt, args.steps, ws=pws, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_f = e0.elapsed_time(e1)
+    npts = box.npoints
+    out = {"metric": METRIC, "value": npts * args.steps / (ms_t * 1e-3), "unit": UNIT, "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_t / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "sphere_signal_96", "grid": [96, 96, 96], "dx": box.dx, "dt": dt,
+                      "sphere_radius": 6.0, "directions": ["lambda", "g2", "A"],
+                      "method": "forward-mode tangent-linear evolution (value + 3 tangents per grid value)"},
+           "gpu_launches": 5 * args.steps,
+           "differentiated_vs_plain": {"tangent_ms_per_step": ms_t / args.steps, "plain_ms_per_step": ms_f / args.steps,
+                                       "ratio": ms_t / ms_f},
+           "signal": loss.cpu().numpy().tolist(), "roofline": None, "e2e": None, "cpu_baseline": None}
+    print(json.dumps(out), flush=True)
 
 
 def run_batched(args, rank, world, local_rank):
@@ -428,6 +486,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.workload == "sphere_signal_96":
+        run_tangent(args, rank, world, local_rank)
         return
     if args.workload in ("amr_boxes_96", "coupling_sweep_32"):
         run_batched(args, rank, world, local_rank)

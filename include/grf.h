@@ -165,6 +165,35 @@ int grf_batched_rk4(const grf_batch_item* items, int nitems, const grf_params* p
                     const grf_batch_config* cfg, void* ws, size_t ws_bytes, int* status_host, grf_stream_t stream);
 
 /* ---------------------------------------------------------------------------------------
+ * Differentiation of an extracted scalar signal (the paper extracts scalar waveforms on
+ * spheres, section "Key features": Diagnostics). The signal is
+ *   L = sum_{n=1..nsteps} dt * sum_{q=1..26} w_q phi(c + R x_q, t_n)
+ * (26-point degree-7 rule on the sphere of radius R about c, trilinear interpolation of phi on
+ * the interior points, evaluated after every RK4 step). grf_tlm_rk4 advances the state exactly
+ * like grf_rk4_step and, at the same time, three tangent states (forward-mode derivatives):
+ * every operation of the step is differentiated, so after the call loss[1 + k] is the exact
+ * derivative of loss[0] in direction k.
+ * ------------------------------------------------------------------------------------- */
+typedef struct {
+    double radius;        /* R > 0; the sphere must stay inside the interior points */
+    double cx, cy, cz;    /* centre c */
+} grf_sphere;
+
+/* Scratch bytes for grf_tlm_rk4: 12 state-sized buffers (stage states and accumulators of the
+ * value and the 3 tangents) plus 256 bytes. */
+size_t grf_tlm_workspace_bytes(const grf_box* box);
+
+/* state: device, advanced in place (as grf_rk4_step). tangents: device, 3 consecutive states in
+ * the same layout holding d state / d theta_k (the caller seeds them, e.g. d(initial state)/d
+ * amplitude), advanced in place. dparams: host, 6 doubles {d lambda/d theta_k, d g2/d theta_k}
+ * for k = 0, 1, 2. loss: device, 4 doubles {L, dL/dtheta_0..2}, ACCUMULATED (zero it first).
+ * Synchronises `stream`; GRF_EINVAL if the sphere leaves the interior, GRF_ESINGULAR if a
+ * coupled system was singular. */
+int grf_tlm_rk4(const grf_box* box, const grf_params* params, const double* dparams, double* state, double* tangents,
+                double dt, int nsteps, const grf_sphere* sphere, double* loss, void* ws, size_t ws_bytes,
+                grf_stream_t stream);
+
+/* ---------------------------------------------------------------------------------------
  * No-allocation variant (the paper has no counterpart: this is a library convenience).
  * Some callers cannot call cudaMalloc: code that runs inside an already-captured CUDA
  * graph region, host frameworks that hand out device pointers but own all allocation, or

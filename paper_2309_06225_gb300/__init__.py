@@ -54,6 +54,10 @@ class grf_batch_config(C.Structure):
                 ("blocks_per_sm", C.c_int), ("barrier_timeout_cycles", C.c_longlong)]
 
 
+class grf_sphere(C.Structure):
+    _fields_ = [("radius", C.c_double), ("cx", C.c_double), ("cy", C.c_double), ("cz", C.c_double)]
+
+
 class GrfError(RuntimeError):
     def __init__(self, code, what):
         self.code = code
@@ -89,6 +93,11 @@ def lib():
         L.grf_batched_workspace_bytes.restype = C.c_size_t
         L.grf_batched_rk4.argtypes = [BI, C.c_int, P, C.c_int, C.c_int, BC, _VP, C.c_size_t, C.POINTER(C.c_int), _VP]
         L.grf_batched_rk4.restype = C.c_int
+        L.grf_tlm_workspace_bytes.argtypes = [B]
+        L.grf_tlm_workspace_bytes.restype = C.c_size_t
+        L.grf_tlm_rk4.argtypes = [B, P, C.POINTER(C.c_double), _VP, _VP, C.c_double, C.c_int, C.POINTER(grf_sphere),
+                                  _VP, _VP, C.c_size_t, _VP]
+        L.grf_tlm_rk4.restype = C.c_int
         L.grf_rk4_step_noalloc.argtypes = [B, P, _VP, C.c_double, C.c_int, _VP]
         L.grf_rk4_step_noalloc.restype = C.c_int
         L.grf_error_string.argtypes = [C.c_int]
@@ -273,3 +282,21 @@ def grf_rk4_step_noalloc(box: grf_box, params: grf_params, state, dt, nsteps, st
     exceed it are rejected with GRF_ETOOLARGE). See include/grf.h."""
     return _check(lib().grf_rk4_step_noalloc(C.byref(box), C.byref(params), _dev(state), float(dt), int(nsteps),
                                              _stream(stream)), "grf_rk4_step_noalloc")
+
+
+# ------------------------------------------------------------------------------ tangent-linear signal
+def grf_tlm_workspace_bytes(box: grf_box) -> int:
+    return int(lib().grf_tlm_workspace_bytes(C.byref(box)))
+
+
+def grf_tlm_rk4(box: grf_box, params: grf_params, dparams, state, tangents, dt, nsteps, sphere: grf_sphere, loss,
+                ws=None, stream=None):
+    """Advances state and its 3 tangent states by nsteps RK4 steps and accumulates the sphere
+    signal and its 3 directional derivatives into loss (device, 4 doubles). dparams: 6 floats
+    {d lambda, d g2} per direction. See include/grf.h."""
+    if ws is None:
+        ws = alloc_workspace(grf_tlm_workspace_bytes(box))
+    dp = (C.c_double * 6)(*[float(x) for x in dparams])
+    return _check(lib().grf_tlm_rk4(C.byref(box), C.byref(params), dp, _dev(state), _dev(tangents), float(dt),
+                                    int(nsteps), C.byref(sphere), _dev(loss), _dev(ws), ws.numel(), _stream(stream)),
+                  "grf_tlm_rk4")

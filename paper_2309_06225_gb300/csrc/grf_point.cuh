@@ -55,12 +55,17 @@ __host__ __device__ constexpr int sidx(int i, int j) {
 enum { F_CHI = 0, F_H = 1, F_K = 7, F_A = 8, F_TH = 14, F_GAM = 15, F_LAPSE = 18, F_SHIFT = 19,
        F_B = 22, F_PHI = 25, F_PI = 26, NFIELDS = 27 };
 
-struct Coeffs {
-    double kappa1, kappa2, kappa3, shift_F, eta, lam, g2;
+// Per-launch coefficients. P is the type of the two couplings (double, or a dual number when
+// their tangents are propagated).
+template <typename P>
+struct CoeffsT {
+    double kappa1, kappa2, kappa3, shift_F, eta;
+    P lam, g2;
     double inv_1pa, a_1pa;        // 1/(1+a), a/(1+a)
     double bK, bTh;               // 3b/(4(1+b)), 1/(2(1+b))
     int beta_kind;
 };
+using Coeffs = CoeffsT<double>;
 
 template <typename T>
 struct PointInT {
@@ -179,8 +184,8 @@ GRF_HD void q_of(const T X[6], const T gd[6], const T gw[6], const T Phd[6], con
         }
 }
 
-template <typename T>
-GRF_HD void point_rhs(const Coeffs& c, const PointInT<T>& in, T rhs[NFIELDS], PointExtraT<T>* extra, bool& ok) {
+template <typename T, typename P = double>
+GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS], PointExtraT<T>* extra, bool& ok) {
     GRF_SECTION(0);
     const T* v = in.v;
     const T chi = v[F_CHI], K = v[F_K], Th = v[F_TH], al = v[F_LAPSE], phi = v[F_PHI], Pi = v[F_PI];
@@ -521,7 +526,7 @@ GRF_HD void point_rhs(const Coeffs& c, const PointInT<T>& in, T rhs[NFIELDS], Po
     for (int i = 0; i < 3; ++i) dphiu[i] = gu[sidx(i, 0)] * dphi[0] + gu[sidx(i, 1)] * dphi[1] + gu[sidx(i, 2)] * dphi[2];
     const T dphi2 = dphi[0] * dphiu[0] + dphi[1] * dphiu[1] + dphi[2] * dphiu[2];
     const T X = 0.5 * (Pi * Pi - dphi2);
-    const double g2 = c.g2;
+    const T g2 = c.g2;
     T Hij[6], Hn[3];
 #pragma unroll
     for (int m = 0; m < 6; ++m) Hij[m] = fma(Kp[m], Pi, DDp[m]);
