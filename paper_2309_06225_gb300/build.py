@@ -17,6 +17,10 @@ SOURCES = ["grf_api.cu", "grf_stage.cu", "grf_rhs.cu", "grf_batch.cu", "grf_noal
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INC, "-I" + CSRC]
+# Per-source ptxas flags. The dual-number (tangent) kernels are very large functions on which
+# ptxas -O2/-O3 settles for 32 registers and an 87 KB stack; -O1 keeps 255 registers and a
+# 36 KB stack.
+SOURCE_FLAGS = {"grf_tlm.cu": ["-Xptxas", "-O1"]}
 
 
 def _deps():
@@ -50,7 +54,7 @@ def build(force=False, verbose=False, ptxas_verbose=False):
 
     def compile_one(src):
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [NVCC] + ARCH + FLAGS + extra + ["-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [NVCC] + ARCH + FLAGS + SOURCE_FLAGS.get(src, []) + extra + ["-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
         res = subprocess.run(cmd, capture_output=True, text=True)
