@@ -94,6 +94,34 @@ int grf_rhs(const grf_box* box, const grf_params* params, double* state, double*
 int grf_rk4_step(const grf_box* box, const grf_params* params, double* state, double dt,
                  int nsteps, void* ws, size_t ws_bytes, grf_stream_t stream);
 
+/* grf_rk4_step from host memory to host memory, with the host<->device copies overlapped with
+ * the first and the last RK stage (the time stepping of section "Key features"; the overlap
+ * has no counterpart in the paper, whose states never leave the node's memory).
+ *   host_in:  host, the state in the layout above (27 * pitch * (ny+6) * (nz+6) doubles).
+ *             GRF_BC_PERIODIC: only interior values are read (ghosts are rebuilt by periodic
+ *             wrap, as grf_rk4_step does); GRF_BC_FROZEN: ghosts are read as given.
+ *   host_out: host, same size; receives the state after nsteps steps, ghosts included.
+ *             May equal host_in.
+ *   state:    device buffer of the same size; overwritten, and on completion it holds the
+ *             same result as host_out.
+ *   ws:       as for grf_rk4_step.
+ * The interior is copied in slabs of z-planes (at most 16) on a copy stream owned by the
+ * library; each slab's first-stage launch waits only for the planes its stencils read. The last
+ * stage runs slab by slab and each finished slab is copied to host_out while the next is
+ * computed. Results are bit-identical to: copy host_in to state, grf_rk4_step, copy state to
+ * host_out. The stage kernels run on `stream`; the copies are ordered after the work already
+ * queued on `stream`, and later work on `stream` is ordered after the last copy, so host_out is
+ * complete once `stream` is synchronised. Host buffers should be page-locked (cudaHostAlloc,
+ * cudaHostRegister, pinned torch tensors); pageable buffers give the same results, but the
+ * driver then stages the copies and they no longer overlap the kernels.
+ * The first call on a device creates that device's copy stream and events (no memory is
+ * allocated); make it before any stream capture. Calls from several host threads are
+ * serialised while they queue work. Errors: GRF_EINVAL (box, params, null pointers, nsteps < 0),
+ * GRF_EWORKSPACE, GRF_ECUDA. */
+int grf_rk4_step_host(const grf_box* box, const grf_params* params, const double* host_in,
+                      double* host_out, double* state, double dt, int nsteps, void* ws,
+                      size_t ws_bytes, grf_stream_t stream);
+
 /* Hamiltonian and momentum constraints (section "Key features", Diagnostics):
  *   H = R + K^2 - K_ij K^ij - 16 pi rho,  M_i = D_j K^j_i - D_i K - 8 pi S_i,
  * with the full 4dST rho and S_i. out4: device, 4 fields in the state layout (H, M1, M2,

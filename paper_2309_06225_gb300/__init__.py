@@ -81,6 +81,7 @@ def lib():
         B, P = C.POINTER(grf_box), C.POINTER(grf_params)
         L.grf_rhs.argtypes = [B, P, _VP, _VP, _VP, C.c_size_t, _VP]
         L.grf_rk4_step.argtypes = [B, P, _VP, C.c_double, C.c_int, _VP, C.c_size_t, _VP]
+        L.grf_rk4_step_host.argtypes = [B, P, _VP, _VP, _VP, C.c_double, C.c_int, _VP, C.c_size_t, _VP]
         L.grf_constraints.argtypes = [B, P, _VP, _VP, C.POINTER(C.c_double), _VP, C.c_size_t, _VP]
         L.grf_ko_dissipation.argtypes = [B, C.c_double, _VP, _VP, _VP]
         L.grf_fill_ghosts.argtypes = [B, _VP, _VP]
@@ -103,7 +104,7 @@ def lib():
         L.grf_error_string.argtypes = [C.c_int]
         L.grf_error_string.restype = C.c_char_p
         L.grf_last_cuda_error.restype = C.c_char_p
-        for name in ("grf_rhs", "grf_rk4_step", "grf_constraints", "grf_ko_dissipation", "grf_fill_ghosts",
+        for name in ("grf_rhs", "grf_rk4_step", "grf_rk4_step_host", "grf_constraints", "grf_ko_dissipation", "grf_fill_ghosts",
                      "grf_check_status", "grf_check_finite"):
             getattr(L, name).restype = C.c_int
         _lib = L
@@ -182,6 +183,15 @@ def _dev(t):
     return _VP(t.data_ptr())
 
 
+def _host(t, n):
+    """Address of a contiguous float64 host array of n elements (numpy array or CPU tensor)."""
+    if isinstance(t, np.ndarray):
+        assert t.dtype == np.float64 and t.flags.c_contiguous and t.size == n
+        return _VP(t.ctypes.data)
+    assert (not t.is_cuda) and t.is_contiguous() and t.dtype == _torch().float64 and t.numel() == n
+    return _VP(t.data_ptr())
+
+
 def _check(code, what):
     if code != GRF_OK:
         raise GrfError(code, what)
@@ -208,6 +218,18 @@ def grf_rk4_step(box: grf_box, params: grf_params, state, dt, nsteps, ws=None, s
         ws = alloc_workspace(grf_workspace_bytes(box, GRF_OP_RK4), state.device)
     return _check(lib().grf_rk4_step(C.byref(box), C.byref(params), _dev(state), float(dt), int(nsteps), _dev(ws),
                                      ws.numel(), _stream(stream)), "grf_rk4_step")
+
+
+def grf_rk4_step_host(box: grf_box, params: grf_params, host_in, host_out, state, dt, nsteps, ws=None, stream=None):
+    """grf_rk4_step from a host array to a host array (layout state_shape(box)), the copies
+    overlapped with the first and last RK stage; `state` is the device buffer the step runs in.
+    host_in and host_out may be the same array; pinned CPU tensors let the copies overlap."""
+    n = int(np.prod(state_shape(box)))
+    if ws is None:
+        ws = alloc_workspace(grf_workspace_bytes(box, GRF_OP_RK4), state.device)
+    return _check(lib().grf_rk4_step_host(C.byref(box), C.byref(params), _host(host_in, n), _host(host_out, n),
+                                          _dev(state), float(dt), int(nsteps), _dev(ws), ws.numel(),
+                                          _stream(stream)), "grf_rk4_step_host")
 
 
 def grf_constraints(box: grf_box, params: grf_params, state, out4, norms=True, ws=None, stream=None):

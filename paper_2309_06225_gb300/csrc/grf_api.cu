@@ -1,7 +1,9 @@
 // C-ABI entry points of libgrf.so (declared in include/grf.h).
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <cstdint>
+#include <mutex>
 
 #include "grf.h"
 #include "grf_kernels.cuh"
@@ -32,6 +34,34 @@ __global__ void ghost_fill_kernel(Geom g, double* __restrict__ s) {
         const int wk = wrap(k, g.nz);
         if (!ghost_ij && wk == k) continue;
         u[gidx(g, i, j, k)] = u[gidx(g, wi, wj, wk)];
+    }
+}
+
+// Ghost preparation for one slab of z-planes [K0, K1) of the host-to-device pipeline of
+// grf_rk4_step_host. Periodic: in-plane (x, y) wrap of the ghost columns of `s`; the z-ghost
+// planes themselves were copied from the interior planes they are images of, so after this the
+// planes hold what a full periodic refill gives. Frozen: the ghost points of `s` are copied into
+// the stage buffers A and B, which carry the caller's ghosts through the stages.
+__global__ void slab_ghost_kernel(Geom g, double* __restrict__ s, double* __restrict__ A, double* __restrict__ B,
+                                  int K0, int K1) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const long long fo = (long long)blockIdx.z * g.fstride;
+    if (i >= g.NX || j >= g.NY) return;
+    if (g.periodic) {
+        auto wrap = [](int a, int n) { int x = (a - NG) % n; if (x < 0) x += n; return x + NG; };
+        const int wi = wrap(i, g.nx), wj = wrap(j, g.ny);
+        if (wi == i && wj == j) return;
+        for (int k = K0; k < K1; ++k) s[fo + gidx(g, i, j, k)] = s[fo + gidx(g, wi, wj, k)];
+    } else {
+        const bool ghost_ij = i < NG || i >= g.nx + NG || j < NG || j >= g.ny + NG;
+        for (int k = K0; k < K1; ++k) {
+            if (!ghost_ij && k >= NG && k < g.nz + NG) continue;
+            const long long q = fo + gidx(g, i, j, k);
+            const double v = s[q];
+            A[q] = v;
+            B[q] = v;
+        }
     }
 }
 
@@ -148,6 +178,95 @@ size_t constraint_partials(const Geom& g) {
     return (size_t)grd.x * grd.y * grd.z;
 }
 
+// ---- host-to-host stepping (grf_rk4_step_host): per-device copy stream and events
+constexpr int kMaxSlabs = 16;
+constexpr int kMaxDevices = 64;
+
+struct CopyPipe {
+    bool ready = false;
+    cudaStream_t copy = nullptr;
+    cudaEvent_t start = nullptr, done = nullptr;
+    cudaEvent_t h2d[kMaxSlabs] = {}, s4[kMaxSlabs] = {};
+};
+
+std::mutex g_pipe_mu;
+CopyPipe g_pipe[kMaxDevices];
+
+void destroy_pipe(CopyPipe& p) {
+    if (p.copy) cudaStreamDestroy(p.copy);
+    for (cudaEvent_t* e : {&p.start, &p.done})
+        if (*e) cudaEventDestroy(*e);
+    for (int s = 0; s < kMaxSlabs; ++s) {
+        if (p.h2d[s]) cudaEventDestroy(p.h2d[s]);
+        if (p.s4[s]) cudaEventDestroy(p.s4[s]);
+    }
+    p = CopyPipe();
+}
+
+// The current device's copy stream and events, created on first use (caller holds g_pipe_mu).
+int pipe_for_current_device(CopyPipe*& out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (dev < 0 || dev >= kMaxDevices) return GRF_EINVAL;
+    CopyPipe& p = g_pipe[dev];
+    if (!p.ready) {
+        e = cudaStreamCreateWithFlags(&p.copy, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.start, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.done, cudaEventDisableTiming);
+        for (int s = 0; s < kMaxSlabs && e == cudaSuccess; ++s) {
+            e = cudaEventCreateWithFlags(&p.h2d[s], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.s4[s], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) {
+            destroy_pipe(p);
+            return cuda_fail(e);
+        }
+        p.ready = true;
+    }
+    out = &p;
+    return GRF_OK;
+}
+
+// Host -> device copy of ghosted z-planes [K0, K1) of all fields. For periodic boxes the host
+// source of a z-ghost plane is the interior plane it is an image of (the host ghosts are not read).
+cudaError_t copy_planes_h2d(const Geom& g, double* dev, const double* host, int K0, int K1, cudaStream_t st) {
+    const size_t pb = (size_t)g.plane * sizeof(double);
+    int K = K0;
+    while (K < K1) {
+        int end, shift = 0;
+        if (K < NG) {
+            end = std::min(K1, NG);
+            shift = g.periodic ? g.nz : 0;
+        } else if (K < g.nz + NG) {
+            end = std::min(K1, g.nz + NG);
+        } else {
+            end = K1;
+            shift = g.periodic ? -g.nz : 0;
+        }
+        for (int f = 0; f < NFIELDS; ++f) {
+            const long long off = (long long)f * g.fstride;
+            cudaError_t e = cudaMemcpyAsync(dev + off + (long long)K * g.plane, host + off + (long long)(K + shift) * g.plane,
+                                            (size_t)(end - K) * pb, cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) return e;
+        }
+        K = end;
+    }
+    return cudaSuccess;
+}
+
+// Device -> host copy of ghosted z-planes [K0, K1) of all fields.
+cudaError_t copy_planes_d2h(const Geom& g, double* host, const double* dev, int K0, int K1, cudaStream_t st) {
+    if (K1 <= K0) return cudaSuccess;
+    const size_t pb = (size_t)g.plane * sizeof(double);
+    for (int f = 0; f < NFIELDS; ++f) {
+        const long long off = (long long)f * g.fstride + (long long)K0 * g.plane;
+        cudaError_t e = cudaMemcpyAsync(host + off, dev + off, (size_t)(K1 - K0) * pb, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 }  // namespace
 
 extern "C" {
@@ -230,6 +349,7 @@ int grf_rk4_step(const grf_box* box, const grf_params* params, double* state, do
     a.min_lapse = params->min_lapse;
     a.enforce = params->enforce_algebraic;
     a.status = status_ptr();
+    a.k0 = 0;
     a.un = state;
     a.acc = acc;
     const dim3 grd = interior_grid(g);
@@ -246,6 +366,107 @@ int grf_rk4_step(const grf_box* box, const grf_params* params, double* state, do
         if (r) return r;
     }
     return GRF_OK;
+}
+
+int grf_rk4_step_host(const grf_box* box, const grf_params* params, const double* host_in, double* host_out,
+                      double* state, double dt, int nsteps, void* ws, size_t ws_bytes, grf_stream_t stream) {
+    if (!box_ok(box) || !params_ok(params) || !host_in || !host_out || !state || nsteps < 0) return GRF_EINVAL;
+    Geom g = make_geom(box);
+    const size_t sb = state_bytes(g);
+    if (!ws || ws_bytes < 3 * sb || ((uintptr_t)ws & 255)) return GRF_EWORKSPACE;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lock(g_pipe_mu);
+    CopyPipe* pp = nullptr;
+    int r = pipe_for_current_device(pp);
+    if (r) return r;
+    const CopyPipe& P = *pp;
+    cudaError_t e = cudaEventRecord(P.start, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(P.copy, P.start, 0);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (nsteps == 0) {  // the state makes the round trip unchanged
+        e = cudaMemcpyAsync(state, host_in, sb, cudaMemcpyHostToDevice, P.copy);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, state, sb, cudaMemcpyDeviceToHost, P.copy);
+        if (e == cudaSuccess) e = cudaEventRecord(P.done, P.copy);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, P.done, 0);
+        return e == cudaSuccess ? GRF_OK : cuda_fail(e);
+    }
+    double* A = (double*)ws;
+    double* B = (double*)((char*)ws + sb);
+    double* acc = (double*)((char*)ws + 2 * sb);
+    // Slab s = interior planes [lo(s), hi(s)); its copy chunk = ghosted planes [clo(s), chi(s)), the
+    // first and last chunks also holding the z-ghost planes. Q >= 4 planes, so the planes a slab's
+    // stencils read (up to interior plane hi + 2) lie in chunks s-1, s and s+1.
+    const int Q = std::max(4, (g.nz + kMaxSlabs - 1) / kMaxSlabs);
+    const int S = (g.nz + Q - 1) / Q;
+    auto lo = [&](int s) { return s * Q; };
+    auto hi = [&](int s) { return std::min(g.nz, (s + 1) * Q); };
+    auto clo = [&](int s) { return s == 0 ? 0 : lo(s) + NG; };
+    auto chi = [&](int s) { return s == S - 1 ? g.NZ : hi(s) + NG; };
+    const Coeffs c = make_coeffs(params);
+    StageArgs a;
+    a.dt = dt;
+    a.ko = params->sigma_ko / (64.0 * box->dx);
+    a.min_chi = params->min_chi;
+    a.min_lapse = params->min_lapse;
+    a.enforce = params->enforce_algebraic;
+    a.status = status_ptr();
+    a.un = state;
+    a.acc = acc;
+    const dim3 full = interior_grid(g);
+    auto slab_grid = [&](int s) { return dim3(full.x, full.y, (unsigned)(hi(s) - lo(s))); };
+    const dim3 gblk(32, 8, 1), ggrd((g.NX + 31) / 32, (g.NY + 7) / 8, NFIELDS);
+
+    for (int s = 0; s < S && e == cudaSuccess; ++s) {
+        e = copy_planes_h2d(g, state, host_in, clo(s), chi(s), P.copy);
+        if (e == cudaSuccess) e = cudaEventRecord(P.h2d[s], P.copy);
+    }
+    if (e != cudaSuccess) return cuda_fail(e);
+    for (int n = 0; n < nsteps; ++n) {
+        a.src = state;
+        a.dst = A;
+        if (n == 0) {  // first stage, slab by slab as the planes arrive
+            for (int s = 0; s <= S; ++s) {
+                if (s < S) {
+                    e = cudaStreamWaitEvent(st, P.h2d[s], 0);
+                    if (e != cudaSuccess) return cuda_fail(e);
+                    slab_ghost_kernel<<<ggrd, gblk, 0, st>>>(g, state, A, B, clo(s), chi(s));
+                }
+                if (s >= 1) {
+                    a.k0 = lo(s - 1);
+                    launch_stage(0, slab_grid(s - 1), kBlock, st, g, c, a);
+                }
+            }
+        } else {
+            a.k0 = 0;
+            launch_stage(0, full, kBlock, st, g, c, a);
+        }
+        a.k0 = 0;
+        a.src = A; a.dst = B;
+        launch_stage(1, full, kBlock, st, g, c, a);
+        a.src = B; a.dst = A;
+        launch_stage(2, full, kBlock, st, g, c, a);
+        a.src = A; a.dst = state;
+        if (n < nsteps - 1) {
+            launch_stage(3, full, kBlock, st, g, c, a);
+        } else {  // last stage, slab by slab, each finished slab copied out behind the next
+            for (int s = 0; s < S; ++s) {
+                a.k0 = lo(s);
+                launch_stage(3, slab_grid(s), kBlock, st, g, c, a);
+                e = cudaEventRecord(P.s4[s], st);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(P.copy, P.s4[s], 0);
+                if (e == cudaSuccess) e = copy_planes_d2h(g, host_out, state, lo(s) + NG, hi(s) + NG, P.copy);
+                if (e != cudaSuccess) return cuda_fail(e);
+            }
+        }
+        r = check_launch();
+        if (r) return r;
+    }
+    // z-ghost planes (periodic images written by the first and last slabs; frozen: as given)
+    e = copy_planes_d2h(g, host_out, state, 0, NG, P.copy);
+    if (e == cudaSuccess) e = copy_planes_d2h(g, host_out, state, g.nz + NG, g.NZ, P.copy);
+    if (e == cudaSuccess) e = cudaEventRecord(P.done, P.copy);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, P.done, 0);
+    return e == cudaSuccess ? GRF_OK : cuda_fail(e);
 }
 
 int grf_constraints(const grf_box* box, const grf_params* params, double* state, double* out4, double* norms_host,

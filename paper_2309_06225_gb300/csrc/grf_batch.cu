@@ -51,6 +51,7 @@ __device__ __forceinline__ void batch_tile(const BoxDesc* __restrict__ boxes, co
     a.min_lapse = d.min_lapse;
     a.enforce = d.enforce;
     a.status = status;
+    a.k0 = 0;
     a.src = (STAGE == 0) ? d.un : (STAGE == 1 ? d.A : (STAGE == 2 ? d.B : d.A));
     a.dst = (STAGE == 0) ? d.A : (STAGE == 1 ? d.B : (STAGE == 2 ? d.A : d.un));
     stage_point<STAGE>(d.g, d.c, a, i, j, k);

@@ -140,6 +140,7 @@ struct StageArgs {
     double min_chi, min_lapse;
     int enforce;
     int* status;
+    int k0;              // first interior z-plane of the launch (grid.z covers planes k0, k0+1, ...)
 };
 
 // One RK4 stage at one interior point, fused: gather -> pointwise RHS -> + KO -> stage update
@@ -175,6 +176,8 @@ template <int STAGE>
 __global__ void __launch_bounds__(128) rk4_stage_kernel(Geom g, Coeffs c, StageArgs a) {
     int i, j, k;
     if (!interior_thread(g, i, j, k)) return;
+    k += a.k0;
+    if (k >= g.nz) return;
     stage_point<STAGE>(g, c, a, i, j, k);
 }
 

@@ -57,3 +57,13 @@ def test_workspace_and_validation_without_gpu(grf):
     good_state = C.c_void_p(0x1000)
     assert L.grf_rk4_step(C.byref(b), C.byref(p), good_state, 0.1, 1, None, 0, None) == grf.GRF_EWORKSPACE
     assert "workspace" in grf.grf_error_string(grf.GRF_EWORKSPACE)
+
+
+def test_host_step_validation_without_gpu(grf):
+    b = grf.make_box(16, 16, 16, 0.25)
+    p = grf.grf_params()
+    L = grf.lib()
+    fake = C.c_void_p(0x1000)
+    assert L.grf_rk4_step_host(C.byref(b), C.byref(p), None, fake, fake, 0.1, 1, fake, 1 << 30, None) == grf.GRF_EINVAL
+    assert L.grf_rk4_step_host(C.byref(b), C.byref(p), fake, fake, fake, 0.1, -1, fake, 1 << 30, None) == grf.GRF_EINVAL
+    assert L.grf_rk4_step_host(C.byref(b), C.byref(p), fake, fake, fake, 0.1, 1, None, 0, None) == grf.GRF_EWORKSPACE
