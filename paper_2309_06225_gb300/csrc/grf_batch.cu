@@ -58,7 +58,7 @@ __device__ __forceinline__ void batch_tile(const BoxDesc* __restrict__ boxes, co
 }
 
 template <int STAGE>
-__global__ void __launch_bounds__(128) batch_stage_kernel(const BoxDesc* __restrict__ boxes,
+__global__ void __launch_bounds__(128, 3) batch_stage_kernel(const BoxDesc* __restrict__ boxes,
                                                           const TileDesc* __restrict__ tiles, int ntiles, int* status) {
     const int t = blockIdx.x;
     if (t >= ntiles) return;
@@ -101,7 +101,7 @@ __device__ bool grid_barrier(unsigned* bar, unsigned nblocks, long long timeout,
     return ok_s != 0;
 }
 
-__global__ void __launch_bounds__(128) batch_persistent_kernel(const BoxDesc* __restrict__ boxes,
+__global__ void __launch_bounds__(128, 3) batch_persistent_kernel(const BoxDesc* __restrict__ boxes,
                                                                const TileDesc* __restrict__ tiles, int ntiles,
                                                                int nsteps, unsigned* bar, int* status,
                                                                long long timeout) {

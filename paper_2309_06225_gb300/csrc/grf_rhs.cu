@@ -10,13 +10,14 @@ __global__ void __launch_bounds__(128) rhs_kernel(Geom g, Coeffs c, const double
     if (!interior_thread(g, i, j, k)) return;
     const long long p = gidx(g, i + NG, j + NG, k + NG);
     PointIn in;
-    gather(g, s, p, in);
+    double kos[NFIELDS];
+    gather(g, s, p, in, kos);
     double r[NFIELDS];
     bool ok = true;
     point_rhs<double>(c, in, r, nullptr, ok);
     if (!ok) atomicOr(status, 1);
 #pragma unroll 1
-    for (int f = 0; f < NFIELDS; ++f) rhs[f * g.fstride + p] = r[f] + ko * ko6(s + f * g.fstride, p, g.pitch, g.plane);
+    for (int f = 0; f < NFIELDS; ++f) rhs[f * g.fstride + p] = r[f] + ko * kos[f];
 }
 
 // Constraints H, M_i at interior points (state layout, 4 fields) and per-block partial norms:

@@ -4,7 +4,8 @@ The pointwise part (RHS + 7x7 solve) is counted by running the kernel's own sour
 operation-counting scalar (libgrf_flops.so). The stencil gather, KO dissipation and stage
 update are fixed expressions in grf_kernels.cuh and are counted here from their code:
   fd1  (u-2 - u+2) + 8 (u+1 - u-1), * 1/(12dx)            : 2 add, 1 fma, 1 mul
-  fd2  16 (u+1 + u-1) - (u+2 + u-2) - 30 u0, * 1/(12dx^2)  : 2 add, 2 fma, 1 mul
+  fd2  16 (u+1 + u-1) - (u+2 + u-2) - 30 u0, * 1/(12dx^2)  : 2 fma, 1 mul (the two pair sums
+       are shared with the KO sum of the same field)
   fdm  4 rows of fd1-type sums, combined the same way      : 10 add, 5 fma, 1 mul
   ko6  3 x (3 pair sums + 3 accumulations) - 3, 3 fma; + ko*value into the RHS: 15 add, 4 fma
   stage update (per field): 1-2 fma (+1 add on the last stage)
@@ -45,7 +46,7 @@ def point_ops(params, v=None, d1=None, d2=None):
 def stencil_ops():
     """(add, mul, fma) of the gather + KO + stage update per point and stage (mean over stages)."""
     fd1 = np.array([2, 1, 1])      # add, mul, fma
-    fd2 = np.array([2, 1, 2])
+    fd2 = np.array([0, 1, 2])
     fdm = np.array([10, 1, 5])
     gather = N_D1_FIELDS * 3 * fd1 + N_D2_FIELDS * 3 * (fd2 + fdm)
     ko = NFIELDS * np.array([15, 0, 4])
