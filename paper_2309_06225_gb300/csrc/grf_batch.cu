@@ -41,7 +41,11 @@ template <int STAGE>
 __device__ __forceinline__ void batch_tile(const BoxDesc* __restrict__ boxes, const TileDesc& td, int* status) {
     const BoxDesc& d = boxes[td.box];
     const int i = td.i0 + threadIdx.x, j = td.j0 + threadIdx.y, k = td.k0 + threadIdx.z;
-    if (i >= d.g.nx || j >= d.g.ny || k >= d.g.nz) return;
+    // Tiles whose width is a multiple of 32: every warp is one x-row segment, and the x-mixed
+    // derivatives use shuffles (all lanes stay for the gather); narrower tiles evaluate them per
+    // thread. Results are identical.
+    const bool warp = (blockDim.x & 31) == 0;
+    if (j >= d.g.ny || k >= d.g.nz || (!warp && i >= d.g.nx)) return;
     StageArgs a;
     a.un = d.un;
     a.acc = d.acc;
@@ -54,7 +58,7 @@ __device__ __forceinline__ void batch_tile(const BoxDesc* __restrict__ boxes, co
     a.k0 = 0;
     a.src = (STAGE == 0) ? d.un : (STAGE == 1 ? d.A : (STAGE == 2 ? d.B : d.A));
     a.dst = (STAGE == 0) ? d.A : (STAGE == 1 ? d.B : (STAGE == 2 ? d.A : d.un));
-    stage_point<STAGE>(d.g, d.c, a, i, j, k);
+    stage_point<STAGE>(d.g, d.c, a, i, j, k, warp);
 }
 
 template <int STAGE>

@@ -45,11 +45,72 @@ __device__ __forceinline__ bool has_d2(int f) {
     return f == F_CHI || (f >= F_H && f < F_H + 6) || f == F_LAPSE || (f >= F_SHIFT && f < F_SHIFT + 3) || f == F_PHI;
 }
 
-// Values, first derivatives and second derivatives of all fields at ghosted offset p; with
-// kos != nullptr also each field's Kreiss-Oliger sum (as ko6 below, same order of additions),
-// sharing the pair sums at distances 1 and 2 with the second derivatives.
+// Field index of d2 slot b (inverse of d2slot).
+__host__ __device__ constexpr int d2field(int b) { return b < 7 ? b : (b == 7 ? F_LAPSE : (b < 11 ? b + 11 : F_PHI)); }
+
+// Mixed derivatives d_x d_t u (t = y or z) are the x-stencil applied to the scaled first
+// t-derivatives at x-2, x-1, x+1, x+2:  ((D(x-2) - D(x+2)) + 8 (D(x+1) - D(x-1))) / (12 dx),
+// D = fd1 along t. Where a warp is one x-row of 32 consecutive points, the four D values come
+// from the neighbouring lanes by shuffles (the lanes computed them as their own first
+// derivatives), and the 4 points beyond the row ends from a halo computed once per warp.
+// Elsewhere each thread evaluates the four D itself. Both give bit-identical results.
+struct WarpRow {
+    int lane;      // lane = x offset in the row
+    int selA, selB;  // halo slot for the x-2 / x+2 (A) and x-1 / x+1 (B) neighbours of end lanes
+    double hv[3];  // this lane's share of the halo: 12 d2 slots x {y, z} x 4 points, 3 per lane
+};
+
+// Halo of the warp's row: the first t-derivatives (t = y, z) of the 12 fields with second
+// derivatives at x0-2, x0-1, x0+32, x0+33 (clamped to the last ghost column; values beyond
+// nx+1 are never used by an interior point). Value (b, t, q) lives in lane 8 (b % 4) + 4 t + q,
+// register b / 4. Every lane of the warp must call this.
+__device__ __forceinline__ void warp_row_halo(const Geom& g, const double* __restrict__ s, int x0, int j, int k,
+                                              int lane, WarpRow& wr) {
+    const double i12 = 1.0 / (12.0 * g.dx);
+    const int q = lane & 3, t = (lane >> 2) & 1, bq = lane >> 3;
+    const int hx = min(q < 2 ? x0 - 2 + q : x0 + 30 + q, g.nx + 2);
+    const long long ph = gidx(g, hx + NG, j + NG, k + NG);
+    const long long sd = t ? g.plane : g.pitch;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) wr.hv[r] = fd1(s + (long long)d2field(4 * r + bq) * g.fstride, ph, sd, i12);
+    wr.lane = lane;
+    wr.selA = lane == 0 ? 0 : (lane == 1 ? 1 : (lane == 30 ? 2 : 3));
+    wr.selB = lane == 0 ? 1 : 2;
+}
+
+// d_x d_t u for d2 slot b from this lane's own D = fd1_t(u) and the neighbours' (warp path).
+__device__ __forceinline__ double mixed_x_warp(const WarpRow& wr, int b, int t, double own, double i12) {
+    const unsigned full = 0xffffffffu;
+    const int base = 8 * (b & 3) + 4 * t;
+    const double hA = __shfl_sync(full, wr.hv[b >> 2], base + wr.selA);
+    const double hB = __shfl_sync(full, wr.hv[b >> 2], base + wr.selB);
+    const double vm2 = __shfl_up_sync(full, own, 2), vm1 = __shfl_up_sync(full, own, 1);
+    const double vp1 = __shfl_down_sync(full, own, 1), vp2 = __shfl_down_sync(full, own, 2);
+    const double m2 = wr.lane < 2 ? hA : vm2;
+    const double m1 = wr.lane < 1 ? hB : vm1;
+    const double p1 = wr.lane > 30 ? hB : vp1;
+    const double p2 = wr.lane > 29 ? hA : vp2;
+    return __dmul_rn((m2 - p2) + 8.0 * (p1 - m1), i12);
+}
+
+// d_x d_t u with the four t-derivatives evaluated here. The scalings are explicitly rounded
+// (__dmul_rn, never fused into a neighbouring add), so the sums are those of mixed_x_warp, whose
+// neighbour values arrive rounded through the shuffles.
+__device__ __forceinline__ double fd1_rounded(const double* __restrict__ u, long long p, long long s, double i12) {
+    return __dmul_rn((__ldg(u + p - 2 * s) - __ldg(u + p + 2 * s)) + 8.0 * (__ldg(u + p + s) - __ldg(u + p - s)), i12);
+}
+__device__ __forceinline__ double mixed_x_local(const double* __restrict__ u, long long p, long long t, double i12) {
+    const double m2 = fd1_rounded(u, p - 2, t, i12), m1 = fd1_rounded(u, p - 1, t, i12);
+    const double p1 = fd1_rounded(u, p + 1, t, i12), p2 = fd1_rounded(u, p + 2, t, i12);
+    return __dmul_rn((m2 - p2) + 8.0 * (p1 - m1), i12);
+}
+
+// Values, first derivatives and second derivatives of all fields at ghosted offset p, and each
+// field's Kreiss-Oliger sum (as ko6 below, same order of additions), the pair sums at distances
+// 1 and 2 shared with the second derivatives. wr != nullptr: the warp is one x-row and the
+// x-mixed derivatives come from the neighbouring lanes (every lane of the warp must call this).
 __device__ __forceinline__ void gather(const Geom& g, const double* __restrict__ s, long long p, PointIn& in,
-                                       double* kos = nullptr) {
+                                       double kos[NFIELDS], const WarpRow* wr) {
     const double i12 = 1.0 / (12.0 * g.dx), i12s = 1.0 / (12.0 * g.dx * g.dx), i144 = 1.0 / (144.0 * g.dx * g.dx);
     const long long st[3] = {1, g.pitch, g.plane};
 #pragma unroll
@@ -57,32 +118,31 @@ __device__ __forceinline__ void gather(const Geom& g, const double* __restrict__
         const double* u = s + f * g.fstride;
         const double u0 = __ldg(u + p);
         in.v[f] = u0;
-        double p1[3], p2[3];
+        double p1[3], p2[3], d1[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const double m1 = __ldg(u + p - st[d]), q1 = __ldg(u + p + st[d]);
             const double m2 = __ldg(u + p - 2 * st[d]), q2 = __ldg(u + p + 2 * st[d]);
-            if (!(f >= F_B && f < F_B + 3)) in.d1[d1slot(f)][d] = ((m2 - q2) + 8.0 * (q1 - m1)) * i12;
+            d1[d] = ((m2 - q2) + 8.0 * (q1 - m1)) * i12;
+            if (!(f >= F_B && f < F_B + 3)) in.d1[d1slot(f)][d] = d1[d];
             p1[d] = q1 + m1;
             p2[d] = q2 + m2;
         }
         if (has_d2(f)) {
             const int b = d2slot(f);
             in.d2[b][0] = (16.0 * p1[0] - p2[0] - 30.0 * u0) * i12s;
-            in.d2[b][1] = fdm(u, p, st[0], st[1], i144);
-            in.d2[b][2] = fdm(u, p, st[0], st[2], i144);
+            in.d2[b][1] = wr ? mixed_x_warp(*wr, b, 0, d1[1], i12) : mixed_x_local(u, p, st[1], i12);
+            in.d2[b][2] = wr ? mixed_x_warp(*wr, b, 1, d1[2], i12) : mixed_x_local(u, p, st[2], i12);
             in.d2[b][3] = (16.0 * p1[1] - p2[1] - 30.0 * u0) * i12s;
             in.d2[b][4] = fdm(u, p, st[1], st[2], i144);
             in.d2[b][5] = (16.0 * p1[2] - p2[2] - 30.0 * u0) * i12s;
         }
-        if (kos) {
-            const double t3 = ((__ldg(u + p - 3 * st[0]) + __ldg(u + p + 3 * st[0])) +
-                               (__ldg(u + p - 3 * st[1]) + __ldg(u + p + 3 * st[1]))) +
-                              (__ldg(u + p - 3 * st[2]) + __ldg(u + p + 3 * st[2]));
-            const double t2 = (p2[0] + p2[1]) + p2[2];
-            const double t1 = (p1[0] + p1[1]) + p1[2];
-            kos[f] = t3 - 6.0 * t2 + 15.0 * t1 - 60.0 * u0;
-        }
+        const double t3 = ((__ldg(u + p - 3 * st[0]) + __ldg(u + p + 3 * st[0])) +
+                           (__ldg(u + p - 3 * st[1]) + __ldg(u + p + 3 * st[1]))) +
+                          (__ldg(u + p - 3 * st[2]) + __ldg(u + p + 3 * st[2]));
+        const double t2 = (p2[0] + p2[1]) + p2[2];
+        const double t1 = (p1[0] + p1[1]) + p1[2];
+        kos[f] = t3 - 6.0 * t2 + 15.0 * t1 - 60.0 * u0;
     }
 }
 
@@ -156,14 +216,27 @@ struct StageArgs {
     int k0;              // first interior z-plane of the launch (grid.z covers planes k0, k0+1, ...)
 };
 
-// One RK4 stage at one interior point, fused: gather -> pointwise RHS -> + KO -> stage update
-// -> enforcement -> store (with periodic images). STAGE 0..3.
+// One RK4 stage at one point, fused: gather -> pointwise RHS -> + KO -> stage update ->
+// enforcement -> store (with periodic images). STAGE 0..3. warp: the calling warp is one x-row
+// of 32 consecutive points (x0 = i - lane); its lanes past the interior (i >= nx) still take
+// part in the gather, at the last ghost column at most, and then write nothing.
 template <int STAGE>
-__device__ __forceinline__ void stage_point(const Geom& g, const Coeffs& c, const StageArgs& a, int i, int j, int k) {
-    const long long p = gidx(g, i + NG, j + NG, k + NG);
+__device__ __forceinline__ void stage_point(const Geom& g, const Coeffs& c, const StageArgs& a, int i, int j, int k,
+                                            bool warp) {
+    const bool live = i < g.nx;
+    const int ic = min(i, g.nx + 2);
+    const long long p = gidx(g, ic + NG, j + NG, k + NG);
     PointIn in;
     double kos[NFIELDS];
-    gather(g, a.src, p, in, kos);
+    if (warp) {
+        WarpRow wr;
+        const int lane = threadIdx.x & 31;
+        warp_row_halo(g, a.src, i - lane, j, k, lane, wr);
+        gather(g, a.src, p, in, kos, &wr);
+    } else {
+        gather(g, a.src, p, in, kos, nullptr);
+    }
+    if (!live) return;
     double r[NFIELDS];
     bool ok = true;
     point_rhs<double>(c, in, r, nullptr, ok);
@@ -186,15 +259,16 @@ __device__ __forceinline__ void stage_point(const Geom& g, const Coeffs& c, cons
     for (int f = 0; f < NFIELDS; ++f) store_with_images(g, a.dst, f, i, j, k, out[f]);
 }
 
+// Launched with blocks of (32, by, 1) threads: every warp is one x-row segment. Planes k0, k0+1, ...
 // 3 resident blocks of 128 threads per SM (168 registers a thread): the extra warps hide more
 // FP64 dependency latency than the added spills cost (measured 2% faster than 2 blocks).
 template <int STAGE>
 __global__ void __launch_bounds__(128, 3) rk4_stage_kernel(Geom g, Coeffs c, StageArgs a) {
-    int i, j, k;
-    if (!interior_thread(g, i, j, k)) return;
-    k += a.k0;
-    if (k >= g.nz) return;
-    stage_point<STAGE>(g, c, a, i, j, k);
+    const int i = blockIdx.x * 32 + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z + a.k0;
+    if (j >= g.ny || k >= g.nz) return;  // whole warps
+    stage_point<STAGE>(g, c, a, i, j, k, true);
 }
 
 }  // namespace grf

@@ -106,22 +106,47 @@ GRF_HD T sym3_inv(const T h[6], T hi[6], T& id) {
     return det;
 }
 
-// 7x7 LU with partial pivoting (row swaps by compare-and-exchange, so every index stays a
-// compile-time constant and the matrix stays in registers). Returns false on a pivot
-// smaller than 1e-300 times the largest entry.
+// |a| > |b|, and the largest |M_ij| of the 7x7 block. For doubles on the device both run on the
+// integer pipe: with the sign bit cleared, the bit patterns of non-NaN doubles order like their
+// magnitudes (a NaN entry makes the maximum a NaN, which then fails every pivot test).
 template <typename T>
-GRF_HD bool solve7(T M[7][8]) {
+GRF_HD bool abs_gt(const T& a, const T& b) { return fabs(a) > fabs(b); }
+template <typename T>
+GRF_HD T abs_max7(const T M[7][8]) {
     T mx = 0.0;
 #pragma unroll
     for (int i = 0; i < 7; ++i)
 #pragma unroll
         for (int j = 0; j < 7; ++j) mx = fmax(mx, fabs(M[i][j]));
+    return mx;
+}
+#ifdef __CUDA_ARCH__
+__device__ __forceinline__ long long abs_bits(double x) { return __double_as_longlong(x) & 0x7fffffffffffffffLL; }
+__device__ __forceinline__ bool abs_gt(double a, double b) { return abs_bits(a) > abs_bits(b); }
+__device__ __forceinline__ double abs_max7(const double M[7][8]) {
+    long long m = 0;
+#pragma unroll
+    for (int i = 0; i < 7; ++i)
+#pragma unroll
+        for (int j = 0; j < 7; ++j) m = max(m, abs_bits(M[i][j]));
+    return __longlong_as_double(m);
+}
+#endif
+
+// 7x7 LU with partial pivoting (row swaps by compare-and-exchange, so every index stays a
+// compile-time constant and the matrix stays in registers); the pivot rows are not normalised,
+// the back substitution multiplies by the stored pivot reciprocals. Returns false on a pivot
+// not larger than 1e-300 times the largest entry.
+template <typename T>
+GRF_HD bool solve7(T M[7][8]) {
+    const T thr = 1e-300 * abs_max7(M);
     bool ok = true;
+    T ipv[7];
 #pragma unroll
     for (int k = 0; k < 7; ++k) {
 #pragma unroll
         for (int i = k + 1; i < 7; ++i) {
-            const bool sw = fabs(M[i][k]) > fabs(M[k][k]);
+            const bool sw = abs_gt(M[i][k], M[k][k]);
 #pragma unroll
             for (int j = k; j < 8; ++j) {
                 const T a = M[k][j], b = M[i][j];
@@ -131,22 +156,22 @@ GRF_HD bool solve7(T M[7][8]) {
                 GRF_OPAQUE(M[i][j]);
             }
         }
-        ok = ok && (fabs(M[k][k]) > 1e-300 * mx);
+        ok = ok && abs_gt(M[k][k], thr);
         const T ip = 1.0 / M[k][k];
+        ipv[k] = ip;
 #pragma unroll
         for (int i = k + 1; i < 7; ++i) {
             const T f = M[i][k] * ip;
 #pragma unroll
             for (int j = k + 1; j < 8; ++j) M[i][j] = fma(-f, M[k][j], M[i][j]);
         }
-        M[k][7] *= ip;
-#pragma unroll
-        for (int j = k + 1; j < 7; ++j) M[k][j] *= ip;
     }
 #pragma unroll
     for (int k = 6; k >= 0; --k) {
+        T x = M[k][7];
 #pragma unroll
-        for (int j = k + 1; j < 7; ++j) M[k][7] = fma(-M[k][j], M[j][7], M[k][7]);
+        for (int j = k + 1; j < 7; ++j) x = fma(-M[k][j], M[j][7], x);
+        M[k][7] = x * ipv[k];
     }
     return ok;
 }
@@ -254,6 +279,14 @@ GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS]
     // ---- dGl[m][l] = d_m Gl_l = d_m h^ij Gt_lij + h^ij d_m d_i h_lj - h^ij d_m d_l h_ij / 2
     GRF_SECTION(3);
     T dGl[3][3];
+    T hdd[6];  // h^pq d_m d_l h_pq, symmetric in (m, l)
+#pragma unroll
+    for (int ml = 0; ml < 6; ++ml) {
+        T b = hw[0] * D2(F_H + 0, ml);
+#pragma unroll
+        for (int q = 1; q < 6; ++q) b = fma(hw[q], D2(F_H + q, ml), b);
+        hdd[ml] = b;
+    }
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
         T Tm[3][3];  // h^ac d_m h_cd
@@ -278,10 +311,7 @@ GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS]
             for (int i = 0; i < 3; ++i)
 #pragma unroll
                 for (int j = 0; j < 3; ++j) s = fma(hi[sidx(i, j)], D2(F_H + sidx(l, j), sidx(m, i)), s);
-            T b = 0.0;
-#pragma unroll
-            for (int q = 0; q < 6; ++q) b = (q == 0) ? hw[0] * D2(F_H + 0, sidx(m, l)) : fma(hw[q], D2(F_H + q, sidx(m, l)), b);
-            dGl[m][l] = fma(-0.5, b, s);
+            dGl[m][l] = fma(-0.5, hdd[sidx(m, l)], s);
         }
     }
 
@@ -451,30 +481,21 @@ GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS]
             for (int k = 0; k < 3; ++k) s = fma(Kp[sidx(k, j)], db[i][k], fma(Kp[sidx(i, k)], db[j][k], s));
             LbK[sidx(i, j)] = s;
         }
-    // Codazzi block through its dual: bb[k][m] = B_{k,(m+1),(m+2)} = D_(m+1) K_k(m+2) - D_(m+2) K_k(m+1)
+    // Codazzi block through its dual: bb[k][m] = B_{k,(m+1),(m+2)} = D_a K_kb - D_b K_ka with
+    // (a, b) = (m+1, m+2). The Gp^l_ab K_kl parts of the two covariant derivatives cancel (the
+    // connection is symmetric), leaving d_a K_kb - d_b K_ka - Gp^l_ak K_lb + Gp^l_bk K_la.
     T bb[3][3];
-    {
-        T DK[3][6];  // D_k K_ij
 #pragma unroll
-        for (int k = 0; k < 3; ++k)
+    for (int k = 0; k < 3; ++k)
 #pragma unroll
-            for (int i = 0; i < 3; ++i)
+        for (int m = 0; m < 3; ++m) {
+            const int a = (m + 1) % 3, b = (m + 2) % 3;
+            T s = dKp[a][sidx(k, b)] - dKp[b][sidx(k, a)];
 #pragma unroll
-                for (int j = i; j < 3; ++j) {
-                    T s = dKp[k][sidx(i, j)];
-#pragma unroll
-                    for (int l = 0; l < 3; ++l)
-                        s = fma(-Gp[l][sidx(k, i)], Kp[sidx(l, j)], fma(-Gp[l][sidx(k, j)], Kp[sidx(i, l)], s));
-                    DK[k][sidx(i, j)] = s;
-                }
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-#pragma unroll
-            for (int m = 0; m < 3; ++m) {
-                const int a = (m + 1) % 3, b = (m + 2) % 3;
-                bb[k][m] = DK[a][sidx(k, b)] - DK[b][sidx(k, a)];
-            }
-    }
+            for (int l = 0; l < 3; ++l)
+                s = fma(-Gp[l][sidx(a, k)], Kp[sidx(l, b)], fma(Gp[l][sidx(b, k)], Kp[sidx(l, a)], s));
+            bb[k][m] = s;
+        }
 #define BC(k, i, j) (cyclic(i, j) ? bb[k][third(i, j)] : -bb[k][third(i, j)])
     T Bv[3];  // B_j = gamma^ab B_abj
 #pragma unroll

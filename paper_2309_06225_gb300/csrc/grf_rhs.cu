@@ -4,14 +4,21 @@
 
 namespace grf {
 
+// Launched with blocks of (32, by, 1) threads: every warp is one x-row segment (see stage_point).
 __global__ void __launch_bounds__(128) rhs_kernel(Geom g, Coeffs c, const double* __restrict__ s, double* __restrict__ rhs,
                                                   double ko, int* status) {
-    int i, j, k;
-    if (!interior_thread(g, i, j, k)) return;
-    const long long p = gidx(g, i + NG, j + NG, k + NG);
+    const int i = blockIdx.x * 32 + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (j >= g.ny || k >= g.nz) return;  // whole warps
+    const int lane = threadIdx.x & 31;
+    const long long p = gidx(g, min(i, g.nx + 2) + NG, j + NG, k + NG);
     PointIn in;
     double kos[NFIELDS];
-    gather(g, s, p, in, kos);
+    WarpRow wr;
+    warp_row_halo(g, s, i - lane, j, k, lane, wr);
+    gather(g, s, p, in, kos, &wr);
+    if (i >= g.nx) return;
     double r[NFIELDS];
     bool ok = true;
     point_rhs<double>(c, in, r, nullptr, ok);
@@ -31,7 +38,8 @@ __global__ void __launch_bounds__(128) constraints_kernel(Geom g, Coeffs c, cons
     if (live) {
         const long long p = gidx(g, i + NG, j + NG, k + NG);
         PointIn in;
-        gather(g, s, p, in);
+        double kos[NFIELDS];
+        gather(g, s, p, in, kos, nullptr);
         double r[NFIELDS];
         PointExtra ex;
         bool ok = true;

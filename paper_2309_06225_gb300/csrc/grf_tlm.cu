@@ -47,8 +47,8 @@ __device__ __forceinline__ void gather_d3(const Geom& g, const double* const* s,
             }
             if (second) {
                 d2[c][0] = fd2(u, p, sx, v[c], i12s);
-                d2[c][1] = fdm(u, p, sx, sy, i144);
-                d2[c][2] = fdm(u, p, sx, sz, i144);
+                d2[c][1] = mixed_x_local(u, p, sy, i12);
+                d2[c][2] = mixed_x_local(u, p, sz, i12);
                 d2[c][3] = fd2(u, p, sy, v[c], i12s);
                 d2[c][4] = fdm(u, p, sy, sz, i144);
                 d2[c][5] = fd2(u, p, sz, v[c], i12s);
