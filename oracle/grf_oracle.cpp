@@ -26,6 +26,11 @@
 //   * Kreiss-Oliger dissipation sigma/(64 dx) sum_d Delta^6_d u on all fields
 //   * classical RK4 with post-stage algebraic enforcement (trace-free A, chi and lapse floors)
 //
+// Parity unpinned (no pin fixes these terms independently of the equations as read; they vanish
+// or reduce to their pinned limits on the pinned data): the modified-gauge a/b terms beyond
+// a = b = 0 and their vanishing on constraint-satisfying data, the 1+log / Gamma-driver gauge
+// coefficients, and the Theta damping term of the K equation.
+//
 // Plain loops, no blocking, FP64 (long double only inside the linear solve).
 // Build: g++ -O2 -ffp-contract=off -fopenmp -shared -fPIC (see oracle/build.py).
 

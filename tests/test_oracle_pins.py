@@ -35,6 +35,69 @@ def test_flat_space_rhs_is_exactly_zero(orc, kw):
     assert np.all(r == 0.0)
 
 
+# ----------------------------------------------------------------------------- P1b damping
+@pytest.mark.parametrize("k1,k2,alpha,chi,a0,b0", [(0.1, 0.0, 1.0, 1.0, 0.0, 0.0), (0.5, 0.3, 0.7, 0.6, 0.2, 0.4),
+                                                   (0.25, -0.4, 1.3, 0.9, 0.0, 1.1)])
+def test_z4_constraint_damping_rates_on_flat_data(orc, k1, k2, alpha, chi, a0, b0):
+    """Damped Z4 on a flat slice: constant conformal factor, h = delta, K = A = 0, zero shift,
+    a constant lapse, a constant Theta and a constant Z_i. Z_i is carried by Gamma-hat^i =
+    Gamma-tilde^i + 2 h^ij Z_j with Gamma-tilde = 0. Every curvature, gradient and Z-derivative
+    term vanishes, so only the damping is left. The constraint fields decay at the damped-Z4
+    rates
+        d_t Theta = -alpha kappa1 (2 + kappa2) Theta,   d_t Z_i = -alpha kappa1 Z_i,
+    and the metric and A_ij stay static. Catches a dropped or anti-damping kappa term, kappa2
+    in the wrong place, a missing lapse factor, and Z read with the wrong metric factor."""
+    v = np.zeros(27)
+    v[0] = chi
+    v[1], v[4], v[6] = 1.0, 1.0, 1.0
+    theta = 0.3
+    ghat = np.array([0.2, -0.1, 0.05])
+    v[14] = theta
+    v[15:18] = ghat
+    v[18] = alpha
+    d1 = np.zeros((27, 3))
+    d2 = np.zeros((27, 6))
+    p = P(kappa1=k1, kappa2=k2, kappa3=0.7, a0=a0, b0=b0, lam=0.2, g2=0.1)
+    r, _, st = orc.point_rhs(p, v, d1, d2)
+    assert st == 0
+    assert r[14] == pytest.approx(-alpha * k1 * (2.0 + k2) * theta, rel=1e-14, abs=1e-15)
+    # d_t Gamma-hat^i = 2 h^ij d_t Z_j = -alpha kappa1 Gamma-hat^i (h static, Gamma-tilde = 0)
+    np.testing.assert_allclose(r[15:18], -alpha * k1 * ghat, rtol=1e-14, atol=1e-15)
+    assert np.all(r[0:7] == 0.0) and np.all(r[8:14] == 0.0)     # chi, h_ij, A_ij static
+    assert np.all(r[19:22] == 0.0) and r[25] == 0.0  # shift, phi
+    assert abs(r[26]) < 1e-15  # Pi: zero up to the rounding of the oracle's residual-based solve
+    # the same data with the damping switched off: the constraint fields do not move
+    r0, _, _ = orc.point_rhs(P(kappa1=0.0, kappa2=k2, kappa3=0.7, a0=a0, b0=b0, lam=0.2, g2=0.1), v, d1, d2)
+    assert r0[14] == 0.0 and np.all(r0[15:18] == 0.0)
+
+
+@pytest.mark.parametrize("k3", [0.0, 0.5, 1.0])
+def test_z_part_of_gamma_hat_is_shift_transported_by_kappa3(orc, k3):
+    """The same flat slice with a constant Z_i and a shift whose gradient M^i_k = d_k beta^i is
+    constant (beta = 0 at the point). The conformal Christoffels, all second derivatives and every
+    gradient of the other fields vanish, so the Gamma-hat^i equation keeps only the damping and
+    the transport of its Z part: kappa3 = 1 transports 2 h^ij Z_j by the shift exactly as
+    Gamma-tilde^i is transported, i.e. as a vector density of weight 2/3 (2/3 G^i tr M - G^k M^i_k);
+    kappa3 scales that transport. Catches a wrong kappa3 placement, a transposed M, or a 2/3
+    weight error."""
+    alpha, k1 = 0.9, 0.2
+    v = np.zeros(27)
+    v[0] = 0.8
+    v[1], v[4], v[6] = 1.0, 1.0, 1.0
+    ghat = np.array([0.3, -0.2, 0.1])
+    v[15:18] = ghat
+    v[18] = alpha
+    d1 = np.zeros((27, 3))
+    M = np.array([[0.2, -0.1, 0.05], [0.3, 0.1, -0.2], [-0.15, 0.25, 0.4]])  # M[i][k] = d_k beta^i
+    for i in range(3):
+        d1[19 + i, :] = M[i]
+    d2 = np.zeros((27, 6))
+    r, _, st = orc.point_rhs(P(kappa1=k1, kappa2=0.1, kappa3=k3), v, d1, d2)
+    assert st == 0
+    expect = -alpha * k1 * ghat + k3 * ((2.0 / 3.0) * ghat * np.trace(M) - M @ ghat)
+    np.testing.assert_allclose(r[15:18], expect, rtol=1e-13, atol=1e-15)
+
+
 # ----------------------------------------------------------------------------- P3 stencils
 def _poly(X, Y, Z, coef, deg):
     out = np.zeros_like(X)
