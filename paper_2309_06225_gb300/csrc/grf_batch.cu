@@ -38,14 +38,16 @@ struct TileDesc {
 };
 
 template <int STAGE>
-__device__ __forceinline__ void batch_tile(const BoxDesc* __restrict__ boxes, const TileDesc& td, int* status) {
+__device__ __forceinline__ void batch_tile(const BoxDesc* __restrict__ boxes, const TileDesc& td, int* status,
+                                           YzRows& sh) {
     const BoxDesc& d = boxes[td.box];
     const int i = td.i0 + threadIdx.x, j = td.j0 + threadIdx.y, k = td.k0 + threadIdx.z;
-    // Tiles whose width is a multiple of 32: every warp is one x-row segment, and the x-mixed
-    // derivatives use shuffles (all lanes stay for the gather); narrower tiles evaluate them per
-    // thread. Results are identical.
-    const bool warp = (blockDim.x & 31) == 0;
-    if (j >= d.g.ny || k >= d.g.nz || (!warp && i >= d.g.nx)) return;
+    // Tile shape -> gather mode (all modes give the same bits):
+    //   32 x 4 x 1: block mode, d_y d_z through the shared rows; every thread stays to the barrier.
+    //   width a multiple of 32: warp mode; whole warps stay for the shuffles.
+    //   otherwise: per-thread mode.
+    const int mode = (blockDim.x == 32 && blockDim.y == 4 && blockDim.z == 1) ? GATHER_BLOCK
+                     : ((blockDim.x & 31) == 0 ? GATHER_WARP : GATHER_LOCAL);
     StageArgs a;
     a.un = d.un;
     a.acc = d.acc;
@@ -58,16 +60,25 @@ __device__ __forceinline__ void batch_tile(const BoxDesc* __restrict__ boxes, co
     a.k0 = 0;
     a.src = (STAGE == 0) ? d.un : (STAGE == 1 ? d.A : (STAGE == 2 ? d.B : d.A));
     a.dst = (STAGE == 0) ? d.A : (STAGE == 1 ? d.B : (STAGE == 2 ? d.A : d.un));
-    stage_point<STAGE>(d.g, d.c, a, i, j, k, warp);
+    if (mode == GATHER_BLOCK) {
+        if (k >= d.g.nz) return;  // the whole block (k = td.k0)
+        __syncthreads();          // readers of the previous tile's rows are done
+        yz_rows_fill(d.g, a.src, i, td.j0, threadIdx.y, k, threadIdx.x, sh);
+        __syncthreads();
+    } else if (j >= d.g.ny || k >= d.g.nz || (mode == GATHER_LOCAL && i >= d.g.nx)) {
+        return;
+    }
+    stage_point<STAGE>(d.g, d.c, a, i, j, k, mode, &sh);
 }
 
 template <int STAGE>
 __global__ void __launch_bounds__(128, 3) batch_stage_kernel(const BoxDesc* __restrict__ boxes,
                                                           const TileDesc* __restrict__ tiles, int ntiles, int* status) {
+    __shared__ YzRows sh;
     const int t = blockIdx.x;
     if (t >= ntiles) return;
     const TileDesc td = tiles[t];
-    batch_tile<STAGE>(boxes, td, status);
+    batch_tile<STAGE>(boxes, td, status, sh);
 }
 
 // Grid-wide barrier for a cooperative launch. Thread 0 of each block arrives on a counter;
@@ -109,16 +120,17 @@ __global__ void __launch_bounds__(128, 3) batch_persistent_kernel(const BoxDesc*
                                                                const TileDesc* __restrict__ tiles, int ntiles,
                                                                int nsteps, unsigned* bar, int* status,
                                                                long long timeout) {
+    __shared__ YzRows sh;
     for (int n = 0; n < nsteps; ++n) {
 #pragma unroll 1
         for (int s = 0; s < 4; ++s) {
             for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
                 const TileDesc td = tiles[t];
                 switch (s) {
-                    case 0: batch_tile<0>(boxes, td, status); break;
-                    case 1: batch_tile<1>(boxes, td, status); break;
-                    case 2: batch_tile<2>(boxes, td, status); break;
-                    default: batch_tile<3>(boxes, td, status); break;
+                    case 0: batch_tile<0>(boxes, td, status, sh); break;
+                    case 1: batch_tile<1>(boxes, td, status, sh); break;
+                    case 2: batch_tile<2>(boxes, td, status, sh); break;
+                    default: batch_tile<3>(boxes, td, status, sh); break;
                 }
             }
             if (!grid_barrier(bar, gridDim.x, timeout, status)) return;

@@ -24,21 +24,15 @@ __device__ __forceinline__ long long gidx(const Geom& g, int i, int j, int k) { 
     return (long long)k * g.plane + (long long)j * g.pitch + i;
 }
 
-// Centred 4th-order first, second and mixed derivatives at ghosted offset p.
+// Centred 4th-order first and second derivatives at ghosted offset p.
 // first: (u_-2 - 8 u_-1 + 8 u_+1 - u_+2)/(12 dx) ; second: (-u_-2 + 16 u_-1 - 30 u_0 + 16 u_+1 - u_+2)/(12 dx^2)
-// mixed: tensor product of the first-derivative weights, /(144 dx^2).
+// Mixed derivatives (tensor product of the first-derivative weights) are formed below as the
+// first-derivative stencil applied to rounded first derivatives.
 __device__ __forceinline__ double fd1(const double* __restrict__ u, long long p, long long s, double i12) {
     return ((__ldg(u + p - 2 * s) - __ldg(u + p + 2 * s)) + 8.0 * (__ldg(u + p + s) - __ldg(u + p - s))) * i12;
 }
 __device__ __forceinline__ double fd2(const double* __restrict__ u, long long p, long long s, double u0, double i12s) {
     return (16.0 * (__ldg(u + p + s) + __ldg(u + p - s)) - (__ldg(u + p + 2 * s) + __ldg(u + p - 2 * s)) - 30.0 * u0) * i12s;
-}
-__device__ __forceinline__ double fdm(const double* __restrict__ u, long long p, long long s, long long t, double i144) {
-    // sum_a c_a * (first-derivative combination along t at offset a*s), c = (1, -8, 8, -1) at (-2,-1,1,2)
-    auto row = [&](long long q) {
-        return (__ldg(u + q - 2 * t) - __ldg(u + q + 2 * t)) + 8.0 * (__ldg(u + q + t) - __ldg(u + q - t));
-    };
-    return ((row(p - 2 * s) - row(p + 2 * s)) + 8.0 * (row(p + s) - row(p - s))) * i144;
 }
 
 __device__ __forceinline__ bool has_d2(int f) {
@@ -93,26 +87,58 @@ __device__ __forceinline__ double mixed_x_warp(const WarpRow& wr, int b, int t, 
     return __dmul_rn((m2 - p2) + 8.0 * (p1 - m1), i12);
 }
 
-// d_x d_t u with the four t-derivatives evaluated here. The scalings are explicitly rounded
-// (__dmul_rn, never fused into a neighbouring add), so the sums are those of mixed_x_warp, whose
-// neighbour values arrive rounded through the shuffles.
+// d_s d_t u with the four t-derivatives at the s-neighbours evaluated here (s = x or y). The
+// scalings are explicitly rounded (__dmul_rn, never fused into a neighbouring add), so the sums
+// are those of the shuffle and shared-memory paths, whose neighbour values arrive rounded.
 __device__ __forceinline__ double fd1_rounded(const double* __restrict__ u, long long p, long long s, double i12) {
     return __dmul_rn((__ldg(u + p - 2 * s) - __ldg(u + p + 2 * s)) + 8.0 * (__ldg(u + p + s) - __ldg(u + p - s)), i12);
 }
-__device__ __forceinline__ double mixed_x_local(const double* __restrict__ u, long long p, long long t, double i12) {
-    const double m2 = fd1_rounded(u, p - 2, t, i12), m1 = fd1_rounded(u, p - 1, t, i12);
-    const double p1 = fd1_rounded(u, p + 1, t, i12), p2 = fd1_rounded(u, p + 2, t, i12);
+__device__ __forceinline__ double mixed_local(const double* __restrict__ u, long long p, long long so, long long t,
+                                              double i12) {
+    const double m2 = fd1_rounded(u, p - 2 * so, t, i12), m1 = fd1_rounded(u, p - so, t, i12);
+    const double p1 = fd1_rounded(u, p + so, t, i12), p2 = fd1_rounded(u, p + 2 * so, t, i12);
     return __dmul_rn((m2 - p2) + 8.0 * (p1 - m1), i12);
+}
+
+// d_y d_z in blocks of 32 x 4 threads (every warp one x-row, the 4 warps consecutive y-rows):
+// the rounded first z-derivatives of the 12 fields with second derivatives on rows y0-2 .. y0+5
+// (row index y - y0 + 2) are shared through shared memory; each warp adds one halo row.
+struct YzRows {
+    double dz[12][8][32];
+};
+
+// Every thread of the block calls this, then __syncthreads(). x, y0 + wy: the thread's point
+// (clamped to the last ghost column / row: values there are only read by points outside the
+// interior); k: an interior plane.
+__device__ __forceinline__ void yz_rows_fill(const Geom& g, const double* __restrict__ s, int x, int y0, int wy,
+                                             int k, int lane, YzRows& sh) {
+    const double i12 = 1.0 / (12.0 * g.dx);
+    const int xc = min(x, g.nx + 2);
+    const int yo = min(y0 + wy, g.ny + 2);
+    const int yh = min(wy < 2 ? y0 - 2 + wy : y0 + 2 + wy, g.ny + 2);  // rows y0-2, y0-1, y0+4, y0+5
+    const int rh = wy < 2 ? wy : wy + 4;
+    const long long po = gidx(g, xc + NG, yo + NG, k + NG), ph = gidx(g, xc + NG, yh + NG, k + NG);
+#pragma unroll
+    for (int b = 0; b < 12; ++b) {
+        const double* u = s + (long long)d2field(b) * g.fstride;
+        sh.dz[b][wy + 2][lane] = fd1_rounded(u, po, g.plane, i12);
+        sh.dz[b][rh][lane] = fd1_rounded(u, ph, g.plane, i12);
+    }
 }
 
 // Values, first derivatives and second derivatives of all fields at ghosted offset p, and each
 // field's Kreiss-Oliger sum (as ko6 below, same order of additions), the pair sums at distances
-// 1 and 2 shared with the second derivatives. wr != nullptr: the warp is one x-row and the
-// x-mixed derivatives come from the neighbouring lanes (every lane of the warp must call this).
+// 1 and 2 shared with the second derivatives.
+//   wr != nullptr: the warp is one x-row; d_x d_y and d_x d_z come from the neighbouring lanes
+//                  (every lane of the warp must call this).
+//   sh != nullptr: d_y d_z (and the first z-derivatives of the 12 fields with second
+//                  derivatives) come from the block's shared rows; wy = the thread's row.
+// Every combination gives the same bits.
 __device__ __forceinline__ void gather(const Geom& g, const double* __restrict__ s, long long p, PointIn& in,
-                                       double kos[NFIELDS], const WarpRow* wr) {
-    const double i12 = 1.0 / (12.0 * g.dx), i12s = 1.0 / (12.0 * g.dx * g.dx), i144 = 1.0 / (144.0 * g.dx * g.dx);
+                                       double kos[NFIELDS], const WarpRow* wr, const YzRows* sh, int wy) {
+    const double i12 = 1.0 / (12.0 * g.dx), i12s = 1.0 / (12.0 * g.dx * g.dx);
     const long long st[3] = {1, g.pitch, g.plane};
+    const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int f = 0; f < NFIELDS; ++f) {
         const double* u = s + f * g.fstride;
@@ -123,7 +149,11 @@ __device__ __forceinline__ void gather(const Geom& g, const double* __restrict__
         for (int d = 0; d < 3; ++d) {
             const double m1 = __ldg(u + p - st[d]), q1 = __ldg(u + p + st[d]);
             const double m2 = __ldg(u + p - 2 * st[d]), q2 = __ldg(u + p + 2 * st[d]);
-            d1[d] = ((m2 - q2) + 8.0 * (q1 - m1)) * i12;
+            if (d == 2 && has_d2(f)) {  // rounded: shared with the neighbours' d_y d_z
+                d1[d] = sh ? sh->dz[d2slot(f)][wy + 2][lane] : __dmul_rn((m2 - q2) + 8.0 * (q1 - m1), i12);
+            } else {
+                d1[d] = ((m2 - q2) + 8.0 * (q1 - m1)) * i12;
+            }
             if (!(f >= F_B && f < F_B + 3)) in.d1[d1slot(f)][d] = d1[d];
             p1[d] = q1 + m1;
             p2[d] = q2 + m2;
@@ -131,10 +161,15 @@ __device__ __forceinline__ void gather(const Geom& g, const double* __restrict__
         if (has_d2(f)) {
             const int b = d2slot(f);
             in.d2[b][0] = (16.0 * p1[0] - p2[0] - 30.0 * u0) * i12s;
-            in.d2[b][1] = wr ? mixed_x_warp(*wr, b, 0, d1[1], i12) : mixed_x_local(u, p, st[1], i12);
-            in.d2[b][2] = wr ? mixed_x_warp(*wr, b, 1, d1[2], i12) : mixed_x_local(u, p, st[2], i12);
+            in.d2[b][1] = wr ? mixed_x_warp(*wr, b, 0, d1[1], i12) : mixed_local(u, p, st[0], st[1], i12);
+            in.d2[b][2] = wr ? mixed_x_warp(*wr, b, 1, d1[2], i12) : mixed_local(u, p, st[0], st[2], i12);
             in.d2[b][3] = (16.0 * p1[1] - p2[1] - 30.0 * u0) * i12s;
-            in.d2[b][4] = fdm(u, p, st[1], st[2], i144);
+            if (sh) {
+                const double(*r)[32] = sh->dz[b];
+                in.d2[b][4] = __dmul_rn((r[wy][lane] - r[wy + 4][lane]) + 8.0 * (r[wy + 3][lane] - r[wy + 1][lane]), i12);
+            } else {
+                in.d2[b][4] = mixed_local(u, p, st[1], st[2], i12);
+            }
             in.d2[b][5] = (16.0 * p1[2] - p2[2] - 30.0 * u0) * i12s;
         }
         const double t3 = ((__ldg(u + p - 3 * st[0]) + __ldg(u + p + 3 * st[0])) +
@@ -216,25 +251,33 @@ struct StageArgs {
     int k0;              // first interior z-plane of the launch (grid.z covers planes k0, k0+1, ...)
 };
 
+// How a stage's gather takes its mixed derivatives (all modes give the same bits).
+enum GatherMode {
+    GATHER_LOCAL = 0,  // per thread
+    GATHER_WARP = 1,   // warps are x-rows: d_x d_y, d_x d_z by shuffles
+    GATHER_BLOCK = 2,  // blocks of 32 x 4 (x-rows stacked in y): also d_y d_z through shared memory
+};
+
 // One RK4 stage at one point, fused: gather -> pointwise RHS -> + KO -> stage update ->
-// enforcement -> store (with periodic images). STAGE 0..3. warp: the calling warp is one x-row
-// of 32 consecutive points (x0 = i - lane); its lanes past the interior (i >= nx) still take
-// part in the gather, at the last ghost column at most, and then write nothing.
+// enforcement -> store (with periodic images). STAGE 0..3. In the warp and block modes the
+// threads past the interior (i >= nx, and j >= ny in block mode) take part in the gather, at the
+// last ghost column / row at most, and then write nothing. sh: the block's rows (block mode,
+// already filled and synchronised).
 template <int STAGE>
 __device__ __forceinline__ void stage_point(const Geom& g, const Coeffs& c, const StageArgs& a, int i, int j, int k,
-                                            bool warp) {
-    const bool live = i < g.nx;
-    const int ic = min(i, g.nx + 2);
-    const long long p = gidx(g, ic + NG, j + NG, k + NG);
+                                            int mode, const YzRows* sh) {
+    const bool live = i < g.nx && j < g.ny;
+    const int ic = min(i, g.nx + 2), jc = min(j, g.ny + 2);
+    const long long p = gidx(g, ic + NG, jc + NG, k + NG);
     PointIn in;
     double kos[NFIELDS];
-    if (warp) {
+    if (mode != GATHER_LOCAL) {
         WarpRow wr;
         const int lane = threadIdx.x & 31;
-        warp_row_halo(g, a.src, i - lane, j, k, lane, wr);
-        gather(g, a.src, p, in, kos, &wr);
+        warp_row_halo(g, a.src, i - lane, jc, k, lane, wr);
+        gather(g, a.src, p, in, kos, &wr, mode == GATHER_BLOCK ? sh : nullptr, threadIdx.y);
     } else {
-        gather(g, a.src, p, in, kos, nullptr);
+        gather(g, a.src, p, in, kos, nullptr, nullptr, 0);
     }
     if (!live) return;
     double r[NFIELDS];
@@ -259,16 +302,19 @@ __device__ __forceinline__ void stage_point(const Geom& g, const Coeffs& c, cons
     for (int f = 0; f < NFIELDS; ++f) store_with_images(g, a.dst, f, i, j, k, out[f]);
 }
 
-// Launched with blocks of (32, by, 1) threads: every warp is one x-row segment. Planes k0, k0+1, ...
+// Launched with blocks of (32, 4, 1) threads (block gather mode). Planes k0, k0+1, ...
 // 3 resident blocks of 128 threads per SM (168 registers a thread): the extra warps hide more
 // FP64 dependency latency than the added spills cost (measured 2% faster than 2 blocks).
 template <int STAGE>
 __global__ void __launch_bounds__(128, 3) rk4_stage_kernel(Geom g, Coeffs c, StageArgs a) {
+    __shared__ YzRows sh;
     const int i = blockIdx.x * 32 + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int j = blockIdx.y * 4 + threadIdx.y;
     const int k = blockIdx.z + a.k0;
-    if (j >= g.ny || k >= g.nz) return;  // whole warps
-    stage_point<STAGE>(g, c, a, i, j, k, true);
+    if (k >= g.nz) return;  // whole block
+    yz_rows_fill(g, a.src, i, blockIdx.y * 4, threadIdx.y, k, threadIdx.x, sh);
+    __syncthreads();
+    stage_point<STAGE>(g, c, a, i, j, k, GATHER_BLOCK, &sh);
 }
 
 }  // namespace grf

@@ -4,21 +4,24 @@
 
 namespace grf {
 
-// Launched with blocks of (32, by, 1) threads: every warp is one x-row segment (see stage_point).
+// Launched with blocks of (32, 4, 1) threads (block gather mode, see stage_point).
 __global__ void __launch_bounds__(128) rhs_kernel(Geom g, Coeffs c, const double* __restrict__ s, double* __restrict__ rhs,
                                                   double ko, int* status) {
-    const int i = blockIdx.x * 32 + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    __shared__ YzRows sh;
+    const int lane = threadIdx.x;
+    const int i = blockIdx.x * 32 + lane;
+    const int j = blockIdx.y * 4 + threadIdx.y;
     const int k = blockIdx.z;
-    if (j >= g.ny || k >= g.nz) return;  // whole warps
-    const int lane = threadIdx.x & 31;
-    const long long p = gidx(g, min(i, g.nx + 2) + NG, j + NG, k + NG);
+    yz_rows_fill(g, s, i, blockIdx.y * 4, threadIdx.y, k, lane, sh);
+    __syncthreads();
+    const int jc = min(j, g.ny + 2);
+    const long long p = gidx(g, min(i, g.nx + 2) + NG, jc + NG, k + NG);
     PointIn in;
     double kos[NFIELDS];
     WarpRow wr;
-    warp_row_halo(g, s, i - lane, j, k, lane, wr);
-    gather(g, s, p, in, kos, &wr);
-    if (i >= g.nx) return;
+    warp_row_halo(g, s, i - lane, jc, k, lane, wr);
+    gather(g, s, p, in, kos, &wr, &sh, threadIdx.y);
+    if (i >= g.nx || j >= g.ny) return;
     double r[NFIELDS];
     bool ok = true;
     point_rhs<double>(c, in, r, nullptr, ok);
@@ -39,7 +42,7 @@ __global__ void __launch_bounds__(128) constraints_kernel(Geom g, Coeffs c, cons
         const long long p = gidx(g, i + NG, j + NG, k + NG);
         PointIn in;
         double kos[NFIELDS];
-        gather(g, s, p, in, kos, nullptr);
+        gather(g, s, p, in, kos, nullptr, nullptr, 0);
         double r[NFIELDS];
         PointExtra ex;
         bool ok = true;

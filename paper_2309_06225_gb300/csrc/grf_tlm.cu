@@ -29,7 +29,7 @@ struct TlmArgs {
 };
 
 __device__ __forceinline__ void gather_d3(const Geom& g, const double* const* s, long long p, PointInT<D3>& in) {
-    const double i12 = 1.0 / (12.0 * g.dx), i12s = 1.0 / (12.0 * g.dx * g.dx), i144 = 1.0 / (144.0 * g.dx * g.dx);
+    const double i12 = 1.0 / (12.0 * g.dx), i12s = 1.0 / (12.0 * g.dx * g.dx);
     const long long sx = 1, sy = g.pitch, sz = g.plane;
 #pragma unroll 1
     for (int f = 0; f < NFIELDS; ++f) {
@@ -43,14 +43,14 @@ __device__ __forceinline__ void gather_d3(const Geom& g, const double* const* s,
             if (first) {
                 d1[c][0] = fd1(u, p, sx, i12);
                 d1[c][1] = fd1(u, p, sy, i12);
-                d1[c][2] = fd1(u, p, sz, i12);
+                d1[c][2] = second ? fd1_rounded(u, p, sz, i12) : fd1(u, p, sz, i12);  // as in gather()
             }
             if (second) {
                 d2[c][0] = fd2(u, p, sx, v[c], i12s);
-                d2[c][1] = mixed_x_local(u, p, sy, i12);
-                d2[c][2] = mixed_x_local(u, p, sz, i12);
+                d2[c][1] = mixed_local(u, p, sx, sy, i12);
+                d2[c][2] = mixed_local(u, p, sx, sz, i12);
                 d2[c][3] = fd2(u, p, sy, v[c], i12s);
-                d2[c][4] = fdm(u, p, sy, sz, i144);
+                d2[c][4] = mixed_local(u, p, sy, sz, i12);
                 d2[c][5] = fd2(u, p, sz, v[c], i12s);
             }
         }

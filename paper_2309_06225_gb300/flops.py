@@ -6,11 +6,12 @@ update are fixed expressions in grf_kernels.cuh and are counted here from their 
   fd1  (u-2 - u+2) + 8 (u+1 - u-1), * 1/(12dx)            : 2 add, 1 fma, 1 mul
   fd2  16 (u+1 + u-1) - (u+2 + u-2) - 30 u0, * 1/(12dx^2)  : 2 fma, 1 mul (the two pair sums
        are shared with the KO sum of the same field)
-  fdm  (d_y d_z) 4 rows of fd1-type sums, combined the same way : 10 add, 5 fma, 1 mul
-  d_x d_y, d_x d_z: the x-stencil applied to the rounded first y / z derivatives of the four
-       x-neighbours (taken from the neighbouring lanes of the warp)   : 2 add, 1 fma, 1 mul
-  warp halo: 3 first derivatives per point (the y / z derivatives at the 4 points past the ends
-       of a 32-point row, for the 12 fields with second derivatives)   : 3 x (2 add, 1 fma, 1 mul)
+  d_x d_y, d_x d_z, d_y d_z: the first-derivative stencil applied to the rounded first
+       derivatives of the four neighbours (neighbouring lanes of the warp for x, the block's
+       shared rows for y)                                              : 2 add, 1 fma, 1 mul
+  halos: 3 first derivatives per point for the warp's row ends (the y / z derivatives at the 4
+       points past the ends of a 32-point row, 12 fields) and 12 per point for the block's 4 halo
+       rows of z-derivatives                                          : 15 x (2 add, 1 fma, 1 mul)
   ko6  3 x (3 pair sums + 3 accumulations) - 3, 3 fma; + ko*value into the RHS: 15 add, 4 fma
   stage update (per field): 1-2 fma (+1 add on the last stage)
 Counting convention: add/sub/mul = 1 flop, fma = 2, division = 1.
@@ -51,9 +52,8 @@ def stencil_ops():
     """(add, mul, fma) of the gather + KO + stage update per point and stage (mean over stages)."""
     fd1 = np.array([2, 1, 1])      # add, mul, fma
     fd2 = np.array([0, 1, 2])
-    fdm = np.array([10, 1, 5])
-    mixx = np.array([2, 1, 1])
-    gather = N_D1_FIELDS * 3 * fd1 + N_D2_FIELDS * (3 * fd2 + fdm + 2 * mixx) + 3 * fd1
+    mix = np.array([2, 1, 1])
+    gather = N_D1_FIELDS * 3 * fd1 + N_D2_FIELDS * (3 * fd2 + 3 * mix) + 15 * fd1
     ko = NFIELDS * np.array([15, 0, 4])
     update = NFIELDS * np.array([0.25, 0, 1.75])   # stages: 1, 2, 2, 2 fma (+1 add on the last)
     return gather + ko + update
