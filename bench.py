@@ -36,7 +36,7 @@ UNIT = "point-updates/s"
 BYTES_PER_POINT_UPDATE = 216 * (3 + 5 + 5 + 4)
 # dram__bytes_read.sum + dram__bytes_write.sum of one stage launch per interior point, from the
 # ncu capture of the current stage kernel (profiles/); None when the kernel changed since.
-TRAFFIC_BYTES_PER_POINT_STAGE = None  # re-captured after every kernel change (profiles/rk4_stage_kernel_bl_pair_96.md)
+TRAFFIC_BYTES_PER_POINT_STAGE = 12649  # mean of stage 0 and 1, 96^3 capture (profiles/rk4_stage_kernel_bl_pair_96.md)
 # FP64 (non-tensor) peak of GB300: 152 SMs x 2 FP64 FMA lanes/clk x 2 flop x ~2.06 GHz = 1.25 TFLOP/s
 FP64_PEAK_TFLOPS = 1.25
 
