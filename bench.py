@@ -41,6 +41,23 @@ TRAFFIC_BYTES_PER_POINT_STAGE = 12649  # mean of stage 0 and 1, 96^3 capture (pr
 FP64_PEAK_TFLOPS = 1.25
 
 
+def job_time_ms(ms_local, dist=None, device="cuda"):
+    """The job's timed-region duration: the max over ranks (the job ends with its slowest rank);
+    the rank's own value when it runs alone."""
+    if dist is None:
+        return ms_local
+    import torch
+    t = torch.tensor([ms_local], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, steps, ms, world):
+    """Units all ranks processed per second over the job's timed region (weak scaling: every rank
+    advances its own replica)."""
+    return world * units_per_rank * steps / (ms * 1e-3)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -415,11 +432,8 @@ def run_ours(args, rank, world, local_rank):
     ms = ev[0].elapsed_time(ev[-1])
     status = grf.grf_check_status()
     finite = grf.grf_check_finite(b, state)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * npts * args.steps / (ms * 1e-3)
+    ms = job_time_ms(ms, dist)
+    value = whole_job_rate(npts, args.steps, ms, world)
 
     e2e = None
     if not args.no_e2e:
@@ -437,16 +451,13 @@ def run_ours(args, rank, world, local_rank):
         e1.record(stream)
         barrier()
         ems = e0.elapsed_time(e1)
-        if dist is not None:
-            t = torch.tensor([ems], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
+        ems = job_time_ms(ems, dist)
         # outside the timed region: the host-to-host result equals the device-resident step
         state.copy_(host_in)
         grf.grf_rk4_step(b, p, state, dt, 1, ws=ws, stream=stream)
         nxg = box.nx + 6
         identical = bool(torch.equal(state.cpu()[..., :nxg], host_out[..., :nxg]))
-        e2e = {"value": world * npts * args.steps / (ems * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+        e2e = {"value": whole_job_rate(npts, args.steps, ems, world), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "ms_per_step": ems / args.steps,
                "bit_identical_to_device_step": identical,
                "path": "grf_rk4_step_host: pinned host -> device in z-slabs overlapped with stage 1, "
