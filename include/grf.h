@@ -105,15 +105,17 @@ int grf_rk4_step(const grf_box* box, const grf_params* params, double* state, do
  *   state:    device buffer of the same size; overwritten, and on completion it holds the
  *             same result as host_out.
  *   ws:       as for grf_rk4_step.
- * The interior is copied in slabs of z-planes (at most 16) on a copy stream owned by the
- * library; each slab's first-stage launch waits only for the planes its stencils read. The last
- * stage runs slab by slab and each finished slab is copied to host_out while the next is
- * computed. Results are bit-identical to: copy host_in to state, grf_rk4_step, copy state to
- * host_out. The stage kernels run on `stream`; the copies are ordered after the work already
+ * The state is copied in slabs of z-planes (at most 16) on a high-priority copy stream owned by
+ * the library; each slab's first-stage launch waits only for the planes its stencils read. The
+ * last stage runs slab by slab and each finished slab is copied to host_out while the next is
+ * computed. Page-locked buffers are copied by a small kernel (48 blocks) that reads or writes
+ * host memory directly, which keeps the full host-link rate while the stages run; pageable
+ * buffers are copied with cudaMemcpyAsync. Results are bit-identical to: copy host_in to state,
+ * grf_rk4_step, copy state to host_out. The stage kernels run on `stream`; the copies are ordered after the work already
  * queued on `stream`, and later work on `stream` is ordered after the last copy, so host_out is
  * complete once `stream` is synchronised. Host buffers should be page-locked (cudaHostAlloc,
- * cudaHostRegister, pinned torch tensors); pageable buffers give the same results, but the
- * driver then stages the copies and they no longer overlap the kernels.
+ * cudaHostRegister, pinned torch tensors); pageable buffers give the same results, but their
+ * copies are staged by the driver and overlap the kernels poorly.
  * The first call on a device creates that device's copy stream and events (no memory is
  * allocated); make it before any stream capture. Calls from several host threads are
  * serialised while they queue work. Errors: GRF_EINVAL (box, params, null pointers, nsteps < 0),

@@ -65,6 +65,44 @@ __global__ void slab_ghost_kernel(Geom g, double* __restrict__ s, double* __rest
     }
 }
 
+// Copy of up to 81 contiguous runs (offsets and lengths in doubles) between page-locked host
+// memory and device memory by the SMs (grf_rk4_step_host). On GB300 the copy engines lose most of
+// their host-link bandwidth after, and while, the FP64 kernels run; loads and stores issued by a
+// few dozen blocks keep the full link rate and take few block slots from the concurrent stages.
+constexpr int kMaxRuns = 81;
+struct CopyRuns {
+    int n;
+    long long dst[kMaxRuns], src[kMaxRuns], len[kMaxRuns];
+};
+
+template <bool V2>
+__global__ void __launch_bounds__(256) run_copy_kernel(const double* __restrict__ src, double* __restrict__ dst,
+                                                       CopyRuns r) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int q = 0; q < r.n; ++q) {
+        if (V2) {  // 16-byte units, 4 in flight per thread
+            const double2* s = reinterpret_cast<const double2*>(src + r.src[q]);
+            double2* d = reinterpret_cast<double2*>(dst + r.dst[q]);
+            const long long n = r.len[q] / 2;
+            long long i = t0;
+            for (; i + 3 * stride < n; i += 4 * stride) {
+                const double2 a = s[i], b = s[i + stride], c = s[i + 2 * stride], e = s[i + 3 * stride];
+                d[i] = a;
+                d[i + stride] = b;
+                d[i + 2 * stride] = c;
+                d[i + 3 * stride] = e;
+            }
+            for (; i < n; i += stride) d[i] = s[i];
+        } else {
+            const double* s = src + r.src[q];
+            double* d = dst + r.dst[q];
+            const long long n = r.len[q];
+            for (long long i = t0; i < n; i += stride) d[i] = s[i];
+        }
+    }
+}
+
 // Deterministic final reduction of the per-block partials (single block, fixed order).
 __global__ void norms_final_kernel(const double* __restrict__ part, long long nblocks, double npts, double* __restrict__ out8) {
     __shared__ double red[8][256];
@@ -211,7 +249,9 @@ int pipe_for_current_device(CopyPipe*& out) {
     if (dev < 0 || dev >= kMaxDevices) return GRF_EINVAL;
     CopyPipe& p = g_pipe[dev];
     if (!p.ready) {
-        e = cudaStreamCreateWithFlags(&p.copy, cudaStreamNonBlocking);
+        int least = 0, greatest = 0;
+        e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&p.copy, cudaStreamNonBlocking, greatest);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.start, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p.done, cudaEventDisableTiming);
         for (int s = 0; s < kMaxSlabs && e == cudaSuccess; ++s) {
@@ -228,40 +268,62 @@ int pipe_for_current_device(CopyPipe*& out) {
     return GRF_OK;
 }
 
-// Host -> device copy of ghosted z-planes [K0, K1) of all fields. For periodic boxes the host
-// source of a z-ghost plane is the interior plane it is an image of (the host ghosts are not read).
-cudaError_t copy_planes_h2d(const Geom& g, double* dev, const double* host, int K0, int K1, cudaStream_t st) {
-    const size_t pb = (size_t)g.plane * sizeof(double);
+// Ghosted z-planes [K0, K1) of all fields as contiguous runs (offsets and lengths in doubles).
+// The source of a run is the same planes, except for host -> device copies of periodic boxes,
+// where the source of a z-ghost plane is the interior plane it is an image of (the host's ghosts
+// are not read).
+void plane_runs(const Geom& g, int K0, int K1, bool image_source, CopyRuns& r) {
+    r.n = 0;
     int K = K0;
     while (K < K1) {
         int end, shift = 0;
         if (K < NG) {
             end = std::min(K1, NG);
-            shift = g.periodic ? g.nz : 0;
+            shift = (image_source && g.periodic) ? g.nz : 0;
         } else if (K < g.nz + NG) {
             end = std::min(K1, g.nz + NG);
         } else {
             end = K1;
-            shift = g.periodic ? -g.nz : 0;
+            shift = (image_source && g.periodic) ? -g.nz : 0;
         }
         for (int f = 0; f < NFIELDS; ++f) {
             const long long off = (long long)f * g.fstride;
-            cudaError_t e = cudaMemcpyAsync(dev + off + (long long)K * g.plane, host + off + (long long)(K + shift) * g.plane,
-                                            (size_t)(end - K) * pb, cudaMemcpyHostToDevice, st);
-            if (e != cudaSuccess) return e;
+            r.dst[r.n] = off + (long long)K * g.plane;
+            r.src[r.n] = off + (long long)(K + shift) * g.plane;
+            r.len[r.n] = (long long)(end - K) * g.plane;
+            ++r.n;
         }
         K = end;
     }
-    return cudaSuccess;
 }
 
-// Device -> host copy of ghosted z-planes [K0, K1) of all fields.
-cudaError_t copy_planes_d2h(const Geom& g, double* host, const double* dev, int K0, int K1, cudaStream_t st) {
-    if (K1 <= K0) return cudaSuccess;
-    const size_t pb = (size_t)g.plane * sizeof(double);
-    for (int f = 0; f < NFIELDS; ++f) {
-        const long long off = (long long)f * g.fstride + (long long)K0 * g.plane;
-        cudaError_t e = cudaMemcpyAsync(host + off, dev + off, (size_t)(K1 - K0) * pb, cudaMemcpyDeviceToHost, st);
+// The device address of a page-locked (cudaHostAlloc'ed or registered) host buffer, nullptr for
+// pageable memory, whose copies then go through cudaMemcpyAsync.
+const double* device_view(const double* host) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return (a.type == cudaMemoryTypeHost && a.devicePointer) ? (const double*)a.devicePointer : nullptr;
+}
+
+constexpr int kCopyBlocks = 48;  // enough blocks to reach the host-link rate, few enough to share the SMs
+
+// Copies the runs from src to dst on `st`: by the SMs when both sides are device-addressable
+// (dev_src / dev_dst non-null), else one cudaMemcpyAsync per run.
+cudaError_t copy_runs(const CopyRuns& r, const double* src, const double* dev_src, double* dst, double* dev_dst,
+                      cudaMemcpyKind kind, cudaStream_t st) {
+    if (r.n == 0) return cudaSuccess;
+    if (dev_src && dev_dst) {
+        bool v2 = (((uintptr_t)dev_src | (uintptr_t)dev_dst) & 15) == 0;
+        for (int q = 0; q < r.n; ++q) v2 = v2 && ((r.src[q] | r.dst[q] | r.len[q]) & 1) == 0;
+        if (v2) run_copy_kernel<true><<<kCopyBlocks, 256, 0, st>>>(dev_src, dev_dst, r);
+        else run_copy_kernel<false><<<kCopyBlocks, 256, 0, st>>>(dev_src, dev_dst, r);
+        return cudaGetLastError();
+    }
+    for (int q = 0; q < r.n; ++q) {
+        cudaError_t e = cudaMemcpyAsync(dst + r.dst[q], src + r.src[q], (size_t)r.len[q] * sizeof(double), kind, st);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -383,9 +445,15 @@ int grf_rk4_step_host(const grf_box* box, const grf_params* params, const double
     cudaError_t e = cudaEventRecord(P.start, st);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(P.copy, P.start, 0);
     if (e != cudaSuccess) return cuda_fail(e);
+    const double* dev_in = device_view(host_in);
+    double* dev_out = const_cast<double*>(device_view(host_out));
+    CopyRuns runs;
     if (nsteps == 0) {  // the state makes the round trip unchanged
-        e = cudaMemcpyAsync(state, host_in, sb, cudaMemcpyHostToDevice, P.copy);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, state, sb, cudaMemcpyDeviceToHost, P.copy);
+        runs.n = 1;
+        runs.dst[0] = runs.src[0] = 0;
+        runs.len[0] = (long long)(sb / sizeof(double));
+        e = copy_runs(runs, host_in, dev_in, state, state, cudaMemcpyHostToDevice, P.copy);
+        if (e == cudaSuccess) e = copy_runs(runs, state, state, host_out, dev_out, cudaMemcpyDeviceToHost, P.copy);
         if (e == cudaSuccess) e = cudaEventRecord(P.done, P.copy);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st, P.done, 0);
         return e == cudaSuccess ? GRF_OK : cuda_fail(e);
@@ -417,7 +485,8 @@ int grf_rk4_step_host(const grf_box* box, const grf_params* params, const double
     const dim3 gblk(32, 8, 1), ggrd((g.NX + 31) / 32, (g.NY + 7) / 8, NFIELDS);
 
     for (int s = 0; s < S && e == cudaSuccess; ++s) {
-        e = copy_planes_h2d(g, state, host_in, clo(s), chi(s), P.copy);
+        plane_runs(g, clo(s), chi(s), true, runs);
+        e = copy_runs(runs, host_in, dev_in, state, state, cudaMemcpyHostToDevice, P.copy);
         if (e == cudaSuccess) e = cudaEventRecord(P.h2d[s], P.copy);
     }
     if (e != cudaSuccess) return cuda_fail(e);
@@ -454,7 +523,8 @@ int grf_rk4_step_host(const grf_box* box, const grf_params* params, const double
                 launch_stage(3, slab_grid(s), kBlock, st, g, c, a);
                 e = cudaEventRecord(P.s4[s], st);
                 if (e == cudaSuccess) e = cudaStreamWaitEvent(P.copy, P.s4[s], 0);
-                if (e == cudaSuccess) e = copy_planes_d2h(g, host_out, state, lo(s) + NG, hi(s) + NG, P.copy);
+                plane_runs(g, lo(s) + NG, hi(s) + NG, false, runs);
+                if (e == cudaSuccess) e = copy_runs(runs, state, state, host_out, dev_out, cudaMemcpyDeviceToHost, P.copy);
                 if (e != cudaSuccess) return cuda_fail(e);
             }
         }
@@ -462,8 +532,10 @@ int grf_rk4_step_host(const grf_box* box, const grf_params* params, const double
         if (r) return r;
     }
     // z-ghost planes (periodic images written by the first and last slabs; frozen: as given)
-    e = copy_planes_d2h(g, host_out, state, 0, NG, P.copy);
-    if (e == cudaSuccess) e = copy_planes_d2h(g, host_out, state, g.nz + NG, g.NZ, P.copy);
+    plane_runs(g, 0, NG, false, runs);
+    e = copy_runs(runs, state, state, host_out, dev_out, cudaMemcpyDeviceToHost, P.copy);
+    plane_runs(g, g.nz + NG, g.NZ, false, runs);
+    if (e == cudaSuccess) e = copy_runs(runs, state, state, host_out, dev_out, cudaMemcpyDeviceToHost, P.copy);
     if (e == cudaSuccess) e = cudaEventRecord(P.done, P.copy);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st, P.done, 0);
     return e == cudaSuccess ? GRF_OK : cuda_fail(e);

@@ -144,3 +144,18 @@ def test_host_step_sixteen_slabs_128(g):
     g.grf_rk4_step_host(b, p, hin, hout, g.alloc_state(b), dt, 1)
     torch.cuda.synchronize()
     assert same_state(box, hout, ref)
+
+
+def test_host_step_pinned_input_pageable_output(g):
+    """Page-locked host_in (copied in by the SMs) with a pageable host_out (copied out by
+    cudaMemcpyAsync): both copy paths in one call."""
+    import torch
+    box = gi.Box(18, 10, 23, 0.3, -2.6, -1.4, -3.3)
+    b = g.box_like(box)
+    params = g.params_like(gi.Params(lam=0.15, g2=0.05, beta_kind=gi.BETA_QUADRATIC))
+    hin = host_state(g, box, initial(box, 11))
+    hout = np.full(tuple(hin.shape), np.nan)
+    ref = reference(g, b, params, hin, 0.25 * box.dx, 2)
+    g.grf_rk4_step_host(b, params, hin, hout, g.alloc_state(b), 0.25 * box.dx, 2)
+    torch.cuda.synchronize()
+    assert np.array_equal(hout[..., :box.nx + 6], ref.numpy()[..., :box.nx + 6])
