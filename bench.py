@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="bl_pair_256", choices=["bl_pair_256", "bl_pair_128", "bl_pair_96", "bl_pair_64", "amr_boxes_96", "coupling_sweep_32", "sphere_signal_96"])
+    ap.add_argument("--workload", default="bl_pair_256", choices=["bl_pair_256", "bl_pair_128", "bl_pair_96", "bl_pair_64", "amr_boxes_96", "coupling_sweep_32", "sphere_signal_96", "calls_256"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-peak", action="store_true", help="skip the FP64 microbenchmark")
@@ -92,6 +92,86 @@ def batched_workload(name):
         pidx = list(range(len(boxes)))
     dts = [0.25 * b.dx for b in boxes]
     return boxes, params, pidx, dts
+
+
+def run_calls(args, rank, world, local_rank):
+    """The standalone entry points on the 256^3 Brill-Lindquist state: one RHS evaluation with
+    dissipation (grf_rhs), the dissipation alone (grf_ko_dissipation, added into an RHS array) and
+    the constraints (grf_constraints, the 4 fields without the norms). The timed RK4 step fuses the
+    first two; the constraints are a diagnostic taken between steps."""
+    import torch
+    import paper_2309_06225_gb300 as grf
+    from paper_2309_06225_gb300 import flops as grf_flops
+    if rank != 0:
+        return
+    cfg = workload("bl_pair_256")
+    box, params = cfg["box"], cfg["params"]
+    b = grf.box_like(box)
+    p = grf.params_like(params)
+    state = grf.to_device(cfg["make_state"](), b)
+    rhs = grf.alloc_state(b)
+    out4 = grf.alloc_state(b, 4)
+    npts = box.nx * box.ny * box.nz
+    stream = torch.cuda.current_stream()
+    calls = {
+        "grf_rhs": lambda: grf.grf_rhs(b, p, state, rhs),
+        "grf_ko_dissipation": lambda: grf.grf_ko_dissipation(b, params.sigma_ko, state, rhs),
+        "grf_constraints": lambda: grf.grf_constraints(b, p, state, out4, norms=False),
+    }
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    hbm_src = "of measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "of fallback 6.8 TB/s"
+    flop_rhs = grf_flops.flops_per_point_rhs(p)
+    clocks = ClockSampler(gpu_selector(local_rank))
+    clocks.start()
+    time.sleep(0.3)
+    out = {}
+    for name, fn in calls.items():
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        rec = {"ms_per_call": ms, "points_per_s": npts / (ms * 1e-3)}
+        if name == "grf_ko_dissipation":
+            # FP64-bound even alone: per field 9 pair sums + 6 accumulations + 3 fma + the fma into
+            # the RHS (23 flops) against 24 bytes (state read once, RHS read and written)
+            flop_ko = 27 * 23
+            nbytes = 27 * 8 * 3
+            tf = flop_ko * npts / (ms * 1e-3) / 1e12
+            rec["roofline"] = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                               "frac": tf / FP64_PEAK_TFLOPS, "flop_per_point": flop_ko,
+                               "peak_source": "GB300 FP64 non-tensor, 1.25 TFLOP/s (nominal)",
+                               "hbm_frac": nbytes * npts / (ms * 1e-3) / 1e9 / hbm, "hbm_peak_source": hbm_src}
+        elif name == "grf_rhs":
+            tf = flop_rhs * npts / (ms * 1e-3) / 1e12
+            rec["roofline"] = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                               "frac": tf / FP64_PEAK_TFLOPS, "flop_per_point": flop_rhs,
+                               "peak_source": "GB300 FP64 non-tensor, 1.25 TFLOP/s (nominal)"}
+        else:  # the constraints use a subset of the RHS (the compiler drops the CCZ4 update and the solve)
+            rec["roofline"] = None
+            rec["note"] = "FP64-bound like grf_rhs; its flop count is a subset of the RHS and is not counted"
+        out[name] = rec
+    clk = clocks.stop()
+    status = grf.grf_check_status()
+    line = {"metric": "FP64 grid-point RHS evaluations/s (grf_rhs, standalone)", "value": out["grf_rhs"]["points_per_s"],
+            "unit": "points/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": out["grf_rhs"]["ms_per_call"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "calls_256", "grid": [box.nx, box.ny, box.nz],
+                       "l2": "inputs larger than L2 (no flush needed)"},
+            "gpu_launches": 4 * args.steps, "calls": out, "clocks": clk, "status": {"solve": status},
+            "roofline": out["grf_rhs"]["roofline"], "e2e": None, "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
 
 
 def run_tangent(args, rank, world, local_rank):
@@ -503,6 +583,9 @@ def main():
         return
     if args.workload == "sphere_signal_96":
         run_tangent(args, rank, world, local_rank)
+        return
+    if args.workload == "calls_256":
+        run_calls(args, rank, world, local_rank)
         return
     if args.workload in ("amr_boxes_96", "coupling_sweep_32"):
         run_batched(args, rank, world, local_rank)

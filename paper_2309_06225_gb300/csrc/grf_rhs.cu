@@ -34,15 +34,25 @@ __global__ void __launch_bounds__(128) rhs_kernel(Geom g, Coeffs c, const double
 // part[block][8] = {sum H^2, max|H|, sum M1^2, max|M1|, ...}
 __global__ void __launch_bounds__(128) constraints_kernel(Geom g, Coeffs c, const double* __restrict__ s,
                                                           double* __restrict__ out4, double* __restrict__ part) {
+    // blocks of (32, 4, 1): block gather mode, as rhs_kernel; every thread stays to the reduction
     __shared__ double red[8][128];
-    int i, j, k;
-    const bool live = interior_thread(g, i, j, k);
+    __shared__ YzRows sh;
+    const int lane = threadIdx.x;
+    const int i = blockIdx.x * 32 + lane;
+    const int j = blockIdx.y * 4 + threadIdx.y;
+    const int k = blockIdx.z;
+    const bool live = i < g.nx && j < g.ny;
+    yz_rows_fill(g, s, i, blockIdx.y * 4, threadIdx.y, k, lane, sh);
+    __syncthreads();
+    const int jc = min(j, g.ny + 2);
+    const long long p = gidx(g, min(i, g.nx + 2) + NG, jc + NG, k + NG);
+    PointIn in;
+    double kos[NFIELDS];
+    WarpRow wr;
+    warp_row_halo(g, s, i - lane, jc, k, lane, wr);
+    gather(g, s, p, in, kos, &wr, &sh, threadIdx.y);
     double vals[4] = {0.0, 0.0, 0.0, 0.0};
     if (live) {
-        const long long p = gidx(g, i + NG, j + NG, k + NG);
-        PointIn in;
-        double kos[NFIELDS];
-        gather(g, s, p, in, kos, nullptr, nullptr, 0);
         double r[NFIELDS];
         PointExtra ex;
         bool ok = true;

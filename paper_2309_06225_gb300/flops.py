@@ -59,6 +59,15 @@ def stencil_ops():
     return gather + ko + update
 
 
+def flops_per_point_rhs(params):
+    """Algorithmic FP64 flops per interior point of one RHS evaluation with dissipation
+    (grf_rhs; the constraints kernel does the same work): the stage without its update."""
+    ops = point_ops(params).sum(axis=0)
+    add, mul, fma, div = ops[0], ops[1], ops[2], ops[3]
+    s = stencil_ops() - NFIELDS * np.array([0.25, 0, 1.75])
+    return float(add + mul + 2 * fma + div + s[0] + s[1] + 2 * s[2])
+
+
 def flops_per_point_stage(params):
     """Algorithmic FP64 flops per interior point per RK4 stage kernel."""
     ops = point_ops(params).sum(axis=0)
