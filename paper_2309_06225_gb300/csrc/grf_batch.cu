@@ -71,6 +71,14 @@ __device__ __forceinline__ void batch_tile(const BoxDesc* __restrict__ boxes, co
     stage_point<STAGE>(d.g, d.c, a, i, j, k, mode, &sh);
 }
 
+// Out-of-line copy of batch_tile for the persistent kernel: with the four stages inlined into one
+// kernel, ptxas spilled 52 KB per thread; called, each stage is allocated on its own (13 KB).
+template <int STAGE>
+__device__ __noinline__ void batch_tile_call(const BoxDesc* __restrict__ boxes, const TileDesc& td, int* status,
+                                             YzRows& sh) {
+    batch_tile<STAGE>(boxes, td, status, sh);
+}
+
 template <int STAGE>
 __global__ void __launch_bounds__(128, 3) batch_stage_kernel(const BoxDesc* __restrict__ boxes,
                                                           const TileDesc* __restrict__ tiles, int ntiles, int* status) {
@@ -127,10 +135,10 @@ __global__ void __launch_bounds__(128, 3) batch_persistent_kernel(const BoxDesc*
             for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
                 const TileDesc td = tiles[t];
                 switch (s) {
-                    case 0: batch_tile<0>(boxes, td, status, sh); break;
-                    case 1: batch_tile<1>(boxes, td, status, sh); break;
-                    case 2: batch_tile<2>(boxes, td, status, sh); break;
-                    default: batch_tile<3>(boxes, td, status, sh); break;
+                    case 0: batch_tile_call<0>(boxes, td, status, sh); break;
+                    case 1: batch_tile_call<1>(boxes, td, status, sh); break;
+                    case 2: batch_tile_call<2>(boxes, td, status, sh); break;
+                    default: batch_tile_call<3>(boxes, td, status, sh); break;
                 }
             }
             if (!grid_barrier(bar, gridDim.x, timeout, status)) return;
