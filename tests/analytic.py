@@ -8,7 +8,7 @@ import numpy as np
 
 try:
     import sympy as sp
-except ImportError:  # pragma: no cover - the GPU machine has no sympy; these tests are CPU-only
+except ImportError:  # pragma: no cover - sympy is optional; these tests are CPU-only
     sp = None
 
 SYM_PAIRS = [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]
