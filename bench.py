@@ -37,8 +37,19 @@ BYTES_PER_POINT_UPDATE = 216 * (3 + 5 + 5 + 4)
 # dram__bytes_read.sum + dram__bytes_write.sum of one stage launch per interior point, from the
 # ncu capture of the current stage kernel (profiles/); None when the kernel changed since.
 TRAFFIC_BYTES_PER_POINT_STAGE = 12649  # mean of stage 0 and 1, 96^3 capture (profiles/rk4_stage_kernel_bl_pair_96.md)
+# FP64 thread instructions (dadd + dmul + dfma) per interior point and stage, same capture; the
+# pipe issues 2 per SM per clock (152 SMs x 2 x 2.06 GHz = 6.26e11 / s, half the flop peak).
+FP64_INSTR_PER_POINT_STAGE = 4161
 # FP64 (non-tensor) peak of GB300: 152 SMs x 2 FP64 FMA lanes/clk x 2 flop x ~2.06 GHz = 1.25 TFLOP/s
 FP64_PEAK_TFLOPS = 1.25
+
+
+def measured_hbm_gbs():
+    """(GB/s, source) of the HBM copy peak: MEASURED_PEAKS.json when present, else the fallback."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "of measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "of fallback"
 
 
 def job_time_ms(ms_local, dist=None, device="cuda"):
@@ -64,7 +75,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="bl_pair_256", choices=["bl_pair_256", "bl_pair_128", "bl_pair_96", "bl_pair_64", "amr_boxes_96", "coupling_sweep_32", "sphere_signal_96", "calls_256"])
+    ap.add_argument("--workload", default="bl_pair_256", choices=["bl_pair_256", "bl_pair_128", "bl_pair_96", "bl_pair_64", "amr_boxes_96", "coupling_sweep_32", "sphere_signal_96", "calls_256", "calls_96"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-peak", action="store_true", help="skip the FP64 microbenchmark")
@@ -95,7 +106,8 @@ def batched_workload(name):
 
 
 def run_calls(args, rank, world, local_rank):
-    """The standalone entry points on the 256^3 Brill-Lindquist state: one RHS evaluation with
+    """The standalone entry points on the 256^3 (calls_256) or 96^3 (calls_96, small enough for a
+    full profiler capture) Brill-Lindquist state: one RHS evaluation with
     dissipation (grf_rhs), the dissipation alone (grf_ko_dissipation, added into an RHS array) and
     the constraints (grf_constraints, the 4 fields without the norms). The timed RK4 step fuses the
     first two; the constraints are a diagnostic taken between steps."""
@@ -104,7 +116,7 @@ def run_calls(args, rank, world, local_rank):
     from paper_2309_06225_gb300 import flops as grf_flops
     if rank != 0:
         return
-    cfg = workload("bl_pair_256")
+    cfg = workload("bl_pair_" + args.workload.rsplit("_", 1)[1])
     box, params = cfg["box"], cfg["params"]
     b = grf.box_like(box)
     p = grf.params_like(params)
@@ -118,13 +130,7 @@ def run_calls(args, rank, world, local_rank):
         "grf_ko_dissipation": lambda: grf.grf_ko_dissipation(b, params.sigma_ko, state, rhs),
         "grf_constraints": lambda: grf.grf_constraints(b, p, state, out4, norms=False),
     }
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    hbm_src = "of measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "of fallback 6.8 TB/s"
+    hbm, hbm_src = measured_hbm_gbs()
     flop_rhs = grf_flops.flops_per_point_rhs(p)
     clocks = ClockSampler(gpu_selector(local_rank))
     clocks.start()
@@ -167,7 +173,7 @@ def run_calls(args, rank, world, local_rank):
             "unit": "points/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": out["grf_rhs"]["ms_per_call"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "calls_256", "grid": [box.nx, box.ny, box.nz],
+            "config": {"workload": args.workload, "grid": [box.nx, box.ny, box.nz],
                        "l2": "inputs larger than L2 (no flush needed)"},
             "gpu_launches": 4 * args.steps, "calls": out, "clocks": clk, "status": {"solve": status},
             "roofline": out["grf_rhs"]["roofline"], "e2e": None, "cpu_baseline": None}
@@ -557,7 +563,12 @@ def run_ours(args, rank, world, local_rank):
             "peak_dfma_microbenchmark": peak, "flop_per_point_stage": flop_ps,
             "flop_convention": "counted from the kernel source: add/sub/mul 1, fma 2, div 1",
             "traffic": TRAFFIC_BYTES_PER_POINT_STAGE * npts if TRAFFIC_BYTES_PER_POINT_STAGE else None}
-    roof["hbm_frac_of_measured"] = BYTES_PER_POINT_UPDATE * value / 6771.1e9
+    hbm_gbs, hbm_src = measured_hbm_gbs()
+    roof["hbm_frac"] = BYTES_PER_POINT_UPDATE * value / (hbm_gbs * 1e9)
+    roof["hbm_peak_source"] = f"{hbm_src} {hbm_gbs:.1f} GB/s"
+    if FP64_INSTR_PER_POINT_STAGE:
+        # how full the FP64 pipe is: adds and multiplies take an issue slot but count one flop
+        roof["fp64_issue_frac"] = FP64_INSTR_PER_POINT_STAGE * npts / (launch_ms * 1e-3) / (FP64_PEAK_TFLOPS * 1e12 / 2)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -584,7 +595,7 @@ def main():
     if args.workload == "sphere_signal_96":
         run_tangent(args, rank, world, local_rank)
         return
-    if args.workload == "calls_256":
+    if args.workload in ("calls_256", "calls_96"):
         run_calls(args, rank, world, local_rank)
         return
     if args.workload in ("amr_boxes_96", "coupling_sweep_32"):
