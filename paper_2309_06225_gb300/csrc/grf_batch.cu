@@ -35,19 +35,25 @@ struct BoxDesc {
 
 struct TileDesc {
     int box, i0, j0, k0;
+    int w;  // x-points per row: blockDim.x (one row per warp), or 8 / 16 (a folded 32-wide tile:
+            // each warp covers 32 / w rows of a narrow box)
 };
 
 template <int STAGE>
 __device__ __forceinline__ void batch_tile(const BoxDesc* __restrict__ boxes, const TileDesc& td, int* status,
                                            YzRows& sh) {
     const BoxDesc& d = boxes[td.box];
-    const int i = td.i0 + threadIdx.x, j = td.j0 + threadIdx.y, k = td.k0 + threadIdx.z;
+    const bool folded = td.w != (int)blockDim.x;
+    const int i = td.i0 + (folded ? (int)threadIdx.x % td.w : (int)threadIdx.x);
+    const int j = td.j0 + (folded ? (int)threadIdx.y * ((int)blockDim.x / td.w) + (int)threadIdx.x / td.w : (int)threadIdx.y);
+    const int k = td.k0 + threadIdx.z;
     // Tile shape -> gather mode (all modes give the same bits):
     //   32 x 4 x 1: block mode, d_y d_z through the shared rows; every thread stays to the barrier.
     //   width a multiple of 32: warp mode; whole warps stay for the shuffles.
-    //   otherwise: per-thread mode.
-    const int mode = (blockDim.x == 32 && blockDim.y == 4 && blockDim.z == 1) ? GATHER_BLOCK
-                     : ((blockDim.x & 31) == 0 ? GATHER_WARP : GATHER_LOCAL);
+    //   folded tiles and other shapes: per-thread mode.
+    const int mode = folded ? GATHER_LOCAL
+                     : ((blockDim.x == 32 && blockDim.y == 4 && blockDim.z == 1) ? GATHER_BLOCK
+                        : ((blockDim.x & 31) == 0 ? GATHER_WARP : GATHER_LOCAL));
     StageArgs a;
     a.un = d.un;
     a.acc = d.acc;
@@ -204,9 +210,25 @@ Geom geom_of(const grf_box* b) {
 
 size_t state_bytes_of(const Geom& g) { return sizeof(double) * (size_t)NFIELDS * (size_t)g.fstride; }
 
+// x-points per tile row for a box. With 32 x 4 x 1 tiles, a box whose x-extent is not a
+// multiple of 32 would leave lanes idle through the whole stage; its tiles are folded instead,
+// each warp covering 32 / w rows of w = 8 or 16 points, whichever fills the most lanes (the
+// folded tiles take the per-thread gather).
+int row_width(const grf_box* b, const grf_batch_config* c) {
+    if (!(c->tile_x == 32 && c->tile_y == 4 && c->tile_z == 1) || b->nx % 32 == 0) return c->tile_x;
+    int best = 32;
+    double best_eff = (double)b->nx / (32.0 * ((b->nx + 31) / 32));
+    for (int w : {16, 8}) {
+        const double eff = (double)b->nx / ((double)w * ((b->nx + w - 1) / w));
+        if (eff > best_eff + 1e-12) { best = w; best_eff = eff; }
+    }
+    return best;
+}
+
 long long tiles_of(const grf_box* b, const grf_batch_config* c) {
-    return (long long)((b->nx + c->tile_x - 1) / c->tile_x) * ((b->ny + c->tile_y - 1) / c->tile_y) *
-           ((b->nz + c->tile_z - 1) / c->tile_z);
+    const int w = row_width(b, c);
+    const int rows = c->tile_y * (c->tile_x / w);
+    return (long long)((b->nx + w - 1) / w) * ((b->ny + rows - 1) / rows) * ((b->nz + c->tile_z - 1) / c->tile_z);
 }
 
 struct Layout {
@@ -360,9 +382,11 @@ int grf_batched_rk4(const grf_batch_item* items, int nitems, const grf_params* p
         d.min_chi = p->min_chi;
         d.min_lapse = p->min_lapse;
         d.enforce = p->enforce_algebraic;
+        const int w = row_width(&it.box, cfg);
+        const int rows = cfg->tile_y * (cfg->tile_x / w);
         for (int k = 0; k < it.box.nz; k += cfg->tile_z)
-            for (int j = 0; j < it.box.ny; j += cfg->tile_y)
-                for (int i = 0; i < it.box.nx; i += cfg->tile_x) ht.push_back(TileDesc{b, i, j, k});
+            for (int j = 0; j < it.box.ny; j += rows)
+                for (int i = 0; i < it.box.nx; i += w) ht.push_back(TileDesc{b, i, j, k, w});
     }
     cudaError_t e = cudaMemcpyAsync(dboxes, hb.data(), sizeof(BoxDesc) * nitems, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
