@@ -160,3 +160,24 @@ def test_autograd_function(g, tlm):
     L = diff.SphereSignal.apply(theta, b, g.params_like(params_of(THETA)), s0, ds, 0.25 * BOX.dx, NSTEPS, diff.sphere(R))
     (gr,) = torch.autograd.grad(3.0 * L, theta)
     np.testing.assert_allclose(gr.numpy(), 3.0 * tlm[1], rtol=1e-12)
+
+
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_tlm_gradient_matches_richardson_differences(g, tlm, k):
+    """Forward mode differentiates the discrete evolution exactly, so the gradient must agree with
+    Richardson-extrapolated central differences of the GPU evolution, (4 D(h/2) - D(h)) / 3 with
+    truncation error O(h^4), down to the rounding floor of the difference quotient:
+    ~eps |L| / (h |dL/dtheta|), or 1e-10 relative where that is smaller (lambda and A reach
+    1e-12; dL/dg2 is small, so its quotient carries ~1e-7 of rounding)."""
+    L, grad = tlm
+    h = 1e-3 * max(abs(THETA[k]), 1e-2)
+
+    def central(hh):
+        tp = list(THETA); tm = list(THETA)
+        tp[k] += hh
+        tm[k] -= hh
+        return (gpu_signal(g, tp) - gpu_signal(g, tm)) / (2 * hh)
+
+    rich = (4.0 * central(h / 2) - central(h)) / 3.0
+    floor = 20 * np.finfo(float).eps * abs(L) / (h * abs(grad[k]))
+    assert abs(rich / grad[k] - 1.0) <= max(1e-10, floor), (k, grad[k], rich, floor)
