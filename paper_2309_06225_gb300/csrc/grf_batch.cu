@@ -64,6 +64,7 @@ __device__ __forceinline__ void batch_tile(const BoxDesc* __restrict__ boxes, co
     a.enforce = d.enforce;
     a.status = status;
     a.k0 = 0;
+    a.fold = 32;
     a.src = (STAGE == 0) ? d.un : (STAGE == 1 ? d.A : (STAGE == 2 ? d.B : d.A));
     a.dst = (STAGE == 0) ? d.A : (STAGE == 1 ? d.B : (STAGE == 2 ? d.A : d.un));
     if (mode == GATHER_BLOCK) {

@@ -249,6 +249,7 @@ struct StageArgs {
     int enforce;
     int* status;
     int k0;              // first interior z-plane of the launch (grid.z covers planes k0, k0+1, ...)
+    int fold;            // x-points per warp row: 32, or 16 / 8 / 4 for rk4_stage_fold_kernel
 };
 
 // How a stage's gather takes its mixed derivatives (all modes give the same bits).
@@ -315,6 +316,19 @@ __global__ void __launch_bounds__(128, 3) rk4_stage_kernel(Geom g, Coeffs c, Sta
     yz_rows_fill(g, a.src, i, blockIdx.y * 4, threadIdx.y, k, threadIdx.x, sh);
     __syncthreads();
     stage_point<STAGE>(g, c, a, i, j, k, GATHER_BLOCK, &sh);
+}
+
+// Folded variant for boxes whose x-extent is not a multiple of 32, chosen by the host when it
+// fills more lanes: blocks of (32, 4, 1), each warp covering 32 / w rows of w = a.fold x-points,
+// with the per-thread gather. It gives the same bits as rk4_stage_kernel.
+template <int STAGE>
+__global__ void __launch_bounds__(128, 3) rk4_stage_fold_kernel(Geom g, Coeffs c, StageArgs a) {
+    const int w = a.fold, per = 32 / a.fold;
+    const int i = blockIdx.x * w + (int)threadIdx.x % w;
+    const int j = blockIdx.y * (4 * per) + (int)threadIdx.y * per + (int)threadIdx.x / w;
+    const int k = blockIdx.z + a.k0;
+    if (i >= g.nx || j >= g.ny || k >= g.nz) return;
+    stage_point<STAGE>(g, c, a, i, j, k, GATHER_LOCAL, nullptr);
 }
 
 }  // namespace grf

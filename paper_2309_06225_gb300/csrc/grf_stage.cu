@@ -4,6 +4,10 @@
 
 namespace grf {
 void launch_stage(int stage, dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c, const StageArgs& a) {
+    if (a.fold != 32) {
+        launch_stage_folded(stage, grid, block, st, g, c, a);
+        return;
+    }
     switch (stage) {
         case 0: rk4_stage_kernel<0><<<grid, block, 0, st>>>(g, c, a); break;
         case 1: rk4_stage_kernel<1><<<grid, block, 0, st>>>(g, c, a); break;

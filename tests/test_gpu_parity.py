@@ -137,6 +137,33 @@ def test_rk4_parity_ragged_perturbed(g, orc, bc):
     assert np.max(errs) < 1e-10, describe(errs)
 
 
+@pytest.mark.parametrize("bc", [gi.BC_PERIODIC, gi.BC_FROZEN])
+def test_rk4_parity_folded_launch(g, orc, bc):
+    """48 x 40 x 36: the x-extent is not a multiple of 32 and the grid is large enough, so the
+    stage runs as the folded kernel (each warp covers 2 rows of 16 points, per-thread gather).
+    One RK4 step <= 1e-11 per field against the oracle; the host-to-host step on the same box
+    gives the same bits."""
+    import torch
+    box = gi.Box(48, 40, 36, 0.25, -5.8, -4.9, -4.4, bc=bc)
+    params = P(lam=0.2, g2=0.1, beta_kind=1)
+    s0 = make_state(box, "perturbed", 17)
+    assert np.all(np.isfinite(s0))
+    cpu = s0.copy()
+    if bc == gi.BC_PERIODIC:
+        orc.fill_ghosts(box, cpu)
+    orc.rk4(box, params, cpu, 0.25 * box.dx, 1)
+    gpu = gpu_rk4(g, box, params, s0, 0.25 * box.dx, 1)
+    errs = field_errors(gpu, cpu, box)
+    assert np.max(errs) < 1e-11, describe(errs)
+    b = g.box_like(box)
+    hin = torch.zeros(g.state_shape(b), dtype=torch.float64, pin_memory=True)
+    hin[..., :box.nx + 6] = torch.from_numpy(np.ascontiguousarray(s0))
+    hout = torch.empty_like(hin).pin_memory()
+    g.grf_rk4_step_host(b, g.params_like(params), hin, hout, g.alloc_state(b), 0.25 * box.dx, 1)
+    torch.cuda.synchronize()
+    assert np.array_equal(hout.numpy()[..., :box.nx + 6], gpu)
+
+
 def test_constraints_parity(g, orc):
     box = gi.Box(13, 12, 10, 0.3, -1.9, -1.7, -1.4)
     params = P(lam=0.3, g2=0.2)
