@@ -91,6 +91,7 @@ class Params:
     min_chi: float = 1e-4
     min_lapse: float = 1e-4
     enforce_algebraic: int = 1
+    decoupled: int = 0          # 1: 4dST without backreaction (metric evolves by vacuum CCZ4)
 
     def to_dict(self):
         return asdict(self)

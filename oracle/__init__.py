@@ -20,7 +20,7 @@ class OrcParams(C.Structure):
                 ("a0", C.c_double), ("b0", C.c_double),
                 ("lam", C.c_double), ("g2", C.c_double),
                 ("sigma_ko", C.c_double), ("min_chi", C.c_double), ("min_lapse", C.c_double),
-                ("beta_kind", C.c_int), ("enforce_algebraic", C.c_int)]
+                ("beta_kind", C.c_int), ("enforce_algebraic", C.c_int), ("decoupled", C.c_int)]
 
 
 class OrcBox(C.Structure):
@@ -65,7 +65,8 @@ def _ptr(a):
 def params(p) -> OrcParams:
     """From a grf_inputs.Params (or anything with the same attributes)."""
     return OrcParams(p.kappa1, p.kappa2, p.kappa3, p.shift_F, p.eta, p.a0, p.b0, p.lam, p.g2,
-                     p.sigma_ko, p.min_chi, p.min_lapse, int(p.beta_kind), int(p.enforce_algebraic))
+                     p.sigma_ko, p.min_chi, p.min_lapse, int(p.beta_kind), int(p.enforce_algebraic),
+                     int(getattr(p, "decoupled", 0)))
 
 
 def box(b) -> OrcBox:

@@ -23,6 +23,10 @@
 //     equation) and nabla_n nabla_n phi. The residual of the equations is affine in v, so
 //     it is evaluated at v = 0 and at the 7 scaled unit vectors and the 7x7 system is
 //     solved by Gaussian elimination with FULL pivoting in long double.
+//   * decoupled mode (params.decoupled = 1; "Key features": 4dST without backreaction onto the
+//     metric, for comparison with decoupling-limit codes): T_ab is dropped from the metric
+//     equations, which become vacuum CCZ4 in the same gauge, while the scalar evolves with the
+//     full scalar equation on that metric
 //   * Kreiss-Oliger dissipation sigma/(64 dx) sum_d Delta^6_d u on all fields
 //   * classical RK4 with post-stage algebraic enforcement (trace-free A, chi and lapse floors)
 //
@@ -50,6 +54,7 @@ typedef struct {
     double sigma_ko, min_chi, min_lapse;
     int beta_kind;          // 0: beta = lam*phi ; 1: beta = lam*phi^2/2
     int enforce_algebraic;  // 1: trace-free A, chi/lapse floors after every RK stage
+    int decoupled;          // 1: no backreaction: the metric evolves by vacuum CCZ4, the scalar on it
 } orc_params;
 
 typedef struct {
@@ -368,10 +373,14 @@ void sources(const orc_params& P, const Phys& p, const Geo& G, const double u[3]
             for (int c = 0; c < 4; ++c) for (int d = 0; d < 4; ++d) x -= 4.0 * Pd[a][c][b][d] * Phiu[c][d];
             T8[a][b] = x;
         }
-    s.rho8 = T8[0][0];
+    // Without backreaction ("Key features": 4dST without backreaction onto the metric) the
+    // scalar's stress-energy is left out of the metric equations; the scalar equation below still
+    // uses the full 4D curvature of the evolving metric.
+    const double keep = P.decoupled ? 0.0 : 1.0;
+    s.rho8 = keep * T8[0][0];
     for (int i = 0; i < 3; ++i) {
-        s.S8[i] = -T8[i + 1][0];
-        for (int j = 0; j < 3; ++j) s.Sij8[i][j] = T8[i + 1][j + 1];
+        s.S8[i] = -keep * T8[i + 1][0];
+        for (int j = 0; j < 3; ++j) s.Sij8[i][j] = keep * T8[i + 1][j + 1];
     }
     double dphu[4];
     for (int a = 0; a < 4; ++a) { double x = 0; for (int b = 0; b < 4; ++b) x += g4i[a][b] * dph[b]; dphu[a] = x; }

@@ -509,6 +509,44 @@ def test_solve_matrix_is_identity_at_zero_coupling(orc, conformal_generic):
     assert diag1[18] < 1e-12  # residual of the coupled equations after the solve
 
 
+@pytest.mark.parametrize("kind", [0, 1])
+def test_decoupled_metric_is_vacuum_and_blind_to_the_scalar(orc, conformal_generic, kind):
+    """4dST without backreaction onto the metric ("Key features"): with decoupled = 1 the metric
+    and gauge right-hand sides (fields 0..24) do not see the scalar at all. For any scalar data
+    they equal the full theory's with the scalar switched off (phi = Pi = 0 with zero derivatives,
+    where T_ab vanishes for both couplings: vacuum CCZ4 in the same gauge). With backreaction the
+    same scalar data does move the metric, and the decoupled scalar still evolves. Catches a
+    stress-energy term left in a metric equation, or a mode switch that does nothing.
+    The vacuum reference also switches the couplings off: with beta = lambda phi a zero scalar is
+    still sourced by L_GB (d_t Pi != 0), and its Gauss-Bonnet stress does not vanish."""
+    v, d1, d2, ph = conformal_generic
+    gauge = dict(a0=0.3, b0=0.5)
+    kw = dict(lam=0.4, g2=0.3, beta_kind=kind, **gauge)
+    r_dec, diag_dec, st = orc.point_rhs(P(decoupled=1, **kw), v, d1, d2)
+    assert st == 0
+    v0, d10, d20 = v.copy(), d1.copy(), d2.copy()
+    v0[25:27] = 0.0
+    d10[25:27] = 0.0
+    d20[25:27] = 0.0
+    r_vac, diag_vac, _ = orc.point_rhs(P(lam=0.0, g2=0.0, **gauge), v0, d10, d20)
+    assert np.all(diag_vac[0:10] == 0.0)          # no stress-energy without a scalar
+    np.testing.assert_allclose(r_dec[:25], r_vac[:25], rtol=1e-12, atol=1e-13)
+    assert np.all(diag_dec[0:10] == 0.0)          # decoupled: rho, S_i, S_ij left out
+    r_full, _, _ = orc.point_rhs(P(**kw), v, d1, d2)
+    assert np.max(np.abs(r_full[:25] - r_vac[:25])) > 1e-4
+    assert abs(r_dec[26]) > 1e-4 and abs(r_dec[26] - r_full[26]) > 1e-8
+    assert diag_dec[18] < 1e-12                   # residual of the scalar equation after the solve
+
+
+def test_decoupled_scalar_at_zero_coupling_is_klein_gordon(orc, conformal_generic):
+    """Without couplings the scalar equation does not involve d_t K_ij, so the decoupled d_t Pi
+    equals the full theory's, which the Klein-Gordon pin fixes."""
+    v, d1, d2, ph = conformal_generic
+    r_full, _, _ = orc.point_rhs(P(lam=0.0, g2=0.0), v, d1, d2)
+    r_dec, _, _ = orc.point_rhs(P(lam=0.0, g2=0.0, decoupled=1), v, d1, d2)
+    assert abs(r_dec[26] - r_full[26]) < 1e-13
+
+
 # ----------------------------------------------------------------------------- constraints
 def test_constraints_converge_to_zero_on_kerr_schild(orc):
     """H and M_i of the exact Kerr-Schild data, computed with 4th-order differences on boxes
