@@ -78,6 +78,8 @@ def parse():
     ap.add_argument("--workload", default="bl_pair_256", choices=["bl_pair_256", "bl_pair_128", "bl_pair_96", "bl_pair_64", "amr_boxes_96", "coupling_sweep_32", "sphere_signal_96", "calls_256", "calls_96"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--decoupled", action="store_true",
+                    help="4dST without backreaction onto the metric (bl_pair workloads)")
     ap.add_argument("--no-peak", action="store_true", help="skip the FP64 microbenchmark")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     return ap.parse_args()
@@ -471,6 +473,8 @@ def run_ours(args, rank, world, local_rank):
     cfg = workload(args.workload)
     box = cfg["box"]
     params, dt = cfg["params"], cfg["dt"]
+    if args.decoupled:
+        params.decoupled = 1
 
     # CPU oracle baseline first (rank 0, N = 1), before any CUDA work in this process
     cpu = None
@@ -574,6 +578,7 @@ def run_ours(args, rank, world, local_rank):
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": cfg["name"], "grid": [box.nx, box.ny, box.nz], "ghosts": 3, "dx": box.dx,
                       "dt": dt, "beta": "lambda phi^2/2", "lambda": params.lam, "g2": params.g2,
+                      "backreaction": not args.decoupled,
                       "state_bytes": int(state.numel() * 8), "l2": "inputs larger than L2 (no flush needed)",
                       "parallelism": f"{world} independent replica(s), one box per GPU"},
            "gpu_launches": 5 * args.steps, "roofline": roof, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,

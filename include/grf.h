@@ -76,6 +76,9 @@ typedef struct {
     double min_chi, min_lapse;       /* floors applied after every RK stage */
     int beta_kind;                   /* GRF_BETA_LINEAR or GRF_BETA_QUADRATIC */
     int enforce_algebraic;           /* 1: trace-free A_ij and the floors after every stage */
+    int decoupled;                   /* 0: full 4dST; 1: without backreaction onto the metric
+                                        ("Key features"): the metric evolves by vacuum CCZ4 in the
+                                        same gauge, the scalar by its full equation on that metric */
 } grf_params;
 
 /* d_t of all 27 fields at the interior points of `state` (modified CCZ4 + 4dST, section
@@ -111,8 +114,9 @@ int grf_rk4_step(const grf_box* box, const grf_params* params, double* state, do
  * computed. Page-locked buffers are copied by a small kernel (48 blocks) that reads or writes
  * host memory directly, which keeps the full host-link rate while the stages run; pageable
  * buffers are copied with cudaMemcpyAsync. Results are bit-identical to: copy host_in to state,
- * grf_rk4_step, copy state to host_out. The stage kernels run on `stream`; the copies are ordered after the work already
- * queued on `stream`, and later work on `stream` is ordered after the last copy, so host_out is
+ * grf_rk4_step, copy state to host_out. The stage kernels run on `stream`; the copies are
+ * ordered after the work already queued on `stream`, and later work on `stream` is ordered
+ * after the last copy, so host_out is
  * complete once `stream` is synchronised. Host buffers should be page-locked (cudaHostAlloc,
  * cudaHostRegister, pinned torch tensors); pageable buffers give the same results, but their
  * copies are staged by the driver and overlap the kernels poorly.

@@ -39,7 +39,7 @@ class grf_params(C.Structure):
                 ("shift_F", C.c_double), ("eta", C.c_double), ("a0", C.c_double), ("b0", C.c_double),
                 ("lambda_", C.c_double), ("g2", C.c_double), ("sigma_ko", C.c_double),
                 ("min_chi", C.c_double), ("min_lapse", C.c_double),
-                ("beta_kind", C.c_int), ("enforce_algebraic", C.c_int)]
+                ("beta_kind", C.c_int), ("enforce_algebraic", C.c_int), ("decoupled", C.c_int)]
 
 
 GRF_BATCH_GRAPH, GRF_BATCH_PERSISTENT, GRF_BATCH_STREAM = 1, 2, 3
@@ -130,7 +130,8 @@ def box_like(b, pitch=None) -> grf_box:
 def params_like(p) -> grf_params:
     """grf_params from any object with the parameter attributes (lambda under `lam`)."""
     return grf_params(p.kappa1, p.kappa2, p.kappa3, p.shift_F, p.eta, p.a0, p.b0, p.lam, p.g2, p.sigma_ko,
-                      p.min_chi, p.min_lapse, int(p.beta_kind), int(p.enforce_algebraic))
+                      p.min_chi, p.min_lapse, int(p.beta_kind), int(p.enforce_algebraic),
+                      int(getattr(p, "decoupled", 0)))
 
 
 def state_shape(box: grf_box, nfields=NFIELDS):

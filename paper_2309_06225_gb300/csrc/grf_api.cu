@@ -187,6 +187,7 @@ Coeffs make_coeffs(const grf_params* p) {
     c.bK = 3.0 * p->b0 / (4.0 * (1.0 + p->b0));
     c.bTh = 1.0 / (2.0 * (1.0 + p->b0));
     c.beta_kind = p->beta_kind;
+    c.decoupled = p->decoupled;
     return c;
 }
 

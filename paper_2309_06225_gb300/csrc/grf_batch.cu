@@ -39,7 +39,7 @@ struct TileDesc {
             // each warp covers 32 / w rows of a narrow box)
 };
 
-template <int STAGE>
+template <int STAGE, int DEC>
 __device__ __forceinline__ void batch_tile(const BoxDesc* __restrict__ boxes, const TileDesc& td, int* status,
                                            YzRows& sh) {
     const BoxDesc& d = boxes[td.box];
@@ -75,15 +75,15 @@ __device__ __forceinline__ void batch_tile(const BoxDesc* __restrict__ boxes, co
     } else if (j >= d.g.ny || k >= d.g.nz || (mode == GATHER_LOCAL && i >= d.g.nx)) {
         return;
     }
-    stage_point<STAGE>(d.g, d.c, a, i, j, k, mode, &sh);
+    stage_point<STAGE, DEC>(d.g, d.c, a, i, j, k, mode, &sh);
 }
 
 // Out-of-line copy of batch_tile for the persistent kernel: with the four stages inlined into one
 // kernel, ptxas spilled 52 KB per thread; called, each stage is allocated on its own (13 KB).
-template <int STAGE>
+template <int STAGE, int DEC>
 __device__ __noinline__ void batch_tile_call(const BoxDesc* __restrict__ boxes, const TileDesc& td, int* status,
                                              YzRows& sh) {
-    batch_tile<STAGE>(boxes, td, status, sh);
+    batch_tile<STAGE, DEC>(boxes, td, status, sh);
 }
 
 template <int STAGE>
@@ -93,7 +93,10 @@ __global__ void __launch_bounds__(128, 3) batch_stage_kernel(const BoxDesc* __re
     const int t = blockIdx.x;
     if (t >= ntiles) return;
     const TileDesc td = tiles[t];
-    batch_tile<STAGE>(boxes, td, status, sh);
+    // the decoupled mode is a compile-time instantiation (as in the single-box kernels, whose bits
+    // these must match); the full theory stays inlined
+    if (boxes[td.box].c.decoupled) batch_tile_call<STAGE, 1>(boxes, td, status, sh);
+    else batch_tile<STAGE, 0>(boxes, td, status, sh);
 }
 
 // Grid-wide barrier for a cooperative launch. Thread 0 of each block arrives on a counter;
@@ -141,11 +144,12 @@ __global__ void __launch_bounds__(128, 3) batch_persistent_kernel(const BoxDesc*
         for (int s = 0; s < 4; ++s) {
             for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
                 const TileDesc td = tiles[t];
+                const bool dec = boxes[td.box].c.decoupled != 0;
                 switch (s) {
-                    case 0: batch_tile_call<0>(boxes, td, status, sh); break;
-                    case 1: batch_tile_call<1>(boxes, td, status, sh); break;
-                    case 2: batch_tile_call<2>(boxes, td, status, sh); break;
-                    default: batch_tile_call<3>(boxes, td, status, sh); break;
+                    case 0: dec ? batch_tile_call<0, 1>(boxes, td, status, sh) : batch_tile_call<0, 0>(boxes, td, status, sh); break;
+                    case 1: dec ? batch_tile_call<1, 1>(boxes, td, status, sh) : batch_tile_call<1, 0>(boxes, td, status, sh); break;
+                    case 2: dec ? batch_tile_call<2, 1>(boxes, td, status, sh) : batch_tile_call<2, 0>(boxes, td, status, sh); break;
+                    default: dec ? batch_tile_call<3, 1>(boxes, td, status, sh) : batch_tile_call<3, 0>(boxes, td, status, sh); break;
                 }
             }
             if (!grid_barrier(bar, gridDim.x, timeout, status)) return;
@@ -372,6 +376,7 @@ int grf_batched_rk4(const grf_batch_item* items, int nitems, const grf_params* p
         d.c.inv_1pa = 1.0 / (1.0 + p->a0); d.c.a_1pa = p->a0 / (1.0 + p->a0);
         d.c.bK = 3.0 * p->b0 / (4.0 * (1.0 + p->b0)); d.c.bTh = 1.0 / (2.0 * (1.0 + p->b0));
         d.c.beta_kind = p->beta_kind;
+        d.c.decoupled = p->decoupled;
         const size_t sb = align_up(state_bytes_of(d.g));
         d.un = it.state;
         d.A = (double*)(base + off);

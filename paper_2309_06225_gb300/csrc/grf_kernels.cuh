@@ -264,7 +264,7 @@ enum GatherMode {
 // threads past the interior (i >= nx, and j >= ny in block mode) take part in the gather, at the
 // last ghost column / row at most, and then write nothing. sh: the block's rows (block mode,
 // already filled and synchronised).
-template <int STAGE>
+template <int STAGE, int DEC = -1>
 __device__ __forceinline__ void stage_point(const Geom& g, const Coeffs& c, const StageArgs& a, int i, int j, int k,
                                             int mode, const YzRows* sh) {
     const bool live = i < g.nx && j < g.ny;
@@ -283,7 +283,7 @@ __device__ __forceinline__ void stage_point(const Geom& g, const Coeffs& c, cons
     if (!live) return;
     double r[NFIELDS];
     bool ok = true;
-    point_rhs<double>(c, in, r, nullptr, ok);
+    point_rhs<double, double, DEC>(c, in, r, nullptr, ok);
     if (!ok) atomicOr(a.status, 1);
     double out[NFIELDS];
 #pragma unroll 1
@@ -306,7 +306,9 @@ __device__ __forceinline__ void stage_point(const Geom& g, const Coeffs& c, cons
 // Launched with blocks of (32, 4, 1) threads (block gather mode). Planes k0, k0+1, ...
 // 3 resident blocks of 128 threads per SM (168 registers a thread): the extra warps hide more
 // FP64 dependency latency than the added spills cost (measured 2% faster than 2 blocks).
-template <int STAGE>
+// DEC: 0 full theory, 1 without backreaction (a separate instantiation each, so the full
+// theory's kernel carries no test of the mode).
+template <int STAGE, int DEC = 0>
 __global__ void __launch_bounds__(128, 3) rk4_stage_kernel(Geom g, Coeffs c, StageArgs a) {
     __shared__ YzRows sh;
     const int i = blockIdx.x * 32 + threadIdx.x;
@@ -315,20 +317,20 @@ __global__ void __launch_bounds__(128, 3) rk4_stage_kernel(Geom g, Coeffs c, Sta
     if (k >= g.nz) return;  // whole block
     yz_rows_fill(g, a.src, i, blockIdx.y * 4, threadIdx.y, k, threadIdx.x, sh);
     __syncthreads();
-    stage_point<STAGE>(g, c, a, i, j, k, GATHER_BLOCK, &sh);
+    stage_point<STAGE, DEC>(g, c, a, i, j, k, GATHER_BLOCK, &sh);
 }
 
 // Folded variant for boxes whose x-extent is not a multiple of 32, chosen by the host when it
 // fills more lanes: blocks of (32, 4, 1), each warp covering 32 / w rows of w = a.fold x-points,
 // with the per-thread gather. It gives the same bits as rk4_stage_kernel.
-template <int STAGE>
+template <int STAGE, int DEC>
 __global__ void __launch_bounds__(128, 3) rk4_stage_fold_kernel(Geom g, Coeffs c, StageArgs a) {
     const int w = a.fold, per = 32 / a.fold;
     const int i = blockIdx.x * w + (int)threadIdx.x % w;
     const int j = blockIdx.y * (4 * per) + (int)threadIdx.y * per + (int)threadIdx.x / w;
     const int k = blockIdx.z + a.k0;
     if (i >= g.nx || j >= g.ny || k >= g.nz) return;
-    stage_point<STAGE>(g, c, a, i, j, k, GATHER_LOCAL, nullptr);
+    stage_point<STAGE, DEC>(g, c, a, i, j, k, GATHER_LOCAL, nullptr);
 }
 
 }  // namespace grf

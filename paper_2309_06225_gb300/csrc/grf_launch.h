@@ -10,6 +10,8 @@ namespace grf {
 struct Geom;
 struct StageArgs;
 void launch_stage(int stage, dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c, const StageArgs& a);
+void launch_stage_decoupled(int stage, dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c,
+                            const StageArgs& a);
 void launch_stage_folded(int stage, dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c,
                          const StageArgs& a);
 void launch_rhs(dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c, const double* s, double* rhs,

@@ -64,6 +64,7 @@ struct CoeffsT {
     double inv_1pa, a_1pa;        // 1/(1+a), a/(1+a)
     double bK, bTh;               // 3b/(4(1+b)), 1/(2(1+b))
     int beta_kind;
+    int decoupled;  // 1: the scalar's stress-energy is left out of the metric equations
 };
 using Coeffs = CoeffsT<double>;
 
@@ -209,7 +210,9 @@ GRF_HD void q_of(const T X[6], const T gd[6], const T gw[6], const T Phd[6], con
         }
 }
 
-template <typename T, typename P = double>
+// DEC: the decoupled mode as a compile-time constant (0: full theory, 1: no backreaction), or -1
+// to read c.decoupled at run time.
+template <typename T, typename P = double, int DEC = -1>
 GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS], PointExtraT<T>* extra, bool& ok) {
     GRF_SECTION(0);
     const T* v = in.v;
@@ -583,7 +586,10 @@ GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS]
     GRF_SECTION(11);
     const T fX = fma(2.0 * g2, X, 1.0);
     const T XX = fma(g2 * X, X, X);  // X + g2 X^2
-    const T rho8 = fma(0.5 * fX, Pi * Pi, fma(-4.0, sdotw(GS, Phuw), -0.5 * XX));
+    // decoupled mode: the scalar's stress-energy is left out of the metric equations (rho, S_i,
+    // S_ij and their coupling to d_t K_ij); the scalar equation below is unchanged
+    const bool dec = (DEC < 0) ? (c.decoupled != 0) : (DEC == 1);
+    const T rho8 = dec ? T(0.0) : fma(0.5 * fX, Pi * Pi, fma(-4.0, sdotw(GS, Phuw), -0.5 * XX));
     T S8[3];
     const T BPn = Bv[0] * Phnu[0] + Bv[1] * Phnu[1] + Bv[2] * Phnu[2];
 #pragma unroll
@@ -598,7 +604,7 @@ GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS]
                     const T pkl = (k == l) ? Phuw[sidx(k, l)] : 0.5 * Phuw[sidx(k, l)];
                     s = fma(BC(k, i, l), pkl, s);
                 }
-        S8[i] = fma(-0.5 * fX * Pi, dphi[i], 4.0 * s);
+        S8[i] = dec ? T(0.0) : fma(-0.5 * fX * Pi, dphi[i], 4.0 * s);
     }
     T S1[6], Y[6];
     const T fXh = 0.5 * fX, XXh = 0.5 * XX;
@@ -606,7 +612,7 @@ GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS]
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = i; j < 3; ++j) {
-            S1[sidx(i, j)] = fma(fXh * dphi[i], dphi[j], XXh * gd[sidx(i, j)]);
+            S1[sidx(i, j)] = dec ? T(0.0) : fma(fXh * dphi[i], dphi[j], XXh * gd[sidx(i, j)]);
             T y = fma(Bv[j], Phn[i], Bv[i] * Phn[j]);
             y = fma(-2.0 * BPn, gd[sidx(i, j)], y);
 #pragma unroll
@@ -614,7 +620,7 @@ GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS]
                 if (l != j) y = fma(BC(i, j, l), Phnu[l], y);
                 if (l != i) y = fma(BC(j, i, l), Phnu[l], y);
             }
-            Y[sidx(i, j)] = y;
+            Y[sidx(i, j)] = dec ? T(0.0) : y;
         }
 
     // C0 = C at d_t K_ij = 0
@@ -749,9 +755,9 @@ GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS]
         for (int m = 0; m < 6; ++m) {
             const T LGS = fma(-Ss4, gd[m], S[m]);
             const T U0 = fma(-Kp[m], chid, fma(rhs[F_H + m], K3, fma(h[m], Kdot0 * (1.0 / 3.0), Adot0[m]))) * ichi;
-            const T lin = fma(LGS, Phnn0, (Y[m] + QC0[m]) - gd[m] * (trYh + trQh));
+            const T lin = dec ? T(0.0) : fma(LGS, Phnn0, (Y[m] + QC0[m]) - gd[m] * (trYh + trQh));
             Msys[m][7] = fma(al4, lin, fma(-al, fma(-trS1h, gd[m], S1[m]), U0));
-            Msys[m][6] = -four_b1 * LGS;
+            Msys[m][6] = dec ? T(0.0) : -four_b1 * LGS;
         }
         // 6x6 block, column (a,b): -4 L(Q(E_ab)) with E_ab the unit symmetric matrix
         //   = -2 gamma_ij w_ab (Phi^ab - gamma^ab tr Phi) - 4 w_ab gamma^ab Phi_ij + 4 P_ij,ab - 4 tr(Phi) [ij == ab]
@@ -779,7 +785,7 @@ GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS]
                         T e = fma(-2.0 * gd[row], sab, tab * Phd[row]);
                         if (any) e = fma(4.0, p, e);
                         if (row == col) e = e + one4P;
-                        Msys[row][col] = e;
+                        Msys[row][col] = dec ? T(row == col ? 1.0 : 0.0) : e;
                     }
             }
         const T Dphi = fma(2.0 * g2, Pi * Pi, fX);
@@ -814,7 +820,8 @@ GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS]
         const T Phnn = fma(b1 * ial, w, Phnn0);
         T S8ij[6];
 #pragma unroll
-        for (int m = 0; m < 6; ++m) S8ij[m] = fma(-4.0, fma(GS[m], Phnn, Y[m] + fma(Qu[m], ial, QC0[m])), S1[m]);
+        for (int m = 0; m < 6; ++m)
+            S8ij[m] = dec ? T(0.0) : fma(-4.0, fma(GS[m], Phnn, Y[m] + fma(Qu[m], ial, QC0[m])), S1[m]);
         const T Ss8 = sdotw(S8ij, gw);
         rhs[F_K] = fma(0.5 * al, Ss8, Kdot0);
         const T trh3 = sdotw(S8ij, hw) * (1.0 / 3.0);

@@ -8,6 +8,10 @@ void launch_stage(int stage, dim3 grid, dim3 block, cudaStream_t st, const Geom&
         launch_stage_folded(stage, grid, block, st, g, c, a);
         return;
     }
+    if (c.decoupled) {
+        launch_stage_decoupled(stage, grid, block, st, g, c, a);
+        return;
+    }
     switch (stage) {
         case 0: rk4_stage_kernel<0><<<grid, block, 0, st>>>(g, c, a); break;
         case 1: rk4_stage_kernel<1><<<grid, block, 0, st>>>(g, c, a); break;

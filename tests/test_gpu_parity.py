@@ -164,6 +164,33 @@ def test_rk4_parity_folded_launch(g, orc, bc):
     assert np.array_equal(hout.numpy()[..., :box.nx + 6], gpu)
 
 
+@pytest.mark.parametrize("bc", [gi.BC_PERIODIC, gi.BC_FROZEN])
+def test_decoupled_mode_parity(g, orc, bc):
+    """4dST without backreaction: the RHS and 3 RK4 steps against the oracle's decoupled mode;
+    the metric fields after the steps equal those of a vacuum evolution (couplings off, no
+    scalar) to 1e-12."""
+    box = gi.Box(14, 11, 9, 0.3, -2.0, -1.6, -1.3, bc=bc)
+    params = P(lam=0.3, g2=0.2, beta_kind=1, decoupled=1)
+    s0 = make_state(box, "perturbed", 23)
+    s = s0.copy()
+    if bc == gi.BC_PERIODIC:
+        orc.fill_ghosts(box, s)
+    ref = orc.rhs(box, params, s)
+    out = gpu_rhs(g, box, params, s)
+    errs = field_errors(out, ref, box, state=s, sigma=params.sigma_ko)
+    assert np.max(errs) < 1e-11, describe(errs)
+    cpu = s0.copy()
+    orc.rk4(box, params, cpu, 0.25 * box.dx, 3)
+    gpu = gpu_rk4(g, box, params, s0, 0.25 * box.dx, 3)
+    errs = field_errors(gpu, cpu, box)
+    assert np.max(errs) < 1e-10, describe(errs)
+    vac0 = s0.copy()
+    vac0[25:27] = 0.0
+    vac = gpu_rk4(g, box, P(lam=0.0, g2=0.0, beta_kind=1), vac0, 0.25 * box.dx, 3)
+    errs = field_errors(gpu[:25], vac[:25], box)
+    assert np.max(errs) < 1e-12, describe(errs)
+
+
 def test_constraints_parity(g, orc):
     box = gi.Box(13, 12, 10, 0.3, -1.9, -1.7, -1.4)
     params = P(lam=0.3, g2=0.2)

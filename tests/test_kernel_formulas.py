@@ -20,9 +20,10 @@ def flops():
     return fl
 
 
+@pytest.mark.parametrize("decoupled", [0, 1])
 @pytest.mark.parametrize("seed", range(6))
 @pytest.mark.parametrize("kind", [0, 1])
-def test_kernel_pointwise_rhs_matches_oracle(orc, flops, seed, kind):
+def test_kernel_pointwise_rhs_matches_oracle(orc, flops, seed, kind, decoupled):
     import paper_2309_06225_gb300 as grf
     rng = np.random.default_rng(100 + seed)
     v = rng.uniform(-0.2, 0.2, 27)
@@ -33,7 +34,7 @@ def test_kernel_pointwise_rhs_matches_oracle(orc, flops, seed, kind):
     d1 = rng.normal(size=(27, 3)) * 0.3
     d2 = rng.normal(size=(27, 6)) * 0.3
     p = gi.Params(lam=rng.uniform(0.0, 0.6), g2=rng.uniform(0.0, 0.4), beta_kind=kind, a0=0.3, b0=0.7,
-                  kappa2=0.2, kappa3=0.6)
+                  kappa2=0.2, kappa3=0.6, decoupled=decoupled)
     ref, diag, st = orc.point_rhs(p, v, d1, d2)
     assert st == 0
     s1, s2 = slots(d1, d2)
