@@ -30,6 +30,7 @@ IDX = {n: i for i, n in enumerate(FIELD_NAMES)}
 
 BC_PERIODIC = 0
 BC_FROZEN = 1
+BC_REFLECT_LOW = 2   # mirror planes half a cell below the first point of the three low faces
 BETA_LINEAR = 0      # beta(phi) = lambda * phi
 BETA_QUADRATIC = 1   # beta(phi) = lambda * phi^2 / 2
 
@@ -166,6 +167,28 @@ def gaussian_bumps(seed, n_bumps, lo, hi):
     widths = [rng.uniform(1.0, 3.0) for _ in range(n_bumps)]
     amps = [1e-2 * rng.uniform(-1.0, 1.0) for _ in range(n_bumps)]
     return centres, widths, amps
+
+
+def mirror_symmetric_state(box, M=1.0, amp=0.05, eps=1e-2):
+    """Puncture at the origin with a scalar shell, plus small smooth fields with the parity of
+    each component under x_d -> -x_d (so that the state is symmetric under all three
+    reflections): K ~ exp(-r^2/8), A_ij ~ (x_i x_j - delta_ij r^2/3) exp(-r^2/8) (trace-free in
+    the flat conformal metric), shift^i, B^i and Gamma^i ~ x^i exp(-r^2/8), Pi ~ exp(-r^2/8)."""
+    s = single_puncture(box, M=M, amp=amp)
+    X, Y, Z = box.coords()
+    xs = (X, Y, Z)
+    e = np.exp(-(X ** 2 + Y ** 2 + Z ** 2) / 8.0)
+    r2 = X ** 2 + Y ** 2 + Z ** 2
+    s[IDX["K"]] = eps * e
+    for n, (a, b) in zip(("A11", "A12", "A13", "A22", "A23", "A33"),
+                         ((0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2))):
+        s[IDX[n]] = 0.5 * eps * (xs[a] * xs[b] - (r2 / 3.0 if a == b else 0.0)) * e
+    for d, c in enumerate("123"):
+        s[IDX["shift" + c]] = eps * xs[d] * e
+        s[IDX["B" + c]] = 0.5 * eps * xs[d] * e
+        s[IDX["Gamma" + c]] = 0.3 * eps * xs[d] * e
+    s[IDX["Pi"]] = 0.5 * eps * e
+    return s
 
 
 def brill_lindquist_pair(box, m1=0.5, m2=0.5, sep=6.0, seed=0, n_bumps=8, lo=-16.0, hi=16.0):

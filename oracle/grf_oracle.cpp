@@ -61,7 +61,8 @@ typedef struct {
     int nx, ny, nz, ng;     // interior points per axis, ghost layers (3)
     double dx;
     double x0, y0, z0;      // coordinate of interior point 0 (unused by the operator itself)
-    int bc;                 // 0 periodic (ghosts refilled by wrap), 1 frozen (ghosts kept)
+    int bc;                 // 0 periodic (ghosts refilled by wrap), 1 frozen (ghosts kept),
+                            // 2 mirror planes at the three low faces (high-face ghosts kept)
     int pad_;
 } orc_box;
 
@@ -796,6 +797,44 @@ void fill_periodic(const Grid& g, double* s) {
                 }
 }
 
+// Parity of field f under the reflection x_d -> -x_d: -1 for components with an odd number of
+// indices along d (the d-component of Gamma-hat, shift and B; h_de and A_de with exactly one
+// index d), +1 for scalars and the rest.
+double parity(int f, int d) {
+    if (f >= F_GAM && f < F_GAM + 3) return (f - F_GAM == d) ? -1.0 : 1.0;
+    if (f >= F_SHIFT && f < F_SHIFT + 3) return (f - F_SHIFT == d) ? -1.0 : 1.0;
+    if (f >= F_B && f < F_B + 3) return (f - F_B == d) ? -1.0 : 1.0;
+    int m = -1;
+    if (f >= F_H && f < F_H + 6) m = f - F_H;
+    if (f >= F_A && f < F_A + 6) m = f - F_A;
+    if (m >= 0) return ((SYM_I[m] == d) != (SYM_J[m] == d)) ? -1.0 : 1.0;
+    return 1.0;
+}
+
+// Mirror planes half a cell below the first interior point on the three low faces: a ghost point
+// whose coordinates are interior or low ghosts (at least one) takes the value of its mirror image
+// in the interior, times the field's parity under each reflected axis. Ghosts on the high faces
+// (any coordinate past the interior) are left as given.
+void fill_reflect(const Grid& g, double* s) {
+    for (int f = 0; f < NF; ++f)
+        for (int k = 0; k < g.ng + g.nz; ++k)
+            for (int j = 0; j < g.ng + g.ny; ++j)
+                for (int i = 0; i < g.ng + g.nx; ++i) {
+                    if (i >= g.ng && j >= g.ng && k >= g.ng) continue;
+                    double sign = 1.0;
+                    int a = i, b = j, c = k;
+                    if (i < g.ng) { a = 2 * g.ng - 1 - i; sign *= parity(f, 0); }
+                    if (j < g.ng) { b = 2 * g.ng - 1 - j; sign *= parity(f, 1); }
+                    if (k < g.ng) { c = 2 * g.ng - 1 - k; sign *= parity(f, 2); }
+                    s[g.at(f, i, j, k)] = sign * s[g.at(f, a, b, c)];
+                }
+}
+
+void fill_bc(const orc_box& b, const Grid& g, double* s) {
+    if (b.bc == 0) fill_periodic(g, s);
+    else if (b.bc == 2) fill_reflect(g, s);
+}
+
 int rhs_box(const orc_box& b, const orc_params& P, const double* s, double* rhs, int with_ko) {
     Grid g(b);
     int bad = 0;
@@ -906,7 +945,7 @@ void orc_phys_sources(const orc_params* P, const double* phys, const double* u6,
 int orc_solve(int n, const double* M, const double* r, double* x) { return solve_full_pivot(n, M, r, x); }
 
 void orc_fill_ghosts(const orc_box* b, double* s) {
-    if (b->bc == 0) fill_periodic(Grid(*b), s);
+    fill_bc(*b, Grid(*b), s);
 }
 
 // First and second derivatives of every field at every interior point:
@@ -958,7 +997,7 @@ int orc_rk4(const orc_box* b, const orc_params* P, double* s, double dt, int nst
     const double c[3] = {0.5, 0.5, 1.0};
     int st = 0;
     for (int step = 0; step < nsteps; ++step) {
-        if (b->bc == 0) fill_periodic(g, s);
+        fill_bc(*b, g, s);
         std::copy(s, s + n, us.begin());
         for (int stage = 0; stage < 4; ++stage) {
             const double* src = (stage == 0) ? s : us.data();
@@ -976,7 +1015,7 @@ int orc_rk4(const orc_box* b, const orc_params* P, double* s, double dt, int nst
                         }
             if (stage < 3) {
                 if (P->enforce_algebraic) enforce(g, *P, us.data());
-                if (b->bc == 0) fill_periodic(g, us.data());
+                fill_bc(*b, g, us.data());
             }
         }
 #pragma omp parallel for collapse(3)
@@ -988,7 +1027,7 @@ int orc_rk4(const orc_box* b, const orc_params* P, double* s, double dt, int nst
                         s[q] = s[q] + dt / 6.0 * acc[q];
                     }
         if (P->enforce_algebraic) enforce(g, *P, s);
-        if (b->bc == 0) fill_periodic(g, s);
+        fill_bc(*b, g, s);
     }
     return st;
 }
