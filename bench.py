@@ -75,7 +75,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="bl_pair_256", choices=["bl_pair_256", "bl_pair_128", "bl_pair_96", "bl_pair_64", "amr_boxes_96", "coupling_sweep_32", "sphere_signal_96", "calls_256", "calls_96"])
+    ap.add_argument("--workload", default="bl_pair_256", choices=["bl_pair_256", "bl_pair_128", "bl_pair_96", "bl_pair_64", "amr_boxes_96", "coupling_sweep_32", "sphere_signal_96", "calls_256", "calls_96", "bl_pair_octant_128"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--decoupled", action="store_true",
@@ -88,6 +88,8 @@ def parse():
 def workload(name):
     import grf_inputs as gi
     n = int(name.rsplit("_", 1)[1])
+    if name.startswith("bl_pair_octant_"):
+        return gi.config_bl_pair_octant(n)
     return gi.config_bl_pair_256(n)
 
 
@@ -579,11 +581,14 @@ def run_ours(args, rank, world, local_rank):
            "config": {"workload": cfg["name"], "grid": [box.nx, box.ny, box.nz], "ghosts": 3, "dx": box.dx,
                       "dt": dt, "beta": "lambda phi^2/2", "lambda": params.lam, "g2": params.g2,
                       "backreaction": not args.decoupled,
+                      "boundary": {0: "periodic", 1: "frozen", 2: "mirror planes at the low faces, analytic high-face ghosts"}[box.bc],
                       "state_bytes": int(state.numel() * 8), "l2": "inputs larger than L2 (no flush needed)",
                       "parallelism": f"{world} independent replica(s), one box per GPU"},
            "gpu_launches": 5 * args.steps, "roofline": roof, "clocks": clk, "e2e": e2e, "cpu_baseline": cpu,
            "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
            "status": {"solve": status, "finite": finite}}
+    if box.bc == 2:  # an octant with mirror planes evolves the symmetric full box on 1/8 of its points
+        out["config"]["full_box_equivalent_point_updates_per_s"] = 8 * value
     print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()

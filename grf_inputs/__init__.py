@@ -256,6 +256,30 @@ def config_bl_pair_256(n=256):
                 make_state=lambda b=box: brill_lindquist_pair(b))
 
 
+def brill_lindquist_pair_symmetric(box, m1=0.5, m2=0.5, sep=6.0, amp=1e-2, r0=4.0, width=2.0):
+    """The Brill-Lindquist pair on the z axis at +-sep/2 with equal masses, which is symmetric under
+    the x, y and z reflections, plus a spherical scalar shell phi = amp exp(-(r - r0)^2 / width^2)
+    that shares the symmetry."""
+    X, Y, Z = box.coords()
+    r1 = np.sqrt(X ** 2 + Y ** 2 + (Z - sep / 2) ** 2)
+    r2 = np.sqrt(X ** 2 + Y ** 2 + (Z + sep / 2) ** 2)
+    psi = 1.0 + m1 / (2 * r1) + m2 / (2 * r2)
+    r = np.sqrt(X ** 2 + Y ** 2 + Z ** 2)
+    return conformally_flat_puncture(box, psi, amp * np.exp(-((r - r0) ** 2) / width ** 2))
+
+
+def config_bl_pair_octant(n=128):
+    """The positive octant [0, 16]^3 of the 256^3 Brill-Lindquist domain (dx = 0.125), n^3 interior
+    points, with mirror planes at the three low faces and the analytic data in the high-face
+    ghosts; the scalar is the symmetric shell of brill_lindquist_pair_symmetric. It evolves the
+    symmetric full-box problem on 1/8 of its points."""
+    dx = 16.0 / n
+    box = Box(n, n, n, dx, 0.5 * dx, 0.5 * dx, 0.5 * dx, bc=BC_REFLECT_LOW)
+    params = Params(beta_kind=BETA_QUADRATIC, lam=0.05, g2=0.01)
+    return dict(name=f"bl_pair_octant_{n}", box=box, params=params, dt=0.25 * dx, nsteps=100,
+                make_state=lambda b=box: brill_lindquist_pair_symmetric(b))
+
+
 def coupling_sweep(n_instances=32, seed=0):
     """Seeded couplings of the 32-instance sweep: lambda ~ U[0,0.1], g2 ~ U[0,0.05]."""
     rng = SplitMix64(seed)

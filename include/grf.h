@@ -50,7 +50,7 @@ enum {
     GRF_ETOOLARGE = -7     /* box too large for the fixed scratch of grf_rk4_step_noalloc */
 };
 
-enum { GRF_BC_PERIODIC = 0, GRF_BC_FROZEN = 1 };
+enum { GRF_BC_PERIODIC = 0, GRF_BC_FROZEN = 1, GRF_BC_REFLECT_LOW = 2 };
 enum { GRF_BETA_LINEAR = 0, GRF_BETA_QUADRATIC = 1 };
 enum { GRF_OP_RHS = 0, GRF_OP_RK4 = 1, GRF_OP_CONSTRAINTS = 2 };
 
@@ -61,7 +61,12 @@ typedef struct {
     double dx;            /* grid spacing, > 0 */
     double x0, y0, z0;    /* coordinates of interior point (0,0,0) */
     int bc;               /* GRF_BC_PERIODIC: ghosts refilled by periodic wrap;
-                             GRF_BC_FROZEN: ghosts are read as given and never written */
+                             GRF_BC_FROZEN: ghosts are read as given and never written;
+                             GRF_BC_REFLECT_LOW: the three low faces are mirror planes (half a
+                             cell below the first point; "Boundary Conditions", reflective),
+                             their ghosts rebuilt from the interior with each component's
+                             parity; ghosts on the high faces are read as given. Needs n >= 3.
+                             Not accepted by grf_batched_rk4 and grf_tlm_rk4. */
     long long pitch;      /* doubles per x row, >= nx + 2 ng */
 } grf_box;
 

@@ -37,6 +37,24 @@ __global__ void ghost_fill_kernel(Geom g, double* __restrict__ s) {
     }
 }
 
+// Mirror-plane ghost fill (GRF_BC_REFLECT_LOW): every ghost point whose coordinates are interior
+// or low ghosts takes its mirror image in the interior times the component's parity; ghosts on
+// the high faces are left as given. One thread per (i, j) column and field; walks k.
+__global__ void reflect_fill_kernel(Geom g, double* __restrict__ s) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int f = blockIdx.z;
+    if (i >= g.nx + NG || j >= g.ny + NG) return;
+    double* u = s + (long long)f * g.fstride;
+    const int a = i < NG ? 2 * NG - 1 - i : i, b = j < NG ? 2 * NG - 1 - j : j;
+    const int mij = (i < NG ? 1 : 0) | (j < NG ? 2 : 0);
+    for (int k = 0; k < g.nz + NG; ++k) {
+        const int m = mij | (k < NG ? 4 : 0);
+        if (m == 0) continue;
+        u[gidx(g, i, j, k)] = mirror_sign(f, m) * u[gidx(g, a, b, k < NG ? 2 * NG - 1 - k : k)];
+    }
+}
+
 // Ghost preparation for one slab of z-planes [K0, K1) of the host-to-device pipeline of
 // grf_rk4_step_host. Periodic: in-plane (x, y) wrap of the ghost columns of `s`; the z-ghost
 // planes themselves were copied from the interior planes they are images of, so after this the
@@ -53,12 +71,20 @@ __global__ void slab_ghost_kernel(Geom g, double* __restrict__ s, double* __rest
         const int wi = wrap(i, g.nx), wj = wrap(j, g.ny);
         if (wi == i && wj == j) return;
         for (int k = K0; k < K1; ++k) s[fo + gidx(g, i, j, k)] = s[fo + gidx(g, wi, wj, k)];
-    } else {
+    } else {  // frozen and mirror boxes: the ghosts go to A and B; mirror boxes rebuild their low ones
         const bool ghost_ij = i < NG || i >= g.nx + NG || j < NG || j >= g.ny + NG;
+        const int mij = (i < NG ? 1 : 0) | (j < NG ? 2 : 0);
+        const bool low_ij = i < g.nx + NG && j < g.ny + NG;
         for (int k = K0; k < K1; ++k) {
             if (!ghost_ij && k >= NG && k < g.nz + NG) continue;
             const long long q = fo + gidx(g, i, j, k);
-            const double v = s[q];
+            double v = s[q];
+            if (g.reflect && low_ij && k < g.nz + NG) {  // a mirrored ghost: its source is interior
+                const int m = mij | (k < NG ? 4 : 0);
+                v = mirror_sign((int)blockIdx.z, m) *
+                    s[fo + gidx(g, i < NG ? 2 * NG - 1 - i : i, j < NG ? 2 * NG - 1 - j : j, k < NG ? 2 * NG - 1 - k : k)];
+                s[q] = v;
+            }
             A[q] = v;
             B[q] = v;
         }
@@ -154,8 +180,8 @@ bool box_ok(const grf_box* b) {
     if (!b) return false;
     if (b->ng != 3 || b->nx < 1 || b->ny < 1 || b->nz < 1 || !(b->dx > 0.0)) return false;
     if (b->pitch < (long long)b->nx + 6) return false;
-    if (b->bc != GRF_BC_PERIODIC && b->bc != GRF_BC_FROZEN) return false;
-    if (b->bc == GRF_BC_PERIODIC && (b->nx < 3 || b->ny < 3 || b->nz < 3)) return false;
+    if (b->bc != GRF_BC_PERIODIC && b->bc != GRF_BC_FROZEN && b->bc != GRF_BC_REFLECT_LOW) return false;
+    if (b->bc != GRF_BC_FROZEN && (b->nx < 3 || b->ny < 3 || b->nz < 3)) return false;
     return true;
 }
 
@@ -168,6 +194,7 @@ Geom make_geom(const grf_box* b) {
     g.fstride = g.plane * g.NZ;
     g.dx = b->dx;
     g.periodic = (b->bc == GRF_BC_PERIODIC);
+    g.reflect = (b->bc == GRF_BC_REFLECT_LOW);
     return g;
 }
 
@@ -239,6 +266,11 @@ int* status_ptr() {
 }
 
 int fill_ghosts(const Geom& g, double* s, cudaStream_t st) {
+    if (g.reflect) {
+        dim3 blk(32, 8, 1), grd((g.nx + NG + 31) / 32, (g.ny + NG + 7) / 8, NFIELDS);
+        reflect_fill_kernel<<<grd, blk, 0, st>>>(g, s);
+        return check_launch();
+    }
     if (!g.periodic) return GRF_OK;
     dim3 blk(32, 8, 1), grd((g.NX + 31) / 32, (g.NY + 7) / 8, NFIELDS);
     ghost_fill_kernel<<<grd, blk, 0, st>>>(g, s);

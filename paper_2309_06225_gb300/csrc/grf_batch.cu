@@ -210,6 +210,7 @@ Geom geom_of(const grf_box* b) {
     g.fstride = g.plane * g.NZ;
     g.dx = b->dx;
     g.periodic = (b->bc == GRF_BC_PERIODIC);
+    g.reflect = 0;  // mirror boxes are not accepted here
     return g;
 }
 

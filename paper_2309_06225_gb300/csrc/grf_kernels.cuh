@@ -15,7 +15,8 @@ struct Geom {
     long long plane;         // pitch * NY
     long long fstride;       // plane * NZ
     double dx;
-    int periodic;
+    int periodic;            // ghosts are periodic images (written by the owner of each value)
+    int reflect;             // the three low faces are mirror planes (images written by the owner)
 };
 
 constexpr int NG = 3;
@@ -199,13 +200,40 @@ __device__ __forceinline__ bool interior_thread(const Geom& g, int& i, int& j, i
     return i < g.nx && j < g.ny && k < g.nz;
 }
 
-// Writes value x of field f for interior point (i,j,k) and, for periodic boxes, to every
-// ghost location that is a periodic image of it.
+// Parity of field f under the reflections x_d -> -x_d of the axes in `mask` (bit d): -1 when
+// the component has an odd number of indices along the reflected axes (the d-components of
+// Gamma-hat, shift and B; h_ab and A_ab with exactly one index reflected), +1 otherwise.
+__host__ __device__ __forceinline__ double mirror_sign(int f, int mask) {
+    int odd = 0;
+    if (f >= F_GAM && f < F_GAM + 3) odd = (mask >> (f - F_GAM)) & 1;
+    else if (f >= F_SHIFT && f < F_SHIFT + 3) odd = (mask >> (f - F_SHIFT)) & 1;
+    else if (f >= F_B && f < F_B + 3) odd = (mask >> (f - F_B)) & 1;
+    else if ((f >= F_H && f < F_H + 6) || (f >= F_A && f < F_A + 6)) {
+        const int m = (f < F_A) ? f - F_H : f - F_A;  // sym index of (a, b), a <= b
+        const int a = m < 3 ? 0 : (m < 5 ? 1 : 2);
+        const int b = m < 3 ? m : (m < 5 ? m - 2 : 2);
+        odd = ((mask >> a) & 1) ^ ((mask >> b) & 1);
+    }
+    return odd ? -1.0 : 1.0;
+}
+
+// Writes value x of field f for interior point (i,j,k) and to every ghost location that is an
+// image of it: periodic images, or for mirror boxes its reflections in the low faces (the
+// mirror plane lies half a cell below the first point; ghost NG-1-i mirrors interior i), with
+// the component's parity.
 __device__ __forceinline__ void store_with_images(const Geom& g, double* __restrict__ dst, int f, int i, int j, int k,
                                                   double x) {
     double* d = dst + f * g.fstride;
     if (!g.periodic) {
         d[gidx(g, i + NG, j + NG, k + NG)] = x;
+        if (g.reflect) {
+            const int near = (i < NG ? 1 : 0) | (j < NG ? 2 : 0) | (k < NG ? 4 : 0);
+            for (int m = 1; m < 8; ++m) {
+                if (m & ~near) continue;
+                d[gidx(g, (m & 1) ? NG - 1 - i : i + NG, (m & 2) ? NG - 1 - j : j + NG, (m & 4) ? NG - 1 - k : k + NG)] =
+                    mirror_sign(f, m) * x;
+            }
+        }
         return;
     }
     int xi[3], yi[3], zi[3];

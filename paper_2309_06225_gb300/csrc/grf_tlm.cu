@@ -217,6 +217,7 @@ Geom geom_from(const grf_box* b) {
     g.fstride = g.plane * g.NZ;
     g.dx = b->dx;
     g.periodic = (b->bc == GRF_BC_PERIODIC);
+    g.reflect = 0;  // mirror boxes are not accepted here
     return g;
 }
 

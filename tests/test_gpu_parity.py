@@ -191,6 +191,38 @@ def test_decoupled_mode_parity(g, orc, bc):
     assert np.max(errs) < 1e-12, describe(errs)
 
 
+def test_mirror_planes_parity(g, orc):
+    """Mirror planes at the three low faces (GRF_BC_REFLECT_LOW) on a generic state: the ghost
+    fill bit for bit against the oracle's, the RHS and 3 RK4 steps against the oracle's mirror
+    boxes, and the host-to-host step's bits against the device step."""
+    import torch
+    box = gi.Box(17, 14, 12, 0.3, 0.15, 0.15, 0.15, bc=gi.BC_REFLECT_LOW)
+    params = P(lam=0.3, g2=0.2, beta_kind=1)
+    s0 = gi.random_perturbed_state(box, 29, base=gi.mirror_symmetric_state(box), eps=2e-2)
+    assert np.all(np.isfinite(s0))
+    b = g.box_like(box)
+    t = g.to_device(s0, b)
+    g.grf_fill_ghosts(b, t)
+    filled = s0.copy()
+    orc.fill_ghosts(box, filled)
+    assert np.array_equal(g.to_host(t, b), filled)
+    ref = orc.rhs(box, params, filled)
+    out = gpu_rhs(g, box, params, s0)
+    errs = field_errors(out, ref, box, state=filled, sigma=params.sigma_ko)
+    assert np.max(errs) < 1e-11, describe(errs)
+    cpu = s0.copy()
+    orc.rk4(box, params, cpu, 0.25 * box.dx, 3)
+    gpu = gpu_rk4(g, box, params, s0, 0.25 * box.dx, 3)
+    errs = field_errors(gpu, cpu, box)
+    assert np.max(errs) < 1e-10, describe(errs)
+    hin = torch.zeros(g.state_shape(b), dtype=torch.float64, pin_memory=True)
+    hin[..., :box.nx + 6] = torch.from_numpy(np.ascontiguousarray(s0))
+    hout = torch.empty_like(hin).pin_memory()
+    g.grf_rk4_step_host(b, g.params_like(params), hin, hout, g.alloc_state(b), 0.25 * box.dx, 3)
+    torch.cuda.synchronize()
+    assert np.array_equal(hout.numpy()[..., :box.nx + 6], gpu)
+
+
 def test_constraints_parity(g, orc):
     box = gi.Box(13, 12, 10, 0.3, -1.9, -1.7, -1.4)
     params = P(lam=0.3, g2=0.2)
