@@ -53,6 +53,8 @@ def lib():
         L.orc_rk4.argtypes = [C.POINTER(OrcBox), C.POINTER(OrcParams), _P, C.c_double, C.c_int]
         L.orc_rk4.restype = C.c_int
         L.orc_constraints.argtypes = [C.POINTER(OrcBox), C.POINTER(OrcParams), _P, _P]
+        L.orc_energy_densities.argtypes = [C.POINTER(OrcBox), C.POINTER(OrcParams), _P, _P]
+        L.orc_point_energy.argtypes = [C.POINTER(OrcParams), _P, _P, _P, _P]
         _lib = L
     return _lib
 
@@ -159,4 +161,20 @@ def rk4(b, p, s, dt, nsteps):
 def constraints(b, p, s):
     out = np.zeros((4, b.nz, b.ny, b.nx))
     lib().orc_constraints(C.byref(box(b)), C.byref(params(p)), _ptr(s), _ptr(out))
+    return out
+
+
+def point_energy(p, v, d1, d2):
+    """8 pi rho of the X, g2 X^2 and Gauss-Bonnet terms at one point (3 doubles)."""
+    out = np.zeros(3)
+    lib().orc_point_energy(C.byref(params(p)), _ptr(np.ascontiguousarray(v, dtype=np.float64)),
+                           _ptr(np.ascontiguousarray(d1, dtype=np.float64)),
+                           _ptr(np.ascontiguousarray(d2, dtype=np.float64)), _ptr(out))
+    return out
+
+
+def energy_densities(b, p, s):
+    """8 pi rho of the three scalar terms at the interior points: array (3, nz, ny, nx)."""
+    out = np.zeros((3, b.nz, b.ny, b.nx))
+    lib().orc_energy_densities(C.byref(box(b)), C.byref(params(p)), _ptr(s), _ptr(out))
     return out

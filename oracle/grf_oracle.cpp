@@ -259,6 +259,7 @@ void geometry(const Phys& p, Geo& G) {
 // ------------------------------------------------------------------------------------
 struct Src {
     double rho8, S8[3], Sij8[3][3], LGB, E;  // 8 pi rho, 8 pi S_i, 8 pi S_ij, L_GB, scalar eq.
+    double rho8_parts[3];  // 8 pi rho of the X, g2 X^2 and beta(phi) L_GB terms (with backreaction or not)
 };
 
 void beta_derivs(const orc_params& P, double phi, double& b1, double& b2) {
@@ -374,6 +375,15 @@ void sources(const orc_params& P, const Phys& p, const Geo& G, const double u[3]
             for (int c = 0; c < 4; ++c) for (int d = 0; d < 4; ++d) x -= 4.0 * Pd[a][c][b][d] * Phiu[c][d];
             T8[a][b] = x;
         }
+    // energy densities of the three scalar terms of the action ("Diagnostics"): the n-n components
+    // of the three parts of 8 pi T_ab
+    {
+        double gb = 0;
+        for (int c = 0; c < 4; ++c) for (int d = 0; d < 4; ++d) gb -= 4.0 * Pd[0][c][0][d] * Phiu[c][d];
+        s.rho8_parts[0] = 0.5 * dph[0] * dph[0] + 0.5 * g4[0][0] * X;
+        s.rho8_parts[1] = g2 * X * dph[0] * dph[0] + 0.5 * g4[0][0] * g2 * X * X;
+        s.rho8_parts[2] = gb;
+    }
     // Without backreaction ("Key features": 4dST without backreaction onto the metric) the
     // scalar's stress-energy is left out of the metric equations; the scalar equation below still
     // uses the full 4D curvature of the evolving metric.
@@ -728,6 +738,16 @@ void point_constraints(const orc_params& P, const double* v, const double* d1, c
     }
 }
 
+// 8 pi rho of the X, g2 X^2 and Gauss-Bonnet terms at one point (independent of d_t K_ij, d_t Pi).
+void point_energy(const orc_params& P, const double* v, const double* d1, const double* d2, double* out3) {
+    static thread_local Conf c;
+    conf_setup(v, d1, d2, c);
+    double u[3][3] = {{0}};
+    Src s;
+    sources(P, c.p, c.G, u, 0.0, s);
+    for (int m = 0; m < 3; ++m) out3[m] = s.rho8_parts[m];
+}
+
 // ------------------------------------------------------------------------------------
 // Grid operations
 // ------------------------------------------------------------------------------------
@@ -1033,6 +1053,26 @@ int orc_rk4(const orc_box* b, const orc_params* P, double* s, double dt, int nst
 }
 
 // Hamiltonian and momentum constraints at interior points: out[4][nz][ny][nx] (ghosts valid).
+void orc_point_energy(const orc_params* P, const double* v, const double* d1, const double* d2, double* out3) {
+    point_energy(*P, v, d1, d2, out3);
+}
+
+// Energy densities of the three scalar terms at interior points: out[3][nz][ny][nx] (ghosts valid).
+void orc_energy_densities(const orc_box* b, const orc_params* P, const double* s, double* out) {
+    Grid g(*b);
+    const long long npt = (long long)b->nx * b->ny * b->nz;
+#pragma omp parallel for collapse(2)
+    for (int k = 0; k < b->nz; ++k)
+        for (int j = 0; j < b->ny; ++j)
+            for (int i = 0; i < b->nx; ++i) {
+                double v[NF], d1[NF * 3], d2[NF * 6], o[3];
+                point_derivs(g, s, b->dx, i + g.ng, j + g.ng, k + g.ng, v, d1, d2);
+                point_energy(*P, v, d1, d2, o);
+                long long p = ((long long)k * b->ny + j) * b->nx + i;
+                for (int m = 0; m < 3; ++m) out[m * npt + p] = o[m];
+            }
+}
+
 void orc_constraints(const orc_box* b, const orc_params* P, const double* s, double* out) {
     Grid g(*b);
     const long long npt = (long long)b->nx * b->ny * b->nz;

@@ -582,6 +582,34 @@ def test_mirror_planes_reproduce_the_symmetric_full_box(orc):
     assert np.max(err_frozen) > 1e-6
 
 
+@pytest.mark.parametrize("couplings", [(0.0, 0.0), (0.4, 0.3)])
+@pytest.mark.parametrize("kind", [0, 1])
+def test_energy_densities_of_the_three_scalar_terms(orc, conformal_generic, couplings, kind):
+    """The energy density is split by the terms of the action R + X + g2 X^2 + beta(phi) L_GB
+    ("Diagnostics"), in the 8 pi rho units of the right-hand sides:
+        X term:    (Pi^2 + |D phi|^2) / 4 for any couplings (the minimally coupled scalar);
+        X^2 term:  g2 (X Pi^2 - X^2 / 2) with X = (Pi^2 - |D phi|^2) / 2;
+        GB term:   zero when lambda = 0;
+    and the three add up to the 8 pi rho that enters the equations. Catches a term assigned to
+    the wrong part, a sign of X, or a missing g2."""
+    v, d1, d2, ph = conformal_generic
+    lam, g2 = couplings
+    p = P(lam=lam, g2=g2, beta_kind=kind)
+    parts = orc.point_energy(p, v, d1, d2)
+    _, diag, _ = orc.point_rhs(p, v, d1, d2)
+    gi3 = np.linalg.inv(ph["g"])
+    Pi, dphi = v[26], d1[25]
+    grad2 = dphi @ gi3 @ dphi
+    X = 0.5 * (Pi ** 2 - grad2)
+    assert abs(parts[0] - 0.25 * (Pi ** 2 + grad2)) < 1e-14
+    assert abs(parts[1] - g2 * (X * Pi ** 2 - 0.5 * X ** 2)) < 1e-14
+    if lam == 0.0:
+        assert parts[2] == 0.0
+    else:
+        assert abs(parts[2]) > 1e-6
+    assert abs(parts.sum() - diag[0]) < 1e-13
+
+
 # ----------------------------------------------------------------------------- constraints
 def test_constraints_converge_to_zero_on_kerr_schild(orc):
     """H and M_i of the exact Kerr-Schild data, computed with 4th-order differences on boxes
