@@ -112,9 +112,12 @@ def batched_workload(name):
 def run_calls(args, rank, world, local_rank):
     """The standalone entry points on the 256^3 (calls_256) or 96^3 (calls_96, small enough for a
     full profiler capture) Brill-Lindquist state: one RHS evaluation with
-    dissipation (grf_rhs), the dissipation alone (grf_ko_dissipation, added into an RHS array) and
-    the constraints (grf_constraints, the 4 fields without the norms). The timed RK4 step fuses the
-    first two; the constraints are a diagnostic taken between steps."""
+    dissipation (grf_rhs), the dissipation alone (grf_ko_dissipation, added into an RHS array), the
+    constraints (grf_constraints, the 4 fields without the norms) and the energy densities of the
+    three scalar terms (grf_energy_densities). The timed RK4 step fuses the first two; the last two
+    are diagnostics taken between steps. On the periodic box grf_rhs, grf_constraints and
+    grf_energy_densities each launch the ghost fill and their kernel, grf_ko_dissipation one
+    kernel: 7 launches per timed iteration over the four calls."""
     import torch
     import paper_2309_06225_gb300 as grf
     from paper_2309_06225_gb300 import flops as grf_flops
@@ -127,12 +130,14 @@ def run_calls(args, rank, world, local_rank):
     state = grf.to_device(cfg["make_state"](), b)
     rhs = grf.alloc_state(b)
     out4 = grf.alloc_state(b, 4)
+    out3 = grf.alloc_state(b, 3)
     npts = box.nx * box.ny * box.nz
     stream = torch.cuda.current_stream()
     calls = {
         "grf_rhs": lambda: grf.grf_rhs(b, p, state, rhs),
         "grf_ko_dissipation": lambda: grf.grf_ko_dissipation(b, params.sigma_ko, state, rhs),
         "grf_constraints": lambda: grf.grf_constraints(b, p, state, out4, norms=False),
+        "grf_energy_densities": lambda: grf.grf_energy_densities(b, p, state, out3),
     }
     hbm, hbm_src = measured_hbm_gbs()
     flop_rhs = grf_flops.flops_per_point_rhs(p)
@@ -167,7 +172,7 @@ def run_calls(args, rank, world, local_rank):
             rec["roofline"] = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                                "frac": tf / FP64_PEAK_TFLOPS, "flop_per_point": flop_rhs,
                                "peak_source": "GB300 FP64 non-tensor, 1.25 TFLOP/s (nominal)"}
-        else:  # the constraints use a subset of the RHS (the compiler drops the CCZ4 update and the solve)
+        else:  # constraints and densities use a subset of the RHS (no CCZ4 update, no solve)
             rec["roofline"] = None
             rec["note"] = "FP64-bound like grf_rhs; its flop count is a subset of the RHS and is not counted"
         out[name] = rec
@@ -179,7 +184,7 @@ def run_calls(args, rank, world, local_rank):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "grid": [box.nx, box.ny, box.nz],
                        "l2": "inputs larger than L2 (no flush needed)"},
-            "gpu_launches": 4 * args.steps, "calls": out, "clocks": clk, "status": {"solve": status},
+            "gpu_launches": 7 * args.steps, "calls": out, "clocks": clk, "status": {"solve": status},
             "roofline": out["grf_rhs"]["roofline"], "e2e": None, "cpu_baseline": None}
     print(json.dumps(line), flush=True)
 

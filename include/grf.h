@@ -143,6 +143,17 @@ int grf_rk4_step_host(const grf_box* box, const grf_params* params, const double
 int grf_constraints(const grf_box* box, const grf_params* params, double* state, double* out4,
                     double* norms_host, void* ws, size_t ws_bytes, grf_stream_t stream);
 
+/* Energy densities of the three scalar terms of the action ("Diagnostics": the energy densities
+ * associated with the different scalar terms), in the 8 pi rho units of the equations:
+ *   out3[0] = X term        = (Pi^2 + |D phi|^2) / 4
+ *   out3[1] = g2 X^2 term   = g2 (X Pi^2 - X^2 / 2),  X = (Pi^2 - |D phi|^2) / 2
+ *   out3[2] = beta(phi) L_GB term = -4 G_S^ij Phi_ij  (Phi = nabla nabla beta, G_S the Einstein
+ *             tensor of the Gauss block)
+ * Their sum is the 8 pi rho that enters the equations (with backreaction). out3: device, 3 fields
+ * in the state layout, interior entries written. Ghosts of `state` are refilled as for grf_rhs. */
+int grf_energy_densities(const grf_box* box, const grf_params* params, double* state, double* out3,
+                         grf_stream_t stream);
+
 /* rhs_accum += sigma/(64 dx) sum_{d=x,y,z} (u_-3 - 6u_-2 + 15u_-1 - 20u_0 + 15u_+1 - 6u_+2 + u_+3)
  * for all 27 fields at the interior points (Kreiss-Oliger dissipation). Ghosts of
  * `state` must be valid (call grf_fill_ghosts first for periodic boxes). */

@@ -83,6 +83,7 @@ def lib():
         L.grf_rk4_step.argtypes = [B, P, _VP, C.c_double, C.c_int, _VP, C.c_size_t, _VP]
         L.grf_rk4_step_host.argtypes = [B, P, _VP, _VP, _VP, C.c_double, C.c_int, _VP, C.c_size_t, _VP]
         L.grf_constraints.argtypes = [B, P, _VP, _VP, C.POINTER(C.c_double), _VP, C.c_size_t, _VP]
+        L.grf_energy_densities.argtypes = [B, P, _VP, _VP, _VP]
         L.grf_ko_dissipation.argtypes = [B, C.c_double, _VP, _VP, _VP]
         L.grf_fill_ghosts.argtypes = [B, _VP, _VP]
         L.grf_workspace_bytes.argtypes = [B, C.c_int]
@@ -104,7 +105,7 @@ def lib():
         L.grf_error_string.argtypes = [C.c_int]
         L.grf_error_string.restype = C.c_char_p
         L.grf_last_cuda_error.restype = C.c_char_p
-        for name in ("grf_rhs", "grf_rk4_step", "grf_rk4_step_host", "grf_constraints", "grf_ko_dissipation", "grf_fill_ghosts",
+        for name in ("grf_rhs", "grf_rk4_step", "grf_rk4_step_host", "grf_constraints", "grf_energy_densities", "grf_ko_dissipation", "grf_fill_ghosts",
                      "grf_check_status", "grf_check_finite"):
             getattr(L, name).restype = C.c_int
         _lib = L
@@ -242,6 +243,12 @@ def grf_constraints(box: grf_box, params: grf_params, state, out4, norms=True, w
     _check(lib().grf_constraints(C.byref(box), C.byref(params), _dev(state), _dev(out4), host, _dev(ws), nb,
                                  _stream(stream)), "grf_constraints")
     return np.array(list(host)) if norms else None
+
+
+def grf_energy_densities(box: grf_box, params: grf_params, state, out3, stream=None):
+    """8 pi rho of the X, g2 X^2 and Gauss-Bonnet terms into out3 (3 fields, state layout)."""
+    return _check(lib().grf_energy_densities(C.byref(box), C.byref(params), _dev(state), _dev(out3),
+                                             _stream(stream)), "grf_energy_densities")
 
 
 def grf_ko_dissipation(box: grf_box, sigma, state, rhs_accum, stream=None):

@@ -621,7 +621,7 @@ int grf_constraints(const grf_box* box, const grf_params* params, double* state,
     int r = fill_ghosts(g, state, st);
     if (r) return r;
     double* part = norms_host ? (double*)ws : nullptr;
-    launch_constraints(interior_grid(g), kBlock, st, g, make_coeffs(params), state, out4, part);
+    launch_constraints(interior_grid(g), kBlock, st, g, make_coeffs(params), state, out4, part, nullptr);
     r = check_launch();
     if (r || !norms_host) return r;
     double* out8 = part + nb * 8;
@@ -631,6 +631,17 @@ int grf_constraints(const grf_box* box, const grf_params* params, double* state,
     cudaError_t e = cudaMemcpyAsync(norms_host, out8, 8 * sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return e == cudaSuccess ? GRF_OK : cuda_fail(e);
+}
+
+int grf_energy_densities(const grf_box* box, const grf_params* params, double* state, double* out3,
+                         grf_stream_t stream) {
+    if (!box_ok(box) || !params_ok(params) || !state || !out3) return GRF_EINVAL;
+    Geom g = make_geom(box);
+    cudaStream_t st = (cudaStream_t)stream;
+    int r = fill_ghosts(g, state, st);
+    if (r) return r;
+    launch_constraints(interior_grid(g), kBlock, st, g, make_coeffs(params), state, nullptr, nullptr, out3);
+    return check_launch();
 }
 
 int grf_check_status(grf_stream_t stream) {

@@ -17,7 +17,7 @@ void launch_stage_folded(int stage, dim3 grid, dim3 block, cudaStream_t st, cons
 void launch_rhs(dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c, const double* s, double* rhs,
                 double ko, int* status);
 void launch_constraints(dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c, const double* s,
-                        double* out4, double* part);
+                        double* out4, double* part, double* dens);
 // Records a CUDA error for grf_last_cuda_error() and returns GRF_ECUDA.
 int record_cuda_error(cudaError_t e);
 }  // namespace grf

@@ -81,6 +81,8 @@ template <typename T>
 struct PointExtraT {
     T ham;      // H = S - 2 (8 pi rho)
     T mom[3];   // M_i = B_i - 8 pi S_i
+    T rho8[3];  // 8 pi rho of the X, g2 X^2 and beta(phi) L_GB terms of the action (their sum is
+                // the 8 pi rho of the equations; reported with and without backreaction)
 };
 using PointExtra = PointExtraT<double>;
 
@@ -834,6 +836,10 @@ GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS]
         extra->ham = fma(-2.0, rho8, Ss);
 #pragma unroll
         for (int i = 0; i < 3; ++i) extra->mom[i] = Bv[i] - S8[i];
+        const T X2 = X * X;
+        extra->rho8[0] = 0.5 * (Pi * Pi - X);
+        extra->rho8[1] = g2 * fma(X, Pi * Pi, -0.5 * X2);
+        extra->rho8[2] = -4.0 * sdotw(GS, Phuw);
     }
 #undef BC
 #undef D1

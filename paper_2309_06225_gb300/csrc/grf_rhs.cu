@@ -32,8 +32,11 @@ __global__ void __launch_bounds__(128) rhs_kernel(Geom g, Coeffs c, const double
 
 // Constraints H, M_i at interior points (state layout, 4 fields) and per-block partial norms:
 // part[block][8] = {sum H^2, max|H|, sum M1^2, max|M1|, ...}
+// out4 (H, M_i; with the per-block norm partials in `part`) and dens (the energy densities of the
+// three scalar terms) are each written when non-null.
 __global__ void __launch_bounds__(128) constraints_kernel(Geom g, Coeffs c, const double* __restrict__ s,
-                                                          double* __restrict__ out4, double* __restrict__ part) {
+                                                          double* __restrict__ out4, double* __restrict__ part,
+                                                          double* __restrict__ dens) {
     // blocks of (32, 4, 1): block gather mode, as rhs_kernel; every thread stays to the reduction
     __shared__ double red[8][128];
     __shared__ YzRows sh;
@@ -61,7 +64,10 @@ __global__ void __launch_bounds__(128) constraints_kernel(Geom g, Coeffs c, cons
         vals[1] = ex.mom[0];
         vals[2] = ex.mom[1];
         vals[3] = ex.mom[2];
-        for (int m = 0; m < 4; ++m) out4[m * g.fstride + p] = vals[m];
+        if (out4)
+            for (int m = 0; m < 4; ++m) out4[m * g.fstride + p] = vals[m];
+        if (dens)
+            for (int m = 0; m < 3; ++m) dens[m * g.fstride + p] = ex.rho8[m];
     }
     const int t = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
     for (int m = 0; m < 4; ++m) {
@@ -88,7 +94,7 @@ void launch_rhs(dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coe
     rhs_kernel<<<grid, block, 0, st>>>(g, c, s, rhs, ko, status);
 }
 void launch_constraints(dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c, const double* s,
-                        double* out4, double* part) {
-    constraints_kernel<<<grid, block, 0, st>>>(g, c, s, out4, part);
+                        double* out4, double* part, double* dens) {
+    constraints_kernel<<<grid, block, 0, st>>>(g, c, s, out4, part, dens);
 }
 }  // namespace grf

@@ -243,6 +243,30 @@ def test_constraints_parity(g, orc):
         np.testing.assert_allclose(norms[2 * m + 1], np.max(np.abs(ref[m])), rtol=1e-11)
 
 
+@pytest.mark.parametrize("bc,decoupled", [(gi.BC_PERIODIC, 0), (gi.BC_FROZEN, 1)])
+def test_energy_densities_parity(g, orc, bc, decoupled):
+    """The three energy densities (X, g2 X^2 and Gauss-Bonnet terms) against the oracle's split
+    of its covariant stress tensor, each to 1e-11 of its own maximum; the split does not depend
+    on whether the scalar backreacts. Ghosts of the device state are refilled by the call."""
+    box = gi.Box(15, 11, 13, 0.3, -2.1, -1.5, -1.8, bc=bc)
+    params = P(lam=0.3, g2=0.2, beta_kind=1, decoupled=decoupled)
+    s = make_state(box, "perturbed", 31)
+    orc.enforce(box, params, s)
+    filled = s.copy()
+    orc.fill_ghosts(box, filled)
+    ref = orc.energy_densities(box, params, filled)
+    b = g.box_like(box)
+    t = g.to_device(s, b)
+    out = g.alloc_state(b, 3)
+    g.grf_energy_densities(b, g.params_like(params), t, out)
+    assert g.grf_check_status() == 0
+    got = box.interior(g.to_host(out, b)[:3])
+    for m in range(3):
+        den = np.max(np.abs(ref[m]))
+        assert den > 0, m
+        assert np.max(np.abs(got[m] - ref[m])) <= 1e-11 * den, m
+
+
 def test_bl_pair_256_sampled_outputs(g, orc):
     """Full-size 256^3 Brill-Lindquist workload, one RK4 step in the production launch
     configuration; sampled points are recomputed by the oracle on 19^3 frozen-ghost sub-boxes
