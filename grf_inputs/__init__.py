@@ -93,6 +93,7 @@ class Params:
     min_lapse: float = 1e-4
     enforce_algebraic: int = 1
     decoupled: int = 0          # 1: 4dST without backreaction (metric evolves by vacuum CCZ4)
+    advection: int = 0          # 0: centred advection derivatives, 1: lopsided (upwind-biased)
 
     def to_dict(self):
         return asdict(self)

@@ -20,7 +20,8 @@ class OrcParams(C.Structure):
                 ("a0", C.c_double), ("b0", C.c_double),
                 ("lam", C.c_double), ("g2", C.c_double),
                 ("sigma_ko", C.c_double), ("min_chi", C.c_double), ("min_lapse", C.c_double),
-                ("beta_kind", C.c_int), ("enforce_algebraic", C.c_int), ("decoupled", C.c_int)]
+                ("beta_kind", C.c_int), ("enforce_algebraic", C.c_int), ("decoupled", C.c_int),
+                ("advection", C.c_int)]
 
 
 class OrcBox(C.Structure):
@@ -40,6 +41,9 @@ def lib():
         L = C.CDLL(path)
         L.orc_point_rhs.argtypes = [C.POINTER(OrcParams), _P, _P, _P, _P, _P]
         L.orc_point_rhs.restype = C.c_int
+        L.orc_point_rhs_adv.argtypes = [C.POINTER(OrcParams), _P, _P, _P, _P, _P, _P]
+        L.orc_point_rhs_adv.restype = C.c_int
+        L.orc_adv_lopsided.argtypes = [C.POINTER(OrcBox), _P, _P]
         L.orc_point_constraints.argtypes = [C.POINTER(OrcParams), _P, _P, _P, _P]
         L.orc_phys_sources.argtypes = [C.POINTER(OrcParams), _P, _P, C.c_double, _P]
         L.orc_solve.argtypes = [C.c_int, _P, _P, _P]
@@ -68,7 +72,7 @@ def params(p) -> OrcParams:
     """From a grf_inputs.Params (or anything with the same attributes)."""
     return OrcParams(p.kappa1, p.kappa2, p.kappa3, p.shift_F, p.eta, p.a0, p.b0, p.lam, p.g2,
                      p.sigma_ko, p.min_chi, p.min_lapse, int(p.beta_kind), int(p.enforce_algebraic),
-                     int(getattr(p, "decoupled", 0)))
+                     int(getattr(p, "decoupled", 0)), int(getattr(p, "advection", 0)))
 
 
 def box(b) -> OrcBox:
@@ -88,6 +92,25 @@ def point_rhs(p, v, d1, d2):
     diag = np.zeros(64)
     st = lib().orc_point_rhs(C.byref(params(p)), _ptr(v), _ptr(d1), _ptr(d2), _ptr(rhs), _ptr(diag))
     return rhs, diag, st
+
+
+def point_rhs_adv(p, v, d1, d2, adv):
+    """As point_rhs with the 27 advection terms beta^k d_k u given."""
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    d1 = np.ascontiguousarray(d1, dtype=np.float64)
+    d2 = np.ascontiguousarray(d2, dtype=np.float64)
+    adv = np.ascontiguousarray(adv, dtype=np.float64)
+    rhs = np.zeros(27)
+    diag = np.zeros(64)
+    st = lib().orc_point_rhs_adv(C.byref(params(p)), _ptr(v), _ptr(d1), _ptr(d2), _ptr(adv), _ptr(rhs), _ptr(diag))
+    return rhs, diag, st
+
+
+def adv_lopsided(b, s):
+    """Lopsided advection terms beta^k d_k u of every field at the interior points: (27, nz, ny, nx)."""
+    out = np.zeros((27, b.nz, b.ny, b.nx))
+    lib().orc_adv_lopsided(C.byref(box(b)), _ptr(s), _ptr(out))
+    return out
 
 
 def point_constraints(p, v, d1, d2):

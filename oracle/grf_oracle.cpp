@@ -10,7 +10,11 @@
 // followed here are the published modified-CCZ4 / 4dST equations as stated (with every
 // reading listed) in the project design notes:
 //   * fields: chi, h_ij, K, A_ij, Theta, Gamma^i, lapse, shift^i, B^i, phi, Pi (27 doubles)
-//   * derivatives: centred 4th-order first, second and mixed differences
+//   * derivatives ("Accuracy": 4th and 6th order): the box's ghost width chooses the scheme,
+//     ng = 3 -> centred 4th-order first, second and mixed differences, ng = 4 -> 6th order
+//   * advection terms beta^k d_k u: centred differences (params.advection = 0) or lopsided
+//     differences biased one point towards the side the shift points to (advection = 1;
+//     4th order: offsets -1..3, 6th order: -2..4, mirrored for beta^k < 0)
 //   * 4dST sources: built COVARIANTLY. At each point the 4D Riemann tensor is assembled in
 //     the basis (n, d_i) from the Gauss, Codazzi and Ricci equations, the double dual P,
 //     the Gauss-Bonnet invariant, the effective stress tensor
@@ -27,7 +31,9 @@
 //     metric, for comparison with decoupling-limit codes): T_ab is dropped from the metric
 //     equations, which become vacuum CCZ4 in the same gauge, while the scalar evolves with the
 //     full scalar equation on that metric
-//   * Kreiss-Oliger dissipation sigma/(64 dx) sum_d Delta^6_d u on all fields
+//   * Kreiss-Oliger dissipation on all fields: sigma/(64 dx) sum_d Delta^6_d u for the 4th-order
+//     scheme, -sigma/(256 dx) sum_d Delta^8_d u for the 6th-order one (both damp the grid's
+//     Nyquist mode at sigma/dx per direction)
 //   * classical RK4 with post-stage algebraic enforcement (trace-free A, chi and lapse floors)
 //
 // Parity unpinned (no pin fixes these terms independently of the equations as read; they vanish
@@ -55,10 +61,11 @@ typedef struct {
     int beta_kind;          // 0: beta = lam*phi ; 1: beta = lam*phi^2/2
     int enforce_algebraic;  // 1: trace-free A, chi/lapse floors after every RK stage
     int decoupled;          // 1: no backreaction: the metric evolves by vacuum CCZ4, the scalar on it
+    int advection;          // 0: centred advection derivatives; 1: lopsided (upwind-biased)
 } orc_params;
 
 typedef struct {
-    int nx, ny, nz, ng;     // interior points per axis, ghost layers (3)
+    int nx, ny, nz, ng;     // interior points per axis, ghost layers (3: 4th order, 4: 6th order)
     double dx;
     double x0, y0, z0;      // coordinate of interior point 0 (unused by the operator itself)
     int bc;                 // 0 periodic (ghosts refilled by wrap), 1 frozen (ghosts kept),
@@ -144,6 +151,7 @@ struct Phys {
     double beta[3], dbeta[3][3];                   // dbeta[j][i] = d_j beta^i
     double phi, dphi[3], ddphi[3][3];
     double Pi, dPi[3];
+    double bdK[3][3], bdPi;                        // advection derivatives beta^k d_k K_ij, beta^k d_k Pi
 };
 
 struct Geo {
@@ -240,9 +248,8 @@ void geometry(const Phys& p, Geo& G) {
         }
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) {
-            double s = 0;
-            for (int k = 0; k < 3; ++k)
-                s += p.beta[k] * p.dK[k][i][j] + p.K[k][j] * p.dbeta[i][k] + p.K[i][k] * p.dbeta[j][k];
+            double s = p.bdK[i][j];
+            for (int k = 0; k < 3; ++k) s += p.K[k][j] * p.dbeta[i][k] + p.K[i][k] * p.dbeta[j][k];
             G.LbK[i][j] = s;
         }
     for (int i = 0; i < 3; ++i)
@@ -344,10 +351,9 @@ void sources(const orc_params& P, const Phys& p, const Geo& G, const double u[3]
     double dph[4] = {p.Pi, p.dphi[0], p.dphi[1], p.dphi[2]};
     double H[4][4];
     {
-        double bdPi = 0, dadp = 0;
-        for (int k = 0; k < 3; ++k) bdPi += p.beta[k] * p.dPi[k];
+        double dadp = 0;
         for (int k = 0; k < 3; ++k) for (int l = 0; l < 3; ++l) dadp += G.gi[k][l] * p.dalpha[k] * p.dphi[l];
-        H[0][0] = (w - bdPi - dadp) / p.alpha;
+        H[0][0] = (w - p.bdPi - dadp) / p.alpha;
         for (int i = 0; i < 3; ++i) {
             double kd = 0;
             for (int k = 0; k < 3; ++k) kd += G.Kud[k][i] * p.dphi[k];  // K_i^k d_k phi
@@ -408,6 +414,7 @@ struct Conf {
     double chi, h[3][3], K, A[3][3], Th, Gam[3], alpha, beta[3], B[3], phi, Pi;
     double d1[NF][3];
     double d2[NF][6];
+    double adv[NF];  // advection terms beta^k d_k u of every field
     // derived
     double hi[3][3], dh[3][3][3], Gt[3][3][3], Gtc[3], dGtc[3][3];  // Gt[k][i][j], dGtc[m][k]
     double Zl[3], Zu[3], RZ[3][3], RZs, Ric[3][3], Rs, Au[3][3], Aud[3][3], AA, DDa[3][3], DDa_tr, divb;
@@ -416,7 +423,21 @@ struct Conf {
     Geo G;
 };
 
-void conf_setup(const double* v, const double* d1, const double* d2, Conf& c) {
+// Sets the shift-contracted derivatives of the physical data: from the advection terms `adv`
+// (beta^k d_k of every conformal field; the chain rule of K_ij = (A_ij + h_ij K/3)/chi), or,
+// when adv is null, as beta^k times the centred derivatives.
+void advection_terms(const double* adv, Conf& c) {
+    Phys& p = c.p;
+    for (int f = 0; f < NF; ++f)
+        c.adv[f] = adv ? adv[f] : c.beta[0] * c.d1[f][0] + c.beta[1] * c.d1[f][1] + c.beta[2] * c.d1[f][2];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            p.bdK[i][j] = (c.adv[F_A + SYM[i][j]] + c.adv[F_H + SYM[i][j]] * c.K / 3.0 + c.h[i][j] * c.adv[F_K] / 3.0) / c.chi
+                          - p.K[i][j] * c.adv[F_CHI] / c.chi;
+    p.bdPi = c.adv[F_PI];
+}
+
+void conf_setup(const double* v, const double* d1, const double* d2, const double* adv, Conf& c) {
     c.chi = v[F_CHI];
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) { c.h[i][j] = v[F_H + SYM[i][j]]; c.A[i][j] = v[F_A + SYM[i][j]]; }
@@ -470,6 +491,7 @@ void conf_setup(const double* v, const double* d1, const double* d2, Conf& c) {
     for (int k = 0; k < 3; ++k) for (int l = 0; l < 3; ++l) p.ddphi[k][l] = d2[F_PHI * 6 + SYM[k][l]];
     p.Pi = c.Pi;
     for (int k = 0; k < 3; ++k) p.dPi[k] = d1[F_PI * 3 + k];
+    advection_terms(adv, c);
 
     geometry(p, c.G);
     for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) c.Ric[i][j] = c.G.Ric[i][j];
@@ -570,7 +592,7 @@ void conf_setup(const double* v, const double* d1, const double* d2, Conf& c) {
 void ccz4_rhs(const orc_params& P, const Conf& c, const Src& s, double* rhs) {
     const double al = c.alpha, chi = c.chi, K = c.K, Th = c.Th;
     const double a = P.a0, b = P.b0;
-    auto adv = [&](int f) { return c.beta[0] * c.d1[f][0] + c.beta[1] * c.d1[f][1] + c.beta[2] * c.d1[f][2]; };
+    auto adv = [&](int f) { return c.adv[f]; };
     auto db = [&](int j, int i) { return c.d1[F_SHIFT + i][j]; };  // d_j beta^i
     double S8tr = 0;
     for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) S8tr += c.G.gi[i][j] * s.Sij8[i][j];
@@ -672,9 +694,11 @@ void residual(const orc_params& P, const Conf& c, const double* v, double* R, Sr
 // [0] 8pi rho [1..3] 8pi S_i [4..9] 8pi S_ij [10] L_GB [11..16] d_t K_ij [17] d_t Pi
 // [18] |residual| after solve [19] solve status [20..25] R_ij + 2 D_(i Z_j) [26] its trace
 // [27] R [28..33] R_ij [34..36] Z^i [37] D^i D_i lapse [38..44] solve matrix diagonal
-int point_rhs(const orc_params& P, const double* v, const double* d1, const double* d2, double* rhs, double* diag) {
+// adv (optional): the advection terms beta^k d_k u of the 27 fields; null: centred, from d1.
+int point_rhs(const orc_params& P, const double* v, const double* d1, const double* d2, const double* adv, double* rhs,
+              double* diag) {
     static thread_local Conf c;
-    conf_setup(v, d1, d2, c);
+    conf_setup(v, d1, d2, adv, c);
     double zero[7] = {0, 0, 0, 0, 0, 0, 0}, R0[7], J[49], x[7];
     residual(P, c, zero, R0, nullptr, nullptr);
     double sc = 1.0;
@@ -716,7 +740,7 @@ int point_rhs(const orc_params& P, const double* v, const double* d1, const doub
 //   H = R + K^2 - K_ij K^ij - 16 pi rho,  M_i = D_j K^j_i - D_i K - 8 pi S_i
 void point_constraints(const orc_params& P, const double* v, const double* d1, const double* d2, double* out4) {
     static thread_local Conf c;
-    conf_setup(v, d1, d2, c);
+    conf_setup(v, d1, d2, nullptr, c);
     double u[3][3] = {{0}};
     Src s;
     sources(P, c.p, c.G, u, 0.0, s);
@@ -741,7 +765,7 @@ void point_constraints(const orc_params& P, const double* v, const double* d1, c
 // 8 pi rho of the X, g2 X^2 and Gauss-Bonnet terms at one point (independent of d_t K_ij, d_t Pi).
 void point_energy(const orc_params& P, const double* v, const double* d1, const double* d2, double* out3) {
     static thread_local Conf c;
-    conf_setup(v, d1, d2, c);
+    conf_setup(v, d1, d2, nullptr, c);
     double u[3][3] = {{0}};
     Src s;
     sources(P, c.p, c.G, u, 0.0, s);
@@ -763,46 +787,104 @@ struct Grid {
     }
 };
 
-// centred 4th-order stencils at ghosted point (i,j,k)
+// Difference weights of the two schemes ("Accuracy": 4th and 6th order), on offsets -r..r
+// (centred) or lo..lo+n-1 (lopsided, for beta >= 0), each sum divided by den dx (den dx^2 for the
+// second derivative). The box's ghost width chooses the scheme: ng = 3 -> 4th, ng = 4 -> 6th.
+struct Scheme {
+    int r;             // half-width of the centred stencils
+    double c1[7], c2[7], den1, den2;
+    int lo, nl;        // lopsided stencil: first offset and length
+    double cl[7], denl;
+    int rko;           // Kreiss-Oliger half-width; weights binomial, factor ko_sign sigma / (4^rko dx)
+    double cko[9], ko_sign, ko_div;
+};
+
+Scheme scheme(int ng) {
+    Scheme q;
+    if (ng == 4) {
+        q = {3, {-1, 9, -45, 0, 45, -9, 1}, {2, -27, 270, -490, 270, -27, 2}, 60.0, 180.0,
+             -2, 7, {2, -24, -35, 80, -30, 8, -1}, 60.0,
+             4, {1, -8, 28, -56, 70, -56, 28, -8, 1}, -1.0, 256.0};
+    } else {
+        q = {2, {1, -8, 0, 8, -1}, {-1, 16, -30, 16, -1}, 12.0, 12.0,
+             -1, 5, {-3, -10, 18, -6, 1}, 12.0,
+             3, {1, -6, 15, -20, 15, -6, 1}, 1.0, 64.0};
+    }
+    return q;
+}
+
+// centred stencils of the box's scheme at ghosted point (i,j,k); mixed derivatives are the
+// tensor product of two first-derivative stencils
 void point_derivs(const Grid& g, const double* s, double dx, int i, int j, int k, double* v, double* d1, double* d2) {
-    const double c1[4] = {1.0, -8.0, 8.0, -1.0};
-    const int off[4] = {-2, -1, 1, 2};
-    const double i12 = 1.0 / (12.0 * dx), i12s = 1.0 / (12.0 * dx * dx), i144 = 1.0 / (144.0 * dx * dx);
+    const Scheme q = scheme(g.ng);
+    const int n = 2 * q.r + 1;
+    const double i1 = 1.0 / (q.den1 * dx), i2 = 1.0 / (q.den2 * dx * dx), imx = 1.0 / (q.den1 * q.den1 * dx * dx);
     for (int f = 0; f < NF; ++f) {
         auto U = [&](int a, int b, int cc) { return s[g.at(f, i + a, j + b, k + cc)]; };
         v[f] = U(0, 0, 0);
         int e[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
         for (int d = 0; d < 3; ++d) {
-            double x = 0;
-            for (int m = 0; m < 4; ++m) x += c1[m] * U(off[m] * e[d][0], off[m] * e[d][1], off[m] * e[d][2]);
-            d1[f * 3 + d] = x * i12;
-            double y = -U(-2 * e[d][0], -2 * e[d][1], -2 * e[d][2]) + 16.0 * U(-e[d][0], -e[d][1], -e[d][2])
-                       - 30.0 * U(0, 0, 0) + 16.0 * U(e[d][0], e[d][1], e[d][2]) - U(2 * e[d][0], 2 * e[d][1], 2 * e[d][2]);
-            d2[f * 6 + SYM[d][d]] = y * i12s;
+            double x = 0, y = 0;
+            for (int m = 0; m < n; ++m) {
+                const int o = m - q.r;
+                x += q.c1[m] * U(o * e[d][0], o * e[d][1], o * e[d][2]);
+                y += q.c2[m] * U(o * e[d][0], o * e[d][1], o * e[d][2]);
+            }
+            d1[f * 3 + d] = x * i1;
+            d2[f * 6 + SYM[d][d]] = y * i2;
         }
         for (int d = 0; d < 3; ++d)
-            for (int q = d + 1; q < 3; ++q) {
+            for (int p = d + 1; p < 3; ++p) {
                 double x = 0;
-                for (int m = 0; m < 4; ++m)
-                    for (int n = 0; n < 4; ++n) {
+                for (int m = 0; m < n; ++m)
+                    for (int l = 0; l < n; ++l) {
                         int o[3] = {0, 0, 0};
-                        o[d] += off[m];
-                        o[q] += off[n];
-                        x += c1[m] * c1[n] * U(o[0], o[1], o[2]);
+                        o[d] += m - q.r;
+                        o[p] += l - q.r;
+                        x += q.c1[m] * q.c1[l] * U(o[0], o[1], o[2]);
                     }
-                d2[f * 6 + SYM[d][q]] = x * i144;
+                d2[f * 6 + SYM[d][p]] = x * imx;
             }
     }
 }
 
+// Lopsided advection terms adv[f] = sum_d beta^d D_d u_f at ghosted point (i,j,k): D_d is the
+// lopsided stencil of the box's scheme, biased towards +d where beta^d >= 0 and mirrored (offsets
+// negated, sum negated) where beta^d < 0.
+void point_adv_lopsided(const Grid& g, const double* s, double dx, int i, int j, int k, double* adv) {
+    const Scheme q = scheme(g.ng);
+    double beta[3];
+    for (int d = 0; d < 3; ++d) beta[d] = s[g.at(F_SHIFT + d, i, j, k)];
+    for (int f = 0; f < NF; ++f) {
+        double a = 0;
+        for (int d = 0; d < 3; ++d) {
+            const int sg = beta[d] >= 0.0 ? 1 : -1;
+            double x = 0;
+            for (int m = 0; m < q.nl; ++m) {
+                const int o = sg * (q.lo + m);
+                x += q.cl[m] * s[g.at(f, i + (d == 0 ? o : 0), j + (d == 1 ? o : 0), k + (d == 2 ? o : 0))];
+            }
+            a += beta[d] * (sg * x / (q.denl * dx));
+        }
+        adv[f] = a;
+    }
+}
+
+// Kreiss-Oliger difference sum_d Delta^(2 rko)_d u (unscaled)
 double ko_point(const Grid& g, const double* s, int f, int i, int j, int k) {
-    const double w[7] = {1, -6, 15, -20, 15, -6, 1};
+    const Scheme q = scheme(g.ng);
     double t = 0;
-    for (int m = 0; m < 7; ++m) {
-        int o = m - 3;
-        t += w[m] * (s[g.at(f, i + o, j, k)] + s[g.at(f, i, j + o, k)] + s[g.at(f, i, j, k + o)]);
+    for (int m = 0; m < 2 * q.rko + 1; ++m) {
+        int o = m - q.rko;
+        t += q.cko[m] * (s[g.at(f, i + o, j, k)] + s[g.at(f, i, j + o, k)] + s[g.at(f, i, j, k + o)]);
     }
     return t;
+}
+
+// sigma times the Kreiss-Oliger factor of the box's scheme
+double ko_factor(int ng, double sigma, double dx) {
+    const Scheme q = scheme(ng);
+    return q.ko_sign * sigma / (q.ko_div * dx);
 }
 
 void fill_periodic(const Grid& g, double* s) {
@@ -858,14 +940,15 @@ void fill_bc(const orc_box& b, const Grid& g, double* s) {
 int rhs_box(const orc_box& b, const orc_params& P, const double* s, double* rhs, int with_ko) {
     Grid g(b);
     int bad = 0;
-    const double ko = P.sigma_ko / (64.0 * b.dx);
+    const double ko = ko_factor(b.ng, P.sigma_ko, b.dx);
 #pragma omp parallel for collapse(2) schedule(dynamic) reduction(+ : bad)
     for (int k = g.ng; k < g.ng + g.nz; ++k)
         for (int j = g.ng; j < g.ng + g.ny; ++j)
             for (int i = g.ng; i < g.ng + g.nx; ++i) {
-                double v[NF], d1[NF * 3], d2[NF * 6], r[NF];
+                double v[NF], d1[NF * 3], d2[NF * 6], r[NF], adv[NF];
                 point_derivs(g, s, b.dx, i, j, k, v, d1, d2);
-                if (point_rhs(P, v, d1, d2, r, nullptr) != 0) bad++;
+                if (P.advection) point_adv_lopsided(g, s, b.dx, i, j, k, adv);
+                if (point_rhs(P, v, d1, d2, P.advection ? adv : nullptr, r, nullptr) != 0) bad++;
                 for (int f = 0; f < NF; ++f) {
                     double x = r[f];
                     if (with_ko) x += ko * ko_point(g, s, f, i, j, k);
@@ -903,7 +986,13 @@ void enforce(const Grid& g, const orc_params& P, double* s) {
 extern "C" {
 
 int orc_point_rhs(const orc_params* P, const double* v, const double* d1, const double* d2, double* rhs, double* diag) {
-    return point_rhs(*P, v, d1, d2, rhs, diag);
+    return point_rhs(*P, v, d1, d2, nullptr, rhs, diag);
+}
+
+// As orc_point_rhs with the 27 advection terms beta^k d_k u given (adv).
+int orc_point_rhs_adv(const orc_params* P, const double* v, const double* d1, const double* d2, const double* adv,
+                      double* rhs, double* diag) {
+    return point_rhs(*P, v, d1, d2, adv, rhs, diag);
 }
 
 void orc_point_constraints(const orc_params* P, const double* v, const double* d1, const double* d2, double* out4) {
@@ -947,6 +1036,13 @@ void orc_phys_sources(const orc_params* P, const double* phys, const double* u6,
     q += 6;
     p.Pi = *q++;
     for (int k = 0; k < 3; ++k) p.dPi[k] = *q++;
+    p.bdPi = 0;
+    for (int k = 0; k < 3; ++k) p.bdPi += p.beta[k] * p.dPi[k];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            p.bdK[i][j] = 0;
+            for (int k = 0; k < 3; ++k) p.bdK[i][j] += p.beta[k] * p.dK[k][i][j];
+        }
     Geo G;
     geometry(p, G);
     double u[3][3];
@@ -987,16 +1083,32 @@ void orc_derivs(const orc_box* b, const double* s, double* d1out, double* d2out)
             }
 }
 
+// Lopsided advection terms of every field at every interior point: adv[f][k][j][i].
+void orc_adv_lopsided(const orc_box* b, const double* s, double* out) {
+    Grid g(*b);
+    const long long npt = (long long)b->nx * b->ny * b->nz;
+#pragma omp parallel for collapse(2)
+    for (int k = 0; k < b->nz; ++k)
+        for (int j = 0; j < b->ny; ++j)
+            for (int i = 0; i < b->nx; ++i) {
+                double a[NF];
+                point_adv_lopsided(g, s, b->dx, i + g.ng, j + g.ng, k + g.ng, a);
+                long long p = ((long long)k * b->ny + j) * b->nx + i;
+                for (int f = 0; f < NF; ++f) out[f * npt + p] = a[f];
+            }
+}
+
 // rhs (ghosted layout) <- right-hand side at interior points, including KO dissipation.
 // The ghosts of s must be valid. Returns 0, or -5 if some point's linear solve was singular.
 int orc_rhs(const orc_box* b, const orc_params* P, const double* s, double* rhs, int with_ko) {
     return rhs_box(*b, *P, s, rhs, with_ko);
 }
 
-// rhs += sigma/(64 dx) sum_d Delta^6_d s on interior points (ghosts of s must be valid).
+// rhs += the box's scheme's Kreiss-Oliger term on interior points (ghosts of s must be valid):
+// sigma/(64 dx) sum_d Delta^6_d s (ng = 3) or -sigma/(256 dx) sum_d Delta^8_d s (ng = 4).
 void orc_ko(const orc_box* b, double sigma, const double* s, double* rhs) {
     Grid g(*b);
-    const double c = sigma / (64.0 * b->dx);
+    const double c = ko_factor(b->ng, sigma, b->dx);
 #pragma omp parallel for collapse(2)
     for (int k = g.ng; k < g.ng + g.nz; ++k)
         for (int j = g.ng; j < g.ng + g.ny; ++j)

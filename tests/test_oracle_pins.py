@@ -194,6 +194,169 @@ def test_ko_annihilates_quintics_and_damps_nyquist(orc):
     np.testing.assert_allclose(b.interior(r), -0.3 / b.dx * b.interior(s), rtol=0, atol=1e-12)
 
 
+# ----------------------------------------------------------------------------- 6th order, lopsided advection
+# ("Accuracy": 4th- and 6th-order stencils.) A box with 4 ghost layers takes the 6th-order scheme.
+NYQ_LOPSIDED = {3: -32.0 / 12.0, 4: -128.0 / 60.0}     # symbol of the lopsided stencil at the Nyquist mode
+NYQ_SECOND = {3: -64.0 / 12.0, 4: -1088.0 / 180.0}     # ... of the centred second derivative
+
+
+def test_sixth_order_stencils_exact_on_sextic_polynomials(orc):
+    """With ng = 4 the first, second and mixed stencils are exact on every monomial of total
+    degree <= 6. Catches a wrong 6th-order weight, a wrong 1/(60 dx), 1/(180 dx^2) or
+    1/(3600 dx^2) scale, or a stencil still of 4th order (not exact on degree 5 and 6)."""
+    b = gi.Box(6, 5, 5, 0.3, -0.4, 0.2, 0.5, bc=gi.BC_FROZEN, ng=4)
+    X, Y, Z = b.coords()
+    rng = np.random.default_rng(11)
+    s = np.zeros(b.shape)
+    coefs = []
+    for f in range(27):
+        coef = rng.uniform(-1, 1, 84)
+        coefs.append(coef)
+        s[f], terms = _poly(X, Y, Z, coef, 6)
+    d1, d2 = orc.derivs(b, s)
+    Xi, Yi, Zi = (b.interior(a) for a in (X, Y, Z))
+    for f in range(27):
+        for d in range(3):
+            o = [0, 0, 0]
+            o[d] = 1
+            ex = _poly_deriv(Xi, Yi, Zi, coefs[f], terms, o)
+            assert np.max(np.abs(d1[f, d] - ex)) <= 1e-11 * max(1.0, np.max(np.abs(ex)))
+        for m, (p, q) in enumerate(an.SYM_PAIRS):
+            o = [0, 0, 0]
+            o[p] += 1
+            o[q] += 1
+            ex = _poly_deriv(Xi, Yi, Zi, coefs[f], terms, o)
+            assert np.max(np.abs(d2[f, m] - ex)) <= 1e-10 * max(1.0, np.max(np.abs(ex)))
+
+
+def test_sixth_order_stencils_converge_at_sixth_order(orc):
+    """Halving dx on a smooth periodic field divides the 6th-order first/second/mixed derivative
+    errors by ~64."""
+    errs = []
+    for n in (16, 32):
+        b = gi.Box(n, n, n, 2.0 / n, 1.0 / n, 1.0 / n, 1.0 / n, ng=4)
+        X, Y, Z = b.coords()
+        k = math.pi
+        s = np.zeros(b.shape)
+        s[0] = np.sin(k * X) * np.cos(k * Y) * np.sin(k * Z + 0.3)
+        orc.fill_ghosts(b, s)
+        d1, d2 = orc.derivs(b, s)
+        Xi, Yi, Zi = (b.interior(a) for a in (X, Y, Z))
+        ex_x = k * np.cos(k * Xi) * np.cos(k * Yi) * np.sin(k * Zi + 0.3)
+        ex_xx = -k * k * np.sin(k * Xi) * np.cos(k * Yi) * np.sin(k * Zi + 0.3)
+        ex_xy = -k * k * np.cos(k * Xi) * np.sin(k * Yi) * np.sin(k * Zi + 0.3)
+        errs.append([np.max(np.abs(d1[0, 0] - ex_x)), np.max(np.abs(d2[0, 0] - ex_xx)),
+                     np.max(np.abs(d2[0, 1] - ex_xy))])
+    ratios = np.array(errs[0]) / np.array(errs[1])
+    assert np.all(ratios > 56.0) and np.all(ratios < 72.0), ratios
+
+
+def test_ko8_annihilates_septics_and_damps_nyquist(orc):
+    """The 6th-order scheme's dissipation -sigma/(256 dx) sum_d Delta^8_d u is zero on degree-7
+    polynomials and gives exactly -sigma/dx * u per direction on the Nyquist mode. Catches the
+    anti-damping sign (Delta^8 is positive on that mode), a missing 1/256 or wrong binomials."""
+    b = gi.Box(6, 5, 5, 0.25, 0.1, -0.3, 0.2, bc=gi.BC_FROZEN, ng=4)
+    X, Y, Z = b.coords()
+    rng = np.random.default_rng(8)
+    s = np.zeros(b.shape)
+    for f in range(27):
+        s[f], _ = _poly(X, Y, Z, rng.uniform(-1, 1, 120), 7)
+    r = orc.ko(b, 0.3, s)
+    assert np.max(np.abs(b.interior(r))) < 1e-8
+    for axis in range(3):
+        idx = np.indices(b.shape[1:])[2 - axis]
+        s = np.zeros(b.shape)
+        s[:] = np.where(idx % 2 == 0, 1.0, -1.0)
+        r = orc.ko(b, 0.3, s)
+        np.testing.assert_allclose(b.interior(r), -0.3 / b.dx * b.interior(s), rtol=0, atol=1e-12)
+
+
+def _nyquist_scalar(ng, axis, shift):
+    """Flat slice, constant shift component `shift` along `axis`, Pi = 0 and phi = 1e-3 (-1)^i
+    along that axis (the grid's Nyquist mode), on all points including the ghosts."""
+    b = gi.Box(6, 6, 6, 0.2, 0.0, 0.0, 0.0, bc=gi.BC_FROZEN, ng=ng)
+    s = gi.flat_state(b)
+    idx = np.indices(b.shape[1:])[2 - axis]
+    s[25] = 1e-3 * np.where(idx % 2 == 0, 1.0, -1.0)
+    s[19 + axis] = shift
+    return b, s
+
+
+@pytest.mark.parametrize("ng", [3, 4])
+@pytest.mark.parametrize("axis", [0, 1])
+@pytest.mark.parametrize("shift", [0.3, -0.45])
+def test_lopsided_advection_damps_the_nyquist_mode(orc, ng, axis, shift):
+    """On the Nyquist mode the centred first derivative vanishes, so with centred advection
+    d_t phi = 0; the lopsided stencil, biased towards the side the shift points to, damps it:
+    d_t phi = -|beta| c / dx phi with c = 8/3 (4th order) or 32/15 (6th order), for either sign
+    of the shift. A stencil biased the wrong way gives +|beta| c / dx (growth). d_t Pi is the
+    centred second derivative: -16/3 / dx^2 phi (4th order), -272/45 / dx^2 phi (6th order)."""
+    b, s = _nyquist_scalar(ng, axis, shift)
+    zero = P(lam=0.0, g2=0.0)
+    r0 = orc.rhs(b, zero, s, with_ko=False)
+    rl = orc.rhs(b, P(lam=0.0, g2=0.0, advection=1), s, with_ko=False)
+    phi = b.interior(s)[25]
+    assert np.max(np.abs(b.interior(r0)[25])) < 1e-15
+    np.testing.assert_allclose(b.interior(rl)[25], NYQ_LOPSIDED[ng] * abs(shift) / b.dx * phi, rtol=1e-12, atol=0)
+    for r in (r0, rl):
+        np.testing.assert_allclose(b.interior(r)[26], NYQ_SECOND[ng] / b.dx ** 2 * phi, rtol=1e-12, atol=0)
+        others = np.delete(b.interior(r), [25, 26], axis=0)   # zero up to the solve's rounding
+        assert np.max(np.abs(others)) < 1e-13 * np.max(np.abs(b.interior(r)[26]))
+
+
+@pytest.mark.parametrize("ng,deg", [(3, 4), (4, 6)])
+def test_lopsided_equals_centred_on_polynomial_data(orc, ng, deg):
+    """Both stencils are exact on polynomials of degree <= the scheme's order, so on a state whose
+    27 fields are such polynomials (a perturbed flat slice with a shift that changes sign inside
+    the box, couplings on) the lopsided and centred right-hand sides agree to rounding. Catches a
+    wrong lopsided weight, scale or offset, and a wrong chain rule of the shift-contracted
+    derivative of K_ij inside the coupled system."""
+    b = gi.Box(5, 5, 4, 0.25, -0.5, -0.45, -0.4, bc=gi.BC_FROZEN, ng=ng)
+    X, Y, Z = b.coords()
+    rng = np.random.default_rng(20 + ng)
+    nterm = len(_poly(X, Y, Z, np.zeros(200), deg)[1])
+    s = gi.flat_state(b)
+    for f in range(27):
+        amp = 0.3 if f in (19, 20, 21, 25, 26) else 0.02
+        s[f] += _poly(X, Y, Z, amp * rng.uniform(-1, 1, nterm), deg)[0]
+    for f in range(19, 22):
+        s[f] += 0.4 * (X, Y, Z)[f - 19]   # sign changes across the box
+    p = dict(lam=0.3, g2=0.2, beta_kind=1)
+    rc = b.interior(orc.rhs(b, P(**p), s, with_ko=False))
+    rl = b.interior(orc.rhs(b, P(advection=1, **p), s, with_ko=False))
+    scale = np.maximum(np.max(np.abs(rc), axis=(1, 2, 3)), 1e-3)
+    err = np.max(np.abs(rl - rc), axis=(1, 2, 3)) / scale
+    assert np.max(err) < 1e-11, err
+    adv = orc.adv_lopsided(b, s)
+    assert np.any(b.interior(s)[19] > 0) and np.any(b.interior(s)[19] < 0)
+    assert np.all(np.isfinite(adv))
+
+
+@pytest.mark.parametrize("ng,ratio", [(3, 16.0), (4, 64.0)])
+def test_lopsided_advection_converges_at_the_scheme_order(orc, ng, ratio):
+    """beta^k d_k u with the lopsided stencils, on smooth periodic fields and a shift of either
+    sign, converges to the exact value with the scheme's order (error ratio ~2^order)."""
+    errs = []
+    for n in (16, 32):
+        b = gi.Box(n, n, n, 2.0 / n, 1.0 / n, 1.0 / n, 1.0 / n, ng=ng)
+        X, Y, Z = b.coords()
+        k = math.pi
+        s = gi.flat_state(b)
+        s[0] = 1.0 + 0.1 * np.sin(k * X) * np.cos(k * Y) * np.sin(k * Z + 0.3)
+        s[19] = 0.5 * np.sin(k * Y + 0.2)
+        s[20] = 0.5 * np.cos(k * Z)
+        s[21] = 0.5 * np.sin(k * X - 0.4)
+        orc.fill_ghosts(b, s)
+        adv = orc.adv_lopsided(b, s)
+        Xi, Yi, Zi = (b.interior(a) for a in (X, Y, Z))
+        ex = 0.1 * k * (0.5 * np.sin(k * Yi + 0.2) * np.cos(k * Xi) * np.cos(k * Yi) * np.sin(k * Zi + 0.3)
+                        - 0.5 * np.cos(k * Zi) * np.sin(k * Xi) * np.sin(k * Yi) * np.sin(k * Zi + 0.3)
+                        + 0.5 * np.sin(k * Xi - 0.4) * np.sin(k * Xi) * np.cos(k * Yi) * np.cos(k * Zi + 0.3))
+        errs.append(np.max(np.abs(adv[0] - ex)))
+    r = errs[0] / errs[1]
+    assert 0.8 * ratio < r < 1.25 * ratio, errs
+
+
 # ----------------------------------------------------------------------------- P9 solve
 def test_full_pivot_solve(orc):
     """The long-double full-pivot elimination solves random systems (residual < 1e-14 relative,
