@@ -41,7 +41,7 @@ typedef struct CUstream_st* grf_stream_t; /* same type as cudaStream_t */
 
 enum {
     GRF_OK = 0,
-    GRF_EINVAL = -1,       /* bad sizes, null pointers, ng != 3, pitch too small */
+    GRF_EINVAL = -1,       /* bad sizes, null pointers, ng not 3 or 4, pitch too small */
     GRF_EWORKSPACE = -2,   /* ws too small or misaligned */
     GRF_ECUDA = -3,        /* a CUDA call failed; see grf_last_cuda_error() */
     GRF_ENONFINITE = -4,   /* non-finite value found by grf_check_finite() */
@@ -54,10 +54,17 @@ enum { GRF_BC_PERIODIC = 0, GRF_BC_FROZEN = 1, GRF_BC_REFLECT_LOW = 2 };
 enum { GRF_BETA_LINEAR = 0, GRF_BETA_QUADRATIC = 1 };
 enum { GRF_OP_RHS = 0, GRF_OP_RK4 = 1, GRF_OP_CONSTRAINTS = 2 };
 
-/* Grid box. Points sit at x = x0 + (i - ng) dx (ghosted index i); ng must be 3. */
+/* Grid box. Points sit at x = x0 + (i - ng) dx (ghosted index i). The ghost width chooses the
+ * finite-difference scheme ("Accuracy": 4th- and 6th-order stencils):
+ *   ng = 3: centred 4th-order first / second / mixed differences, Kreiss-Oliger dissipation
+ *           sigma/(64 dx) sum_d Delta^6_d, lopsided advection on offsets -1..3;
+ *   ng = 4: centred 6th-order differences, dissipation -sigma/(256 dx) sum_d Delta^8_d,
+ *           lopsided advection on offsets -2..4.
+ * 4-ghost boxes are accepted by grf_rhs, grf_rk4_step(_noalloc), grf_constraints,
+ * grf_energy_densities, grf_ko_dissipation, grf_fill_ghosts and grf_check_finite. */
 typedef struct {
-    int nx, ny, nz;       /* interior points per axis, each >= 1 (periodic: >= 3) */
-    int ng;               /* ghost layers: must be 3 */
+    int nx, ny, nz;       /* interior points per axis, each >= 1 (periodic, mirror: >= ng) */
+    int ng;               /* ghost layers: 3 or 4 (above) */
     double dx;            /* grid spacing, > 0 */
     double x0, y0, z0;    /* coordinates of interior point (0,0,0) */
     int bc;               /* GRF_BC_PERIODIC: ghosts refilled by periodic wrap;
@@ -65,7 +72,7 @@ typedef struct {
                              GRF_BC_REFLECT_LOW: the three low faces are mirror planes (half a
                              cell below the first point; "Boundary Conditions", reflective),
                              their ghosts rebuilt from the interior with each component's
-                             parity; ghosts on the high faces are read as given. Needs n >= 3.
+                             parity; ghosts on the high faces are read as given. Needs n >= ng.
                              Not accepted by grf_batched_rk4 and grf_tlm_rk4. */
     long long pitch;      /* doubles per x row, >= nx + 2 ng */
 } grf_box;
@@ -84,6 +91,11 @@ typedef struct {
     int decoupled;                   /* 0: full 4dST; 1: without backreaction onto the metric
                                         ("Key features"): the metric evolves by vacuum CCZ4 in the
                                         same gauge, the scalar by its full equation on that metric */
+    int advection;                   /* 0: centred differences in the advection terms beta^k d_k u;
+                                        1: lopsided differences, one point further towards the side
+                                        beta^k points to (every beta^k d_k of an evolved field, those
+                                        inside the coupled 4dST system included). 1 is not accepted by
+                                        grf_batched_rk4 and grf_tlm_rk4 */
 } grf_params;
 
 /* d_t of all 27 fields at the interior points of `state` (modified CCZ4 + 4dST, section
@@ -127,8 +139,8 @@ int grf_rk4_step(const grf_box* box, const grf_params* params, double* state, do
  * copies are staged by the driver and overlap the kernels poorly.
  * The first call on a device creates that device's copy stream and events (no memory is
  * allocated); make it before any stream capture. Calls from several host threads are
- * serialised while they queue work. Errors: GRF_EINVAL (box, params, null pointers, nsteps < 0),
- * GRF_EWORKSPACE, GRF_ECUDA. */
+ * serialised while they queue work. Errors: GRF_EINVAL (box, params, null pointers, nsteps < 0,
+ * ng = 4: the slab pipeline is laid out for 3 ghost layers), GRF_EWORKSPACE, GRF_ECUDA. */
 int grf_rk4_step_host(const grf_box* box, const grf_params* params, const double* host_in,
                       double* host_out, double* state, double dt, int nsteps, void* ws,
                       size_t ws_bytes, grf_stream_t stream);

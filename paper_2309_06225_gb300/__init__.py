@@ -39,7 +39,8 @@ class grf_params(C.Structure):
                 ("shift_F", C.c_double), ("eta", C.c_double), ("a0", C.c_double), ("b0", C.c_double),
                 ("lambda_", C.c_double), ("g2", C.c_double), ("sigma_ko", C.c_double),
                 ("min_chi", C.c_double), ("min_lapse", C.c_double),
-                ("beta_kind", C.c_int), ("enforce_algebraic", C.c_int), ("decoupled", C.c_int)]
+                ("beta_kind", C.c_int), ("enforce_algebraic", C.c_int), ("decoupled", C.c_int),
+                ("advection", C.c_int)]
 
 
 GRF_BATCH_GRAPH, GRF_BATCH_PERSISTENT, GRF_BATCH_STREAM = 1, 2, 3
@@ -113,30 +114,31 @@ def lib():
 
 
 # ------------------------------------------------------------------------------ marshalling
-def pitch_for(nx):
-    """Row pitch in doubles: nx + 6 rounded up to a multiple of 4 (32-byte rows)."""
-    return ((nx + 2 * NG + 3) // 4) * 4
+def pitch_for(nx, ng=NG):
+    """Row pitch in doubles: nx + 2 ng rounded up to a multiple of 4 (32-byte rows)."""
+    return ((nx + 2 * ng + 3) // 4) * 4
 
 
-def make_box(nx, ny, nz, dx, x0=0.0, y0=0.0, z0=0.0, bc=GRF_BC_PERIODIC, pitch=None) -> grf_box:
-    return grf_box(int(nx), int(ny), int(nz), NG, float(dx), float(x0), float(y0), float(z0), int(bc),
-                   int(pitch if pitch is not None else pitch_for(nx)))
+def make_box(nx, ny, nz, dx, x0=0.0, y0=0.0, z0=0.0, bc=GRF_BC_PERIODIC, pitch=None, ng=NG) -> grf_box:
+    """ng = 3: 4th-order scheme, ng = 4: 6th-order scheme."""
+    return grf_box(int(nx), int(ny), int(nz), int(ng), float(dx), float(x0), float(y0), float(z0), int(bc),
+                   int(pitch if pitch is not None else pitch_for(nx, ng)))
 
 
 def box_like(b, pitch=None) -> grf_box:
-    """grf_box from any object with nx, ny, nz, dx, x0, y0, z0, bc attributes."""
-    return make_box(b.nx, b.ny, b.nz, b.dx, b.x0, b.y0, b.z0, b.bc, pitch)
+    """grf_box from any object with nx, ny, nz, dx, x0, y0, z0, bc (and optionally ng) attributes."""
+    return make_box(b.nx, b.ny, b.nz, b.dx, b.x0, b.y0, b.z0, b.bc, pitch, int(getattr(b, "ng", NG)))
 
 
 def params_like(p) -> grf_params:
     """grf_params from any object with the parameter attributes (lambda under `lam`)."""
     return grf_params(p.kappa1, p.kappa2, p.kappa3, p.shift_F, p.eta, p.a0, p.b0, p.lam, p.g2, p.sigma_ko,
                       p.min_chi, p.min_lapse, int(p.beta_kind), int(p.enforce_algebraic),
-                      int(getattr(p, "decoupled", 0)))
+                      int(getattr(p, "decoupled", 0)), int(getattr(p, "advection", 0)))
 
 
 def state_shape(box: grf_box, nfields=NFIELDS):
-    return (nfields, box.nz + 2 * NG, box.ny + 2 * NG, box.pitch)
+    return (nfields, box.nz + 2 * box.ng, box.ny + 2 * box.ng, box.pitch)
 
 
 def _torch():
@@ -150,9 +152,9 @@ def alloc_state(box: grf_box, nfields=NFIELDS, device="cuda"):
 
 
 def to_device(state_np, box: grf_box, device="cuda", out=None):
-    """Copies a (27, nz+6, ny+6, nx+6) numpy array into a padded device tensor."""
+    """Copies a (27, nz + 2 ng, ny + 2 ng, nx + 2 ng) numpy array into a padded device tensor."""
     torch = _torch()
-    nxg = box.nx + 2 * NG
+    nxg = box.nx + 2 * box.ng
     if out is None:
         out = alloc_state(box, state_np.shape[0], device)
     out[..., :nxg].copy_(torch.from_numpy(np.ascontiguousarray(state_np)))
@@ -160,7 +162,7 @@ def to_device(state_np, box: grf_box, device="cuda", out=None):
 
 
 def to_host(t, box: grf_box):
-    return t[..., :box.nx + 2 * NG].cpu().numpy()
+    return t[..., :box.nx + 2 * box.ng].cpu().numpy()
 
 
 def alloc_workspace(nbytes, device="cuda"):

@@ -6,7 +6,7 @@
 #include <mutex>
 
 #include "grf.h"
-#include "grf_kernels.cuh"
+#include "grf_kernels6.cuh"
 #include "grf_launch.h"
 
 namespace grf {
@@ -20,13 +20,22 @@ __global__ void ko_kernel(Geom g, const double* __restrict__ s, double* __restri
     for (int f = 0; f < NFIELDS; ++f) rhs[f * g.fstride + p] += ko * ko6(s + f * g.fstride, p, g.pitch, g.plane);
 }
 
+// The 6th-order scheme's dissipation: rhs += ko sum_d Delta^8_d u (ko = -sigma / (256 dx)).
+__global__ void ko8_kernel(Geom g, const double* __restrict__ s, double* __restrict__ rhs, double ko) {
+    int i, j, k;
+    if (!interior_thread(g, i, j, k)) return;
+    const long long p = gidx(g, i + NG6, j + NG6, k + NG6);
+    for (int f = 0; f < NFIELDS; ++f) rhs[f * g.fstride + p] += ko * ko8(s + f * g.fstride, p, g.pitch, g.plane);
+}
+
 // Periodic ghost fill: one thread per ghosted (i, j) column and field; walks k.
 __global__ void ghost_fill_kernel(Geom g, double* __restrict__ s) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int f = blockIdx.z;
     if (i >= g.NX || j >= g.NY) return;
-    auto wrap = [](int a, int n) { int x = (a - NG) % n; if (x < 0) x += n; return x + NG; };
+    const int ng = g.ng;
+    auto wrap = [ng](int a, int n) { int x = (a - ng) % n; if (x < 0) x += n; return x + ng; };
     const int wi = wrap(i, g.nx), wj = wrap(j, g.ny);
     const bool ghost_ij = (wi != i) || (wj != j);
     double* u = s + f * g.fstride;
@@ -44,14 +53,15 @@ __global__ void reflect_fill_kernel(Geom g, double* __restrict__ s) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int f = blockIdx.z;
-    if (i >= g.nx + NG || j >= g.ny + NG) return;
+    const int ng = g.ng;
+    if (i >= g.nx + ng || j >= g.ny + ng) return;
     double* u = s + (long long)f * g.fstride;
-    const int a = i < NG ? 2 * NG - 1 - i : i, b = j < NG ? 2 * NG - 1 - j : j;
-    const int mij = (i < NG ? 1 : 0) | (j < NG ? 2 : 0);
-    for (int k = 0; k < g.nz + NG; ++k) {
-        const int m = mij | (k < NG ? 4 : 0);
+    const int a = i < ng ? 2 * ng - 1 - i : i, b = j < ng ? 2 * ng - 1 - j : j;
+    const int mij = (i < ng ? 1 : 0) | (j < ng ? 2 : 0);
+    for (int k = 0; k < g.nz + ng; ++k) {
+        const int m = mij | (k < ng ? 4 : 0);
         if (m == 0) continue;
-        u[gidx(g, i, j, k)] = mirror_sign(f, m) * u[gidx(g, a, b, k < NG ? 2 * NG - 1 - k : k)];
+        u[gidx(g, i, j, k)] = mirror_sign(f, m) * u[gidx(g, a, b, k < ng ? 2 * ng - 1 - k : k)];
     }
 }
 
@@ -151,7 +161,7 @@ __global__ void norms_final_kernel(const double* __restrict__ part, long long nb
 __global__ void finite_kernel(Geom g, const double* __restrict__ s, int* flag) {
     int i, j, k;
     if (!interior_thread(g, i, j, k)) return;
-    const long long p = gidx(g, i + NG, j + NG, k + NG);
+    const long long p = gidx(g, i + g.ng, j + g.ng, k + g.ng);
     for (int f = 0; f < NFIELDS; ++f)
         if (!isfinite(s[f * g.fstride + p])) { atomicOr(flag, 1); return; }
 }
@@ -178,17 +188,18 @@ int check_launch() {
 
 bool box_ok(const grf_box* b) {
     if (!b) return false;
-    if (b->ng != 3 || b->nx < 1 || b->ny < 1 || b->nz < 1 || !(b->dx > 0.0)) return false;
-    if (b->pitch < (long long)b->nx + 6) return false;
+    if ((b->ng != NG && b->ng != NG6) || b->nx < 1 || b->ny < 1 || b->nz < 1 || !(b->dx > 0.0)) return false;
+    if (b->pitch < (long long)b->nx + 2 * b->ng) return false;
     if (b->bc != GRF_BC_PERIODIC && b->bc != GRF_BC_FROZEN && b->bc != GRF_BC_REFLECT_LOW) return false;
-    if (b->bc != GRF_BC_FROZEN && (b->nx < 3 || b->ny < 3 || b->nz < 3)) return false;
+    if (b->bc != GRF_BC_FROZEN && (b->nx < b->ng || b->ny < b->ng || b->nz < b->ng)) return false;
     return true;
 }
 
 Geom make_geom(const grf_box* b) {
     Geom g;
     g.nx = b->nx; g.ny = b->ny; g.nz = b->nz;
-    g.NX = b->nx + 6; g.NY = b->ny + 6; g.NZ = b->nz + 6;
+    g.NX = b->nx + 2 * b->ng; g.NY = b->ny + 2 * b->ng; g.NZ = b->nz + 2 * b->ng;
+    g.ng = b->ng;
     g.pitch = b->pitch;
     g.plane = b->pitch * g.NY;
     g.fstride = g.plane * g.NZ;
@@ -202,7 +213,15 @@ bool params_ok(const grf_params* p) {
     if (!p) return false;
     if (p->beta_kind != GRF_BETA_LINEAR && p->beta_kind != GRF_BETA_QUADRATIC) return false;
     if (!(1.0 + p->a0 > 0.0) || !(1.0 + p->b0 > 0.0)) return false;
+    if (p->advection != 0 && p->advection != 1) return false;
     return true;
+}
+
+// sigma times the dissipation factor of the box's scheme: sigma / (64 dx) with the 6th difference
+// (4th order), -sigma / (256 dx) with the 8th difference (6th order); both damp the grid's
+// Nyquist mode at sigma / dx per direction.
+double ko_factor(const Geom& g, double sigma) {
+    return g.ng == NG6 ? -sigma / (256.0 * g.dx) : sigma / (64.0 * g.dx);
 }
 
 Coeffs make_coeffs(const grf_params* p) {
@@ -215,6 +234,7 @@ Coeffs make_coeffs(const grf_params* p) {
     c.bTh = 1.0 / (2.0 * (1.0 + p->b0));
     c.beta_kind = p->beta_kind;
     c.decoupled = p->decoupled;
+    c.advection = p->advection;
     return c;
 }
 
@@ -231,9 +251,9 @@ dim3 interior_grid(const Geom& g) {
 // faster; 100^3 folded to rows of 4 ran 3% slower than unfolded).
 // Folding also cuts the number of blocks, so it is used only when the folded grid still fills
 // at least one wave of resident blocks (3 per SM); a smaller box ran 10% slower folded (13^3).
-int fold_width(const Geom& g) {
+int fold_width(const Geom& g, const grf_params* p) {
     const int nx = g.nx;
-    if (nx % 32 == 0) return 32;
+    if (nx % 32 == 0 || g.ng != NG || p->advection) return 32;  // the folded kernel: 4th order, centred
     int sms = 0, dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();
@@ -267,7 +287,7 @@ int* status_ptr() {
 
 int fill_ghosts(const Geom& g, double* s, cudaStream_t st) {
     if (g.reflect) {
-        dim3 blk(32, 8, 1), grd((g.nx + NG + 31) / 32, (g.ny + NG + 7) / 8, NFIELDS);
+        dim3 blk(32, 8, 1), grd((g.nx + g.ng + 31) / 32, (g.ny + g.ng + 7) / 8, NFIELDS);
         reflect_fill_kernel<<<grd, blk, 0, st>>>(g, s);
         return check_launch();
     }
@@ -439,7 +459,7 @@ int grf_rhs(const grf_box* box, const grf_params* params, double* state, double*
     cudaStream_t st = (cudaStream_t)stream;
     int r = fill_ghosts(g, state, st);
     if (r) return r;
-    launch_rhs(interior_grid(g), kBlock, st, g, make_coeffs(params), state, rhs, params->sigma_ko / (64.0 * box->dx),
+    launch_rhs(interior_grid(g), kBlock, st, g, make_coeffs(params), state, rhs, ko_factor(g, params->sigma_ko),
                status_ptr());
     return check_launch();
 }
@@ -447,7 +467,10 @@ int grf_rhs(const grf_box* box, const grf_params* params, double* state, double*
 int grf_ko_dissipation(const grf_box* box, double sigma, const double* state, double* rhs_accum, grf_stream_t stream) {
     if (!box_ok(box) || !state || !rhs_accum) return GRF_EINVAL;
     Geom g = make_geom(box);
-    ko_kernel<<<interior_grid(g), kBlock, 0, (cudaStream_t)stream>>>(g, state, rhs_accum, sigma / (64.0 * box->dx));
+    if (g.ng == NG6)
+        ko8_kernel<<<interior_grid(g), kBlock, 0, (cudaStream_t)stream>>>(g, state, rhs_accum, ko_factor(g, sigma));
+    else
+        ko_kernel<<<interior_grid(g), kBlock, 0, (cudaStream_t)stream>>>(g, state, rhs_accum, ko_factor(g, sigma));
     return check_launch();
 }
 
@@ -472,13 +495,13 @@ int grf_rk4_step(const grf_box* box, const grf_params* params, double* state, do
     const Coeffs c = make_coeffs(params);
     StageArgs a;
     a.dt = dt;
-    a.ko = params->sigma_ko / (64.0 * box->dx);
+    a.ko = ko_factor(g, params->sigma_ko);
     a.min_chi = params->min_chi;
     a.min_lapse = params->min_lapse;
     a.enforce = params->enforce_algebraic;
     a.status = status_ptr();
     a.k0 = 0;
-    a.fold = fold_width(g);
+    a.fold = fold_width(g, params);
     a.un = state;
     a.acc = acc;
     const dim3 grd = stage_grid(g, g.nz, a.fold);
@@ -500,6 +523,7 @@ int grf_rk4_step(const grf_box* box, const grf_params* params, double* state, do
 int grf_rk4_step_host(const grf_box* box, const grf_params* params, const double* host_in, double* host_out,
                       double* state, double dt, int nsteps, void* ws, size_t ws_bytes, grf_stream_t stream) {
     if (!box_ok(box) || !params_ok(params) || !host_in || !host_out || !state || nsteps < 0) return GRF_EINVAL;
+    if (box->ng != NG) return GRF_EINVAL;  // the slab pipeline is laid out for 3 ghost layers
     Geom g = make_geom(box);
     const size_t sb = state_bytes(g);
     if (!ws || ws_bytes < 3 * sb || ((uintptr_t)ws & 255)) return GRF_EWORKSPACE;
@@ -540,14 +564,14 @@ int grf_rk4_step_host(const grf_box* box, const grf_params* params, const double
     const Coeffs c = make_coeffs(params);
     StageArgs a;
     a.dt = dt;
-    a.ko = params->sigma_ko / (64.0 * box->dx);
+    a.ko = ko_factor(g, params->sigma_ko);
     a.min_chi = params->min_chi;
     a.min_lapse = params->min_lapse;
     a.enforce = params->enforce_algebraic;
     a.status = status_ptr();
     a.un = state;
     a.acc = acc;
-    a.fold = fold_width(g);
+    a.fold = fold_width(g, params);
     const dim3 full = stage_grid(g, g.nz, a.fold);
     auto slab_grid = [&](int s) { return stage_grid(g, hi(s) - lo(s), a.fold); };
     const dim3 gblk(32, 8, 1), ggrd((g.NX + 31) / 32, (g.NY + 7) / 8, NFIELDS);

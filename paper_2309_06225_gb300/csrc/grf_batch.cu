@@ -205,6 +205,7 @@ Geom geom_of(const grf_box* b) {
     Geom g;
     g.nx = b->nx; g.ny = b->ny; g.nz = b->nz;
     g.NX = b->nx + 6; g.NY = b->ny + 6; g.NZ = b->nz + 6;
+    g.ng = NG;
     g.pitch = b->pitch;
     g.plane = b->pitch * g.NY;
     g.fstride = g.plane * g.NZ;
@@ -347,6 +348,7 @@ int grf_batched_rk4(const grf_batch_item* items, int nitems, const grf_params* p
         const grf_params* p = &params[pi];
         if (p->beta_kind != GRF_BETA_LINEAR && p->beta_kind != GRF_BETA_QUADRATIC) return GRF_EINVAL;
         if (!(1.0 + p->a0 > 0.0) || !(1.0 + p->b0 > 0.0)) return GRF_EINVAL;
+        if (p->advection != 0) return GRF_EINVAL;  // centred advection only
     }
     const Layout L = layout(items, nitems, cfg);
     DBG("entry: %d boxes, %lld tiles, ws %zu of %zu bytes, variant %d, tile %dx%dx%d", nitems, L.ntiles, ws_bytes,

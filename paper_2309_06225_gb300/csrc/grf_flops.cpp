@@ -98,6 +98,7 @@ int grf_count_point_ops(const grf_params* p, const double* v, const double* d1, 
     c.kappa1 = p->kappa1; c.kappa2 = p->kappa2; c.kappa3 = p->kappa3; c.shift_F = p->shift_F; c.eta = p->eta;
     c.lam = p->lambda; c.g2 = p->g2; c.inv_1pa = 1.0 / (1.0 + p->a0); c.a_1pa = p->a0 / (1.0 + p->a0);
     c.bK = 3.0 * p->b0 / (4.0 * (1.0 + p->b0)); c.bTh = 1.0 / (2.0 * (1.0 + p->b0)); c.beta_kind = p->beta_kind; c.decoupled = p->decoupled;
+    c.advection = 0;  // operation counts of the centred-advection instance
     CD rhs[grf::NFIELDS];
     grf::PointExtraT<CD> ex;
     bool ok = true;
@@ -124,6 +125,7 @@ int grf_host_point_rhs(const grf_params* p, const double* v, const double* d1, c
     c.kappa1 = p->kappa1; c.kappa2 = p->kappa2; c.kappa3 = p->kappa3; c.shift_F = p->shift_F; c.eta = p->eta;
     c.lam = p->lambda; c.g2 = p->g2; c.inv_1pa = 1.0 / (1.0 + p->a0); c.a_1pa = p->a0 / (1.0 + p->a0);
     c.bK = 3.0 * p->b0 / (4.0 * (1.0 + p->b0)); c.bTh = 1.0 / (2.0 * (1.0 + p->b0)); c.beta_kind = p->beta_kind; c.decoupled = p->decoupled;
+    c.advection = 0;  // operation counts of the centred-advection instance
     grf::PointExtraT<double> ex;
     bool ok = true;
     grf::point_rhs(c, in, rhs, &ex, ok);

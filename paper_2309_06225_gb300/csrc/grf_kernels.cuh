@@ -10,16 +10,17 @@ namespace grf {
 
 struct Geom {
     int nx, ny, nz;          // interior points
-    int NX, NY, NZ;          // ghosted extents (n + 6)
+    int NX, NY, NZ;          // ghosted extents (n + 2 ng)
     long long pitch;         // doubles per x row
     long long plane;         // pitch * NY
     long long fstride;       // plane * NZ
     double dx;
     int periodic;            // ghosts are periodic images (written by the owner of each value)
     int reflect;             // the three low faces are mirror planes (images written by the owner)
+    int ng;                  // ghost layers: 3 (4th-order scheme) or 4 (6th-order scheme)
 };
 
-constexpr int NG = 3;
+constexpr int NG = 3;        // ghost layers of the 4th-order kernels (those of this header)
 
 __device__ __forceinline__ long long gidx(const Geom& g, int i, int j, int k) {  // ghosted indices
     return (long long)k * g.plane + (long long)j * g.pitch + i;
@@ -135,21 +136,41 @@ __device__ __forceinline__ void yz_rows_fill(const Geom& g, const double* __rest
 //   sh != nullptr: d_y d_z (and the first z-derivatives of the 12 fields with second
 //                  derivatives) come from the block's shared rows; wy = the thread's row.
 // Every combination gives the same bits.
+//   LOP = 1: also the lopsided advection terms adv[f] = sum_d beta^d D_d u_f, D_d the 4th-order
+//            stencil on offsets -1..3 biased towards the side beta^d points to (mirrored for
+//            beta^d < 0): beta^d D_d u = |beta^d| (-3 b1 - 10 u0 + 18 a1 - 6 a2 + a3) / (12 dx),
+//            a_n = u at n points towards that side, b1 = u one point away from it. The points
+//            are those the centred and Kreiss-Oliger stencils load anyway.
+template <int LOP = 0>
 __device__ __forceinline__ void gather(const Geom& g, const double* __restrict__ s, long long p, PointIn& in,
-                                       double kos[NFIELDS], const WarpRow* wr, const YzRows* sh, int wy) {
+                                       double kos[NFIELDS], const WarpRow* wr, const YzRows* sh, int wy,
+                                       double* adv = nullptr) {
     const double i12 = 1.0 / (12.0 * g.dx), i12s = 1.0 / (12.0 * g.dx * g.dx);
     const long long st[3] = {1, g.pitch, g.plane};
     const int lane = threadIdx.x & 31;
+    double bet[3] = {0.0, 0.0, 0.0};
+    if (LOP) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) bet[d] = __ldg(s + (F_SHIFT + d) * g.fstride + p);
+    }
 #pragma unroll
     for (int f = 0; f < NFIELDS; ++f) {
         const double* u = s + f * g.fstride;
         const double u0 = __ldg(u + p);
         in.v[f] = u0;
-        double p1[3], p2[3], d1[3];
+        double p1[3], p2[3], d1[3], p3[3], av = 0.0;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             const double m1 = __ldg(u + p - st[d]), q1 = __ldg(u + p + st[d]);
             const double m2 = __ldg(u + p - 2 * st[d]), q2 = __ldg(u + p + 2 * st[d]);
+            if (LOP) {
+                const double m3 = __ldg(u + p - 3 * st[d]), q3 = __ldg(u + p + 3 * st[d]);
+                p3[d] = m3 + q3;
+                const bool fw = bet[d] >= 0.0;
+                const double a1 = fw ? q1 : m1, a2 = fw ? q2 : m2, a3 = fw ? q3 : m3, b1 = fw ? m1 : q1;
+                const double x = fma(18.0, a1, fma(-6.0, a2, a3)) - fma(3.0, b1, 10.0 * u0);
+                av = fma(fabs(bet[d]), x * i12, av);
+            }
             if (d == 2 && has_d2(f)) {  // rounded: shared with the neighbours' d_y d_z
                 d1[d] = sh ? sh->dz[d2slot(f)][wy + 2][lane] : __dmul_rn((m2 - q2) + 8.0 * (q1 - m1), i12);
             } else {
@@ -173,9 +194,11 @@ __device__ __forceinline__ void gather(const Geom& g, const double* __restrict__
             }
             in.d2[b][5] = (16.0 * p1[2] - p2[2] - 30.0 * u0) * i12s;
         }
-        const double t3 = ((__ldg(u + p - 3 * st[0]) + __ldg(u + p + 3 * st[0])) +
-                           (__ldg(u + p - 3 * st[1]) + __ldg(u + p + 3 * st[1]))) +
-                          (__ldg(u + p - 3 * st[2]) + __ldg(u + p + 3 * st[2]));
+        if (LOP) adv[f] = av;
+        const double t3 = LOP ? (p3[0] + p3[1]) + p3[2]
+                              : ((__ldg(u + p - 3 * st[0]) + __ldg(u + p + 3 * st[0])) +
+                                 (__ldg(u + p - 3 * st[1]) + __ldg(u + p + 3 * st[1]))) +
+                                    (__ldg(u + p - 3 * st[2]) + __ldg(u + p + 3 * st[2]));
         const double t2 = (p2[0] + p2[1]) + p2[2];
         const double t1 = (p1[0] + p1[1]) + p1[2];
         kos[f] = t3 - 6.0 * t2 + 15.0 * t1 - 60.0 * u0;
@@ -221,8 +244,10 @@ __host__ __device__ __forceinline__ double mirror_sign(int f, int mask) {
 // image of it: periodic images, or for mirror boxes its reflections in the low faces (the
 // mirror plane lies half a cell below the first point; ghost NG-1-i mirrors interior i), with
 // the component's parity.
+template <int NGT = NG>
 __device__ __forceinline__ void store_with_images(const Geom& g, double* __restrict__ dst, int f, int i, int j, int k,
                                                   double x) {
+    constexpr int NG = NGT;
     double* d = dst + f * g.fstride;
     if (!g.periodic) {
         d[gidx(g, i + NG, j + NG, k + NG)] = x;
@@ -280,6 +305,9 @@ struct StageArgs {
     int fold;            // x-points per warp row: 32, or 16 / 8 / 4 for rk4_stage_fold_kernel
 };
 
+// Lopsided advection: the ADV terms of point_rhs come from in.adv (filled by the gather).
+constexpr int kLopsided = 1;
+
 // How a stage's gather takes its mixed derivatives (all modes give the same bits).
 enum GatherMode {
     GATHER_LOCAL = 0,  // per thread
@@ -292,7 +320,7 @@ enum GatherMode {
 // threads past the interior (i >= nx, and j >= ny in block mode) take part in the gather, at the
 // last ghost column / row at most, and then write nothing. sh: the block's rows (block mode,
 // already filled and synchronised).
-template <int STAGE, int DEC = -1>
+template <int STAGE, int DEC = -1, int LOP = 0>
 __device__ __forceinline__ void stage_point(const Geom& g, const Coeffs& c, const StageArgs& a, int i, int j, int k,
                                             int mode, const YzRows* sh) {
     const bool live = i < g.nx && j < g.ny;
@@ -300,18 +328,19 @@ __device__ __forceinline__ void stage_point(const Geom& g, const Coeffs& c, cons
     const long long p = gidx(g, ic + NG, jc + NG, k + NG);
     PointIn in;
     double kos[NFIELDS];
+    double adv[LOP ? NFIELDS : 1];
     if (mode != GATHER_LOCAL) {
         WarpRow wr;
         const int lane = threadIdx.x & 31;
         warp_row_halo(g, a.src, i - lane, jc, k, lane, wr);
-        gather(g, a.src, p, in, kos, &wr, mode == GATHER_BLOCK ? sh : nullptr, threadIdx.y);
+        gather<LOP>(g, a.src, p, in, kos, &wr, mode == GATHER_BLOCK ? sh : nullptr, threadIdx.y, adv);
     } else {
-        gather(g, a.src, p, in, kos, nullptr, nullptr, 0);
+        gather<LOP>(g, a.src, p, in, kos, nullptr, nullptr, 0, adv);
     }
     if (!live) return;
     double r[NFIELDS];
     bool ok = true;
-    point_rhs<double, double, DEC>(c, in, r, nullptr, ok);
+    point_rhs<double, double, DEC, LOP>(c, in, r, nullptr, ok, adv);
     if (!ok) atomicOr(a.status, 1);
     double out[NFIELDS];
 #pragma unroll 1
@@ -335,8 +364,8 @@ __device__ __forceinline__ void stage_point(const Geom& g, const Coeffs& c, cons
 // 3 resident blocks of 128 threads per SM (168 registers a thread): the extra warps hide more
 // FP64 dependency latency than the added spills cost (measured 2% faster than 2 blocks).
 // DEC: 0 full theory, 1 without backreaction (a separate instantiation each, so the full
-// theory's kernel carries no test of the mode).
-template <int STAGE, int DEC = 0>
+// theory's kernel carries no test of the mode), -1 the mode read from c. LOP: lopsided advection.
+template <int STAGE, int DEC = 0, int LOP = 0>
 __global__ void __launch_bounds__(128, 3) rk4_stage_kernel(Geom g, Coeffs c, StageArgs a) {
     __shared__ YzRows sh;
     const int i = blockIdx.x * 32 + threadIdx.x;
@@ -345,7 +374,7 @@ __global__ void __launch_bounds__(128, 3) rk4_stage_kernel(Geom g, Coeffs c, Sta
     if (k >= g.nz) return;  // whole block
     yz_rows_fill(g, a.src, i, blockIdx.y * 4, threadIdx.y, k, threadIdx.x, sh);
     __syncthreads();
-    stage_point<STAGE, DEC>(g, c, a, i, j, k, GATHER_BLOCK, &sh);
+    stage_point<STAGE, DEC, LOP>(g, c, a, i, j, k, GATHER_BLOCK, &sh);
 }
 
 // Folded variant for boxes whose x-extent is not a multiple of 32, chosen by the host when it

@@ -1,0 +1,140 @@
+// 6th-order scheme ("Accuracy": 4th- and 6th-order finite differences) on boxes with 4 ghost
+// layers: centred 6th-order first, second and mixed differences, Kreiss-Oliger dissipation with
+// the 8th difference, and the 6th-order lopsided advection stencil (offsets -2..4 towards the
+// side the shift points to). Each thread gathers its own point (no shuffles or shared rows).
+#pragma once
+
+#include "grf_kernels.cuh"
+
+namespace grf {
+
+constexpr int NG6 = 4;  // ghost layers of the 6th-order scheme
+
+// 6th-order centred first difference times 60 dx at offset p along stride t:
+//   (u_3 - u_-3) - 9 (u_2 - u_-2) + 45 (u_1 - u_-1)
+__device__ __forceinline__ double fd1_6(const double* __restrict__ u, long long p, long long t) {
+    return fma(45.0, __ldg(u + p + t) - __ldg(u + p - t),
+               fma(-9.0, __ldg(u + p + 2 * t) - __ldg(u + p - 2 * t), __ldg(u + p + 3 * t) - __ldg(u + p - 3 * t)));
+}
+
+// Values, first and second derivatives, lopsided advection terms adv[f] (LOP = 1) and the 8th
+// differences sum_d Delta^8_d u of all fields at ghosted offset p.
+//   first:  ((u_3 - u_-3) - 9 (u_2 - u_-2) + 45 (u_1 - u_-1)) / (60 dx)
+//   second: (2 (u_3 + u_-3) - 27 (u_2 + u_-2) + 270 (u_1 + u_-1) - 490 u_0) / (180 dx^2)
+//   mixed:  the first-difference stencil along s applied to first differences along t
+//   KO:     (u_4 + u_-4) - 8 (u_3 + u_-3) + 28 (u_2 + u_-2) - 56 (u_1 + u_-1) + 70 u_0 per axis
+//   lopsided, beta^d >= 0 (mirrored for beta^d < 0; a_n = u at n points towards the side beta^d
+//   points to, b_n = u at n points away from it):
+//           beta^d D_d u = |beta^d| (2 b_2 - 24 b_1 - 35 u_0 + 80 a_1 - 30 a_2 + 8 a_3 - a_4) / (60 dx)
+template <int LOP>
+__device__ __forceinline__ void gather6(const Geom& g, const double* __restrict__ s, long long p, PointIn& in,
+                                        double kos[NFIELDS], double* adv) {
+    const double i60 = 1.0 / (60.0 * g.dx), i180s = 1.0 / (180.0 * g.dx * g.dx);
+    const long long st[3] = {1, g.pitch, g.plane};
+    double bet[3] = {0.0, 0.0, 0.0};
+    if (LOP) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) bet[d] = __ldg(s + (F_SHIFT + d) * g.fstride + p);
+    }
+#pragma unroll 1
+    for (int f = 0; f < NFIELDS; ++f) {
+        const double* u = s + f * g.fstride;
+        const double u0 = __ldg(u + p);
+        in.v[f] = u0;
+        double t[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // pair sums at distance 1..4 over the three axes
+        double pr[3][5];
+        double av = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            double m[5], q[5];
+#pragma unroll
+            for (int r = 1; r <= 4; ++r) {
+                m[r] = __ldg(u + p - r * st[d]);
+                q[r] = __ldg(u + p + r * st[d]);
+                pr[d][r] = m[r] + q[r];
+            }
+            const double d1 = fma(45.0, q[1] - m[1], fma(-9.0, q[2] - m[2], q[3] - m[3])) * i60;
+            if (!(f >= F_B && f < F_B + 3)) in.d1[d1slot(f)][d] = d1;
+            if (LOP) {
+                const bool fw = bet[d] >= 0.0;
+                const double a1 = fw ? q[1] : m[1], a2 = fw ? q[2] : m[2], a3 = fw ? q[3] : m[3], a4 = fw ? q[4] : m[4];
+                const double b1 = fw ? m[1] : q[1], b2 = fw ? m[2] : q[2];
+                const double x = fma(80.0, a1, fma(-30.0, a2, fma(8.0, a3, -a4))) + fma(2.0, b2, fma(-24.0, b1, -35.0 * u0));
+                av = fma(fabs(bet[d]), x * i60, av);
+            }
+        }
+        if (LOP) adv[f] = av;
+        if (has_d2(f)) {
+            const int b = d2slot(f);
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                in.d2[b][d == 0 ? 0 : (d == 1 ? 3 : 5)] =
+                    fma(270.0, pr[d][1], fma(-27.0, pr[d][2], fma(2.0, pr[d][3], -490.0 * u0))) * i180s;
+            const int pairs[3][3] = {{0, 1, 1}, {0, 2, 2}, {1, 2, 4}};  // (s, t, slot)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const long long so = st[pairs[c][0]], to = st[pairs[c][1]];
+                const double dp1 = fd1_6(u, p + so, to) * i60, dm1 = fd1_6(u, p - so, to) * i60;
+                const double dp2 = fd1_6(u, p + 2 * so, to) * i60, dm2 = fd1_6(u, p - 2 * so, to) * i60;
+                const double dp3 = fd1_6(u, p + 3 * so, to) * i60, dm3 = fd1_6(u, p - 3 * so, to) * i60;
+                in.d2[b][pairs[c][2]] = fma(45.0, dp1 - dm1, fma(-9.0, dp2 - dm2, dp3 - dm3)) * i60;
+            }
+        }
+#pragma unroll
+        for (int r = 1; r <= 4; ++r) t[r] = (pr[0][r] + pr[1][r]) + pr[2][r];
+        kos[f] = fma(-56.0, t[1], fma(28.0, t[2], fma(-8.0, t[3], t[4]))) + 210.0 * u0;
+    }
+}
+
+// One RK4 stage at one point of a 6th-order box, as stage_point (a.ko = -sigma/(256 dx)).
+template <int STAGE, int LOP>
+__device__ __forceinline__ void stage_point6(const Geom& g, const Coeffs& c, const StageArgs& a, int i, int j, int k) {
+    const long long p = gidx(g, i + NG6, j + NG6, k + NG6);
+    PointIn in;
+    double kos[NFIELDS], adv[LOP ? NFIELDS : 1];
+    gather6<LOP>(g, a.src, p, in, kos, adv);
+    double r[NFIELDS];
+    bool ok = true;
+    point_rhs<double, double, -1, LOP>(c, in, r, nullptr, ok, adv);
+    if (!ok) atomicOr(a.status, 1);
+    double out[NFIELDS];
+#pragma unroll 1
+    for (int f = 0; f < NFIELDS; ++f) {
+        const double kf = r[f] + a.ko * kos[f];
+        const double unf = (STAGE == 0) ? in.v[f] : a.un[f * g.fstride + p];
+        double accf;
+        if (STAGE == 0) accf = kf;
+        else if (STAGE == 3) accf = a.acc[f * g.fstride + p] + kf;
+        else accf = a.acc[f * g.fstride + p] + 2.0 * kf;
+        if (STAGE < 3) a.acc[f * g.fstride + p] = accf;
+        const double cs = (STAGE == 0 || STAGE == 1) ? 0.5 * a.dt : (STAGE == 2 ? a.dt : a.dt * (1.0 / 6.0));
+        out[f] = (STAGE == 3) ? fma(cs, accf, unf) : fma(cs, kf, unf);
+    }
+    if (a.enforce) enforce_point(out, a.min_chi, a.min_lapse);
+#pragma unroll 1
+    for (int f = 0; f < NFIELDS; ++f) store_with_images<NG6>(g, a.dst, f, i, j, k, out[f]);
+}
+
+// Blocks of (32, 4, 1) threads, one point each; planes k0, k0+1, ... The decoupled mode is read
+// from c at run time.
+template <int STAGE, int LOP>
+__global__ void __launch_bounds__(128, 3) rk4_stage6_kernel(Geom g, Coeffs c, StageArgs a) {
+    const int i = blockIdx.x * 32 + threadIdx.x;
+    const int j = blockIdx.y * 4 + threadIdx.y;
+    const int k = blockIdx.z + a.k0;
+    if (i >= g.nx || j >= g.ny || k >= g.nz) return;
+    stage_point6<STAGE, LOP>(g, c, a, i, j, k);
+}
+
+// sum_d Delta^8_d u at ghosted offset p (pair sums added x, y, z)
+__device__ __forceinline__ double ko8(const double* __restrict__ u, long long p, long long sy, long long sz) {
+    const long long st[3] = {1, sy, sz};
+    double t[5];
+#pragma unroll
+    for (int r = 1; r <= 4; ++r)
+        t[r] = ((__ldg(u + p - r * st[0]) + __ldg(u + p + r * st[0])) + (__ldg(u + p - r * st[1]) + __ldg(u + p + r * st[1]))) +
+               (__ldg(u + p - r * st[2]) + __ldg(u + p + r * st[2]));
+    return fma(-56.0, t[1], fma(28.0, t[2], fma(-8.0, t[3], t[4]))) + 210.0 * __ldg(u + p);
+}
+
+}  // namespace grf

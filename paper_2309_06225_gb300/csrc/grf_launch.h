@@ -14,6 +14,17 @@ void launch_stage_decoupled(int stage, dim3 grid, dim3 block, cudaStream_t st, c
                             const StageArgs& a);
 void launch_stage_folded(int stage, dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c,
                          const StageArgs& a);
+// 4th-order scheme with lopsided advection; 6th-order scheme (centred / lopsided advection)
+void launch_stage_lopsided(int stage, dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c,
+                           const StageArgs& a);
+void launch_stage6(int stage, dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c,
+                   const StageArgs& a);
+void launch_stage6_lopsided(int stage, dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c,
+                            const StageArgs& a);
+void launch_rhs6(dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c, const double* s, double* rhs,
+                 double ko, int* status);
+void launch_constraints6(dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c, const double* s,
+                         double* out4, double* part, double* dens);
 void launch_rhs(dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c, const double* s, double* rhs,
                 double ko, int* status);
 void launch_constraints(dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c, const double* s,

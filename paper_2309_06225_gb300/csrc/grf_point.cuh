@@ -65,6 +65,7 @@ struct CoeffsT {
     double bK, bTh;               // 3b/(4(1+b)), 1/(2(1+b))
     int beta_kind;
     int decoupled;  // 1: the scalar's stress-energy is left out of the metric equations
+    int advection;  // 1: lopsided advection derivatives (kernels instantiated with LOP = 1)
 };
 using Coeffs = CoeffsT<double>;
 
@@ -214,8 +215,13 @@ GRF_HD void q_of(const T X[6], const T gd[6], const T gw[6], const T Phd[6], con
 
 // DEC: the decoupled mode as a compile-time constant (0: full theory, 1: no backreaction), or -1
 // to read c.decoupled at run time.
-template <typename T, typename P = double, int DEC = -1>
-GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS], PointExtraT<T>* extra, bool& ok) {
+// LOP = 1: every advection term beta^k d_k u of an evolved field (the CCZ4 advection terms and
+// the shift-contracted derivatives of K_ij and Pi inside the coupled system) is taken from
+// adv[27], the lopsided differences; all other derivatives stay centred. adv is not read when
+// LOP = 0.
+template <typename T, typename P = double, int DEC = -1, int LOP = 0>
+GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS], PointExtraT<T>* extra, bool& ok,
+                      const T* adv = nullptr) {
     GRF_SECTION(0);
     const T* v = in.v;
     const T chi = v[F_CHI], K = v[F_K], Th = v[F_TH], al = v[F_LAPSE], phi = v[F_PHI], Pi = v[F_PI];
@@ -258,7 +264,7 @@ GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS]
         for (int i = 0; i < 3; ++i) db[j][i] = D1(F_SHIFT + i, j);
     const T divb = db[0][0] + db[1][1] + db[2][2];
     const T bx = v[F_SHIFT], by = v[F_SHIFT + 1], bz = v[F_SHIFT + 2];
-#define ADV(f) (bx * D1(f, 0) + by * D1(f, 1) + bz * D1(f, 2))
+#define ADV(f) (LOP ? adv[f] : (bx * D1(f, 0) + by * D1(f, 1) + bz * D1(f, 2)))
 
     // ---- conformal Christoffels: G1[l][ij] = Gt_{l ij}, G2[k][ij] = Gt^k_ij,
     //      Gl_l = h^ij Gt_lij (= h_lk Gt^k), Gtc^k = h^kl Gl_l
@@ -481,7 +487,9 @@ GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS]
     for (int i = 0; i < 3; ++i)
 #pragma unroll
         for (int j = i; j < 3; ++j) {
-            T s = bx * dKp[0][sidx(i, j)] + by * dKp[1][sidx(i, j)] + bz * dKp[2][sidx(i, j)];
+            const int m = sidx(i, j);
+            T s = LOP ? fma(-Kp[m], adv[F_CHI], fma(adv[F_H + m], K3, fma(h[m], adv[F_K] * (1.0 / 3.0), adv[F_A + m]))) * ichi
+                      : bx * dKp[0][m] + by * dKp[1][m] + bz * dKp[2][m];
 #pragma unroll
             for (int k = 0; k < 3; ++k) s = fma(Kp[sidx(k, j)], db[i][k], fma(Kp[sidx(i, k)], db[j][k], s));
             LbK[sidx(i, j)] = s;
@@ -630,7 +638,7 @@ GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS]
     T C0[6];
 #pragma unroll
     for (int m = 0; m < 6; ++m) C0[m] = fma(DDa[m] - LbK[m], ial, KK[m]);
-    const T bdPi = bx * dPi[0] + by * dPi[1] + bz * dPi[2];
+    const T bdPi = LOP ? adv[F_PI] : bx * dPi[0] + by * dPi[1] + bz * dPi[2];
     const T dadp = dal[0] * dphiu[0] + dal[1] * dphiu[1] + dal[2] * dphiu[2];
     const T Phnn0 = fma(b1 * ial, -(bdPi + dadp), b2Pi * Pi);
 

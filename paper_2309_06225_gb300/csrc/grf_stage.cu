@@ -4,6 +4,14 @@
 
 namespace grf {
 void launch_stage(int stage, dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c, const StageArgs& a) {
+    if (g.ng != NG) {
+        launch_stage6(stage, grid, block, st, g, c, a);
+        return;
+    }
+    if (c.advection) {
+        launch_stage_lopsided(stage, grid, block, st, g, c, a);
+        return;
+    }
     if (a.fold != 32) {
         launch_stage_folded(stage, grid, block, st, g, c, a);
         return;

@@ -1,0 +1,15 @@
+// RK4 stage kernels of the 6th-order scheme with lopsided advection.
+#include "grf_kernels6.cuh"
+#include "grf_launch.h"
+
+namespace grf {
+void launch_stage6_lopsided(int stage, dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c,
+                            const StageArgs& a) {
+    switch (stage) {
+        case 0: rk4_stage6_kernel<0, kLopsided><<<grid, block, 0, st>>>(g, c, a); break;
+        case 1: rk4_stage6_kernel<1, kLopsided><<<grid, block, 0, st>>>(g, c, a); break;
+        case 2: rk4_stage6_kernel<2, kLopsided><<<grid, block, 0, st>>>(g, c, a); break;
+        default: rk4_stage6_kernel<3, kLopsided><<<grid, block, 0, st>>>(g, c, a); break;
+    }
+}
+}  // namespace grf

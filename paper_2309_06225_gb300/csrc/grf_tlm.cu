@@ -212,6 +212,7 @@ Geom geom_from(const grf_box* b) {
     Geom g;
     g.nx = b->nx; g.ny = b->ny; g.nz = b->nz;
     g.NX = b->nx + 6; g.NY = b->ny + 6; g.NZ = b->nz + 6;
+    g.ng = NG;
     g.pitch = b->pitch;
     g.plane = b->pitch * g.NY;
     g.fstride = g.plane * g.NZ;
@@ -254,6 +255,7 @@ int grf_tlm_rk4(const grf_box* box, const grf_params* params, const double* dpar
     if (!box_valid(box) || !params || !dparams || !state || !tangents || !sphere || !loss || nsteps < 0)
         return GRF_EINVAL;
     if (params->beta_kind != GRF_BETA_LINEAR && params->beta_kind != GRF_BETA_QUADRATIC) return GRF_EINVAL;
+    if (params->advection != 0) return GRF_EINVAL;  // centred advection only
     if (!(1.0 + params->a0 > 0.0) || !(1.0 + params->b0 > 0.0) || !(sphere->radius > 0.0)) return GRF_EINVAL;
     const Geom g = geom_from(box);
     const size_t sb = sbytes(g);

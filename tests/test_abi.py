@@ -67,3 +67,31 @@ def test_host_step_validation_without_gpu(grf):
     assert L.grf_rk4_step_host(C.byref(b), C.byref(p), None, fake, fake, 0.1, 1, fake, 1 << 30, None) == grf.GRF_EINVAL
     assert L.grf_rk4_step_host(C.byref(b), C.byref(p), fake, fake, fake, 0.1, -1, fake, 1 << 30, None) == grf.GRF_EINVAL
     assert L.grf_rk4_step_host(C.byref(b), C.byref(p), fake, fake, fake, 0.1, 1, None, 0, None) == grf.GRF_EWORKSPACE
+
+
+def test_scheme_validation_without_gpu(grf):
+    """4-ghost boxes (6th-order scheme) are sized with their ghosts; the host-to-host step rejects
+    them; lopsided advection is rejected by the batched and tangent calls and any other advection
+    value everywhere, all before a CUDA call."""
+    b6 = grf.make_box(20, 18, 16, 0.25, ng=4)
+    assert b6.pitch >= 28 and b6.pitch % 4 == 0
+    assert grf.grf_workspace_bytes(b6, grf.GRF_OP_RK4) == 3 * 8 * 27 * 24 * 26 * b6.pitch
+    small = grf.make_box(3, 8, 8, 0.25, ng=4)  # periodic 6th-order boxes need >= 4 points per axis
+    assert grf.grf_workspace_bytes(small, grf.GRF_OP_RK4) == 0
+    L = grf.lib()
+    fake = C.c_void_p(0x1000)
+    p = grf.grf_params()
+    assert L.grf_rk4_step_host(C.byref(b6), C.byref(p), fake, fake, fake, 0.1, 1, fake, 1 << 40, None) == grf.GRF_EINVAL
+    b3 = grf.make_box(16, 16, 16, 0.25)
+    p.advection = 2
+    assert L.grf_rhs(C.byref(b3), C.byref(p), fake, fake, None, 0, None) == grf.GRF_EINVAL
+    p.advection = 1
+    item = grf.grf_batch_item(b3, fake, 0, 0.1)
+    cfg = grf.grf_batch_config(grf.GRF_BATCH_STREAM, 32, 4, 1, 0, 0)
+    assert L.grf_batched_rk4(C.byref(item), 1, C.byref(p), 1, 1, C.byref(cfg), fake, 1 << 40, None, None) == grf.GRF_EINVAL
+    sphere = grf.grf_sphere()
+    sphere.radius = 1.0
+    dpar = (C.c_double * 6)()
+    loss = (C.c_double * 4)()
+    assert L.grf_tlm_rk4(C.byref(b3), C.byref(p), dpar, fake, fake, 0.1, 1, C.byref(sphere), loss, fake, 1 << 40,
+                         None) == grf.GRF_EINVAL
