@@ -31,6 +31,8 @@ IDX = {n: i for i, n in enumerate(FIELD_NAMES)}
 BC_PERIODIC = 0
 BC_FROZEN = 1
 BC_REFLECT_LOW = 2   # mirror planes half a cell below the first point of the three low faces
+BC_EXTRAPOLATE = 3   # ghosts refilled by linear extrapolation from the interior, axis by axis
+BC_SOMMERFELD = 4    # ghosts evolved by the radiative (Sommerfeld) condition
 BETA_LINEAR = 0      # beta(phi) = lambda * phi
 BETA_QUADRATIC = 1   # beta(phi) = lambda * phi^2 / 2
 

@@ -69,7 +69,9 @@ typedef struct {
     double dx;
     double x0, y0, z0;      // coordinate of interior point 0 (unused by the operator itself)
     int bc;                 // 0 periodic (ghosts refilled by wrap), 1 frozen (ghosts kept),
-                            // 2 mirror planes at the three low faces (high-face ghosts kept)
+                            // 2 mirror planes at the three low faces (high-face ghosts kept),
+                            // 3 extrapolating (ghosts refilled by linear extrapolation),
+                            // 4 Sommerfeld (ghosts evolved by the radiative condition)
     int pad_;
 } orc_box;
 
@@ -932,9 +934,88 @@ void fill_reflect(const Grid& g, double* s) {
                 }
 }
 
+// Extrapolating boundaries ("Boundary Conditions": extrapolating): every ghost point takes the
+// linear extrapolation, along one axis, of the last two points before it,
+//   u(last + m) = u(last) + m (u(last) - u(last - 1)),  m = 1 .. ng,
+// axis by axis: x-ghosts on rows of interior (y, z), then y-ghosts on rows of any x and interior
+// z, then z-ghosts on rows of any x and y, so edges and corners extrapolate values already set.
+void fill_extrapolate(const Grid& g, double* s) {
+    const int n[3] = {g.nx, g.ny, g.nz};
+    const int N[3] = {g.NX, g.NY, g.NZ};
+    for (int ax = 0; ax < 3; ++ax) {
+        const int a1 = (ax + 1) % 3, a2 = (ax + 2) % 3;
+        for (int f = 0; f < NF; ++f)
+            for (int c2 = 0; c2 < N[a2]; ++c2)
+                for (int c1 = 0; c1 < N[a1]; ++c1) {
+                    // the transverse coordinates range over what earlier axes have filled
+                    auto inside = [&](int a, int c) { return a < ax || (c >= g.ng && c < g.ng + n[a]); };
+                    if (!inside(a1, c1) || !inside(a2, c2)) continue;
+                    auto at = [&](int c) {
+                        int ijk[3];
+                        ijk[ax] = c; ijk[a1] = c1; ijk[a2] = c2;
+                        return g.at(f, ijk[0], ijk[1], ijk[2]);
+                    };
+                    const int lo = g.ng, hi = g.ng + n[ax] - 1;
+                    for (int m = 1; m <= g.ng; ++m) {
+                        s[at(hi + m)] = s[at(hi)] + m * (s[at(hi)] - s[at(hi - 1)]);
+                        s[at(lo - m)] = s[at(lo)] + m * (s[at(lo)] - s[at(lo + 1)]);
+                    }
+                }
+    }
+}
+
 void fill_bc(const orc_box& b, const Grid& g, double* s) {
     if (b.bc == 0) fill_periodic(g, s);
     else if (b.bc == 2) fill_reflect(g, s);
+    else if (b.bc == 3) fill_extrapolate(g, s);
+}
+
+// Sommerfeld (radiative) boundaries ("Boundary Conditions": Sommerfeld): every ghost point of the
+// box is evolved with
+//   d_t u = - v (u - u_inf) / r - v (x^i / r) d_i u,   v = 1, r = |x| (centre at the origin),
+// u_inf the flat values (chi = h_11 = h_22 = h_33 = lapse = 1, all else 0). Along an axis on
+// which the point lies beyond the interior, d_i is the 2nd-order one-sided difference pointing
+// into the box ((3 u - 4 u_-1 + u_-2) / (2 dx) past the high face, (-3 u + 4 u_1 - u_2) / (2 dx)
+// past the low face); along the other axes the centred 2nd-order difference. At r = 0 the right
+// side is taken as 0.
+double u_inf(int f) {
+    return (f == F_CHI || f == F_H + 0 || f == F_H + 3 || f == F_H + 5 || f == F_LAPSE) ? 1.0 : 0.0;
+}
+
+bool is_ghost(const Grid& g, int i, int j, int k) {
+    return i < g.ng || i >= g.ng + g.nx || j < g.ng || j >= g.ng + g.ny || k < g.ng || k >= g.ng + g.nz;
+}
+
+double sommerfeld_rhs(const orc_box& b, const Grid& g, const double* s, int f, int i, int j, int k) {
+    const int idx[3] = {i, j, k};
+    const int n[3] = {g.nx, g.ny, g.nz};
+    const double x[3] = {b.x0 + (i - g.ng) * b.dx, b.y0 + (j - g.ng) * b.dx, b.z0 + (k - g.ng) * b.dx};
+    const double r = std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+    if (r == 0.0) return 0.0;
+    auto U = [&](int d, int o) {
+        int q[3] = {i, j, k};
+        q[d] += o;
+        return s[g.at(f, q[0], q[1], q[2])];
+    };
+    double adv = 0;
+    for (int d = 0; d < 3; ++d) {
+        double du;
+        if (idx[d] >= g.ng + n[d]) du = (3.0 * U(d, 0) - 4.0 * U(d, -1) + U(d, -2)) / (2.0 * b.dx);
+        else if (idx[d] < g.ng) du = (-3.0 * U(d, 0) + 4.0 * U(d, 1) - U(d, 2)) / (2.0 * b.dx);
+        else du = (U(d, 1) - U(d, -1)) / (2.0 * b.dx);
+        adv += x[d] * du;
+    }
+    return -(U(0, 0) - u_inf(f)) / r - adv / r;
+}
+
+// rhs at every ghost point of a Sommerfeld box
+void sommerfeld_box(const orc_box& b, const Grid& g, const double* s, double* rhs) {
+#pragma omp parallel for collapse(2)
+    for (int f = 0; f < NF; ++f)
+        for (int k = 0; k < g.NZ; ++k)
+            for (int j = 0; j < g.NY; ++j)
+                for (int i = 0; i < g.NX; ++i)
+                    if (is_ghost(g, i, j, k)) rhs[g.at(f, i, j, k)] = sommerfeld_rhs(b, g, s, f, i, j, k);
 }
 
 int rhs_box(const orc_box& b, const orc_params& P, const double* s, double* rhs, int with_ko) {
@@ -955,6 +1036,7 @@ int rhs_box(const orc_box& b, const orc_params& P, const double* s, double* rhs,
                     rhs[g.at(f, i, j, k)] = x;
                 }
             }
+    if (b.bc == 4) sommerfeld_box(b, g, s, rhs);
     return bad ? -5 : 0;
 }
 
@@ -1098,7 +1180,8 @@ void orc_adv_lopsided(const orc_box* b, const double* s, double* out) {
             }
 }
 
-// rhs (ghosted layout) <- right-hand side at interior points, including KO dissipation.
+// rhs (ghosted layout) <- right-hand side at interior points, including KO dissipation, and for
+// Sommerfeld boxes the radiative right-hand side at every ghost point.
 // The ghosts of s must be valid. Returns 0, or -5 if some point's linear solve was singular.
 int orc_rhs(const orc_box* b, const orc_params* P, const double* s, double* rhs, int with_ko) {
     return rhs_box(*b, *P, s, rhs, with_ko);
@@ -1120,8 +1203,9 @@ void orc_enforce(const orc_box* b, const orc_params* P, double* s) { enforce(Gri
 
 // Classical RK4: k_s = RHS(u_{s-1}) (with KO); u_1 = u_n + dt/2 k_1, u_2 = u_n + dt/2 k_2,
 // u_3 = u_n + dt k_3, u_{n+1} = u_n + dt/6 (k_1 + 2k_2 + 2k_3 + k_4); every written state is
-// passed through the algebraic enforcement when enabled. Periodic boxes refill ghosts before
-// every RHS evaluation; frozen boxes keep the ghosts of the input state.
+// passed through the algebraic enforcement (interior points) when enabled. Periodic, mirror and
+// extrapolating boxes refill ghosts before every RHS evaluation; frozen boxes keep the ghosts of
+// the input state; Sommerfeld boxes evolve their ghosts with the same RK4 stages.
 int orc_rk4(const orc_box* b, const orc_params* P, double* s, double dt, int nsteps) {
     Grid g(*b);
     const long long n = NF * g.fstride;
@@ -1135,11 +1219,15 @@ int orc_rk4(const orc_box* b, const orc_params* P, double* s, double dt, int nst
             const double* src = (stage == 0) ? s : us.data();
             int r = rhs_box(*b, *P, src, k.data(), 1);
             if (r) st = r;
+            // the evolved points: the interior, and for Sommerfeld boxes the ghosts as well
+            const int e0 = b->bc == 4 ? 0 : g.ng;
+            const int ex = b->bc == 4 ? g.NX : g.ng + g.nx, ey = b->bc == 4 ? g.NY : g.ng + g.ny,
+                      ez = b->bc == 4 ? g.NZ : g.ng + g.nz;
 #pragma omp parallel for collapse(3)
             for (int f = 0; f < NF; ++f)
-                for (int kk = g.ng; kk < g.ng + g.nz; ++kk)
-                    for (int j = g.ng; j < g.ng + g.ny; ++j)
-                        for (int i = g.ng; i < g.ng + g.nx; ++i) {
+                for (int kk = e0; kk < ez; ++kk)
+                    for (int j = e0; j < ey; ++j)
+                        for (int i = e0; i < ex; ++i) {
                             long long q = g.at(f, i, j, kk);
                             double w = (stage == 0 || stage == 3) ? 1.0 : 2.0;
                             acc[q] = (stage == 0 ? 0.0 : acc[q]) + w * k[q];
@@ -1150,11 +1238,14 @@ int orc_rk4(const orc_box* b, const orc_params* P, double* s, double dt, int nst
                 fill_bc(*b, g, us.data());
             }
         }
+        const int e0 = b->bc == 4 ? 0 : g.ng;
+        const int ex = b->bc == 4 ? g.NX : g.ng + g.nx, ey = b->bc == 4 ? g.NY : g.ng + g.ny,
+                  ez = b->bc == 4 ? g.NZ : g.ng + g.nz;
 #pragma omp parallel for collapse(3)
         for (int f = 0; f < NF; ++f)
-            for (int kk = g.ng; kk < g.ng + g.nz; ++kk)
-                for (int j = g.ng; j < g.ng + g.ny; ++j)
-                    for (int i = g.ng; i < g.ng + g.nx; ++i) {
+            for (int kk = e0; kk < ez; ++kk)
+                for (int j = e0; j < ey; ++j)
+                    for (int i = e0; i < ex; ++i) {
                         long long q = g.at(f, i, j, kk);
                         s[q] = s[q] + dt / 6.0 * acc[q];
                     }

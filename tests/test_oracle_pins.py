@@ -357,6 +357,96 @@ def test_lopsided_advection_converges_at_the_scheme_order(orc, ng, ratio):
     assert 0.8 * ratio < r < 1.25 * ratio, errs
 
 
+# ----------------------------------------------------------------------------- outer boundaries
+# ("Boundary Conditions": extrapolating and Sommerfeld.)
+@pytest.mark.parametrize("ng", [3, 4])
+def test_extrapolating_ghosts_are_linear_extrapolations(orc, ng):
+    """Every ghost of an extrapolating box is exact on affine data, and on u = x^2 + 2 y^2 - z^2
+    it misses by exactly -(mx(mx+1) + 2 my(my+1) - mz(mz+1)) dx^2, m the distance (in points)
+    beyond the face along each axis: catches a wrong distance, a wrong sign or a non-linear
+    formula, and an interior point overwritten."""
+    b = gi.Box(6, 5, 7, 0.2, 0.3, -0.4, 0.1, bc=gi.BC_EXTRAPOLATE, ng=ng)
+    X, Y, Z = b.coords()
+    s = np.zeros(b.shape)
+    s[0] = 0.7 + 1.3 * X - 0.4 * Y + 2.1 * Z
+    s[1] = X ** 2 + 2 * Y ** 2 - Z ** 2
+    s[2:] = 1.0
+    ref = s.copy()
+    t = s.copy()
+    t[:, :ng] = np.nan
+    t[:, -ng:] = np.nan
+    t[:, :, :ng] = np.nan
+    t[:, :, -ng:] = np.nan
+    t[..., :ng] = np.nan
+    t[..., -ng:] = np.nan
+    orc.fill_ghosts(b, t)
+    np.testing.assert_allclose(t[0], ref[0], rtol=0, atol=1e-13)
+    def beyond(n, N):
+        i = np.arange(N)
+        return np.where(i < ng, ng - i, np.where(i >= ng + n, i - (ng + n - 1), 0))
+    mz, my, mx = np.meshgrid(beyond(b.nz, b.nz + 2 * ng), beyond(b.ny, b.ny + 2 * ng), beyond(b.nx, b.nx + 2 * ng),
+                             indexing="ij")
+    miss = -(mx * (mx + 1) + 2 * my * (my + 1) - mz * (mz + 1)) * b.dx ** 2
+    np.testing.assert_allclose(t[1] - ref[1], miss, rtol=0, atol=1e-12)
+    assert np.array_equal(b.interior(t), b.interior(ref))
+
+
+def _outgoing(b, amp=1e-6, r0=2.5, w=0.3, t=0.0):
+    """Flat slice with phi = A f(r - t) / r and Pi = d_t phi, f a Gaussian pulse: an exact
+    outgoing solution of the scalar wave equation, and of the Sommerfeld condition."""
+    s = gi.flat_state(b)
+    X, Y, Z = b.coords()
+    r = np.sqrt(X ** 2 + Y ** 2 + Z ** 2)
+    f = np.exp(-((r - t - r0) / w) ** 2)
+    fp = -2 * (r - t - r0) / w ** 2 * f
+    s[25] = amp * f / r
+    s[26] = -amp * fp / r
+    return s, r, f, fp
+
+
+def test_sommerfeld_rhs_is_exact_for_outgoing_waves_to_second_order(orc):
+    """At the ghosts of a Sommerfeld box the right-hand side of u = u_inf + A f(r - t)/r is
+    -A f'(r - t)/r up to the one-sided differences' error (ratio ~4 per halving); for the static
+    u = u_inf + c/r it is 0 to the same order; asymptotic values give exactly 0."""
+    errs, errs_static = [], []
+    for n in (16, 32):
+        b = gi.Box(n, n, n, 1.0 / n, 2.0 + 0.5 / n, 0.5 / n, 1.0 + 0.5 / n, bc=gi.BC_SOMMERFELD)
+        s, r, f, fp = _outgoing(b)
+        rhs = orc.rhs(b, gi.Params(lam=0.0, g2=0.0), s)
+        ghost = np.ones(r.shape, bool)
+        ghost[b.ng:-b.ng, b.ng:-b.ng, b.ng:-b.ng] = False
+        errs.append(np.max(np.abs(rhs[25][ghost] - (-1e-6 * fp / r)[ghost])) / 1e-6)
+        assert np.max(np.abs(rhs[:25][:, ghost])) == 0.0  # the asymptotic values are steady
+        s2 = gi.flat_state(b)
+        s2[18] = 1.0 + 0.3 / r  # lapse
+        rhs2 = orc.rhs(b, gi.Params(lam=0.0, g2=0.0), s2)
+        errs_static.append(np.max(np.abs(rhs2[18][ghost])))
+    assert 3.3 < errs[0] / errs[1] < 4.8, errs
+    assert 3.3 < errs_static[0] / errs_static[1] < 4.8, errs_static
+
+
+def test_sommerfeld_box_evolves_an_outgoing_wave(orc):
+    """A scalar pulse leaving a box that contains the origin (the radiative condition holds on
+    outer faces, where x^i/r points out of the box and the inward one-sided differences are
+    upwind): with Sommerfeld ghosts evolved by the RK4 stages the interior follows the exact
+    solution at 2nd order (ratio ~3.2 at these resolutions, tending to 4), while frozen ghosts
+    leave an error 35x larger that does not converge."""
+    T, r0, w = 0.5, 2.3, 0.5
+    errs, frozen = [], []
+    for n in (40, 80):
+        dx = 5.0 / n
+        for bc, out in ((gi.BC_SOMMERFELD, errs), (gi.BC_FROZEN, frozen)):
+            b = gi.Box(n, 4, 4, dx, -2.5 + 0.5 * dx, -1.5 * dx, -1.5 * dx, bc=bc)
+            s, *_ = _outgoing(b, r0=r0, w=w)
+            dt = 0.25 * dx
+            nsteps = int(round(T / dt))
+            orc.rk4(b, gi.Params(lam=0.0, g2=0.0), s, dt, nsteps)
+            ex, *_ = _outgoing(b, r0=r0, w=w, t=nsteps * dt)
+            out.append(np.max(np.abs(b.interior(s)[25] - b.interior(ex)[25])) / 1e-6)
+    assert 2.7 < errs[0] / errs[1] < 4.5, errs
+    assert frozen[1] > 20 * errs[0] and frozen[0] / frozen[1] < 1.5, (frozen, errs)
+
+
 # ----------------------------------------------------------------------------- P9 solve
 def test_full_pivot_solve(orc):
     """The long-double full-pivot elimination solves random systems (residual < 1e-14 relative,
