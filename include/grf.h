@@ -50,7 +50,7 @@ enum {
     GRF_ETOOLARGE = -7     /* box too large for the fixed scratch of grf_rk4_step_noalloc */
 };
 
-enum { GRF_BC_PERIODIC = 0, GRF_BC_FROZEN = 1, GRF_BC_REFLECT_LOW = 2 };
+enum { GRF_BC_PERIODIC = 0, GRF_BC_FROZEN = 1, GRF_BC_REFLECT_LOW = 2, GRF_BC_EXTRAPOLATE = 3, GRF_BC_SOMMERFELD = 4 };
 enum { GRF_BETA_LINEAR = 0, GRF_BETA_QUADRATIC = 1 };
 enum { GRF_OP_RHS = 0, GRF_OP_RK4 = 1, GRF_OP_CONSTRAINTS = 2 };
 
@@ -73,7 +73,23 @@ typedef struct {
                              cell below the first point; "Boundary Conditions", reflective),
                              their ghosts rebuilt from the interior with each component's
                              parity; ghosts on the high faces are read as given. Needs n >= ng.
-                             Not accepted by grf_batched_rk4 and grf_tlm_rk4. */
+                             Not accepted by grf_batched_rk4 and grf_tlm_rk4.
+                           GRF_BC_EXTRAPOLATE ("Boundary Conditions", extrapolating): every ghost
+                             is refilled before each right-hand side by linear extrapolation along
+                             one axis, u(last + m) = u(last) + m (u(last) - u(last - 1)), axis by
+                             axis (x-ghosts on rows of interior y, z; then y-ghosts on rows of any x
+                             and interior z; then z-ghosts on rows of any x, y).
+                           GRF_BC_SOMMERFELD ("Boundary Conditions", Sommerfeld / radiative): the
+                             ghosts are evolved state. Each ghost point takes the RK4 stages of
+                             d_t u = -(u - u_inf)/r - (x^i/r) d_i u, r = |x| (radiation centre at
+                             the coordinate origin, speed 1), u_inf = 1 for chi, h_11, h_22, h_33
+                             and the lapse and 0 for the rest; d_i is the 2nd-order one-sided
+                             difference into the box along axes on which the point lies beyond
+                             the interior, centred 2nd-order along the others. Meant for boxes
+                             that contain the origin (outer faces, where the one-sided differences
+                             are upwind). Needs n >= ng.
+                           Extrapolating and Sommerfeld boxes are not accepted by
+                             grf_rk4_step_host, grf_batched_rk4 and grf_tlm_rk4. */
     long long pitch;      /* doubles per x row, >= nx + 2 ng */
 } grf_box;
 
@@ -99,10 +115,11 @@ typedef struct {
 } grf_params;
 
 /* d_t of all 27 fields at the interior points of `state` (modified CCZ4 + 4dST, section
- * "Key features"), including Kreiss-Oliger dissipation sigma/(64 dx) sum_d Delta^6_d.
- * For GRF_BC_PERIODIC the ghost layers of `state` are first refilled by periodic wrap
- * (the interior is not modified); for GRF_BC_FROZEN they are read as given.
- * rhs: same layout as state; only interior entries are written. ws may be NULL. */
+ * "Key features"), including Kreiss-Oliger dissipation (the box's scheme, see grf_box).
+ * The ghost layers of `state` are first refilled as the box's boundary type says (periodic
+ * wrap, mirror images, extrapolation; the interior is not modified); frozen and Sommerfeld
+ * ghosts are read as given. rhs: same layout as state; interior entries are written, and for
+ * GRF_BC_SOMMERFELD also every ghost entry (the radiative right-hand side). ws may be NULL. */
 int grf_rhs(const grf_box* box, const grf_params* params, double* state, double* rhs,
             void* ws, size_t ws_bytes, grf_stream_t stream);
 

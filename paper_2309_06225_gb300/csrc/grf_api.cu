@@ -190,7 +190,9 @@ bool box_ok(const grf_box* b) {
     if (!b) return false;
     if ((b->ng != NG && b->ng != NG6) || b->nx < 1 || b->ny < 1 || b->nz < 1 || !(b->dx > 0.0)) return false;
     if (b->pitch < (long long)b->nx + 2 * b->ng) return false;
-    if (b->bc != GRF_BC_PERIODIC && b->bc != GRF_BC_FROZEN && b->bc != GRF_BC_REFLECT_LOW) return false;
+    if (b->bc != GRF_BC_PERIODIC && b->bc != GRF_BC_FROZEN && b->bc != GRF_BC_REFLECT_LOW && b->bc != GRF_BC_EXTRAPOLATE &&
+        b->bc != GRF_BC_SOMMERFELD)
+        return false;
     if (b->bc != GRF_BC_FROZEN && (b->nx < b->ng || b->ny < b->ng || b->nz < b->ng)) return false;
     return true;
 }
@@ -285,7 +287,13 @@ int* status_ptr() {
     return p;
 }
 
-int fill_ghosts(const Geom& g, double* s, cudaStream_t st) {
+// Ghosts read by the next right-hand side: periodic wrap, mirror images, or extrapolation;
+// frozen and Sommerfeld ghosts are state as given.
+int fill_ghosts(const Geom& g, int bc, double* s, cudaStream_t st) {
+    if (bc == GRF_BC_EXTRAPOLATE) {
+        launch_extrapolate(g, s, st);
+        return check_launch();
+    }
     if (g.reflect) {
         dim3 blk(32, 8, 1), grd((g.nx + g.ng + 31) / 32, (g.ny + g.ng + 7) / 8, NFIELDS);
         reflect_fill_kernel<<<grd, blk, 0, st>>>(g, s);
@@ -448,7 +456,7 @@ size_t grf_workspace_bytes(const grf_box* box, int op) {
 
 int grf_fill_ghosts(const grf_box* box, double* state, grf_stream_t stream) {
     if (!box_ok(box) || !state) return GRF_EINVAL;
-    return fill_ghosts(make_geom(box), state, (cudaStream_t)stream);
+    return fill_ghosts(make_geom(box), box->bc, state, (cudaStream_t)stream);
 }
 
 int grf_rhs(const grf_box* box, const grf_params* params, double* state, double* rhs, void* ws, size_t ws_bytes,
@@ -457,10 +465,15 @@ int grf_rhs(const grf_box* box, const grf_params* params, double* state, double*
     if (!box_ok(box) || !params_ok(params) || !state || !rhs) return GRF_EINVAL;
     Geom g = make_geom(box);
     cudaStream_t st = (cudaStream_t)stream;
-    int r = fill_ghosts(g, state, st);
+    int r = fill_ghosts(g, box->bc, state, st);
     if (r) return r;
     launch_rhs(interior_grid(g), kBlock, st, g, make_coeffs(params), state, rhs, ko_factor(g, params->sigma_ko),
                status_ptr());
+    if (box->bc == GRF_BC_SOMMERFELD) {  // the evolved ghosts' radiative right-hand side
+        StageArgs a{};
+        a.src = state;
+        launch_sommerfeld(-1, g, a, rhs, box->x0, box->y0, box->z0, st);
+    }
     return check_launch();
 }
 
@@ -485,9 +498,9 @@ int grf_rk4_step(const grf_box* box, const grf_params* params, double* state, do
     double* A = (double*)ws;
     double* B = (double*)((char*)ws + sb);
     double* acc = (double*)((char*)ws + 2 * sb);
-    int r = fill_ghosts(g, state, st);
+    int r = fill_ghosts(g, box->bc, state, st);
     if (r) return r;
-    if (!g.periodic) {  // frozen ghosts: the stage buffers carry the caller's ghosts
+    if (box->bc == GRF_BC_FROZEN || box->bc == GRF_BC_REFLECT_LOW) {  // the stage buffers carry the caller's ghosts
         cudaError_t e = cudaMemcpyAsync(A, state, sb, cudaMemcpyDeviceToDevice, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(B, state, sb, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return cuda_fail(e);
@@ -505,15 +518,25 @@ int grf_rk4_step(const grf_box* box, const grf_params* params, double* state, do
     a.un = state;
     a.acc = acc;
     const dim3 grd = stage_grid(g, g.nz, a.fold);
+    // outer boundaries after each stage: Sommerfeld ghosts take the same stage update, extrapolated
+    // ghosts are refilled from the stage's new interior
+    auto boundary = [&](int stage) {
+        if (box->bc == GRF_BC_SOMMERFELD) launch_sommerfeld(stage, g, a, nullptr, box->x0, box->y0, box->z0, st);
+        else if (box->bc == GRF_BC_EXTRAPOLATE) launch_extrapolate(g, a.dst, st);
+    };
     for (int n = 0; n < nsteps; ++n) {
         a.src = state; a.dst = A;
         launch_stage(0, grd, kBlock, st, g, c, a);
+        boundary(0);
         a.src = A; a.dst = B;
         launch_stage(1, grd, kBlock, st, g, c, a);
+        boundary(1);
         a.src = B; a.dst = A;
         launch_stage(2, grd, kBlock, st, g, c, a);
+        boundary(2);
         a.src = A; a.dst = state;
         launch_stage(3, grd, kBlock, st, g, c, a);
+        boundary(3);
         r = check_launch();
         if (r) return r;
     }
@@ -523,7 +546,8 @@ int grf_rk4_step(const grf_box* box, const grf_params* params, double* state, do
 int grf_rk4_step_host(const grf_box* box, const grf_params* params, const double* host_in, double* host_out,
                       double* state, double dt, int nsteps, void* ws, size_t ws_bytes, grf_stream_t stream) {
     if (!box_ok(box) || !params_ok(params) || !host_in || !host_out || !state || nsteps < 0) return GRF_EINVAL;
-    if (box->ng != NG) return GRF_EINVAL;  // the slab pipeline is laid out for 3 ghost layers
+    // the slab pipeline is laid out for 3 ghost layers and ghosts that are state or images
+    if (box->ng != NG || box->bc == GRF_BC_EXTRAPOLATE || box->bc == GRF_BC_SOMMERFELD) return GRF_EINVAL;
     Geom g = make_geom(box);
     const size_t sb = state_bytes(g);
     if (!ws || ws_bytes < 3 * sb || ((uintptr_t)ws & 255)) return GRF_EWORKSPACE;
@@ -642,7 +666,7 @@ int grf_constraints(const grf_box* box, const grf_params* params, double* state,
     if (norms_host) {
         if (!ws || ws_bytes < (nb * 8 + 8) * sizeof(double) || ((uintptr_t)ws & 255)) return GRF_EWORKSPACE;
     }
-    int r = fill_ghosts(g, state, st);
+    int r = fill_ghosts(g, box->bc, state, st);
     if (r) return r;
     double* part = norms_host ? (double*)ws : nullptr;
     launch_constraints(interior_grid(g), kBlock, st, g, make_coeffs(params), state, out4, part, nullptr);
@@ -662,7 +686,7 @@ int grf_energy_densities(const grf_box* box, const grf_params* params, double* s
     if (!box_ok(box) || !params_ok(params) || !state || !out3) return GRF_EINVAL;
     Geom g = make_geom(box);
     cudaStream_t st = (cudaStream_t)stream;
-    int r = fill_ghosts(g, state, st);
+    int r = fill_ghosts(g, box->bc, state, st);
     if (r) return r;
     launch_constraints(interior_grid(g), kBlock, st, g, make_coeffs(params), state, nullptr, nullptr, out3);
     return check_launch();

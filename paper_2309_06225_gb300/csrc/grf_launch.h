@@ -29,6 +29,12 @@ void launch_rhs(dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coe
                 double ko, int* status);
 void launch_constraints(dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c, const double* s,
                         double* out4, double* part, double* dens);
+// Outer boundaries (grf_boundary.cu): the extrapolation fill of all ghosts of s, and the
+// Sommerfeld ghost update of one RK4 stage (stage 0..3) or, with stage -1, the ghosts' right-hand
+// side written to out (a.src the state).
+void launch_extrapolate(const Geom& g, double* s, cudaStream_t st);
+void launch_sommerfeld(int stage, const Geom& g, const StageArgs& a, double* out, double x0, double y0, double z0,
+                       cudaStream_t st);
 // Records a CUDA error for grf_last_cuda_error() and returns GRF_ECUDA.
 int record_cuda_error(cudaError_t e);
 }  // namespace grf

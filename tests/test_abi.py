@@ -95,3 +95,16 @@ def test_scheme_validation_without_gpu(grf):
     loss = (C.c_double * 4)()
     assert L.grf_tlm_rk4(C.byref(b3), C.byref(p), dpar, fake, fake, 0.1, 1, C.byref(sphere), loss, fake, 1 << 40,
                          None) == grf.GRF_EINVAL
+
+
+def test_outer_boundaries_validation_without_gpu(grf):
+    """Extrapolating and Sommerfeld boxes need n >= ng and are refused by the host-to-host step."""
+    L = grf.lib()
+    fake = C.c_void_p(0x1000)
+    p = grf.grf_params()
+    for bc in (grf.GRF_BC_EXTRAPOLATE, grf.GRF_BC_SOMMERFELD):
+        b = grf.make_box(8, 8, 8, 0.25, bc=bc)
+        assert grf.grf_workspace_bytes(b, grf.GRF_OP_RK4) > 0
+        assert L.grf_rk4_step_host(C.byref(b), C.byref(p), fake, fake, fake, 0.1, 1, fake, 1 << 40, None) == grf.GRF_EINVAL
+        assert grf.grf_workspace_bytes(grf.make_box(2, 8, 8, 0.25, bc=bc), grf.GRF_OP_RK4) == 0
+    assert grf.grf_workspace_bytes(grf.make_box(8, 8, 8, 0.25, bc=5), grf.GRF_OP_RK4) == 0

@@ -185,3 +185,53 @@ def test_sixth_order_converges_faster_on_a_plane_wave(g):
             exact_dPi = -amp * k * k * np.sin(k * X)  # d_t Pi = lapse * Laplacian(phi) on flat space
             errs.append(np.max(np.abs(box.interior(out)[26] - exact_dPi)) / (amp * k * k))
         assert lo < errs[0] / errs[1] < hi, (ng, errs)
+
+
+def _all_points_errors(gpu, cpu):
+    """Per field max|gpu - cpu| over every point of the ghosted box / that field's maximum."""
+    nf = cpu.shape[0]
+    return np.array([np.max(np.abs(gpu[f] - cpu[f])) / max(np.max(np.abs(cpu[f])), 1e-12) for f in range(nf)])
+
+
+@pytest.mark.parametrize("ng", [3, 4])
+def test_extrapolating_boundaries_parity(g, orc, ng):
+    """Extrapolating boxes ("Boundary Conditions"): the ghost fill bit for bit against the
+    oracle's (the roundings are pinned on both sides), the RHS and 3 RK4 steps within the parity
+    bar, for both schemes."""
+    box = gi.Box(14, 11, 9, 0.3, -1.95, -1.5, -1.2, bc=gi.BC_EXTRAPOLATE, ng=ng)
+    b = g.box_like(box)
+    s0 = state_for(box, 61)
+    t = g.to_device(s0, b)
+    g.grf_fill_ghosts(b, t)
+    filled = s0.copy()
+    orc.fill_ghosts(box, filled)
+    assert np.array_equal(g.to_host(t, b), filled)
+    s, _, gpu = check_rhs_and_rk4(g, orc, box, P(lam=0.3, g2=0.2, beta_kind=1), 61)
+    cpu = s0.copy()
+    orc.rk4(box, P(lam=0.3, g2=0.2, beta_kind=1), cpu, 0.25 * box.dx, 3)
+    errs = _all_points_errors(gpu, cpu)  # the returned ghosts are extrapolated from the new interior
+    assert np.max(errs) < 1e-10, describe(errs)
+
+
+@pytest.mark.parametrize("ng", [3, 4])
+def test_sommerfeld_boundaries_parity(g, orc, ng):
+    """Sommerfeld boxes around the origin: the RHS at interior and ghost points, and 3 RK4 steps
+    with the ghosts evolved, at every point against the oracle."""
+    n = (14, 11, 9)
+    box = gi.Box(*n, 0.3, *(-(m - 1) * 0.15 for m in n), bc=gi.BC_SOMMERFELD, ng=ng)
+    params = P(lam=0.3, g2=0.2, beta_kind=1)
+    s0 = state_for(box, 67)
+    ref = orc.rhs(box, params, s0)
+    out = gpu_rhs(g, box, params, s0)
+    errs = field_errors(out, ref, box, state=s0, sigma=params.sigma_ko)
+    assert np.max(errs) < 1e-11, describe(errs)
+    ghost = np.ones(s0.shape[1:], bool)
+    ghost[ng:-ng, ng:-ng, ng:-ng] = False
+    errs = _all_points_errors(out[:, ghost], ref[:, ghost])
+    assert np.max(errs) < 1e-12, describe(errs)
+    cpu = s0.copy()
+    orc.rk4(box, params, cpu, 0.25 * box.dx, 3)
+    gpu = gpu_rk4(g, box, params, s0, 0.25 * box.dx, 3)
+    errs = _all_points_errors(gpu, cpu)
+    assert np.max(errs) < 1e-10, describe(errs)
+    assert not np.array_equal(gpu[:, ghost], s0[:, ghost])  # the ghosts evolved
