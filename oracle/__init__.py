@@ -59,6 +59,12 @@ def lib():
         L.orc_constraints.argtypes = [C.POINTER(OrcBox), C.POINTER(OrcParams), _P, _P]
         L.orc_energy_densities.argtypes = [C.POINTER(OrcBox), C.POINTER(OrcParams), _P, _P]
         L.orc_point_energy.argtypes = [C.POINTER(OrcParams), _P, _P, _P, _P]
+        L.orc_gauss_legendre.argtypes = [C.c_int, _P, _P]
+        L.orc_sylm.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, _P, _P]
+        L.orc_extract_modes.argtypes = [C.POINTER(OrcBox), _P, _P, C.c_int, C.c_double, C.c_double, C.c_double,
+                                        C.c_double, C.c_int, C.c_int, C.c_int, _P]
+        L.orc_extract_modes.restype = C.c_int
+        L.orc_interp.argtypes = [C.POINTER(OrcBox), _P, C.c_int, _P, _P]
         _lib = L
     return _lib
 
@@ -200,4 +206,38 @@ def energy_densities(b, p, s):
     """8 pi rho of the three scalar terms at the interior points: array (3, nz, ny, nx)."""
     out = np.zeros((3, b.nz, b.ny, b.nx))
     lib().orc_energy_densities(C.byref(box(b)), C.byref(params(p)), _ptr(s), _ptr(out))
+    return out
+
+
+def gauss_legendre(n):
+    x, w = np.zeros(n), np.zeros(n)
+    lib().orc_gauss_legendre(n, _ptr(x), _ptr(w))
+    return x, w
+
+
+def sylm(s, l, m, theta, phi):
+    re, im = C.c_double(), C.c_double()
+    lib().orc_sylm(s, l, m, float(theta), float(phi), C.byref(re), C.byref(im))
+    return complex(re.value, im.value)
+
+
+def extract_modes(b, f_re, f_im, spin, radius, centre, ntheta, nphi, lmax):
+    """Modes a_lm (complex array indexed l^2 + l + m) of the single ghosted field f_re (+ i f_im)
+    on the sphere of the given radius and centre."""
+    f_re = np.ascontiguousarray(f_re, dtype=np.float64)
+    fi = None if f_im is None else np.ascontiguousarray(f_im, dtype=np.float64)
+    out = np.zeros(2 * (lmax + 1) ** 2)
+    st = lib().orc_extract_modes(C.byref(box(b)), _ptr(f_re), None if fi is None else _ptr(fi), int(spin),
+                                 float(radius), *map(float, centre), int(ntheta), int(nphi), int(lmax), _ptr(out))
+    if st != 0:
+        raise ValueError("sphere stencil leaves the box")
+    return out[0::2] + 1j * out[1::2]
+
+
+def interp(b, f, xyz):
+    """4-point Lagrange interpolant of the single ghosted field f at the points xyz (n, 3)."""
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    out = np.zeros(xyz.shape[0])
+    lib().orc_interp(C.byref(box(b)), _ptr(f), xyz.shape[0], _ptr(xyz), _ptr(out))
     return out

@@ -1255,6 +1255,124 @@ int orc_rk4(const orc_box* b, const orc_params* P, double* s, double dt, int nst
     return st;
 }
 
+// ------------------------------------------------------------------------------------
+// Waveform extraction on spheres ("Diagnostics": tensor and scalar waveforms): modes
+//   a_lm = integral over the sphere of f(c + R n) conj(sY_lm(theta, phi)) dOmega,
+// theta from the z axis, phi from x towards y, f = f_re + i f_im a field of the grid.
+// Quadrature: Gauss-Legendre in cos(theta) (ntheta nodes) times nphi equally spaced phi.
+// Interpolation: tensor product of 4-point Lagrange polynomials (cubic, 4th order) on the
+// points i0-1 .. i0+2 around the sample along each axis.
+// ------------------------------------------------------------------------------------
+
+// Gauss-Legendre nodes and weights on [-1, 1] by Newton's method on P_n (three-term recurrence).
+void orc_gauss_legendre(int n, double* x, double* w) {
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1, p1 = z;  // P_0, P_1
+            for (int k = 2; k <= n; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            const double pn = n == 0 ? 1.0 : (n == 1 ? z : p1), pm = n == 1 ? 1.0 : p0;
+            dp = n * (z * pn - pm) / (z * z - 1.0);
+            const double dz = pn / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+// Spin-weighted spherical harmonic sY_lm (Goldberg et al.'s sum formula, Condon-Shortley phase;
+// s = 0 is the ordinary Y_lm):
+//   sY_lm = (-1)^m sqrt((l+m)! (l-m)! (2l+1) / (4 pi (l+s)! (l-s)!)) sin^{2l}(theta/2)
+//           sum_r C(l-s, r) C(l+s, r+s-m) (-1)^{l-r-s} cot^{2r+s-m}(theta/2) e^{i m phi}
+void orc_sylm(int s, int l, int m, double theta, double phi, double* re, double* im) {
+    auto fact = [](int n) { double f = 1; for (int k = 2; k <= n; ++k) f *= k; return f; };
+    auto binom = [&](int n, int k) { return (k < 0 || k > n) ? 0.0 : fact(n) / (fact(k) * fact(n - k)); };
+    if (l < std::abs(s) || std::abs(m) > l) { *re = *im = 0; return; }
+    const double pre = ((m & 1) ? -1.0 : 1.0) *
+                       std::sqrt(fact(l + m) * fact(l - m) * (2 * l + 1) / (4 * M_PI * fact(l + s) * fact(l - s)));
+    const double ct = 1.0 / std::tan(0.5 * theta);
+    double sum = 0;
+    for (int r = 0; r <= l - s; ++r) {
+        const double c = binom(l - s, r) * binom(l + s, r + s - m);
+        if (c == 0) continue;
+        sum += c * (((l - r - s) & 1) ? -1.0 : 1.0) * std::pow(ct, 2 * r + s - m);
+    }
+    const double a = pre * std::pow(std::sin(0.5 * theta), 2 * l) * sum;
+    *re = a * std::cos(m * phi);
+    *im = a * std::sin(m * phi);
+}
+
+// 4-point Lagrange interpolation of the field f (ghosted layout of box b) at point (x, y, z)
+double interp_lagrange4(const orc_box& b, const Grid& g, const double* f, double x, double y, double z) {
+    const double p[3] = {(x - b.x0) / b.dx + g.ng, (y - b.y0) / b.dx + g.ng, (z - b.z0) / b.dx + g.ng};
+    int i0[3];
+    double L[3][4];
+    for (int d = 0; d < 3; ++d) {
+        i0[d] = (int)std::floor(p[d]);
+        const double t = p[d] - i0[d];
+        L[d][0] = -t * (t - 1) * (t - 2) / 6.0;
+        L[d][1] = (t + 1) * (t - 1) * (t - 2) / 2.0;
+        L[d][2] = -(t + 1) * t * (t - 2) / 2.0;
+        L[d][3] = (t + 1) * t * (t - 1) / 6.0;
+    }
+    double v = 0;
+    for (int c = 0; c < 4; ++c)
+        for (int bb = 0; bb < 4; ++bb)
+            for (int a = 0; a < 4; ++a)
+                v += L[0][a] * L[1][bb] * L[2][c] * f[g.at(0, i0[0] - 1 + a, i0[1] - 1 + bb, i0[2] - 1 + c)];
+    return v;
+}
+
+// The interpolant of a single ghosted field at n points (xyz[3 n]).
+void orc_interp(const orc_box* b, const double* f, int n, const double* xyz, double* out) {
+    Grid g(*b);
+    for (int q = 0; q < n; ++q) out[q] = interp_lagrange4(*b, g, f, xyz[3 * q], xyz[3 * q + 1], xyz[3 * q + 2]);
+}
+
+// modes[2 (l^2 + l + m) + {0, 1}] for l = 0 .. lmax, m = -l .. l (zero for l < |s|). f_im may be
+// null (a real field). Returns -1 when a stencil would leave the ghosted box.
+int orc_extract_modes(const orc_box* b, const double* f_re, const double* f_im, int spin, double R, double cx,
+                      double cy, double cz, int ntheta, int nphi, int lmax, double* modes) {
+    Grid g(*b);
+    std::vector<double> mu(ntheta), w(ntheta);
+    orc_gauss_legendre(ntheta, mu.data(), w.data());
+    const int nm = (lmax + 1) * (lmax + 1);
+    for (int q = 0; q < 2 * nm; ++q) modes[q] = 0;
+    const int N[3] = {g.NX, g.NY, g.NZ};
+    const double o[3] = {b->x0, b->y0, b->z0};
+    for (int i = 0; i < ntheta; ++i) {
+        const double th = std::acos(mu[i]);
+        for (int j = 0; j < nphi; ++j) {
+            const double ph = 2.0 * M_PI * j / nphi;
+            const double x[3] = {cx + R * std::sin(th) * std::cos(ph), cy + R * std::sin(th) * std::sin(ph),
+                                 cz + R * mu[i]};
+            for (int d = 0; d < 3; ++d) {
+                const int i0 = (int)std::floor((x[d] - o[d]) / b->dx + g.ng);
+                if (i0 - 1 < 0 || i0 + 2 > N[d] - 1) return -1;
+            }
+            const double fr = interp_lagrange4(*b, g, f_re, x[0], x[1], x[2]);
+            const double fi = f_im ? interp_lagrange4(*b, g, f_im, x[0], x[1], x[2]) : 0.0;
+            const double dO = w[i] * 2.0 * M_PI / nphi;
+            for (int l = 0; l <= lmax; ++l)
+                for (int m = -l; m <= l; ++m) {
+                    double yr, yi;
+                    orc_sylm(spin, l, m, th, ph, &yr, &yi);
+                    const int q = l * l + l + m;
+                    // (fr + i fi) (yr - i yi)
+                    modes[2 * q] += dO * (fr * yr + fi * yi);
+                    modes[2 * q + 1] += dO * (fi * yr - fr * yi);
+                }
+        }
+    }
+    return 0;
+}
+
 // Hamiltonian and momentum constraints at interior points: out[4][nz][ny][nx] (ghosts valid).
 void orc_point_energy(const orc_params* P, const double* v, const double* d1, const double* d2, double* out3) {
     point_energy(*P, v, d1, d2, out3);

@@ -447,6 +447,119 @@ def test_sommerfeld_box_evolves_an_outgoing_wave(orc):
     assert frozen[1] > 20 * errs[0] and frozen[0] / frozen[1] < 1.5, (frozen, errs)
 
 
+# ----------------------------------------------------------------------------- waveform extraction
+# ("Diagnostics": tensor and scalar waveforms, extracted on spheres.)
+def test_gauss_legendre_rule_matches_the_library(orc):
+    for n in (1, 2, 5, 12, 33):
+        x, w = orc.gauss_legendre(n)
+        X, W = np.polynomial.legendre.leggauss(n)
+        np.testing.assert_allclose(np.sort(x), np.sort(X), rtol=0, atol=1e-14)
+        np.testing.assert_allclose(w[np.argsort(x)], W[np.argsort(X)], rtol=1e-13, atol=0)
+
+
+def test_spin_weighted_harmonics(orc):
+    """s = 0 equals the library's Y_lm; s = -2, l = 2 equals its closed forms; both families are
+    orthonormal under the extraction's quadrature (catches a wrong normalisation, phase or
+    quadrature weight)."""
+    sph = pytest.importorskip("scipy.special")
+    rng = np.random.default_rng(4)
+    for _ in range(5):
+        th, ph = rng.uniform(0.05, math.pi - 0.05), rng.uniform(0, 2 * math.pi)
+        for l in range(7):
+            for m in range(-l, l + 1):
+                ref = sph.sph_harm_y(l, m, th, ph)
+                assert abs(orc.sylm(0, l, m, th, ph) - ref) < 1e-12
+        c = math.cos(th)
+        closed = {2: math.sqrt(5 / (64 * math.pi)) * (1 + c) ** 2, 1: math.sqrt(5 / (16 * math.pi)) * math.sin(th) * (1 + c),
+                  0: math.sqrt(15 / (32 * math.pi)) * math.sin(th) ** 2,
+                  -1: math.sqrt(5 / (16 * math.pi)) * math.sin(th) * (1 - c),
+                  -2: math.sqrt(5 / (64 * math.pi)) * (1 - c) ** 2}
+        for m, a in closed.items():
+            assert abs(orc.sylm(-2, 2, m, th, ph) - a * np.exp(1j * m * ph)) < 1e-12
+    mu, w = orc.gauss_legendre(8)
+    nphi = 16
+    for s in (0, -2):
+        lm = [(l, m) for l in range(abs(s), 7) for m in range(-l, l + 1)]
+        Y = np.array([[orc.sylm(s, l, m, math.acos(x), 2 * math.pi * j / nphi) for x in mu for j in range(nphi)]
+                      for (l, m) in lm])
+        wq = np.repeat(w, nphi) * 2 * math.pi / nphi
+        G = (Y * wq) @ Y.conj().T
+        np.testing.assert_allclose(G, np.eye(len(lm)), rtol=0, atol=1e-12)
+
+
+def _solid_harmonic_box(l, m, centre, ng=3):
+    sph = pytest.importorskip("scipy.special")
+    b = gi.Box(20, 18, 19, 0.2, -1.9, -1.7, -1.8, bc=gi.BC_FROZEN, ng=ng)
+    X, Y, Z = b.coords()
+    dx, dy, dz = X - centre[0], Y - centre[1], Z - centre[2]
+    r = np.sqrt(dx * dx + dy * dy + dz * dz)
+    th = np.arccos(np.clip(np.where(r > 0, dz / np.where(r > 0, r, 1), 1.0), -1, 1))
+    ph = np.arctan2(dy, dx)
+    f = r ** l * sph.sph_harm_y(l, m, th, ph)
+    return b, np.ascontiguousarray(f.real), np.ascontiguousarray(f.imag)
+
+
+@pytest.mark.parametrize("lm", [(0, 0), (1, -1), (2, 1), (3, 3), (3, -2)])
+def test_extraction_is_exact_on_solid_harmonics(orc, lm):
+    """r^l Y_lm (l <= 3) is a polynomial of degree <= 3 along each axis, which the cubic
+    interpolation reproduces; the quadrature is exact for the band limit. So the modes are
+    exactly R^l at (l, m) and 0 elsewhere; a real field Re(r^l Y_lm) splits into R^l / 2 at
+    (l, m) and (-1)^m R^l / 2 at (l, -m)."""
+    l, m = lm
+    c = (0.13, -0.07, 0.21)
+    R = 1.1
+    b, fre, fim = _solid_harmonic_box(l, m, c)
+    a = orc.extract_modes(b, fre, fim, 0, R, c, 8, 16, 4)
+    ref = np.zeros(25, complex)
+    ref[l * l + l + m] = R ** l
+    np.testing.assert_allclose(a, ref, rtol=0, atol=1e-12)
+    a = orc.extract_modes(b, fre, None, 0, R, c, 8, 16, 4)
+    ref = np.zeros(25, complex)
+    ref[l * l + l + m] += R ** l / 2
+    ref[l * l + l - m] += (-1) ** m * R ** l / 2
+    np.testing.assert_allclose(a, ref, rtol=0, atol=1e-12)
+
+
+def test_sphere_interpolation_is_fourth_order(orc):
+    """The 4-point Lagrange interpolant at random points: pointwise error ratio ~16 per halving
+    of dx on a smooth field, and exact on cubics along each axis."""
+    rng = np.random.default_rng(9)
+    pts = rng.uniform(-0.9, 0.9, size=(200, 3))
+    errs = []
+    for dx in (0.1, 0.05):
+        n = int(round(3.0 / dx))
+        b = gi.Box(n, n, n, dx, -1.5 + 0.5 * dx, -1.5 + 0.5 * dx, -1.5 + 0.5 * dx, bc=gi.BC_FROZEN)
+        X, Y, Z = b.coords()
+        f = np.sin(2 * X + 0.3) * np.cos(1.5 * Y) * np.exp(0.5 * Z)
+        ex = np.sin(2 * pts[:, 0] + 0.3) * np.cos(1.5 * pts[:, 1]) * np.exp(0.5 * pts[:, 2])
+        errs.append(np.max(np.abs(orc.interp(b, f, pts) - ex)))
+        cub = (X ** 3 - 2 * X) * (Y ** 3 + Y ** 2) * (1 - Z ** 3)
+        ex_c = (pts[:, 0] ** 3 - 2 * pts[:, 0]) * (pts[:, 1] ** 3 + pts[:, 1] ** 2) * (1 - pts[:, 2] ** 3)
+        np.testing.assert_allclose(orc.interp(b, cub, pts), ex_c, rtol=0, atol=1e-13)
+    assert 13 < errs[0] / errs[1] < 19, errs
+
+
+def test_spin_minus_two_extraction_converges(orc):
+    """A field equal to -2Y_22 of the direction from the centre (smooth near the sphere): the
+    extracted a_22 tends to 1 and every other mode to 0, at least at the interpolation's 4th
+    order (the sphere integral cancels part of the pointwise error, so the ratio can be larger)."""
+    errs = []
+    for dx in (0.1, 0.05):
+        n = int(round(3.2 / dx))
+        b = gi.Box(n, n, n, dx, -1.6 + 0.5 * dx, -1.6 + 0.5 * dx, -1.6 + 0.5 * dx, bc=gi.BC_FROZEN)
+        X, Y, Z = b.coords()
+        r = np.sqrt(X * X + Y * Y + Z * Z)
+        c = Z / r
+        f = math.sqrt(5 / (64 * math.pi)) * (1 + c) ** 2 * np.exp(2j * np.arctan2(Y, X))
+        a = orc.extract_modes(b, np.ascontiguousarray(f.real), np.ascontiguousarray(f.imag), -2, 1.0,
+                              (0.0, 0.0, 0.0), 10, 20, 4)
+        ref = np.zeros(25, complex)
+        ref[2 * 2 + 2 + 2] = 1.0
+        errs.append(np.max(np.abs(a - ref)))
+    assert errs[1] < 1e-4
+    assert errs[0] / errs[1] > 12, errs
+
+
 # ----------------------------------------------------------------------------- P9 solve
 def test_full_pivot_solve(orc):
     """The long-double full-pivot elimination solves random systems (residual < 1e-14 relative,
