@@ -136,7 +136,7 @@ def run_calls(args, rank, world, local_rank):
     three scalar terms (grf_energy_densities). The timed RK4 step fuses the first two; the last two
     are diagnostics taken between steps. On the periodic box grf_rhs, grf_constraints and
     grf_energy_densities each launch the ghost fill and their kernel, grf_ko_dissipation one
-    kernel: 7 launches per timed iteration over the four calls."""
+    kernel, grf_extract_modes three: 10 launches per timed iteration over the five calls."""
     import torch
     import paper_2309_06225_gb300 as grf
     from paper_2309_06225_gb300 import flops as grf_flops
@@ -150,6 +150,7 @@ def run_calls(args, rank, world, local_rank):
     rhs = grf.alloc_state(b)
     out4 = grf.alloc_state(b, 4)
     out3 = grf.alloc_state(b, 3)
+    ews = grf.alloc_workspace(grf.grf_extract_workspace_bytes(32, 8))
     npts = box.nx * box.ny * box.nz
     stream = torch.cuda.current_stream()
     calls = {
@@ -157,6 +158,9 @@ def run_calls(args, rank, world, local_rank):
         "grf_ko_dissipation": lambda: grf.grf_ko_dissipation(b, params.sigma_ko, state, rhs),
         "grf_constraints": lambda: grf.grf_constraints(b, p, state, out4, norms=False),
         "grf_energy_densities": lambda: grf.grf_energy_densities(b, p, state, out3),
+        # the scalar waveform: spin-0 modes of phi up to l = 8 on a sphere of radius 0.75 L/2
+        "grf_extract_modes": lambda: grf.grf_extract_modes(b, state[25], None, 0, 0.375 * box.nx * box.dx,
+                                                           (0.0, 0.0, 0.0), 32, 64, 8, ws=ews),
     }
     hbm, hbm_src = measured_hbm_gbs()
     flop_rhs = grf_flops.flops_per_point_rhs(p)
@@ -176,7 +180,10 @@ def run_calls(args, rank, world, local_rank):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / args.steps
         rec = {"ms_per_call": ms, "points_per_s": npts / (ms * 1e-3)}
-        if name == "grf_ko_dissipation":
+        if name == "grf_extract_modes":  # 2048 samples of a 64-point stencil, 81 modes; synchronises
+            rec = {"ms_per_call": ms, "samples": 32 * 64, "modes": 81, "roofline": None,
+                   "note": "latency-bound: three small launches and a device-to-host copy of the modes"}
+        elif name == "grf_ko_dissipation":
             # FP64-bound even alone: per field 9 pair sums + 6 accumulations + 3 fma + the fma into
             # the RHS (23 flops) against 24 bytes (state read once, RHS read and written)
             flop_ko = 27 * 23
@@ -203,7 +210,7 @@ def run_calls(args, rank, world, local_rank):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "grid": [box.nx, box.ny, box.nz],
                        "l2": "inputs larger than L2 (no flush needed)"},
-            "gpu_launches": 7 * args.steps, "calls": out, "clocks": clk, "status": {"solve": status},
+            "gpu_launches": 10 * args.steps, "calls": out, "clocks": clk, "status": {"solve": status},
             "roofline": out["grf_rhs"]["roofline"], "e2e": None, "cpu_baseline": None}
     print(json.dumps(line), flush=True)
 

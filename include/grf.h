@@ -273,6 +273,31 @@ int grf_tlm_rk4(const grf_box* box, const grf_params* params, const double* dpar
                 grf_stream_t stream);
 
 /* ---------------------------------------------------------------------------------------
+ * Waveform extraction on spheres ("Diagnostics": tensor and scalar gravitational waveforms).
+ * Modes of a field f = f_re + i f_im on the sphere of radius R about c,
+ *   a_lm = integral over the sphere of f(c + R n) conj(sY_lm(theta, phi)) dOmega,
+ * l = 0 .. lmax, m = -l .. l, theta from the z axis, phi from x towards y, spin weight s = 0
+ * (scalar waveforms, e.g. the scalar field phi) or -2 (tensor waveforms, from Psi_4). sY_lm:
+ * Goldberg et al.'s sum formula with the Condon-Shortley phase (s = 0: the usual Y_lm).
+ * Quadrature: ntheta Gauss-Legendre nodes in cos(theta) times nphi equally spaced phi (exact for
+ * band limits below 2 ntheta in theta and nphi in phi); f is interpolated at each sample with
+ * the tensor product of 4-point Lagrange polynomials (4th order) on the points i0-1 .. i0+2.
+ * ------------------------------------------------------------------------------------- */
+
+/* Scratch bytes for grf_extract_modes (the rule, the ring sums, the modes); 0 if out of range. */
+size_t grf_extract_workspace_bytes(int ntheta, int lmax);
+
+/* f_re, f_im: device, single fields in the state layout of `box` (e.g. state + f * fstride;
+ * f_im may be NULL for a real field), read as given, ghosts included where the stencils reach.
+ * 1 <= ntheta <= 512, 1 <= nphi <= 2048, 0 <= lmax <= 12, spin 0 or -2. modes_host: host,
+ * 2 (lmax + 1)^2 doubles, (re, im) of a_lm at index l^2 + l + m (0 for l < |spin|).
+ * Synchronises `stream`. GRF_EINVAL if an argument is out of range or a sample's stencil would
+ * leave the ghosted box; GRF_EWORKSPACE if ws is too small or not 256-byte aligned. */
+int grf_extract_modes(const grf_box* box, const double* f_re, const double* f_im, int spin, const grf_sphere* sphere,
+                      int ntheta, int nphi, int lmax, double* modes_host, void* ws, size_t ws_bytes,
+                      grf_stream_t stream);
+
+/* ---------------------------------------------------------------------------------------
  * No-allocation variant (the paper has no counterpart: this is a library convenience).
  * Some callers cannot call cudaMalloc: code that runs inside an already-captured CUDA
  * graph region, host frameworks that hand out device pointers but own all allocation, or

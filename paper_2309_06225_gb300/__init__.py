@@ -98,6 +98,10 @@ def lib():
         L.grf_batched_rk4.restype = C.c_int
         L.grf_tlm_workspace_bytes.argtypes = [B]
         L.grf_tlm_workspace_bytes.restype = C.c_size_t
+        L.grf_extract_workspace_bytes.argtypes = [C.c_int, C.c_int]
+        L.grf_extract_workspace_bytes.restype = C.c_size_t
+        L.grf_extract_modes.argtypes = [B, _VP, _VP, C.c_int, C.POINTER(grf_sphere), C.c_int, C.c_int, C.c_int,
+                                        C.POINTER(C.c_double), _VP, C.c_size_t, _VP]
         L.grf_tlm_rk4.argtypes = [B, P, C.POINTER(C.c_double), _VP, _VP, C.c_double, C.c_int, C.POINTER(grf_sphere),
                                   _VP, _VP, C.c_size_t, _VP]
         L.grf_tlm_rk4.restype = C.c_int
@@ -106,7 +110,8 @@ def lib():
         L.grf_error_string.argtypes = [C.c_int]
         L.grf_error_string.restype = C.c_char_p
         L.grf_last_cuda_error.restype = C.c_char_p
-        for name in ("grf_rhs", "grf_rk4_step", "grf_rk4_step_host", "grf_constraints", "grf_energy_densities", "grf_ko_dissipation", "grf_fill_ghosts",
+        for name in ("grf_rhs", "grf_rk4_step", "grf_rk4_step_host", "grf_constraints", "grf_energy_densities",
+                     "grf_extract_modes", "grf_ko_dissipation", "grf_fill_ghosts",
                      "grf_check_status", "grf_check_finite"):
             getattr(L, name).restype = C.c_int
         _lib = L
@@ -251,6 +256,25 @@ def grf_energy_densities(box: grf_box, params: grf_params, state, out3, stream=N
     """8 pi rho of the X, g2 X^2 and Gauss-Bonnet terms into out3 (3 fields, state layout)."""
     return _check(lib().grf_energy_densities(C.byref(box), C.byref(params), _dev(state), _dev(out3),
                                              _stream(stream)), "grf_energy_densities")
+
+
+def grf_extract_workspace_bytes(ntheta, lmax):
+    return lib().grf_extract_workspace_bytes(int(ntheta), int(lmax))
+
+
+def grf_extract_modes(box: grf_box, f_re, f_im, spin, radius, centre, ntheta, nphi, lmax, ws=None, stream=None):
+    """Modes a_lm (complex numpy array indexed l^2 + l + m) of the single device field f_re
+    (+ i f_im) on the sphere; synchronises."""
+    n = 2 * (int(lmax) + 1) ** 2
+    host = (C.c_double * n)()
+    if ws is None:
+        ws = alloc_workspace(lib().grf_extract_workspace_bytes(int(ntheta), int(lmax)), f_re.device)
+    sph = grf_sphere(float(radius), *map(float, centre))
+    _check(lib().grf_extract_modes(C.byref(box), _dev(f_re), _dev(f_im), int(spin), C.byref(sph), int(ntheta),
+                                   int(nphi), int(lmax), host, _dev(ws), ws.numel(), _stream(stream)),
+           "grf_extract_modes")
+    a = np.array(list(host))
+    return a[0::2] + 1j * a[1::2]
 
 
 def grf_ko_dissipation(box: grf_box, sigma, state, rhs_accum, stream=None):

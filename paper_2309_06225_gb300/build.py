@@ -14,7 +14,7 @@ INC = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgrf.so")
 SOURCES = ["grf_api.cu", "grf_stage.cu", "grf_stage_dec.cu", "grf_stage_fold.cu", "grf_stage_lop.cu", "grf_stage6.cu",
-           "grf_stage6l.cu", "grf_rhs.cu", "grf_rhs6.cu", "grf_boundary.cu", "grf_batch.cu",
+           "grf_stage6l.cu", "grf_rhs.cu", "grf_rhs6.cu", "grf_boundary.cu", "grf_extract.cu", "grf_batch.cu",
            "grf_noalloc.cu", "grf_tlm.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

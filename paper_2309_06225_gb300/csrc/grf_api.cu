@@ -692,6 +692,14 @@ int grf_energy_densities(const grf_box* box, const grf_params* params, double* s
     return check_launch();
 }
 
+int grf_extract_modes(const grf_box* box, const double* f_re, const double* f_im, int spin, const grf_sphere* sphere,
+                      int ntheta, int nphi, int lmax, double* modes_host, void* ws, size_t ws_bytes,
+                      grf_stream_t stream) {
+    if (!box_ok(box)) return GRF_EINVAL;
+    return extract_modes(box, make_geom(box), f_re, f_im, spin, sphere, ntheta, nphi, lmax, modes_host, ws, ws_bytes,
+                         (cudaStream_t)stream);
+}
+
 int grf_check_status(grf_stream_t stream) {
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaStreamSynchronize(st);

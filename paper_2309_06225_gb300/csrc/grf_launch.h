@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include "grf.h"
 #include "grf_point.cuh"
 
 namespace grf {
@@ -35,6 +36,10 @@ void launch_constraints(dim3 grid, dim3 block, cudaStream_t st, const Geom& g, c
 void launch_extrapolate(const Geom& g, double* s, cudaStream_t st);
 void launch_sommerfeld(int stage, const Geom& g, const StageArgs& a, double* out, double x0, double y0, double z0,
                        cudaStream_t st);
+// Waveform modes of a field on a sphere (grf_extract.cu; grf_extract_modes validates the box).
+int extract_modes(const grf_box* box, const Geom& g, const double* f_re, const double* f_im, int spin,
+                  const grf_sphere* sphere, int ntheta, int nphi, int lmax, double* modes_host, void* ws,
+                  size_t ws_bytes, cudaStream_t st);
 // Records a CUDA error for grf_last_cuda_error() and returns GRF_ECUDA.
 int record_cuda_error(cudaError_t e);
 }  // namespace grf

@@ -108,3 +108,20 @@ def test_outer_boundaries_validation_without_gpu(grf):
         assert L.grf_rk4_step_host(C.byref(b), C.byref(p), fake, fake, fake, 0.1, 1, fake, 1 << 40, None) == grf.GRF_EINVAL
         assert grf.grf_workspace_bytes(grf.make_box(2, 8, 8, 0.25, bc=bc), grf.GRF_OP_RK4) == 0
     assert grf.grf_workspace_bytes(grf.make_box(8, 8, 8, 0.25, bc=5), grf.GRF_OP_RK4) == 0
+
+
+def test_extraction_validation_without_gpu(grf):
+    """Argument ranges of grf_extract_modes are checked before any CUDA call."""
+    L = grf.lib()
+    b = grf.make_box(16, 16, 16, 0.2, -1.5, -1.5, -1.5, bc=grf.GRF_BC_FROZEN)
+    fake = C.c_void_p(0x1000)
+    host = (C.c_double * 400)()
+    assert grf.grf_extract_workspace_bytes(8, 4) > 0
+    assert grf.grf_extract_workspace_bytes(8, 13) == 0 and grf.grf_extract_workspace_bytes(0, 4) == 0
+    for spin, R, nth, nph, lmax in ((1, 1.0, 8, 16, 4), (0, 1.0, 8, 4096, 4), (0, 1.0, 8, 16, 13), (0, -1.0, 8, 16, 4),
+                                    (0, 1.7, 8, 16, 4), (-2, 1.0, 600, 16, 4)):
+        sph = grf.grf_sphere(R, 0.0, 0.0, 0.0)
+        assert L.grf_extract_modes(C.byref(b), fake, None, spin, C.byref(sph), nth, nph, lmax, host, fake, 1 << 30,
+                                   None) == grf.GRF_EINVAL
+    sph = grf.grf_sphere(1.0, 0.0, 0.0, 0.0)
+    assert L.grf_extract_modes(C.byref(b), fake, None, 0, C.byref(sph), 8, 16, 4, host, fake, 8, None) == grf.GRF_EWORKSPACE
