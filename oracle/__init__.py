@@ -65,6 +65,9 @@ def lib():
                                         C.c_double, C.c_int, C.c_int, C.c_int, _P]
         L.orc_extract_modes.restype = C.c_int
         L.orc_interp.argtypes = [C.POINTER(OrcBox), _P, C.c_int, _P, _P]
+        L.orc_point_psi4.argtypes = [C.POINTER(OrcParams), _P, _P, _P, _P, _P]
+        L.orc_psi4.argtypes = [C.POINTER(OrcBox), C.POINTER(OrcParams), _P, _P]
+        L.orc_phys_sources_psi4.argtypes = [C.POINTER(OrcParams), _P, _P, C.c_double, _P, _P]
         _lib = L
     return _lib
 
@@ -241,3 +244,30 @@ def interp(b, f, xyz):
     out = np.zeros(xyz.shape[0])
     lib().orc_interp(C.byref(box(b)), _ptr(f), xyz.shape[0], _ptr(xyz), _ptr(out))
     return out
+
+
+def point_psi4(p, v, d1, d2, xyz):
+    """Psi_4 (complex) at one point with the triad about the origin at coordinates xyz."""
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    d1 = np.ascontiguousarray(d1, dtype=np.float64)
+    d2 = np.ascontiguousarray(d2, dtype=np.float64)
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    out = np.zeros(2)
+    lib().orc_point_psi4(C.byref(params(p)), _ptr(v), _ptr(d1), _ptr(d2), _ptr(xyz), _ptr(out))
+    return complex(out[0], out[1])
+
+
+def psi4(b, p, s):
+    """Psi_4 at the interior points: complex array (nz, ny, nx)."""
+    out = np.zeros((2, b.nz, b.ny, b.nx))
+    lib().orc_psi4(C.byref(box(b)), C.byref(params(p)), _ptr(s), _ptr(out))
+    return out[0] + 1j * out[1]
+
+
+def phys_psi4(p, phys, u6, w, xyz):
+    phys = np.ascontiguousarray(phys, dtype=np.float64)
+    u6 = np.ascontiguousarray(u6, dtype=np.float64)
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    out = np.zeros(21)
+    lib().orc_phys_sources_psi4(C.byref(params(p)), _ptr(phys), _ptr(u6), float(w), _ptr(xyz), _ptr(out))
+    return complex(out[19], out[20])

@@ -269,6 +269,8 @@ void geometry(const Phys& p, Geo& G) {
 struct Src {
     double rho8, S8[3], Sij8[3][3], LGB, E;  // 8 pi rho, 8 pi S_i, 8 pi S_ij, L_GB, scalar eq.
     double rho8_parts[3];  // 8 pi rho of the X, g2 X^2 and beta(phi) L_GB terms (with backreaction or not)
+    double R4[4][4][4][4];  // the 4D Riemann tensor in the basis (n, d_i), all indices down
+    double Ric4[4][4], R4s;  // its Ricci tensor and scalar
 };
 
 void beta_derivs(const orc_params& P, double phi, double& b1, double& b2) {
@@ -336,6 +338,9 @@ void sources(const orc_params& P, const Phys& p, const Geo& G, const double u[3]
             for (int c = 0; c < 4; ++c) for (int d = 0; d < 4; ++d) x += g4i[a][c] * g4i[b][d] * Ric4[c][d];
             Ric4u[a][b] = x;
         }
+    std::memcpy(s.R4, R4, sizeof(R4));
+    std::memcpy(s.Ric4, Ric4, sizeof(Ric4));
+    s.R4s = R4s;
     double riem2 = 0, ric2 = 0;
     for (int a = 0; a < 4; ++a) for (int b = 0; b < 4; ++b) for (int c = 0; c < 4; ++c) for (int d = 0; d < 4; ++d)
         riem2 += R4[a][b][c][d] * R4u[a][b][c][d];
@@ -690,6 +695,58 @@ void residual(const orc_params& P, const Conf& c, const double* v, double* R, Sr
     R[6] = -c.alpha * s.E;
     if (s_out) *s_out = s;
     if (rhs_out) { std::memcpy(rhs_out, rhs, sizeof(rhs)); rhs_out[F_PI] = v[6]; }
+}
+
+// Tensor-waveform source ("Diagnostics": tensor gravitational waveforms): the Weyl scalar
+//   Psi_4 = C_abcd n^a mbar^b n^c mbar^d,  n = (u - e_r)/sqrt(2),  m = (e_theta + i e_phi)/sqrt(2),
+// u the unit normal of the slice, (e_r, e_theta, e_phi) the orthonormal triad (Gram-Schmidt with
+// respect to gamma, in that order) of the coordinate directions (x, y, z), (x z, y z, -(x^2 + y^2))
+// and (-y, x, 0) at the point's coordinates xyz relative to the origin. C is the 4D Weyl tensor
+//   C_abcd = R_abcd - 1/2 (g_ac R_bd - g_ad R_bc - g_bc R_ad + g_bd R_ac) + R/6 (g_ac g_bd - g_ad g_bc)
+// of the Riemann tensor assembled as for the sources (with the solved d_t K_ij). Psi_4 = 0 on the
+// polar axis (x = y = 0), where the triad is not defined.
+void weyl_psi4(const Phys& p, const Src& s, const double xyz[3], double out[2]) {
+    out[0] = out[1] = 0;
+    const double x = xyz[0], y = xyz[1], z = xyz[2];
+    if (x * x + y * y == 0.0) return;
+    double g4[4][4] = {{0}};
+    g4[0][0] = -1;
+    for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) g4[i + 1][j + 1] = p.g[i][j];
+    auto dot = [&](const double* a, const double* b) {
+        double d = 0;
+        for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) d += p.g[i][j] * a[i] * b[j];
+        return d;
+    };
+    double e[3][3] = {{x, y, z}, {x * z, y * z, -(x * x + y * y)}, {-y, x, 0}};  // r, theta, phi
+    for (int a = 0; a < 3; ++a) {
+        for (int b = 0; b < a; ++b) {
+            const double d = dot(e[a], e[b]);
+            for (int i = 0; i < 3; ++i) e[a][i] -= d * e[b][i];
+        }
+        const double nrm = std::sqrt(dot(e[a], e[a]));
+        for (int i = 0; i < 3; ++i) e[a][i] /= nrm;
+    }
+    // tetrad components in the basis (n, d_i)
+    const double h = 1.0 / std::sqrt(2.0);
+    double nv[4] = {h, -h * e[0][0], -h * e[0][1], -h * e[0][2]};
+    double mr[4] = {0, h * e[1][0], h * e[1][1], h * e[1][2]};   // Re mbar
+    double mi[4] = {0, -h * e[2][0], -h * e[2][1], -h * e[2][2]};  // Im mbar
+    double re = 0, im = 0;
+    for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b)
+            for (int c = 0; c < 4; ++c)
+                for (int d = 0; d < 4; ++d) {
+                    const double C = s.R4[a][b][c][d]
+                                     - 0.5 * (g4[a][c] * s.Ric4[b][d] - g4[a][d] * s.Ric4[b][c]
+                                              - g4[b][c] * s.Ric4[a][d] + g4[b][d] * s.Ric4[a][c])
+                                     + s.R4s / 6.0 * (g4[a][c] * g4[b][d] - g4[a][d] * g4[b][c]);
+                    const double nn = nv[a] * nv[c] * C;
+                    // mbar^b mbar^d = (mr + i mi)^b (mr + i mi)^d
+                    re += nn * (mr[b] * mr[d] - mi[b] * mi[d]);
+                    im += nn * (mr[b] * mi[d] + mi[b] * mr[d]);
+                }
+    out[0] = re;
+    out[1] = im;
 }
 
 // Pointwise right-hand side (no dissipation). diag (optional, 64 doubles) receives:
@@ -1081,11 +1138,47 @@ void orc_point_constraints(const orc_params* P, const double* v, const double* d
     point_constraints(*P, v, d1, d2, out4);
 }
 
+// Psi_4 at one point: the coupled system is solved as for the right-hand side, the Riemann tensor
+// assembled with the solved d_t K_ij. xyz: coordinates relative to the origin of the triad.
+void orc_point_psi4(const orc_params* P, const double* v, const double* d1, const double* d2, const double* xyz,
+                    double* out2) {
+    double rhs[NF], diag[64];
+    point_rhs(*P, v, d1, d2, nullptr, rhs, diag);
+    static thread_local Conf c;
+    conf_setup(v, d1, d2, nullptr, c);
+    double u[3][3];
+    for (int m = 0; m < 6; ++m) u[SYM_I[m]][SYM_J[m]] = u[SYM_J[m]][SYM_I[m]] = diag[11 + m];
+    Src s;
+    sources(*P, c.p, c.G, u, diag[17], s);
+    weyl_psi4(c.p, s, xyz, out2);
+}
+
+// Psi_4 at the interior points (ghosts of s valid): out[2][nz][ny][nx], coordinates
+// x = x0 + i dx etc. relative to the origin.
+void orc_psi4(const orc_box* b, const orc_params* P, const double* s, double* out) {
+    Grid g(*b);
+    const long long npt = (long long)b->nx * b->ny * b->nz;
+#pragma omp parallel for collapse(2)
+    for (int k = 0; k < b->nz; ++k)
+        for (int j = 0; j < b->ny; ++j)
+            for (int i = 0; i < b->nx; ++i) {
+                double v[NF], d1[NF * 3], d2[NF * 6], o[2];
+                point_derivs(g, s, b->dx, i + g.ng, j + g.ng, k + g.ng, v, d1, d2);
+                const double xyz[3] = {b->x0 + i * b->dx, b->y0 + j * b->dx, b->z0 + k * b->dx};
+                orc_point_psi4(P, v, d1, d2, xyz, o);
+                long long p = ((long long)k * b->ny + j) * b->nx + i;
+                out[p] = o[0];
+                out[npt + p] = o[1];
+            }
+}
+
 // Physical 3+1 interface for the 4D brute-force checks. phys: g(6) dg(3x6) ddg(6x6)
 // K(6) dK(3x6) alpha dalpha(3) ddalpha(6) beta(3) dbeta(3x3, [j][i] = d_j beta^i) phi dphi(3)
 // ddphi(6) Pi dPi(3)  (120 doubles; symmetric pairs in the order 11,12,13,22,23,33).
 // out: 8pi rho, 8pi S_i(3), 8pi S_ij(6), L_GB, E, R_ij(6), R  (19 doubles)
-void orc_phys_sources(const orc_params* P, const double* phys, const double* u6, double w, double* out) {
+// With xyz_psi4 non-null, out[19], out[20] receive Psi_4 for the triad at those coordinates.
+void orc_phys_sources_psi4(const orc_params* P, const double* phys, const double* u6, double w, const double* xyz_psi4,
+                           double* out) {
     Phys p;
     const double* q = phys;
     for (int m = 0; m < 6; ++m) p.g[SYM_I[m]][SYM_J[m]] = p.g[SYM_J[m]][SYM_I[m]] = q[m];
@@ -1138,6 +1231,11 @@ void orc_phys_sources(const orc_params* P, const double* phys, const double* u6,
     out[11] = s.E;
     for (int m = 0; m < 6; ++m) out[12 + m] = G.Ric[SYM_I[m]][SYM_J[m]];
     out[18] = G.Rs;
+    if (xyz_psi4) weyl_psi4(p, s, xyz_psi4, out + 19);
+}
+
+void orc_phys_sources(const orc_params* P, const double* phys, const double* u6, double w, double* out) {
+    orc_phys_sources_psi4(P, phys, u6, w, nullptr, out);
 }
 
 int orc_solve(int n, const double* M, const double* r, double* x) { return solve_full_pivot(n, M, r, x); }
