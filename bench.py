@@ -135,8 +135,9 @@ def run_calls(args, rank, world, local_rank):
     constraints (grf_constraints, the 4 fields without the norms) and the energy densities of the
     three scalar terms (grf_energy_densities). The timed RK4 step fuses the first two; the last two
     are diagnostics taken between steps. On the periodic box grf_rhs, grf_constraints and
-    grf_energy_densities each launch the ghost fill and their kernel, grf_ko_dissipation one
-    kernel, grf_extract_modes three: 10 launches per timed iteration over the five calls."""
+    grf_energy_densities and grf_weyl_psi4 each launch the ghost fill and their kernel,
+    grf_ko_dissipation one kernel, grf_extract_modes three: 12 launches per timed iteration over
+    the six calls."""
     import torch
     import paper_2309_06225_gb300 as grf
     from paper_2309_06225_gb300 import flops as grf_flops
@@ -150,6 +151,7 @@ def run_calls(args, rank, world, local_rank):
     rhs = grf.alloc_state(b)
     out4 = grf.alloc_state(b, 4)
     out3 = grf.alloc_state(b, 3)
+    out2 = grf.alloc_state(b, 2)
     ews = grf.alloc_workspace(grf.grf_extract_workspace_bytes(32, 8))
     npts = box.nx * box.ny * box.nz
     stream = torch.cuda.current_stream()
@@ -158,6 +160,7 @@ def run_calls(args, rank, world, local_rank):
         "grf_ko_dissipation": lambda: grf.grf_ko_dissipation(b, params.sigma_ko, state, rhs),
         "grf_constraints": lambda: grf.grf_constraints(b, p, state, out4, norms=False),
         "grf_energy_densities": lambda: grf.grf_energy_densities(b, p, state, out3),
+        "grf_weyl_psi4": lambda: grf.grf_weyl_psi4(b, p, state, out2),
         # the scalar waveform: spin-0 modes of phi up to l = 8 on a sphere of radius 0.75 L/2
         "grf_extract_modes": lambda: grf.grf_extract_modes(b, state[25], None, 0, 0.375 * box.nx * box.dx,
                                                            (0.0, 0.0, 0.0), 32, 64, 8, ws=ews),
@@ -198,7 +201,7 @@ def run_calls(args, rank, world, local_rank):
             rec["roofline"] = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                                "frac": tf / FP64_PEAK_TFLOPS, "flop_per_point": flop_rhs,
                                "peak_source": "GB300 FP64 non-tensor, 1.25 TFLOP/s (nominal)"}
-        else:  # constraints and densities use a subset of the RHS (no CCZ4 update, no solve)
+        else:  # constraints, densities and Psi_4 use the RHS's gather and pointwise algebra
             rec["roofline"] = None
             rec["note"] = "FP64-bound like grf_rhs; its flop count is a subset of the RHS and is not counted"
         out[name] = rec
@@ -210,7 +213,7 @@ def run_calls(args, rank, world, local_rank):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "grid": [box.nx, box.ny, box.nz],
                        "l2": "inputs larger than L2 (no flush needed)"},
-            "gpu_launches": 10 * args.steps, "calls": out, "clocks": clk, "status": {"solve": status},
+            "gpu_launches": 12 * args.steps, "calls": out, "clocks": clk, "status": {"solve": status},
             "roofline": out["grf_rhs"]["roofline"], "e2e": None, "cpu_baseline": None}
     print(json.dumps(line), flush=True)
 

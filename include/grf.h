@@ -284,6 +284,16 @@ int grf_tlm_rk4(const grf_box* box, const grf_params* params, const double* dpar
  * the tensor product of 4-point Lagrange polynomials (4th order) on the points i0-1 .. i0+2.
  * ------------------------------------------------------------------------------------- */
 
+/* Weyl scalar Psi_4, the source of the tensor waveforms: Psi_4 = C_abcd n^a mbar^b n^c mbar^d
+ * with n = (u - e_r)/sqrt2, m = (e_theta + i e_phi)/sqrt2, u the slice normal and (e_r, e_theta,
+ * e_phi) the triad orthonormalised (Gram-Schmidt with respect to gamma, in that order) from the
+ * coordinate directions (x, y, z), (x z, y z, -(x^2 + y^2)), (-y, x, 0) about the coordinate
+ * origin. On a null tetrad the Ricci terms of the Weyl tensor drop out, so Psi_4 is evaluated from
+ * the Riemann blocks (Gauss, Codazzi, and the Ricci equation with d_t K_ij solved as for the
+ * right-hand side). 0 on the polar axis x = y = 0. out2: device, 2 fields in the state layout
+ * (re, im), interior entries written. Ghosts of `state` are refilled as for grf_rhs. */
+int grf_weyl_psi4(const grf_box* box, const grf_params* params, double* state, double* out2, grf_stream_t stream);
+
 /* Scratch bytes for grf_extract_modes (the rule, the ring sums, the modes); 0 if out of range. */
 size_t grf_extract_workspace_bytes(int ntheta, int lmax);
 

@@ -98,6 +98,7 @@ def lib():
         L.grf_batched_rk4.restype = C.c_int
         L.grf_tlm_workspace_bytes.argtypes = [B]
         L.grf_tlm_workspace_bytes.restype = C.c_size_t
+        L.grf_weyl_psi4.argtypes = [B, P, _VP, _VP, _VP]
         L.grf_extract_workspace_bytes.argtypes = [C.c_int, C.c_int]
         L.grf_extract_workspace_bytes.restype = C.c_size_t
         L.grf_extract_modes.argtypes = [B, _VP, _VP, C.c_int, C.POINTER(grf_sphere), C.c_int, C.c_int, C.c_int,
@@ -111,7 +112,7 @@ def lib():
         L.grf_error_string.restype = C.c_char_p
         L.grf_last_cuda_error.restype = C.c_char_p
         for name in ("grf_rhs", "grf_rk4_step", "grf_rk4_step_host", "grf_constraints", "grf_energy_densities",
-                     "grf_extract_modes", "grf_ko_dissipation", "grf_fill_ghosts",
+                     "grf_extract_modes", "grf_weyl_psi4", "grf_ko_dissipation", "grf_fill_ghosts",
                      "grf_check_status", "grf_check_finite"):
             getattr(L, name).restype = C.c_int
         _lib = L
@@ -256,6 +257,12 @@ def grf_energy_densities(box: grf_box, params: grf_params, state, out3, stream=N
     """8 pi rho of the X, g2 X^2 and Gauss-Bonnet terms into out3 (3 fields, state layout)."""
     return _check(lib().grf_energy_densities(C.byref(box), C.byref(params), _dev(state), _dev(out3),
                                              _stream(stream)), "grf_energy_densities")
+
+
+def grf_weyl_psi4(box: grf_box, params: grf_params, state, out2, stream=None):
+    """Psi_4 (re, im) at the interior points into out2 (2 fields, state layout)."""
+    return _check(lib().grf_weyl_psi4(C.byref(box), C.byref(params), _dev(state), _dev(out2), _stream(stream)),
+                  "grf_weyl_psi4")
 
 
 def grf_extract_workspace_bytes(ntheta, lmax):

@@ -669,7 +669,8 @@ int grf_constraints(const grf_box* box, const grf_params* params, double* state,
     int r = fill_ghosts(g, box->bc, state, st);
     if (r) return r;
     double* part = norms_host ? (double*)ws : nullptr;
-    launch_constraints(interior_grid(g), kBlock, st, g, make_coeffs(params), state, out4, part, nullptr);
+    launch_constraints(interior_grid(g), kBlock, st, g, make_coeffs(params), state, out4, part, nullptr, nullptr,
+                       make_double3(0.0, 0.0, 0.0));
     r = check_launch();
     if (r || !norms_host) return r;
     double* out8 = part + nb * 8;
@@ -688,7 +689,19 @@ int grf_energy_densities(const grf_box* box, const grf_params* params, double* s
     cudaStream_t st = (cudaStream_t)stream;
     int r = fill_ghosts(g, box->bc, state, st);
     if (r) return r;
-    launch_constraints(interior_grid(g), kBlock, st, g, make_coeffs(params), state, nullptr, nullptr, out3);
+    launch_constraints(interior_grid(g), kBlock, st, g, make_coeffs(params), state, nullptr, nullptr, out3, nullptr,
+                       make_double3(0.0, 0.0, 0.0));
+    return check_launch();
+}
+
+int grf_weyl_psi4(const grf_box* box, const grf_params* params, double* state, double* out2, grf_stream_t stream) {
+    if (!box_ok(box) || !params_ok(params) || !state || !out2) return GRF_EINVAL;
+    Geom g = make_geom(box);
+    cudaStream_t st = (cudaStream_t)stream;
+    int r = fill_ghosts(g, box->bc, state, st);
+    if (r) return r;
+    launch_constraints(interior_grid(g), kBlock, st, g, make_coeffs(params), state, nullptr, nullptr, nullptr, out2,
+                       make_double3(box->x0, box->y0, box->z0));
     return check_launch();
 }
 

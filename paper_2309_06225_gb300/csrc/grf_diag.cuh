@@ -10,10 +10,13 @@ namespace grf {
 // out4 (H, M_i; with the per-block norm partials in `part`) and dens (the energy densities of the
 // three scalar terms) are each written when non-null.
 // ORD = 4: block gather mode (as rhs_kernel); ORD = 6: the 6th-order per-thread gather.
+// psi4 (2 fields, re and im) receives the Weyl scalar with the triad about the origin; o = the
+// coordinates of interior point (0, 0, 0).
 template <int ORD>
 __global__ void __launch_bounds__(128) constraints_kernel(Geom g, Coeffs c, const double* __restrict__ s,
                                                           double* __restrict__ out4, double* __restrict__ part,
-                                                          double* __restrict__ dens) {
+                                                          double* __restrict__ dens, double* __restrict__ psi4,
+                                                          double3 o) {
     // blocks of (32, 4, 1); every thread stays to the reduction
     __shared__ double red[8][128];
     const int lane = threadIdx.x;
@@ -41,6 +44,12 @@ __global__ void __launch_bounds__(128) constraints_kernel(Geom g, Coeffs c, cons
     if (live) {
         double r[NFIELDS];
         PointExtra ex;
+        if (psi4) {
+            ex.want_psi4 = 1;
+            ex.xyz[0] = o.x + i * g.dx;
+            ex.xyz[1] = o.y + j * g.dx;
+            ex.xyz[2] = o.z + k * g.dx;
+        }
         bool ok = true;
         point_rhs<double>(c, in, r, &ex, ok);
         vals[0] = ex.ham;
@@ -51,6 +60,10 @@ __global__ void __launch_bounds__(128) constraints_kernel(Geom g, Coeffs c, cons
             for (int m = 0; m < 4; ++m) out4[m * g.fstride + p] = vals[m];
         if (dens)
             for (int m = 0; m < 3; ++m) dens[m * g.fstride + p] = ex.rho8[m];
+        if (psi4) {
+            psi4[p] = ex.psi4[0];
+            psi4[g.fstride + p] = ex.psi4[1];
+        }
     }
     const int t = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
     for (int m = 0; m < 4; ++m) {

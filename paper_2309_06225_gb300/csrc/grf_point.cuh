@@ -21,6 +21,8 @@
 // is assembled from these expressions and solved by LU with partial pivoting.
 #pragma once
 
+#include <type_traits>
+
 #ifdef __CUDACC__
 #include <cuda_runtime.h>
 #define GRF_HD __host__ __device__ __forceinline__
@@ -84,6 +86,11 @@ struct PointExtraT {
     T mom[3];   // M_i = B_i - 8 pi S_i
     T rho8[3];  // 8 pi rho of the X, g2 X^2 and beta(phi) L_GB terms of the action (their sum is
                 // the 8 pi rho of the equations; reported with and without backreaction)
+    // Weyl scalar Psi_4 (double instances only), computed when want_psi4 is set: xyz are the
+    // point's coordinates relative to the origin of the tetrad's triad.
+    int want_psi4 = 0;
+    double xyz[3];
+    T psi4[2];
 };
 using PointExtra = PointExtraT<double>;
 
@@ -848,6 +855,82 @@ GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS]
         extra->rho8[0] = 0.5 * (Pi * Pi - X);
         extra->rho8[1] = g2 * fma(X, Pi * Pi, -0.5 * X2);
         extra->rho8[2] = -4.0 * sdotw(GS, Phuw);
+        if constexpr (std::is_same<T, double>::value) {
+            if (extra->want_psi4) {
+                // Psi_4 = R(n, mbar, n, mbar) with n = (u - e_r)/sqrt2, m = (e_theta + i e_phi)/sqrt2: the
+                // Ricci and scalar terms of the Weyl tensor vanish on a null tetrad with g(n, mbar) = 0,
+                // so with the Riemann blocks (Ricci equation, Codazzi, Gauss)
+                //   Psi_4 = 1/2 R_ninj mbar^i mbar^j - R_nikj mbar^i e_r^k mbar^j + 1/2 R_kilj e_r^k mbar^i e_r^l mbar^j,
+                //   R_ninj = (d_t K_ij - L_beta K_ij + D_i D_j alpha)/alpha + K_ik K^k_j,
+                //   R_nikj = D_k K_ij - D_j K_ik,  R_kilj e_r e_r = R_ij + K_rr K_ij - K_ri K_rj (3D: Ricci form).
+                const double x = extra->xyz[0], y = extra->xyz[1], z = extra->xyz[2];
+                double pr = 0.0, pim = 0.0;
+                if (x * x + y * y != 0.0) {
+                    double e[3][3] = {{x, y, z}, {x * z, y * z, -(x * x + y * y)}, {-y, x, 0.0}};
+                    auto dotg = [&](const double* a, const double* b) {
+                        double d = 0.0;
+#pragma unroll
+                        for (int i = 0; i < 3; ++i)
+#pragma unroll
+                            for (int j = 0; j < 3; ++j) d = fma(gd[sidx(i, j)] * a[i], b[j], d);
+                        return d;
+                    };
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+#pragma unroll
+                        for (int b = 0; b < a; ++b) {
+                            const double d = dotg(e[a], e[b]);
+#pragma unroll
+                            for (int i = 0; i < 3; ++i) e[a][i] -= d * e[b][i];
+                        }
+                        const double inv = 1.0 / sqrt(dotg(e[a], e[a]));
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) e[a][i] *= inv;
+                    }
+                    // symmetric forms on (e_theta, e_phi) give Q(mbar, mbar) = (Q_tt - Q_pp - 2i Q_tp)/2
+                    auto form = [&](const double* S6, const double* a, const double* b) {
+                        double q = 0.0;
+#pragma unroll
+                        for (int i = 0; i < 3; ++i)
+#pragma unroll
+                            for (int j = 0; j < 3; ++j) q = fma(S6[sidx(i, j)] * a[i], b[j], q);
+                        return q;
+                    };
+                    double Rn[6];
+#pragma unroll
+                    for (int m = 0; m < 6; ++m) Rn[m] = fma(u[m] - LbK[m] + DDa[m], ial, KK[m]);
+                    const double E1r = 0.5 * (form(Rn, e[1], e[1]) - form(Rn, e[2], e[2]));
+                    const double E1i = -form(Rn, e[1], e[2]);
+                    const double Krr = form(Kp, e[0], e[0]), Krt = form(Kp, e[0], e[1]), Krp = form(Kp, e[0], e[2]);
+                    const double E3r = 0.5 * (form(Ric, e[1], e[1]) - form(Ric, e[2], e[2]))
+                                       + Krr * 0.5 * (form(Kp, e[1], e[1]) - form(Kp, e[2], e[2]))
+                                       - 0.5 * (Krt * Krt - Krp * Krp);
+                    const double E3i = -form(Ric, e[1], e[2]) - Krr * form(Kp, e[1], e[2]) + Krt * Krp;
+                    // E2 = sum_i mbar^i W_i, W_i = sum_{k != j} R_nikj e_r^k mbar^j, mbar = (e_t - i e_p)/sqrt2
+                    double E2r = 0.0, E2i = 0.0;
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        double wr = 0.0, wi = 0.0;
+#pragma unroll
+                        for (int k = 0; k < 3; ++k)
+#pragma unroll
+                            for (int j = 0; j < 3; ++j)
+                                if (k != j) {
+                                    const double Rnikj = BC(i, k, j);
+                                    wr = fma(Rnikj * e[0][k], e[1][j], wr);
+                                    wi = fma(-Rnikj * e[0][k], e[2][j], wi);
+                                }
+                        // mbar^i W_i with both factors carrying 1/sqrt2
+                        E2r += 0.5 * (e[1][i] * wr + e[2][i] * wi);
+                        E2i += 0.5 * (e[1][i] * wi - e[2][i] * wr);
+                    }
+                    pr = 0.5 * E1r - E2r + 0.5 * E3r;
+                    pim = 0.5 * E1i - E2i + 0.5 * E3i;
+                }
+                extra->psi4[0] = pr;
+                extra->psi4[1] = pim;
+            }
+        }
     }
 #undef BC
 #undef D1

@@ -31,6 +31,7 @@ def _lib():
     P = C.POINTER(C.c_double)
     L.grf_count_point_ops.argtypes = [C.c_void_p, P, P, P, C.POINTER(C.c_longlong)]
     L.grf_host_point_rhs.argtypes = [C.c_void_p, P, P, P, P, P]
+    L.grf_host_point_psi4.argtypes = [C.c_void_p, P, P, P, P, P]
     return L
 
 
@@ -87,3 +88,12 @@ def host_point_rhs(params, v, d1, d2):
     st = _lib().grf_host_point_rhs(C.byref(params), v.ctypes.data_as(P), d1.ctypes.data_as(P), d2.ctypes.data_as(P),
                                    rhs.ctypes.data_as(P), extra.ctypes.data_as(P))
     return rhs, extra, st
+
+
+def host_point_psi4(params, v, d1, d2, xyz):
+    """The kernel's Psi_4 (Riemann blocks on the null tetrad) evaluated on the host in FP64."""
+    P = C.POINTER(C.c_double)
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (v, d1, d2, xyz)]
+    out = np.zeros(2)
+    st = _lib().grf_host_point_psi4(C.byref(params), *[a.ctypes.data_as(P) for a in arrs], out.ctypes.data_as(P))
+    return complex(out[0], out[1]), st

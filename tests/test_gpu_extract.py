@@ -85,3 +85,38 @@ def test_extraction_rejects_spheres_leaving_the_box(g):
     with pytest.raises(g.GrfError) as e:
         g.grf_extract_modes(b, f, None, 0, 1.7, (0.0, 0.0, 0.0), 4, 8, 2)
     assert e.value.code == g.GRF_EINVAL
+
+
+@pytest.mark.parametrize("ng", [3, 4])
+def test_weyl_psi4_parity(g, orc, ng):
+    """Psi_4 on a generic state (couplings on) against the oracle's full-Weyl contraction, to
+    1e-11 of its maximum; then the tensor waveform: the spin -2 modes of the GPU's Psi_4 against
+    the oracle's modes of its own Psi_4."""
+    import torch
+    box = gi.Box(22, 20, 18, 0.25, -2.6, -2.4, -2.1, bc=gi.BC_PERIODIC, ng=ng)
+    params = gi.Params(lam=0.3, g2=0.2, beta_kind=1)
+    s = gi.random_perturbed_state(box, 79, base=gi.single_puncture(box, amp=0.05), eps=3e-2)
+    orc.enforce(box, params, s)
+    orc.fill_ghosts(box, s)
+    ref = orc.psi4(box, params, s)
+    b = g.box_like(box)
+    t = g.to_device(s, b)
+    out = g.alloc_state(b, 2)
+    g.grf_weyl_psi4(b, g.params_like(params), t, out)
+    assert g.grf_check_status() == 0
+    got = g.to_host(out, b)
+    psi = box.interior(got[0]) + 1j * box.interior(got[1])
+    assert np.max(np.abs(ref)) > 1e-4
+    assert np.max(np.abs(psi - ref)) <= 1e-11 * np.max(np.abs(ref))
+    # modes: the oracle extracts from its Psi_4 placed in a ghosted field (ghosts from the GPU's
+    # fill, which the sphere's stencils do not reach)
+    full = np.zeros((2,) + box.shape[1:])
+    full[0], full[1] = got[0], got[1]
+    gg = box.ng
+    full[0][gg:-gg, gg:-gg, gg:-gg] = ref.real
+    full[1][gg:-gg, gg:-gg, gg:-gg] = ref.imag
+    c, R = (0.1, 0.05, -0.1), 1.6
+    mref = orc.extract_modes(box, full[0], full[1], -2, R, c, 12, 24, 6)
+    mgot = g.grf_extract_modes(b, out[0], out[1], -2, R, c, 12, 24, 6)
+    assert np.max(np.abs(mgot - mref)) <= 1e-10 * np.max(np.abs(mref))
+    torch.cuda.synchronize()

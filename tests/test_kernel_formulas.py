@@ -49,6 +49,29 @@ def test_kernel_pointwise_rhs_matches_oracle(orc, flops, seed, kind, decoupled):
     np.testing.assert_allclose(extra, con, rtol=1e-9, atol=1e-9 * np.max(np.abs(con)))
 
 
+@pytest.mark.parametrize("seed", range(4))
+def test_kernel_psi4_matches_oracle(orc, flops, seed):
+    """The kernel's Psi_4 (the Riemann tensor on the null tetrad from the Gauss, Codazzi and
+    Ricci-equation blocks) equals the oracle's contraction of the full Weyl tensor on generic
+    non-vacuum points, couplings on."""
+    import paper_2309_06225_gb300 as grf
+    rng = np.random.default_rng(200 + seed)
+    v = rng.uniform(-0.2, 0.2, 27)
+    v[0] = rng.uniform(0.3, 1.0)
+    for m, d in zip(range(1, 7), [1, 0, 0, 1, 0, 1]):
+        v[m] = d + rng.uniform(-0.15, 0.15)
+    v[18] = rng.uniform(0.4, 1.0)
+    d1 = rng.normal(size=(27, 3)) * 0.3
+    d2 = rng.normal(size=(27, 6)) * 0.3
+    p = gi.Params(lam=rng.uniform(0.0, 0.6), g2=rng.uniform(0.0, 0.4), beta_kind=seed % 2)
+    xyz = rng.uniform(-2, 2, 3)
+    ref = orc.point_psi4(p, v, d1, d2, xyz)
+    s1, s2 = slots(d1, d2)
+    got, st = flops.host_point_psi4(grf.params_like(p), v, s1, s2, xyz)
+    assert st == 0 and abs(ref) > 1e-3
+    assert abs(got - ref) < 1e-11 * max(1.0, abs(ref)), (got, ref)
+
+
 def test_operation_count_is_stable(flops):
     """The per-point FP64 operation count of the kernels (the roofline numerator) is a fixed
     property of the formulation: independent of the point data."""
