@@ -33,6 +33,7 @@ BC_FROZEN = 1
 BC_REFLECT_LOW = 2   # mirror planes half a cell below the first point of the three low faces
 BC_EXTRAPOLATE = 3   # ghosts refilled by linear extrapolation from the interior, axis by axis
 BC_SOMMERFELD = 4    # ghosts evolved by the radiative (Sommerfeld) condition
+BC_REFLECT_LOW_SOMMERFELD = 5  # mirror planes at the low faces, Sommerfeld at the high faces
 BETA_LINEAR = 0      # beta(phi) = lambda * phi
 BETA_QUADRATIC = 1   # beta(phi) = lambda * phi^2 / 2
 

@@ -50,7 +50,14 @@ enum {
     GRF_ETOOLARGE = -7     /* box too large for the fixed scratch of grf_rk4_step_noalloc */
 };
 
-enum { GRF_BC_PERIODIC = 0, GRF_BC_FROZEN = 1, GRF_BC_REFLECT_LOW = 2, GRF_BC_EXTRAPOLATE = 3, GRF_BC_SOMMERFELD = 4 };
+enum {
+    GRF_BC_PERIODIC = 0,
+    GRF_BC_FROZEN = 1,
+    GRF_BC_REFLECT_LOW = 2,
+    GRF_BC_EXTRAPOLATE = 3,
+    GRF_BC_SOMMERFELD = 4,
+    GRF_BC_REFLECT_LOW_SOMMERFELD = 5
+};
 enum { GRF_BETA_LINEAR = 0, GRF_BETA_QUADRATIC = 1 };
 enum { GRF_OP_RHS = 0, GRF_OP_RK4 = 1, GRF_OP_CONSTRAINTS = 2 };
 
@@ -88,8 +95,16 @@ typedef struct {
                              the interior, centred 2nd-order along the others. Meant for boxes
                              that contain the origin (outer faces, where the one-sided differences
                              are upwind). Needs n >= ng.
-                           Extrapolating and Sommerfeld boxes are not accepted by
-                             grf_rk4_step_host, grf_batched_rk4 and grf_tlm_rk4. */
+                           GRF_BC_REFLECT_LOW_SOMMERFELD: mirror planes at the three low faces and
+                             Sommerfeld at the high faces, for the octant of a problem with the
+                             three reflection symmetries about the origin. Every ghost beyond a
+                             high face with no coordinate below the box is evolved by the radiative
+                             condition (centred differences along the axes where it is inside, the
+                             mirror images supplying the points below the box); every ghost with
+                             a coordinate below the box is a mirror image, refilled after each
+                             stage. Needs n >= ng.
+                           Extrapolating and Sommerfeld boxes (also behind mirror planes) are not
+                             accepted by grf_rk4_step_host, grf_batched_rk4 and grf_tlm_rk4. */
     long long pitch;      /* doubles per x row, >= nx + 2 ng */
 } grf_box;
 

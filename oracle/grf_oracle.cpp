@@ -71,7 +71,8 @@ typedef struct {
     int bc;                 // 0 periodic (ghosts refilled by wrap), 1 frozen (ghosts kept),
                             // 2 mirror planes at the three low faces (high-face ghosts kept),
                             // 3 extrapolating (ghosts refilled by linear extrapolation),
-                            // 4 Sommerfeld (ghosts evolved by the radiative condition)
+                            // 4 Sommerfeld (ghosts evolved by the radiative condition),
+                            // 5 mirror planes at the low faces, Sommerfeld at the high faces
     int pad_;
 } orc_box;
 
@@ -976,11 +977,14 @@ double parity(int f, int d) {
 // whose coordinates are interior or low ghosts (at least one) takes the value of its mirror image
 // in the interior, times the field's parity under each reflected axis. Ghosts on the high faces
 // (any coordinate past the interior) are left as given.
-void fill_reflect(const Grid& g, double* s) {
+// With all = true every ghost with a low coordinate is an image, also those beyond a high face
+// in another axis (mirror planes combined with evolved high-face ghosts).
+void fill_reflect(const Grid& g, double* s, bool all = false) {
+    const int ex = all ? g.NX : g.ng + g.nx, ey = all ? g.NY : g.ng + g.ny, ez = all ? g.NZ : g.ng + g.nz;
     for (int f = 0; f < NF; ++f)
-        for (int k = 0; k < g.ng + g.nz; ++k)
-            for (int j = 0; j < g.ng + g.ny; ++j)
-                for (int i = 0; i < g.ng + g.nx; ++i) {
+        for (int k = 0; k < ez; ++k)
+            for (int j = 0; j < ey; ++j)
+                for (int i = 0; i < ex; ++i) {
                     if (i >= g.ng && j >= g.ng && k >= g.ng) continue;
                     double sign = 1.0;
                     int a = i, b = j, c = k;
@@ -1025,6 +1029,7 @@ void fill_bc(const orc_box& b, const Grid& g, double* s) {
     if (b.bc == 0) fill_periodic(g, s);
     else if (b.bc == 2) fill_reflect(g, s);
     else if (b.bc == 3) fill_extrapolate(g, s);
+    else if (b.bc == 5) fill_reflect(g, s, true);
 }
 
 // Sommerfeld (radiative) boundaries ("Boundary Conditions": Sommerfeld): every ghost point of the
@@ -1041,6 +1046,14 @@ double u_inf(int f) {
 
 bool is_ghost(const Grid& g, int i, int j, int k) {
     return i < g.ng || i >= g.ng + g.nx || j < g.ng || j >= g.ng + g.ny || k < g.ng || k >= g.ng + g.nz;
+}
+
+// The ghosts a box evolves with the radiative condition: all of them (bc 4), or, behind mirror
+// planes (bc 5), those beyond a high face with no coordinate below the box.
+bool is_sommerfeld_point(const orc_box& b, const Grid& g, int i, int j, int k) {
+    if (b.bc == 4) return is_ghost(g, i, j, k);
+    if (b.bc != 5) return false;
+    return i >= g.ng && j >= g.ng && k >= g.ng && is_ghost(g, i, j, k);
 }
 
 double sommerfeld_rhs(const orc_box& b, const Grid& g, const double* s, int f, int i, int j, int k) {
@@ -1072,7 +1085,7 @@ void sommerfeld_box(const orc_box& b, const Grid& g, const double* s, double* rh
         for (int k = 0; k < g.NZ; ++k)
             for (int j = 0; j < g.NY; ++j)
                 for (int i = 0; i < g.NX; ++i)
-                    if (is_ghost(g, i, j, k)) rhs[g.at(f, i, j, k)] = sommerfeld_rhs(b, g, s, f, i, j, k);
+                    if (is_sommerfeld_point(b, g, i, j, k)) rhs[g.at(f, i, j, k)] = sommerfeld_rhs(b, g, s, f, i, j, k);
 }
 
 int rhs_box(const orc_box& b, const orc_params& P, const double* s, double* rhs, int with_ko) {
@@ -1093,7 +1106,7 @@ int rhs_box(const orc_box& b, const orc_params& P, const double* s, double* rhs,
                     rhs[g.at(f, i, j, k)] = x;
                 }
             }
-    if (b.bc == 4) sommerfeld_box(b, g, s, rhs);
+    if (b.bc == 4 || b.bc == 5) sommerfeld_box(b, g, s, rhs);
     return bad ? -5 : 0;
 }
 
@@ -1317,10 +1330,11 @@ int orc_rk4(const orc_box* b, const orc_params* P, double* s, double dt, int nst
             const double* src = (stage == 0) ? s : us.data();
             int r = rhs_box(*b, *P, src, k.data(), 1);
             if (r) st = r;
-            // the evolved points: the interior, and for Sommerfeld boxes the ghosts as well
+            // the evolved points: the interior, and the Sommerfeld ghosts (all ghosts for bc 4,
+            // those with no coordinate below the box for bc 5)
+            const bool som = b->bc == 4 || b->bc == 5;
             const int e0 = b->bc == 4 ? 0 : g.ng;
-            const int ex = b->bc == 4 ? g.NX : g.ng + g.nx, ey = b->bc == 4 ? g.NY : g.ng + g.ny,
-                      ez = b->bc == 4 ? g.NZ : g.ng + g.nz;
+            const int ex = som ? g.NX : g.ng + g.nx, ey = som ? g.NY : g.ng + g.ny, ez = som ? g.NZ : g.ng + g.nz;
 #pragma omp parallel for collapse(3)
             for (int f = 0; f < NF; ++f)
                 for (int kk = e0; kk < ez; ++kk)
@@ -1336,9 +1350,9 @@ int orc_rk4(const orc_box* b, const orc_params* P, double* s, double dt, int nst
                 fill_bc(*b, g, us.data());
             }
         }
+        const bool som = b->bc == 4 || b->bc == 5;
         const int e0 = b->bc == 4 ? 0 : g.ng;
-        const int ex = b->bc == 4 ? g.NX : g.ng + g.nx, ey = b->bc == 4 ? g.NY : g.ng + g.ny,
-                  ez = b->bc == 4 ? g.NZ : g.ng + g.nz;
+        const int ex = som ? g.NX : g.ng + g.nx, ey = som ? g.NY : g.ng + g.ny, ez = som ? g.NZ : g.ng + g.nz;
 #pragma omp parallel for collapse(3)
         for (int f = 0; f < NF; ++f)
             for (int kk = e0; kk < ez; ++kk)

@@ -23,6 +23,7 @@ GRF_OK, GRF_EINVAL, GRF_EWORKSPACE, GRF_ECUDA, GRF_ENONFINITE, GRF_ESINGULAR, GR
 GRF_ETOOLARGE = -7
 GRF_NOALLOC_SCRATCH_BYTES = 48 * 1024 * 1024
 GRF_BC_PERIODIC, GRF_BC_FROZEN, GRF_BC_REFLECT_LOW, GRF_BC_EXTRAPOLATE, GRF_BC_SOMMERFELD = 0, 1, 2, 3, 4
+GRF_BC_REFLECT_LOW_SOMMERFELD = 5
 GRF_BETA_LINEAR, GRF_BETA_QUADRATIC = 0, 1
 GRF_OP_RHS, GRF_OP_RK4, GRF_OP_CONSTRAINTS = 0, 1, 2
 NFIELDS, NG = 27, 3

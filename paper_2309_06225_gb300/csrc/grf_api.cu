@@ -46,19 +46,22 @@ __global__ void ghost_fill_kernel(Geom g, double* __restrict__ s) {
     }
 }
 
-// Mirror-plane ghost fill (GRF_BC_REFLECT_LOW): every ghost point whose coordinates are interior
-// or low ghosts takes its mirror image in the interior times the component's parity; ghosts on
-// the high faces are left as given. One thread per (i, j) column and field; walks k.
-__global__ void reflect_fill_kernel(Geom g, double* __restrict__ s) {
+// Mirror-plane ghost fill: every ghost point with a coordinate below the box takes its mirror
+// image times the component's parity. GRF_BC_REFLECT_LOW (all = 0): only ghosts whose other
+// coordinates are interior or low (the high faces are left as given); GRF_BC_REFLECT_LOW_SOMMERFELD
+// (all = 1): also those beyond a high face in another axis, images of evolved high-face ghosts.
+// One thread per (i, j) column and field; walks k.
+__global__ void reflect_fill_kernel(Geom g, double* __restrict__ s, int all) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int f = blockIdx.z;
     const int ng = g.ng;
-    if (i >= g.nx + ng || j >= g.ny + ng) return;
+    const int ex = all ? g.NX : g.nx + ng, ey = all ? g.NY : g.ny + ng, ez = all ? g.NZ : g.nz + ng;
+    if (i >= ex || j >= ey) return;
     double* u = s + (long long)f * g.fstride;
     const int a = i < ng ? 2 * ng - 1 - i : i, b = j < ng ? 2 * ng - 1 - j : j;
     const int mij = (i < ng ? 1 : 0) | (j < ng ? 2 : 0);
-    for (int k = 0; k < g.nz + ng; ++k) {
+    for (int k = 0; k < ez; ++k) {
         const int m = mij | (k < ng ? 4 : 0);
         if (m == 0) continue;
         u[gidx(g, i, j, k)] = mirror_sign(f, m) * u[gidx(g, a, b, k < ng ? 2 * ng - 1 - k : k)];
@@ -191,7 +194,7 @@ bool box_ok(const grf_box* b) {
     if ((b->ng != NG && b->ng != NG6) || b->nx < 1 || b->ny < 1 || b->nz < 1 || !(b->dx > 0.0)) return false;
     if (b->pitch < (long long)b->nx + 2 * b->ng) return false;
     if (b->bc != GRF_BC_PERIODIC && b->bc != GRF_BC_FROZEN && b->bc != GRF_BC_REFLECT_LOW && b->bc != GRF_BC_EXTRAPOLATE &&
-        b->bc != GRF_BC_SOMMERFELD)
+        b->bc != GRF_BC_SOMMERFELD && b->bc != GRF_BC_REFLECT_LOW_SOMMERFELD)
         return false;
     if (b->bc != GRF_BC_FROZEN && (b->nx < b->ng || b->ny < b->ng || b->nz < b->ng)) return false;
     return true;
@@ -207,7 +210,7 @@ Geom make_geom(const grf_box* b) {
     g.fstride = g.plane * g.NZ;
     g.dx = b->dx;
     g.periodic = (b->bc == GRF_BC_PERIODIC);
-    g.reflect = (b->bc == GRF_BC_REFLECT_LOW);
+    g.reflect = (b->bc == GRF_BC_REFLECT_LOW || b->bc == GRF_BC_REFLECT_LOW_SOMMERFELD);
     return g;
 }
 
@@ -295,8 +298,9 @@ int fill_ghosts(const Geom& g, int bc, double* s, cudaStream_t st) {
         return check_launch();
     }
     if (g.reflect) {
-        dim3 blk(32, 8, 1), grd((g.nx + g.ng + 31) / 32, (g.ny + g.ng + 7) / 8, NFIELDS);
-        reflect_fill_kernel<<<grd, blk, 0, st>>>(g, s);
+        const int all = bc == GRF_BC_REFLECT_LOW_SOMMERFELD;
+        dim3 blk(32, 8, 1), grd(((all ? g.NX : g.nx + g.ng) + 31) / 32, ((all ? g.NY : g.ny + g.ng) + 7) / 8, NFIELDS);
+        reflect_fill_kernel<<<grd, blk, 0, st>>>(g, s, all);
         return check_launch();
     }
     if (!g.periodic) return GRF_OK;
@@ -469,7 +473,7 @@ int grf_rhs(const grf_box* box, const grf_params* params, double* state, double*
     if (r) return r;
     launch_rhs(interior_grid(g), kBlock, st, g, make_coeffs(params), state, rhs, ko_factor(g, params->sigma_ko),
                status_ptr());
-    if (box->bc == GRF_BC_SOMMERFELD) {  // the evolved ghosts' radiative right-hand side
+    if (box->bc == GRF_BC_SOMMERFELD || box->bc == GRF_BC_REFLECT_LOW_SOMMERFELD) {  // evolved ghosts' RHS
         StageArgs a{};
         a.src = state;
         launch_sommerfeld(-1, g, a, rhs, box->x0, box->y0, box->z0, st);
@@ -520,9 +524,15 @@ int grf_rk4_step(const grf_box* box, const grf_params* params, double* state, do
     const dim3 grd = stage_grid(g, g.nz, a.fold);
     // outer boundaries after each stage: Sommerfeld ghosts take the same stage update, extrapolated
     // ghosts are refilled from the stage's new interior
+    // ghosts are refilled from the stage's new interior; behind mirror planes the images of the
+    // evolved high-face ghosts follow their update
     auto boundary = [&](int stage) {
         if (box->bc == GRF_BC_SOMMERFELD) launch_sommerfeld(stage, g, a, nullptr, box->x0, box->y0, box->z0, st);
         else if (box->bc == GRF_BC_EXTRAPOLATE) launch_extrapolate(g, a.dst, st);
+        else if (box->bc == GRF_BC_REFLECT_LOW_SOMMERFELD) {
+            launch_sommerfeld(stage, g, a, nullptr, box->x0, box->y0, box->z0, st);
+            fill_ghosts(g, box->bc, a.dst, st);
+        }
     };
     for (int n = 0; n < nsteps; ++n) {
         a.src = state; a.dst = A;
@@ -547,7 +557,9 @@ int grf_rk4_step_host(const grf_box* box, const grf_params* params, const double
                       double* state, double dt, int nsteps, void* ws, size_t ws_bytes, grf_stream_t stream) {
     if (!box_ok(box) || !params_ok(params) || !host_in || !host_out || !state || nsteps < 0) return GRF_EINVAL;
     // the slab pipeline is laid out for 3 ghost layers and ghosts that are state or images
-    if (box->ng != NG || box->bc == GRF_BC_EXTRAPOLATE || box->bc == GRF_BC_SOMMERFELD) return GRF_EINVAL;
+    if (box->ng != NG || box->bc == GRF_BC_EXTRAPOLATE || box->bc == GRF_BC_SOMMERFELD ||
+        box->bc == GRF_BC_REFLECT_LOW_SOMMERFELD)
+        return GRF_EINVAL;
     Geom g = make_geom(box);
     const size_t sb = state_bytes(g);
     if (!ws || ws_bytes < 3 * sb || ((uintptr_t)ws & 255)) return GRF_EWORKSPACE;

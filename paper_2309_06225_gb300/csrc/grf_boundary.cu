@@ -7,7 +7,8 @@
 // The roundings are pinned (no fused multiply-add), which makes the fill bit-exact against a plain
 // evaluation of the formula.
 //
-// Sommerfeld boxes evolve every ghost point with
+// Sommerfeld boxes evolve every ghost point (behind mirror planes at the low faces: every ghost
+// beyond a high face with no coordinate below the box; the rest are mirror images) with
 //   d_t u = - (u - u_inf) / r - (x^i / r) d_i u,   r = |x| (the radiation centre is the origin),
 // u_inf the flat values (chi = h_11 = h_22 = h_33 = lapse = 1, the rest 0), wave speed 1. Along an
 // axis on which the point lies beyond the interior, d_i is the 2nd-order one-sided difference
@@ -96,53 +97,60 @@ __device__ __forceinline__ double sommerfeld_rhs(const Geom& g, const Sommerfeld
     return -fma(u0 - u_inf(f), q.ir, adv);
 }
 
-// Ghost point number t of a box (0 <= t < ghost_count): first the 2 ng full ghost planes
-// (k < ng, then k >= nz + ng), then, plane by plane through the interior planes, the ghost ring
-// of each: the ng full rows below and above the interior rows, then the ng points at both ends
-// of every interior row.
-__device__ __forceinline__ void ghost_point(const Geom& g, long long t, int& i, int& j, int& k) {
-    const long long plane = (long long)g.NX * g.NY;
-    const long long full = 2LL * g.ng * plane;
+// Point number t (0 <= t < shell_count) of the shell [L, N)^3 minus the interior, in ghosted
+// indices: L = 0 gives every ghost point, L = ng the ghosts beyond a high face with no coordinate
+// below the box. Order: the full planes below and above the interior planes, then, plane by plane
+// through the interior planes, the full rows below and above the interior rows, then the points
+// before and after every interior row.
+__device__ __forceinline__ void shell_point(const Geom& g, int L, long long t, int& i, int& j, int& k) {
+    const int ex = g.NX - L, ey = g.NY - L, ez = g.NZ - L, a = g.ng - L;
+    const long long plane = (long long)ex * ey;
+    const long long full = (long long)(ez - g.nz) * plane;
     if (t < full) {
         const int q = (int)(t / plane);
         const long long r = t - q * plane;
-        k = q < g.ng ? q : g.nz + q;  // q - ng + nz + ng
-        j = (int)(r / g.NX);
-        i = (int)(r - (long long)j * g.NX);
-        return;
+        k = q < a ? q : q + g.nz;
+        j = (int)(r / ex);
+        i = (int)(r - (long long)j * ex);
+    } else {
+        t -= full;
+        const long long rows = (long long)(ey - g.ny) * ex, ring = rows + (long long)g.ny * (ex - g.nx);
+        const int q = (int)(t / ring);
+        long long r = t - q * ring;
+        k = a + q;
+        if (r < rows) {
+            const int jr = (int)(r / ex);
+            j = jr < a ? jr : jr + g.ny;
+            i = (int)(r - (long long)jr * ex);
+        } else {
+            r -= rows;
+            const int w = ex - g.nx;
+            j = a + (int)(r / w);
+            const int e = (int)(r - (long long)(j - a) * w);
+            i = e < a ? e : e + g.nx;
+        }
     }
-    t -= full;
-    const long long rows = 2LL * g.ng * g.NX, ring = rows + 2LL * g.ng * g.ny;
-    const int q = (int)(t / ring);
-    long long r = t - q * ring;
-    k = g.ng + q;
-    if (r < rows) {
-        const int jr = (int)(r / g.NX);
-        j = jr < g.ng ? jr : g.ny + jr;
-        i = (int)(r - (long long)jr * g.NX);
-        return;
-    }
-    r -= rows;
-    const int w = 2 * g.ng;
-    j = g.ng + (int)(r / w);
-    const int e = (int)(r - (long long)(j - g.ng) * w);
-    i = e < g.ng ? e : g.nx + e;
+    i += L;
+    j += L;
+    k += L;
 }
 
-__host__ __device__ __forceinline__ long long ghost_count(const Geom& g) {
-    return 2LL * g.ng * g.NX * g.NY + (long long)g.nz * (2LL * g.ng * g.NX + 2LL * g.ng * g.ny);
+__host__ __device__ __forceinline__ long long shell_count(const Geom& g, int L) {
+    const long long ex = g.NX - L, ey = g.NY - L, ez = g.NZ - L;
+    return (ez - g.nz) * ex * ey + (long long)g.nz * ((ey - g.ny) * ex + (long long)g.ny * (ex - g.nx));
 }
 
-// Every ghost point of a Sommerfeld box, one thread per ghost point (all 27 fields). STAGE < 0:
-// the right-hand side is written to `out`; STAGE 0..3: the RK4 stage update of a (as the interior
-// stage kernels, without dissipation or enforcement).
+// The evolved ghost points of a Sommerfeld box (the shell from L: 0 for every ghost, ng behind
+// mirror planes), one thread per point (all 27 fields). STAGE < 0: the right-hand side is written
+// to `out`; STAGE 0..3: the RK4 stage update of a (as the interior stage kernels, without
+// dissipation or enforcement).
 template <int STAGE>
 __global__ void __launch_bounds__(256) sommerfeld_kernel(Geom g, StageArgs a, double* __restrict__ out, double x0,
-                                                         double y0, double z0) {
+                                                         double y0, double z0, int L) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= ghost_count(g)) return;
+    if (t >= shell_count(g, L)) return;
     int i, j, k;
-    ghost_point(g, t, i, j, k);
+    shell_point(g, L, t, i, j, k);
     const SommerfeldPoint q = sommerfeld_geometry(g, i, j, k, x0, y0, z0);
     const long long p = gidx(g, i, j, k);
 #pragma unroll 1
@@ -177,13 +185,14 @@ void launch_extrapolate(const Geom& g, double* s, cudaStream_t st) {
 
 void launch_sommerfeld(int stage, const Geom& g, const StageArgs& a, double* out, double x0, double y0, double z0,
                        cudaStream_t st) {
-    const dim3 blk(256, 1, 1), grd((unsigned)((ghost_count(g) + 255) / 256), 1, 1);
+    const int L = g.reflect ? g.ng : 0;  // behind mirror planes only the high-face shell is evolved
+    const dim3 blk(256, 1, 1), grd((unsigned)((shell_count(g, L) + 255) / 256), 1, 1);
     switch (stage) {
-        case -1: sommerfeld_kernel<-1><<<grd, blk, 0, st>>>(g, a, out, x0, y0, z0); break;
-        case 0: sommerfeld_kernel<0><<<grd, blk, 0, st>>>(g, a, out, x0, y0, z0); break;
-        case 1: sommerfeld_kernel<1><<<grd, blk, 0, st>>>(g, a, out, x0, y0, z0); break;
-        case 2: sommerfeld_kernel<2><<<grd, blk, 0, st>>>(g, a, out, x0, y0, z0); break;
-        default: sommerfeld_kernel<3><<<grd, blk, 0, st>>>(g, a, out, x0, y0, z0); break;
+        case -1: sommerfeld_kernel<-1><<<grd, blk, 0, st>>>(g, a, out, x0, y0, z0, L); break;
+        case 0: sommerfeld_kernel<0><<<grd, blk, 0, st>>>(g, a, out, x0, y0, z0, L); break;
+        case 1: sommerfeld_kernel<1><<<grd, blk, 0, st>>>(g, a, out, x0, y0, z0, L); break;
+        case 2: sommerfeld_kernel<2><<<grd, blk, 0, st>>>(g, a, out, x0, y0, z0, L); break;
+        default: sommerfeld_kernel<3><<<grd, blk, 0, st>>>(g, a, out, x0, y0, z0, L); break;
     }
 }
 

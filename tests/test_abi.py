@@ -107,7 +107,7 @@ def test_outer_boundaries_validation_without_gpu(grf):
         assert grf.grf_workspace_bytes(b, grf.GRF_OP_RK4) > 0
         assert L.grf_rk4_step_host(C.byref(b), C.byref(p), fake, fake, fake, 0.1, 1, fake, 1 << 40, None) == grf.GRF_EINVAL
         assert grf.grf_workspace_bytes(grf.make_box(2, 8, 8, 0.25, bc=bc), grf.GRF_OP_RK4) == 0
-    assert grf.grf_workspace_bytes(grf.make_box(8, 8, 8, 0.25, bc=5), grf.GRF_OP_RK4) == 0
+    assert grf.grf_workspace_bytes(grf.make_box(8, 8, 8, 0.25, bc=6), grf.GRF_OP_RK4) == 0
 
 
 def test_extraction_validation_without_gpu(grf):
@@ -125,3 +125,14 @@ def test_extraction_validation_without_gpu(grf):
                                    None) == grf.GRF_EINVAL
     sph = grf.grf_sphere(1.0, 0.0, 0.0, 0.0)
     assert L.grf_extract_modes(C.byref(b), fake, None, 0, C.byref(sph), 8, 16, 4, host, fake, 8, None) == grf.GRF_EWORKSPACE
+
+
+def test_mirror_sommerfeld_validation_without_gpu(grf):
+    L = grf.lib()
+    fake = C.c_void_p(0x1000)
+    p = grf.grf_params()
+    b = grf.make_box(8, 8, 8, 0.25, bc=grf.GRF_BC_REFLECT_LOW_SOMMERFELD)
+    assert grf.grf_workspace_bytes(b, grf.GRF_OP_RK4) > 0
+    assert L.grf_rk4_step_host(C.byref(b), C.byref(p), fake, fake, fake, 0.1, 1, fake, 1 << 40, None) == grf.GRF_EINVAL
+    assert grf.grf_workspace_bytes(grf.make_box(2, 8, 8, 0.25, bc=grf.GRF_BC_REFLECT_LOW_SOMMERFELD),
+                                   grf.GRF_OP_RK4) == 0

@@ -235,3 +235,33 @@ def test_sommerfeld_boundaries_parity(g, orc, ng):
     errs = _all_points_errors(gpu, cpu)
     assert np.max(errs) < 1e-10, describe(errs)
     assert not np.array_equal(gpu[:, ghost], s0[:, ghost])  # the ghosts evolved
+
+
+@pytest.mark.parametrize("ng", [3, 4])
+def test_mirror_planes_with_sommerfeld_faces_parity(g, orc, ng):
+    """Mirror planes at the low faces and Sommerfeld high faces (GRF_BC_REFLECT_LOW_SOMMERFELD): the
+    ghost fill bit for bit, the RHS at the interior and the evolved high-face ghosts, and 3 RK4
+    steps at every point against the oracle."""
+    box = gi.Box(13, 11, 10, 0.3, 0.15, 0.15, 0.15, bc=gi.BC_REFLECT_LOW_SOMMERFELD, ng=ng)
+    params = P(lam=0.3, g2=0.2, beta_kind=1)
+    s0 = gi.random_perturbed_state(box, 83, base=gi.mirror_symmetric_state(box), eps=2e-2)
+    b = g.box_like(box)
+    t = g.to_device(s0, b)
+    g.grf_fill_ghosts(b, t)
+    filled = s0.copy()
+    orc.fill_ghosts(box, filled)
+    assert np.array_equal(g.to_host(t, b), filled)
+    ref = orc.rhs(box, params, filled)
+    out = gpu_rhs(g, box, params, s0)
+    errs = field_errors(out, ref, box, state=filled, sigma=params.sigma_ko)
+    assert np.max(errs) < 1e-11, describe(errs)
+    som = np.zeros(s0.shape[1:], bool)
+    som[ng:, ng:, ng:] = True
+    som[ng:-ng, ng:-ng, ng:-ng] = False
+    errs = _all_points_errors(out[:, som], ref[:, som])
+    assert np.max(errs) < 1e-12, describe(errs)
+    cpu = s0.copy()
+    orc.rk4(box, params, cpu, 0.25 * box.dx, 3)
+    gpu = gpu_rk4(g, box, params, s0, 0.25 * box.dx, 3)
+    errs = _all_points_errors(gpu, cpu)
+    assert np.max(errs) < 1e-10, describe(errs)
