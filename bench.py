@@ -572,17 +572,12 @@ def run_ours(args, rank, world, local_rank):
         host_in.copy_(init)
         host_out = torch.empty(state.shape, dtype=torch.float64, pin_memory=True)
         nbytes = state.numel() * 8
-        # the slab pipeline of grf_rk4_step_host is laid out for 3 ghost layers and ghosts that are
-        # images or frozen state
-        sliced = box.ng == 3 and box.bc in (0, 1, 2)  # mirror + Sommerfeld (5) is not sliced
+        # grf_rk4_step_host overlaps the copies slab by slab for 3 ghost layers with image or frozen
+        # ghosts; other boxes get whole-state copies around the device step
+        sliced = box.ng == 3 and box.bc in (0, 1, 2)
 
         def host_step():
-            if sliced:
-                grf.grf_rk4_step_host(b, p, host_in, host_out, state, dt, 1, ws=ws, stream=stream)
-            else:  # copy in, step, copy out (cudaMemcpyAsync from / to the pinned buffers)
-                state.copy_(host_in, non_blocking=True)
-                grf.grf_rk4_step(b, p, state, dt, 1, ws=ws, stream=stream)
-                host_out.copy_(state, non_blocking=True)
+            grf.grf_rk4_step_host(b, p, host_in, host_out, state, dt, 1, ws=ws, stream=stream)
 
         host_step()
         barrier()
@@ -604,8 +599,8 @@ def run_ours(args, rank, world, local_rank):
                "bit_identical_to_device_step": identical,
                "path": ("grf_rk4_step_host: pinned host -> device in z-slabs overlapped with stage 1, "
                         "stage 4 in z-slabs overlapped with device -> pinned host, every step") if sliced else
-                       ("pinned host -> device copy, grf_rk4_step, device -> pinned host copy, every step "
-                        "(not overlapped)")}
+                       ("grf_rk4_step_host: whole-state pinned host -> device copy by the SMs, the device step, "
+                        "whole-state copy back, every step (not overlapped)")}
 
     if rank != 0:
         if dist is not None:

@@ -67,8 +67,7 @@ enum { GRF_OP_RHS = 0, GRF_OP_RK4 = 1, GRF_OP_CONSTRAINTS = 2 };
  *           sigma/(64 dx) sum_d Delta^6_d, lopsided advection on offsets -1..3;
  *   ng = 4: centred 6th-order differences, dissipation -sigma/(256 dx) sum_d Delta^8_d,
  *           lopsided advection on offsets -2..4.
- * 4-ghost boxes are accepted by grf_rhs, grf_rk4_step(_noalloc), grf_constraints,
- * grf_energy_densities, grf_ko_dissipation, grf_fill_ghosts and grf_check_finite. */
+ * 4-ghost boxes are accepted by every call but grf_batched_rk4 and grf_tlm_rk4. */
 typedef struct {
     int nx, ny, nz;       /* interior points per axis, each >= 1 (periodic, mirror: >= ng) */
     int ng;               /* ghost layers: 3 or 4 (above) */
@@ -104,7 +103,7 @@ typedef struct {
                              a coordinate below the box is a mirror image, refilled after each
                              stage. Needs n >= ng.
                            Extrapolating and Sommerfeld boxes (also behind mirror planes) are not
-                             accepted by grf_rk4_step_host, grf_batched_rk4 and grf_tlm_rk4. */
+                             accepted by grf_batched_rk4 and grf_tlm_rk4. */
     long long pitch;      /* doubles per x row, >= nx + 2 ng */
 } grf_box;
 
@@ -171,8 +170,11 @@ int grf_rk4_step(const grf_box* box, const grf_params* params, double* state, do
  * copies are staged by the driver and overlap the kernels poorly.
  * The first call on a device creates that device's copy stream and events (no memory is
  * allocated); make it before any stream capture. Calls from several host threads are
- * serialised while they queue work. Errors: GRF_EINVAL (box, params, null pointers, nsteps < 0,
- * ng = 4: the slab pipeline is laid out for 3 ghost layers), GRF_EWORKSPACE, GRF_ECUDA. */
+ * serialised while they queue work. The slab pipeline serves boxes with 3 ghost layers whose
+ * ghosts are periodic or mirror images or frozen; other boxes (4 ghost layers, extrapolated or
+ * Sommerfeld ghosts) copy the whole state in by the same copy path, run grf_rk4_step and copy it
+ * out, without the overlap. Errors: GRF_EINVAL (box, params, null pointers, nsteps < 0),
+ * GRF_EWORKSPACE, GRF_ECUDA. */
 int grf_rk4_step_host(const grf_box* box, const grf_params* params, const double* host_in,
                       double* host_out, double* state, double dt, int nsteps, void* ws,
                       size_t ws_bytes, grf_stream_t stream);

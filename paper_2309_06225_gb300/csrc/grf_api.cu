@@ -523,7 +523,6 @@ int grf_rk4_step(const grf_box* box, const grf_params* params, double* state, do
     a.acc = acc;
     const dim3 grd = stage_grid(g, g.nz, a.fold);
     // outer boundaries after each stage: Sommerfeld ghosts take the same stage update, extrapolated
-    // ghosts are refilled from the stage's new interior
     // ghosts are refilled from the stage's new interior; behind mirror planes the images of the
     // evolved high-face ghosts follow their update
     auto boundary = [&](int stage) {
@@ -556,10 +555,6 @@ int grf_rk4_step(const grf_box* box, const grf_params* params, double* state, do
 int grf_rk4_step_host(const grf_box* box, const grf_params* params, const double* host_in, double* host_out,
                       double* state, double dt, int nsteps, void* ws, size_t ws_bytes, grf_stream_t stream) {
     if (!box_ok(box) || !params_ok(params) || !host_in || !host_out || !state || nsteps < 0) return GRF_EINVAL;
-    // the slab pipeline is laid out for 3 ghost layers and ghosts that are state or images
-    if (box->ng != NG || box->bc == GRF_BC_EXTRAPOLATE || box->bc == GRF_BC_SOMMERFELD ||
-        box->bc == GRF_BC_REFLECT_LOW_SOMMERFELD)
-        return GRF_EINVAL;
     Geom g = make_geom(box);
     const size_t sb = state_bytes(g);
     if (!ws || ws_bytes < 3 * sb || ((uintptr_t)ws & 255)) return GRF_EWORKSPACE;
@@ -580,6 +575,27 @@ int grf_rk4_step_host(const grf_box* box, const grf_params* params, const double
         runs.dst[0] = runs.src[0] = 0;
         runs.len[0] = (long long)(sb / sizeof(double));
         e = copy_runs(runs, host_in, dev_in, state, state, cudaMemcpyHostToDevice, P.copy);
+        if (e == cudaSuccess) e = copy_runs(runs, state, state, host_out, dev_out, cudaMemcpyDeviceToHost, P.copy);
+        if (e == cudaSuccess) e = cudaEventRecord(P.done, P.copy);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, P.done, 0);
+        return e == cudaSuccess ? GRF_OK : cuda_fail(e);
+    }
+    // The slab pipeline below is laid out for 3 ghost layers whose ghosts are images or frozen state.
+    // Other boxes (4 ghost layers; extrapolated or Sommerfeld ghosts) copy the whole state in, run
+    // the device step, and copy it out, with the same stream ordering.
+    if (box->ng != NG || box->bc == GRF_BC_EXTRAPOLATE || box->bc == GRF_BC_SOMMERFELD ||
+        box->bc == GRF_BC_REFLECT_LOW_SOMMERFELD) {
+        runs.n = 1;
+        runs.dst[0] = runs.src[0] = 0;
+        runs.len[0] = (long long)(sb / sizeof(double));
+        e = copy_runs(runs, host_in, dev_in, state, state, cudaMemcpyHostToDevice, P.copy);
+        if (e == cudaSuccess) e = cudaEventRecord(P.h2d[0], P.copy);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, P.h2d[0], 0);
+        if (e != cudaSuccess) return cuda_fail(e);
+        const int r = grf_rk4_step(box, params, state, dt, nsteps, ws, ws_bytes, stream);
+        if (r) return r;
+        e = cudaEventRecord(P.s4[0], st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(P.copy, P.s4[0], 0);
         if (e == cudaSuccess) e = copy_runs(runs, state, state, host_out, dev_out, cudaMemcpyDeviceToHost, P.copy);
         if (e == cudaSuccess) e = cudaEventRecord(P.done, P.copy);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st, P.done, 0);

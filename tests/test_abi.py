@@ -70,9 +70,9 @@ def test_host_step_validation_without_gpu(grf):
 
 
 def test_scheme_validation_without_gpu(grf):
-    """4-ghost boxes (6th-order scheme) are sized with their ghosts; the host-to-host step rejects
-    them; lopsided advection is rejected by the batched and tangent calls and any other advection
-    value everywhere, all before a CUDA call."""
+    """4-ghost boxes (6th-order scheme) are sized with their ghosts; lopsided advection is rejected
+    by the batched and tangent calls and any other advection value everywhere, all before a CUDA
+    call."""
     b6 = grf.make_box(20, 18, 16, 0.25, ng=4)
     assert b6.pitch >= 28 and b6.pitch % 4 == 0
     assert grf.grf_workspace_bytes(b6, grf.GRF_OP_RK4) == 3 * 8 * 27 * 24 * 26 * b6.pitch
@@ -81,7 +81,7 @@ def test_scheme_validation_without_gpu(grf):
     L = grf.lib()
     fake = C.c_void_p(0x1000)
     p = grf.grf_params()
-    assert L.grf_rk4_step_host(C.byref(b6), C.byref(p), fake, fake, fake, 0.1, 1, fake, 1 << 40, None) == grf.GRF_EINVAL
+    assert L.grf_rk4_step_host(C.byref(b6), C.byref(p), None, fake, fake, 0.1, 1, fake, 1 << 40, None) == grf.GRF_EINVAL
     b3 = grf.make_box(16, 16, 16, 0.25)
     p.advection = 2
     assert L.grf_rhs(C.byref(b3), C.byref(p), fake, fake, None, 0, None) == grf.GRF_EINVAL
@@ -98,14 +98,14 @@ def test_scheme_validation_without_gpu(grf):
 
 
 def test_outer_boundaries_validation_without_gpu(grf):
-    """Extrapolating and Sommerfeld boxes need n >= ng and are refused by the host-to-host step."""
+    """Extrapolating and Sommerfeld boxes need n >= ng."""
     L = grf.lib()
     fake = C.c_void_p(0x1000)
     p = grf.grf_params()
     for bc in (grf.GRF_BC_EXTRAPOLATE, grf.GRF_BC_SOMMERFELD):
         b = grf.make_box(8, 8, 8, 0.25, bc=bc)
         assert grf.grf_workspace_bytes(b, grf.GRF_OP_RK4) > 0
-        assert L.grf_rk4_step_host(C.byref(b), C.byref(p), fake, fake, fake, 0.1, 1, fake, 1 << 40, None) == grf.GRF_EINVAL
+        assert L.grf_rk4_step_host(C.byref(b), C.byref(p), fake, fake, None, 0.1, 1, fake, 1 << 40, None) == grf.GRF_EINVAL
         assert grf.grf_workspace_bytes(grf.make_box(2, 8, 8, 0.25, bc=bc), grf.GRF_OP_RK4) == 0
     assert grf.grf_workspace_bytes(grf.make_box(8, 8, 8, 0.25, bc=6), grf.GRF_OP_RK4) == 0
 
@@ -133,6 +133,6 @@ def test_mirror_sommerfeld_validation_without_gpu(grf):
     p = grf.grf_params()
     b = grf.make_box(8, 8, 8, 0.25, bc=grf.GRF_BC_REFLECT_LOW_SOMMERFELD)
     assert grf.grf_workspace_bytes(b, grf.GRF_OP_RK4) > 0
-    assert L.grf_rk4_step_host(C.byref(b), C.byref(p), fake, fake, fake, 0.1, 1, fake, 1 << 40, None) == grf.GRF_EINVAL
+    assert L.grf_rk4_step_host(C.byref(b), C.byref(p), fake, None, fake, 0.1, 1, fake, 1 << 40, None) == grf.GRF_EINVAL
     assert grf.grf_workspace_bytes(grf.make_box(2, 8, 8, 0.25, bc=grf.GRF_BC_REFLECT_LOW_SOMMERFELD),
                                    grf.GRF_OP_RK4) == 0

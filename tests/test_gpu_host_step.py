@@ -159,3 +159,35 @@ def test_host_step_pinned_input_pageable_output(g):
     g.grf_rk4_step_host(b, params, hin, hout, g.alloc_state(b), 0.25 * box.dx, 2)
     torch.cuda.synchronize()
     assert np.array_equal(hout[..., :box.nx + 6], ref.numpy()[..., :box.nx + 6])
+
+
+OTHER_BOXES = {
+    # boxes outside the slab pipeline: whole-state copies around the device step
+    "sixth_order_periodic": (gi.Box(14, 11, 12, 0.3, -2.0, -1.6, -1.8, ng=4), dict()),
+    "sommerfeld": (gi.Box(14, 12, 11, 0.3, -1.95, -1.65, -1.5, bc=gi.BC_SOMMERFELD), dict()),
+    "extrapolating_lopsided": (gi.Box(13, 12, 10, 0.3, -1.8, -1.65, -1.35, bc=gi.BC_EXTRAPOLATE), dict(advection=1)),
+    "mirror_sommerfeld_sixth": (gi.Box(12, 11, 10, 0.3, 0.15, 0.15, 0.15, bc=gi.BC_REFLECT_LOW_SOMMERFELD, ng=4),
+                                dict()),
+}
+
+
+@pytest.mark.parametrize("case", sorted(OTHER_BOXES))
+def test_host_step_other_boxes_bit_identical(g, case):
+    import torch
+    box, extra = OTHER_BOXES[case]
+    b = g.box_like(box)
+    params = g.params_like(gi.Params(lam=0.2, g2=0.1, beta_kind=gi.BETA_QUADRATIC, **extra))
+    base = gi.mirror_symmetric_state(box) if box.bc == gi.BC_REFLECT_LOW_SOMMERFELD else None
+    s0 = gi.random_perturbed_state(box, 13, base=base if base is not None else gi.single_puncture(box, amp=0.05),
+                                   eps=2e-2)
+    hin = torch.zeros(g.state_shape(b), dtype=torch.float64, pin_memory=True)
+    hin[..., :box.nx + 2 * box.ng] = torch.from_numpy(s0)
+    dt = 0.25 * box.dx
+    dev = hin.cuda()
+    g.grf_rk4_step(b, params, dev, dt, 2)
+    ref = dev.cpu()
+    hout = torch.full_like(hin, float("nan")).pin_memory()
+    g.grf_rk4_step_host(b, params, hin, hout, g.alloc_state(b), dt, 2)
+    torch.cuda.synchronize()
+    w = box.nx + 2 * box.ng
+    assert torch.equal(hout[..., :w], ref[..., :w]), case
