@@ -163,13 +163,7 @@ __global__ void __launch_bounds__(256) sommerfeld_kernel(Geom g, StageArgs a, do
             continue;
         }
         const double unf = (STAGE == 0) ? src[p] : a.un[fo + p];
-        double accf;
-        if (STAGE == 0) accf = kf;
-        else if (STAGE == 3) accf = a.acc[fo + p] + kf;
-        else accf = a.acc[fo + p] + 2.0 * kf;
-        if (STAGE < 3) a.acc[fo + p] = accf;
-        const double cs = (STAGE == 0 || STAGE == 1) ? 0.5 * a.dt : (STAGE == 2 ? a.dt : a.dt * (1.0 / 6.0));
-        a.dst[fo + p] = (STAGE == 3) ? fma(cs, accf, unf) : fma(cs, kf, unf);
+        a.dst[fo + p] = rk4_value<STAGE < 0 ? 0 : STAGE>(a, fo + p, kf, unf);
     }
 }
 

@@ -308,6 +308,21 @@ struct StageArgs {
 // Lopsided advection: the ADV terms of point_rhs come from in.adv (filled by the gather).
 constexpr int kLopsided = 1;
 
+// RK4 stage arithmetic for one value at offset q (u_1 = u_n + dt/2 k_1, u_2 = u_n + dt/2 k_2,
+// u_3 = u_n + dt k_3, u_{n+1} = u_n + dt/6 (k_1 + 2 k_2 + 2 k_3 + k_4)): kf the stage's right-hand
+// side, unf = u_n; the accumulator a.acc[q] is read (STAGE > 0) and written (STAGE < 3). Returns
+// the stage's output value.
+template <int STAGE>
+__device__ __forceinline__ double rk4_value(const StageArgs& a, long long q, double kf, double unf) {
+    double accf;
+    if (STAGE == 0) accf = kf;
+    else if (STAGE == 3) accf = a.acc[q] + kf;
+    else accf = a.acc[q] + 2.0 * kf;
+    if (STAGE < 3) a.acc[q] = accf;
+    const double cs = (STAGE == 0 || STAGE == 1) ? 0.5 * a.dt : (STAGE == 2 ? a.dt : a.dt * (1.0 / 6.0));
+    return (STAGE == 3) ? fma(cs, accf, unf) : fma(cs, kf, unf);
+}
+
 // How a stage's gather takes its mixed derivatives (all modes give the same bits).
 enum GatherMode {
     GATHER_LOCAL = 0,  // per thread
@@ -347,13 +362,7 @@ __device__ __forceinline__ void stage_point(const Geom& g, const Coeffs& c, cons
     for (int f = 0; f < NFIELDS; ++f) {
         const double kf = r[f] + a.ko * kos[f];
         const double unf = (STAGE == 0) ? in.v[f] : a.un[f * g.fstride + p];
-        double accf;
-        if (STAGE == 0) accf = kf;
-        else if (STAGE == 3) accf = a.acc[f * g.fstride + p] + kf;
-        else accf = a.acc[f * g.fstride + p] + 2.0 * kf;
-        if (STAGE < 3) a.acc[f * g.fstride + p] = accf;
-        const double cs = (STAGE == 0 || STAGE == 1) ? 0.5 * a.dt : (STAGE == 2 ? a.dt : a.dt * (1.0 / 6.0));
-        out[f] = (STAGE == 3) ? fma(cs, accf, unf) : fma(cs, kf, unf);
+        out[f] = rk4_value<STAGE>(a, f * g.fstride + p, kf, unf);
     }
     if (a.enforce) enforce_point(out, a.min_chi, a.min_lapse);
 #pragma unroll 1

@@ -255,13 +255,7 @@ __device__ __forceinline__ void stage_point6(const Geom& g, const Coeffs& c, con
     for (int f = 0; f < NFIELDS; ++f) {
         const double kf = r[f] + a.ko * kos[f];
         const double unf = (STAGE == 0) ? in.v[f] : a.un[f * g.fstride + p];
-        double accf;
-        if (STAGE == 0) accf = kf;
-        else if (STAGE == 3) accf = a.acc[f * g.fstride + p] + kf;
-        else accf = a.acc[f * g.fstride + p] + 2.0 * kf;
-        if (STAGE < 3) a.acc[f * g.fstride + p] = accf;
-        const double cs = (STAGE == 0 || STAGE == 1) ? 0.5 * a.dt : (STAGE == 2 ? a.dt : a.dt * (1.0 / 6.0));
-        out[f] = (STAGE == 3) ? fma(cs, accf, unf) : fma(cs, kf, unf);
+        out[f] = rk4_value<STAGE>(a, f * g.fstride + p, kf, unf);
     }
     if (a.enforce) enforce_point(out, a.min_chi, a.min_lapse);
 #pragma unroll 1
