@@ -4,16 +4,25 @@
 
 namespace grf {
 
-// Blocks of (32, 4, 1) threads, one point each. LOP: lopsided advection.
+// Blocks of (32, 4, 1) threads (block gather, as rk4_stage6_kernel). LOP: lopsided advection.
 template <int LOP>
 __global__ void __launch_bounds__(128) rhs6_kernel(Geom g, Coeffs c, const double* __restrict__ s,
                                                    double* __restrict__ rhs, double ko, int* status) {
-    int i, j, k;
-    if (!interior_thread(g, i, j, k)) return;
-    const long long p = gidx(g, i + NG6, j + NG6, k + NG6);
+    __shared__ YzRows6 sh;
+    const int lane = threadIdx.x;
+    const int i = blockIdx.x * 32 + lane;
+    const int j = blockIdx.y * 4 + threadIdx.y;
+    const int k = blockIdx.z;
+    yz_rows_fill6(g, s, i, blockIdx.y * 4, threadIdx.y, k, lane, sh);
+    __syncthreads();
+    const int jc = min(j, g.ny + 2);
+    const long long p = gidx(g, min(i, g.nx + 2) + NG6, jc + NG6, k + NG6);
     PointIn in;
     double kos[NFIELDS], adv[LOP ? NFIELDS : 1];
-    gather6<LOP>(g, s, p, in, kos, adv);
+    WarpRow6 wr;
+    warp_row_halo6(g, s, i - lane, jc, k, lane, wr);
+    gather6_block<LOP>(g, s, p, in, kos, adv, wr, sh, threadIdx.y);
+    if (i >= g.nx || j >= g.ny) return;
     double r[NFIELDS];
     bool ok = true;
     point_rhs<double, double, -1, LOP>(c, in, r, nullptr, ok, adv);
