@@ -40,6 +40,20 @@ def test_library_exports_every_declared_symbol(grf):
         assert hasattr(L, name), name
 
 
+def test_peak_library_exports_its_declared_symbol():
+    """include/grf_peak.h (the FP64 microbenchmark of the roofline denominator) and libgrf_peak.so."""
+    from paper_2309_06225_gb300 import build_peak
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "grf_peak.h")).read(), flags=re.S)
+    names = sorted(set(re.findall(r"\b(grf_[a-z0-9_]+)\s*\(", src)))
+    assert names == ["grf_peak_fp64"]
+    try:
+        L = C.CDLL(build_peak.build())
+    except OSError as e:  # libcudart missing on a machine without the toolkit
+        pytest.skip(f"cannot load libgrf_peak.so here: {e}")
+    for name in names:
+        assert hasattr(L, name), name
+
+
 def test_workspace_and_validation_without_gpu(grf):
     b = grf.make_box(32, 32, 32, 0.25)
     nbytes = grf.grf_workspace_bytes(b, grf.GRF_OP_RK4)
