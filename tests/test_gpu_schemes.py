@@ -265,3 +265,34 @@ def test_mirror_planes_with_sommerfeld_faces_parity(g, orc, ng):
     gpu = gpu_rk4(g, box, params, s0, 0.25 * box.dx, 3)
     errs = _all_points_errors(gpu, cpu)
     assert np.max(errs) < 1e-10, describe(errs)
+
+
+@pytest.mark.parametrize("ng,advection", [(3, 1), (4, 0), (4, 1)])
+def test_bl_pair_256_sampled_outputs_schemes(g, orc, ng, advection):
+    """The 256^3 workload (bench.py --order / --advection) in its production launch, one RK4 step;
+    sampled points recomputed by the oracle on frozen-ghost sub-boxes whose ghosts lie beyond the
+    step's domain of dependence (4 stages x the stencil reach: 12 points with 3 ghost layers, 16
+    with 4), so their centres are exact."""
+    import dataclasses
+    cfg = gi.config_bl_pair_256()
+    box = dataclasses.replace(cfg["box"], ng=ng)
+    params = P(**{k: v for k, v in cfg["params"].to_dict().items()})
+    params.advection = advection
+    s0 = gi.brill_lindquist_pair(box)
+    gpu = gpu_rk4(g, box, params, s0, cfg["dt"], 1)
+    assert np.all(np.isfinite(box.interior(gpu)))
+    orc.fill_ghosts(box, s0)
+    R = 16 - ng
+    n = box.nx
+    rng = np.random.default_rng(7 + ng + advection)
+    samples = [(128, 128, 128 + 24)] + [tuple(int(x) for x in rng.integers(0, n, 3)) for _ in range(2)]
+    scale = np.maximum(np.max(np.abs(box.interior(gpu)), axis=(1, 2, 3)), 1e-12)
+    for (i, j, k) in samples:
+        sub = gi.Box(2 * R + 1, 2 * R + 1, 2 * R + 1, box.dx, 0.0, 0.0, 0.0, bc=gi.BC_FROZEN, ng=ng)
+        idx = [(np.arange(2 * R + 1 + 2 * ng) + c - R - ng) % n + ng for c in (k, j, i)]
+        ss = np.ascontiguousarray(s0[:, idx[0]][:, :, idx[1]][:, :, :, idx[2]])
+        orc.rk4(sub, params, ss, cfg["dt"], 1)
+        ref = ss[:, R + ng, R + ng, R + ng]
+        got = gpu[:, k + ng, j + ng, i + ng]
+        err = np.abs(got - ref) / scale
+        assert np.max(err) < 1e-11, (i, j, k, describe(err))
