@@ -296,3 +296,21 @@ def test_bl_pair_256_sampled_outputs_schemes(g, orc, ng, advection):
         got = gpu[:, k + ng, j + ng, i + ng]
         err = np.abs(got - ref) / scale
         assert np.max(err) < 1e-11, (i, j, k, describe(err))
+
+
+@pytest.mark.parametrize("bc,ng", [(gi.BC_SOMMERFELD, 3), (gi.BC_EXTRAPOLATE, 4), (gi.BC_REFLECT_LOW_SOMMERFELD, 3)])
+def test_outer_boundaries_multi_tile(g, orc, bc, ng):
+    """Outer boundaries on a box spanning two 32-wide tiles with ragged x and y edges, 2 RK4 steps,
+    every point against the oracle."""
+    if bc == gi.BC_REFLECT_LOW_SOMMERFELD:
+        box = gi.Box(37, 10, 6, 0.3, 0.15, 0.15, 0.15, bc=bc, ng=ng)
+        s0 = gi.random_perturbed_state(box, 89, base=gi.mirror_symmetric_state(box), eps=2e-2)
+    else:
+        box = gi.Box(37, 10, 6, 0.3, -5.4, -1.35, -0.75, bc=bc, ng=ng)
+        s0 = state_for(box, 89)
+    params = P(lam=0.2, g2=0.1, beta_kind=1)
+    cpu = s0.copy()
+    orc.rk4(box, params, cpu, 0.25 * box.dx, 2)
+    gpu = gpu_rk4(g, box, params, s0, 0.25 * box.dx, 2)
+    errs = _all_points_errors(gpu, cpu)
+    assert np.max(errs) < 1e-10, describe(errs)
