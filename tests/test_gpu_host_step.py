@@ -64,7 +64,9 @@ CASES = {
     "periodic_minimal_one_slab": (gi.Box(3, 3, 3, 0.4, -0.5, -0.5, -0.5), 2),
     "frozen_single_plane": (gi.Box(5, 4, 1, 0.3, 0.9, 0.6, -1.2, bc=gi.BC_FROZEN), 1),
     "periodic_two_slabs_3_steps": (gi.Box(12, 10, 8, 0.3, -1.7, -1.4, -1.1), 3),
+    "periodic_lopsided_8_slabs": (gi.Box(17, 12, 33, 0.3, -2.5, -1.7, -4.8), 2),
 }
+LOPSIDED = {"periodic_lopsided_8_slabs"}
 
 
 @pytest.mark.parametrize("case", sorted(CASES))
@@ -72,7 +74,8 @@ def test_host_step_bit_identical_to_device_step(g, case):
     import torch
     box, nsteps = CASES[case]
     b = g.box_like(box)
-    params = g.params_like(gi.Params(lam=0.2, g2=0.1, beta_kind=gi.BETA_QUADRATIC))
+    params = g.params_like(gi.Params(lam=0.2, g2=0.1, beta_kind=gi.BETA_QUADRATIC,
+                                     advection=1 if case in LOPSIDED else 0))
     periodic = box.bc == gi.BC_PERIODIC
     hin = host_state(g, box, initial(box, 5), poison_ghosts=periodic)
     dt = 0.25 * box.dx

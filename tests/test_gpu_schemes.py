@@ -314,3 +314,10 @@ def test_outer_boundaries_multi_tile(g, orc, bc, ng):
     gpu = gpu_rk4(g, box, params, s0, 0.25 * box.dx, 2)
     errs = _all_points_errors(gpu, cpu)
     assert np.max(errs) < 1e-10, describe(errs)
+
+
+def test_sixth_order_decoupled_parity(g, orc):
+    """The 6th-order kernels read the decoupled mode at run time: RHS and 2 RK4 steps without
+    backreaction against the oracle."""
+    box = gi.Box(12, 11, 10, 0.3, -1.65, -1.5, -1.35, bc=gi.BC_PERIODIC, ng=4)
+    check_rhs_and_rk4(g, orc, box, P(lam=0.3, g2=0.2, beta_kind=1, decoupled=1, advection=1), 97, nsteps=2)
