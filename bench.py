@@ -37,6 +37,9 @@ BYTES_PER_POINT_UPDATE = 216 * (3 + 5 + 5 + 4)
 # dram__bytes_read.sum + dram__bytes_write.sum of one stage launch per interior point, from the
 # ncu capture of the current stage kernel (profiles/); None when the kernel changed since.
 TRAFFIC_BYTES_PER_POINT_STAGE = 12619  # mean of stage 0 and 1, 96^3 capture (profiles/rk4_stage_kernel_bl_pair_96.md)
+# the 6th-order stage kernel with centred advection (profiles/rk4_stage6_kernel_bl_pair_96.md, mean of stages 0, 1)
+FP64_INSTR_PER_POINT_STAGE_6 = 4835
+TRAFFIC_BYTES_PER_POINT_STAGE_6 = 11033
 # FP64 thread instructions (dadd + dmul + dfma) per interior point and stage, same capture; the
 # pipe issues 2 per SM per clock (152 SMs x 2 x 2.06 GHz = 6.26e11 / s, half the flop peak).
 FP64_INSTR_PER_POINT_STAGE = 4161
@@ -619,15 +622,19 @@ def run_ours(args, rank, world, local_rank):
             "peak_dfma_microbenchmark": peak, "flop_per_point_stage": flop_ps,
             "flop_convention": "counted from the kernel source: add/sub/mul 1, fma 2, div 1",
             "traffic": TRAFFIC_BYTES_PER_POINT_STAGE * npts if TRAFFIC_BYTES_PER_POINT_STAGE and default_scheme else None}
+    sixth_centred = scheme == {"order": 6, "advection": "centred"}
+    if sixth_centred:
+        roof["traffic"] = TRAFFIC_BYTES_PER_POINT_STAGE_6 * npts
     if not default_scheme:
         roof["note"] = ("flop_per_point_stage is the count of the 4th-order centred scheme; this scheme does more "
                         "work per point, so achieved and frac are lower bounds")
     hbm_gbs, hbm_src = measured_hbm_gbs()
     roof["hbm_frac"] = BYTES_PER_POINT_UPDATE * value / (hbm_gbs * 1e9)
     roof["hbm_peak_source"] = f"{hbm_src} {hbm_gbs:.1f} GB/s"
-    if FP64_INSTR_PER_POINT_STAGE and default_scheme:
+    if FP64_INSTR_PER_POINT_STAGE and (default_scheme or sixth_centred):
         # how full the FP64 pipe is: adds and multiplies take an issue slot but count one flop
-        roof["fp64_issue_frac"] = FP64_INSTR_PER_POINT_STAGE * npts / (launch_ms * 1e-3) / (FP64_PEAK_TFLOPS * 1e12 / 2)
+        instr = FP64_INSTR_PER_POINT_STAGE if default_scheme else FP64_INSTR_PER_POINT_STAGE_6
+        roof["fp64_issue_frac"] = instr * npts / (launch_ms * 1e-3) / (FP64_PEAK_TFLOPS * 1e12 / 2)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
