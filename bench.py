@@ -42,7 +42,7 @@ FP64_INSTR_PER_POINT_STAGE_6 = 4835
 TRAFFIC_BYTES_PER_POINT_STAGE_6 = 11033
 # FP64 thread instructions (dadd + dmul + dfma) per interior point and stage, same capture; the
 # pipe issues 2 per SM per clock (152 SMs x 2 x 2.06 GHz = 6.26e11 / s, half the flop peak).
-FP64_INSTR_PER_POINT_STAGE = 4161
+FP64_INSTR_PER_POINT_STAGE = 4162
 # FP64 (non-tensor) peak of GB300: 152 SMs x 2 FP64 FMA lanes/clk x 2 flop x ~2.06 GHz = 1.25 TFLOP/s
 FP64_PEAK_TFLOPS = 1.25
 
