@@ -125,7 +125,7 @@ typedef struct {
                                         1: lopsided differences, one point further towards the side
                                         beta^k points to (every beta^k d_k of an evolved field, those
                                         inside the coupled 4dST system included). 1 is not accepted by
-                                        grf_batched_rk4 and grf_tlm_rk4 */
+                                        grf_tlm_rk4 */
 } grf_params;
 
 /* d_t of all 27 fields at the interior points of `state` (modified CCZ4 + 4dST, section

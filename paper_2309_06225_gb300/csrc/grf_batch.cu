@@ -16,75 +16,10 @@
 #include <vector>
 
 #include "grf.h"
-#include "grf_kernels.cuh"
+#include "grf_batch.cuh"
 #include "grf_launch.h"
 
 namespace grf {
-
-struct BoxDesc {
-    Geom g;
-    Coeffs c;
-    double* un;
-    double* A;
-    double* B;
-    double* acc;
-    double dt, ko, min_chi, min_lapse;
-    int enforce;
-    int pad_;
-};
-
-struct TileDesc {
-    int box, i0, j0, k0;
-    int w;  // x-points per row: blockDim.x (one row per warp), or 8 / 16 (a folded 32-wide tile:
-            // each warp covers 32 / w rows of a narrow box)
-};
-
-template <int STAGE, int DEC>
-__device__ __forceinline__ void batch_tile(const BoxDesc* __restrict__ boxes, const TileDesc& td, int* status,
-                                           YzRows& sh) {
-    const BoxDesc& d = boxes[td.box];
-    const bool folded = td.w != (int)blockDim.x;
-    const int i = td.i0 + (folded ? (int)threadIdx.x % td.w : (int)threadIdx.x);
-    const int j = td.j0 + (folded ? (int)threadIdx.y * ((int)blockDim.x / td.w) + (int)threadIdx.x / td.w : (int)threadIdx.y);
-    const int k = td.k0 + threadIdx.z;
-    // Tile shape -> gather mode (all modes give the same bits):
-    //   32 x 4 x 1: block mode, d_y d_z through the shared rows; every thread stays to the barrier.
-    //   width a multiple of 32: warp mode; whole warps stay for the shuffles.
-    //   folded tiles and other shapes: per-thread mode.
-    const int mode = folded ? GATHER_LOCAL
-                     : ((blockDim.x == 32 && blockDim.y == 4 && blockDim.z == 1) ? GATHER_BLOCK
-                        : ((blockDim.x & 31) == 0 ? GATHER_WARP : GATHER_LOCAL));
-    StageArgs a;
-    a.un = d.un;
-    a.acc = d.acc;
-    a.dt = d.dt;
-    a.ko = d.ko;
-    a.min_chi = d.min_chi;
-    a.min_lapse = d.min_lapse;
-    a.enforce = d.enforce;
-    a.status = status;
-    a.k0 = 0;
-    a.fold = 32;
-    a.src = (STAGE == 0) ? d.un : (STAGE == 1 ? d.A : (STAGE == 2 ? d.B : d.A));
-    a.dst = (STAGE == 0) ? d.A : (STAGE == 1 ? d.B : (STAGE == 2 ? d.A : d.un));
-    if (mode == GATHER_BLOCK) {
-        if (k >= d.g.nz) return;  // the whole block (k = td.k0)
-        __syncthreads();          // readers of the previous tile's rows are done
-        yz_rows_fill(d.g, a.src, i, td.j0, threadIdx.y, k, threadIdx.x, sh);
-        __syncthreads();
-    } else if (j >= d.g.ny || k >= d.g.nz || (mode == GATHER_LOCAL && i >= d.g.nx)) {
-        return;
-    }
-    stage_point<STAGE, DEC>(d.g, d.c, a, i, j, k, mode, &sh);
-}
-
-// Out-of-line copy of batch_tile for the persistent kernel: with the four stages inlined into one
-// kernel, ptxas spilled 52 KB per thread; called, each stage is allocated on its own (13 KB).
-template <int STAGE, int DEC>
-__device__ __noinline__ void batch_tile_call(const BoxDesc* __restrict__ boxes, const TileDesc& td, int* status,
-                                             YzRows& sh) {
-    batch_tile<STAGE, DEC>(boxes, td, status, sh);
-}
 
 template <int STAGE>
 __global__ void __launch_bounds__(128, 3) batch_stage_kernel(const BoxDesc* __restrict__ boxes,
@@ -93,68 +28,12 @@ __global__ void __launch_bounds__(128, 3) batch_stage_kernel(const BoxDesc* __re
     const int t = blockIdx.x;
     if (t >= ntiles) return;
     const TileDesc td = tiles[t];
-    // the decoupled mode is a compile-time instantiation (as in the single-box kernels, whose bits
-    // these must match); the full theory stays inlined
-    if (boxes[td.box].c.decoupled) batch_tile_call<STAGE, 1>(boxes, td, status, sh);
-    else batch_tile<STAGE, 0>(boxes, td, status, sh);
-}
-
-// Grid-wide barrier for a cooperative launch. Thread 0 of each block arrives on a counter;
-// the last arrival resets it and bumps the generation. Waiting is bounded by `timeout`
-// clock cycles: on expiry the status word gets bit 2 and false is returned (the caller
-// returns from the kernel), so a barrier can never hang the device.
-__device__ bool grid_barrier(unsigned* bar, unsigned nblocks, long long timeout, int* status) {
-    __shared__ int ok_s;
-    __syncthreads();
-    if (threadIdx.x == 0 && threadIdx.y == 0 && threadIdx.z == 0) {
-        int ok = 1;
-        volatile unsigned* gen = bar + 1;
-        const unsigned g0 = *gen;
-        __threadfence();
-        const unsigned arrived = atomicAdd(bar, 1u) + 1u;
-        if (arrived == nblocks) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            const long long t0 = clock64();
-            while (*gen == g0) {
-                if (clock64() - t0 > timeout) {
-                    atomicOr(status, 2);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(256);
-            }
-        }
-        __threadfence();
-        ok_s = ok;
-    }
-    __syncthreads();
-    return ok_s != 0;
-}
-
-__global__ void __launch_bounds__(128, 3) batch_persistent_kernel(const BoxDesc* __restrict__ boxes,
-                                                               const TileDesc* __restrict__ tiles, int ntiles,
-                                                               int nsteps, unsigned* bar, int* status,
-                                                               long long timeout) {
-    __shared__ YzRows sh;
-    for (int n = 0; n < nsteps; ++n) {
-#pragma unroll 1
-        for (int s = 0; s < 4; ++s) {
-            for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-                const TileDesc td = tiles[t];
-                const bool dec = boxes[td.box].c.decoupled != 0;
-                switch (s) {
-                    case 0: dec ? batch_tile_call<0, 1>(boxes, td, status, sh) : batch_tile_call<0, 0>(boxes, td, status, sh); break;
-                    case 1: dec ? batch_tile_call<1, 1>(boxes, td, status, sh) : batch_tile_call<1, 0>(boxes, td, status, sh); break;
-                    case 2: dec ? batch_tile_call<2, 1>(boxes, td, status, sh) : batch_tile_call<2, 0>(boxes, td, status, sh); break;
-                    default: dec ? batch_tile_call<3, 1>(boxes, td, status, sh) : batch_tile_call<3, 0>(boxes, td, status, sh); break;
-                }
-            }
-            if (!grid_barrier(bar, gridDim.x, timeout, status)) return;
-        }
-    }
+    // the decoupled mode and lopsided advection are compile-time instantiations (as in the single-box
+    // kernels, whose bits these must match); the full theory with centred advection stays inlined
+    const Coeffs& c = boxes[td.box].c;
+    if (c.advection) batch_tile_call<STAGE, -1, 1>(boxes, td, status, sh);
+    else if (c.decoupled) batch_tile_call<STAGE, 1, 0>(boxes, td, status, sh);
+    else batch_tile<STAGE, 0, 0>(boxes, td, status, sh);
 }
 
 __global__ void batch_ghost_fill_kernel(const BoxDesc* __restrict__ boxes, int box) {
@@ -348,7 +227,7 @@ int grf_batched_rk4(const grf_batch_item* items, int nitems, const grf_params* p
         const grf_params* p = &params[pi];
         if (p->beta_kind != GRF_BETA_LINEAR && p->beta_kind != GRF_BETA_QUADRATIC) return GRF_EINVAL;
         if (!(1.0 + p->a0 > 0.0) || !(1.0 + p->b0 > 0.0)) return GRF_EINVAL;
-        if (p->advection != 0) return GRF_EINVAL;  // centred advection only
+        if (p->advection != 0 && p->advection != 1) return GRF_EINVAL;
     }
     const Layout L = layout(items, nitems, cfg);
     DBG("entry: %d boxes, %lld tiles, ws %zu of %zu bytes, variant %d, tile %dx%dx%d", nitems, L.ntiles, ws_bytes,
@@ -380,6 +259,7 @@ int grf_batched_rk4(const grf_batch_item* items, int nitems, const grf_params* p
         d.c.bK = 3.0 * p->b0 / (4.0 * (1.0 + p->b0)); d.c.bTh = 1.0 / (2.0 * (1.0 + p->b0));
         d.c.beta_kind = p->beta_kind;
         d.c.decoupled = p->decoupled;
+        d.c.advection = p->advection;
         const size_t sb = align_up(state_bytes_of(d.g));
         d.un = it.state;
         d.A = (double*)(base + off);
@@ -420,12 +300,13 @@ int grf_batched_rk4(const grf_batch_item* items, int nitems, const grf_params* p
     if (e != cudaSuccess) return cuda_err(e);
     // load the stage kernels before any graph work
     for (const void* f : {(const void*)batch_stage_kernel<0>, (const void*)batch_stage_kernel<1>,
-                          (const void*)batch_stage_kernel<2>, (const void*)batch_stage_kernel<3>,
-                          (const void*)batch_persistent_kernel}) {
+                          (const void*)batch_stage_kernel<2>, (const void*)batch_stage_kernel<3>}) {
         cudaFuncAttributes fa;
         e = cudaFuncGetAttributes(&fa, f);
         if (e != cudaSuccess) return cuda_err(e);
     }
+    e = batch_persistent_attributes();
+    if (e != cudaSuccess) return cuda_err(e);
     DBG("kernels loaded");
 
     const dim3 block(cfg->tile_x, cfg->tile_y, cfg->tile_z);
@@ -461,20 +342,16 @@ int grf_batched_rk4(const grf_batch_item* items, int nitems, const grf_params* p
         e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         const int nthreads = cfg->tile_x * cfg->tile_y * cfg->tile_z;
-        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_persistent_kernel, nthreads, 0);
+        if (e == cudaSuccess) e = batch_persistent_occupancy(nthreads, &per_sm);
         if (e != cudaSuccess) return cuda_err(e);
         if (per_sm < 1) return GRF_EINVAL;
         if (cfg->blocks_per_sm > 0 && cfg->blocks_per_sm < per_sm) per_sm = cfg->blocks_per_sm;
         long long nb = (long long)per_sm * nsm;
         if (nb > L.ntiles) nb = L.ntiles;
         const long long timeout = cfg->barrier_timeout_cycles > 0 ? cfg->barrier_timeout_cycles : 20000000000LL;
-        int nt = (int)L.ntiles;
-        const BoxDesc* pb = dboxes;
-        const TileDesc* pt = dtiles;
-        void* args[] = {(void*)&pb, (void*)&pt, (void*)&nt, (void*)&nsteps, (void*)&bar, (void*)&status,
-                        (void*)&timeout};
         DBG("persistent: %lld blocks (%d per SM x %d SMs)", nb, per_sm, nsm);
-        e = cudaLaunchCooperativeKernel((const void*)batch_persistent_kernel, dim3((unsigned)nb), block, args, 0, st);
+        e = launch_batch_persistent(dim3((unsigned)nb), block, dboxes, dtiles, (int)L.ntiles, nsteps, bar, status,
+                                    timeout, st);
         DBG("persistent: launched (%s)", cudaGetErrorName(e));
     }
     if (e != cudaSuccess) return cuda_err(e);

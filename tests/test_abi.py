@@ -85,7 +85,7 @@ def test_host_step_validation_without_gpu(grf):
 
 def test_scheme_validation_without_gpu(grf):
     """4-ghost boxes (6th-order scheme) are sized with their ghosts; lopsided advection is rejected
-    by the batched and tangent calls and any other advection value everywhere, all before a CUDA
+    by the tangent call and any advection value other than 0 or 1 everywhere, all before a CUDA
     call."""
     b6 = grf.make_box(20, 18, 16, 0.25, ng=4)
     assert b6.pitch >= 28 and b6.pitch % 4 == 0
@@ -99,10 +99,10 @@ def test_scheme_validation_without_gpu(grf):
     b3 = grf.make_box(16, 16, 16, 0.25)
     p.advection = 2
     assert L.grf_rhs(C.byref(b3), C.byref(p), fake, fake, None, 0, None) == grf.GRF_EINVAL
-    p.advection = 1
     item = grf.grf_batch_item(b3, fake, 0, 0.1)
     cfg = grf.grf_batch_config(grf.GRF_BATCH_STREAM, 32, 4, 1, 0, 0)
     assert L.grf_batched_rk4(C.byref(item), 1, C.byref(p), 1, 1, C.byref(cfg), fake, 1 << 40, None, None) == grf.GRF_EINVAL
+    p.advection = 1
     sphere = grf.grf_sphere()
     sphere.radius = 1.0
     dpar = (C.c_double * 6)()

@@ -65,6 +65,32 @@ def test_batched_equals_single_box_path(g, variant, tile):
         assert np.array_equal(got, r)
 
 
+@pytest.mark.parametrize("variant,tile", [(1, (32, 4, 1)), (2, (32, 4, 1)), (3, (16, 4, 2))])
+def test_batched_lopsided_advection_equals_single_box_path(g, variant, tile):
+    """Boxes with lopsided advection (and one without backreaction) mixed with centred ones: each
+    box's bits equal its single-box evolution, in every launch variant and gather mode."""
+    import torch
+    boxes, params, pidx, states, dts = small_batch()
+    params = [gi.Params(lam=0.05, g2=0.02, advection=1), gi.Params(lam=0.3, g2=0.1, beta_kind=1),
+              gi.Params(lam=0.2, g2=0.1, advection=1, decoupled=1)]
+    gb = [g.box_like(b) for b in boxes]
+    gp = g.params_array([g.params_like(p) for p in params])
+    nsteps = 2
+    ref = []
+    for b, s, pi, dt in zip(gb, states, pidx, dts):
+        t = g.to_device(s, b)
+        g.grf_rk4_step(b, gp[pi], t, dt, nsteps)
+        ref.append(g.to_host(t, b))
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        dev = [g.to_device(s, b) for s, b in zip(states, gb)]
+        items = g.batch_items(gb, dev, pidx, dts)
+        g.grf_batched_rk4(items, gp, nsteps, g.batch_config(variant, tile), stream=stream)
+    stream.synchronize()
+    for b, d, r in zip(gb, dev, ref):
+        assert np.array_equal(g.to_host(d, b), r)
+
+
 def test_batched_graph_replay_and_oracle(g, orc):
     """Stepping the same batch twice replays the cached CUDA graph; the result after 2 x 1 steps
     equals 2 steps of the oracle for one of the boxes (within the parity tolerance)."""
