@@ -11,8 +11,10 @@ namespace grf {
 // three scalar terms) are each written when non-null.
 // ORD = 4: block gather mode (as rhs_kernel); ORD = 6: the 6th-order per-thread gather.
 // psi4 (2 fields, re and im) receives the Weyl scalar with the triad about the origin; o = the
-// coordinates of interior point (0, 0, 0).
-template <int ORD>
+// coordinates of interior point (0, 0, 0). PSI4 = 1 compiles that output in (it needs the solved
+// d_t K_ij); with PSI4 = 0 the compiler drops the coupled solve, which H, M_i and the densities do
+// not use.
+template <int ORD, int PSI4>
 __global__ void __launch_bounds__(128) constraints_kernel(Geom g, Coeffs c, const double* __restrict__ s,
                                                           double* __restrict__ out4, double* __restrict__ part,
                                                           double* __restrict__ dens, double* __restrict__ psi4,
@@ -44,7 +46,7 @@ __global__ void __launch_bounds__(128) constraints_kernel(Geom g, Coeffs c, cons
     if (live) {
         double r[NFIELDS];
         PointExtra ex;
-        if (psi4) {
+        if (PSI4 && psi4) {
             ex.want_psi4 = 1;
             ex.xyz[0] = o.x + i * g.dx;
             ex.xyz[1] = o.y + j * g.dx;
@@ -60,7 +62,7 @@ __global__ void __launch_bounds__(128) constraints_kernel(Geom g, Coeffs c, cons
             for (int m = 0; m < 4; ++m) out4[m * g.fstride + p] = vals[m];
         if (dens)
             for (int m = 0; m < 3; ++m) dens[m * g.fstride + p] = ex.rho8[m];
-        if (psi4) {
+        if (PSI4 && psi4) {
             psi4[p] = ex.psi4[0];
             psi4[g.fstride + p] = ex.psi4[1];
         }

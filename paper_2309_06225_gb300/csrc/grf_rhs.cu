@@ -42,6 +42,7 @@ void launch_rhs(dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coe
 void launch_constraints(dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c, const double* s,
                         double* out4, double* part, double* dens, double* psi4, double3 origin) {
     if (g.ng == NG6) launch_constraints6(grid, block, st, g, c, s, out4, part, dens, psi4, origin);
-    else constraints_kernel<4><<<grid, block, 0, st>>>(g, c, s, out4, part, dens, psi4, origin);
+    else if (psi4) constraints_kernel<4, 1><<<grid, block, 0, st>>>(g, c, s, out4, part, dens, psi4, origin);
+    else constraints_kernel<4, 0><<<grid, block, 0, st>>>(g, c, s, out4, part, dens, psi4, origin);
 }
 }  // namespace grf
