@@ -37,6 +37,8 @@ BYTES_PER_POINT_UPDATE = 216 * (3 + 5 + 5 + 4)
 # dram__bytes_read.sum + dram__bytes_write.sum of one stage launch per interior point, from the
 # ncu capture of the current stage kernel (profiles/); None when the kernel changed since.
 TRAFFIC_BYTES_PER_POINT_STAGE = 12619  # mean of stage 0 and 1, 96^3 capture (profiles/rk4_stage_kernel_bl_pair_96.md)
+# the tangent-linear (dual-number) stage kernel (profiles/tlm_stage_kernel_sphere_signal_96.md)
+TLM_FP64_INSTR_PER_POINT_STAGE = 28537
 # the 6th-order stage kernel with centred advection (profiles/rk4_stage6_kernel_bl_pair_96.md, mean of stages 0, 1)
 FP64_INSTR_PER_POINT_STAGE_6 = 4835
 TRAFFIC_BYTES_PER_POINT_STAGE_6 = 11033
@@ -279,7 +281,16 @@ def run_tangent(args, rank, world, local_rank):
            "gpu_launches": 5 * args.steps,
            "differentiated_vs_plain": {"tangent_ms_per_step": ms_t / args.steps, "plain_ms_per_step": ms_f / args.steps,
                                        "ratio": ms_t / ms_f},
-           "signal": loss.cpu().numpy().tolist(), "roofline": None, "e2e": None, "cpu_baseline": None}
+           "signal": loss.cpu().numpy().tolist(), "e2e": None, "cpu_baseline": None}
+    # FP64-bound like the plain stage: the dual-number stage's FP64 instruction count (ncu, 96^3,
+    # profiles/tlm_stage_kernel_sphere_signal_96.md) against the pipe's issue rate
+    stage_ms = ms_t / (4 * args.steps)
+    issue = TLM_FP64_INSTR_PER_POINT_STAGE * npts / (stage_ms * 1e-3) / (FP64_PEAK_TFLOPS * 1e12 / 2)
+    out["roofline"] = {"bound": "alu", "unit": "FP64 instructions/s", "kernel": "tlm_stage_kernel",
+                       "achieved": TLM_FP64_INSTR_PER_POINT_STAGE * npts / (stage_ms * 1e-3),
+                       "peak": FP64_PEAK_TFLOPS * 1e12 / 2, "frac": issue,
+                       "peak_source": "GB300 FP64 pipe: 152 SMs x 2 instructions/clk x 2.06 GHz (nominal)",
+                       "fp64_instr_per_point_stage": TLM_FP64_INSTR_PER_POINT_STAGE, "traffic": None}
     print(json.dumps(out), flush=True)
 
 
