@@ -36,6 +36,7 @@ BC_SOMMERFELD = 4    # ghosts evolved by the radiative (Sommerfeld) condition
 BC_REFLECT_LOW_SOMMERFELD = 5  # mirror planes at the low faces, Sommerfeld at the high faces
 BETA_LINEAR = 0      # beta(phi) = lambda * phi
 BETA_QUADRATIC = 1   # beta(phi) = lambda * phi^2 / 2
+BETA_EXPONENTIAL = 2  # beta(phi) = lambda / (2 kappa) * (1 - exp(-kappa phi^2))
 
 
 @dataclass
@@ -97,6 +98,7 @@ class Params:
     enforce_algebraic: int = 1
     decoupled: int = 0          # 1: 4dST without backreaction (metric evolves by vacuum CCZ4)
     advection: int = 0          # 0: centred advection derivatives, 1: lopsided (upwind-biased)
+    beta_kappa: float = 1.0     # kappa of the exponential coupling (beta_kind = BETA_EXPONENTIAL)
 
     def to_dict(self):
         return asdict(self)

@@ -58,10 +58,12 @@ typedef struct {
     double a0, b0;
     double lam, g2;
     double sigma_ko, min_chi, min_lapse;
-    int beta_kind;          // 0: beta = lam*phi ; 1: beta = lam*phi^2/2
+    int beta_kind;          // 0: beta = lam*phi ; 1: beta = lam*phi^2/2 ;
+                            // 2: beta = lam/(2 kappa) (1 - exp(-kappa phi^2))
     int enforce_algebraic;  // 1: trace-free A, chi/lapse floors after every RK stage
     int decoupled;          // 1: no backreaction: the metric evolves by vacuum CCZ4, the scalar on it
     int advection;          // 0: centred advection derivatives; 1: lopsided (upwind-biased)
+    double beta_kappa;      // kappa of the exponential coupling (beta_kind 2)
 } orc_params;
 
 typedef struct {
@@ -274,9 +276,18 @@ struct Src {
     double Ric4[4][4], R4s;  // its Ricci tensor and scalar
 };
 
+// beta'(phi), beta''(phi) of the Gauss-Bonnet coupling. The exponential kind ("Statement of
+// Need": spin-induced scalarisation with an exponential coupling) is
+//   beta = lam/(2 kappa) (1 - e^{-kappa phi^2}):  beta' = lam phi e^{-kappa phi^2},
+//   beta'' = lam e^{-kappa phi^2} (1 - 2 kappa phi^2),
+// which tends to the quadratic kind as kappa -> 0.
 void beta_derivs(const orc_params& P, double phi, double& b1, double& b2) {
     if (P.beta_kind == 1) { b1 = P.lam * phi; b2 = P.lam; }
-    else { b1 = P.lam; b2 = 0.0; }
+    else if (P.beta_kind == 2) {
+        const double e = std::exp(-P.beta_kappa * phi * phi);
+        b1 = P.lam * phi * e;
+        b2 = P.lam * e * (1.0 - 2.0 * P.beta_kappa * phi * phi);
+    } else { b1 = P.lam; b2 = 0.0; }
 }
 
 void sources(const orc_params& P, const Phys& p, const Geo& G, const double u[3][3], double w, Src& s) {

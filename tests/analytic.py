@@ -212,13 +212,20 @@ def geometry4(g, dg, ddg):
     return gi, Gam, Rdn, Ric, Rs
 
 
-def stress_and_scalar(g, gi, Gam, Rdn, Ric, Rs, dphi, ddphi, phi, lam, g2, beta_kind):
+def beta_derivatives(phi, lam, beta_kind, kappa=1.0):
+    """beta'(phi), beta''(phi) by symbolic differentiation of the coupling function."""
+    f = sp.Symbol("f", real=True)
+    beta = {0: lam * f, 1: lam * f ** 2 / 2,
+            2: lam / (2 * kappa) * (1 - sp.exp(-kappa * f ** 2))}[beta_kind]
+    b1 = sp.diff(beta, f)
+    b2 = sp.diff(b1, f)
+    return float(b1.subs(f, phi)), float(b2.subs(f, phi))
+
+
+def stress_and_scalar(g, gi, Gam, Rdn, Ric, Rs, dphi, ddphi, phi, lam, g2, beta_kind, kappa=1.0):
     """8 pi T_mn and the scalar-equation residual E for the 4dST action
     (1/16 pi) int [R + X + g2 X^2 + beta(phi) L_GB]."""
-    if beta_kind == 1:
-        b1, b2 = lam * phi, lam
-    else:
-        b1, b2 = lam, 0.0
+    b1, b2 = beta_derivatives(phi, lam, beta_kind, kappa)
     Hphi = ddphi - np.einsum("lmn,l->mn", Gam, dphi)
     Phi = b1 * Hphi + b2 * np.outer(dphi, dphi)
     Phiu = gi @ Phi @ gi

@@ -696,14 +696,18 @@ def spacetime():
     return T, alpha, beta_u, g, phi, at, phifn
 
 
+KAPPA = 0.8  # exponential coupling scale used by the brute-force pins
+
+
 def _stress_at(at, phifn, pt, lam, g2, kind):
     g, dg, ddg, dphi, ddphi = at(pt)
     gi4, Gam, Rdn, Ric, Rs = an.geometry4(g, dg, ddg)
-    T8, E, LGB, T8gb = an.stress_and_scalar(g, gi4, Gam, Rdn, Ric, Rs, dphi, ddphi, phifn(*pt), lam, g2, kind)
+    T8, E, LGB, T8gb = an.stress_and_scalar(g, gi4, Gam, Rdn, Ric, Rs, dphi, ddphi, phifn(*pt), lam, g2, kind,
+                                            KAPPA)
     return g, gi4, Gam, T8, E, LGB, dphi, T8gb
 
 
-@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("kind", [0, 1, 2])
 def test_3p1_assembly_matches_4d_brute_force(orc, spacetime, kind):
     """The oracle's 3+1 assembly (Gauss/Codazzi/Ricci-equation blocks in the (n, d_i) basis,
     nabla nabla phi projections, T and the scalar equation) reproduces rho, S_i, S_ij, L_GB and
@@ -720,7 +724,7 @@ def test_3p1_assembly_matches_4d_brute_force(orc, spacetime, kind):
     S8 = -(T8 @ n_up)[1:]
     Sij8 = T8[1:, 1:]
     phys, u6, w = an.phys_pack_generic(alpha, beta_u, g, phi, T, pt)
-    p = P(lam=lam, g2=g2, beta_kind=kind)
+    p = P(lam=lam, g2=g2, beta_kind=kind, beta_kappa=KAPPA)
     out = orc.phys_sources(p, phys, u6, w)
     scale = max(1.0, abs(rho8), np.max(np.abs(Sij8)))
     assert abs(out[0] - rho8) < 1e-10 * scale
@@ -779,7 +783,7 @@ def test_psi4_vanishes_for_schwarzschild_with_the_radial_tetrad(orc, ks_data):
         assert abs(orc.point_psi4(p, v, d1, d2, off)) > 1e-4
 
 
-@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("kind", [0, 1, 2])
 def test_effective_stress_tensor_obeys_bianchi(spacetime, kind):
     """Contracted Bianchi identity, off shell: nabla^m (8 pi T_mn) = (1/2) E d_n phi for the
     4dST effective stress tensor, on a generic spacetime. This fixes the Gauss-Bonnet
@@ -1052,6 +1056,19 @@ def test_energy_densities_of_the_three_scalar_terms(orc, conformal_generic, coup
     else:
         assert abs(parts[2]) > 1e-6
     assert abs(parts.sum() - diag[0]) < 1e-13
+
+
+def test_exponential_coupling_tends_to_the_quadratic_one(orc, conformal_generic):
+    """beta = lam/(2 kappa) (1 - e^{-kappa phi^2}) -> lam phi^2 / 2 as kappa -> 0: the right-hand side
+    with kappa = 1e-7 equals the quadratic coupling's to O(kappa phi^2), while kappa = 0.8 differs;
+    the brute-force pins above check the exponential kind's beta', beta'' at finite kappa."""
+    v, d1, d2, ph = conformal_generic
+    quad, _, _ = orc.point_rhs(P(lam=0.4, g2=0.2, beta_kind=1), v, d1, d2)
+    small, _, _ = orc.point_rhs(P(lam=0.4, g2=0.2, beta_kind=2, beta_kappa=1e-7), v, d1, d2)
+    big, _, _ = orc.point_rhs(P(lam=0.4, g2=0.2, beta_kind=2, beta_kappa=0.8), v, d1, d2)
+    scale = np.maximum(np.abs(quad), 1e-6)
+    assert np.max(np.abs(small - quad) / scale) < 1e-6
+    assert np.max(np.abs(big - quad) / scale) > 1e-5
 
 
 # ----------------------------------------------------------------------------- constraints
