@@ -58,7 +58,7 @@ enum {
     GRF_BC_SOMMERFELD = 4,
     GRF_BC_REFLECT_LOW_SOMMERFELD = 5
 };
-enum { GRF_BETA_LINEAR = 0, GRF_BETA_QUADRATIC = 1 };
+enum { GRF_BETA_LINEAR = 0, GRF_BETA_QUADRATIC = 1, GRF_BETA_EXPONENTIAL = 2 };
 enum { GRF_OP_RHS = 0, GRF_OP_RK4 = 1, GRF_OP_CONSTRAINTS = 2 };
 
 /* Grid box. Points sit at x = x0 + (i - ng) dx (ghosted index i). The ghost width chooses the
@@ -108,7 +108,9 @@ typedef struct {
 } grf_box;
 
 /* Theory, gauge and numerical parameters (modified puncture gauge with constant a, b;
- * beta(phi) = lambda phi or lambda phi^2 / 2; the X^2 coupling is the constant g2). */
+ * beta(phi) = lambda phi, lambda phi^2 / 2, or lambda / (2 kappa) (1 - exp(-kappa phi^2)), the
+ * exponential coupling of spin-induced scalarisation ("Statement of Need"); the X^2 coupling is
+ * the constant g2). */
 typedef struct {
     double kappa1, kappa2, kappa3;   /* CCZ4 constraint damping */
     double shift_F, eta;             /* Gamma-driver: d_t shift = F B / (1 + a) - ..., d_t B = d_t Gamma - eta B */
@@ -116,7 +118,8 @@ typedef struct {
     double lambda, g2;               /* Gauss-Bonnet coupling constant, X^2 coupling */
     double sigma_ko;                 /* Kreiss-Oliger strength sigma */
     double min_chi, min_lapse;       /* floors applied after every RK stage */
-    int beta_kind;                   /* GRF_BETA_LINEAR or GRF_BETA_QUADRATIC */
+    int beta_kind;                   /* GRF_BETA_LINEAR, GRF_BETA_QUADRATIC or GRF_BETA_EXPONENTIAL
+                                        (the last not accepted by grf_tlm_rk4) */
     int enforce_algebraic;           /* 1: trace-free A_ij and the floors after every stage */
     int decoupled;                   /* 0: full 4dST; 1: without backreaction onto the metric
                                         ("Key features"): the metric evolves by vacuum CCZ4 in the
@@ -126,6 +129,7 @@ typedef struct {
                                         beta^k points to (every beta^k d_k of an evolved field, those
                                         inside the coupled 4dST system included). 1 is not accepted by
                                         grf_tlm_rk4 */
+    double beta_kappa;               /* kappa >= 0 of GRF_BETA_EXPONENTIAL (ignored by the other kinds) */
 } grf_params;
 
 /* d_t of all 27 fields at the interior points of `state` (modified CCZ4 + 4dST, section

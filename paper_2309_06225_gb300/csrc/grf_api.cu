@@ -216,7 +216,9 @@ Geom make_geom(const grf_box* b) {
 
 bool params_ok(const grf_params* p) {
     if (!p) return false;
-    if (p->beta_kind != GRF_BETA_LINEAR && p->beta_kind != GRF_BETA_QUADRATIC) return false;
+    if (p->beta_kind != GRF_BETA_LINEAR && p->beta_kind != GRF_BETA_QUADRATIC && p->beta_kind != GRF_BETA_EXPONENTIAL)
+        return false;
+    if (p->beta_kind == GRF_BETA_EXPONENTIAL && !(p->beta_kappa >= 0.0 && p->beta_kappa < 1e300)) return false;
     if (!(1.0 + p->a0 > 0.0) || !(1.0 + p->b0 > 0.0)) return false;
     if (p->advection != 0 && p->advection != 1) return false;
     return true;
@@ -238,6 +240,7 @@ Coeffs make_coeffs(const grf_params* p) {
     c.bK = 3.0 * p->b0 / (4.0 * (1.0 + p->b0));
     c.bTh = 1.0 / (2.0 * (1.0 + p->b0));
     c.beta_kind = p->beta_kind;
+    c.beta_kappa = p->beta_kappa;
     c.decoupled = p->decoupled;
     c.advection = p->advection;
     return c;

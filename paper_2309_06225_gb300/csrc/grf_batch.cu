@@ -225,7 +225,10 @@ int grf_batched_rk4(const grf_batch_item* items, int nitems, const grf_params* p
         const int pi = items[i].params_index;
         if (pi < 0 || pi >= nparams) return GRF_EINVAL;
         const grf_params* p = &params[pi];
-        if (p->beta_kind != GRF_BETA_LINEAR && p->beta_kind != GRF_BETA_QUADRATIC) return GRF_EINVAL;
+        if (p->beta_kind != GRF_BETA_LINEAR && p->beta_kind != GRF_BETA_QUADRATIC &&
+            p->beta_kind != GRF_BETA_EXPONENTIAL)
+            return GRF_EINVAL;
+        if (p->beta_kind == GRF_BETA_EXPONENTIAL && !(p->beta_kappa >= 0.0 && p->beta_kappa < 1e300)) return GRF_EINVAL;
         if (!(1.0 + p->a0 > 0.0) || !(1.0 + p->b0 > 0.0)) return GRF_EINVAL;
         if (p->advection != 0 && p->advection != 1) return GRF_EINVAL;
     }
@@ -258,6 +261,7 @@ int grf_batched_rk4(const grf_batch_item* items, int nitems, const grf_params* p
         d.c.inv_1pa = 1.0 / (1.0 + p->a0); d.c.a_1pa = p->a0 / (1.0 + p->a0);
         d.c.bK = 3.0 * p->b0 / (4.0 * (1.0 + p->b0)); d.c.bTh = 1.0 / (2.0 * (1.0 + p->b0));
         d.c.beta_kind = p->beta_kind;
+        d.c.beta_kappa = p->beta_kappa;
         d.c.decoupled = p->decoupled;
         d.c.advection = p->advection;
         const size_t sb = align_up(state_bytes_of(d.g));

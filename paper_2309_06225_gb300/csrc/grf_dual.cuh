@@ -37,6 +37,10 @@ GRF_DHD D3 operator/(const D3& a, const D3& b) {
     return D3(q, (a.d0 - q * b.d0) * ib, (a.d1 - q * b.d1) * ib, (a.d2 - q * b.d2) * ib);
 }
 GRF_DHD D3 operator/(const D3& a, double b) { return a * (1.0 / b); }
+GRF_DHD D3 exp(const D3& a) {
+    const double e = ::exp(a.v);
+    return D3(e, e * a.d0, e * a.d1, e * a.d2);
+}
 GRF_DHD D3 operator/(double a, const D3& b) {
     const double q = a / b.v;
     const double r = -q / b.v;

@@ -65,6 +65,10 @@ inline CD fma(const CD& a, const CD& b, const CD& c) {
     return mk(std::fma(a.v, b.v, c.v), false);
 }
 inline CD fabs(const CD& a) { return mk(std::fabs(a.v), a.k); }
+inline CD exp(const CD& a) {  // counted as one division-class operation
+    if (!a.k) C().div++;
+    return mk(std::exp(a.v), a.k);
+}
 inline CD fmax(const CD& a, const CD& b) {
     if (a.k && b.k) return CD(std::fmax(a.v, b.v));
     C().cmp++;
@@ -98,6 +102,7 @@ int grf_count_point_ops(const grf_params* p, const double* v, const double* d1, 
     c.kappa1 = p->kappa1; c.kappa2 = p->kappa2; c.kappa3 = p->kappa3; c.shift_F = p->shift_F; c.eta = p->eta;
     c.lam = p->lambda; c.g2 = p->g2; c.inv_1pa = 1.0 / (1.0 + p->a0); c.a_1pa = p->a0 / (1.0 + p->a0);
     c.bK = 3.0 * p->b0 / (4.0 * (1.0 + p->b0)); c.bTh = 1.0 / (2.0 * (1.0 + p->b0)); c.beta_kind = p->beta_kind; c.decoupled = p->decoupled;
+    c.beta_kappa = p->beta_kappa;
     c.advection = 0;  // operation counts of the centred-advection instance
     CD rhs[grf::NFIELDS];
     grf::PointExtraT<CD> ex;
@@ -125,6 +130,7 @@ int grf_host_point_rhs(const grf_params* p, const double* v, const double* d1, c
     c.kappa1 = p->kappa1; c.kappa2 = p->kappa2; c.kappa3 = p->kappa3; c.shift_F = p->shift_F; c.eta = p->eta;
     c.lam = p->lambda; c.g2 = p->g2; c.inv_1pa = 1.0 / (1.0 + p->a0); c.a_1pa = p->a0 / (1.0 + p->a0);
     c.bK = 3.0 * p->b0 / (4.0 * (1.0 + p->b0)); c.bTh = 1.0 / (2.0 * (1.0 + p->b0)); c.beta_kind = p->beta_kind; c.decoupled = p->decoupled;
+    c.beta_kappa = p->beta_kappa;
     c.advection = 0;  // operation counts of the centred-advection instance
     grf::PointExtraT<double> ex;
     bool ok = true;
@@ -151,6 +157,7 @@ int grf_host_point_psi4(const grf_params* p, const double* v, const double* d1, 
     c.lam = p->lambda; c.g2 = p->g2; c.inv_1pa = 1.0 / (1.0 + p->a0); c.a_1pa = p->a0 / (1.0 + p->a0);
     c.bK = 3.0 * p->b0 / (4.0 * (1.0 + p->b0)); c.bTh = 1.0 / (2.0 * (1.0 + p->b0)); c.beta_kind = p->beta_kind;
     c.decoupled = p->decoupled;
+    c.beta_kappa = p->beta_kappa;
     c.advection = 0;
     grf::PointExtraT<double> ex;
     ex.want_psi4 = 1;

@@ -66,6 +66,7 @@ struct CoeffsT {
     double inv_1pa, a_1pa;        // 1/(1+a), a/(1+a)
     double bK, bTh;               // 3b/(4(1+b)), 1/(2(1+b))
     int beta_kind;
+    double beta_kappa;  // kappa of the exponential coupling (beta_kind 2)
     int decoupled;  // 1: the scalar's stress-energy is left out of the metric equations
     int advection;  // 1: lopsided advection derivatives (kernels instantiated with LOP = 1)
 };
@@ -561,7 +562,18 @@ GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS]
     // ---- scalar: nabla nabla phi blocks, Phi = nabla nabla beta(phi)
     GRF_SECTION(10);
     T b1, b2;
-    if (c.beta_kind == 1) { b1 = c.lam * phi; b2 = c.lam; } else { b1 = c.lam; b2 = 0.0; }
+    // beta' and beta'' of the coupling: lam phi, lam phi^2 / 2, or lam / (2 kappa) (1 - e^{-kappa phi^2})
+    // (beta' = lam phi e^{-kappa phi^2}, beta'' = lam e^{-kappa phi^2} (1 - 2 kappa phi^2))
+    if (c.beta_kind == 1) {
+        b1 = c.lam * phi; b2 = c.lam;
+    } else if (c.beta_kind == 2) {
+        const T kp2 = c.beta_kappa * (phi * phi);
+        const T e = exp(-kp2);
+        b1 = c.lam * (phi * e);
+        b2 = c.lam * (e * fma(-2.0, kp2, 1.0));
+    } else {
+        b1 = c.lam; b2 = 0.0;
+    }
     T dphiu[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) dphiu[i] = gu[sidx(i, 0)] * dphi[0] + gu[sidx(i, 1)] * dphi[1] + gu[sidx(i, 2)] * dphi[2];

@@ -289,6 +289,7 @@ int grf_tlm_rk4(const grf_box* box, const grf_params* params, const double* dpar
     c.bK = 3.0 * params->b0 / (4.0 * (1.0 + params->b0));
     c.bTh = 1.0 / (2.0 * (1.0 + params->b0));
     c.beta_kind = params->beta_kind;
+    c.beta_kappa = params->beta_kappa;
     c.decoupled = params->decoupled;
     TlmArgs a;
     a.dt = dt;

@@ -67,11 +67,12 @@ def test_batched_equals_single_box_path(g, variant, tile):
 
 @pytest.mark.parametrize("variant,tile", [(1, (32, 4, 1)), (2, (32, 4, 1)), (3, (16, 4, 2))])
 def test_batched_lopsided_advection_equals_single_box_path(g, variant, tile):
-    """Boxes with lopsided advection (and one without backreaction) mixed with centred ones: each
-    box's bits equal its single-box evolution, in every launch variant and gather mode."""
+    """Boxes with lopsided advection (and one without backreaction) mixed with centred ones with the
+    exponential coupling: each box's bits equal its single-box evolution, in every launch variant
+    and gather mode."""
     import torch
     boxes, params, pidx, states, dts = small_batch()
-    params = [gi.Params(lam=0.05, g2=0.02, advection=1), gi.Params(lam=0.3, g2=0.1, beta_kind=1),
+    params = [gi.Params(lam=0.05, g2=0.02, advection=1), gi.Params(lam=0.3, g2=0.1, beta_kind=2, beta_kappa=1.5),
               gi.Params(lam=0.2, g2=0.1, advection=1, decoupled=1)]
     gb = [g.box_like(b) for b in boxes]
     gp = g.params_array([g.params_like(p) for p in params])

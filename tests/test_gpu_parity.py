@@ -318,3 +318,25 @@ def test_error_codes(g):
     t[5, 5, 5, 5] = float("nan")
     assert g.grf_check_finite(b, t) == g.GRF_ENONFINITE
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("bc", [gi.BC_PERIODIC, gi.BC_FROZEN])
+def test_exponential_coupling_parity(g, orc, bc):
+    """The exponential Gauss-Bonnet coupling (GRF_BETA_EXPONENTIAL): RHS and 3 RK4 steps against the
+    oracle on a state whose scalar is large enough for e^{-kappa phi^2} to matter."""
+    box = gi.Box(13, 11, 10, 0.3, -1.95, -1.65, -1.5, bc=bc)
+    params = P(lam=0.3, g2=0.2, beta_kind=gi.BETA_EXPONENTIAL, beta_kappa=2.0)
+    s0 = make_state(box, "perturbed", 37)
+    s0[25] += 0.6 * np.exp(-sum(c ** 2 for c in box.coords()) / 4.0)
+    s = s0.copy()
+    if bc == gi.BC_PERIODIC:
+        orc.fill_ghosts(box, s)
+    ref = orc.rhs(box, params, s)
+    out = gpu_rhs(g, box, params, s)
+    errs = field_errors(out, ref, box, state=s, sigma=params.sigma_ko)
+    assert np.max(errs) < 1e-11, describe(errs)
+    cpu = s0.copy()
+    orc.rk4(box, params, cpu, 0.25 * box.dx, 3)
+    gpu = gpu_rk4(g, box, params, s0, 0.25 * box.dx, 3)
+    errs = field_errors(gpu, cpu, box)
+    assert np.max(errs) < 1e-10, describe(errs)

@@ -22,7 +22,7 @@ def flops():
 
 @pytest.mark.parametrize("decoupled", [0, 1])
 @pytest.mark.parametrize("seed", range(6))
-@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("kind", [0, 1, 2])
 def test_kernel_pointwise_rhs_matches_oracle(orc, flops, seed, kind, decoupled):
     import paper_2309_06225_gb300 as grf
     rng = np.random.default_rng(100 + seed)
@@ -34,7 +34,7 @@ def test_kernel_pointwise_rhs_matches_oracle(orc, flops, seed, kind, decoupled):
     d1 = rng.normal(size=(27, 3)) * 0.3
     d2 = rng.normal(size=(27, 6)) * 0.3
     p = gi.Params(lam=rng.uniform(0.0, 0.6), g2=rng.uniform(0.0, 0.4), beta_kind=kind, a0=0.3, b0=0.7,
-                  kappa2=0.2, kappa3=0.6, decoupled=decoupled)
+                  kappa2=0.2, kappa3=0.6, decoupled=decoupled, beta_kappa=rng.uniform(0.5, 3.0))
     ref, diag, st = orc.point_rhs(p, v, d1, d2)
     assert st == 0
     s1, s2 = slots(d1, d2)
