@@ -261,7 +261,8 @@ dim3 interior_grid(const Geom& g) {
 // at least one wave of resident blocks (3 per SM); a smaller box ran 10% slower folded (13^3).
 int fold_width(const Geom& g, const grf_params* p) {
     const int nx = g.nx;
-    if (nx % 32 == 0 || g.ng != NG || p->advection) return 32;  // the folded kernel: 4th order, centred
+    // the folded kernel: 4th order, centred advection, linear or quadratic coupling
+    if (nx % 32 == 0 || g.ng != NG || p->advection || p->beta_kind == GRF_BETA_EXPONENTIAL) return 32;
     int sms = 0, dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();

@@ -335,7 +335,7 @@ enum GatherMode {
 // threads past the interior (i >= nx, and j >= ny in block mode) take part in the gather, at the
 // last ghost column / row at most, and then write nothing. sh: the block's rows (block mode,
 // already filled and synchronised).
-template <int STAGE, int DEC = -1, int LOP = 0>
+template <int STAGE, int DEC = -1, int LOP = 0, int COUP = 1>
 __device__ __forceinline__ void stage_point(const Geom& g, const Coeffs& c, const StageArgs& a, int i, int j, int k,
                                             int mode, const YzRows* sh) {
     const bool live = i < g.nx && j < g.ny;
@@ -355,7 +355,7 @@ __device__ __forceinline__ void stage_point(const Geom& g, const Coeffs& c, cons
     if (!live) return;
     double r[NFIELDS];
     bool ok = true;
-    point_rhs<double, double, DEC, LOP>(c, in, r, nullptr, ok, adv);
+    point_rhs<double, double, DEC, LOP, COUP>(c, in, r, nullptr, ok, adv);
     if (!ok) atomicOr(a.status, 1);
     double out[NFIELDS];
 #pragma unroll 1
@@ -374,7 +374,8 @@ __device__ __forceinline__ void stage_point(const Geom& g, const Coeffs& c, cons
 // FP64 dependency latency than the added spills cost (measured 2% faster than 2 blocks).
 // DEC: 0 full theory, 1 without backreaction (a separate instantiation each, so the full
 // theory's kernel carries no test of the mode), -1 the mode read from c. LOP: lopsided advection.
-template <int STAGE, int DEC = 0, int LOP = 0>
+// COUP = 0: the linear and quadratic couplings only.
+template <int STAGE, int DEC = 0, int LOP = 0, int COUP = 1>
 __global__ void __launch_bounds__(128, 3) rk4_stage_kernel(Geom g, Coeffs c, StageArgs a) {
     __shared__ YzRows sh;
     const int i = blockIdx.x * 32 + threadIdx.x;
@@ -383,7 +384,7 @@ __global__ void __launch_bounds__(128, 3) rk4_stage_kernel(Geom g, Coeffs c, Sta
     if (k >= g.nz) return;  // whole block
     yz_rows_fill(g, a.src, i, blockIdx.y * 4, threadIdx.y, k, threadIdx.x, sh);
     __syncthreads();
-    stage_point<STAGE, DEC, LOP>(g, c, a, i, j, k, GATHER_BLOCK, &sh);
+    stage_point<STAGE, DEC, LOP, COUP>(g, c, a, i, j, k, GATHER_BLOCK, &sh);
 }
 
 // Folded variant for boxes whose x-extent is not a multiple of 32, chosen by the host when it

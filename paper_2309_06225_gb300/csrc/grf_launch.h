@@ -18,6 +18,9 @@ void launch_stage_folded(int stage, dim3 grid, dim3 block, cudaStream_t st, cons
 // 4th-order scheme with lopsided advection; 6th-order scheme (centred / lopsided advection)
 void launch_stage_lopsided(int stage, dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c,
                            const StageArgs& a);
+// 4th-order scheme, centred advection, every coupling (both decoupled modes compiled in)
+void launch_stage_general(int stage, dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c,
+                          const StageArgs& a);
 void launch_stage6(int stage, dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c,
                    const StageArgs& a);
 void launch_stage6_lopsided(int stage, dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c,

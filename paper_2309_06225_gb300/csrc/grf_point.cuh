@@ -226,8 +226,9 @@ GRF_HD void q_of(const T X[6], const T gd[6], const T gw[6], const T Phd[6], con
 // LOP = 1: every advection term beta^k d_k u of an evolved field (the CCZ4 advection terms and
 // the shift-contracted derivatives of K_ij and Pi inside the coupled system) is taken from
 // adv[27], the lopsided differences; all other derivatives stay centred. adv is not read when
-// LOP = 0.
-template <typename T, typename P = double, int DEC = -1, int LOP = 0>
+// LOP = 0. COUP = 0 compiles the linear and quadratic couplings only (the exponential one is then
+// routed to another instantiation by the host).
+template <typename T, typename P = double, int DEC = -1, int LOP = 0, int COUP = 1>
 GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS], PointExtraT<T>* extra, bool& ok,
                       const T* adv = nullptr) {
     GRF_SECTION(0);
@@ -566,7 +567,7 @@ GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS]
     // (beta' = lam phi e^{-kappa phi^2}, beta'' = lam e^{-kappa phi^2} (1 - 2 kappa phi^2))
     if (c.beta_kind == 1) {
         b1 = c.lam * phi; b2 = c.lam;
-    } else if (c.beta_kind == 2) {
+    } else if (COUP && c.beta_kind == 2) {
         const T kp2 = c.beta_kappa * (phi * phi);
         const T e = exp(-kp2);
         b1 = c.lam * (phi * e);

@@ -12,6 +12,10 @@ void launch_stage(int stage, dim3 grid, dim3 block, cudaStream_t st, const Geom&
         launch_stage_lopsided(stage, grid, block, st, g, c, a);
         return;
     }
+    if (c.beta_kind == 2) {  // the exponential coupling: the general instantiation
+        launch_stage_general(stage, grid, block, st, g, c, a);
+        return;
+    }
     if (a.fold != 32) {
         launch_stage_folded(stage, grid, block, st, g, c, a);
         return;
@@ -21,10 +25,10 @@ void launch_stage(int stage, dim3 grid, dim3 block, cudaStream_t st, const Geom&
         return;
     }
     switch (stage) {
-        case 0: rk4_stage_kernel<0><<<grid, block, 0, st>>>(g, c, a); break;
-        case 1: rk4_stage_kernel<1><<<grid, block, 0, st>>>(g, c, a); break;
-        case 2: rk4_stage_kernel<2><<<grid, block, 0, st>>>(g, c, a); break;
-        default: rk4_stage_kernel<3><<<grid, block, 0, st>>>(g, c, a); break;
+        case 0: rk4_stage_kernel<0, 0, 0, 0><<<grid, block, 0, st>>>(g, c, a); break;
+        case 1: rk4_stage_kernel<1, 0, 0, 0><<<grid, block, 0, st>>>(g, c, a); break;
+        case 2: rk4_stage_kernel<2, 0, 0, 0><<<grid, block, 0, st>>>(g, c, a); break;
+        default: rk4_stage_kernel<3, 0, 0, 0><<<grid, block, 0, st>>>(g, c, a); break;
     }
 }
 }  // namespace grf

@@ -7,10 +7,10 @@ namespace grf {
 void launch_stage_decoupled(int stage, dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c,
                             const StageArgs& a) {
     switch (stage) {
-        case 0: rk4_stage_kernel<0, 1><<<grid, block, 0, st>>>(g, c, a); break;
-        case 1: rk4_stage_kernel<1, 1><<<grid, block, 0, st>>>(g, c, a); break;
-        case 2: rk4_stage_kernel<2, 1><<<grid, block, 0, st>>>(g, c, a); break;
-        default: rk4_stage_kernel<3, 1><<<grid, block, 0, st>>>(g, c, a); break;
+        case 0: rk4_stage_kernel<0, 1, 0, 0><<<grid, block, 0, st>>>(g, c, a); break;
+        case 1: rk4_stage_kernel<1, 1, 0, 0><<<grid, block, 0, st>>>(g, c, a); break;
+        case 2: rk4_stage_kernel<2, 1, 0, 0><<<grid, block, 0, st>>>(g, c, a); break;
+        default: rk4_stage_kernel<3, 1, 0, 0><<<grid, block, 0, st>>>(g, c, a); break;
     }
 }
 }  // namespace grf
