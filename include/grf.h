@@ -118,8 +118,7 @@ typedef struct {
     double lambda, g2;               /* Gauss-Bonnet coupling constant, X^2 coupling */
     double sigma_ko;                 /* Kreiss-Oliger strength sigma */
     double min_chi, min_lapse;       /* floors applied after every RK stage */
-    int beta_kind;                   /* GRF_BETA_LINEAR, GRF_BETA_QUADRATIC or GRF_BETA_EXPONENTIAL
-                                        (the last not accepted by grf_tlm_rk4) */
+    int beta_kind;                   /* GRF_BETA_LINEAR, GRF_BETA_QUADRATIC or GRF_BETA_EXPONENTIAL */
     int enforce_algebraic;           /* 1: trace-free A_ij and the floors after every stage */
     int decoupled;                   /* 0: full 4dST; 1: without backreaction onto the metric
                                         ("Key features"): the metric evolves by vacuum CCZ4 in the

@@ -254,7 +254,11 @@ int grf_tlm_rk4(const grf_box* box, const grf_params* params, const double* dpar
                 grf_stream_t stream) {
     if (!box_valid(box) || !params || !dparams || !state || !tangents || !sphere || !loss || nsteps < 0)
         return GRF_EINVAL;
-    if (params->beta_kind != GRF_BETA_LINEAR && params->beta_kind != GRF_BETA_QUADRATIC) return GRF_EINVAL;
+    if (params->beta_kind != GRF_BETA_LINEAR && params->beta_kind != GRF_BETA_QUADRATIC &&
+        params->beta_kind != GRF_BETA_EXPONENTIAL)
+        return GRF_EINVAL;
+    if (params->beta_kind == GRF_BETA_EXPONENTIAL && !(params->beta_kappa >= 0.0 && params->beta_kappa < 1e300))
+        return GRF_EINVAL;
     if (params->advection != 0) return GRF_EINVAL;  // centred advection only
     if (!(1.0 + params->a0 > 0.0) || !(1.0 + params->b0 > 0.0) || !(sphere->radius > 0.0)) return GRF_EINVAL;
     const Geom g = geom_from(box);

@@ -181,3 +181,38 @@ def test_tlm_gradient_matches_richardson_differences(g, tlm, k):
     rich = (4.0 * central(h / 2) - central(h)) / 3.0
     floor = 20 * np.finfo(float).eps * abs(L) / (h * abs(grad[k]))
     assert abs(rich / grad[k] - 1.0) <= max(1e-10, floor), (k, grad[k], rich, floor)
+
+
+def test_tlm_exponential_coupling_gradients(g, orc):
+    """The tangent evolution with the exponential coupling (exp of the dual numbers): the
+    gradients in (lambda, g2, A) agree with central differences of the oracle's evolution."""
+    import torch
+    from paper_2309_06225_gb300 import diff
+    theta = (0.4, 0.2, 0.3)  # an amplitude large enough for e^{-kappa phi^2} to matter
+
+    def params(t):
+        return gi.Params(lam=t[0], g2=t[1], beta_kind=gi.BETA_EXPONENTIAL, beta_kappa=3.0)
+
+    b = g.box_like(BOX)
+    s0 = g.to_device(initial(theta[2]), b)
+    ds = g.to_device(dstate_dA(), b)
+    _, grad = diff.sphere_signal_and_grad(b, g.params_like(params(theta)), torch.tensor(theta, dtype=torch.float64),
+                                          s0, ds, 0.25 * BOX.dx, NSTEPS, diff.sphere(R))
+    grad = grad.numpy()
+
+    def signal(t):
+        s = initial(t[2])
+        dt = 0.25 * BOX.dx
+        L = 0.0
+        for _ in range(NSTEPS):
+            orc.rk4(BOX, params(t), s, dt, 1)
+            L += dt * host_signal(BOX, s, R)
+        return L
+
+    for k in range(3):
+        h = 1e-4 * max(abs(theta[k]), 1e-2)
+        tp = list(theta); tm = list(theta)
+        tp[k] += h
+        tm[k] -= h
+        fd = (signal(tp) - signal(tm)) / (2 * h)
+        assert abs(grad[k] - fd) <= 1e-5 * abs(fd), (k, grad[k], fd)
