@@ -80,7 +80,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="bl_pair_256", choices=["bl_pair_256", "bl_pair_128", "bl_pair_96", "bl_pair_64", "amr_boxes_96", "coupling_sweep_32", "sphere_signal_96", "calls_256", "calls_96", "bl_pair_octant_128"])
+    ap.add_argument("--workload", default="bl_pair_256", choices=["bl_pair_256", "bl_pair_128", "bl_pair_96", "bl_pair_64", "amr_boxes_96", "coupling_sweep_32", "sphere_signal_96", "calls_256", "calls_96", "bl_pair_octant_128", "patches_256"])
+    ap.add_argument("--patches", default="2,2,2", help="patches per axis of the patches_256 workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--decoupled", action="store_true",
@@ -388,6 +389,92 @@ def run_batched(args, rank, world, local_rank):
     print(json.dumps(out), flush=True)
 
 
+def run_patches(args, rank, world, local_rank):
+    """The 256^3 Brill-Lindquist workload held as px x py x pz patches (grf_patches_rk4): per
+    stage one batched stage launch over all patches and one halo exchange. Beside it, the same
+    steps of grf_rk4_step on the whole box, and the exchange timed alone."""
+    import torch
+    import paper_2309_06225_gb300 as grf
+    from paper_2309_06225_gb300 import flops as grf_flops
+
+    torch.cuda.set_device(local_rank)
+    cfg = workload("bl_pair_256")
+    box, params, dt = cfg["box"], cfg["params"], cfg["dt"]
+    pxyz = [int(v) for v in args.patches.split(",")]
+    b, p = grf.box_like(box), grf.params_like(params)
+    level = grf.patch_level(b, *pxyz)
+    whole = grf.to_device(cfg["make_state"](), b)
+    patches = grf.patch_states(level)
+    ws = grf.alloc_workspace(grf.grf_patches_workspace_bytes(level))
+    npts = box.nx * box.ny * box.nz
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    grf.grf_patch_copy(level, whole, patches, 0)
+    grf.grf_patches_rk4(level, p, patches, dt, args.warmup, ws=ws)
+    clocks = ClockSampler(gpu_selector(local_rank))
+    clocks.start()
+    time.sleep(0.3)
+    ms = timed(lambda: grf.grf_patches_rk4(level, p, patches, dt, args.steps, ws=ws, sync_status=False), 1)
+    clk = clocks.stop()
+    status = grf.grf_check_status()
+    ms_x = timed(lambda: grf.grf_halo_exchange(level, patches), 20) / 20
+    # the whole box, same steps
+    wws = grf.alloc_workspace(grf.grf_workspace_bytes(b, grf.GRF_OP_RK4))
+    grf.grf_rk4_step(b, p, whole, dt, 1, ws=wws)
+    ms_w = timed(lambda: grf.grf_rk4_step(b, p, whole, dt, args.steps, ws=wws), 1)
+    # e2e: the box state from pinned host memory, split, stepped, joined and read back every step
+    host_in = torch.empty(whole.shape, dtype=torch.float64, pin_memory=True)
+    host_in.copy_(whole)
+    host_out = torch.empty_like(host_in, pin_memory=True)
+    nbytes = whole.numel() * 8
+
+    def e2e_step():
+        whole.copy_(host_in, non_blocking=True)
+        grf.grf_patch_copy(level, whole, patches, 0)
+        grf.grf_patches_rk4(level, p, patches, dt, 1, ws=ws, sync_status=False)
+        grf.grf_patch_copy(level, whole, patches, 1)
+        host_out.copy_(whole, non_blocking=True)
+
+    ems = timed(e2e_step, args.steps)
+    value = npts * args.steps / (ms * 1e-3)
+    flop_ps = grf_flops.flops_per_point_stage(p)
+    achieved = flop_ps * npts * 4 * args.steps / (ms * 1e-3) / 1e12
+    # exchange bytes: every ghost point of every patch, 27 fields read and written
+    ghost_pts = 0
+    for q in range(len(patches)):
+        pb = grf.grf_patch_box(level, q)
+        ghost_pts += (pb.nx + 6) * (pb.ny + 6) * (pb.nz + 6) - pb.nx * pb.ny * pb.nz
+    x_bytes = ghost_pts * 27 * 16
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "patches_256", "grid": [box.nx, box.ny, box.nz], "patches": pxyz, "dx": box.dx,
+                      "dt": dt, "beta_kind": params.beta_kind, "lambda": params.lam, "g2": params.g2,
+                      "l2": "inputs larger than L2 (no flush needed)"},
+           "gpu_launches": 8 * args.steps + 1,
+           "roofline": {"bound": "alu", "unit": "TFLOP/s", "kernel": "batch_stage_kernel", "achieved": achieved,
+                        "peak": FP64_PEAK_TFLOPS, "frac": achieved / FP64_PEAK_TFLOPS, "flop_per_point_stage": flop_ps,
+                        "traffic": None},
+           "halo_exchange": {"ms": ms_x, "bytes": x_bytes, "gb_s": x_bytes / (ms_x * 1e-3) / 1e9,
+                             "share_of_step": 4 * ms_x / (ms / args.steps)},
+           "whole_box_path": {"value": npts * args.steps / (ms_w * 1e-3), "ms_per_step": ms_w / args.steps},
+           "clocks": clk, "status": {"solve": status},
+           "e2e": {"value": npts * args.steps / (ems * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                   "d2h_bytes_per_step": nbytes, "ms_per_step": ems / args.steps},
+           "cpu_baseline": None}
+    print(json.dumps(out), flush=True)
+
+
 # ------------------------------------------------------------------------------ clocks
 def gpu_selector(local_rank):
     """nvidia-smi -i argument for this process's GPU (PCI bus id when torch exposes it)."""
@@ -684,6 +771,9 @@ def main():
         return
     if args.workload in ("calls_256", "calls_96"):
         run_calls(args, rank, world, local_rank)
+        return
+    if args.workload == "patches_256":
+        run_patches(args, rank, world, local_rank)
         return
     if args.workload in ("amr_boxes_96", "coupling_sweep_32"):
         run_batched(args, rank, world, local_rank)

@@ -264,6 +264,72 @@ int grf_batched_rk4(const grf_batch_item* items, int nitems, const grf_params* p
                     const grf_batch_config* cfg, void* ws, size_t ws_bytes, int* status_host, grf_stream_t stream);
 
 /* ---------------------------------------------------------------------------------------
+ * One periodic box split into patches (domain decomposition). GRFolres distributes the boxes of
+ * a level over processes and fills each box's ghost cells from its neighbours before every
+ * right-hand side ("Key features": parallelism, AMR). Here the box's interior is
+ * cut into px x py x pz patches, each a state of its own (frozen-ghost layout, below); every RK4
+ * stage advances all patches' points in one launch, and a halo exchange then refills every
+ * patch's ghosts from the interiors of the patches that own those points. The exchange is a
+ * separate step behind a function pointer, so a caller can put its own in its place (one that
+ * moves halos between devices or processes, say); the built-in one is grf_halo_exchange.
+ * With the built-in exchange the patches' interiors after grf_patches_rk4 equal, bit for bit,
+ * those of grf_rk4_step on the whole box.
+ *
+ * Patch (a, b, c), index a + px (b + py c), covers the interior points
+ * [floor(a nx / px), floor((a + 1) nx / px)) along x, and likewise along y and z.
+ * ------------------------------------------------------------------------------------- */
+#define GRF_MAX_PATCHES_PER_AXIS 16
+#define GRF_MAX_PATCHES 256
+
+typedef struct {
+    grf_box box;          /* the whole box: GRF_BC_PERIODIC, ng = 3, each of nx, ny, nz >= 3 */
+    int px, py, pz;       /* patches per axis: 1 .. GRF_MAX_PATCHES_PER_AXIS and at most the axis'
+                             points; px py pz <= GRF_MAX_PATCHES */
+} grf_patch_level;
+
+/* Host only. The geometry of patch `index`: its interior extent, ng = 3, dx of the box, the
+ * centre of its first interior point (box origin + offset dx), bc GRF_BC_FROZEN (its ghosts are
+ * written by the exchange) and pitch = interior x-extent + 6 rounded up to a multiple of 4.
+ * Every patch state passed to the calls below has this layout. GRF_EINVAL on a bad level,
+ * index or null pointer. */
+int grf_patch_box(const grf_patch_level* level, int index, grf_box* out);
+
+/* Copies between a whole-box state (the layout of level->box) and the patches. direction 0:
+ * every patch's interior from the box's interior (the ghosts are then filled by an exchange);
+ * 1: the box's interior from the patches' interiors (its ghosts are left unchanged). patches is a
+ * host array of px py pz device pointers. Asynchronous on `stream`. */
+int grf_patch_copy(const grf_patch_level* level, double* box_state, double* const* patches, int direction,
+                   grf_stream_t stream);
+
+/* The built-in halo exchange: every ghost point of every patch (all 27 fields) takes the value
+ * of the same point of the periodic box, read from the interior of the patch that owns it.
+ * patches: host array of px py pz device pointers (read during the call). Asynchronous on
+ * `stream`. */
+int grf_halo_exchange(const grf_patch_level* level, double* const* patches, grf_stream_t stream);
+
+/* A halo exchange that grf_patches_rk4 calls on the patches' current buffers (a host array of
+ * px py pz device pointers in grf_patch_box layouts, valid for the call only): before the first
+ * step on the patch states, then after every stage on the buffers that stage wrote. It must fill
+ * every ghost point as grf_halo_exchange does, in order on `stream` (or synchronised with it), and
+ * return GRF_OK; another return value ends grf_patches_rk4 with that value. */
+typedef int (*grf_halo_fn)(void* ctx, const grf_patch_level* level, double* const* patches, grf_stream_t stream);
+
+/* Scratch bytes for grf_patches_rk4: descriptors, tile list and three state-sized buffers per
+ * patch. 0 for a bad level. */
+size_t grf_patches_workspace_bytes(const grf_patch_level* level);
+
+/* Advance the whole box, held as its patches (host array of px py pz device pointers, interiors
+ * valid; advanced in place), by nsteps RK4 steps of size dt with the scheme of grf_rk4_step
+ * (4th order, ng = 3; centred or lopsided advection, every coupling kind). exchange: NULL for
+ * grf_halo_exchange, else the caller's, called with exchange_ctx. status_host (host, may be NULL):
+ * when given, the call synchronises `stream` and returns GRF_ESINGULAR if a coupled system was
+ * singular. Errors: GRF_EINVAL (bad level, params, pointers or nsteps < 0), GRF_EWORKSPACE
+ * (ws null, smaller than grf_patches_workspace_bytes or not 256-byte aligned), GRF_ECUDA. */
+int grf_patches_rk4(const grf_patch_level* level, const grf_params* params, double* const* patches, double dt,
+                    int nsteps, grf_halo_fn exchange, void* exchange_ctx, void* ws, size_t ws_bytes, int* status_host,
+                    grf_stream_t stream);
+
+/* ---------------------------------------------------------------------------------------
  * Differentiation of an extracted scalar signal (the paper extracts scalar waveforms on
  * spheres, section "Key features": Diagnostics). The signal is
  *   L = sum_{n=1..nsteps} dt * sum_{q=1..26} w_q phi(c + R x_q, t_n)

@@ -60,6 +60,17 @@ class grf_sphere(C.Structure):
     _fields_ = [("radius", C.c_double), ("cx", C.c_double), ("cy", C.c_double), ("cz", C.c_double)]
 
 
+GRF_MAX_PATCHES_PER_AXIS, GRF_MAX_PATCHES = 16, 256
+
+
+class grf_patch_level(C.Structure):
+    _fields_ = [("box", grf_box), ("px", C.c_int), ("py", C.c_int), ("pz", C.c_int)]
+
+
+# int (*)(void* ctx, const grf_patch_level*, double* const* patches, grf_stream_t)
+grf_halo_fn = C.CFUNCTYPE(C.c_int, C.c_void_p, C.POINTER(grf_patch_level), C.POINTER(C.c_void_p), C.c_void_p)
+
+
 class GrfError(RuntimeError):
     def __init__(self, code, what):
         self.code = code
@@ -109,6 +120,16 @@ def lib():
         L.grf_tlm_rk4.restype = C.c_int
         L.grf_rk4_step_noalloc.argtypes = [B, P, _VP, C.c_double, C.c_int, _VP]
         L.grf_rk4_step_noalloc.restype = C.c_int
+        PL, PP = C.POINTER(grf_patch_level), C.POINTER(C.c_void_p)
+        L.grf_patch_box.argtypes = [PL, C.c_int, B]
+        L.grf_patch_copy.argtypes = [PL, _VP, PP, C.c_int, _VP]
+        L.grf_halo_exchange.argtypes = [PL, PP, _VP]
+        L.grf_patches_workspace_bytes.argtypes = [PL]
+        L.grf_patches_workspace_bytes.restype = C.c_size_t
+        L.grf_patches_rk4.argtypes = [PL, P, PP, C.c_double, C.c_int, grf_halo_fn, _VP, _VP, C.c_size_t,
+                                      C.POINTER(C.c_int), _VP]
+        for name in ("grf_patch_box", "grf_patch_copy", "grf_halo_exchange", "grf_patches_rk4"):
+            getattr(L, name).restype = C.c_int
         L.grf_error_string.argtypes = [C.c_int]
         L.grf_error_string.restype = C.c_char_p
         L.grf_last_cuda_error.restype = C.c_char_p
@@ -339,6 +360,65 @@ def grf_batched_rk4(items, params, nsteps, cfg, ws=None, stream=None, sync_statu
     code = lib().grf_batched_rk4(items, len(items), params, len(params), int(nsteps), C.byref(cfg), _dev(ws),
                                  ws.numel(), C.byref(st) if sync_status else None, _stream(stream))
     return _check(code, "grf_batched_rk4")
+
+
+# ------------------------------------------------------------------------------ one box as patches
+def patch_level(box: grf_box, px: int, py: int, pz: int) -> grf_patch_level:
+    """A periodic box split into px x py x pz patches."""
+    return grf_patch_level(box, int(px), int(py), int(pz))
+
+
+def grf_patch_box(level: grf_patch_level, index: int) -> grf_box:
+    """The geometry (frozen-ghost layout) of patch `index` (a + px (b + py c))."""
+    out = grf_box()
+    _check(lib().grf_patch_box(C.byref(level), int(index), C.byref(out)), "grf_patch_box")
+    return out
+
+
+def patch_states(level: grf_patch_level, device="cuda"):
+    """Zeroed patch states, one per patch, each in its grf_patch_box layout."""
+    import torch
+    n = level.px * level.py * level.pz
+    return [torch.zeros(state_shape(grf_patch_box(level, q)), dtype=torch.float64, device=device) for q in range(n)]
+
+
+def _ptr_array(tensors):
+    arr = (C.c_void_p * len(tensors))()
+    for i, t in enumerate(tensors):
+        assert t.is_cuda and t.is_contiguous()
+        arr[i] = t.data_ptr()
+    return arr
+
+
+def grf_patch_copy(level: grf_patch_level, box_state, patches, direction: int, stream=None):
+    """direction 0: the patches' interiors from the box's; 1: the box's interior from the patches'."""
+    return _check(lib().grf_patch_copy(C.byref(level), _dev(box_state), _ptr_array(patches), int(direction),
+                                       _stream(stream)), "grf_patch_copy")
+
+
+def grf_halo_exchange(level: grf_patch_level, patches, stream=None):
+    """Every ghost point of every patch from the patch that owns it in the periodic box."""
+    return _check(lib().grf_halo_exchange(C.byref(level), _ptr_array(patches), _stream(stream)),
+                  "grf_halo_exchange")
+
+
+def grf_patches_workspace_bytes(level: grf_patch_level) -> int:
+    return int(lib().grf_patches_workspace_bytes(C.byref(level)))
+
+
+def grf_patches_rk4(level: grf_patch_level, params: grf_params, patches, dt, nsteps, exchange=None, ws=None,
+                    stream=None, sync_status=True):
+    """Advances the box held as `patches` by nsteps RK4 steps. exchange: None for the built-in halo
+    exchange, or a Python callable (level_ptr, patch_ptr_array, stream) -> int with the grf_halo_fn
+    contract (it may call the library, e.g. lib().grf_halo_exchange)."""
+    if ws is None:
+        ws = alloc_workspace(grf_patches_workspace_bytes(level))
+    fn = C.cast(None, grf_halo_fn) if exchange is None else grf_halo_fn(lambda ctx, lv, ptrs, st: int(exchange(lv, ptrs, st)))
+    status = C.c_int(0)
+    code = lib().grf_patches_rk4(C.byref(level), C.byref(params), _ptr_array(patches), float(dt), int(nsteps), fn,
+                                 None, _dev(ws), ws.numel(), C.byref(status) if sync_status else None,
+                                 _stream(stream))
+    return _check(code, "grf_patches_rk4")
 
 
 def grf_rk4_step_noalloc(box: grf_box, params: grf_params, state, dt, nsteps, stream=None):

@@ -15,7 +15,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgrf.so")
 SOURCES = ["grf_api.cu", "grf_stage.cu", "grf_stage_dec.cu", "grf_stage_fold.cu", "grf_stage_lop.cu", "grf_stage_gen.cu",
            "grf_stage6.cu", "grf_stage6l.cu", "grf_rhs.cu", "grf_rhs6.cu", "grf_boundary.cu", "grf_extract.cu",
-           "grf_batch.cu", "grf_batch_persistent.cu", "grf_noalloc.cu", "grf_tlm.cu"]
+           "grf_batch.cu", "grf_batch_persistent.cu", "grf_patches.cu", "grf_noalloc.cu", "grf_tlm.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INC, "-I" + CSRC]

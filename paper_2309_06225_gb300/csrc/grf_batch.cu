@@ -54,6 +54,66 @@ __global__ void batch_ghost_fill_kernel(const BoxDesc* __restrict__ boxes, int b
     }
 }
 
+bool batch_params_ok(const grf_params* p) {
+    if (p->beta_kind != GRF_BETA_LINEAR && p->beta_kind != GRF_BETA_QUADRATIC && p->beta_kind != GRF_BETA_EXPONENTIAL)
+        return false;
+    if (p->beta_kind == GRF_BETA_EXPONENTIAL && !(p->beta_kappa >= 0.0 && p->beta_kappa < 1e300)) return false;
+    if (!(1.0 + p->a0 > 0.0) || !(1.0 + p->b0 > 0.0)) return false;
+    return p->advection == 0 || p->advection == 1;
+}
+
+void batch_box_desc(BoxDesc& d, const grf_box* b, const grf_params* p, double dt) {
+    std::memset(&d, 0, sizeof(d));
+    Geom& g = d.g;
+    g.nx = b->nx; g.ny = b->ny; g.nz = b->nz;
+    g.NX = b->nx + 6; g.NY = b->ny + 6; g.NZ = b->nz + 6;
+    g.ng = NG;
+    g.pitch = b->pitch;
+    g.plane = b->pitch * g.NY;
+    g.fstride = g.plane * g.NZ;
+    g.dx = b->dx;
+    g.periodic = (b->bc == GRF_BC_PERIODIC);
+    g.reflect = 0;  // mirror boxes are not accepted here
+    d.c.kappa1 = p->kappa1; d.c.kappa2 = p->kappa2; d.c.kappa3 = p->kappa3;
+    d.c.shift_F = p->shift_F; d.c.eta = p->eta; d.c.lam = p->lambda; d.c.g2 = p->g2;
+    d.c.inv_1pa = 1.0 / (1.0 + p->a0); d.c.a_1pa = p->a0 / (1.0 + p->a0);
+    d.c.bK = 3.0 * p->b0 / (4.0 * (1.0 + p->b0)); d.c.bTh = 1.0 / (2.0 * (1.0 + p->b0));
+    d.c.beta_kind = p->beta_kind;
+    d.c.beta_kappa = p->beta_kappa;
+    d.c.decoupled = p->decoupled;
+    d.c.advection = p->advection;
+    d.dt = dt;
+    d.ko = p->sigma_ko / (64.0 * b->dx);
+    d.min_chi = p->min_chi;
+    d.min_lapse = p->min_lapse;
+    d.enforce = p->enforce_algebraic;
+}
+
+// A box whose x-extent is not a multiple of 32 would leave lanes idle through the whole stage;
+// its tiles are folded instead, each warp covering 32 / w rows of w = 8 or 16 points, whichever
+// fills the most lanes (the folded tiles take the per-thread gather).
+int batch_row_width(int nx) {
+    if (nx % 32 == 0) return 32;
+    int best = 32;
+    double best_eff = (double)nx / (32.0 * ((nx + 31) / 32));
+    for (int w : {16, 8}) {
+        const double eff = (double)nx / ((double)w * ((nx + w - 1) / w));
+        if (eff > best_eff + 1e-12) { best = w; best_eff = eff; }
+    }
+    return best;
+}
+
+void launch_batch_stage(int stage, long long ntiles, dim3 block, cudaStream_t st, const BoxDesc* boxes,
+                        const TileDesc* tiles, int* status) {
+    const dim3 grid((unsigned)ntiles);
+    switch (stage) {
+        case 0: batch_stage_kernel<0><<<grid, block, 0, st>>>(boxes, tiles, (int)ntiles, status); break;
+        case 1: batch_stage_kernel<1><<<grid, block, 0, st>>>(boxes, tiles, (int)ntiles, status); break;
+        case 2: batch_stage_kernel<2><<<grid, block, 0, st>>>(boxes, tiles, (int)ntiles, status); break;
+        default: batch_stage_kernel<3><<<grid, block, 0, st>>>(boxes, tiles, (int)ntiles, status); break;
+    }
+}
+
 }  // namespace grf
 
 using namespace grf;
@@ -81,34 +141,19 @@ bool cfg_ok(const grf_batch_config* c) {
 }
 
 Geom geom_of(const grf_box* b) {
-    Geom g;
-    g.nx = b->nx; g.ny = b->ny; g.nz = b->nz;
-    g.NX = b->nx + 6; g.NY = b->ny + 6; g.NZ = b->nz + 6;
-    g.ng = NG;
-    g.pitch = b->pitch;
-    g.plane = b->pitch * g.NY;
-    g.fstride = g.plane * g.NZ;
-    g.dx = b->dx;
-    g.periodic = (b->bc == GRF_BC_PERIODIC);
-    g.reflect = 0;  // mirror boxes are not accepted here
-    return g;
+    static const grf_params kAny{};  // only the geometry is used
+    BoxDesc d;
+    batch_box_desc(d, b, &kAny, 0.0);
+    return d.g;
 }
 
 size_t state_bytes_of(const Geom& g) { return sizeof(double) * (size_t)NFIELDS * (size_t)g.fstride; }
 
-// x-points per tile row for a box. With 32 x 4 x 1 tiles, a box whose x-extent is not a
-// multiple of 32 would leave lanes idle through the whole stage; its tiles are folded instead,
-// each warp covering 32 / w rows of w = 8 or 16 points, whichever fills the most lanes (the
-// folded tiles take the per-thread gather).
+// x-points per tile row for a box: folded rows (batch_row_width) with 32 x 4 x 1 tiles, else the
+// tile's width.
 int row_width(const grf_box* b, const grf_batch_config* c) {
-    if (!(c->tile_x == 32 && c->tile_y == 4 && c->tile_z == 1) || b->nx % 32 == 0) return c->tile_x;
-    int best = 32;
-    double best_eff = (double)b->nx / (32.0 * ((b->nx + 31) / 32));
-    for (int w : {16, 8}) {
-        const double eff = (double)b->nx / ((double)w * ((b->nx + w - 1) / w));
-        if (eff > best_eff + 1e-12) { best = w; best_eff = eff; }
-    }
-    return best;
+    if (!(c->tile_x == 32 && c->tile_y == 4 && c->tile_z == 1)) return c->tile_x;
+    return batch_row_width(b->nx);
 }
 
 long long tiles_of(const grf_box* b, const grf_batch_config* c) {
@@ -197,13 +242,8 @@ cudaError_t build_stage_graph(int nsteps, long long ntiles, dim3 block, const Bo
 
 void launch_stages(int nsteps, long long ntiles, dim3 block, cudaStream_t st, const BoxDesc* boxes,
                    const TileDesc* tiles, int* status) {
-    const dim3 grid((unsigned)ntiles);
-    for (int n = 0; n < nsteps; ++n) {
-        batch_stage_kernel<0><<<grid, block, 0, st>>>(boxes, tiles, (int)ntiles, status);
-        batch_stage_kernel<1><<<grid, block, 0, st>>>(boxes, tiles, (int)ntiles, status);
-        batch_stage_kernel<2><<<grid, block, 0, st>>>(boxes, tiles, (int)ntiles, status);
-        batch_stage_kernel<3><<<grid, block, 0, st>>>(boxes, tiles, (int)ntiles, status);
-    }
+    for (int n = 0; n < nsteps; ++n)
+        for (int s = 0; s < 4; ++s) launch_batch_stage(s, ntiles, block, st, boxes, tiles, status);
 }
 
 }  // namespace
@@ -224,13 +264,7 @@ int grf_batched_rk4(const grf_batch_item* items, int nitems, const grf_params* p
         if (!item_ok(items[i])) return GRF_EINVAL;
         const int pi = items[i].params_index;
         if (pi < 0 || pi >= nparams) return GRF_EINVAL;
-        const grf_params* p = &params[pi];
-        if (p->beta_kind != GRF_BETA_LINEAR && p->beta_kind != GRF_BETA_QUADRATIC &&
-            p->beta_kind != GRF_BETA_EXPONENTIAL)
-            return GRF_EINVAL;
-        if (p->beta_kind == GRF_BETA_EXPONENTIAL && !(p->beta_kappa >= 0.0 && p->beta_kappa < 1e300)) return GRF_EINVAL;
-        if (!(1.0 + p->a0 > 0.0) || !(1.0 + p->b0 > 0.0)) return GRF_EINVAL;
-        if (p->advection != 0 && p->advection != 1) return GRF_EINVAL;
+        if (!batch_params_ok(&params[pi])) return GRF_EINVAL;
     }
     const Layout L = layout(items, nitems, cfg);
     DBG("entry: %d boxes, %lld tiles, ws %zu of %zu bytes, variant %d, tile %dx%dx%d", nitems, L.ntiles, ws_bytes,
@@ -254,27 +288,13 @@ int grf_batched_rk4(const grf_batch_item* items, int nitems, const grf_params* p
         const grf_batch_item& it = items[b];
         const grf_params* p = &params[it.params_index];
         BoxDesc& d = hb[b];
-        std::memset(&d, 0, sizeof(d));
-        d.g = geom_of(&it.box);
-        d.c.kappa1 = p->kappa1; d.c.kappa2 = p->kappa2; d.c.kappa3 = p->kappa3;
-        d.c.shift_F = p->shift_F; d.c.eta = p->eta; d.c.lam = p->lambda; d.c.g2 = p->g2;
-        d.c.inv_1pa = 1.0 / (1.0 + p->a0); d.c.a_1pa = p->a0 / (1.0 + p->a0);
-        d.c.bK = 3.0 * p->b0 / (4.0 * (1.0 + p->b0)); d.c.bTh = 1.0 / (2.0 * (1.0 + p->b0));
-        d.c.beta_kind = p->beta_kind;
-        d.c.beta_kappa = p->beta_kappa;
-        d.c.decoupled = p->decoupled;
-        d.c.advection = p->advection;
+        batch_box_desc(d, &it.box, p, it.dt);
         const size_t sb = align_up(state_bytes_of(d.g));
         d.un = it.state;
         d.A = (double*)(base + off);
         d.B = (double*)(base + off + sb);
         d.acc = (double*)(base + off + 2 * sb);
         off += 3 * sb;
-        d.dt = it.dt;
-        d.ko = p->sigma_ko / (64.0 * it.box.dx);
-        d.min_chi = p->min_chi;
-        d.min_lapse = p->min_lapse;
-        d.enforce = p->enforce_algebraic;
         const int w = row_width(&it.box, cfg);
         const int rows = cfg->tile_y * (cfg->tile_x / w);
         for (int k = 0; k < it.box.nz; k += cfg->tile_z)

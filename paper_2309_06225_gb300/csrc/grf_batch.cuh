@@ -3,6 +3,7 @@
 // compiled in separate translation units so that the library builds in parallel.
 #pragma once
 
+#include "grf.h"
 #include "grf_kernels.cuh"
 
 namespace grf {
@@ -73,6 +74,16 @@ __device__ __noinline__ void batch_tile_call(const BoxDesc* __restrict__ boxes, 
                                              YzRows& sh) {
     batch_tile<STAGE, DEC, LOP>(boxes, td, status, sh);
 }
+
+// Shared with the split-box evolution (grf_patches.cu), in grf_batch.cu: the couplings check of
+// one parameter set; a box descriptor (geometry, coefficients, dissipation, floors and dt; the
+// buffers are left null); the x-points per row of a box's 32 x 4 x 1 tiles (32, or a folded 16 or 8);
+// one stage launch over a tile list.
+bool batch_params_ok(const grf_params* p);
+void batch_box_desc(BoxDesc& d, const grf_box* b, const grf_params* p, double dt);
+int batch_row_width(int nx);
+void launch_batch_stage(int stage, long long ntiles, dim3 block, cudaStream_t st, const BoxDesc* boxes,
+                        const TileDesc* tiles, int* status);
 
 // The persistent cooperative launch (grf_batch_persistent.cu): its function attributes (loads the
 // kernel), its resident blocks per SM for `nthreads` threads, and the launch.

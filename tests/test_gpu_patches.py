@@ -1,0 +1,176 @@
+"""One periodic box evolved as patches with a halo exchange after every RK4 stage
+(grf_patches_rk4, grf_halo_exchange, grf_patch_copy) on the GPU.
+
+The exchange and the copies move values only, so they are checked bit for bit against the
+periodic images of the whole box. Each patch's stage runs the batched stage kernel on the same
+values the whole-box stage reads, so the patches' interiors after nsteps steps must equal,
+bit for bit, grf_rk4_step on the whole box (itself checked against the oracle in
+test_gpu_parity.py); one case is also compared with the oracle directly.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import grf_inputs as gi
+from parity import describe, field_errors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2309_06225_gb300 import build
+    build.build()
+    import paper_2309_06225_gb300 as grf
+    grf.lib()
+    return grf
+
+
+def offsets(n, p):
+    return [(a * n) // p for a in range(p + 1)]
+
+
+def periodic_block(whole, box, lo, n):
+    """The ghosted block of the periodic box that a patch with interior [lo, lo + n) holds."""
+    idx = [np.arange(l - 3, l + m + 3) % N for l, m, N in zip(lo, n, (box.nx, box.ny, box.nz))]
+    return whole[:, idx[2]][:, :, idx[1]][:, :, :, idx[0]]
+
+
+def split(g, box, s, p):
+    """The patches of a host state of the whole box, interiors copied on the device, ghosts exchanged."""
+    b = g.box_like(box)
+    L = g.patch_level(b, *p)
+    whole = g.to_device(s, b)
+    patches = g.patch_states(L)
+    g.grf_patch_copy(L, whole, patches, 0)
+    g.grf_halo_exchange(L, patches)
+    return L, patches
+
+
+@pytest.mark.parametrize("n,p", [((29, 22, 17), (3, 2, 2)), ((16, 16, 16), (1, 1, 1)), ((9, 8, 12), (3, 4, 4)),
+                                 ((40, 6, 6), (16, 2, 1))])
+def test_exchange_writes_the_periodic_images(g, n, p):
+    """Every patch, ghosts included, equals the block of the periodic box it stands for (patches
+    narrower than the 3 ghost layers read their ghosts from patches two or more away)."""
+    box = gi.Box(*n, 0.2, 0.0, 0.0, 0.0)
+    s = np.random.default_rng(1).normal(size=box.shape)
+    whole = s[:, 3:-3, 3:-3, 3:-3]
+    L, patches = split(g, box, s, p)
+    ox, oy, oz = offsets(n[0], p[0]), offsets(n[1], p[1]), offsets(n[2], p[2])
+    for c in range(p[2]):
+        for b in range(p[1]):
+            for a in range(p[0]):
+                q = a + p[0] * (b + p[1] * c)
+                pb = g.grf_patch_box(L, q)
+                lo, m = (ox[a], oy[b], oz[c]), (pb.nx, pb.ny, pb.nz)
+                assert np.array_equal(g.to_host(patches[q], pb), periodic_block(whole, box, lo, m)), q
+
+
+def test_patch_copy_round_trip(g):
+    box = gi.Box(21, 13, 10, 0.2, 0.0, 0.0, 0.0)
+    s = np.random.default_rng(2).normal(size=box.shape)
+    b = g.box_like(box)
+    L, patches = split(g, box, s, (2, 3, 2))
+    back = g.alloc_state(b)
+    back.zero_()
+    g.grf_patch_copy(L, back, patches, 1)
+    got = g.to_host(back, b)
+    assert np.array_equal(got[:, 3:-3, 3:-3, 3:-3], s[:, 3:-3, 3:-3, 3:-3])
+    assert not np.any(got[:, :3]) and not np.any(got[:, :, :, -3:])  # the box's ghosts are left alone
+
+
+def whole_and_patches(g, box, params, s, p, dt, nsteps, exchange=None):
+    b, gp = g.box_like(box), g.params_like(params)
+    t = g.to_device(s, b)
+    g.grf_rk4_step(b, gp, t, dt, nsteps)
+    assert g.grf_check_status() == 0
+    ref = g.to_host(t, b)
+    L, patches = split(g, box, s, p)
+    g.grf_patches_rk4(L, gp, patches, dt, nsteps, exchange=exchange)
+    out = g.alloc_state(b)
+    g.grf_patch_copy(L, out, patches, 1)
+    return ref, g.to_host(out, b)
+
+
+@pytest.mark.parametrize("p", [(2, 2, 2), (1, 1, 1), (4, 1, 3), (3, 2, 5)])
+def test_patches_equal_the_whole_box_bit_for_bit(g, p):
+    """32^3 single puncture: 32-wide patches take the block gather, 16- and 8-wide ones the folded
+    per-thread gather, ragged ones (10 / 11 points) partial rows."""
+    cfg = gi.config_single_puncture_32()
+    box, params, dt = cfg["box"], cfg["params"], cfg["dt"]
+    s = cfg["make_state"]()
+    ref, got = whole_and_patches(g, box, params, s, p, dt, 2)
+    assert np.array_equal(got[:, 3:-3, 3:-3, 3:-3], ref[:, 3:-3, 3:-3, 3:-3])
+
+
+@pytest.mark.parametrize("params", [gi.Params(lam=0.05, g2=0.02, advection=1),
+                                    gi.Params(lam=0.3, g2=0.1, beta_kind=2, beta_kappa=1.5),
+                                    gi.Params(lam=0.2, g2=0.1, decoupled=1)])
+def test_patches_other_schemes_bit_for_bit(g, params):
+    """Lopsided advection, the exponential coupling and the decoupled mode on a ragged box."""
+    box = gi.Box(26, 19, 14, 0.3, -3.9, -2.85, -2.1)
+    s = gi.random_perturbed_state(box, 5, base=gi.single_puncture(box, amp=0.05), eps=2e-2)
+    ref, got = whole_and_patches(g, box, params, s, (2, 3, 2), 0.25 * box.dx, 2)
+    assert np.array_equal(got[:, 3:-3, 3:-3, 3:-3], ref[:, 3:-3, 3:-3, 3:-3])
+
+
+def test_patches_parity_with_the_oracle(g, orc):
+    box = gi.Box(24, 20, 18, 0.3, -3.6, -3.0, -2.7)
+    params = gi.Params(lam=0.1, g2=0.05, beta_kind=1)
+    s = gi.random_perturbed_state(box, 9, base=gi.single_puncture(box, amp=0.05), eps=1e-2)
+    b = g.box_like(box)
+    L, patches = split(g, box, s, (3, 2, 2))
+    dt = 0.25 * box.dx
+    g.grf_patches_rk4(L, g.params_like(params), patches, dt, 2)
+    out = g.alloc_state(b)
+    g.grf_patch_copy(L, out, patches, 1)
+    cpu = s.copy()
+    orc.fill_ghosts(box, cpu)
+    orc.rk4(box, params, cpu, dt, 2)
+    errs = field_errors(g.to_host(out, b), cpu, box)
+    assert np.max(errs) < 1e-11, describe(errs)
+
+
+def test_exchange_is_pluggable(g):
+    """A caller's exchange (here one that counts its calls and forwards to the built-in one) takes
+    the built-in one's place: called once before the first step and once after every stage, with
+    the same result bits."""
+    cfg = gi.config_single_puncture_32()
+    box, params, dt = cfg["box"], cfg["params"], cfg["dt"]
+    s = cfg["make_state"]()
+    calls = []
+
+    def exchange(level, ptrs, stream):
+        calls.append(stream)
+        return g.lib().grf_halo_exchange(level, ptrs, stream)
+
+    nsteps = 3
+    ref, got = whole_and_patches(g, box, params, s, (2, 1, 2), dt, nsteps, exchange=exchange)
+    assert len(calls) == 1 + 4 * nsteps
+    assert np.array_equal(got[:, 3:-3, 3:-3, 3:-3], ref[:, 3:-3, 3:-3, 3:-3])
+
+
+def test_failing_exchange_ends_the_step(g):
+    """An exchange that reports an error (a lost peer, say) ends grf_patches_rk4 with its code after
+    the stage already in flight; no kernel waits on it."""
+    cfg = gi.config_single_puncture_32()
+    box, params, dt = cfg["box"], cfg["params"], cfg["dt"]
+    s = cfg["make_state"]()
+    calls = []
+
+    def exchange(level, ptrs, stream):
+        calls.append(1)
+        return g.GRF_ETIMEOUT if len(calls) == 3 else g.lib().grf_halo_exchange(level, ptrs, stream)
+
+    L, patches = split(g, box, s, (2, 2, 1))
+    with pytest.raises(g.GrfError) as e:
+        g.grf_patches_rk4(L, g.params_like(params), patches, dt, 2, exchange=exchange)
+    assert e.value.code == g.GRF_ETIMEOUT and len(calls) == 3
+    import torch
+    torch.cuda.synchronize()  # the context is still usable
+    g.grf_halo_exchange(L, patches)
+    torch.cuda.synchronize()
