@@ -264,12 +264,13 @@ int grf_batched_rk4(const grf_batch_item* items, int nitems, const grf_params* p
                     const grf_batch_config* cfg, void* ws, size_t ws_bytes, int* status_host, grf_stream_t stream);
 
 /* ---------------------------------------------------------------------------------------
- * One periodic box split into patches (domain decomposition). GRFolres distributes the boxes of
+ * One box split into patches (domain decomposition). GRFolres distributes the boxes of
  * a level over processes and fills each box's ghost cells from its neighbours before every
  * right-hand side ("Key features": parallelism, AMR). Here the box's interior is
  * cut into px x py x pz patches, each a state of its own (frozen-ghost layout, below); every RK4
  * stage advances all patches' points in one launch, and a halo exchange then refills every
- * patch's ghosts from the interiors of the patches that own those points. The exchange is a
+ * patch's ghosts from the interiors of the patches that own those points (in a box with frozen
+ * ghosts, the patches' ghost points outside the box keep the values they were given). The exchange is a
  * separate step behind a function pointer, so a caller can put its own in its place (one that
  * moves halos between devices or processes, say); the built-in one is grf_halo_exchange.
  * With the built-in exchange the patches' interiors after grf_patches_rk4 equal, bit for bit,
@@ -282,7 +283,7 @@ int grf_batched_rk4(const grf_batch_item* items, int nitems, const grf_params* p
 #define GRF_MAX_PATCHES 256
 
 typedef struct {
-    grf_box box;          /* the whole box: GRF_BC_PERIODIC, ng = 3, each of nx, ny, nz >= 3 */
+    grf_box box;          /* the whole box: ng = 3; GRF_BC_PERIODIC (nx, ny, nz >= 3) or GRF_BC_FROZEN */
     int px, py, pz;       /* patches per axis: 1 .. GRF_MAX_PATCHES_PER_AXIS and at most the axis'
                              points; px py pz <= GRF_MAX_PATCHES */
 } grf_patch_level;
@@ -295,14 +296,17 @@ typedef struct {
 int grf_patch_box(const grf_patch_level* level, int index, grf_box* out);
 
 /* Copies between a whole-box state (the layout of level->box) and the patches. direction 0:
- * every patch's interior from the box's interior (the ghosts are then filled by an exchange);
- * 1: the box's interior from the patches' interiors (its ghosts are left unchanged). patches is a
+ * every point of every patch, ghosts included, from the same point of the box (an exchange then
+ * rewrites the ghosts that lie inside the box, or all of them in a periodic box, so only a frozen
+ * box's ghosts need be set); 1: the box's interior from the patches' interiors (its ghosts are
+ * left unchanged). patches is a
  * host array of px py pz device pointers. Asynchronous on `stream`. */
 int grf_patch_copy(const grf_patch_level* level, double* box_state, double* const* patches, int direction,
                    grf_stream_t stream);
 
-/* The built-in halo exchange: every ghost point of every patch (all 27 fields) takes the value
- * of the same point of the periodic box, read from the interior of the patch that owns it.
+/* The built-in halo exchange: every ghost point of every patch (all 27 fields) that lies in the
+ * box (periodic: all of them, wrapped) takes the value of the same point of the box, read from
+ * the interior of the patch that owns it; the others are left unchanged.
  * patches: host array of px py pz device pointers (read during the call). Asynchronous on
  * `stream`. */
 int grf_halo_exchange(const grf_patch_level* level, double* const* patches, grf_stream_t stream);
@@ -319,7 +323,7 @@ typedef int (*grf_halo_fn)(void* ctx, const grf_patch_level* level, double* cons
 size_t grf_patches_workspace_bytes(const grf_patch_level* level);
 
 /* Advance the whole box, held as its patches (host array of px py pz device pointers, interiors
- * valid; advanced in place), by nsteps RK4 steps of size dt with the scheme of grf_rk4_step
+ * valid, and in a frozen box the ghosts outside it; advanced in place), by nsteps RK4 steps of size dt with the scheme of grf_rk4_step
  * (4th order, ng = 3; centred or lopsided advection, every coupling kind). exchange: NULL for
  * grf_halo_exchange, else the caller's, called with exchange_ctx. status_host (host, may be NULL):
  * when given, the call synchronises `stream` and returns GRF_ESINGULAR if a coupled system was

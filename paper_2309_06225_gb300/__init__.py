@@ -364,7 +364,7 @@ def grf_batched_rk4(items, params, nsteps, cfg, ws=None, stream=None, sync_statu
 
 # ------------------------------------------------------------------------------ one box as patches
 def patch_level(box: grf_box, px: int, py: int, pz: int) -> grf_patch_level:
-    """A periodic box split into px x py x pz patches."""
+    """A box (periodic or with frozen ghosts) split into px x py x pz patches."""
     return grf_patch_level(box, int(px), int(py), int(pz))
 
 
@@ -391,7 +391,8 @@ def _ptr_array(tensors):
 
 
 def grf_patch_copy(level: grf_patch_level, box_state, patches, direction: int, stream=None):
-    """direction 0: the patches' interiors from the box's; 1: the box's interior from the patches'."""
+    """direction 0: every point of the patches, ghosts included, from the box; 1: the box's interior
+    from the patches'."""
     return _check(lib().grf_patch_copy(C.byref(level), _dev(box_state), _ptr_array(patches), int(direction),
                                        _stream(stream)), "grf_patch_copy")
 

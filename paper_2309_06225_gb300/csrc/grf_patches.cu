@@ -1,10 +1,11 @@
-// One periodic box evolved as px x py x pz patches with a halo exchange after every RK4 stage
-// (domain decomposition on one device; the calls are declared in grf.h).
+// One box (periodic or with frozen ghosts) evolved as px x py x pz patches with a halo exchange
+// after every RK4 stage (domain decomposition on one device; the calls are declared in grf.h).
 //
 // The stage work of all patches is one launch of the batched stage kernel over the patches' tiles
 // (each patch a frozen-ghost box: the stage reads its ghosts and writes its interior only). After
 // the stage, the exchange writes every ghost point of every patch from the interior of the patch
-// that owns the point in the periodic box. The stage arithmetic per point is that of grf_rk4_step
+// that owns the point in the box (periodic: every ghost point; frozen: the ghost points inside the
+// box, the others keep the caller's values). The stage arithmetic per point is that of grf_rk4_step
 // and its inputs are the same values, so the results are the same bits.
 #include <cstdint>
 #include <cstring>
@@ -21,6 +22,7 @@ namespace grf {
 struct PatchTable {
     int p[3];                                      // patches per axis
     int n[3];                                      // the box's interior points per axis
+    int periodic;                                  // 1: periodic box, 0: frozen ghosts
     int off[3][GRF_MAX_PATCHES_PER_AXIS + 1];      // first interior point of each patch, per axis
     double* ptr[GRF_MAX_PATCHES];                  // the patch states (device)
 };
@@ -50,7 +52,8 @@ __device__ __forceinline__ int owner(const int* off, int p, int x) {
     return a;
 }
 
-// One thread per ghost point of patch blockIdx.y; 27 fields each.
+// One thread per ghost point of patch blockIdx.y; 27 fields each. In a frozen box the ghost points
+// outside the box are skipped.
 __global__ void __launch_bounds__(256) halo_exchange_kernel(PatchTable t) {
     const int q = blockIdx.y;
     const int a = q % t.p[0], b = (q / t.p[0]) % t.p[1], c = q / (t.p[0] * t.p[1]);
@@ -59,8 +62,9 @@ __global__ void __launch_bounds__(256) halo_exchange_kernel(PatchTable t) {
     if (s >= shell_count(g, 0)) return;
     int i, j, k;
     shell_point(g, 0, s, i, j, k);
-    // the point in the periodic box's interior indices (ghost layers reach at most 3 beyond it)
+    // the point in the box's interior indices (ghost layers reach at most 3 beyond it)
     int x = t.off[0][a] + i - NG, y = t.off[1][b] + j - NG, z = t.off[2][c] + k - NG;
+    if (!t.periodic && (x < 0 || x >= t.n[0] || y < 0 || y >= t.n[1] || z < 0 || z >= t.n[2])) return;
     x += x < 0 ? t.n[0] : (x >= t.n[0] ? -t.n[0] : 0);
     y += y < 0 ? t.n[1] : (y >= t.n[1] ? -t.n[1] : 0);
     z += z < 0 ? t.n[2] : (z >= t.n[2] ? -t.n[2] : 0);
@@ -74,16 +78,18 @@ __global__ void __launch_bounds__(256) halo_exchange_kernel(PatchTable t) {
     for (int f = 0; f < NFIELDS; ++f) dst[(long long)f * g.fstride] = src[(long long)f * h.fstride];
 }
 
-// One thread per interior point of patch blockIdx.y: the patch's interior from the box's
-// (to_patch) or the reverse.
+// One thread per point of patch blockIdx.y: to_patch, every point of the patch, ghosts included,
+// from the same point of the box (the patch's ghosted block lies inside the box's); otherwise the
+// box's interior from the patch's.
 __global__ void __launch_bounds__(256) patch_copy_kernel(PatchTable t, Geom box, double* __restrict__ s, int to_patch) {
     const int q = blockIdx.y;
     const int a = q % t.p[0], b = (q / t.p[0]) % t.p[1], c = q / (t.p[0] * t.p[1]);
     const Geom g = patch_geom(t, a, b, c);
+    const int h = to_patch ? NG : 0;  // extent beyond the interior
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long row = g.nx, plane = (long long)g.nx * g.ny;
-    if (r >= plane * g.nz) return;
-    const int k = (int)(r / plane), j = (int)((r - k * plane) / row), i = (int)(r - k * plane - j * row);
+    const long long row = g.nx + 2 * h, plane = row * (g.ny + 2 * h);
+    if (r >= plane * (g.nz + 2 * h)) return;
+    const int k = (int)(r / plane) - h, j = (int)((r % plane) / row) - h, i = (int)(r % row) - h;
     double* p = t.ptr[q] + gidx(g, i + NG, j + NG, k + NG);
     double* w = s + gidx(box, t.off[0][a] + i + NG, t.off[1][b] + j + NG, t.off[2][c] + k + NG);
 #pragma unroll 9
@@ -105,8 +111,9 @@ size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 bool level_ok(const grf_patch_level* L) {
     if (!L) return false;
     const grf_box& b = L->box;
-    if (b.ng != NG || b.bc != GRF_BC_PERIODIC || !(b.dx > 0.0)) return false;
-    if (b.nx < NG || b.ny < NG || b.nz < NG || b.pitch < (long long)b.nx + 2 * NG) return false;
+    if (b.ng != NG || (b.bc != GRF_BC_PERIODIC && b.bc != GRF_BC_FROZEN) || !(b.dx > 0.0)) return false;
+    if (b.nx < 1 || b.ny < 1 || b.nz < 1 || b.pitch < (long long)b.nx + 2 * NG) return false;
+    if (b.bc == GRF_BC_PERIODIC && (b.nx < NG || b.ny < NG || b.nz < NG)) return false;
     const int p[3] = {L->px, L->py, L->pz}, n[3] = {b.nx, b.ny, b.nz};
     for (int d = 0; d < 3; ++d)
         if (p[d] < 1 || p[d] > GRF_MAX_PATCHES_PER_AXIS || p[d] > n[d]) return false;
@@ -121,6 +128,7 @@ PatchTable table_of(const grf_patch_level* L, double* const* ptrs) {
     std::memset(&t, 0, sizeof(t));
     t.p[0] = L->px; t.p[1] = L->py; t.p[2] = L->pz;
     t.n[0] = L->box.nx; t.n[1] = L->box.ny; t.n[2] = L->box.nz;
+    t.periodic = L->box.bc == GRF_BC_PERIODIC;
     for (int d = 0; d < 3; ++d)
         for (int a = 0; a <= t.p[d]; ++a) t.off[d][a] = (int)((long long)a * t.n[d] / t.p[d]);
     if (ptrs)
@@ -209,10 +217,11 @@ int grf_patch_copy(const grf_patch_level* level, double* box_state, double* cons
     box.dx = B.dx;
     box.periodic = 1;
     box.reflect = 0;
+    const int h = direction == 0 ? 2 * NG : 0;
     long long most = 0;
     for (int q = 0; q < npatches(level); ++q) {
         const Geom g = geom_at(t, q);
-        const long long n = (long long)g.nx * g.ny * g.nz;
+        const long long n = (long long)(g.nx + h) * (g.ny + h) * (g.nz + h);
         if (n > most) most = n;
     }
     const dim3 grd((unsigned)((most + 255) / 256), (unsigned)npatches(level), 1);
@@ -283,6 +292,13 @@ int grf_patches_rk4(const grf_patch_level* level, const grf_params* params, doub
         e = cudaMemcpyAsync(dtiles, ht.data(), sizeof(TileDesc) * ht.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(base, 0, kAlign, st);
     if (e != cudaSuccess) return record_cuda_error(e);  // (pageable sources: staged before the calls return)
+    if (level->box.bc == GRF_BC_FROZEN)  // the stage buffers carry the ghosts outside the box
+        for (int q = 0; q < np && e == cudaSuccess; ++q) {
+            const size_t sb = patch_state_bytes(hb[q].g);
+            e = cudaMemcpyAsync(bufA[q], patches[q], sb, cudaMemcpyDeviceToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(bufB[q], patches[q], sb, cudaMemcpyDeviceToDevice, st);
+        }
+    if (e != cudaSuccess) return record_cuda_error(e);
 
     auto halo = [&](std::vector<double*>& bufs) -> int {
         return exchange ? exchange(exchange_ctx, level, bufs.data(), stream)

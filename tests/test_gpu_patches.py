@@ -1,4 +1,4 @@
-"""One periodic box evolved as patches with a halo exchange after every RK4 stage
+"""One box (periodic, or with frozen ghosts) evolved as patches with a halo exchange after every RK4 stage
 (grf_patches_rk4, grf_halo_exchange, grf_patch_copy) on the GPU.
 
 The exchange and the copies move values only, so they are checked bit for bit against the
@@ -70,6 +70,23 @@ def test_exchange_writes_the_periodic_images(g, n, p):
                 assert np.array_equal(g.to_host(patches[q], pb), periodic_block(whole, box, lo, m)), q
 
 
+@pytest.mark.parametrize("n,p", [((29, 22, 17), (3, 2, 2)), ((9, 8, 2), (3, 4, 2)), ((7, 5, 4), (1, 1, 1))])
+def test_exchange_in_a_frozen_box(g, n, p):
+    """Frozen box: each patch equals the block of the ghosted box it covers; ghosts inside the box
+    come from the neighbouring patches, those outside it are the box's own ghosts, left as copied."""
+    box = gi.Box(*n, 0.2, 0.0, 0.0, 0.0, bc=gi.BC_FROZEN)
+    s = np.random.default_rng(3).normal(size=box.shape)
+    L, patches = split(g, box, s, p)
+    ox, oy, oz = offsets(n[0], p[0]), offsets(n[1], p[1]), offsets(n[2], p[2])
+    for c in range(p[2]):
+        for b in range(p[1]):
+            for a in range(p[0]):
+                q = a + p[0] * (b + p[1] * c)
+                pb = g.grf_patch_box(L, q)
+                want = s[:, oz[c]:oz[c] + pb.nz + 6, oy[b]:oy[b] + pb.ny + 6, ox[a]:ox[a] + pb.nx + 6]
+                assert np.array_equal(g.to_host(patches[q], pb), want), q
+
+
 def test_patch_copy_round_trip(g):
     box = gi.Box(21, 13, 10, 0.2, 0.0, 0.0, 0.0)
     s = np.random.default_rng(2).normal(size=box.shape)
@@ -115,6 +132,16 @@ def test_patches_other_schemes_bit_for_bit(g, params):
     box = gi.Box(26, 19, 14, 0.3, -3.9, -2.85, -2.1)
     s = gi.random_perturbed_state(box, 5, base=gi.single_puncture(box, amp=0.05), eps=2e-2)
     ref, got = whole_and_patches(g, box, params, s, (2, 3, 2), 0.25 * box.dx, 2)
+    assert np.array_equal(got[:, 3:-3, 3:-3, 3:-3], ref[:, 3:-3, 3:-3, 3:-3])
+
+
+@pytest.mark.parametrize("p", [(2, 3, 2), (3, 1, 4), (1, 1, 1)])
+def test_patches_of_a_frozen_box_bit_for_bit(g, p):
+    """A box with frozen ghosts (single-puncture data in them): the patches on its faces keep
+    those ghosts through the stages, the inner faces are exchanged."""
+    box = gi.Box(26, 19, 14, 0.3, -3.9, -2.85, -2.1, bc=gi.BC_FROZEN)
+    s = gi.random_perturbed_state(box, 6, base=gi.single_puncture(box, amp=0.05), eps=2e-2)
+    ref, got = whole_and_patches(g, box, gi.Params(lam=0.1, g2=0.05, beta_kind=1), s, p, 0.25 * box.dx, 3)
     assert np.array_equal(got[:, 3:-3, 3:-3, 3:-3], ref[:, 3:-3, 3:-3, 3:-3])
 
 

@@ -46,7 +46,8 @@ def test_patch_level_validation(grf):
     out = grf.grf_box()
     bad = [grf.patch_level(box, 0, 1, 1), grf.patch_level(box, 17, 1, 1), grf.patch_level(box, 1, 1, 17),
            grf.patch_level(grf.make_box(4, 16, 16, 0.25), 5, 1, 1),                 # more patches than points
-           grf.patch_level(grf.make_box(16, 16, 16, 0.25, bc=grf.GRF_BC_FROZEN), 2, 2, 2),
+           grf.patch_level(grf.make_box(16, 16, 16, 0.25, bc=grf.GRF_BC_REFLECT_LOW), 2, 2, 2),
+           grf.patch_level(grf.make_box(16, 16, 16, 0.25, bc=grf.GRF_BC_SOMMERFELD), 2, 2, 2),
            grf.patch_level(grf.make_box(16, 16, 16, 0.25, ng=4), 2, 2, 2),
            grf.patch_level(grf.make_box(2, 16, 16, 0.25), 1, 1, 1),                 # periodic box below 3 points
            grf.patch_level(grf.make_box(16, 16, 16, 0.0), 2, 2, 2)]
@@ -56,6 +57,10 @@ def test_patch_level_validation(grf):
         assert lib.grf_patches_workspace_bytes(C.byref(L)) == 0
         ptrs = (C.c_void_p * 512)(*([256] * 512))
         assert lib.grf_halo_exchange(C.byref(L), ptrs, None) == grf.GRF_EINVAL
+    # a frozen box may be thinner than the ghost layers; a periodic one may not
+    thin = grf.patch_level(grf.make_box(2, 16, 1, 0.25, bc=grf.GRF_BC_FROZEN), 2, 4, 1)
+    assert lib.grf_patch_box(C.byref(thin), 7, C.byref(out)) == grf.GRF_OK and (out.nx, out.ny, out.nz) == (1, 4, 1)
+    assert lib.grf_patches_workspace_bytes(C.byref(thin)) > 0
     ok = grf.patch_level(box, 2, 2, 2)
     assert lib.grf_patch_box(C.byref(ok), 8, C.byref(out)) == grf.GRF_EINVAL       # index out of range
     assert lib.grf_patch_box(C.byref(ok), -1, C.byref(out)) == grf.GRF_EINVAL
