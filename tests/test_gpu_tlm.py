@@ -183,6 +183,27 @@ def test_tlm_gradient_matches_richardson_differences(g, tlm, k):
     assert abs(rich / grad[k] - 1.0) <= max(1e-10, floor), (k, grad[k], rich, floor)
 
 
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_tlm_gradient_matches_oracle_richardson_differences(orc, tlm, k):
+    """The oracle's own derivative of the same discrete evolution, taken by Richardson-extrapolated
+    central differences (truncation O(h^4)), against the GPU's forward-mode derivative: they agree
+    to the rounding floor of the oracle's difference quotient, or 1e-10 relative where that is
+    smaller. The two codes share no arithmetic, so this pins the tangent to the oracle well
+    below the 1e-5 of plain differences."""
+    L, grad = tlm
+    h = 1e-3 * max(abs(THETA[k]), 1e-2)
+
+    def central(hh):
+        tp = list(THETA); tm = list(THETA)
+        tp[k] += hh
+        tm[k] -= hh
+        return (oracle_signal(orc, tp) - oracle_signal(orc, tm)) / (2 * hh)
+
+    rich = (4.0 * central(h / 2) - central(h)) / 3.0
+    floor = 20 * np.finfo(float).eps * abs(L) / (h * abs(grad[k]))
+    assert abs(rich / grad[k] - 1.0) <= max(1e-10, floor), (k, grad[k], rich, floor)
+
+
 def test_tlm_exponential_coupling_gradients(g, orc):
     """The tangent evolution with the exponential coupling (exp of the dual numbers): the
     gradients in (lambda, g2, A) agree with central differences of the oracle's evolution."""
