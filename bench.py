@@ -567,6 +567,24 @@ def oracle_sample(cfg, seconds, steps=1):
     return n ** 3 * steps / el, cores, f"{steps} RK4 step(s) of a {n}^3 frozen-ghost sub-block of the workload ({el:.1f} s)"
 
 
+def oracle_single_core(args, seconds):
+    """The same oracle sample on one host core (a child process with OMP_NUM_THREADS=1, started
+    before this process touches CUDA). Returns {"value", "sample"} or None if it failed."""
+    code = ("import json, bench\n"
+            f"cfg = bench.workload({args.workload!r}, {args.order}, {args.advection!r}, {args.boundary!r})\n"
+            f"cfg['params'].decoupled = {1 if args.decoupled else 0}\n"
+            f"r = bench.oracle_sample(cfg, {float(seconds)})\n"
+            "print(json.dumps([r[0], r[2]]))\n")
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, cwd=ROOT, capture_output=True, text=True,
+                             timeout=20 * seconds + 60)
+        rate, desc = json.loads(out.stdout.strip().splitlines()[-1])
+    except (subprocess.SubprocessError, OSError, ValueError, IndexError):
+        return None
+    return {"value": rate, "cores": 1, "sample": desc}
+
+
 def run_reference(args, rank):
     cfg = workload(args.workload, args.order, args.advection, args.boundary)
     if rank != 0:
@@ -622,7 +640,8 @@ def run_ours(args, rank, world, local_rank):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, desc = oracle_sample(cfg, args.cpu_seconds)
-        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+               "single_core": oracle_single_core(args, max(2.0, args.cpu_seconds / 3))}
 
     torch.cuda.set_device(local_rank)
     dist = None
