@@ -36,12 +36,12 @@ UNIT = "point-updates/s"
 BYTES_PER_POINT_UPDATE = 216 * (3 + 5 + 5 + 4)
 # dram__bytes_read.sum + dram__bytes_write.sum of one stage launch per interior point, from the
 # ncu capture of the current stage kernel (profiles/); None when the kernel changed since.
-TRAFFIC_BYTES_PER_POINT_STAGE = 12619  # mean of stage 0 and 1, 96^3 capture (profiles/rk4_stage_kernel_bl_pair_96.md)
+TRAFFIC_BYTES_PER_POINT_STAGE = 12622  # mean of stage 0 and 1, 96^3 capture (profiles/rk4_stage_kernel_bl_pair_96.md)
 # the tangent-linear (dual-number) stage kernel (profiles/tlm_stage_kernel_sphere_signal_96.md)
-TLM_FP64_INSTR_PER_POINT_STAGE = 28537
+TLM_FP64_INSTR_PER_POINT_STAGE = 28826
 # the 6th-order stage kernel with centred advection (profiles/rk4_stage6_kernel_bl_pair_96.md, mean of stages 0, 1)
-FP64_INSTR_PER_POINT_STAGE_6 = 4835
-TRAFFIC_BYTES_PER_POINT_STAGE_6 = 11033
+FP64_INSTR_PER_POINT_STAGE_6 = 4823
+TRAFFIC_BYTES_PER_POINT_STAGE_6 = 10852
 # FP64 thread instructions (dadd + dmul + dfma) per interior point and stage, same capture; the
 # pipe issues 2 per SM per clock (152 SMs x 2 x 2.06 GHz = 6.26e11 / s, half the flop peak).
 FP64_INSTR_PER_POINT_STAGE = 4162
