@@ -115,6 +115,37 @@ def test_batched_graph_replay_and_oracle(g, orc):
     assert np.max(errs) < 1e-10, describe(errs)
 
 
+@pytest.mark.parametrize("name", ["amr_boxes_96", "coupling_sweep_32"])
+def test_full_size_batches_in_the_bench_launch(g, orc, name):
+    """The batched bench workloads at full size (96 AMR-like boxes, 6.27M points; 32 x 64^3), in
+    the launch the autotuner picks for them (graph of 32 x 4 x 1 tiles): after one step every box
+    equals, bit for bit, the box stepped alone by grf_rk4_step, and the smallest, a middle and the
+    largest box match one oracle step."""
+    import torch
+    import bench
+    boxes, params, pidx, dts = bench.batched_workload(name)
+    gb = [g.box_like(b) for b in boxes]
+    gp = g.params_array([g.params_like(p) for p in params])
+    init = [gi.single_puncture(b) for b in boxes]
+    dev = [g.to_device(s, b) for s, b in zip(init, gb)]
+    cfg = g.batch_config(g.GRF_BATCH_GRAPH, (32, 4, 1))
+    items = g.batch_items(gb, dev, pidx, dts)
+    g.grf_batched_rk4(items, gp, 1, cfg)
+    torch.cuda.synchronize()
+    for b2, s, d, pi, dt in zip(gb, init, dev, pidx, dts):
+        t = g.to_device(s, b2)
+        g.grf_rk4_step(b2, gp[pi], t, dt, 1)
+        n = 3 + b2.nx
+        assert torch.equal(t[:, 3:-3, 3:-3, 3:n], d[:, 3:-3, 3:-3, 3:n])
+    sizes = [b.npoints for b in boxes]
+    order = sorted(range(len(boxes)), key=lambda i: sizes[i])
+    for k in (order[0], order[len(order) // 2], order[-1]):
+        cpu = init[k].copy()
+        orc.rk4(boxes[k], params[pidx[k]], cpu, dts[k], 1)
+        errs = field_errors(g.to_host(dev[k], gb[k]), cpu, boxes[k])
+        assert np.max(errs) < 1e-11, (k, describe(errs))
+
+
 def test_persistent_barrier_timeout_is_reported_and_context_survives(g):
     """A grid barrier given a 1-cycle spin limit runs out (the other blocks have not arrived):
     the call returns GRF_ETIMEOUT instead of hanging, and the device stays usable."""

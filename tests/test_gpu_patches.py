@@ -145,6 +145,28 @@ def test_patches_of_a_frozen_box_bit_for_bit(g, p):
     assert np.array_equal(got[:, 3:-3, 3:-3, 3:-3], ref[:, 3:-3, 3:-3, 3:-3])
 
 
+def test_patches_256_bit_for_bit_at_full_size(g):
+    """The split-box bench workload at full size: the 256^3 Brill-Lindquist box as 2 x 2 x 2 patches
+    of 128^3, one step, against the whole box's step, bit for bit (compared on the device)."""
+    import torch
+    cfg = gi.config_bl_pair_256()
+    box, params, dt = cfg["box"], cfg["params"], cfg["dt"]
+    b, p = g.box_like(box), g.params_like(params)
+    whole = g.to_device(cfg["make_state"](), b)
+    level = g.patch_level(b, 2, 2, 2)
+    patches = g.patch_states(level)
+    g.grf_patch_copy(level, whole, patches, 0)
+    g.grf_patches_rk4(level, p, patches, dt, 1)
+    g.grf_rk4_step(b, p, whole, dt, 1)
+    out = torch.zeros_like(whole)
+    g.grf_patch_copy(level, out, patches, 1)
+    torch.cuda.synchronize()
+    n = 3 + box.nx
+    assert torch.equal(out[:, 3:-3, 3:-3, 3:n], whole[:, 3:-3, 3:-3, 3:n])
+    del patches, out, whole
+    torch.cuda.empty_cache()
+
+
 def test_patches_parity_with_the_oracle(g, orc):
     box = gi.Box(24, 20, 18, 0.3, -3.6, -3.0, -2.7)
     params = gi.Params(lam=0.1, g2=0.05, beta_kind=1)
