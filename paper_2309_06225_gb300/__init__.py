@@ -414,11 +414,24 @@ def grf_patches_rk4(level: grf_patch_level, params: grf_params, patches, dt, nst
     contract (it may call the library, e.g. lib().grf_halo_exchange)."""
     if ws is None:
         ws = alloc_workspace(grf_patches_workspace_bytes(level))
-    fn = C.cast(None, grf_halo_fn) if exchange is None else grf_halo_fn(lambda ctx, lv, ptrs, st: int(exchange(lv, ptrs, st)))
+    raised = []
+
+    def call(ctx, lv, ptrs, st):
+        # an exception cannot cross the C frames: it ends the step with GRF_EINVAL and is
+        # raised again once the call has returned
+        try:
+            return int(exchange(lv, ptrs, st))
+        except BaseException as e:  # noqa: BLE001
+            raised.append(e)
+            return GRF_EINVAL
+
+    fn = C.cast(None, grf_halo_fn) if exchange is None else grf_halo_fn(call)
     status = C.c_int(0)
     code = lib().grf_patches_rk4(C.byref(level), C.byref(params), _ptr_array(patches), float(dt), int(nsteps), fn,
                                  None, _dev(ws), ws.numel(), C.byref(status) if sync_status else None,
                                  _stream(stream))
+    if raised:
+        raise raised[0]
     return _check(code, "grf_patches_rk4")
 
 

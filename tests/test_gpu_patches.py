@@ -223,3 +223,19 @@ def test_failing_exchange_ends_the_step(g):
     torch.cuda.synchronize()  # the context is still usable
     g.grf_halo_exchange(L, patches)
     torch.cuda.synchronize()
+
+
+def test_exchange_that_raises(g):
+    """A Python exchange that raises ends the step after the stage in flight, and the exception
+    reaches the caller."""
+    cfg = gi.config_single_puncture_32()
+    box, params, dt = cfg["box"], cfg["params"], cfg["dt"]
+    L, patches = split(g, box, cfg["make_state"](), (1, 2, 2))
+
+    def exchange(level, ptrs, stream):
+        raise KeyError("peer lost")
+
+    with pytest.raises(KeyError):
+        g.grf_patches_rk4(L, g.params_like(params), patches, dt, 1, exchange=exchange)
+    import torch
+    torch.cuda.synchronize()
