@@ -333,6 +333,21 @@ int grf_patches_rk4(const grf_patch_level* level, const grf_params* params, doub
                     int nsteps, grf_halo_fn exchange, void* exchange_ctx, void* ws, size_t ws_bytes, int* status_host,
                     grf_stream_t stream);
 
+/* Scratch bytes for grf_patches_constraints (the largest patch's grf_constraints scratch); 0 for a
+ * bad level. */
+size_t grf_patches_constraints_workspace_bytes(const grf_patch_level* level);
+
+/* The constraints of the whole box from its patches (the patches' ghosts as the last exchange left
+ * them): grf_constraints on every patch, writing its H, M1, M2, M3 into out4[q] (host array of
+ * px py pz device pointers, 4 fields each in the patch's layout), and, when norms_host is given,
+ * the 8 norms of grf_constraints over the whole box's interior, combined on the host from the
+ * patches' sums of squares and maxima (the one reduction of a few scalars that a run over several
+ * devices would all-reduce). The per-point values equal grf_constraints on the whole box bit for
+ * bit; the L2 norms differ from it by the order of summation only. Synchronises `stream` when
+ * norms_host is given. Errors as grf_constraints, GRF_EINVAL for a bad level or pointer array. */
+int grf_patches_constraints(const grf_patch_level* level, const grf_params* params, double* const* patches,
+                            double* const* out4, double* norms_host, void* ws, size_t ws_bytes, grf_stream_t stream);
+
 /* ---------------------------------------------------------------------------------------
  * Differentiation of an extracted scalar signal (the paper extracts scalar waveforms on
  * spheres, section "Key features": Diagnostics). The signal is

@@ -128,7 +128,11 @@ def lib():
         L.grf_patches_workspace_bytes.restype = C.c_size_t
         L.grf_patches_rk4.argtypes = [PL, P, PP, C.c_double, C.c_int, grf_halo_fn, _VP, _VP, C.c_size_t,
                                       C.POINTER(C.c_int), _VP]
-        for name in ("grf_patch_box", "grf_patch_copy", "grf_halo_exchange", "grf_patches_rk4"):
+        L.grf_patches_constraints_workspace_bytes.argtypes = [PL]
+        L.grf_patches_constraints_workspace_bytes.restype = C.c_size_t
+        L.grf_patches_constraints.argtypes = [PL, P, PP, PP, C.POINTER(C.c_double), _VP, C.c_size_t, _VP]
+        for name in ("grf_patch_box", "grf_patch_copy", "grf_halo_exchange", "grf_patches_rk4",
+                     "grf_patches_constraints"):
             getattr(L, name).restype = C.c_int
         L.grf_error_string.argtypes = [C.c_int]
         L.grf_error_string.restype = C.c_char_p
@@ -433,6 +437,17 @@ def grf_patches_rk4(level: grf_patch_level, params: grf_params, patches, dt, nst
     if raised:
         raise raised[0]
     return _check(code, "grf_patches_rk4")
+
+
+def grf_patches_constraints(level: grf_patch_level, params: grf_params, patches, out4, ws=None, stream=None):
+    """H, M_i of every patch into out4 (one 4-field tensor per patch); returns the whole box's 8 norms
+    (L2 and max of H, M1, M2, M3)."""
+    if ws is None:
+        ws = alloc_workspace(lib().grf_patches_constraints_workspace_bytes(C.byref(level)))
+    norms = (C.c_double * 8)()
+    _check(lib().grf_patches_constraints(C.byref(level), C.byref(params), _ptr_array(patches), _ptr_array(out4),
+                                         norms, _dev(ws), ws.numel(), _stream(stream)), "grf_patches_constraints")
+    return np.array(norms[:])
 
 
 def grf_rk4_step_noalloc(box: grf_box, params: grf_params, state, dt, nsteps, stream=None):

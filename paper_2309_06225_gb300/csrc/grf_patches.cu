@@ -7,6 +7,7 @@
 // that owns the point in the box (periodic: every ghost point; frozen: the ghost points inside the
 // box, the others keep the caller's values). The stage arithmetic per point is that of grf_rk4_step
 // and its inputs are the same values, so the results are the same bits.
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -324,6 +325,46 @@ int grf_patches_rk4(const grf_patch_level* level, const grf_params* params, doub
         if (e != cudaSuccess) return record_cuda_error(e);
         if (*status_host & 1) return GRF_ESINGULAR;
     }
+    return GRF_OK;
+}
+
+size_t grf_patches_constraints_workspace_bytes(const grf_patch_level* level) {
+    if (!level_ok(level)) return 0;
+    size_t most = 0;
+    for (int q = 0; q < npatches(level); ++q) {
+        grf_box pb;
+        grf_patch_box(level, q, &pb);
+        const size_t n = grf_workspace_bytes(&pb, GRF_OP_CONSTRAINTS);
+        if (n > most) most = n;
+    }
+    return most;
+}
+
+int grf_patches_constraints(const grf_patch_level* level, const grf_params* params, double* const* patches,
+                            double* const* out4, double* norms_host, void* ws, size_t ws_bytes, grf_stream_t stream) {
+    if (!level_ok(level) || !params || !ptrs_ok(level, patches) || !ptrs_ok(level, out4)) return GRF_EINVAL;
+    double sq[4] = {0, 0, 0, 0}, mx[4] = {0, 0, 0, 0};
+    long long total = 0;
+    for (int q = 0; q < npatches(level); ++q) {
+        grf_box pb;
+        grf_patch_box(level, q, &pb);
+        double n8[8];
+        const int r = grf_constraints(&pb, params, patches[q], out4[q], norms_host ? n8 : nullptr, ws, ws_bytes,
+                                      stream);
+        if (r) return r;
+        if (!norms_host) continue;
+        const long long n = (long long)pb.nx * pb.ny * pb.nz;
+        for (int m = 0; m < 4; ++m) {
+            sq[m] += n8[2 * m] * n8[2 * m] * (double)n;  // the patch's sum of squares
+            mx[m] = n8[2 * m + 1] > mx[m] ? n8[2 * m + 1] : mx[m];
+        }
+        total += n;
+    }
+    if (norms_host)
+        for (int m = 0; m < 4; ++m) {
+            norms_host[2 * m] = std::sqrt(sq[m] / (double)total);
+            norms_host[2 * m + 1] = mx[m];
+        }
     return GRF_OK;
 }
 

@@ -167,6 +167,35 @@ def test_patches_256_bit_for_bit_at_full_size(g):
     torch.cuda.empty_cache()
 
 
+@pytest.mark.parametrize("bc", [gi.BC_PERIODIC, gi.BC_FROZEN])
+def test_constraints_over_patches(g, bc):
+    """H and M_i of every patch equal the whole box's at the same points, bit for bit; the norms
+    combined from the patches equal the whole box's (maxima exactly, L2 to the summation order)."""
+    box = gi.Box(26, 19, 14, 0.3, -3.9, -2.85, -2.1, bc=bc)
+    s = gi.random_perturbed_state(box, 7, base=gi.single_puncture(box, amp=0.05), eps=1e-2)
+    params = g.params_like(gi.Params(lam=0.1, g2=0.05, beta_kind=1))
+    b = g.box_like(box)
+    whole = g.to_device(s, b)
+    out_w = g.alloc_state(b, 4)
+    nw = g.grf_constraints(b, params, whole, out_w)
+    p = (2, 3, 2)
+    L, patches = split(g, box, s, p)
+    outs = [g.alloc_state(g.grf_patch_box(L, q), 4) for q in range(len(patches))]
+    npch = g.grf_patches_constraints(L, params, patches, outs)
+    ox, oy, oz = offsets(box.nx, p[0]), offsets(box.ny, p[1]), offsets(box.nz, p[2])
+    w = g.to_host(out_w, b)
+    for c in range(p[2]):
+        for bb in range(p[1]):
+            for a in range(p[0]):
+                q = a + p[0] * (bb + p[1] * c)
+                pb = g.grf_patch_box(L, q)
+                got = g.to_host(outs[q], pb)[:, 3:-3, 3:-3, 3:-3]
+                want = w[:, 3 + oz[c]:3 + oz[c] + pb.nz, 3 + oy[bb]:3 + oy[bb] + pb.ny, 3 + ox[a]:3 + ox[a] + pb.nx]
+                assert np.array_equal(got, want), q
+    assert np.array_equal(npch[1::2], nw[1::2])
+    np.testing.assert_allclose(npch[0::2], nw[0::2], rtol=1e-13, atol=0)
+
+
 def test_patches_parity_with_the_oracle(g, orc):
     box = gi.Box(24, 20, 18, 0.3, -3.6, -3.0, -2.7)
     params = gi.Params(lam=0.1, g2=0.05, beta_kind=1)

@@ -57,6 +57,7 @@ def test_patch_level_validation(grf):
         assert lib.grf_patches_workspace_bytes(C.byref(L)) == 0
         ptrs = (C.c_void_p * 512)(*([256] * 512))
         assert lib.grf_halo_exchange(C.byref(L), ptrs, None) == grf.GRF_EINVAL
+        assert lib.grf_patches_constraints_workspace_bytes(C.byref(L)) == 0
     # a frozen box may be thinner than the ghost layers; a periodic one may not
     thin = grf.patch_level(grf.make_box(2, 16, 1, 0.25, bc=grf.GRF_BC_FROZEN), 2, 4, 1)
     assert lib.grf_patch_box(C.byref(thin), 7, C.byref(out)) == grf.GRF_OK and (out.nx, out.ny, out.nz) == (1, 4, 1)
@@ -71,6 +72,12 @@ def test_patch_level_validation(grf):
     assert lib.grf_halo_exchange(C.byref(ok), None, None) == grf.GRF_EINVAL
     assert lib.grf_patch_copy(C.byref(ok), C.c_void_p(256), ptrs, 2, None) == grf.GRF_EINVAL
     assert lib.grf_patch_copy(C.byref(ok), None, ptrs, 0, None) == grf.GRF_EINVAL
+    p = grf.grf_params()
+    assert lib.grf_patches_constraints(C.byref(ok), C.byref(p), ptrs, ptrs_null, None, None, 0, None) == grf.GRF_EINVAL
+    assert lib.grf_patches_constraints(C.byref(ok), None, ptrs, ptrs, None, None, 0, None) == grf.GRF_EINVAL
+    # the largest patch's constraint scratch
+    assert lib.grf_patches_constraints_workspace_bytes(C.byref(ok)) == \
+        grf.grf_workspace_bytes(grf.grf_patch_box(ok, 0), grf.GRF_OP_CONSTRAINTS)
 
 
 def test_patches_rk4_rejects_before_any_cuda_call(grf):
