@@ -67,7 +67,8 @@ enum { GRF_OP_RHS = 0, GRF_OP_RK4 = 1, GRF_OP_CONSTRAINTS = 2 };
  *           sigma/(64 dx) sum_d Delta^6_d, lopsided advection on offsets -1..3;
  *   ng = 4: centred 6th-order differences, dissipation -sigma/(256 dx) sum_d Delta^8_d,
  *           lopsided advection on offsets -2..4.
- * 4-ghost boxes are accepted by every call but grf_batched_rk4 and grf_tlm_rk4. */
+ * 4-ghost boxes are accepted by every call but grf_batched_rk4, grf_tlm_rk4 and the split-box
+ * calls (grf_patch_level). */
 typedef struct {
     int nx, ny, nz;       /* interior points per axis, each >= 1 (periodic, mirror: >= ng) */
     int ng;               /* ghost layers: 3 or 4 (above) */
@@ -79,7 +80,7 @@ typedef struct {
                              cell below the first point; "Boundary Conditions", reflective),
                              their ghosts rebuilt from the interior with each component's
                              parity; ghosts on the high faces are read as given. Needs n >= ng.
-                             Not accepted by grf_batched_rk4 and grf_tlm_rk4.
+                             Not accepted by grf_batched_rk4, grf_tlm_rk4 and the split-box calls.
                            GRF_BC_EXTRAPOLATE ("Boundary Conditions", extrapolating): every ghost
                              is refilled before each right-hand side by linear extrapolation along
                              one axis, u(last + m) = u(last) + m (u(last) - u(last - 1)), axis by
@@ -103,7 +104,7 @@ typedef struct {
                              a coordinate below the box is a mirror image, refilled after each
                              stage. Needs n >= ng.
                            Extrapolating and Sommerfeld boxes (also behind mirror planes) are not
-                             accepted by grf_batched_rk4 and grf_tlm_rk4. */
+                             accepted by grf_batched_rk4, grf_tlm_rk4 and the split-box calls. */
     long long pitch;      /* doubles per x row, >= nx + 2 ng */
 } grf_box;
 
