@@ -52,7 +52,7 @@ def split(g, box, s, p):
 
 
 @pytest.mark.parametrize("n,p", [((29, 22, 17), (3, 2, 2)), ((16, 16, 16), (1, 1, 1)), ((9, 8, 12), (3, 4, 4)),
-                                 ((40, 6, 6), (16, 2, 1))])
+                                 ((40, 6, 6), (16, 2, 1)), ((16, 16, 5), (16, 16, 1)), ((3, 3, 3), (3, 3, 3))])
 def test_exchange_writes_the_periodic_images(g, n, p):
     """Every patch, ghosts included, equals the block of the periodic box it stands for (patches
     narrower than the 3 ghost layers read their ghosts from patches two or more away)."""
@@ -113,10 +113,11 @@ def whole_and_patches(g, box, params, s, p, dt, nsteps, exchange=None):
     return ref, g.to_host(out, b)
 
 
-@pytest.mark.parametrize("p", [(2, 2, 2), (1, 1, 1), (4, 1, 3), (3, 2, 5)])
+@pytest.mark.parametrize("p", [(2, 2, 2), (1, 1, 1), (4, 1, 3), (3, 2, 5), (16, 1, 1), (8, 16, 2)])
 def test_patches_equal_the_whole_box_bit_for_bit(g, p):
     """32^3 single puncture: 32-wide patches take the block gather, 16- and 8-wide ones the folded
-    per-thread gather, ragged ones (10 / 11 points) partial rows."""
+    per-thread gather, ragged ones (10 / 11 points) partial rows; patches of 2 points along an axis
+    read their ghosts from patches up to two away; 256 patches is the most a level takes."""
     cfg = gi.config_single_puncture_32()
     box, params, dt = cfg["box"], cfg["params"], cfg["dt"]
     s = cfg["make_state"]()
