@@ -85,6 +85,35 @@ def kerr_schild_fields(M=1.0):
     return fields, X
 
 
+def tt_plane_wave_point(direction, amp_a, amp_b, k, X0):
+    """A transverse-traceless gravitational plane wave along x on flat space at t = 0:
+    gamma = delta + h, h_yy = -h_zz = a(u), h_yz = b(u), u = t - x (outgoing for x > 0) or
+    u = t + x (ingoing), a = amp_a sin(k u), b = amp_b sin(k u + 0.3); unit lapse, zero shift,
+    K_ij = -d_t gamma_ij / 2, in the 27 conformal variables (Theta = 0, Gamma-hat from h)."""
+    t, x, y, z = symbols()
+    X = (x, y, z)
+    u = t - direction * x
+    a = amp_a * sp.sin(k * u)
+    b = amp_b * sp.sin(k * u + sp.Rational(3, 10))
+    g4 = sp.Matrix([[1, 0, 0], [0, 1 + a, b], [0, b, 1 - a]])
+    Kt = -sp.Rational(1, 2) * sp.diff(g4, t)
+    g = g4.subs(t, 0)
+    K = Kt.subs(t, 0)
+    gi = g.inv()
+    chi = g.det() ** sp.Rational(-1, 3)
+    Ktr = sum(gi[i, j] * K[i, j] for i in range(3) for j in range(3))
+    h = chi * g
+    A = chi * (K - g * Ktr / 3)
+    hi = gi / chi
+    Gt1 = christoffel_first(h, X)
+    Gam = [sum(hi[j, kk] * sum(hi[i, l] * Gt1[l][j][kk] for l in range(3)) for j in range(3) for kk in range(3))
+           for i in range(3)]
+    fields = [chi] + [h[i, j] for i, j in SYM_PAIRS] + [Ktr] + [A[i, j] for i, j in SYM_PAIRS] + [0] \
+        + Gam + [1, 0, 0, 0, 0, 0, 0, 0, 0]
+    ddot = lambda e: float(sp.diff(e, t, 2).subs({t: 0, x: X0}))
+    return conformal_point(fields, (X0, 0.0, 0.0), X), ddot(a), ddot(b)
+
+
 def isotropic_schwarzschild_fields(M=1.0, lapse="precollapsed", phi_amp=0.0):
     """Schwarzschild puncture data (time-symmetric slice, isotropic radius) with a chosen lapse."""
     t, x, y, z = symbols()

@@ -72,6 +72,24 @@ def test_kernel_psi4_matches_oracle(orc, flops, seed):
     assert abs(got - ref) < 1e-11 * max(1.0, abs(ref)), (got, ref)
 
 
+def test_kernel_psi4_of_an_outgoing_plane_wave(flops):
+    """The kernel's Psi_4 on a weak outgoing gravitational plane wave along x, at (X0, 0, 0):
+    a'' - i b'' (the standard -(h+'' - i hx'') in the triad (x, -z, y)); zero to first order for
+    the ingoing wave."""
+    pytest.importorskip("sympy")
+    import analytic as an
+    import paper_2309_06225_gb300 as grf
+    amp, k, X0 = 1e-6, 0.9, 2.3
+    p = grf.params_like(gi.Params(lam=0.0, g2=0.0))
+    for direction in (+1, -1):
+        (v, d1, d2), add, bdd = an.tt_plane_wave_point(direction, amp, 0.7 * amp, k, X0)
+        s1, s2 = slots(d1, d2)
+        got, st = flops.host_point_psi4(p, v, s1, s2, np.array([X0, 0.0, 0.0]))
+        assert st == 0
+        want = add - 1j * bdd if direction > 0 else 0.0
+        assert abs(got - want) < 1e-5 * abs(add - 1j * bdd), (direction, got, want)
+
+
 def test_operation_count_is_stable(flops):
     """The per-point FP64 operation count of the kernels (the roofline numerator) is a fixed
     property of the formulation: independent of the point data."""

@@ -1116,3 +1116,22 @@ def test_scalar_plane_wave_converges_4th_order(orc):
         errs.append(np.max(np.abs(b.interior(s)[25] - b.interior(ex)[25])) / amp)
     assert errs[1] < 1e-3
     assert 13 < errs[0] / errs[1] < 19, errs
+
+
+def test_psi4_of_an_outgoing_plane_wave(orc):
+    """For a weak outgoing wave the Weyl scalar is Psi_4 = -(h+'' - i hx''), with h+ = h_theta theta
+    and hx = h_theta phi in the triad about the origin (the standard relation between Psi_4 and
+    the wave's strain). At (X0, 0, 0) the triad is (x, -z, y), so h+ = -a, hx = -b and
+    Psi_4 = a'' - i b''. An ingoing wave gives Psi_4 = 0 to first order (it is carried by Psi_0):
+    this fixes the choice of the ingoing null vector n, the normalisation of the tetrad and the sign
+    of the imaginary part against physics rather than against a second code's definition."""
+    amp, k, X0 = 1e-6, 0.9, 2.3
+    p = P(lam=0.0, g2=0.0)
+    (v, d1, d2), add, bdd = an.tt_plane_wave_point(+1, amp, 0.7 * amp, k, X0)
+    got = orc.point_psi4(p, v, d1, d2, np.array([X0, 0.0, 0.0]))
+    want = add - 1j * bdd
+    assert abs(want) > 0.3 * amp * k * k
+    assert abs(got - want) < 1e-5 * abs(want), (got, want)
+    (v, d1, d2), add, bdd = an.tt_plane_wave_point(-1, amp, 0.7 * amp, k, X0)
+    got = orc.point_psi4(p, v, d1, d2, np.array([X0, 0.0, 0.0]))
+    assert abs(got) < 1e-5 * abs(add - 1j * bdd), got
