@@ -1241,3 +1241,66 @@ def test_gauge_wave_of_the_modified_puncture_gauge(orc, a0):
         errs.append(max(np.max(np.abs(b.interior(s)[f] - b.interior(ex)[f])) / sc for f, sc in zip(fields, scale)))
     assert errs[1] < 1e-3, errs
     assert 13 < errs[0] / errs[1] < 19, errs
+
+
+def _gamma_driver_wave_state(b, eps, k, t, a, F, eta):
+    """The exact linear longitudinal gauge mode of the modified puncture gauge with the
+    Gamma-driver on: alpha = 1 + A sin(kx), K = K_xx = Kh sin(kx), beta^x = Bs cos(kx),
+    B^x = Bb cos(kx), gamma_xx = 1 + G sin(kx), Gamma-hat^x = (2/3) k G cos(kx), with the amplitudes
+    y = (A, Kh, Bs, Bb, G) solving y' = M y (the linearised slicing, K, shift, B and metric
+    equations below), y(0) = (eps, 0, 0, 0, 0), by the matrix exponential:
+      A' = -2 Kh / (1 + a);  Kh' = k^2 A;  Bs' = F Bb / (1 + a) - (a / (1 + a)) k A;
+      G' = -2 Kh - 2 k Bs;   Bb' = (Gamma-hat amplitude)' - eta Bb, (2/3) k G' = -(4/3) k Kh - (4/3) k^2 Bs."""
+    from scipy.linalg import expm
+    M = np.zeros((5, 5))
+    M[0, 1] = -2.0 / (1.0 + a)
+    M[1, 0] = k * k
+    M[2, 3] = F / (1.0 + a)
+    M[2, 0] = -(a / (1.0 + a)) * k
+    M[4, 1] = -2.0
+    M[4, 2] = -2.0 * k
+    M[3, :] = (2.0 / 3.0) * k * M[4, :]
+    M[3, 3] -= eta
+    A, Kh, Bs, Bb, G = expm(M * t) @ np.array([eps, 0.0, 0.0, 0.0, 0.0])
+    s = gi.flat_state(b)
+    X, _, _ = b.coords()
+    sx, cx = np.sin(k * X), np.cos(k * X)
+    gxx = 1.0 + G * sx
+    chi = gxx ** (-1.0 / 3.0)
+    Ktr = Kh * sx
+    s[0] = chi
+    s[1], s[4], s[6] = gxx ** (2.0 / 3.0), chi, chi
+    s[7] = Ktr
+    s[8], s[11], s[13] = chi * (Ktr - gxx * Ktr / 3.0), -chi * Ktr / 3.0, -chi * Ktr / 3.0
+    s[15] = (2.0 / 3.0) * k * G * cx
+    s[18] = 1.0 + A * sx
+    s[19] = Bs * cx
+    s[22] = Bb * cx
+    return s
+
+
+def test_gamma_driver_gauge_wave(orc):
+    """The same flat-space gauge perturbation with the Gamma-driver on (F = 0.75, eta = 1) and the
+    modified gauge's a = 0.2: the lapse, K, the metric, Gamma-hat, the shift and B converge at 4th
+    order to the exact linear mode, the matrix exponential of the linearised gauge system. Fixes
+    the Gamma-driver as read: F / (1 + a) on B, d_t B = d_t Gamma-hat - eta B, and the shift's second
+    derivatives in the Gamma-hat equation."""
+    eps, L, T = 1e-6, 2.0, 0.6
+    k = 2 * math.pi / L
+    a, F, eta = 0.2, 0.75, 1.0
+    p = gi.Params(lam=0.0, g2=0.0, shift_F=F, eta=eta, a0=a, b0=0.4)
+    errs = []
+    for n in (16, 32):
+        b = gi.Box(n, 4, 4, L / n, 0.5 * L / n, 0.0, 0.0)
+        s = _gamma_driver_wave_state(b, eps, k, 0.0, a, F, eta)
+        dt = 0.25 * b.dx
+        nsteps = int(round(T / dt))
+        orc.rk4(b, p, s, dt, nsteps)
+        ex = _gamma_driver_wave_state(b, eps, k, nsteps * dt, a, F, eta)
+        moved = np.max(np.abs(b.interior(ex)[19])) / eps
+        fields = [18, 7, 1, 15, 19, 22]
+        scale = [eps, eps * k, eps, eps * k, eps, eps * k]
+        errs.append(max(np.max(np.abs(b.interior(s)[f] - b.interior(ex)[f])) / sc for f, sc in zip(fields, scale)))
+    assert moved > 0.05  # the shift is driven to a sizeable fraction of the lapse perturbation
+    assert errs[1] < 1e-3, errs
+    assert 13 < errs[0] / errs[1] < 19, errs
