@@ -1213,3 +1213,25 @@ def test_gamma_driver_gauge_wave(orc):
     assert moved > 0.05  # the shift is driven to a sizeable fraction of the lapse perturbation
     assert errs[1] < 1e-3, errs
     assert 13 < errs[0] / errs[1] < 19, errs
+
+
+def test_gravitational_plane_wave_converges_6th_order_on_4_ghost_boxes(orc):
+    """The same gravitational wave on 4-ghost boxes (6th-order differences, Delta^8 dissipation)
+    with a time step small enough (dx / 16) that RK4's error stays below the spatial one: from 8 to
+    16 points per wavelength the error falls by ~64 (measured 61), against ~16 on 3-ghost boxes.
+    Catches a 6th-order stencil that is only 4th-order accurate in the metric sector."""
+    amp, L, T = 1e-8, 2.0, 0.5
+    k = 2 * math.pi / L
+    errs = []
+    for n in (8, 16):
+        b = gi.Box(n, 4, 4, L / n, 0.5 * L / n, 0.0, 0.0, ng=4)
+        s = waves.tt_wave_state(b, amp, k, 0.0)
+        dt = b.dx / 16
+        nsteps = int(round(T / dt))
+        orc.rk4(b, gi.Params(lam=0.0, g2=0.0), s, dt, nsteps)
+        ex = waves.tt_wave_state(b, amp, k, nsteps * dt)
+        fields = [4, 5, 6, 11, 12, 13]
+        scale = [amp, amp, amp, amp * k, amp * k, amp * k]
+        errs.append(max(np.max(np.abs(b.interior(s)[f] - b.interior(ex)[f])) / sc for f, sc in zip(fields, scale)))
+    assert errs[1] < 1e-5, errs
+    assert 45 < errs[0] / errs[1] < 80, errs
