@@ -7,8 +7,8 @@
 // What it computes (GRFolres, arXiv:2309.06225, section "Key features": modified moving
 // puncture gauge, 4dST theory, 4th-order Runge-Kutta with 4th-order finite differences,
 // periodic boundaries, constraint monitoring). The paper prints no equations; the ones
-// followed here are the published modified-CCZ4 / 4dST equations as stated (with every
-// reading listed) in the project design notes:
+// followed here are the modified-CCZ4 / 4dST equations of the works it cites, written out
+// below and in the functions that evaluate them:
 //   * fields: chi, h_ij, K, A_ij, Theta, Gamma^i, lapse, shift^i, B^i, phi, Pi (27 doubles)
 //   * derivatives ("Accuracy": 4th and 6th order): the box's ghost width chooses the scheme,
 //     ng = 3 -> centred 4th-order first, second and mixed differences, ng = 4 -> 6th order
@@ -36,10 +36,19 @@
 //     Nyquist mode at sigma/dx per direction)
 //   * classical RK4 with post-stage algebraic enforcement (trace-free A, chi and lapse floors)
 //
-// Parity unpinned (no pin fixes these terms independently of the equations as read; they vanish
-// or reduce to their pinned limits on the pinned data): the modified-gauge a/b terms beyond
-// a = b = 0 and their vanishing on constraint-satisfying data, the 1+log / Gamma-driver gauge
-// coefficients, and the Theta damping term of the K equation.
+//   * the CCZ4 equations (K, A_ij, Theta, Gamma-hat) are the 3+1 projection of the covariant
+//     damped Z4 system of the modified gauge,
+//        G^ab + 2 Phat_c^{d ab} nabla_d Z^c - kappa1 [2 n^(a Z^b) + kappa2 (n.Z) g^ab] = 8 pi T^ab,
+//        Phat_c^{d ab} = delta_c^(a gh^b)d - 1/2 delta_c^d gh^ab,   gh^ab = g^ab - b(x) n^a n^b,
+//     with Theta = -n.Z and Gamma-hat^i = Gamma-tilde^i + 2 h^ij Z_j. The auxiliary metric gh
+//     multiplies the time-derivative terms of the nn and ni components by (1 + b); solving for
+//     them gives the b(x) terms of d_t K, d_t Theta and d_t Gamma-hat written in ccz4_rhs. The
+//     other auxiliary metric, with a(x), enters only the lapse and shift conditions.
+//
+// Parity unpinned (no pin fixes these independently of the equations as read): the functional
+// forms a(x) = a0, b(x) = b0 (constants) and the 1+log / Gamma-driver gauge coefficients. The
+// gauge conditions' form is pinned by the linearised gauge waves; the b(x) terms and the damping
+// terms by the covariant Z4 projection above (tests/test_oracle_pins.py).
 //
 // Plain loops, no blocking, FP64 (long double only inside the linear solve).
 // Build: g++ -O2 -ffp-contract=off -fopenmp -shared -fPIC (see oracle/build.py).
@@ -436,7 +445,7 @@ struct Conf {
     double adv[NF];  // advection terms beta^k d_k u of every field
     // derived
     double hi[3][3], dh[3][3][3], Gt[3][3][3], Gtc[3], dGtc[3][3];  // Gt[k][i][j], dGtc[m][k]
-    double Zl[3], Zu[3], RZ[3][3], RZs, Ric[3][3], Rs, Au[3][3], Aud[3][3], AA, DDa[3][3], DDa_tr, divb;
+    double Zl[3], Zu[3], RZ[3][3], RZs, divZ, Ric[3][3], Rs, Au[3][3], Aud[3][3], AA, DDa[3][3], DDa_tr, divb;
     double Kphys[3][3];
     Phys p;
     Geo G;
@@ -582,7 +591,9 @@ void conf_setup(const double* v, const double* d1, const double* d2, const doubl
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) c.RZ[i][j] = c.Ric[i][j] + DZ[i][j] + DZ[j][i];
     c.RZs = 0;
-    for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) c.RZs += c.G.gi[i][j] * c.RZ[i][j];
+    c.divZ = 0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) { c.RZs += c.G.gi[i][j] * c.RZ[i][j]; c.divZ += c.G.gi[i][j] * DZ[i][j]; }
     for (int i = 0; i < 3; ++i) {
         double s = 0;
         for (int j = 0; j < 3; ++j) s += c.G.gi[i][j] * c.Zl[j];
@@ -623,9 +634,11 @@ void ccz4_rhs(const orc_params& P, const Conf& c, const Src& s, double* rhs) {
             for (int k = 0; k < 3; ++k) x += c.h[i][k] * db(j, k) + c.h[j][k] * db(i, k);
             rhs[F_H + SYM[i][j]] = x;
         }
+    // The modified gauge's b(x) enters through the auxiliary metric of the Z terms (see the header):
+    // Hb = H - 16 pi rho - 2 kappa1 (2 + kappa2) Theta, with the plain H = R + K^2 - K_ij K^ij.
+    const double Hb = c.Rs - c.AA + (2.0 / 3.0) * K * K - 2.0 * s.rho8 - 2.0 * P.kappa1 * (2.0 + P.kappa2) * Th;
     rhs[F_K] = adv(F_K) + al * (c.RZs + K * (K - 2.0 * Th)) - 3.0 * al * P.kappa1 * (1.0 + P.kappa2) * Th
-               - c.DDa_tr + 0.5 * al * (S8tr - 3.0 * s.rho8)
-               - (3.0 * al * b / (4.0 * (1.0 + b))) * (c.Rs - c.AA + (2.0 / 3.0) * K * K - 2.0 * s.rho8);
+               - c.DDa_tr + 0.5 * al * (S8tr - 3.0 * s.rho8) - (3.0 * al * b / (4.0 * (1.0 + b))) * Hb;
     {
         double X[3][3], trX = 0;
         for (int i = 0; i < 3; ++i)
@@ -643,9 +656,7 @@ void ccz4_rhs(const orc_params& P, const Conf& c, const Src& s, double* rhs) {
     {
         double zda = 0;
         for (int i = 0; i < 3; ++i) zda += c.Zu[i] * c.d1[F_LAPSE][i];
-        rhs[F_TH] = adv(F_TH)
-                    + (al / (2.0 * (1.0 + b))) * (c.RZs - c.AA + (2.0 / 3.0) * K * K - 2.0 * Th * K - 2.0 * s.rho8)
-                    - zda - al * P.kappa1 * (2.0 + P.kappa2) * Th;
+        rhs[F_TH] = adv(F_TH) + al * (c.divZ - Th * K) - zda + (al / (2.0 * (1.0 + b))) * Hb;
     }
     double rhsG[3];
     for (int i = 0; i < 3; ++i) {
@@ -672,6 +683,18 @@ void ccz4_rhs(const orc_params& P, const Conf& c, const Src& s, double* rhs) {
             for (int k = 0; k < 3; ++k) hzdb += c.hi[j][k] * c.Zl[j] * db(k, i);
         }
         x += 2.0 * P.kappa3 * ((2.0 / 3.0) * hz * c.divb - hzdb) - 2.0 * al * P.kappa1 * hz - 2.0 * al * hs;
+        // b(x) part of d_t Z_j: -(b/(1+b)) alpha (M_j + d_j Theta - K_j^k Z_k - kappa1 Z_j), with the
+        // momentum constraint M_j = D_k K^k_j - D_j K - 8 pi S_j; Gamma-hat^i carries 2 h^ij Z_j
+        double zb = 0;
+        for (int j = 0; j < 3; ++j) {
+            double m = -s.S8[j], kz = 0;
+            for (int a2 = 0; a2 < 3; ++a2) {
+                kz += c.Kphys[j][a2] * c.Zu[a2];
+                for (int b2 = 0; b2 < 3; ++b2) m += c.G.gi[a2][b2] * (c.G.DK[a2][b2][j] - c.G.DK[j][a2][b2]);
+            }
+            zb += c.hi[i][j] * (m + c.d1[F_TH][j] - kz - P.kappa1 * c.Zl[j]);
+        }
+        x -= (2.0 * al * b / (1.0 + b)) * zb;
         rhsG[i] = x;
         rhs[F_GAM + i] = x;
     }

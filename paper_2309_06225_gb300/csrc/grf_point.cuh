@@ -701,8 +701,13 @@ GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS]
             rhs[F_H + sidx(i, j)] = x;
         }
     const T K2Th = K - 2.0 * Th;
+    // b(x) of the modified gauge enters through the auxiliary metric g^ab - b n^a n^b of the Z terms
+    // of the covariant equation; its 3+1 projection is carried by Hb = H - 16 pi rho
+    // - 2 kappa1 (2 + kappa2) Theta (plain H = R - A_ij A^ij + 2/3 K^2) in d_t K and d_t Theta, and
+    // by the momentum-constraint combination in d_t Gamma-hat below.
+    const T Hb = fma(-2.0 * c.kappa1 * (2.0 + c.kappa2), Th, Rs - AA + (2.0 / 3.0) * K * K - 2.0 * rho8);
     const T Kdot0 = ADV(F_K) + al * fma(K, K2Th, RZs) - (3.0 * c.kappa1 * (1.0 + c.kappa2)) * al * Th - lapal
-                    - 1.5 * al * rho8 - (c.bK * al) * (Rs - AA + (2.0 / 3.0) * K * K - 2.0 * rho8);
+                    - 1.5 * al * rho8 - (c.bK * al) * Hb;
     T Adot0[6];
     {
         T Xa[6];
@@ -722,8 +727,10 @@ GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS]
                 Adot0[sidx(i, j)] = x;
             }
     }
-    rhs[F_TH] = ADV(F_TH) + (c.bTh * al) * (RZs - AA + (2.0 / 3.0) * K * K - 2.0 * Th * K - 2.0 * rho8)
-                - (Zu[0] * dal[0] + Zu[1] * dal[1] + Zu[2] * dal[2]) - (c.kappa1 * (2.0 + c.kappa2)) * al * Th;
+    // d_t Theta = beta.dTheta + alpha (D_i Z^i - Theta K) - Z^i d_i alpha + alpha Hb / (2 (1 + b)),
+    // with 2 D_i Z^i = RZs - Rs
+    rhs[F_TH] = ADV(F_TH) + al * fma(0.5, RZs - Rs, -Th * K) - (Zu[0] * dal[0] + Zu[1] * dal[1] + Zu[2] * dal[2])
+                + (c.bTh * al) * Hb;
     {
         T hZ[3];
 #pragma unroll
@@ -740,6 +747,19 @@ GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS]
         for (int k = 0; k < 3; ++k) tk[k] = 2.0 * fma(al, dTh[k], fma(-Th, dal[k], -alK23 * Zl[k]));
         const T k3div = (4.0 / 3.0) * c.kappa3 * divb;
         const T ak1 = 2.0 * al * c.kappa1;
+        // b(x) part of d_t Z_j: -(b/(1+b)) alpha wb_j, wb_j = M_j + d_j Theta - K^k_j Z_k - kappa1 Z_j with
+        // the momentum constraint M_j = B_j - 8 pi S_j; Gamma-hat^i carries 2 h^ij Z_j, so d_t Gamma-hat^i
+        // gains -(2b/(1+b)) alpha h^ij wb_j (2b/(1+b) = 2 - 4 bTh)
+        T wb[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            T s = (Bv[j] - S8[j]) + dTh[j];
+            s = fma(-c.kappa1, Zl[j], s);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) s = fma(-Kud(k, j), Zl[k], s);
+            wb[j] = s;
+        }
+        const T abG = (2.0 - 4.0 * c.bTh) * al;
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             const T t1 = sdotw(G2[i], Auw);
@@ -760,6 +780,7 @@ GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS]
             x = fma(k3div - ak1, hZ[i], x);
             x = fma(-2.0 * c.kappa3, t6, x);
             x = fma(-al2, hi[sidx(i, 0)] * S8[0] + hi[sidx(i, 1)] * S8[1] + hi[sidx(i, 2)] * S8[2], x);
+            x = fma(-abG, hi[sidx(i, 0)] * wb[0] + hi[sidx(i, 1)] * wb[1] + hi[sidx(i, 2)] * wb[2], x);
             rhs[F_GAM + i] = x;
             rhs[F_B + i] = fma(-c.eta, v[F_B + i], x);
             rhs[F_SHIFT + i] = fma(c.shift_F * c.inv_1pa, v[F_B + i],

@@ -305,3 +305,131 @@ def phys_pack_generic(alpha, beta_u, g, phi, T, pt):
     ex += [sp.diff(Pi, t)]
     vals = np.array(sp.lambdify(T, ex, modules="math")(*pt), dtype=np.float64)
     return vals[:120].copy(), vals[120:126].copy(), float(vals[126])
+
+
+# ---------------------------------------------------------------------------------------
+# Covariant modified damped Z4 (the equation the CCZ4 system is the 3+1 projection of)
+# ---------------------------------------------------------------------------------------
+def z4_spacetime():
+    """A generic spacetime (lapse, shift, rotated-diagonal spatial metric, scalar) and a generic
+    Z4 covector Z_a, all analytic in (t, x, y, z). The spatial metric is R^T diag(d) R, so its
+    inverse and determinant are closed forms."""
+    t, x, y, z = symbols()
+    alpha = 1 + sp.Rational(1, 5) * sp.sin(0.7 * x + 0.3 * y - 0.5 * z + 0.4 * t)
+    beta_u = [sp.Rational(1, 10) * sp.cos(0.5 * y + 0.2 * t + 0.3 * z),
+              0.15 * sp.sin(0.4 * z - 0.3 * x + 0.25 * t),
+              0.1 * sp.sin(x + t) * sp.cos(0.3 * y)]
+    d = [1 + 0.20 * sp.sin(0.3 * x + 0.2 * t - 0.4 * z), 1 + 0.15 * sp.cos(0.6 * z + 0.2 * x - 0.35 * t + 0.5 * y),
+         1 + 0.18 * sp.sin(0.5 * y + 0.3 * z + 0.45 * t)]
+    g, g_inv = rotated_diag(d)
+    phi = 0.3 * sp.sin(0.6 * x + 0.2 * t - 0.1 * y) * sp.cos(0.4 * y + 0.2 * z) + 0.2 * z * t + 0.1 * x
+    Z = [0.05 * sp.sin(0.3 * x - 0.2 * y + 0.5 * t) + 0.02, 0.04 * sp.cos(0.4 * y + 0.3 * z - 0.2 * t),
+         -0.03 * sp.sin(0.6 * z + 0.1 * x + 0.3 * t), 0.05 * sp.cos(0.2 * x + 0.5 * y - 0.4 * z + 0.1 * t)]
+    return (t, x, y, z), alpha, beta_u, d, g, g_inv, phi, Z
+
+
+def z4_point_data(pt):
+    """Everything the covariant check needs at the spacetime point pt = (t, x, y, z):
+    the 27 conformal fields with their spatial derivatives (oracle input), their exact time
+    derivatives, and the 4-metric, scalar and Z data with derivatives. The conformal fields
+    follow the CCZ4 definitions: chi = det(gamma)^(-1/3), h = chi gamma, K_ij from the metric's
+    time derivative, A = chi (K_ij - gamma_ij K/3), Theta = -n^a Z_a, and Gamma-hat^i =
+    Gamma-tilde^i + 2 h^ij Z_j (Z_j the spatial components of Z_a)."""
+    T, alpha, beta_u, d, g, g_inv, phi, Z = z4_spacetime()
+    t, x, y, z = T
+    X = (x, y, z)
+    chi = (d[0] * d[1] * d[2]) ** sp.Rational(-1, 3)
+    h = chi * g
+    hi = g_inv / chi
+    beta_l = [sum(g[i, j] * beta_u[j] for j in range(3)) for i in range(3)]
+    G1 = christoffel_first(g, X)
+    Dbeta = [[sp.diff(beta_l[j], X[i]) - sum(G1[l][i][j] * beta_u[l] for l in range(3)) for j in range(3)]
+             for i in range(3)]
+    K = sp.Matrix(3, 3, lambda i, j: -(sp.diff(g[i, j], t) - Dbeta[i][j] - Dbeta[j][i]) / (2 * alpha))
+    Ktr = sum(g_inv[i, j] * K[i, j] for i in range(3) for j in range(3))
+    A = chi * (K - g * Ktr / 3)
+    # det h = 1, so Gamma-tilde^i = h^jk Gt^i_jk = -d_j h^ij
+    Gamt = [-sum(sp.diff(hi[i, j], X[j]) for j in range(3)) for i in range(3)]
+    Ghat = [Gamt[i] + 2 * sum(hi[i, j] * Z[1 + j] for j in range(3)) for i in range(3)]
+    Theta = -(Z[0] - sum(beta_u[i] * Z[1 + i] for i in range(3))) / alpha
+    Pi = (sp.diff(phi, t) - sum(beta_u[k] * sp.diff(phi, X[k]) for k in range(3))) / alpha
+    F = [chi] + [h[i, j] for i, j in SYM_PAIRS] + [Ktr] + [A[i, j] for i, j in SYM_PAIRS] + [Theta] \
+        + Ghat + [alpha] + list(beta_u) + [sp.Float(0.01), sp.Float(-0.02), sp.Float(0.03)] + [phi, Pi]
+    F0 = [sp.sympify(f).subs(t, pt[0]) for f in F]
+    v, d1, d2 = conformal_point(F0, pt[1:], X)
+    dt = np.array(sp.lambdify(T, [sp.diff(sp.sympify(f), t) for f in F], modules="math")(*pt), dtype=np.float64)
+    g4 = four_metric(alpha, beta_u, g)
+    g4v, dg, ddg, dphi, ddphi = lambdify_metric_derivs(g4, phi, T)(pt)
+    zv = np.array(sp.lambdify(T, Z + [sp.diff(Za, s) for Za in Z for s in T], modules="math")(*pt), dtype=np.float64)
+    return dict(v=v, d1=d1, d2=d2, dt=dt, g4=g4v, dg=dg, ddg=ddg, dphi=dphi, ddphi=ddphi,
+                phi=float(v[F_PHI]), Z=zv[:4], dZ=zv[4:].reshape(4, 4).T.copy())
+
+
+def z4_residual(D, unk, b, k1, k2, lam, g2, kind, variant="covariant"):
+    """Residual of the covariant modified damped Z4 equations with the 4dST stress tensor,
+        G^mn + 2 Phat_a^{b mn} nabla_b Z^a - kappa1 [n^m Z^n + n^n Z^m + kappa2 (n.Z) g^mn] - 8 pi T^mn = 0,
+        Phat_a^{b mn} = delta_a^(m gh^n)b - 1/2 delta_a^b gh^mn,   gh^mn = g^mn - b n^m n^n,
+    and of the scalar equation, at the data of z4_point_data modified by the unknowns
+    unk = (d_t^2 gamma_ij (6, added), d_t Z_a (4, added), d_t^2 phi (1, added)). Every
+    component is affine in unk. `variant` plants a change in the equation for the
+    discrimination checks: "b_half" (b/2 in gh), "k2_moved" ((1 + kappa2) instead of kappa2
+    in the damping), "gh_first_only" (g instead of gh in the trace term of Phat)."""
+    g = D["g4"]
+    ddg = D["ddg"].copy()
+    for m, (i, j) in enumerate(SYM_PAIRS):
+        ddg[0, 0, i + 1, j + 1] += unk[m]
+        if i != j:
+            ddg[0, 0, j + 1, i + 1] += unk[m]
+    dZ = D["dZ"].copy()
+    dZ[0, :] += unk[6:10]
+    ddphi = D["ddphi"].copy()
+    ddphi[0, 0] += unk[10]
+    gi, Gam, Rdn, Ric, Rs = geometry4(g, D["dg"], ddg)
+    Z = D["Z"]
+    nabZu = (dZ - np.einsum("cba,c->ba", Gam, Z)) @ gi   # [b, m] = nabla_b Z^m
+    divZ = np.trace(nabZu)
+    al = 1.0 / np.sqrt(-gi[0, 0])
+    n_up = gi @ np.array([-al, 0.0, 0.0, 0.0])
+    bb = 0.5 * b if variant == "b_half" else b
+    gh = gi - bb * np.outer(n_up, n_up)
+    gh_tr = gi if variant == "gh_first_only" else gh
+    Zpart = np.einsum("nb,bm->mn", gh, nabZu) + np.einsum("mb,bn->mn", gh, nabZu) - gh_tr * divZ
+    Zu = gi @ Z
+    nZ = n_up @ Z
+    c2 = 1.0 + k2 if variant == "k2_moved" else k2
+    damp = -k1 * (np.outer(n_up, Zu) + np.outer(Zu, n_up) + c2 * nZ * gi)
+    T8, E, _, _ = stress_and_scalar(g, gi, Gam, Rdn, Ric, Rs, D["dphi"], ddphi, D["phi"], lam, g2, kind)
+    Emn = gi @ (Ric - 0.5 * g * Rs) @ gi + Zpart + damp - gi @ T8 @ gi
+    return np.array([Emn[i, j] for i in range(4) for j in range(i, 4)] + [E])
+
+
+def z4_time_derivatives(D, **kw):
+    """Solves the 11 covariant equations for the unknowns (affine: exact from 12 evaluations)
+    and returns the resulting exact time derivatives of the 27 conformal fields at the point."""
+    f0 = z4_residual(D, np.zeros(11), **kw)
+    J = np.empty((11, 11))
+    for c in range(11):
+        e = np.zeros(11)
+        e[c] = 1.0
+        J[:, c] = z4_residual(D, e, **kw) - f0
+    unk = np.linalg.solve(J, -f0)
+    # the unknowns shift the time derivatives of K_ij, Theta, Z_j and Pi at the point
+    out = D["dt"].copy()
+    gam = D["g4"][1:, 1:]
+    gam_i = np.linalg.inv(gam)
+    al = 1.0 / np.sqrt(-np.linalg.inv(D["g4"])[0, 0])
+    chi = np.linalg.det(gam) ** (-1.0 / 3.0)
+    P = np.zeros((3, 3))
+    for m, (i, j) in enumerate(SYM_PAIRS):
+        P[i, j] = P[j, i] = unk[m]
+    dKij = -P / (2.0 * al)              # K_ij = -(d_t gamma_ij - ...)/(2 alpha)
+    dK = np.einsum("ij,ij->", gam_i, dKij)
+    dA = chi * (dKij - gam * dK / 3.0)
+    out[F_K] += dK
+    for m, (i, j) in enumerate(SYM_PAIRS):
+        out[F_A + m] += dA[i, j]
+    beta_u = gam_i @ D["g4"][0, 1:]
+    out[F_TH] += -(unk[6] - beta_u @ unk[7:10]) / al
+    out[F_GAM:F_GAM + 3] += 2.0 * (gam_i / chi) @ unk[7:10]
+    out[F_PI] += unk[10] / al
+    return out

@@ -46,8 +46,12 @@ def test_z4_constraint_damping_rates_on_flat_data(orc, k1, k2, alpha, chi, a0, b
     term vanishes, so only the damping is left. The constraint fields decay at the damped-Z4
     rates
         d_t Theta = -alpha kappa1 (2 + kappa2) Theta,   d_t Z_i = -alpha kappa1 Z_i,
-    and the metric and A_ij stay static. Catches a dropped or anti-damping kappa term, kappa2
-    in the wrong place, a missing lapse factor, and Z read with the wrong metric factor."""
+    and the metric and A_ij stay static. With the modified gauge's b(x) the auxiliary metric
+    g^ab - b n^a n^b of the Z terms multiplies the time-derivative terms of the nn and ni
+    components of the covariant equation by (1 + b), so both rates are divided by (1 + b)
+    (the covariant pin below checks the general case). Catches a dropped or anti-damping kappa
+    term, kappa2 in the wrong place, a missing lapse factor, and Z read with the wrong metric
+    factor."""
     v = np.zeros(27)
     v[0] = chi
     v[1], v[4], v[6] = 1.0, 1.0, 1.0
@@ -61,10 +65,16 @@ def test_z4_constraint_damping_rates_on_flat_data(orc, k1, k2, alpha, chi, a0, b
     p = P(kappa1=k1, kappa2=k2, kappa3=0.7, a0=a0, b0=b0, lam=0.2, g2=0.1)
     r, _, st = orc.point_rhs(p, v, d1, d2)
     assert st == 0
-    assert r[14] == pytest.approx(-alpha * k1 * (2.0 + k2) * theta, rel=1e-14, abs=1e-15)
-    # d_t Gamma-hat^i = 2 h^ij d_t Z_j = -alpha kappa1 Gamma-hat^i (h static, Gamma-tilde = 0)
-    np.testing.assert_allclose(r[15:18], -alpha * k1 * ghat, rtol=1e-14, atol=1e-15)
-    assert np.all(r[0:7] == 0.0) and np.all(r[8:14] == 0.0)     # chi, h_ij, A_ij static
+    assert r[14] == pytest.approx(-alpha * k1 * (2.0 + k2) * theta / (1.0 + b0), rel=1e-14, abs=1e-15)
+    # d_t Gamma-hat^i = 2 h^ij d_t Z_j = -alpha kappa1 Gamma-hat^i / (1 + b) (h static, Gamma-tilde = 0)
+    np.testing.assert_allclose(r[15:18], -alpha * k1 * ghat / (1.0 + b0), rtol=1e-14, atol=1e-15)
+    assert np.all(r[0:7] == 0.0)     # chi, h_ij static
+    # A_ij static; K moves only by the damping terms (-3 alpha kappa1 (1 + kappa2) Theta, and the b(x)
+    # term -(3 alpha b/(4 (1 + b))) (-2 kappa1 (2 + kappa2) Theta)); both pass through the oracle's
+    # residual-based coupled solve, which leaves rounding far below 1e-15
+    assert np.all(np.abs(r[8:14]) < 1e-15)
+    kdot = -3.0 * alpha * k1 * (1.0 + k2) * theta + 1.5 * alpha * b0 / (1.0 + b0) * k1 * (2.0 + k2) * theta
+    assert r[7] == pytest.approx(kdot, rel=1e-13, abs=1e-15)
     assert np.all(r[19:22] == 0.0) and r[25] == 0.0  # shift, phi
     assert abs(r[26]) < 1e-15  # Pi: zero up to the rounding of the oracle's residual-based solve
     # the same data with the damping switched off: the constraint fields do not move
@@ -93,10 +103,64 @@ def test_z_part_of_gamma_hat_is_shift_transported_by_kappa3(orc, k3):
     for i in range(3):
         d1[19 + i, :] = M[i]
     d2 = np.zeros((27, 6))
-    r, _, st = orc.point_rhs(P(kappa1=k1, kappa2=0.1, kappa3=k3), v, d1, d2)
+    p = P(kappa1=k1, kappa2=0.1, kappa3=k3)
+    r, _, st = orc.point_rhs(p, v, d1, d2)
     assert st == 0
-    expect = -alpha * k1 * ghat + k3 * ((2.0 / 3.0) * ghat * np.trace(M) - M @ ghat)
+    # damping at the modified gauge's rate -alpha kappa1 / (1 + b) (see the flat-slice damping pin)
+    expect = -alpha * k1 * ghat / (1.0 + p.b0) + k3 * ((2.0 / 3.0) * ghat * np.trace(M) - M @ ghat)
     np.testing.assert_allclose(r[15:18], expect, rtol=1e-13, atol=1e-15)
+
+
+# ----------------------------------------------------------------------------- covariant Z4
+@pytest.fixture(scope="module")
+def z4_point():
+    return an.z4_point_data((0.0, 0.37, -0.52, 0.81))
+
+
+# fields whose time derivative the spacetime fixes (the gauge fields and B^i evolve by choice)
+Z4_FIELDS = list(range(0, 18)) + [25, 26]
+Z4_CASES = [  # b, kappa1, kappa2, lambda, g2, beta kind
+    (0.0, 0.0, 0.0, 0.0, 0.0, 0), (0.0, 0.3, 0.4, 0.0, 0.0, 0), (0.4, 0.0, 0.0, 0.0, 0.0, 0),
+    (0.4, 0.3, 0.4, 0.0, 0.0, 0), (1.1, 0.2, -0.3, 0.0, 0.0, 0), (0.4, 0.1, 0.0, 0.7, 0.3, 0),
+    (0.4, 0.25, 0.5, 0.5, 0.2, 1)]
+
+
+def _z4_compare(orc, D, case, variant="covariant"):
+    b, k1, k2, lam, g2, kind = case
+    want = an.z4_time_derivatives(D, b=b, k1=k1, k2=k2, lam=lam, g2=g2, kind=kind, variant=variant)
+    r, _, st = orc.point_rhs(P(kappa1=k1, kappa2=k2, kappa3=1.0, a0=0.2, b0=b, lam=lam, g2=g2, beta_kind=kind),
+                             D["v"], D["d1"], D["d2"])
+    assert st == 0
+    return np.abs(r[Z4_FIELDS] - want[Z4_FIELDS]) / np.maximum(1.0, np.abs(want[Z4_FIELDS]))
+
+
+@pytest.mark.parametrize("case", Z4_CASES)
+def test_ccz4_is_the_3p1_projection_of_covariant_modified_z4(orc, z4_point, case):
+    """On a generic spacetime with a generic Z4 vector (Theta, Z_i, the constraints and every
+    gradient non-zero; lapse and shift non-trivial) the covariant equations
+        G^mn + 2 Phat_a^{b mn} nabla_b Z^a - kappa1 [2 n^(m Z^n) + kappa2 (n.Z) g^mn] = 8 pi T^mn,
+        Phat_a^{b mn} = delta_a^(m gh^n)b - 1/2 delta_a^b gh^mn,  gh^mn = g^mn - b n^m n^n,
+    together with the 4dST scalar equation, are solved at one point for the 11 second time
+    derivatives (of gamma_ij, Z_a and phi) that they fix, in a brute-force 4D coordinate
+    computation (numpy Christoffels and Riemann of the 4-metric). The resulting exact time
+    derivatives of chi, h_ij, K, A_ij, Theta, Gamma-hat^i, phi and Pi must equal the oracle's
+    3+1 right-hand sides. b = 0 with kappa1, kappa2 != 0 pins the damping terms, including
+    -3 alpha kappa1 (1 + kappa2) Theta in d_t K; b != 0 pins every b(x) term of the modified
+    gauge in d_t K, d_t Theta and d_t Gamma-hat; lambda, g2 != 0 pin the 4dST matter terms
+    inside them."""
+    err = _z4_compare(orc, z4_point, case)
+    assert np.max(err) < 1e-11, dict(zip(Z4_FIELDS, err))
+
+
+@pytest.mark.parametrize("variant,case", [("b_half", Z4_CASES[3]), ("b_half", Z4_CASES[6]),
+                                          ("gh_first_only", Z4_CASES[3]), ("k2_moved", Z4_CASES[1]),
+                                          ("k2_moved", Z4_CASES[4])])
+def test_covariant_z4_pin_discriminates(orc, z4_point, variant, case):
+    """The same comparison with a planted change in the covariant equation (half the b(x)
+    coefficient; g instead of gh in the trace term of Phat; 1 + kappa2 in place of kappa2 in the
+    damping) must fail by far more than the tolerance: the pin above sees each of these terms."""
+    err = _z4_compare(orc, z4_point, case, variant)
+    assert np.max(err) > 1e-6
 
 
 # ----------------------------------------------------------------------------- P3 stencils
