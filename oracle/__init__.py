@@ -68,6 +68,8 @@ def lib():
         L.orc_point_psi4.argtypes = [C.POINTER(OrcParams), _P, _P, _P, _P, _P]
         L.orc_psi4.argtypes = [C.POINTER(OrcBox), C.POINTER(OrcParams), _P, _P]
         L.orc_phys_sources_psi4.argtypes = [C.POINTER(OrcParams), _P, _P, C.c_double, _P, _P]
+        L.orc_rk4_signal.argtypes = [C.POINTER(OrcBox), C.POINTER(OrcParams), _P, C.c_double, C.c_int, _P, _P]
+        L.orc_rk4_signal.restype = C.c_int
         _lib = L
     return _lib
 
@@ -272,3 +274,39 @@ def phys_psi4(p, phys, u6, w, xyz):
     out = np.zeros(21)
     lib().orc_phys_sources_psi4(C.byref(params(p)), _ptr(phys), _ptr(u6), float(w), _ptr(xyz), _ptr(out))
     return complex(out[19], out[20])
+
+
+_tlm = None
+
+
+def tlm_lib():
+    """The tangent-linear builds of the same core (dual numbers and complex step)."""
+    global _tlm
+    if _tlm is None:
+        L = C.CDLL(_build.build_tlm())
+        L.orc_tlm_rk4.argtypes = [C.POINTER(OrcBox), C.POINTER(OrcParams), _P, _P, _P, C.c_double, C.c_int, _P, _P,
+                                  C.c_int, C.c_double]
+        L.orc_tlm_rk4.restype = C.c_int
+        _tlm = L
+    return _tlm
+
+
+def rk4_signal(b, p, s, dt, nsteps, sphere):
+    """RK4 in place with the sphere-averaged scalar signal L = sum_n dt sum_q w_q phi(c + R xhat_q, t_n);
+    sphere = (R, cx, cy, cz). Returns (status, L)."""
+    sp = np.ascontiguousarray(sphere, dtype=np.float64)
+    L = np.zeros(1)
+    st = lib().orc_rk4_signal(C.byref(box(b)), C.byref(params(p)), _ptr(s), dt, nsteps, _ptr(sp), _ptr(L))
+    return st, float(L[0])
+
+
+def tlm_rk4(b, p, s, ds, dparams, dt, nsteps, sphere=None, mode="dual", h=1e-30):
+    """Tangent-linear RK4: s (value) and ds (tangent) in place along (ds, dlambda, dg2) =
+    (ds, dparams[0], dparams[1]). mode "dual" (dual numbers) or "cs" (complex step with step h).
+    Returns (status, L, dL) (L, dL = None without a sphere)."""
+    dp = np.ascontiguousarray(dparams, dtype=np.float64)
+    L = np.zeros(2)
+    sp = None if sphere is None else np.ascontiguousarray(sphere, dtype=np.float64)
+    st = tlm_lib().orc_tlm_rk4(C.byref(box(b)), C.byref(params(p)), _ptr(dp), _ptr(s), _ptr(ds), dt, nsteps,
+                               None if sp is None else _ptr(sp), _ptr(L), 0 if mode == "dual" else 1, h)
+    return (st, None, None) if sp is None else (st, float(L[0]), float(L[1]))

@@ -109,6 +109,15 @@ def test_rhs_parity(g, orc, case):
     ref = orc.rhs(box, params, s)
     out = gpu_rhs(g, box, params, s)
     errs = field_errors(out, ref, box, state=s, sigma=params.sigma_ko)
+    if kind == "puncture":
+        # On constraint-satisfying data d_t Theta is the Hamiltonian-constraint residual
+        # alpha (H - 16 pi rho)/(2 (1 + b)): a truncation residue of Ricci terms of order one, so
+        # its rounding error is eps times those terms, not eps times its own (tiny) value. It is
+        # compared on the scale of d_t K, which carries the same terms.
+        ci, gi_ = box.interior(ref), box.interior(out)
+        th = gi.IDX["Theta"]
+        den = max(np.max(np.abs(ci[gi.IDX["K"]])), np.max(np.abs(ci[th])))
+        errs[th] = np.max(np.abs(gi_[th] - ci[th])) / den
     assert np.max(errs) < 1e-11, describe(errs)
 
 
