@@ -27,26 +27,44 @@ sys.path.insert(0, ROOT)
 METRIC = "FP64 grid-point RK4 updates/s (mCCZ4+4∂ST) and % of FP64/HBM roofline"
 UNIT = "point-updates/s"
 
-# FP64 operations per interior point per RK4 stage kernel are counted from the kernel source
-# itself (paper_2309_06225_gb300.flops: the pointwise RHS run with an operation-counting
-# scalar, plus the stencil/KO/update expressions); add/sub/mul = 1 flop, fma = 2, div = 1.
+# FLOP_alg: the method's FP64 work per interior point and RK4 stage, frozen at 6,615.25 flops. It
+# was counted once by running this formulation's pointwise right-hand side (CCZ4 + 4dST + the
+# 7x7 solve), its stencils, dissipation and stage update with an operation-counting scalar
+# (paper_2309_06225_gb300.flops; add/sub/mul 1, fma 2, div 1). It is not recounted when the
+# kernel changes, so the achieved rate tracks the time per point, not source edits.
+FLOP_ALG_PER_POINT_STAGE = 6615.25
 # algorithmic HBM bytes per point-update (stage-wise RK4, 27 fields, perfect stencil reuse):
 # stage 1: read u_n, write u_1 and acc (3 x 216 B); stages 2-3: read u_s, u_n, acc, write u_s, acc
 # (5 x 216 B each); stage 4: read u_3, u_n, acc, write u_n (4 x 216 B)
 BYTES_PER_POINT_UPDATE = 216 * (3 + 5 + 5 + 4)
-# dram__bytes_read.sum + dram__bytes_write.sum of one stage launch per interior point, from the
-# ncu capture of the current stage kernel (profiles/); None when the kernel changed since.
-TRAFFIC_BYTES_PER_POINT_STAGE = 12622  # mean of stage 0 and 1, 96^3 capture (profiles/rk4_stage_kernel_bl_pair_96.md)
-# the tangent-linear (dual-number) stage kernel (profiles/tlm_stage_kernel_sphere_signal_96.md)
+# Per interior point and stage launch, from an ncu capture of the stage kernel on the 96^3 box
+# (mean of stages 0 and 1): dram__bytes_read.sum + dram__bytes_write.sum, and the FP64 thread
+# instructions (dadd + dmul + dfma). None when the kernel changed since the capture.
+TRAFFIC_BYTES_PER_POINT_STAGE = None
+FP64_INSTR_PER_POINT_STAGE = None
+# the tangent-linear (dual-number) stage kernel's FP64 instructions per point-stage (same kind of capture)
 TLM_FP64_INSTR_PER_POINT_STAGE = 28826
-# the 6th-order stage kernel with centred advection (profiles/rk4_stage6_kernel_bl_pair_96.md, mean of stages 0, 1)
-FP64_INSTR_PER_POINT_STAGE_6 = 4823
-TRAFFIC_BYTES_PER_POINT_STAGE_6 = 10852
-# FP64 thread instructions (dadd + dmul + dfma) per interior point and stage, same capture; the
-# pipe issues 2 per SM per clock (152 SMs x 2 x 2.06 GHz = 6.26e11 / s, half the flop peak).
-FP64_INSTR_PER_POINT_STAGE = 4162
-# FP64 (non-tensor) peak of GB300: 152 SMs x 2 FP64 FMA lanes/clk x 2 flop x ~2.06 GHz = 1.25 TFLOP/s
-FP64_PEAK_TFLOPS = 1.25
+# the 6th-order stage kernel with centred advection (same kind of capture)
+FP64_INSTR_PER_POINT_STAGE_6 = None
+TRAFFIC_BYTES_PER_POINT_STAGE_6 = None
+# nominal FP64 (non-tensor) peak of GB300: 152 SMs x 2 FP64 FMA lanes/clk x 2 flop x ~2.06 GHz;
+# used only when no measured figure is stored
+FP64_NOMINAL_TFLOPS = 1.25
+PEAKS_FP64_FILE = os.path.join(ROOT, "paper_2309_06225_gb300", "peaks_fp64.json")
+
+
+def fp64_peak():
+    """FP64 pipe ceilings: (TFLOP/s, FP64 instructions/s, source). The measured sweep of
+    build_peak.measure() stored in peaks_fp64.json (best DFMA flop rate, best instruction rate of
+    any kind, with the clocks seen), else the nominal figure (instructions at 2 per FMA flop)."""
+    try:
+        d = json.load(open(PEAKS_FP64_FILE))
+        return float(d["tflops"]), float(d["instr_per_s"]), "of measured"
+    except (OSError, ValueError, KeyError):
+        return FP64_NOMINAL_TFLOPS, FP64_NOMINAL_TFLOPS * 1e12 / 2, "of nominal"
+
+
+FP64_PEAK_TFLOPS, FP64_PEAK_INSTR, FP64_PEAK_SOURCE = fp64_peak()
 
 
 def measured_hbm_gbs():
@@ -80,8 +98,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="bl_pair_256", choices=["bl_pair_256", "bl_pair_128", "bl_pair_96", "bl_pair_64", "amr_boxes_96", "coupling_sweep_32", "sphere_signal_96", "calls_256", "calls_96", "bl_pair_octant_128", "patches_256"])
+    ap.add_argument("--workload", default="bl_pair_256", choices=["bl_pair_256", "bl_pair_128", "bl_pair_96", "bl_pair_64", "amr_boxes_96", "coupling_sweep_32", "sphere_signal_96", "adjoint_96", "calls_256", "calls_96", "bl_pair_octant_128", "patches_256"])
     ap.add_argument("--patches", default="2,2,2", help="patches per axis of the patches_256 workload")
+    ap.add_argument("--adjoint-grid", type=int, default=96,
+                    help="points per axis of the adjoint_96 workload's box (dx = 0.2; 96 is the workload, smaller "
+                         "grids are for profiling captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--decoupled", action="store_true",
@@ -92,7 +113,8 @@ def parse():
                     help="stencil of the advection terms beta^k d_k u")
     ap.add_argument("--boundary", default="periodic", choices=["periodic", "extrapolating", "sommerfeld"],
                     help="outer boundary of the bl_pair box (its domain is centred on the origin)")
-    ap.add_argument("--no-peak", action="store_true", help="skip the FP64 microbenchmark")
+    ap.add_argument("--measure-peak", action="store_true",
+                    help="also run the FP64 microbenchmark sweep in this process and report it")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     return ap.parse_args()
 
@@ -204,13 +226,13 @@ def run_calls(args, rank, world, local_rank):
             tf = flop_ko * npts / (ms * 1e-3) / 1e12
             rec["roofline"] = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                                "frac": tf / FP64_PEAK_TFLOPS, "flop_per_point": flop_ko,
-                               "peak_source": "GB300 FP64 non-tensor, 1.25 TFLOP/s (nominal)",
+                               "peak_source": FP64_PEAK_SOURCE,
                                "hbm_frac": nbytes * npts / (ms * 1e-3) / 1e9 / hbm, "hbm_peak_source": hbm_src}
         elif name == "grf_rhs":
             tf = flop_rhs * npts / (ms * 1e-3) / 1e12
             rec["roofline"] = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                                "frac": tf / FP64_PEAK_TFLOPS, "flop_per_point": flop_rhs,
-                               "peak_source": "GB300 FP64 non-tensor, 1.25 TFLOP/s (nominal)"}
+                               "peak_source": FP64_PEAK_SOURCE}
         else:  # constraints, densities and Psi_4 use the RHS's gather and pointwise algebra
             rec["roofline"] = None
             rec["note"] = "FP64-bound like grf_rhs; its flop count is a subset of the RHS and is not counted"
@@ -283,15 +305,98 @@ def run_tangent(args, rank, world, local_rank):
            "differentiated_vs_plain": {"tangent_ms_per_step": ms_t / args.steps, "plain_ms_per_step": ms_f / args.steps,
                                        "ratio": ms_t / ms_f},
            "signal": loss.cpu().numpy().tolist(), "e2e": None, "cpu_baseline": None}
-    # FP64-bound like the plain stage: the dual-number stage's FP64 instruction count (ncu, 96^3,
-    # profiles/tlm_stage_kernel_sphere_signal_96.md) against the pipe's issue rate
+    # FP64-bound like the plain stage: the dual-number stage's FP64 instruction count (ncu, 96^3)
+    # against the pipe's issue rate
     stage_ms = ms_t / (4 * args.steps)
-    issue = TLM_FP64_INSTR_PER_POINT_STAGE * npts / (stage_ms * 1e-3) / (FP64_PEAK_TFLOPS * 1e12 / 2)
+    issue = TLM_FP64_INSTR_PER_POINT_STAGE * npts / (stage_ms * 1e-3) / FP64_PEAK_INSTR
     out["roofline"] = {"bound": "alu", "unit": "FP64 instructions/s", "kernel": "tlm_stage_kernel",
                        "achieved": TLM_FP64_INSTR_PER_POINT_STAGE * npts / (stage_ms * 1e-3),
-                       "peak": FP64_PEAK_TFLOPS * 1e12 / 2, "frac": issue,
-                       "peak_source": "GB300 FP64 pipe: 152 SMs x 2 instructions/clk x 2.06 GHz (nominal)",
+                       "peak": FP64_PEAK_INSTR, "frac": issue, "peak_source": FP64_PEAK_SOURCE,
                        "fp64_instr_per_point_stage": TLM_FP64_INSTR_PER_POINT_STAGE, "traffic": None}
+    print(json.dumps(out), flush=True)
+
+
+def run_adjoint(args, rank, world, local_rank):
+    """The differentiated evolution in reverse mode: the 96^3 single-puncture box on
+    [-9.6, 9.6]^3 (dx = 0.2, periodic), sphere signal at r = 6. One step of this workload is one
+    RK4 step of the forward pass (grf_signal_forward, a checkpoint every 20 steps) plus its share
+    of the reverse sweep (grf_adjoint_rk4: segment recomputation, stage recomputation, four
+    reverse-mode stage kernels and four transposed-stencil kernels). --steps is the number of
+    RK4 steps differentiated; the gradient is with respect to (lambda, g2, A)."""
+    import numpy as np
+    import torch
+    import grf_inputs as gi
+    import paper_2309_06225_gb300 as grf
+
+    torch.cuda.set_device(local_rank)
+    n = args.adjoint_grid
+    box = gi.cube_box(n, -0.1 * n, 0.1 * n)
+    params = gi.Params(lam=0.01, g2=0.01)
+    amp, ce, R = 1e-3, 20, min(6.0, 0.1 * n - 0.5)
+    b, p = grf.box_like(box), grf.params_like(params)
+    dt = 0.25 * box.dx
+    nsteps = args.steps
+    s0 = gi.single_puncture(box, amp=amp)
+    dphi = np.zeros(box.shape)
+    dphi[25] = gi.single_puncture(box, amp=1.0)[25]
+    dA = grf.to_device(dphi, b)
+    sph = grf.grf_sphere(R, 0.0, 0.0, 0.0)
+    torch.cuda.reset_peak_memory_stats()
+    state = grf.to_device(s0, b)
+    ck = torch.empty((grf.checkpoint_count(nsteps, ce),) + tuple(state.shape), dtype=torch.float64, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ws = grf.alloc_workspace(grf.grf_adjoint_workspace_bytes(b, ce))
+    sbar = grf.alloc_state(b)
+    pbar = torch.zeros(2, dtype=torch.float64, device="cuda")
+    dot = torch.zeros(1, dtype=torch.float64, device="cuda")
+    # warm-up: a short differentiated run
+    wn = max(1, min(args.warmup, 2))
+    grf.grf_signal_forward(b, p, state, dt, wn, sph, ce, ck, loss, ws=ws)
+    grf.grf_adjoint_rk4(b, p, ck, dt, wn, sph, ce, 1.0, sbar, pbar, ws=ws)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    state.copy_(grf.to_device(s0, b))
+    sbar.zero_()
+    clocks = ClockSampler(gpu_selector(local_rank))
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    grf.grf_signal_forward(b, p, state, dt, nsteps, sph, ce, ck, loss, ws=ws, stream=stream)
+    ev[1].record(stream)
+    grf.grf_adjoint_rk4(b, p, ck, dt, nsteps, sph, ce, 1.0, sbar, pbar, ws=ws, stream=stream)
+    grf.grf_state_dot(b, sbar, dA, -1, dot, stream=stream)
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    fwd_ms, rev_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    # the plain step on the same box, for the ratio
+    prim = grf.to_device(s0, b)
+    pws = grf.alloc_workspace(grf.grf_workspace_bytes(b, grf.GRF_OP_RK4))
+    grf.grf_rk4_step(b, p, prim, dt, 2, ws=pws)
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    grf.grf_rk4_step(b, p, prim, dt, nsteps, ws=pws, stream=stream)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    plain_ms = ev[0].elapsed_time(ev[1])
+    npts = box.npoints
+    total_ms = fwd_ms + rev_ms
+    grad = [float(x) for x in pbar.cpu()] + [float(dot.cpu()[0])]
+    out = {"metric": METRIC, "value": npts * nsteps / (total_ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+           "steps": nsteps, "warmup": args.warmup, "ms_per_step": total_ms / nsteps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "adjoint_96", "grid": [n, n, n], "dx": box.dx, "dt": dt, "sphere_radius": R,
+                      "checkpoint_every": ce, "parameters": ["lambda", "g2", "A"],
+                      "method": "reverse mode: forward with checkpoints, segment and stage recomputation, "
+                                "taped reverse-mode stage kernels and transposed stencils"},
+           "gpu_launches": None,
+           "adjoint": {"forward_ms_per_step": fwd_ms / nsteps, "reverse_ms_per_step": rev_ms / nsteps,
+                       "plain_ms_per_step": plain_ms / nsteps, "differentiated_vs_plain": total_ms / plain_ms,
+                       "reverse_vs_forward": rev_ms / fwd_ms, "peak_memory_bytes": torch.cuda.max_memory_allocated(),
+                       "workspace_bytes": grf.grf_adjoint_workspace_bytes(b, ce)},
+           "signal": float(loss.cpu()[0]), "gradient": grad, "clocks": clk, "roofline": None, "e2e": None,
+           "cpu_baseline": None}
     print(json.dumps(out), flush=True)
 
 
@@ -300,7 +405,6 @@ def run_batched(args, rank, world, local_rank):
     import grf_inputs as gi
     import paper_2309_06225_gb300 as grf
     from paper_2309_06225_gb300 import autotune
-    from paper_2309_06225_gb300 import flops as grf_flops
 
     torch.cuda.set_device(local_rank)
     boxes, params, pidx, dts = batched_workload(args.workload)
@@ -364,7 +468,7 @@ def run_batched(args, rank, world, local_rank):
         torch.cuda.synchronize()
         ems = x0.elapsed_time(x1)
     value = npts * args.steps / (ms * 1e-3)
-    flop_ps = sum(grf_flops.flops_per_point_stage(gp[pi]) * b.npoints for b, pi in zip(boxes, pidx)) / npts
+    flop_ps = FLOP_ALG_PER_POINT_STAGE
     achieved = flop_ps * npts * 4 * args.steps / (ms * 1e-3) / 1e12
     variant = {grf.GRF_BATCH_GRAPH: "graph", grf.GRF_BATCH_PERSISTENT: "persistent"}.get(cfg.variant, "stream")
     kernel = "batch_persistent_kernel" if cfg.variant == grf.GRF_BATCH_PERSISTENT else "batch_stage_kernel"
@@ -395,7 +499,6 @@ def run_patches(args, rank, world, local_rank):
     steps of grf_rk4_step on the whole box, and the exchange timed alone."""
     import torch
     import paper_2309_06225_gb300 as grf
-    from paper_2309_06225_gb300 import flops as grf_flops
 
     torch.cuda.set_device(local_rank)
     cfg = workload("bl_pair_256")
@@ -447,7 +550,7 @@ def run_patches(args, rank, world, local_rank):
 
     ems = timed(e2e_step, args.steps)
     value = npts * args.steps / (ms * 1e-3)
-    flop_ps = grf_flops.flops_per_point_stage(p)
+    flop_ps = FLOP_ALG_PER_POINT_STAGE
     achieved = flop_ps * npts * 4 * args.steps / (ms * 1e-3) / 1e12
     # exchange bytes: every ghost point of every patch, 27 fields read and written
     ghost_pts = 0
@@ -658,7 +761,7 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     npts = box.nx * box.ny * box.nz
 
-    peak = None if args.no_peak else build_peak.measure()
+    peak = build_peak.measure() if args.measure_peak else None
 
     def barrier():
         if dist is not None:
@@ -726,8 +829,7 @@ def run_ours(args, rank, world, local_rank):
         if dist is not None:
             dist.destroy_process_group()
         return
-    from paper_2309_06225_gb300 import flops as grf_flops
-    flop_ps = grf_flops.flops_per_point_stage(p)
+    flop_ps = FLOP_ALG_PER_POINT_STAGE
     launch_ms = ms / (4 * args.steps)  # the timed region is 4 stage kernels + 1 small ghost fill per step
     achieved = flop_ps * npts / (launch_ms * 1e-3) / 1e12
     scheme = {"order": box.ng * 2 - 2, "advection": "lopsided" if params.advection else "centred"}
@@ -735,9 +837,9 @@ def run_ours(args, rank, world, local_rank):
     roof = {"bound": "alu", "unit": "TFLOP/s",
             "kernel": "rk4_stage_kernel" if box.ng == 3 else "rk4_stage6_kernel", "achieved": achieved,
             "peak": FP64_PEAK_TFLOPS, "frac": achieved / FP64_PEAK_TFLOPS,
-            "peak_source": "GB300 FP64 non-tensor: 152 SMs x 2 FMA/clk x 2 flop x 2.06 GHz (recipe figure 1.25 TFLOP/s)",
+            "peak_source": FP64_PEAK_SOURCE,
             "peak_dfma_microbenchmark": peak, "flop_per_point_stage": flop_ps,
-            "flop_convention": "counted from the kernel source: add/sub/mul 1, fma 2, div 1",
+            "flop_convention": "FLOP_alg frozen: counted once from this formulation with an operation-counting scalar (add/sub/mul 1, fma 2, div 1)",
             "traffic": TRAFFIC_BYTES_PER_POINT_STAGE * npts if TRAFFIC_BYTES_PER_POINT_STAGE and default_scheme else None}
     sixth_centred = scheme == {"order": 6, "advection": "centred"}
     if sixth_centred:
@@ -751,7 +853,7 @@ def run_ours(args, rank, world, local_rank):
     if FP64_INSTR_PER_POINT_STAGE and (default_scheme or sixth_centred):
         # how full the FP64 pipe is: adds and multiplies take an issue slot but count one flop
         instr = FP64_INSTR_PER_POINT_STAGE if default_scheme else FP64_INSTR_PER_POINT_STAGE_6
-        roof["fp64_issue_frac"] = instr * npts / (launch_ms * 1e-3) / (FP64_PEAK_TFLOPS * 1e12 / 2)
+        roof["fp64_issue_frac"] = instr * npts / (launch_ms * 1e-3) / FP64_PEAK_INSTR
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -787,6 +889,9 @@ def main():
         return
     if args.workload == "sphere_signal_96":
         run_tangent(args, rank, world, local_rank)
+        return
+    if args.workload == "adjoint_96":
+        run_adjoint(args, rank, world, local_rank)
         return
     if args.workload in ("calls_256", "calls_96"):
         run_calls(args, rank, world, local_rank)

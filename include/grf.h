@@ -312,6 +312,24 @@ int grf_patch_copy(const grf_patch_level* level, double* box_state, double* cons
  * `stream`. */
 int grf_halo_exchange(const grf_patch_level* level, double* const* patches, grf_stream_t stream);
 
+/* The exchange as data, for exchanges between devices or processes: every ghost point that
+ * grf_halo_exchange writes belongs to exactly one block of this plan, which copies it (all 27
+ * fields) from the interior of the owning patch. A block is a rectangular range of ghosted
+ * indices of patch `dst`, starting at (dst_i, dst_j, dst_k), that equals the range of patch `src`
+ * starting at (src_i, src_j, src_k), both of extent (ni, nj, nk) (periodic boxes: the wrapped
+ * points). The patch's own interior is not part of the plan. */
+typedef struct {
+    int dst, src;             /* patch indices a + px (b + py c) */
+    int dst_i, dst_j, dst_k;  /* first point of the block in patch dst (ghosted indices) */
+    int src_i, src_j, src_k;  /* first point in patch src (ghosted indices, inside its interior) */
+    int ni, nj, nk;           /* extent */
+} grf_halo_block;
+
+/* Host only. Writes the first min(count, max_blocks) blocks of the level's plan to `blocks`
+ * (NULL with max_blocks = 0 to query) and returns the plan's block count, or GRF_EINVAL for a bad
+ * level or arguments. Blocks are ordered by destination patch. */
+int grf_halo_plan(const grf_patch_level* level, grf_halo_block* blocks, int max_blocks);
+
 /* A halo exchange that grf_patches_rk4 calls on the patches' current buffers (a host array of
  * px py pz device pointers in grf_patch_box layouts, valid for the call only): before the first
  * step on the patch states, then after every stage on the buffers that stage wrote. It must fill
@@ -377,6 +395,55 @@ size_t grf_tlm_workspace_bytes(const grf_box* box);
 int grf_tlm_rk4(const grf_box* box, const grf_params* params, const double* dparams, double* state, double* tangents,
                 double dt, int nsteps, const grf_sphere* sphere, double* loss, void* ws, size_t ws_bytes,
                 grf_stream_t stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Reverse mode (discrete adjoint) of the same evolution and signal, with RK4-step
+ * checkpointing ("Key features": scalar waveform diagnostics -- the signal whose gradient is
+ * taken). grf_signal_forward evolves the state and stores a checkpoint every
+ * `checkpoint_every` steps; grf_adjoint_rk4 then runs backwards from them: each segment's step
+ * states are recomputed from its checkpoint, each step's stage states from its step state,
+ * and every stage is reversed by a reverse-mode re-evaluation of the pointwise map (right-hand
+ * side, Kreiss-Oliger term, stage update and enforcement) followed by the transposed stencils.
+ * The result is the exact gradient (to rounding) of
+ *     J = loss_bar * L + <state_bar_in, state_N>   (interior points, all 27 fields)
+ * with respect to the initial state's interior values and to (lambda, g2).
+ * Accepted boxes: 3 ghost layers, periodic or frozen ghosts; params: centred advection, any
+ * coupling kind, with or without backreaction. Calls on one device must not overlap in time:
+ * the tape's device pointers are held in one constant of the library, set by each call.
+ * ------------------------------------------------------------------------------------- */
+
+/* Scratch bytes of grf_signal_forward and grf_adjoint_rk4 (0 for an unsupported box):
+ * 9 + checkpoint_every state-sized buffers, 171 derivative-adjoint fields, and the reverse-mode
+ * tapes of 38,912 threads (about 6.5 GB). */
+size_t grf_adjoint_workspace_bytes(const grf_box* box, int checkpoint_every);
+
+/* Evolves `state` (device, in place, ghosts filled first) by nsteps RK4 steps exactly as
+ * grf_rk4_step does, writes the state before steps 0, c, 2c, ... (c = checkpoint_every) to
+ * `checkpoints` (device, ceil(nsteps / c) consecutive states of the box's layout) and sets
+ * `loss` (device, 1 double) to L. Synchronises `stream`. Errors: GRF_EINVAL (box, params,
+ * pointers, nsteps < 0, c < 1, or a sphere sample outside the interior), GRF_EWORKSPACE,
+ * GRF_ESINGULAR, GRF_ECUDA. */
+int grf_signal_forward(const grf_box* box, const grf_params* params, double* state, double dt, int nsteps,
+                       const grf_sphere* sphere, int checkpoint_every, double* checkpoints, double* loss, void* ws,
+                       size_t ws_bytes, grf_stream_t stream);
+
+/* Reverse sweep over the checkpoints of grf_signal_forward (same box, params, dt, nsteps,
+ * sphere and checkpoint_every). state_bar: device state, IN the cotangent of the final state's
+ * interior (zeros for L alone), OUT the gradient of J with respect to the initial state's
+ * interior values (ghost entries unused). param_bar: device, 2 doubles, OUT dJ/d lambda and
+ * dJ/d g2. loss_bar: host scalar, the cotangent of L. Deterministic (fixed summation orders).
+ * Synchronises `stream`. Errors as grf_signal_forward; GRF_EWORKSPACE also if a point's tape
+ * overflowed. */
+int grf_adjoint_rk4(const grf_box* box, const grf_params* params, const double* checkpoints, double dt, int nsteps,
+                    const grf_sphere* sphere, int checkpoint_every, double loss_bar, double* state_bar,
+                    double* param_bar, void* ws, size_t ws_bytes, grf_stream_t stream);
+
+/* out (device, 1 double) = sum over interior points of x * y for field `field` (0..26), or over
+ * all 27 fields (field = -1), in a fixed order (deterministic). ws: device, 256-byte aligned,
+ * at least 304 doubles. Asynchronous. Used for gradients with respect to parameters of the
+ * initial data (<state_bar, d state_0 / d theta>). */
+int grf_state_dot(const grf_box* box, const double* x, const double* y, int field, double* out, void* ws,
+                  size_t ws_bytes, grf_stream_t stream);
 
 /* ---------------------------------------------------------------------------------------
  * Waveform extraction on spheres ("Diagnostics": tensor and scalar gravitational waveforms).

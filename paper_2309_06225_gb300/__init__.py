@@ -67,6 +67,12 @@ class grf_patch_level(C.Structure):
     _fields_ = [("box", grf_box), ("px", C.c_int), ("py", C.c_int), ("pz", C.c_int)]
 
 
+class grf_halo_block(C.Structure):
+    _fields_ = [("dst", C.c_int), ("src", C.c_int), ("dst_i", C.c_int), ("dst_j", C.c_int), ("dst_k", C.c_int),
+                ("src_i", C.c_int), ("src_j", C.c_int), ("src_k", C.c_int), ("ni", C.c_int), ("nj", C.c_int),
+                ("nk", C.c_int)]
+
+
 # int (*)(void* ctx, const grf_patch_level*, double* const* patches, grf_stream_t)
 grf_halo_fn = C.CFUNCTYPE(C.c_int, C.c_void_p, C.POINTER(grf_patch_level), C.POINTER(C.c_void_p), C.c_void_p)
 
@@ -118,12 +124,24 @@ def lib():
         L.grf_tlm_rk4.argtypes = [B, P, C.POINTER(C.c_double), _VP, _VP, C.c_double, C.c_int, C.POINTER(grf_sphere),
                                   _VP, _VP, C.c_size_t, _VP]
         L.grf_tlm_rk4.restype = C.c_int
+        L.grf_adjoint_workspace_bytes.argtypes = [B, C.c_int]
+        L.grf_adjoint_workspace_bytes.restype = C.c_size_t
+        L.grf_signal_forward.argtypes = [B, P, _VP, C.c_double, C.c_int, C.POINTER(grf_sphere), C.c_int, _VP, _VP,
+                                         _VP, C.c_size_t, _VP]
+        L.grf_signal_forward.restype = C.c_int
+        L.grf_adjoint_rk4.argtypes = [B, P, _VP, C.c_double, C.c_int, C.POINTER(grf_sphere), C.c_int, C.c_double, _VP,
+                                      _VP, _VP, C.c_size_t, _VP]
+        L.grf_adjoint_rk4.restype = C.c_int
+        L.grf_state_dot.argtypes = [B, _VP, _VP, C.c_int, _VP, _VP, C.c_size_t, _VP]
+        L.grf_state_dot.restype = C.c_int
         L.grf_rk4_step_noalloc.argtypes = [B, P, _VP, C.c_double, C.c_int, _VP]
         L.grf_rk4_step_noalloc.restype = C.c_int
         PL, PP = C.POINTER(grf_patch_level), C.POINTER(C.c_void_p)
         L.grf_patch_box.argtypes = [PL, C.c_int, B]
         L.grf_patch_copy.argtypes = [PL, _VP, PP, C.c_int, _VP]
         L.grf_halo_exchange.argtypes = [PL, PP, _VP]
+        L.grf_halo_plan.argtypes = [PL, C.POINTER(grf_halo_block), C.c_int]
+        L.grf_halo_plan.restype = C.c_int
         L.grf_patches_workspace_bytes.argtypes = [PL]
         L.grf_patches_workspace_bytes.restype = C.c_size_t
         L.grf_patches_rk4.argtypes = [PL, P, PP, C.c_double, C.c_int, grf_halo_fn, _VP, _VP, C.c_size_t,
@@ -407,6 +425,16 @@ def grf_halo_exchange(level: grf_patch_level, patches, stream=None):
                   "grf_halo_exchange")
 
 
+def grf_halo_plan(level: grf_patch_level):
+    """The level's halo exchange as a list of grf_halo_block (host data; see include/grf.h)."""
+    n = lib().grf_halo_plan(C.byref(level), None, 0)
+    if n < 0:
+        raise GrfError(n, "grf_halo_plan")
+    arr = (grf_halo_block * max(n, 1))()
+    _check(0 if lib().grf_halo_plan(C.byref(level), arr, n) == n else GRF_EINVAL, "grf_halo_plan")
+    return list(arr)[:n]
+
+
 def grf_patches_workspace_bytes(level: grf_patch_level) -> int:
     return int(lib().grf_patches_workspace_bytes(C.byref(level)))
 
@@ -474,3 +502,44 @@ def grf_tlm_rk4(box: grf_box, params: grf_params, dparams, state, tangents, dt, 
     return _check(lib().grf_tlm_rk4(C.byref(box), C.byref(params), dp, _dev(state), _dev(tangents), float(dt),
                                     int(nsteps), C.byref(sphere), _dev(loss), _dev(ws), ws.numel(), _stream(stream)),
                   "grf_tlm_rk4")
+
+
+# ------------------------------------------------------------------------------ adjoint signal
+def grf_adjoint_workspace_bytes(box: grf_box, checkpoint_every: int) -> int:
+    return int(lib().grf_adjoint_workspace_bytes(C.byref(box), int(checkpoint_every)))
+
+
+def checkpoint_count(nsteps: int, checkpoint_every: int) -> int:
+    """States grf_signal_forward stores: one before steps 0, c, 2c, ... below nsteps."""
+    return (int(nsteps) + int(checkpoint_every) - 1) // int(checkpoint_every)
+
+
+def grf_signal_forward(box: grf_box, params: grf_params, state, dt, nsteps, sphere: grf_sphere, checkpoint_every,
+                       checkpoints, loss, ws=None, stream=None):
+    """Evolves state in place, stores checkpoints (device, checkpoint_count(...) states) and sets
+    loss (device, 1 double) to the sphere signal. See include/grf.h."""
+    if ws is None:
+        ws = alloc_workspace(grf_adjoint_workspace_bytes(box, checkpoint_every))
+    return _check(lib().grf_signal_forward(C.byref(box), C.byref(params), _dev(state), float(dt), int(nsteps),
+                                           C.byref(sphere), int(checkpoint_every), _dev(checkpoints), _dev(loss),
+                                           _dev(ws), ws.numel(), _stream(stream)), "grf_signal_forward")
+
+
+def grf_adjoint_rk4(box: grf_box, params: grf_params, checkpoints, dt, nsteps, sphere: grf_sphere, checkpoint_every,
+                    loss_bar, state_bar, param_bar, ws=None, stream=None):
+    """Reverse sweep: state_bar (device state) in = cotangent of the final state, out = gradient
+    with respect to the initial state; param_bar (device, 2 doubles) = d/d(lambda, g2). See
+    include/grf.h."""
+    if ws is None:
+        ws = alloc_workspace(grf_adjoint_workspace_bytes(box, checkpoint_every))
+    return _check(lib().grf_adjoint_rk4(C.byref(box), C.byref(params), _dev(checkpoints), float(dt), int(nsteps),
+                                        C.byref(sphere), int(checkpoint_every), float(loss_bar), _dev(state_bar),
+                                        _dev(param_bar), _dev(ws), ws.numel(), _stream(stream)), "grf_adjoint_rk4")
+
+
+def grf_state_dot(box: grf_box, x, y, field, out, ws=None, stream=None):
+    """out (device, 1 double) = interior sum of x * y over one field (or all, field = -1)."""
+    if ws is None:
+        ws = alloc_workspace(8 * 304, x.device)
+    return _check(lib().grf_state_dot(C.byref(box), _dev(x), _dev(y), int(field), _dev(out), _dev(ws), ws.numel(),
+                                      _stream(stream)), "grf_state_dot")

@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "grf.h"
@@ -183,9 +184,12 @@ Layout layout(const grf_batch_item* items, int n, const grf_batch_config* c) {
     return L;
 }
 
-// one cached executable graph (re-used when the same batch is stepped again)
+// one cached executable graph (re-used when the same batch is stepped again); the lookup, rebuild
+// and launch hold g_graph_mutex, and the key includes the device, so host threads calling
+// grf_batched_rk4 concurrently (on any devices) never launch or destroy each other's graph
 struct GraphCache {
     cudaGraphExec_t exec = nullptr;
+    int device = -1;
     cudaStream_t stream = nullptr;
     const void* ws = nullptr;
     int nsteps = -1;
@@ -194,6 +198,7 @@ struct GraphCache {
     std::vector<char> key;
 };
 GraphCache g_graph;
+std::mutex g_graph_mutex;
 
 int cuda_err(cudaError_t e) { return grf::record_cuda_error(e); }
 
@@ -344,7 +349,12 @@ int grf_batched_rk4(const grf_batch_item* items, int nitems, const grf_params* p
         // key: everything the graph's launches depend on
         std::vector<char> key(sizeof(BoxDesc) * nitems);
         std::memcpy(key.data(), hb.data(), key.size());
-        const bool hit = g_graph.exec && g_graph.stream == st && g_graph.ws == ws && g_graph.nsteps == nsteps &&
+        int device = -1;
+        e = cudaGetDevice(&device);
+        if (e != cudaSuccess) return cuda_err(e);
+        std::lock_guard<std::mutex> lock(g_graph_mutex);
+        const bool hit = g_graph.exec && g_graph.device == device && g_graph.stream == st && g_graph.ws == ws &&
+                         g_graph.nsteps == nsteps &&
                          g_graph.ntiles == L.ntiles && g_graph.tx == cfg->tile_x && g_graph.ty == cfg->tile_y &&
                          g_graph.tz == cfg->tile_z && g_graph.key == key;
         DBG("graph: cache %s", hit ? "hit" : "miss");
@@ -356,7 +366,7 @@ int grf_batched_rk4(const grf_batch_item* items, int nitems, const grf_params* p
             e = build_stage_graph(nsteps, L.ntiles, block, dboxes, dtiles, status, &g_graph.exec);
             DBG("graph: built (%s)", cudaGetErrorName(e));
             if (e != cudaSuccess) { g_graph.exec = nullptr; return cuda_err(e); }
-            g_graph.stream = st; g_graph.ws = ws; g_graph.nsteps = nsteps; g_graph.ntiles = L.ntiles;
+            g_graph.device = device; g_graph.stream = st; g_graph.ws = ws; g_graph.nsteps = nsteps; g_graph.ntiles = L.ntiles;
             g_graph.tx = cfg->tile_x; g_graph.ty = cfg->tile_y; g_graph.tz = cfg->tile_z; g_graph.key = key;
         }
         e = cudaGraphLaunch(g_graph.exec, st);

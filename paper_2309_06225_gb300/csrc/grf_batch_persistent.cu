@@ -1,6 +1,9 @@
 // The persistent variant of the batched RK4 (GRF_BATCH_PERSISTENT): one cooperative launch of
 // co-resident blocks that loop over the work list for every stage and step, separated by grid
 // barriers whose spin is bounded.
+// The stages of one launch read states that other blocks wrote before the previous grid barrier,
+// so the stencil loads must be coherent (L2), not the read-only path.
+#define GRF_COHERENT_LOADS 1
 #include "grf_batch.cuh"
 
 namespace grf {

@@ -6,6 +6,17 @@
 
 #include "grf_point.cuh"
 
+// Loads of stencil sources. By default the read-only, non-coherent path (__ldg): every kernel
+// that reads a state through these helpers leaves it unwritten for the rest of its launch. A
+// kernel that reads, in one launch, buffers that other blocks wrote earlier in the same launch
+// (the persistent batched kernel, across its grid barriers) defines GRF_COHERENT_LOADS before
+// including this header: the loads then go through L2 only (__ldcg), which is coherent.
+#ifdef GRF_COHERENT_LOADS
+#define GRF_LDG(p) __ldcg(p)
+#else
+#define GRF_LDG(p) __ldg(p)
+#endif
+
 namespace grf {
 
 struct Geom {
@@ -31,10 +42,10 @@ __device__ __forceinline__ long long gidx(const Geom& g, int i, int j, int k) { 
 // Mixed derivatives (tensor product of the first-derivative weights) are formed below as the
 // first-derivative stencil applied to rounded first derivatives.
 __device__ __forceinline__ double fd1(const double* __restrict__ u, long long p, long long s, double i12) {
-    return ((__ldg(u + p - 2 * s) - __ldg(u + p + 2 * s)) + 8.0 * (__ldg(u + p + s) - __ldg(u + p - s))) * i12;
+    return ((GRF_LDG(u + p - 2 * s) - GRF_LDG(u + p + 2 * s)) + 8.0 * (GRF_LDG(u + p + s) - GRF_LDG(u + p - s))) * i12;
 }
 __device__ __forceinline__ double fd2(const double* __restrict__ u, long long p, long long s, double u0, double i12s) {
-    return (16.0 * (__ldg(u + p + s) + __ldg(u + p - s)) - (__ldg(u + p + 2 * s) + __ldg(u + p - 2 * s)) - 30.0 * u0) * i12s;
+    return (16.0 * (GRF_LDG(u + p + s) + GRF_LDG(u + p - s)) - (GRF_LDG(u + p + 2 * s) + GRF_LDG(u + p - 2 * s)) - 30.0 * u0) * i12s;
 }
 
 __device__ __forceinline__ bool has_d2(int f) {
@@ -93,7 +104,7 @@ __device__ __forceinline__ double mixed_x_warp(const WarpRow& wr, int b, int t, 
 // scalings are explicitly rounded (__dmul_rn, never fused into a neighbouring add), so the sums
 // are those of the shuffle and shared-memory paths, whose neighbour values arrive rounded.
 __device__ __forceinline__ double fd1_rounded(const double* __restrict__ u, long long p, long long s, double i12) {
-    return __dmul_rn((__ldg(u + p - 2 * s) - __ldg(u + p + 2 * s)) + 8.0 * (__ldg(u + p + s) - __ldg(u + p - s)), i12);
+    return __dmul_rn((GRF_LDG(u + p - 2 * s) - GRF_LDG(u + p + 2 * s)) + 8.0 * (GRF_LDG(u + p + s) - GRF_LDG(u + p - s)), i12);
 }
 __device__ __forceinline__ double mixed_local(const double* __restrict__ u, long long p, long long so, long long t,
                                               double i12) {
@@ -151,20 +162,20 @@ __device__ __forceinline__ void gather(const Geom& g, const double* __restrict__
     double bet[3] = {0.0, 0.0, 0.0};
     if (LOP) {
 #pragma unroll
-        for (int d = 0; d < 3; ++d) bet[d] = __ldg(s + (F_SHIFT + d) * g.fstride + p);
+        for (int d = 0; d < 3; ++d) bet[d] = GRF_LDG(s + (F_SHIFT + d) * g.fstride + p);
     }
 #pragma unroll
     for (int f = 0; f < NFIELDS; ++f) {
         const double* u = s + f * g.fstride;
-        const double u0 = __ldg(u + p);
+        const double u0 = GRF_LDG(u + p);
         in.v[f] = u0;
         double p1[3], p2[3], d1[3], p3[3], av = 0.0;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            const double m1 = __ldg(u + p - st[d]), q1 = __ldg(u + p + st[d]);
-            const double m2 = __ldg(u + p - 2 * st[d]), q2 = __ldg(u + p + 2 * st[d]);
+            const double m1 = GRF_LDG(u + p - st[d]), q1 = GRF_LDG(u + p + st[d]);
+            const double m2 = GRF_LDG(u + p - 2 * st[d]), q2 = GRF_LDG(u + p + 2 * st[d]);
             if (LOP) {
-                const double m3 = __ldg(u + p - 3 * st[d]), q3 = __ldg(u + p + 3 * st[d]);
+                const double m3 = GRF_LDG(u + p - 3 * st[d]), q3 = GRF_LDG(u + p + 3 * st[d]);
                 p3[d] = m3 + q3;
                 const bool fw = bet[d] >= 0.0;
                 const double a1 = fw ? q1 : m1, a2 = fw ? q2 : m2, a3 = fw ? q3 : m3, b1 = fw ? m1 : q1;
@@ -196,9 +207,9 @@ __device__ __forceinline__ void gather(const Geom& g, const double* __restrict__
         }
         if (LOP) adv[f] = av;
         const double t3 = LOP ? (p3[0] + p3[1]) + p3[2]
-                              : ((__ldg(u + p - 3 * st[0]) + __ldg(u + p + 3 * st[0])) +
-                                 (__ldg(u + p - 3 * st[1]) + __ldg(u + p + 3 * st[1]))) +
-                                    (__ldg(u + p - 3 * st[2]) + __ldg(u + p + 3 * st[2]));
+                              : ((GRF_LDG(u + p - 3 * st[0]) + GRF_LDG(u + p + 3 * st[0])) +
+                                 (GRF_LDG(u + p - 3 * st[1]) + GRF_LDG(u + p + 3 * st[1]))) +
+                                    (GRF_LDG(u + p - 3 * st[2]) + GRF_LDG(u + p + 3 * st[2]));
         const double t2 = (p2[0] + p2[1]) + p2[2];
         const double t1 = (p1[0] + p1[1]) + p1[2];
         kos[f] = t3 - 6.0 * t2 + 15.0 * t1 - 60.0 * u0;
@@ -211,9 +222,9 @@ __device__ __forceinline__ double ko6(const double* __restrict__ u, long long p,
     double t[4];
 #pragma unroll
     for (int r = 1; r <= 3; ++r)
-        t[r] = ((__ldg(u + p - r * st[0]) + __ldg(u + p + r * st[0])) + (__ldg(u + p - r * st[1]) + __ldg(u + p + r * st[1]))) +
-               (__ldg(u + p - r * st[2]) + __ldg(u + p + r * st[2]));
-    return t[3] - 6.0 * t[2] + 15.0 * t[1] - 60.0 * __ldg(u + p);
+        t[r] = ((GRF_LDG(u + p - r * st[0]) + GRF_LDG(u + p + r * st[0])) + (GRF_LDG(u + p - r * st[1]) + GRF_LDG(u + p + r * st[1]))) +
+               (GRF_LDG(u + p - r * st[2]) + GRF_LDG(u + p + r * st[2]));
+    return t[3] - 6.0 * t[2] + 15.0 * t[1] - 60.0 * GRF_LDG(u + p);
 }
 
 __device__ __forceinline__ bool interior_thread(const Geom& g, int& i, int& j, int& k) {

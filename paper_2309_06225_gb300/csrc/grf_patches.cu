@@ -230,6 +230,65 @@ int grf_patch_copy(const grf_patch_level* level, double* box_state, double* cons
     return launch_status();
 }
 
+// The halo exchange as data. Along one axis, the ghosted index range [0, n_a + 6) of patch a maps
+// to the box's interior point x = off[a] + g - 3 (wrapped in a periodic box; outside a frozen box
+// there is nothing to copy), owned by patch o with index x - off[o] + 3. Runs of consecutive g
+// with the same owner and consecutive source indices are the axis's segments; a block of the
+// plan is one segment per axis, except the patch's own interior (the identity on all three).
+namespace {
+struct AxisRun { int g0, len, owner, s0; bool self; };
+
+std::vector<AxisRun> axis_runs(const PatchTable& t, int d, int a) {
+    std::vector<AxisRun> runs;
+    const int n = t.off[d][a + 1] - t.off[d][a], N = t.n[d];
+    for (int g = 0; g < n + 2 * NG; ++g) {
+        int x = t.off[d][a] + g - NG;
+        if (x < 0 || x >= N) {
+            if (!t.periodic) continue;
+            x = (x % N + N) % N;
+        }
+        int o = 0;
+        while (o + 1 < t.p[d] && t.off[d][o + 1] <= x) ++o;
+        const int sg = x - t.off[d][o] + NG;
+        const bool self = (o == a && sg == g);
+        if (!runs.empty()) {
+            AxisRun& r = runs.back();
+            if (r.owner == o && r.self == self && r.g0 + r.len == g && r.s0 + r.len == sg) {
+                ++r.len;
+                continue;
+            }
+        }
+        runs.push_back({g, 1, o, sg, self});
+    }
+    return runs;
+}
+}  // namespace
+
+int grf_halo_plan(const grf_patch_level* level, grf_halo_block* blocks, int max_blocks) {
+    if (!level_ok(level) || max_blocks < 0 || (max_blocks > 0 && !blocks)) return GRF_EINVAL;
+    const PatchTable t = table_of(level, nullptr);
+    int count = 0;
+    for (int q = 0; q < npatches(level); ++q) {
+        const int a = q % t.p[0], b = (q / t.p[0]) % t.p[1], c = q / (t.p[0] * t.p[1]);
+        const std::vector<AxisRun> rx = axis_runs(t, 0, a), ry = axis_runs(t, 1, b), rz = axis_runs(t, 2, c);
+        for (const AxisRun& z : rz)
+            for (const AxisRun& y : ry)
+                for (const AxisRun& x : rx) {
+                    if (x.self && y.self && z.self) continue;
+                    if (count < max_blocks) {
+                        grf_halo_block& k = blocks[count];
+                        k.dst = q;
+                        k.src = x.owner + t.p[0] * (y.owner + t.p[1] * z.owner);
+                        k.dst_i = x.g0; k.dst_j = y.g0; k.dst_k = z.g0;
+                        k.src_i = x.s0; k.src_j = y.s0; k.src_k = z.s0;
+                        k.ni = x.len; k.nj = y.len; k.nk = z.len;
+                    }
+                    ++count;
+                }
+    }
+    return count;
+}
+
 int grf_halo_exchange(const grf_patch_level* level, double* const* patches, grf_stream_t stream) {
     if (!level_ok(level) || !ptrs_ok(level, patches)) return GRF_EINVAL;
     const PatchTable t = table_of(level, patches);

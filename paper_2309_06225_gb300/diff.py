@@ -1,16 +1,25 @@
-"""Differentiable sphere-averaged scalar signal (torch.autograd.Function over grf_tlm_rk4).
+"""Differentiable sphere-averaged scalar signal, as torch.autograd.Functions.
 
 theta = (lambda, g2, A): the Gauss-Bonnet coupling, the X^2 coupling and the amplitude of the
 initial scalar profile. The caller supplies the initial state at the current A together with
 its derivative with respect to A (for phi = A f(x) that is the state with phi = f and every
-other field zero). The forward pass runs the tangent-linear evolution (value and the three
-derivatives together, in one pass over the steps) and keeps dL/dtheta for backward.
+other field zero).
+
+SignalAdjoint (reverse mode): forward evolves the state with grf_signal_forward, storing a
+checkpoint every `checkpoint_every` RK4 steps; backward runs the reverse sweep grf_adjoint_rk4
+from those checkpoints (recomputing each segment and each step's stages) and returns
+grad_out * dL/dtheta, the A component as <d L/d state_0, d state_0/dA> (grf_state_dot).
+
+SphereSignal (forward mode): the tangent-linear evolution grf_tlm_rk4 gives L and the three
+derivatives in one pass; backward returns the stored gradient. It is the cross-check of the
+reverse sweep.
 """
 from __future__ import annotations
 
 import torch
 
-from . import (alloc_state, alloc_workspace, grf_params, grf_sphere, grf_tlm_rk4, grf_tlm_workspace_bytes)
+from . import (alloc_state, alloc_workspace, checkpoint_count, grf_adjoint_rk4, grf_adjoint_workspace_bytes,
+               grf_params, grf_signal_forward, grf_sphere, grf_state_dot, grf_tlm_rk4, grf_tlm_workspace_bytes)
 
 
 def _with_couplings(params: grf_params, lam, g2) -> grf_params:
@@ -47,13 +56,45 @@ class SphereSignal(torch.autograd.Function):
     @staticmethod
     def forward(ctx, theta, box, params, state0, dstate0_dA, dt, nsteps, sphere):
         L, grad = sphere_signal_and_grad(box, params, theta.detach().cpu(), state0, dstate0_dA, dt, nsteps, sphere)
-        ctx.save_for_backward(grad.to(theta.dtype))
-        return torch.tensor(L, dtype=theta.dtype)
+        ctx.save_for_backward(grad.to(device=theta.device, dtype=theta.dtype))
+        return torch.tensor(L, dtype=theta.dtype, device=theta.device)
 
     @staticmethod
     def backward(ctx, grad_out):
         (grad,) = ctx.saved_tensors
         return grad_out * grad, None, None, None, None, None, None, None
+
+
+class SignalAdjoint(torch.autograd.Function):
+    """L(theta) with theta = (lambda, g2, A); backward runs the reverse sweep over the forward
+    pass's checkpoints."""
+
+    @staticmethod
+    def forward(ctx, theta, box, params, state0, dstate0_dA, dt, nsteps, sphere, checkpoint_every=20):
+        if str(theta.dtype) != "torch.float64":
+            raise TypeError("theta must be float64")
+        lam, g2, _ = (float(x) for x in theta.detach().cpu())
+        p = _with_couplings(params, lam, g2)
+        state = state0.clone()
+        ck = torch.empty((max(checkpoint_count(nsteps, checkpoint_every), 1),) + tuple(state.shape),
+                         dtype=torch.float64, device=state.device)
+        loss = torch.zeros(1, dtype=torch.float64, device=state.device)
+        ws = alloc_workspace(grf_adjoint_workspace_bytes(box, checkpoint_every), state.device)
+        grf_signal_forward(box, p, state, dt, nsteps, sphere, checkpoint_every, ck, loss, ws=ws)
+        ctx.saved = (box, p, ck, dstate0_dA, float(dt), int(nsteps), sphere, int(checkpoint_every), ws)
+        return loss[0].to(device=theta.device)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        box, p, ck, dstate0_dA, dt, nsteps, sphere, ce, ws = ctx.saved
+        sbar = torch.zeros_like(dstate0_dA)
+        pbar = torch.zeros(2, dtype=torch.float64, device=sbar.device)
+        grf_adjoint_rk4(box, p, ck, dt, nsteps, sphere, ce, float(grad_out), sbar, pbar, ws=ws)
+        dA = torch.zeros(1, dtype=torch.float64, device=sbar.device)
+        grf_state_dot(box, sbar, dstate0_dA, -1, dA)
+        grad = torch.cat([pbar, dA]).to(device=grad_out.device)
+        ctx.saved = None
+        return grad, None, None, None, None, None, None, None, None
 
 
 def sphere(radius=6.0, centre=(0.0, 0.0, 0.0)) -> grf_sphere:

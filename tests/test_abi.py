@@ -150,3 +150,28 @@ def test_mirror_sommerfeld_validation_without_gpu(grf):
     assert L.grf_rk4_step_host(C.byref(b), C.byref(p), fake, None, fake, 0.1, 1, fake, 1 << 40, None) == grf.GRF_EINVAL
     assert grf.grf_workspace_bytes(grf.make_box(2, 8, 8, 0.25, bc=grf.GRF_BC_REFLECT_LOW_SOMMERFELD),
                                    grf.GRF_OP_RK4) == 0
+
+
+def test_adjoint_validation_without_gpu(grf):
+    """The reverse sweep accepts 3-ghost periodic / frozen boxes with centred advection; other
+    boxes have no workspace size and every bad argument is rejected before any CUDA call."""
+    b = grf.make_box(16, 16, 16, 0.5)
+    assert grf.grf_adjoint_workspace_bytes(b, 20) > 0
+    assert grf.grf_adjoint_workspace_bytes(b, 0) == 0
+    assert grf.grf_adjoint_workspace_bytes(grf.make_box(16, 16, 16, 0.5, ng=4), 20) == 0
+    assert grf.grf_adjoint_workspace_bytes(grf.make_box(16, 16, 16, 0.5, bc=grf.GRF_BC_SOMMERFELD), 20) == 0
+    import grf_inputs as gi
+    L = grf.lib()
+    sph = grf.grf_sphere(2.0, 0.0, 0.0, 0.0)
+    lop = grf.params_like(gi.Params(advection=1))
+    ok = grf.params_like(gi.Params())
+    fake = C.c_void_p(256)  # never dereferenced: validation fails first
+    assert L.grf_adjoint_rk4(C.byref(b), C.byref(lop), fake, 0.1, 4, C.byref(sph), 2, 1.0, fake, fake, fake,
+                             1 << 40, None) == grf.GRF_EINVAL
+    assert L.grf_adjoint_rk4(C.byref(b), C.byref(ok), fake, 0.1, 4, C.byref(sph), 0, 1.0, fake, fake, fake,
+                             1 << 40, None) == grf.GRF_EINVAL
+    bad = grf.grf_sphere(-1.0, 0.0, 0.0, 0.0)
+    assert L.grf_signal_forward(C.byref(b), C.byref(ok), fake, 0.1, 4, C.byref(bad), 2, fake, fake, fake, 1 << 40,
+                                None) == grf.GRF_EINVAL
+    assert L.grf_adjoint_rk4(C.byref(b), C.byref(ok), fake, 0.1, 4, C.byref(sph), 2, 1.0, fake, fake, None, 0,
+                             None) == grf.GRF_EWORKSPACE

@@ -193,3 +193,29 @@ def test_amr_like_and_sweep_generators_shapes():
     bx, ps = gi.coupling_sweep_boxes()
     assert len(bx) == 32 and all(b.nx == 64 for b in bx)
     assert all(0 <= p.lam <= 0.1 and 0 <= p.g2 <= 0.05 for p in ps)
+
+
+@pytest.mark.parametrize("n,tile", [(8, (32, 4, 1)), (16, (32, 4, 1)), (12, (16, 4, 2))])
+def test_persistent_launch_small_box_many_steps_equals_single_box_path(g, n, tile):
+    """One small periodic box (its whole working set fits in the SMs' L1) advanced 20 steps in one
+    persistent launch: every stage reads states that other blocks wrote before the previous grid
+    barrier, so stale non-coherent cache lines would show as differing bits. The result must equal
+    grf_rk4_step's, bit for bit."""
+    import torch
+    box = gi.cube_box(n, -1.5, 1.5)
+    params = gi.Params(lam=0.2, g2=0.1, beta_kind=1)
+    s0 = gi.random_perturbed_state(box, 7, base=gi.single_puncture(box, amp=0.05), eps=2e-2)
+    b = g.box_like(box)
+    p = g.params_like(params)
+    dt = 0.25 * box.dx
+    nsteps = 20
+    ref = g.to_device(s0, b)
+    g.grf_rk4_step(b, p, ref, dt, nsteps)
+    gp = g.params_array([p])
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        dev = [g.to_device(s0, b)]
+        items = g.batch_items([b], dev, [0], [dt])
+        g.grf_batched_rk4(items, gp, nsteps, g.batch_config(g.GRF_BATCH_PERSISTENT, tile), stream=stream)
+    stream.synchronize()
+    assert np.array_equal(g.to_host(dev[0], b), g.to_host(ref, b))

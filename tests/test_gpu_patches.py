@@ -269,3 +269,25 @@ def test_exchange_that_raises(g):
         g.grf_patches_rk4(L, g.params_like(params), patches, dt, 1, exchange=exchange)
     import torch
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("n,p,bc", [((12, 12, 12), (2, 2, 2), gi.BC_PERIODIC), ((8, 8, 8), (4, 4, 4), gi.BC_PERIODIC),
+                                    ((10, 7, 9), (3, 1, 2), gi.BC_PERIODIC), ((9, 8, 7), (2, 3, 1), gi.BC_FROZEN)])
+def test_device_exchange_equals_the_plan(g, n, p, bc):
+    """The built-in device exchange and the exchange plan (grf_halo_plan, applied on the host)
+    write the same ghost points with the same values, bit for bit."""
+    from paper_2309_06225_gb300 import halo
+    box = gi.Box(*n, 0.3, -1.0, -1.0, -1.0, bc=bc)
+    level = g.patch_level(g.box_like(box), *p)
+    rng = np.random.default_rng(3)
+    host = []
+    for q in range(p[0] * p[1] * p[2]):
+        pb = g.grf_patch_box(level, q)
+        host.append(rng.normal(size=(27, pb.nz + 6, pb.ny + 6, pb.pitch)))
+    import torch
+    dev = [torch.from_numpy(a.copy()).cuda() for a in host]
+    g.grf_halo_exchange(level, dev)
+    torch.cuda.synchronize()
+    halo.apply_plan(g.grf_halo_plan(level), host)
+    for q in range(len(host)):
+        assert np.array_equal(dev[q].cpu().numpy(), host[q]), q
