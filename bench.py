@@ -40,8 +40,8 @@ BYTES_PER_POINT_UPDATE = 216 * (3 + 5 + 5 + 4)
 # Per interior point and stage launch, from an ncu capture of the stage kernel on the 96^3 box
 # (mean of stages 0 and 1): dram__bytes_read.sum + dram__bytes_write.sum, and the FP64 thread
 # instructions (dadd + dmul + dfma). None when the kernel changed since the capture.
-TRAFFIC_BYTES_PER_POINT_STAGE = None
-FP64_INSTR_PER_POINT_STAGE = None
+TRAFFIC_BYTES_PER_POINT_STAGE = 12773
+FP64_INSTR_PER_POINT_STAGE = 4196
 # the tangent-linear (dual-number) stage kernel's FP64 instructions per point-stage (same kind of capture)
 TLM_FP64_INSTR_PER_POINT_STAGE = 28826
 # the 6th-order stage kernel with centred advection (same kind of capture)
@@ -65,6 +65,15 @@ def fp64_peak():
 
 
 FP64_PEAK_TFLOPS, FP64_PEAK_INSTR, FP64_PEAK_SOURCE = fp64_peak()
+# The FP64 pipe's issue ceiling: 2 thread-instructions per SM per clock (ncu's peak_sustained of
+# the DFMA/DADD/DMUL thread-instruction counters, 304 per clock over 152 SMs).
+FP64_PIPE_INSTR_PER_SM_CLK = 2
+GB300_SMS = 152
+
+
+def fp64_issue_ceiling(sm_mhz):
+    """FP64 thread-instructions per second the pipe can issue at the given SM clock."""
+    return FP64_PIPE_INSTR_PER_SM_CLK * GB300_SMS * sm_mhz * 1e6
 
 
 def measured_hbm_gbs():
@@ -193,6 +202,7 @@ def run_calls(args, rank, world, local_rank):
         "grf_constraints": lambda: grf.grf_constraints(b, p, state, out4, norms=False),
         "grf_energy_densities": lambda: grf.grf_energy_densities(b, p, state, out3),
         "grf_weyl_psi4": lambda: grf.grf_weyl_psi4(b, p, state, out2),
+        "grf_hyperbolicity": lambda: grf.grf_hyperbolicity(b, p, state, out3),
         # the scalar waveform: spin-0 modes of phi up to l = 8 on a sphere of radius 0.75 L/2
         "grf_extract_modes": lambda: grf.grf_extract_modes(b, state[25], None, 0, 0.375 * box.nx * box.dx,
                                                            (0.0, 0.0, 0.0), 32, 64, 8, ws=ews),
@@ -233,7 +243,7 @@ def run_calls(args, rank, world, local_rank):
             rec["roofline"] = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                                "frac": tf / FP64_PEAK_TFLOPS, "flop_per_point": flop_rhs,
                                "peak_source": FP64_PEAK_SOURCE}
-        else:  # constraints, densities and Psi_4 use the RHS's gather and pointwise algebra
+        else:  # constraints, densities, Psi_4 and the hyperbolicity diagnostics use the RHS's gather and algebra
             rec["roofline"] = None
             rec["note"] = "FP64-bound like grf_rhs; its flop count is a subset of the RHS and is not counted"
         out[name] = rec
@@ -245,7 +255,7 @@ def run_calls(args, rank, world, local_rank):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "grid": [box.nx, box.ny, box.nz],
                        "l2": "inputs larger than L2 (no flush needed)"},
-            "gpu_launches": 12 * args.steps, "calls": out, "clocks": clk, "status": {"solve": status},
+            "gpu_launches": 13 * args.steps, "calls": out, "clocks": clk, "status": {"solve": status},
             "roofline": out["grf_rhs"]["roofline"], "e2e": None, "cpu_baseline": None}
     print(json.dumps(line), flush=True)
 
@@ -308,10 +318,11 @@ def run_tangent(args, rank, world, local_rank):
     # FP64-bound like the plain stage: the dual-number stage's FP64 instruction count (ncu, 96^3)
     # against the pipe's issue rate
     stage_ms = ms_t / (4 * args.steps)
-    issue = TLM_FP64_INSTR_PER_POINT_STAGE * npts / (stage_ms * 1e-3) / FP64_PEAK_INSTR
+    issue = TLM_FP64_INSTR_PER_POINT_STAGE * npts / (stage_ms * 1e-3) / fp64_issue_ceiling(2070.0)
     out["roofline"] = {"bound": "alu", "unit": "FP64 instructions/s", "kernel": "tlm_stage_kernel",
                        "achieved": TLM_FP64_INSTR_PER_POINT_STAGE * npts / (stage_ms * 1e-3),
-                       "peak": FP64_PEAK_INSTR, "frac": issue, "peak_source": FP64_PEAK_SOURCE,
+                       "peak": fp64_issue_ceiling(2070.0), "frac": issue,
+                       "peak_source": "2 FP64 instructions per SM per clock x 152 SMs x 2070 MHz",
                        "fp64_instr_per_point_stage": TLM_FP64_INSTR_PER_POINT_STAGE, "traffic": None}
     print(json.dumps(out), flush=True)
 
@@ -853,7 +864,13 @@ def run_ours(args, rank, world, local_rank):
     if FP64_INSTR_PER_POINT_STAGE and (default_scheme or sixth_centred):
         # how full the FP64 pipe is: adds and multiplies take an issue slot but count one flop
         instr = FP64_INSTR_PER_POINT_STAGE if default_scheme else FP64_INSTR_PER_POINT_STAGE_6
-        roof["fp64_issue_frac"] = instr * npts / (launch_ms * 1e-3) / FP64_PEAK_INSTR
+        rate = instr * npts / (launch_ms * 1e-3)
+        sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+        roof["fp64_issue_frac"] = rate / fp64_issue_ceiling(sm_mhz)
+        roof["fp64_issue"] = {"instr_per_point_stage": instr, "instr_per_s": rate,
+                              "ceiling": fp64_issue_ceiling(sm_mhz),
+                              "ceiling_source": f"2 per SM per clock x 152 SMs x {sm_mhz:.0f} MHz (sampled)",
+                              "vs_measured_chains": rate / FP64_PEAK_INSTR}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",

@@ -9,7 +9,8 @@ extern "C" {
 #endif
 /* Runs `blocks` x `threads` threads, each advancing `chains` (4, 8 or 16) independent chains of
  * FP64 instructions for `iters` iterations; kind 0: DFMA, 1: DADD, 2: DMUL, 3: the mix
- * DADD : DMUL : DFMA = 1 : 1 : 2. One untimed launch, then `launches` back-to-back launches timed
+ * DADD : DMUL : DFMA = 1 : 1 : 2, 4: DFMA with per-chain operand registers, 5: DFMA with an
+ * integer multiply-add beside each. One untimed launch, then `launches` back-to-back launches timed
  * together with CUDA events on `stream`. FP64 instructions executed in the timed region:
  * launches * blocks * threads * chains * iters. out_dev: device buffer of blocks * threads
  * doubles (keeps the chains live). *ms_out (host): the timed duration in milliseconds.

@@ -68,6 +68,8 @@ def lib():
         L.orc_point_psi4.argtypes = [C.POINTER(OrcParams), _P, _P, _P, _P, _P]
         L.orc_psi4.argtypes = [C.POINTER(OrcBox), C.POINTER(OrcParams), _P, _P]
         L.orc_phys_sources_psi4.argtypes = [C.POINTER(OrcParams), _P, _P, C.c_double, _P, _P]
+        L.orc_point_hyperbolicity.argtypes = [C.POINTER(OrcParams), _P, _P, _P, _P]
+        L.orc_hyperbolicity.argtypes = [C.POINTER(OrcBox), C.POINTER(OrcParams), _P, _P]
         L.orc_rk4_signal.argtypes = [C.POINTER(OrcBox), C.POINTER(OrcParams), _P, C.c_double, C.c_int, _P, _P]
         L.orc_rk4_signal.restype = C.c_int
         _lib = L
@@ -274,6 +276,23 @@ def phys_psi4(p, phys, u6, w, xyz):
     out = np.zeros(21)
     lib().orc_phys_sources_psi4(C.byref(params(p)), _ptr(phys), _ptr(u6), float(w), _ptr(xyz), _ptr(out))
     return complex(out[19], out[20])
+
+
+def point_hyperbolicity(p, v, d1, d2):
+    """(det M of the coupled system, det(g_eff)/det(g), -g_eff^nn) at one point."""
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    d1 = np.ascontiguousarray(d1, dtype=np.float64)
+    d2 = np.ascontiguousarray(d2, dtype=np.float64)
+    out = np.zeros(3)
+    lib().orc_point_hyperbolicity(C.byref(params(p)), _ptr(v), _ptr(d1), _ptr(d2), _ptr(out))
+    return out
+
+
+def hyperbolicity(b, p, s):
+    """The three hyperbolicity diagnostics at every interior point: [3, nz, ny, nx]."""
+    out = np.zeros((3, b.nz, b.ny, b.nx))
+    lib().orc_hyperbolicity(C.byref(box(b)), C.byref(params(p)), _ptr(np.ascontiguousarray(s)), _ptr(out))
+    return out
 
 
 _tlm = None

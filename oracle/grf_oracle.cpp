@@ -416,6 +416,27 @@ void orc_energy_densities(const orc_box* b, const orc_params* P, const double* s
             }
 }
 
+// Hyperbolicity diagnostics at one point (point_hyperbolicity) and at every interior point:
+// out[3][nz][ny][nx] (the ghosts of s must be valid).
+void orc_point_hyperbolicity(const orc_params* P, const double* v, const double* d1, const double* d2, double* out3) {
+    point_hyperbolicity(prm_of(*P), v, d1, d2, out3);
+}
+
+void orc_hyperbolicity(const orc_box* b, const orc_params* P, const double* s, double* out) {
+    Grid g(*b);
+    const long long npt = (long long)b->nx * b->ny * b->nz;
+#pragma omp parallel for collapse(2)
+    for (int k = 0; k < b->nz; ++k)
+        for (int j = 0; j < b->ny; ++j)
+            for (int i = 0; i < b->nx; ++i) {
+                double v[NF], d1[NF * 3], d2[NF * 6], o[3];
+                point_derivs(g, s, b->dx, i + g.ng, j + g.ng, k + g.ng, v, d1, d2);
+                point_hyperbolicity(prm_of(*P), v, d1, d2, o);
+                long long p = ((long long)k * b->ny + j) * b->nx + i;
+                for (int m = 0; m < 3; ++m) out[m * npt + p] = o[m];
+            }
+}
+
 void orc_constraints(const orc_box* b, const orc_params* P, const double* s, double* out) {
     Grid g(*b);
     const long long npt = (long long)b->nx * b->ny * b->nz;

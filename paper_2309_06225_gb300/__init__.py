@@ -117,6 +117,8 @@ def lib():
         L.grf_tlm_workspace_bytes.argtypes = [B]
         L.grf_tlm_workspace_bytes.restype = C.c_size_t
         L.grf_weyl_psi4.argtypes = [B, P, _VP, _VP, _VP]
+        L.grf_hyperbolicity.argtypes = [B, P, _VP, _VP, _VP]
+        L.grf_hyperbolicity.restype = C.c_int
         L.grf_extract_workspace_bytes.argtypes = [C.c_int, C.c_int]
         L.grf_extract_workspace_bytes.restype = C.c_size_t
         L.grf_extract_modes.argtypes = [B, _VP, _VP, C.c_int, C.POINTER(grf_sphere), C.c_int, C.c_int, C.c_int,
@@ -302,6 +304,13 @@ def grf_energy_densities(box: grf_box, params: grf_params, state, out3, stream=N
     """8 pi rho of the X, g2 X^2 and Gauss-Bonnet terms into out3 (3 fields, state layout)."""
     return _check(lib().grf_energy_densities(C.byref(box), C.byref(params), _dev(state), _dev(out3),
                                              _stream(stream)), "grf_energy_densities")
+
+
+def grf_hyperbolicity(box: grf_box, params: grf_params, state, out3, stream=None):
+    """det M of the coupled system, det(g_eff)/det(g) and -g_eff^nn at the interior points
+    (out3: device, 3 fields in the state's layout). See include/grf.h."""
+    return _check(lib().grf_hyperbolicity(C.byref(box), C.byref(params), _dev(state), _dev(out3), _stream(stream)),
+                  "grf_hyperbolicity")
 
 
 def grf_weyl_psi4(box: grf_box, params: grf_params, state, out2, stream=None):

@@ -21,13 +21,14 @@ def build(force=False, verbose=False):
     return LIB
 
 
-KINDS = {0: "dfma", 1: "dadd", 2: "dmul", 3: "mix 1:1:2"}
+KINDS = {0: "dfma", 1: "dadd", 2: "dmul", 3: "mix 1:1:2", 4: "dfma, per-chain operands", 5: "dfma + integer"}
 
 
 def measure(target_ms=150.0, repeats=10, sample_clocks=True):
     """Measured FP64 throughput on the current CUDA device.
 
-    Sweeps the instruction kind (DFMA, DADD, DMUL, and the DADD:DMUL:DFMA = 1:1:2 mix), the
+    Sweeps the instruction kind (DFMA, DADD, DMUL, the DADD:DMUL:DFMA = 1:1:2 mix, DFMA with
+    per-chain operands, DFMA beside integer work), the
     chains per thread (4, 8, 16) and the resident blocks per SM (2, 4, 8 of 256 threads). Each
     configuration is sized to about `target_ms` of back-to-back launches, timed `repeats` times;
     its best time counts. nvidia-smi samples the SM clock meanwhile. Returns a dict with the best
@@ -56,7 +57,7 @@ def measure(target_ms=150.0, repeats=10, sample_clocks=True):
         except OSError:
             smi = None
     results = []
-    for kind in (0, 1, 2, 3):
+    for kind in (0, 1, 2, 3, 4, 5):
         for chains in (4, 8, 16):
             for per_sm in (2, 4, 8):
                 blocks = nsm * per_sm
@@ -71,7 +72,7 @@ def measure(target_ms=150.0, repeats=10, sample_clocks=True):
                     assert rc == 0, rc
                     best = min(best, ms.value)
                 instr = float(launches) * blocks * threads * chains * iters
-                flops_per_instr = {0: 2.0, 1: 1.0, 2: 1.0, 3: 1.5}[kind]
+                flops_per_instr = {0: 2.0, 1: 1.0, 2: 1.0, 3: 1.5, 4: 2.0, 5: 2.0}[kind]
                 results.append({"kind": KINDS[kind], "chains": chains, "blocks_per_sm": per_sm, "threads": threads,
                                 "launches": launches, "ms": best, "instr_per_s": instr / (best * 1e-3),
                                 "flops_per_s": flops_per_instr * instr / (best * 1e-3)})

@@ -11,14 +11,15 @@ namespace grf {
 // three scalar terms) are each written when non-null.
 // ORD = 4: block gather mode (as rhs_kernel); ORD = 6: the 6th-order per-thread gather.
 // psi4 (2 fields, re and im) receives the Weyl scalar with the triad about the origin; o = the
-// coordinates of interior point (0, 0, 0). PSI4 = 1 compiles that output in (it needs the solved
-// d_t K_ij); with PSI4 = 0 the compiler drops the coupled solve, which H, M_i and the densities do
-// not use.
+// coordinates of interior point (0, 0, 0); hyp (3 fields) the hyperbolicity diagnostics of the
+// coupled system (PointExtraT::hyp). PSI4 = 1 compiles those outputs in (they need the assembled
+// or solved coupled system); with PSI4 = 0 the compiler drops the coupled solve, which H, M_i and
+// the densities do not use.
 template <int ORD, int PSI4>
 __global__ void __launch_bounds__(128) constraints_kernel(Geom g, Coeffs c, const double* __restrict__ s,
                                                           double* __restrict__ out4, double* __restrict__ part,
                                                           double* __restrict__ dens, double* __restrict__ psi4,
-                                                          double3 o) {
+                                                          double3 o, double* __restrict__ hyp) {
     // blocks of (32, 4, 1); every thread stays to the reduction
     __shared__ double red[8][128];
     const int lane = threadIdx.x;
@@ -52,6 +53,7 @@ __global__ void __launch_bounds__(128) constraints_kernel(Geom g, Coeffs c, cons
             ex.xyz[1] = o.y + j * g.dx;
             ex.xyz[2] = o.z + k * g.dx;
         }
+        if (PSI4 && hyp) ex.want_hyp = 1;
         bool ok = true;
         point_rhs<double>(c, in, r, &ex, ok);
         vals[0] = ex.ham;
@@ -66,6 +68,8 @@ __global__ void __launch_bounds__(128) constraints_kernel(Geom g, Coeffs c, cons
             psi4[p] = ex.psi4[0];
             psi4[g.fstride + p] = ex.psi4[1];
         }
+        if (PSI4 && hyp)
+            for (int m = 0; m < 3; ++m) hyp[m * g.fstride + p] = ex.hyp[m];
     }
     const int t = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
     for (int m = 0; m < 4; ++m) {

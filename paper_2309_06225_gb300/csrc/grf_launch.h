@@ -28,11 +28,13 @@ void launch_stage6_lopsided(int stage, dim3 grid, dim3 block, cudaStream_t st, c
 void launch_rhs6(dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c, const double* s, double* rhs,
                  double ko, int* status);
 void launch_constraints6(dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c, const double* s,
-                         double* out4, double* part, double* dens, double* psi4, double3 origin);
+                         double* out4, double* part, double* dens, double* psi4, double3 origin,
+                         double* hyp = nullptr);
 void launch_rhs(dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c, const double* s, double* rhs,
                 double ko, int* status);
 void launch_constraints(dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c, const double* s,
-                        double* out4, double* part, double* dens, double* psi4, double3 origin);
+                        double* out4, double* part, double* dens, double* psi4, double3 origin,
+                         double* hyp = nullptr);
 // Outer boundaries (grf_boundary.cu): the extrapolation fill of all ghosts of s, and the
 // Sommerfeld ghost update of one RK4 stage (stage 0..3) or, with stage -1, the ghosts' right-hand
 // side written to out (a.src the state).

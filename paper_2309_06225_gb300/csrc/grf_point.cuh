@@ -92,6 +92,17 @@ struct PointExtraT {
     int want_psi4 = 0;
     double xyz[3];
     T psi4[2];
+    // Hyperbolicity diagnostics (double instances only), computed when want_hyp is set:
+    //   hyp[0] = det M of the coupled system for (d_t K_ij, d_t Pi), normalised so that each
+    //            unknown's own coefficient is 1 (M = identity without coupling); where it
+    //            vanishes the equations no longer determine the time derivatives;
+    //   hyp[1] = det(g_eff^ab) / det(g^ab) of the scalar equation's principal symbol
+    //            g_eff^ab = (1 + 2 g2 X) g^ab - 2 g2 d^a phi d^b phi; by the matrix determinant
+    //            lemma (1 + 2 g2 X)^3 (1 + 6 g2 X);
+    //   hyp[2] = -g_eff^nn = 1 + 2 g2 X + 2 g2 Pi^2 (the coefficient of d_t Pi; the normal is
+    //            timelike for the scalar's characteristic cone while it is positive).
+    int want_hyp = 0;
+    double hyp[3];
 };
 using PointExtra = PointExtraT<double>;
 
@@ -144,6 +155,35 @@ __device__ __forceinline__ double abs_max7(const double M[7][8]) {
     return __longlong_as_double(m);
 }
 #endif
+
+// Determinant of the 7x7 block of M (a copy, Gaussian elimination with partial pivoting and the
+// sign of each row exchange). Diagnostics only.
+GRF_HD double det7(const double M[7][8]) {
+    double A[7][7];
+    for (int i = 0; i < 7; ++i)
+        for (int j = 0; j < 7; ++j) A[i][j] = M[i][j];
+    double det = 1.0;
+    for (int k = 0; k < 7; ++k) {
+        int piv = k;
+        for (int i = k + 1; i < 7; ++i)
+            if (fabs(A[i][k]) > fabs(A[piv][k])) piv = i;
+        if (A[piv][k] == 0.0) return 0.0;
+        if (piv != k) {
+            for (int j = 0; j < 7; ++j) {
+                const double t = A[k][j];
+                A[k][j] = A[piv][j];
+                A[piv][j] = t;
+            }
+            det = -det;
+        }
+        det *= A[k][k];
+        for (int i = k + 1; i < 7; ++i) {
+            const double f = A[i][k] / A[k][k];
+            for (int j = k + 1; j < 7; ++j) A[i][j] -= f * A[k][j];
+        }
+    }
+    return det;
+}
 
 // 7x7 LU with partial pivoting (row swaps by compare-and-exchange, so every index stays a
 // compile-time constant and the matrix stays in registers); the pivot rows are not normalised,
@@ -855,6 +895,13 @@ GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS]
         }
         const T src = fma(fX, trH, fma(4.0 * g2 * Pi, Hnd, fma(-2.0 * g2, Hdd, b1 * L0)));
         Msys[6][7] = fma(al * iD, src, bdPi + dadp);
+        if constexpr (std::is_same<T, double>::value) {
+            if (extra && extra->want_hyp) {
+                extra->hyp[0] = det7(Msys);
+                extra->hyp[1] = fX * fX * fX * fma(6.0 * g2, X, 1.0);
+                extra->hyp[2] = Dphi;
+            }
+        }
     }
     GRF_SECTION(16);
     ok = solve7(Msys);

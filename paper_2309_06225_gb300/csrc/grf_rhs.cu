@@ -40,9 +40,9 @@ void launch_rhs(dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coe
     else rhs_kernel<0><<<grid, block, 0, st>>>(g, c, s, rhs, ko, status);
 }
 void launch_constraints(dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c, const double* s,
-                        double* out4, double* part, double* dens, double* psi4, double3 origin) {
-    if (g.ng == NG6) launch_constraints6(grid, block, st, g, c, s, out4, part, dens, psi4, origin);
-    else if (psi4) constraints_kernel<4, 1><<<grid, block, 0, st>>>(g, c, s, out4, part, dens, psi4, origin);
-    else constraints_kernel<4, 0><<<grid, block, 0, st>>>(g, c, s, out4, part, dens, psi4, origin);
+                        double* out4, double* part, double* dens, double* psi4, double3 origin, double* hyp) {
+    if (g.ng == NG6) launch_constraints6(grid, block, st, g, c, s, out4, part, dens, psi4, origin, hyp);
+    else if (psi4 || hyp) constraints_kernel<4, 1><<<grid, block, 0, st>>>(g, c, s, out4, part, dens, psi4, origin, hyp);
+    else constraints_kernel<4, 0><<<grid, block, 0, st>>>(g, c, s, out4, part, dens, psi4, origin, hyp);
 }
 }  // namespace grf

@@ -38,9 +38,9 @@ void launch_rhs6(dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Co
 }
 
 void launch_constraints6(dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c, const double* s,
-                         double* out4, double* part, double* dens, double* psi4, double3 origin) {
-    if (psi4) constraints_kernel<6, 1><<<grid, block, 0, st>>>(g, c, s, out4, part, dens, psi4, origin);
-    else constraints_kernel<6, 0><<<grid, block, 0, st>>>(g, c, s, out4, part, dens, psi4, origin);
+                         double* out4, double* part, double* dens, double* psi4, double3 origin, double* hyp) {
+    if (psi4 || hyp) constraints_kernel<6, 1><<<grid, block, 0, st>>>(g, c, s, out4, part, dens, psi4, origin, hyp);
+    else constraints_kernel<6, 0><<<grid, block, 0, st>>>(g, c, s, out4, part, dens, psi4, origin, hyp);
 }
 
 }  // namespace grf

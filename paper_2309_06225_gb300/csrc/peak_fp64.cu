@@ -7,15 +7,22 @@
 
 namespace {
 // CH independent chains per thread, each advanced `iters` times by an instruction of the kind:
-// 0 DFMA, 1 DADD, 2 DMUL, 3 the mix DADD : DMUL : DFMA = 1 : 1 : 2 (per group of 4 chains).
-// The operands keep every chain bounded and non-constant.
+// 0 DFMA, 1 DADD, 2 DMUL, 3 the mix DADD : DMUL : DFMA = 1 : 1 : 2 (per group of 4 chains),
+// 4 DFMA with each chain's own multiplier and addend registers, 5 DFMA with one integer
+// multiply-add beside each (other pipes busy as in a real kernel). The operands keep every chain
+// bounded and non-constant.
 template <int CH, int KIND>
 __global__ void fp64_chains(int iters, double* out) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    double a[CH];
+    double a[CH], bm[CH], ca[CH];
 #pragma unroll
-    for (int c = 0; c < CH; ++c) a[c] = 1.0 + 1e-9 * t + 0.01 * c;
+    for (int c = 0; c < CH; ++c) {
+        a[c] = 1.0 + 1e-9 * t + 0.01 * c;
+        bm[c] = 0.99999999 - 1e-10 * c - 1e-15 * t;
+        ca[c] = 1e-8 * (1.0 + 0.1 * c);
+    }
     const double b = 0.99999999, cc = 1e-8, m = 1.0000000001;
+    unsigned h = 2654435761u * (unsigned)t;
 #pragma unroll 2
     for (int i = 0; i < iters; ++i) {
 #pragma unroll
@@ -23,10 +30,15 @@ __global__ void fp64_chains(int iters, double* out) {
             const int kind = KIND == 3 ? ((c & 3) == 0 ? 1 : ((c & 3) == 1 ? 2 : 0)) : KIND;
             if (kind == 0) a[c] = fma(a[c], b, cc);
             else if (kind == 1) a[c] = a[c] + (i & 1 ? -cc : cc);
-            else a[c] = a[c] * (i & 1 ? b : m);
+            else if (kind == 2) a[c] = a[c] * (i & 1 ? b : m);
+            else if (kind == 4) a[c] = fma(a[c], bm[c], ca[c]);
+            else {
+                a[c] = fma(a[c], b, cc);
+                h = h * 1664525u + (unsigned)c;
+            }
         }
     }
-    double s = 0.0;
+    double s = (double)(h & 1u) * 1e-300;
 #pragma unroll
     for (int c = 0; c < CH; ++c) s += a[c];
     out[t] = s;
@@ -38,6 +50,8 @@ void launch(int kind, int blocks, int threads, int iters, double* out, cudaStrea
         case 1: fp64_chains<CH, 1><<<blocks, threads, 0, st>>>(iters, out); break;
         case 2: fp64_chains<CH, 2><<<blocks, threads, 0, st>>>(iters, out); break;
         case 3: fp64_chains<CH, 3><<<blocks, threads, 0, st>>>(iters, out); break;
+        case 4: fp64_chains<CH, 4><<<blocks, threads, 0, st>>>(iters, out); break;
+        case 5: fp64_chains<CH, 5><<<blocks, threads, 0, st>>>(iters, out); break;
         default: fp64_chains<CH, 0><<<blocks, threads, 0, st>>>(iters, out); break;
     }
 }
@@ -45,7 +59,7 @@ void launch(int kind, int blocks, int threads, int iters, double* out, cudaStrea
 
 extern "C" int grf_peak_fp64(int kind, int chains, int blocks, int threads, int iters, int launches, double* out_dev,
                              float* ms_out, void* stream) {
-    if (kind < 0 || kind > 3 || (chains != 4 && chains != 8 && chains != 16) || blocks < 1 || threads < 32 ||
+    if (kind < 0 || kind > 5 || (chains != 4 && chains != 8 && chains != 16) || blocks < 1 || threads < 32 ||
         threads > 1024 || iters < 1 || launches < 1 || !out_dev || !ms_out)
         return -1;
     cudaStream_t st = (cudaStream_t)stream;

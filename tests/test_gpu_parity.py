@@ -293,6 +293,9 @@ def test_bl_pair_256_sampled_outputs(g, orc):
     orc.fill_ghosts(box, s0)
     rng = np.random.default_rng(5)
     samples = [(128, 128, 128 + 24), (3, 200, 77)] + [tuple(int(x) for x in rng.integers(0, 256, 3)) for _ in range(2)]
+    # the 8 grid points around each puncture (z = +-3): where the fields sourced by the lapse and
+    # the curvature peak, so the oracle's values there give each field's scale over the box
+    samples += [(i, j, k) for k in (103, 104, 151, 152) for j in (127, 128) for i in (127, 128)]
     R = 9
     refs, gots = [], []
     for (i, j, k) in samples:
@@ -304,7 +307,8 @@ def test_bl_pair_256_sampled_outputs(g, orc):
         gots.append(gpu[:, k + 3, j + 3, i + 3])
     refs, gots = np.array(refs), np.array(gots)
     # per-field scale from the inputs and the oracle only: the field's maximum over the whole
-    # initial box, or over the oracle's sampled results for fields that start at zero
+    # initial box, or over the oracle's sampled results (which include the points next to the
+    # punctures) for fields that start at zero
     scale = np.maximum(np.maximum(np.max(np.abs(box.interior(s0)), axis=(1, 2, 3)), np.max(np.abs(refs), axis=0)),
                        1e-12)
     for n, (i, j, k) in enumerate(samples):
@@ -358,3 +362,24 @@ def test_exponential_coupling_parity(g, orc, bc):
     gpu = gpu_rk4(g, box, params, s0, 0.25 * box.dx, 3)
     errs = field_errors(gpu, cpu, box)
     assert np.max(errs) < 1e-10, describe(errs)
+
+
+@pytest.mark.parametrize("case", ["ragged_perturbed_linear", "ragged_perturbed_quadratic", "single_point_frozen"])
+def test_hyperbolicity_parity(g, orc, case):
+    """grf_hyperbolicity (det M of the coupled system from the kernel's closed-form assembly and
+    its own LU; the effective-metric determinant by the determinant lemma; -g_eff^nn) against the
+    oracle (its residual's Jacobian and long-double full-pivot determinants) to 1e-11."""
+    box, params, kind, seed = RHS_CASES[case]()
+    s = make_state(box, kind, seed)
+    filled = s.copy()
+    orc.fill_ghosts(box, filled)
+    ref = orc.hyperbolicity(box, params, filled)
+    b = g.box_like(box)
+    t = g.to_device(s, b)
+    out = g.alloc_state(b, 3)
+    g.grf_hyperbolicity(b, g.params_like(params), t, out)
+    got = box.interior(g.to_host(out, b)[:3])
+    for m in range(3):
+        den = max(np.max(np.abs(ref[m])), 1e-300)
+        assert np.max(np.abs(got[m] - ref[m])) <= 1e-11 * den, (m, np.max(np.abs(got[m] - ref[m])) / den)
+    assert np.min(ref[0]) != 1.0  # the couplings make the system non-trivial

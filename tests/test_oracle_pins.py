@@ -1299,3 +1299,92 @@ def test_gravitational_plane_wave_converges_6th_order_on_4_ghost_boxes(orc):
         errs.append(max(np.max(np.abs(b.interior(s)[f] - b.interior(ex)[f])) / sc for f, sc in zip(fields, scale)))
     assert errs[1] < 1e-5, errs
     assert 45 < errs[0] / errs[1] < 80, errs
+
+
+# ----------------------------------------------------------------------------- hyperbolicity
+@pytest.fixture(scope="module")
+def schwarzschild_points():
+    fields, X = an.isotropic_schwarzschild_fields(M=1.0, lapse="precollapsed")
+    rs = np.linspace(0.3, 3.0, 28)
+    d = np.array([0.6, -0.3, 0.74])
+    d = d / np.linalg.norm(d)
+    pts = [tuple(r * d) for r in rs]
+    return rs, an.conformal_point(fields, pts, X)
+
+
+@pytest.mark.parametrize("lam", [0.2, 1.0])
+def test_coupled_system_determinant_on_schwarzschild(orc, schwarzschild_points, lam):
+    """Schwarzschild (K = 0, vacuum) with phi = 0 and beta = lambda phi: Phi = nabla nabla beta = 0,
+    so the 6x6 block of the coupled system is the identity and only the Gauss-Bonnet coupling
+    lambda L(G_S) of the scalar equation to d_t K_ij remains:
+        det M = 1 - 32 lambda^2 G_S^ij L(G_S)_ij = 1 - 32 lambda^2 R_ij R^ij = 1 - 192 lambda^2 M^2 / R^6,
+    R the areal radius (R_ij = diag(-2, 1, 1) M / R^3 in an orthonormal frame). The oracle's
+    determinant comes from its covariant residual; the closed form is independent of it. The
+    quadratic coupling has beta'(0) = 0 and det M = 1."""
+    rs, data = schwarzschild_points
+    for r, (v, d1, d2) in zip(rs, data):
+        R = an.areal_radius_isotropic(r, 1.0)
+        det = orc.point_hyperbolicity(P(lam=lam, g2=0.3, beta_kind=gi.BETA_LINEAR), v, d1, d2)[0]
+        assert det == pytest.approx(1.0 - 192.0 * lam ** 2 / R ** 6, rel=1e-12, abs=1e-13)
+        detq = orc.point_hyperbolicity(P(lam=lam, g2=0.3, beta_kind=gi.BETA_QUADRATIC), v, d1, d2)[0]
+        assert detq == pytest.approx(1.0, abs=1e-14)
+
+
+def test_loss_of_solvability_radius_on_schwarzschild(orc, schwarzschild_points):
+    """With lambda = M^2 the determinant crosses zero outside the horizon, at R^6 = 192 lambda^2 M^2:
+    bisection on the oracle's determinant along a radial line finds that areal radius."""
+    fields, X = an.isotropic_schwarzschild_fields(M=1.0, lapse="precollapsed")
+    d = np.array([0.6, -0.3, 0.74])
+    d = d / np.linalg.norm(d)
+    p = P(lam=1.0, g2=0.0, beta_kind=gi.BETA_LINEAR)
+
+    def det(r):
+        v, d1, d2 = an.conformal_point(fields, tuple(r * d), X)
+        return orc.point_hyperbolicity(p, v, d1, d2)[0]
+
+    lo, hi = 0.6, 1.6  # isotropic radii with areal radius 2.12 .. 2.74
+    assert det(lo) < 0.0 < det(hi)
+    for _ in range(40):
+        mid = 0.5 * (lo + hi)
+        lo, hi = (mid, hi) if det(mid) < 0.0 else (lo, mid)
+    assert an.areal_radius_isotropic(0.5 * (lo + hi), 1.0) == pytest.approx(192.0 ** (1.0 / 6.0), rel=1e-9)
+
+
+def test_hyperbolicity_diagnostics_without_coupling(orc, conformal_generic):
+    """lambda = g2 = 0: the coupled system is the identity and g_eff = g."""
+    v, d1, d2, ph = conformal_generic
+    h = orc.point_hyperbolicity(P(lam=0.0, g2=0.0), v, d1, d2)
+    np.testing.assert_allclose(h, [1.0, 1.0, 1.0], rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("g2", [0.3, -0.8])
+def test_effective_metric_of_the_scalar_equation(orc, conformal_generic, g2):
+    """On a generic non-vacuum point (Pi and grad phi non-zero), without backreaction so that the
+    scalar equation alone fixes d_t Pi:
+      * its linearisation in the second derivatives of phi, by differences of the oracle's d_t Pi
+        (exact: d_t Pi is affine in them), is alpha g_eff^ij / D with the principal symbol
+        g_eff^ab = (1 + 2 g2 X) g^ab - 2 g2 nabla^a phi nabla^b phi (the X^2 term of the action)
+        and D = -g_eff^nn, the oracle's third diagnostic;
+      * D is the coefficient of d_t Pi in the oracle's residual (the solve's w-w entry);
+      * det(g_eff)/det(g) is (1 + 2 g2 X)^3 (1 + 6 g2 X), the matrix determinant lemma."""
+    v, d1, d2, ph = conformal_generic
+    p = P(lam=0.4, g2=g2, decoupled=1)
+    h = orc.point_hyperbolicity(p, v, d1, d2)
+    gi3 = np.linalg.inv(ph["g"])
+    al = ph["alpha"]
+    Pi = v[26]
+    dphi = d1[25]
+    X = 0.5 * (Pi * Pi - dphi @ gi3 @ dphi)
+    geff = (1 + 2 * g2 * X) * gi3 - 2 * g2 * np.outer(gi3 @ dphi, gi3 @ dphi)
+    D = 1 + 2 * g2 * X + 2 * g2 * Pi * Pi
+    assert h[2] == pytest.approx(D, rel=1e-13)
+    assert h[1] == pytest.approx((1 + 2 * g2 * X) ** 3 * (1 + 6 * g2 * X), rel=1e-12)
+    _, diag, _ = orc.point_rhs(p, v, d1, d2)
+    assert diag[44] == pytest.approx(D, rel=1e-12)
+    base = orc.point_rhs(p, v, d1, d2)[0][26]
+    for m, (i, j) in enumerate(an.SYM_PAIRS):
+        dd = d2.copy()
+        dd[25, m] += 1e-3
+        got = (orc.point_rhs(p, v, d1, dd)[0][26] - base) / 1e-3
+        want = al * geff[i, j] / D * (1.0 if i == j else 2.0)
+        assert got == pytest.approx(want, rel=1e-8, abs=1e-11), (i, j)
