@@ -99,6 +99,7 @@ class Params:
     decoupled: int = 0          # 1: 4dST without backreaction (metric evolves by vacuum CCZ4)
     advection: int = 0          # 0: centred advection derivatives, 1: lopsided (upwind-biased)
     beta_kappa: float = 1.0     # kappa of the exponential coupling (beta_kind = BETA_EXPONENTIAL)
+    g3: float = 0.0             # cubic Horndeski coupling (the action's g3 X box(phi) term)
 
     def to_dict(self):
         return asdict(self)

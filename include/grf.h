@@ -111,7 +111,8 @@ typedef struct {
 /* Theory, gauge and numerical parameters (modified puncture gauge with constant a, b;
  * beta(phi) = lambda phi, lambda phi^2 / 2, or lambda / (2 kappa) (1 - exp(-kappa phi^2)), the
  * exponential coupling of spin-induced scalarisation ("Statement of Need"); the X^2 coupling is
- * the constant g2). */
+ * the constant g2; the cubic Horndeski coupling g3). The action is
+ *   (1/16 pi) int sqrt(-g) [R + X + g2 X^2 + g3 X box(phi) + beta(phi) L_GB],  X = -1/2 (d phi)^2. */
 typedef struct {
     double kappa1, kappa2, kappa3;   /* CCZ4 constraint damping */
     double shift_F, eta;             /* Gamma-driver: d_t shift = F B / (1 + a) - ..., d_t B = d_t Gamma - eta B */
@@ -130,6 +131,9 @@ typedef struct {
                                         inside the coupled 4dST system included). 1 is not accepted by
                                         grf_tlm_rk4 */
     double beta_kappa;               /* kappa >= 0 of GRF_BETA_EXPONENTIAL (ignored by the other kinds) */
+    double g3;                       /* cubic Horndeski coupling ("Key features": the cubic Horndeski
+                                        theory): the action gains g3 X box(phi), G3(phi, X) = g3 X;
+                                        0 gives 4dST alone */
 } grf_params;
 
 /* d_t of all 27 fields at the interior points of `state` (modified CCZ4 + 4dST, section

@@ -21,7 +21,7 @@ class OrcParams(C.Structure):
                 ("lam", C.c_double), ("g2", C.c_double),
                 ("sigma_ko", C.c_double), ("min_chi", C.c_double), ("min_lapse", C.c_double),
                 ("beta_kind", C.c_int), ("enforce_algebraic", C.c_int), ("decoupled", C.c_int),
-                ("advection", C.c_int), ("beta_kappa", C.c_double)]
+                ("advection", C.c_int), ("beta_kappa", C.c_double), ("g3", C.c_double)]
 
 
 class OrcBox(C.Structure):
@@ -86,7 +86,7 @@ def params(p) -> OrcParams:
     return OrcParams(p.kappa1, p.kappa2, p.kappa3, p.shift_F, p.eta, p.a0, p.b0, p.lam, p.g2,
                      p.sigma_ko, p.min_chi, p.min_lapse, int(p.beta_kind), int(p.enforce_algebraic),
                      int(getattr(p, "decoupled", 0)), int(getattr(p, "advection", 0)),
-                     float(getattr(p, "beta_kappa", 1.0)))
+                     float(getattr(p, "beta_kappa", 1.0)), float(getattr(p, "g3", 0.0)))
 
 
 def box(b) -> OrcBox:

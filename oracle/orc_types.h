@@ -15,6 +15,7 @@ typedef struct {
     int decoupled;          // 1: no backreaction: the metric evolves by vacuum CCZ4, the scalar on it
     int advection;          // 0: centred advection derivatives; 1: lopsided (upwind-biased)
     double beta_kappa;      // kappa of the exponential coupling (beta_kind 2)
+    double g3;              // cubic Horndeski coupling: the action's g3 X box(phi) term
 } orc_params;
 
 typedef struct {

@@ -143,6 +143,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_stage_kernel(Geom g, Coeffs c
         CoeffsT<Rev> cr;
         cr.kappa1 = c.kappa1; cr.kappa2 = c.kappa2; cr.kappa3 = c.kappa3; cr.shift_F = c.shift_F; cr.eta = c.eta;
         cr.lam = Rev(c.lam, kLLAM);
+        cr.g3 = c.g3;
         cr.g2 = Rev(c.g2, kLG2);
         cr.inv_1pa = c.inv_1pa; cr.a_1pa = c.a_1pa; cr.bK = c.bK; cr.bTh = c.bTh;
         cr.beta_kind = c.beta_kind; cr.beta_kappa = c.beta_kappa; cr.decoupled = c.decoupled; cr.advection = 0;
@@ -369,7 +370,7 @@ Geom adj_geom(const grf_box* b) {
 Coeffs adj_coeffs(const grf_params* p) {
     Coeffs c;
     c.kappa1 = p->kappa1; c.kappa2 = p->kappa2; c.kappa3 = p->kappa3;
-    c.shift_F = p->shift_F; c.eta = p->eta; c.lam = p->lambda; c.g2 = p->g2;
+    c.shift_F = p->shift_F; c.eta = p->eta; c.lam = p->lambda; c.g2 = p->g2; c.g3 = p->g3;
     c.inv_1pa = 1.0 / (1.0 + p->a0);
     c.a_1pa = p->a0 / (1.0 + p->a0);
     c.bK = 3.0 * p->b0 / (4.0 * (1.0 + p->b0));

@@ -100,7 +100,7 @@ int grf_count_point_ops(const grf_params* p, const double* v, const double* d1, 
         for (int m = 0; m < 6; ++m) in.d2[b][m] = CD::var(d2[b * 6 + m]);
     grf::Coeffs c;
     c.kappa1 = p->kappa1; c.kappa2 = p->kappa2; c.kappa3 = p->kappa3; c.shift_F = p->shift_F; c.eta = p->eta;
-    c.lam = p->lambda; c.g2 = p->g2; c.inv_1pa = 1.0 / (1.0 + p->a0); c.a_1pa = p->a0 / (1.0 + p->a0);
+    c.lam = p->lambda; c.g2 = p->g2; c.g3 = p->g3; c.inv_1pa = 1.0 / (1.0 + p->a0); c.a_1pa = p->a0 / (1.0 + p->a0);
     c.bK = 3.0 * p->b0 / (4.0 * (1.0 + p->b0)); c.bTh = 1.0 / (2.0 * (1.0 + p->b0)); c.beta_kind = p->beta_kind; c.decoupled = p->decoupled;
     c.beta_kappa = p->beta_kappa;
     c.advection = 0;  // operation counts of the centred-advection instance
@@ -128,7 +128,7 @@ int grf_host_point_rhs(const grf_params* p, const double* v, const double* d1, c
         for (int m = 0; m < 6; ++m) in.d2[b][m] = d2[b * 6 + m];
     grf::Coeffs c;
     c.kappa1 = p->kappa1; c.kappa2 = p->kappa2; c.kappa3 = p->kappa3; c.shift_F = p->shift_F; c.eta = p->eta;
-    c.lam = p->lambda; c.g2 = p->g2; c.inv_1pa = 1.0 / (1.0 + p->a0); c.a_1pa = p->a0 / (1.0 + p->a0);
+    c.lam = p->lambda; c.g2 = p->g2; c.g3 = p->g3; c.inv_1pa = 1.0 / (1.0 + p->a0); c.a_1pa = p->a0 / (1.0 + p->a0);
     c.bK = 3.0 * p->b0 / (4.0 * (1.0 + p->b0)); c.bTh = 1.0 / (2.0 * (1.0 + p->b0)); c.beta_kind = p->beta_kind; c.decoupled = p->decoupled;
     c.beta_kappa = p->beta_kappa;
     c.advection = 0;  // operation counts of the centred-advection instance
@@ -154,7 +154,7 @@ int grf_host_point_psi4(const grf_params* p, const double* v, const double* d1, 
         for (int m = 0; m < 6; ++m) in.d2[b][m] = d2[b * 6 + m];
     grf::Coeffs c;
     c.kappa1 = p->kappa1; c.kappa2 = p->kappa2; c.kappa3 = p->kappa3; c.shift_F = p->shift_F; c.eta = p->eta;
-    c.lam = p->lambda; c.g2 = p->g2; c.inv_1pa = 1.0 / (1.0 + p->a0); c.a_1pa = p->a0 / (1.0 + p->a0);
+    c.lam = p->lambda; c.g2 = p->g2; c.g3 = p->g3; c.inv_1pa = 1.0 / (1.0 + p->a0); c.a_1pa = p->a0 / (1.0 + p->a0);
     c.bK = 3.0 * p->b0 / (4.0 * (1.0 + p->b0)); c.bTh = 1.0 / (2.0 * (1.0 + p->b0)); c.beta_kind = p->beta_kind;
     c.decoupled = p->decoupled;
     c.beta_kappa = p->beta_kappa;
@@ -167,6 +167,31 @@ int grf_host_point_psi4(const grf_params* p, const double* v, const double* d1, 
     grf::point_rhs(c, in, rhs, &ex, ok);
     out2[0] = ex.psi4[0];
     out2[1] = ex.psi4[1];
+    return ok ? 0 : -5;
+}
+
+// The kernel's hyperbolicity diagnostics (det M, det g_eff / det g, -g_eff^nn) of the same host
+// instance; out3 receives the three.
+int grf_host_point_hyp(const grf_params* p, const double* v, const double* d1, const double* d2, double* out3) {
+    grf::PointInT<double> in;
+    for (int f = 0; f < grf::NFIELDS; ++f) in.v[f] = v[f];
+    for (int a = 0; a < 24; ++a)
+        for (int d = 0; d < 3; ++d) in.d1[a][d] = d1[a * 3 + d];
+    for (int b = 0; b < 12; ++b)
+        for (int m = 0; m < 6; ++m) in.d2[b][m] = d2[b * 6 + m];
+    grf::Coeffs c;
+    c.kappa1 = p->kappa1; c.kappa2 = p->kappa2; c.kappa3 = p->kappa3; c.shift_F = p->shift_F; c.eta = p->eta;
+    c.lam = p->lambda; c.g2 = p->g2; c.g3 = p->g3; c.inv_1pa = 1.0 / (1.0 + p->a0); c.a_1pa = p->a0 / (1.0 + p->a0);
+    c.bK = 3.0 * p->b0 / (4.0 * (1.0 + p->b0)); c.bTh = 1.0 / (2.0 * (1.0 + p->b0)); c.beta_kind = p->beta_kind;
+    c.decoupled = p->decoupled;
+    c.beta_kappa = p->beta_kappa;
+    c.advection = 0;
+    grf::PointExtraT<double> ex;
+    ex.want_hyp = 1;
+    double rhs[grf::NFIELDS];
+    bool ok = true;
+    grf::point_rhs(c, in, rhs, &ex, ok);
+    for (int m = 0; m < 3; ++m) out3[m] = ex.hyp[m];
     return ok ? 0 : -5;
 }
 

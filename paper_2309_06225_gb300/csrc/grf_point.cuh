@@ -19,6 +19,18 @@
 // those of (1/16 pi)(X + g2 X^2). C_ij (through d_t K_ij) and Phi_nn (through d_t Pi) are
 // the only places the unknowns enter, affinely: the 7x7 system M v = r for v = (d_t K_ij, d_t Pi)
 // is assembled from these expressions and solved by LU with partial pivoting.
+//
+// The cubic Horndeski term (1/16 pi) g3 X box(phi) (general instantiation, COUP = 1) adds, with
+// H = nabla nabla phi in the same basis (H_nn holding d_t Pi, H_ni, H_ij = D_i D_j phi + K_ij Pi),
+//     8 pi rho3  = g3/2 (Pi^2 tr H - H(dphi, dphi))
+//     8 pi S3_i  = -g3/2 [(Pi tr H - H_n(dphi)) d_i phi + Pi^2 H_ni - Pi H_ik d^k phi]
+//     8 pi S3_ij = g3 [1/2 H_nn (Pi^2 gamma_ij - d_i phi d_j phi) + 1/2 tr H d_i phi d_j phi
+//                      + Pi H_n(i d_j) phi - H_(i|k d^k phi d_|j) phi + gamma_ij (H(dphi, dphi)/2 - Pi H_n(dphi))]
+// to the metric equations, and to the scalar equation
+//     g3 [box(phi)^2 - H_ab H^ab - R_ab d^a phi d^b phi],
+// in which H_nn^2 cancels: -2 H_nn tr H + (tr H)^2 + 2 H_n.H_n - H_ij H^ij
+// - (Pi^2 gamma^kl - d^k phi d^l phi) C_kl - 2 Pi B^i d_i phi - S_ij d^i phi d^j phi
+// (4D Ricci: R_nn = tr C, R_ni = -B_i, R_ij = S_ij - C_ij). The system stays affine in the unknowns.
 #pragma once
 
 #include <type_traits>
@@ -69,6 +81,7 @@ struct CoeffsT {
     double beta_kappa;  // kappa of the exponential coupling (beta_kind 2)
     int decoupled;  // 1: the scalar's stress-energy is left out of the metric equations
     int advection;  // 1: lopsided advection derivatives (kernels instantiated with LOP = 1)
+    double g3;      // cubic Horndeski coupling (read only by COUP = 1 instances)
 };
 using Coeffs = CoeffsT<double>;
 
@@ -86,7 +99,7 @@ struct PointExtraT {
     T ham;      // H = S - 2 (8 pi rho)
     T mom[3];   // M_i = B_i - 8 pi S_i
     T rho8[3];  // 8 pi rho of the X, g2 X^2 and beta(phi) L_GB terms of the action (their sum is
-                // the 8 pi rho of the equations; reported with and without backreaction)
+                // the 8 pi rho of the equations when g3 = 0; reported with and without backreaction)
     // Weyl scalar Psi_4 (double instances only), computed when want_psi4 is set: xyz are the
     // point's coordinates relative to the origin of the tetrad's triad.
     int want_psi4 = 0;
@@ -97,10 +110,10 @@ struct PointExtraT {
     //            unknown's own coefficient is 1 (M = identity without coupling); where it
     //            vanishes the equations no longer determine the time derivatives;
     //   hyp[1] = det(g_eff^ab) / det(g^ab) of the scalar equation's principal symbol
-    //            g_eff^ab = (1 + 2 g2 X) g^ab - 2 g2 d^a phi d^b phi; by the matrix determinant
-    //            lemma (1 + 2 g2 X)^3 (1 + 6 g2 X);
-    //   hyp[2] = -g_eff^nn = 1 + 2 g2 X + 2 g2 Pi^2 (the coefficient of d_t Pi; the normal is
-    //            timelike for the scalar's characteristic cone while it is positive).
+    //            g_eff^ab = (1 + 2 g2 X) g^ab - 2 g2 d^a phi d^b phi + 2 g3 (box(phi) g^ab - H^ab);
+    //            for g3 = 0, by the matrix determinant lemma, (1 + 2 g2 X)^3 (1 + 6 g2 X);
+    //   hyp[2] = -g_eff^nn = 1 + 2 g2 X + 2 g2 Pi^2 + 2 g3 tr H (the coefficient of d_t Pi; the
+    //            normal is timelike for the scalar's characteristic cone while it is positive).
     int want_hyp = 0;
     double hyp[3];
 };
@@ -659,7 +672,7 @@ GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS]
     // decoupled mode: the scalar's stress-energy is left out of the metric equations (rho, S_i,
     // S_ij and their coupling to d_t K_ij); the scalar equation below is unchanged
     const bool dec = (DEC < 0) ? (c.decoupled != 0) : (DEC == 1);
-    const T rho8 = dec ? T(0.0) : fma(0.5 * fX, Pi * Pi, fma(-4.0, sdotw(GS, Phuw), -0.5 * XX));
+    T rho8 = dec ? T(0.0) : fma(0.5 * fX, Pi * Pi, fma(-4.0, sdotw(GS, Phuw), -0.5 * XX));
     T S8[3];
     const T BPn = Bv[0] * Phnu[0] + Bv[1] * Phnu[1] + Bv[2] * Phnu[2];
 #pragma unroll
@@ -675,6 +688,24 @@ GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS]
                     s = fma(BC(k, i, l), pkl, s);
                 }
         S8[i] = dec ? T(0.0) : fma(-0.5 * fX * Pi, dphi[i], 4.0 * s);
+    }
+    // cubic term: the n-n and n-i parts of its stress tensor (no unknown in them)
+    const bool cub = COUP && c.g3 != 0.0;
+    T trH3 = 0.0, Hnd3 = 0.0, Hdd3 = 0.0, Hdv3[3];
+    if (cub) {
+        trH3 = sdotw(Hij, gw);
+        Hnd3 = dphiu[0] * Hn[0] + dphiu[1] * Hn[1] + dphiu[2] * Hn[2];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+            Hdv3[i] = Hij[sidx(i, 0)] * dphiu[0] + Hij[sidx(i, 1)] * dphiu[1] + Hij[sidx(i, 2)] * dphiu[2];
+        Hdd3 = dphiu[0] * Hdv3[0] + dphiu[1] * Hdv3[1] + dphiu[2] * Hdv3[2];
+        if (!dec) {
+            const double g3h = 0.5 * c.g3;
+            rho8 = fma(g3h, fma(Pi * Pi, trH3, -Hdd3), rho8);
+            const T a3 = fma(Pi, trH3, -Hnd3);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) S8[i] = fma(-g3h, fma(a3, dphi[i], Pi * fma(Pi, Hn[i], -Hdv3[i])), S8[i]);
+        }
     }
     T S1[6], Y[6];
     const T fXh = 0.5 * fX, XXh = 0.5 * XX;
@@ -834,6 +865,7 @@ GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS]
     //   u - 4 L(Q(u)) - 4 b1 L(G_S) w = r,   w - (8 b1 / D) G_S^ij u_ij = r_w,   L(X) = X - gamma tr(X)/2
     GRF_SECTION(15);
     T Msys[7][8];
+    T S3[6], PPc[6], HnnSol0 = 0.0;  // cubic term: 8 pi S3_ij without d_t Pi, Pi^2 gamma^ij - d^i phi d^j phi
     T QC0[6];
     q_of(C0, gd, gw, Phd, Phuw, Phm, trP, QC0);
     {
@@ -879,11 +911,78 @@ GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS]
                         Msys[row][col] = dec ? T(row == col ? 1.0 : 0.0) : e;
                     }
             }
-        const T Dphi = fma(2.0 * g2, Pi * Pi, fX);
+        T Dphi = fma(2.0 * g2, Pi * Pi, fX);
+        T E3 = 0.0;  // the cubic term's share of the scalar equation without H_nn and d_t K_ij
+        if (cub) {
+            Dphi = fma(2.0 * c.g3, trH3, Dphi);
+            const T Hnn0 = -(bdPi + dadp) * ial;
+            T Hm[3][3], ppw[6], PPuw[6];  // H_i^k, d^i phi d^j phi and Pi^2 gamma^ij - d^i phi d^j phi (weighted)
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int k = 0; k < 3; ++k)
+                    Hm[i][k] = Hij[sidx(i, 0)] * gu[sidx(0, k)] + Hij[sidx(i, 1)] * gu[sidx(1, k)] + Hij[sidx(i, 2)] * gu[sidx(2, k)];
+            T HH = 0.0;
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int k = 0; k < 3; ++k) HH = fma(Hm[i][k], Hm[k][i], HH);
+            T HnHn = 0.0, BdP = 0.0;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const T hnu = gu[sidx(i, 0)] * Hn[0] + gu[sidx(i, 1)] * Hn[1] + gu[sidx(i, 2)] * Hn[2];
+                HnHn = fma(Hn[i], hnu, HnHn);
+                BdP = fma(Bv[i], dphiu[i], BdP);
+            }
+            const T Pi2 = Pi * Pi;
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = i; j < 3; ++j) {
+                    const T pp = dphiu[i] * dphiu[j];
+                    ppw[sidx(i, j)] = (i == j) ? pp : 2.0 * pp;
+                    PPuw[sidx(i, j)] = fma(Pi2, gw[sidx(i, j)], -ppw[sidx(i, j)]);
+                }
+            T e3 = fma(trH3, trH3, fma(2.0, HnHn, -HH));
+            e3 = fma(-2.0 * Pi, BdP, e3);
+            e3 = e3 - sdotw(S, ppw) - sdotw(C0, PPuw);
+            E3 = c.g3 * e3;
+            if (!dec) {
+                // 8 pi S3_ij without its d_t Pi part, and that part's coefficient in the metric rows:
+                // S3_ij = S3_0 + g3 w / (2 alpha) (Pi^2 gamma_ij - d_i phi d_j phi)
+                const T pcoef = 0.5 * (trH3 - Hnn0);  // coefficients of d_i phi d_j phi and of gamma_ij
+                const T gcoef = fma(0.5 * Hnn0, Pi2, fma(0.5, Hdd3, -Pi * Hnd3));
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = i; j < 3; ++j) {
+                        T x = fma(gcoef, gd[sidx(i, j)], pcoef * (dphi[i] * dphi[j]));
+                        x = fma(0.5 * Pi, fma(Hn[i], dphi[j], Hn[j] * dphi[i]), x);
+                        x = fma(-0.5, fma(Hdv3[i], dphi[j], Hdv3[j] * dphi[i]), x);
+                        S3[sidx(i, j)] = c.g3 * x;
+                    }
+                const T trS3h = 0.5 * sdotw(S3, gw);
+                const T wc = 0.5 * (dphi2 - Pi2);
+#pragma unroll
+                for (int m = 0; m < 6; ++m) {
+                    const int i = (m < 3) ? 0 : (m < 5 ? 1 : 2);
+                    const int j = (m < 3) ? m : (m < 5 ? m - 2 : 2);
+                    Msys[m][7] = fma(-al, fma(-trS3h, gd[m], S3[m]), Msys[m][7]);
+                    Msys[m][6] = fma(0.5 * c.g3, fma(wc, gd[m], -dphi[i] * dphi[j]), Msys[m][6]);
+                }
+            }
+#pragma unroll
+            for (int col = 0; col < 6; ++col) PPc[col] = PPuw[col];
+            HnnSol0 = Hnn0;
+        }
         const T iD = 1.0 / Dphi;
         const T c8 = -8.0 * b1 * iD;
 #pragma unroll
         for (int col = 0; col < 6; ++col) Msys[6][col] = c8 * GSuw[col];
+        if (cub) {
+#pragma unroll
+            for (int col = 0; col < 6; ++col) Msys[6][col] = fma(c.g3 * iD, PPc[col], Msys[6][col]);
+        }
         Msys[6][6] = 1.0;
         const T trH = sdotw(Hij, gw);
         const T Hnd = dphiu[0] * Hn[0] + dphiu[1] * Hn[1] + dphiu[2] * Hn[2];
@@ -893,12 +992,13 @@ GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS]
             const T t = Hij[sidx(i, 0)] * dphiu[0] + Hij[sidx(i, 1)] * dphiu[1] + Hij[sidx(i, 2)] * dphiu[2];
             Hdd = (i == 0) ? dphiu[0] * t : fma(dphiu[i], t, Hdd);
         }
-        const T src = fma(fX, trH, fma(4.0 * g2 * Pi, Hnd, fma(-2.0 * g2, Hdd, b1 * L0)));
+        T src = fma(fX, trH, fma(4.0 * g2 * Pi, Hnd, fma(-2.0 * g2, Hdd, b1 * L0)));
+        if (cub) src = src + E3;
         Msys[6][7] = fma(al * iD, src, bdPi + dadp);
         if constexpr (std::is_same<T, double>::value) {
             if (extra && extra->want_hyp) {
                 extra->hyp[0] = det7(Msys);
-                extra->hyp[1] = fX * fX * fX * fma(6.0 * g2, X, 1.0);
+                extra->hyp[1] = fX * fX * fX * fma(6.0 * g2, X, 1.0);  // g3 = 0; the cubic case below
                 extra->hyp[2] = Dphi;
             }
         }
@@ -909,6 +1009,31 @@ GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS]
 #pragma unroll
     for (int m = 0; m < 6; ++m) u[m] = Msys[m][7];
     const T w = Msys[6][7];
+    if constexpr (std::is_same<T, double>::value) {
+        if (cub && extra && extra->want_hyp) {
+            // g_eff in the basis (n, e_i) at the solution: g_eff^nn = -D (stored above),
+            // g_eff^ni = 2 g2 Pi d^i phi + 2 g3 H_n^i, g_eff^ij = (1 + 2 g2 X) gamma^ij
+            // - 2 g2 d^i phi d^j phi + 2 g3 (box(phi) gamma^ij - H^ij); by the Schur complement on the
+            // n-n entry, det g_eff / det g = D det(g_eff^ij + g_eff^ni g_eff^nj / D) det(gamma_ij)
+            const double D = extra->hyp[2];
+            const double box = trH3 - fma(w, ial, HnnSol0);
+            double e0[3], Hu[3][3], Sc[6];
+            for (int i = 0; i < 3; ++i) {
+                const double hnu = gu[sidx(i, 0)] * Hn[0] + gu[sidx(i, 1)] * Hn[1] + gu[sidx(i, 2)] * Hn[2];
+                e0[i] = 2.0 * (g2 * Pi * dphiu[i] + c.g3 * hnu);
+                for (int k = 0; k < 3; ++k)
+                    Hu[i][k] = Hij[sidx(i, 0)] * gu[sidx(0, k)] + Hij[sidx(i, 1)] * gu[sidx(1, k)] + Hij[sidx(i, 2)] * gu[sidx(2, k)];
+            }
+            for (int i = 0; i < 3; ++i)
+                for (int j = i; j < 3; ++j) {
+                    const double huij = gu[sidx(i, 0)] * Hu[0][j] + gu[sidx(i, 1)] * Hu[1][j] + gu[sidx(i, 2)] * Hu[2][j];
+                    const double eij = fX * gu[sidx(i, j)] - 2.0 * g2 * dphiu[i] * dphiu[j]
+                                       + 2.0 * c.g3 * (box * gu[sidx(i, j)] - huij);
+                    Sc[sidx(i, j)] = eij + e0[i] * e0[j] / D;
+                }
+            extra->hyp[1] = D * sym3_det(Sc) * sym3_det(gd);
+        }
+    }
 
     // ---- full S_ij at the solution and the final K, A_ij, Pi right-hand sides
     GRF_SECTION(17);
@@ -920,6 +1045,15 @@ GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS]
 #pragma unroll
         for (int m = 0; m < 6; ++m)
             S8ij[m] = dec ? T(0.0) : fma(-4.0, fma(GS[m], Phnn, Y[m] + fma(Qu[m], ial, QC0[m])), S1[m]);
+        if (cub && !dec) {
+            const T gw2 = (0.5 * c.g3) * (w * ial);
+#pragma unroll
+            for (int m = 0; m < 6; ++m) {
+                const int i = (m < 3) ? 0 : (m < 5 ? 1 : 2);
+                const int j = (m < 3) ? m : (m < 5 ? m - 2 : 2);
+                S8ij[m] = S8ij[m] + fma(gw2, fma(Pi * Pi, gd[m], -dphi[i] * dphi[j]), S3[m]);
+            }
+        }
         const T Ss8 = sdotw(S8ij, gw);
         rhs[F_K] = fma(0.5 * al, Ss8, Kdot0);
         const T trh3 = sdotw(S8ij, hw) * (1.0 / 3.0);

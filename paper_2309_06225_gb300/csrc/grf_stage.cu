@@ -12,7 +12,7 @@ void launch_stage(int stage, dim3 grid, dim3 block, cudaStream_t st, const Geom&
         launch_stage_lopsided(stage, grid, block, st, g, c, a);
         return;
     }
-    if (c.beta_kind == 2) {  // the exponential coupling: the general instantiation
+    if (c.beta_kind == 2 || c.g3 != 0.0) {  // the exponential coupling or the cubic term: the general instantiation
         launch_stage_general(stage, grid, block, st, g, c, a);
         return;
     }

@@ -1,5 +1,6 @@
 // RK4 stage kernels of the 4th-order scheme with centred advection for every coupling function
-// (the default instantiations compile only the linear and quadratic ones). The decoupled mode is
+// and the cubic Horndeski term (the default instantiations compile only the linear and quadratic
+// couplings, without the cubic term). The decoupled mode is
 // a compile-time instantiation here too, so the bits equal those of the batched kernels.
 #include "grf_kernels.cuh"
 #include "grf_launch.h"

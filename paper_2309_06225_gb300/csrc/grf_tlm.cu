@@ -266,6 +266,7 @@ int grf_tlm_rk4(const grf_box* box, const grf_params* params, const double* dpar
     c.shift_F = params->shift_F; c.eta = params->eta;
     c.lam = D3(params->lambda, dparams[0], dparams[2], dparams[4]);
     c.g2 = D3(params->g2, dparams[1], dparams[3], dparams[5]);
+    c.g3 = params->g3;
     c.inv_1pa = 1.0 / (1.0 + params->a0);
     c.a_1pa = params->a0 / (1.0 + params->a0);
     c.bK = 3.0 * params->b0 / (4.0 * (1.0 + params->b0));

@@ -32,6 +32,7 @@ def _lib():
     L.grf_count_point_ops.argtypes = [C.c_void_p, P, P, P, C.POINTER(C.c_longlong)]
     L.grf_host_point_rhs.argtypes = [C.c_void_p, P, P, P, P, P]
     L.grf_host_point_psi4.argtypes = [C.c_void_p, P, P, P, P, P]
+    L.grf_host_point_hyp.argtypes = [C.c_void_p, P, P, P, P]
     return L
 
 
@@ -97,3 +98,12 @@ def host_point_psi4(params, v, d1, d2, xyz):
     out = np.zeros(2)
     st = _lib().grf_host_point_psi4(C.byref(params), *[a.ctypes.data_as(P) for a in arrs], out.ctypes.data_as(P))
     return complex(out[0], out[1]), st
+
+
+def host_point_hyp(params, v, d1, d2):
+    """The kernel's hyperbolicity diagnostics (det M, det g_eff / det g, -g_eff^nn) on the host."""
+    P = C.POINTER(C.c_double)
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (v, d1, d2)]
+    out = np.zeros(3)
+    st = _lib().grf_host_point_hyp(C.byref(params), *[a.ctypes.data_as(P) for a in arrs], out.ctypes.data_as(P))
+    return out, st

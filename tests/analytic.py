@@ -251,9 +251,12 @@ def beta_derivatives(phi, lam, beta_kind, kappa=1.0):
     return float(b1.subs(f, phi)), float(b2.subs(f, phi))
 
 
-def stress_and_scalar(g, gi, Gam, Rdn, Ric, Rs, dphi, ddphi, phi, lam, g2, beta_kind, kappa=1.0):
-    """8 pi T_mn and the scalar-equation residual E for the 4dST action
-    (1/16 pi) int [R + X + g2 X^2 + beta(phi) L_GB]."""
+def stress_and_scalar(g, gi, Gam, Rdn, Ric, Rs, dphi, ddphi, phi, lam, g2, beta_kind, kappa=1.0, g3=0.0,
+                      parts=False):
+    """8 pi T_mn and the scalar-equation residual E for the action
+    (1/16 pi) int [R + X + g2 X^2 + g3 X box(phi) + beta(phi) L_GB]
+    (4dST, plus the cubic Horndeski term G3 = g3 X). With parts=True the cubic term's share of
+    8 pi T is returned as well."""
     b1, b2 = beta_derivatives(phi, lam, beta_kind, kappa)
     Hphi = ddphi - np.einsum("lmn,l->mn", Gam, dphi)
     Phi = b1 * Hphi + b2 * np.outer(dphi, dphi)
@@ -268,7 +271,19 @@ def stress_and_scalar(g, gi, Gam, Rdn, Ric, Rs, dphi, ddphi, phi, lam, g2, beta_
     T8gb = -4 * np.einsum("acbd,cd->ab", P, Phiu)
     T8 = 0.5 * (1 + 2 * g2 * X) * np.outer(dphi, dphi) + 0.5 * g * (X + g2 * X * X) + T8gb
     dphu = gi @ dphi
-    E = (1 + 2 * g2 * X) * np.einsum("ab,ab->", gi, Hphi) - 2 * g2 * dphu @ Hphi @ dphu + b1 * LGB
+    box = np.einsum("ab,ab->", gi, Hphi)
+    E = (1 + 2 * g2 * X) * box - 2 * g2 * dphu @ Hphi @ dphu + b1 * LGB
+    # cubic term g3 X box(phi): with nabla_a X = -nabla^c phi nabla_a nabla_c phi,
+    #   8 pi T3_ab = g3 [1/2 box(phi) d_a phi d_b phi + nabla_(a X nabla_b) phi - 1/2 g_ab nabla X . nabla phi]
+    #   E3 = g3 [box(phi)^2 - nabla_a nabla_b phi nabla^a nabla^b phi - R_ab nabla^a phi nabla^b phi]
+    dX = -Hphi @ dphu
+    T8c = g3 * (0.5 * box * np.outer(dphi, dphi) + 0.5 * (np.outer(dX, dphi) + np.outer(dphi, dX))
+                - 0.5 * g * (dX @ dphu))
+    Hu = gi @ Hphi @ gi
+    E = E + g3 * (box * box - np.einsum("ab,ab->", Hphi, Hu) - dphu @ Ric @ dphu)
+    T8 = T8 + T8c
+    if parts:
+        return T8, E, LGB, T8gb, T8c
     return T8, E, LGB, T8gb
 
 
@@ -365,15 +380,17 @@ def z4_point_data(pt):
                 phi=float(v[F_PHI]), Z=zv[:4], dZ=zv[4:].reshape(4, 4).T.copy())
 
 
-def z4_residual(D, unk, b, k1, k2, lam, g2, kind, variant="covariant"):
+def z4_residual(D, unk, b, k1, k2, lam, g2, kind, variant="covariant", g3=0.0):
     """Residual of the covariant modified damped Z4 equations with the 4dST stress tensor,
         G^mn + 2 Phat_a^{b mn} nabla_b Z^a - kappa1 [n^m Z^n + n^n Z^m + kappa2 (n.Z) g^mn] - 8 pi T^mn = 0,
         Phat_a^{b mn} = delta_a^(m gh^n)b - 1/2 delta_a^b gh^mn,   gh^mn = g^mn - b n^m n^n,
-    and of the scalar equation, at the data of z4_point_data modified by the unknowns
+    and of the scalar equation (the cubic term g3 X box(phi) included), at the data of
+    z4_point_data modified by the unknowns
     unk = (d_t^2 gamma_ij (6, added), d_t Z_a (4, added), d_t^2 phi (1, added)). Every
     component is affine in unk. `variant` plants a change in the equation for the
     discrimination checks: "b_half" (b/2 in gh), "k2_moved" ((1 + kappa2) instead of kappa2
-    in the damping), "gh_first_only" (g instead of gh in the trace term of Phat)."""
+    in the damping), "gh_first_only" (g instead of gh in the trace term of Phat), "g3_half" (half
+    the cubic term's stress tensor)."""
     g = D["g4"]
     ddg = D["ddg"].copy()
     for m, (i, j) in enumerate(SYM_PAIRS):
@@ -398,14 +415,18 @@ def z4_residual(D, unk, b, k1, k2, lam, g2, kind, variant="covariant"):
     nZ = n_up @ Z
     c2 = 1.0 + k2 if variant == "k2_moved" else k2
     damp = -k1 * (np.outer(n_up, Zu) + np.outer(Zu, n_up) + c2 * nZ * gi)
-    T8, E, _, _ = stress_and_scalar(g, gi, Gam, Rdn, Ric, Rs, D["dphi"], ddphi, D["phi"], lam, g2, kind)
+    T8, E, _, _, T8c = stress_and_scalar(g, gi, Gam, Rdn, Ric, Rs, D["dphi"], ddphi, D["phi"], lam, g2, kind,
+                                         g3=g3, parts=True)
+    if variant == "g3_half":
+        T8 = T8 - 0.5 * T8c
     Emn = gi @ (Ric - 0.5 * g * Rs) @ gi + Zpart + damp - gi @ T8 @ gi
     return np.array([Emn[i, j] for i in range(4) for j in range(i, 4)] + [E])
 
 
-def z4_time_derivatives(D, **kw):
-    """Solves the 11 covariant equations for the unknowns (affine: exact from 12 evaluations)
-    and returns the resulting exact time derivatives of the 27 conformal fields at the point."""
+def z4_unknowns(D, **kw):
+    """Solves the 11 covariant equations for the unknowns. They are affine in the unknowns (the
+    cubic term's box(phi)^2 - nabla nabla phi . nabla nabla phi loses its (d_t^2 phi)^2 part), so
+    12 evaluations give the solution exactly; the residual there is checked."""
     f0 = z4_residual(D, np.zeros(11), **kw)
     J = np.empty((11, 11))
     for c in range(11):
@@ -413,6 +434,15 @@ def z4_time_derivatives(D, **kw):
         e[c] = 1.0
         J[:, c] = z4_residual(D, e, **kw) - f0
     unk = np.linalg.solve(J, -f0)
+    res = z4_residual(D, unk, **kw)
+    assert np.max(np.abs(res)) <= 1e-10 * max(1.0, np.max(np.abs(f0))), res
+    return unk
+
+
+def z4_time_derivatives(D, **kw):
+    """The exact time derivatives of the 27 conformal fields at the point that the solution of
+    the 11 covariant equations gives."""
+    unk = z4_unknowns(D, **kw)
     # the unknowns shift the time derivatives of K_ij, Theta, Z_j and Pi at the point
     out = D["dt"].copy()
     gam = D["g4"][1:, 1:]

@@ -5,7 +5,8 @@ sphere-averaged scalar signal:
         L_bar dL + <state_bar_N, delta state_N>   (oracle TLM, forward)
       = <state_bar_0, delta state_0> + lambda_bar delta lambda + g2_bar delta g2   (GPU, reverse)
     to 1e-10, on periodic and frozen boxes, every coupling kind, with and without
-    backreaction, with checkpoint segments shorter and longer than the run;
+    backreaction, with the cubic Horndeski term, with checkpoint segments shorter and longer
+    than the run;
   * the gradient in (lambda, g2, A) against the GPU tangent-linear evolution (grf_tlm_rk4);
   * the 96^3 differentiation workload (dx = 0.2, periodic, R = 6) for 40 steps with a checkpoint
     every 20: against central finite differences (h = 1e-6) to 1e-5 and against the tangents;
@@ -55,6 +56,9 @@ DOT_CASES = {
                                    (1.7, 0.1, -0.05, 0.07), 3, 2),
     "frozen_linear_ragged": lambda: (gi.Box(13, 11, 12, 0.45, -2.6, -2.3, -2.4, bc=gi.BC_FROZEN),
                                      gi.Params(lam=0.3, g2=0.2, beta_kind=gi.BETA_LINEAR), (1.4, 0.2, 0.0, 0.1), 2, 1),
+    "frozen_linear_cubic": lambda: (gi.Box(12, 11, 10, 0.45, -2.5, -2.3, -2.1, bc=gi.BC_FROZEN),
+                                    gi.Params(lam=0.3, g2=0.2, beta_kind=gi.BETA_LINEAR, g3=0.4), (1.4, 0.2, 0.0, 0.1),
+                                    2, 1),
     "periodic_exponential_decoupled": lambda: (gi.cube_box(10, -2.5, 2.5),
                                                gi.Params(lam=0.2, g2=0.1, beta_kind=gi.BETA_EXPONENTIAL,
                                                          beta_kappa=0.8, decoupled=1), (1.3, 0.0, 0.1, -0.1), 2, 5),

@@ -284,7 +284,8 @@ def test_bl_pair_256_sampled_outputs(g, orc):
     """Full-size 256^3 Brill-Lindquist workload, one RK4 step in the production launch
     configuration; sampled points are recomputed by the oracle on 19^3 frozen-ghost sub-boxes
     centred on them (one RK4 step has a domain of dependence of 12 points, so the centre of
-    such a sub-box is exact)."""
+    such a sub-box is exact). Each field agrees to 1e-11 of its scale, or to 64 times the
+    oracle's own rounding noise at the point where that is larger."""
     cfg = gi.config_bl_pair_256()
     box, params, dt = cfg["box"], cfg["params"], cfg["dt"]
     s0 = cfg["make_state"]()
@@ -297,23 +298,36 @@ def test_bl_pair_256_sampled_outputs(g, orc):
     # the curvature peak, so the oracle's values there give each field's scale over the box
     samples += [(i, j, k) for k in (103, 104, 151, 152) for j in (127, 128) for i in (127, 128)]
     R = 9
-    refs, gots = [], []
+    refs, noise, gots = [], [], []
     for (i, j, k) in samples:
         sub = gi.Box(2 * R + 1, 2 * R + 1, 2 * R + 1, box.dx, 0.0, 0.0, 0.0, bc=gi.BC_FROZEN)
         idx = [(np.arange(2 * R + 7) + c - R - 3) % 256 + 3 for c in (k, j, i)]
-        ss = np.ascontiguousarray(s0[:, idx[0]][:, :, idx[1]][:, :, :, idx[2]])
+        ss0 = np.ascontiguousarray(s0[:, idx[0]][:, :, idx[1]][:, :, :, idx[2]])
+        ss = ss0.copy()
         orc.rk4(sub, params, ss, dt, 1)
-        refs.append(ss[:, R + 3, R + 3, R + 3])
+        ref = ss[:, R + 3, R + 3, R + 3]
+        # the oracle's own rounding noise at this point: the spread of its result when every
+        # input is perturbed by about one unit in the last place
+        spread = np.zeros(ref.shape)
+        for seed in (1, 2):
+            sp = ss0 * (1.0 + 2.0 ** -52 * np.random.default_rng(seed).standard_normal(ss0.shape))
+            orc.rk4(sub, params, sp, dt, 1)
+            spread = np.maximum(spread, np.abs(sp[:, R + 3, R + 3, R + 3] - ref))
+        refs.append(ref)
+        noise.append(spread)
         gots.append(gpu[:, k + 3, j + 3, i + 3])
-    refs, gots = np.array(refs), np.array(gots)
+    refs, noise, gots = np.array(refs), np.array(noise), np.array(gots)
     # per-field scale from the inputs and the oracle only: the field's maximum over the whole
     # initial box, or over the oracle's sampled results (which include the points next to the
     # punctures) for fields that start at zero
     scale = np.maximum(np.maximum(np.max(np.abs(box.interior(s0)), axis=(1, 2, 3)), np.max(np.abs(refs), axis=0)),
                        1e-12)
+    # A field that one step sources by cancelling terms (the A_ij, of order 1e-7 here while the
+    # terms that make them are of order 1) carries rounding above 1e-11 of its own scale; there
+    # the bound is 64 times the oracle's rounding noise at the point instead
     for n, (i, j, k) in enumerate(samples):
-        err = np.abs(gots[n] - refs[n]) / scale
-        assert np.max(err) < 1e-11, (i, j, k, describe(err))
+        err = np.abs(gots[n] - refs[n]) / np.maximum(1e-11 * scale, 64.0 * noise[n])
+        assert np.max(err) < 1.0, (i, j, k, describe(err))
 
 
 def test_error_codes(g):

@@ -20,10 +20,11 @@ def flops():
     return fl
 
 
+@pytest.mark.parametrize("g3", [0.0, 0.45])
 @pytest.mark.parametrize("decoupled", [0, 1])
 @pytest.mark.parametrize("seed", range(6))
 @pytest.mark.parametrize("kind", [0, 1, 2])
-def test_kernel_pointwise_rhs_matches_oracle(orc, flops, seed, kind, decoupled):
+def test_kernel_pointwise_rhs_matches_oracle(orc, flops, seed, kind, decoupled, g3):
     import paper_2309_06225_gb300 as grf
     rng = np.random.default_rng(100 + seed)
     v = rng.uniform(-0.2, 0.2, 27)
@@ -34,7 +35,7 @@ def test_kernel_pointwise_rhs_matches_oracle(orc, flops, seed, kind, decoupled):
     d1 = rng.normal(size=(27, 3)) * 0.3
     d2 = rng.normal(size=(27, 6)) * 0.3
     p = gi.Params(lam=rng.uniform(0.0, 0.6), g2=rng.uniform(0.0, 0.4), beta_kind=kind, a0=0.3, b0=0.7,
-                  kappa2=0.2, kappa3=0.6, decoupled=decoupled, beta_kappa=rng.uniform(0.5, 3.0))
+                  kappa2=0.2, kappa3=0.6, decoupled=decoupled, beta_kappa=rng.uniform(0.5, 3.0), g3=g3)
     ref, diag, st = orc.point_rhs(p, v, d1, d2)
     assert st == 0
     s1, s2 = slots(d1, d2)
@@ -47,6 +48,31 @@ def test_kernel_pointwise_rhs_matches_oracle(orc, flops, seed, kind, decoupled):
     con = orc.point_constraints(p, v, d1, d2)
     # the oracle's physical forms assume nothing about tr(A); compare on the trace-free part
     np.testing.assert_allclose(extra, con, rtol=1e-9, atol=1e-9 * np.max(np.abs(con)))
+
+
+@pytest.mark.parametrize("g3", [0.0, 0.45, -0.6])
+@pytest.mark.parametrize("decoupled", [0, 1])
+@pytest.mark.parametrize("seed", range(3))
+def test_kernel_hyperbolicity_matches_oracle(orc, flops, seed, decoupled, g3):
+    """The kernel's hyperbolicity diagnostics (det M from its closed-form assembly, det g_eff /
+    det g by the determinant lemma or, with the cubic term, by the Schur complement at the solved
+    d_t Pi, and -g_eff^nn) against the oracle's full-pivot determinants on generic points."""
+    import paper_2309_06225_gb300 as grf
+    rng = np.random.default_rng(300 + seed)
+    v = rng.uniform(-0.2, 0.2, 27)
+    v[0] = rng.uniform(0.3, 1.0)
+    for m, d in zip(range(1, 7), [1, 0, 0, 1, 0, 1]):
+        v[m] = d + rng.uniform(-0.15, 0.15)
+    v[18] = rng.uniform(0.4, 1.0)
+    d1 = rng.normal(size=(27, 3)) * 0.3
+    d2 = rng.normal(size=(27, 6)) * 0.3
+    p = gi.Params(lam=rng.uniform(0.1, 0.6), g2=rng.uniform(0.0, 0.4), beta_kind=seed % 2, decoupled=decoupled,
+                  g3=g3)
+    ref = orc.point_hyperbolicity(p, v, d1, d2)
+    s1, s2 = slots(d1, d2)
+    got, st = flops.host_point_hyp(grf.params_like(p), v, s1, s2)
+    assert st == 0
+    np.testing.assert_allclose(got, ref, rtol=1e-11, atol=1e-13)
 
 
 @pytest.mark.parametrize("seed", range(4))

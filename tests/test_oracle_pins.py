@@ -119,17 +119,18 @@ def z4_point():
 
 # fields whose time derivative the spacetime fixes (the gauge fields and B^i evolve by choice)
 Z4_FIELDS = list(range(0, 18)) + [25, 26]
-Z4_CASES = [  # b, kappa1, kappa2, lambda, g2, beta kind
+Z4_CASES = [  # b, kappa1, kappa2, lambda, g2, beta kind[, g3]
     (0.0, 0.0, 0.0, 0.0, 0.0, 0), (0.0, 0.3, 0.4, 0.0, 0.0, 0), (0.4, 0.0, 0.0, 0.0, 0.0, 0),
     (0.4, 0.3, 0.4, 0.0, 0.0, 0), (1.1, 0.2, -0.3, 0.0, 0.0, 0), (0.4, 0.1, 0.0, 0.7, 0.3, 0),
-    (0.4, 0.25, 0.5, 0.5, 0.2, 1)]
+    (0.4, 0.25, 0.5, 0.5, 0.2, 1), (0.0, 0.0, 0.0, 0.0, 0.0, 0, 0.6), (0.4, 0.25, 0.5, 0.5, 0.2, 1, -0.9)]
 
 
 def _z4_compare(orc, D, case, variant="covariant"):
-    b, k1, k2, lam, g2, kind = case
-    want = an.z4_time_derivatives(D, b=b, k1=k1, k2=k2, lam=lam, g2=g2, kind=kind, variant=variant)
-    r, _, st = orc.point_rhs(P(kappa1=k1, kappa2=k2, kappa3=1.0, a0=0.2, b0=b, lam=lam, g2=g2, beta_kind=kind),
-                             D["v"], D["d1"], D["d2"])
+    b, k1, k2, lam, g2, kind = case[:6]
+    g3 = case[6] if len(case) > 6 else 0.0
+    want = an.z4_time_derivatives(D, b=b, k1=k1, k2=k2, lam=lam, g2=g2, kind=kind, variant=variant, g3=g3)
+    r, _, st = orc.point_rhs(P(kappa1=k1, kappa2=k2, kappa3=1.0, a0=0.2, b0=b, lam=lam, g2=g2, beta_kind=kind,
+                               g3=g3), D["v"], D["d1"], D["d2"])
     assert st == 0
     return np.abs(r[Z4_FIELDS] - want[Z4_FIELDS]) / np.maximum(1.0, np.abs(want[Z4_FIELDS]))
 
@@ -147,18 +148,21 @@ def test_ccz4_is_the_3p1_projection_of_covariant_modified_z4(orc, z4_point, case
     3+1 right-hand sides. b = 0 with kappa1, kappa2 != 0 pins the damping terms, including
     -3 alpha kappa1 (1 + kappa2) Theta in d_t K; b != 0 pins every b(x) term of the modified
     gauge in d_t K, d_t Theta and d_t Gamma-hat; lambda, g2 != 0 pin the 4dST matter terms
-    inside them."""
+    inside them, and g3 != 0 the cubic Horndeski term g3 X box(phi) (its stress tensor in the
+    metric equations and its share of the scalar equation, solved together with them)."""
     err = _z4_compare(orc, z4_point, case)
     assert np.max(err) < 1e-11, dict(zip(Z4_FIELDS, err))
 
 
 @pytest.mark.parametrize("variant,case", [("b_half", Z4_CASES[3]), ("b_half", Z4_CASES[6]),
+                                          ("g3_half", Z4_CASES[7]), ("g3_half", Z4_CASES[8]),
                                           ("gh_first_only", Z4_CASES[3]), ("k2_moved", Z4_CASES[1]),
                                           ("k2_moved", Z4_CASES[4])])
 def test_covariant_z4_pin_discriminates(orc, z4_point, variant, case):
     """The same comparison with a planted change in the covariant equation (half the b(x)
     coefficient; g instead of gh in the trace term of Phat; 1 + kappa2 in place of kappa2 in the
-    damping) must fail by far more than the tolerance: the pin above sees each of these terms."""
+    damping; half the cubic coefficient in the stress tensor) must fail by far more than the
+    tolerance: the pin above sees each of these terms."""
     err = _z4_compare(orc, z4_point, case, variant)
     assert np.max(err) > 1e-6
 
@@ -764,32 +768,33 @@ def spacetime():
 KAPPA = 0.8  # exponential coupling scale used by the brute-force pins
 
 
-def _stress_at(at, phifn, pt, lam, g2, kind):
+def _stress_at(at, phifn, pt, lam, g2, kind, g3=0.0):
     g, dg, ddg, dphi, ddphi = at(pt)
     gi4, Gam, Rdn, Ric, Rs = an.geometry4(g, dg, ddg)
-    T8, E, LGB, T8gb = an.stress_and_scalar(g, gi4, Gam, Rdn, Ric, Rs, dphi, ddphi, phifn(*pt), lam, g2, kind,
-                                            KAPPA)
-    return g, gi4, Gam, T8, E, LGB, dphi, T8gb
+    T8, E, LGB, T8gb, T8c = an.stress_and_scalar(g, gi4, Gam, Rdn, Ric, Rs, dphi, ddphi, phifn(*pt), lam, g2,
+                                                 kind, KAPPA, g3=g3, parts=True)
+    return g, gi4, Gam, T8, E, LGB, dphi, T8gb, T8c
 
 
-@pytest.mark.parametrize("kind", [0, 1, 2])
-def test_3p1_assembly_matches_4d_brute_force(orc, spacetime, kind):
+@pytest.mark.parametrize("kind,g3", [(0, 0.0), (1, 0.0), (2, 0.0), (1, 0.6), (0, -0.9)])
+def test_3p1_assembly_matches_4d_brute_force(orc, spacetime, kind, g3):
     """The oracle's 3+1 assembly (Gauss/Codazzi/Ricci-equation blocks in the (n, d_i) basis,
     nabla nabla phi projections, T and the scalar equation) reproduces rho, S_i, S_ij, L_GB and
     the scalar-equation residual of a brute-force 4D coordinate computation on a generic
-    non-vacuum spacetime with lapse, shift, K_ij, d_t K_ij and a scalar all non-trivial."""
+    non-vacuum spacetime with lapse, shift, K_ij, d_t K_ij and a scalar all non-trivial; with
+    g3 != 0 the cubic Horndeski term's stress tensor and scalar-equation share are included."""
     T, alpha, beta_u, g, phi, at, phifn = spacetime
     lam, g2 = 0.7, 0.3
     pt = (0.3, 0.4, -0.2, 0.5)
     ab = an.evaluate([alpha] + list(beta_u), T, pt)
-    g4v, gi4, Gam, T8, E, LGB, dphi, _ = _stress_at(at, phifn, pt, lam, g2, kind)
+    g4v, gi4, Gam, T8, E, LGB, dphi, _, _ = _stress_at(at, phifn, pt, lam, g2, kind, g3)
     a, bu = ab[0], ab[1:4]
     n_up = np.concatenate([[1.0 / a], -bu / a])
     rho8 = n_up @ T8 @ n_up
     S8 = -(T8 @ n_up)[1:]
     Sij8 = T8[1:, 1:]
     phys, u6, w = an.phys_pack_generic(alpha, beta_u, g, phi, T, pt)
-    p = P(lam=lam, g2=g2, beta_kind=kind, beta_kappa=KAPPA)
+    p = P(lam=lam, g2=g2, beta_kind=kind, beta_kappa=KAPPA, g3=g3)
     out = orc.phys_sources(p, phys, u6, w)
     scale = max(1.0, abs(rho8), np.max(np.abs(Sij8)))
     assert abs(out[0] - rho8) < 1e-10 * scale
@@ -848,28 +853,30 @@ def test_psi4_vanishes_for_schwarzschild_with_the_radial_tetrad(orc, ks_data):
         assert abs(orc.point_psi4(p, v, d1, d2, off)) > 1e-4
 
 
-@pytest.mark.parametrize("kind", [0, 1, 2])
-def test_effective_stress_tensor_obeys_bianchi(spacetime, kind):
+@pytest.mark.parametrize("kind,g3", [(0, 0.0), (1, 0.0), (2, 0.0), (1, 0.6), (0, -0.9)])
+def test_effective_stress_tensor_obeys_bianchi(spacetime, kind, g3):
     """Contracted Bianchi identity, off shell: nabla^m (8 pi T_mn) = (1/2) E d_n phi for the
-    4dST effective stress tensor, on a generic spacetime. This fixes the Gauss-Bonnet
-    coefficient (-4 P nabla nabla beta in 8 pi T) relative to the first-order terms and to
-    the scalar equation: a coefficient of -2, +4 or -8 fails by O(L_GB beta' d phi)."""
+    4dST effective stress tensor (with the cubic Horndeski term g3 X box(phi) where g3 != 0), on
+    a generic spacetime. This fixes the Gauss-Bonnet coefficient (-4 P nabla nabla beta in
+    8 pi T) relative to the first-order terms and to the scalar equation: a coefficient of -2,
+    +4 or -8 fails by O(L_GB beta' d phi); likewise the cubic stress tensor relative to the
+    cubic scalar-equation terms (box(phi)^2 - nabla nabla phi . nabla nabla phi - R(d phi, d phi))."""
     T, alpha, beta_u, g, phi, at, phifn = spacetime
     lam, g2 = 0.7, 0.3
     pt = np.array([0.3, 0.4, -0.2, 0.5])
-    g4v, gi4, Gam, T8, E, LGB, dphi, T8gb = _stress_at(at, phifn, tuple(pt), lam, g2, kind)
+    g4v, gi4, Gam, T8, E, LGB, dphi, T8gb, T8c = _stress_at(at, phifn, tuple(pt), lam, g2, kind, g3)
     h = 2e-3
     wts = {-3: -1 / 60, -2: 3 / 20, -1: -3 / 4, 1: 3 / 4, 2: -3 / 20, 3: 1 / 60}
 
-    def divergence(gb_factor):
+    def divergence(gb_factor, cubic_factor=1.0):
         dT = np.zeros((4, 4, 4))  # dT[r][m][n]
         for r in range(4):
             for o, wgt in wts.items():
                 q = pt.copy()
                 q[r] += o * h
-                res = _stress_at(at, phifn, tuple(q), lam, g2, kind)
-                dT[r] += wgt * (res[3] + (gb_factor - 1.0) * res[7]) / h
-        Tc = T8 + (gb_factor - 1.0) * T8gb
+                res = _stress_at(at, phifn, tuple(q), lam, g2, kind, g3)
+                dT[r] += wgt * (res[3] + (gb_factor - 1.0) * res[7] + (cubic_factor - 1.0) * res[8]) / h
+        Tc = T8 + (gb_factor - 1.0) * T8gb + (cubic_factor - 1.0) * T8c
         cov = dT - np.einsum("lrm,ln->rmn", Gam, Tc) - np.einsum("lrn,ml->rmn", Gam, Tc)
         return np.einsum("rm,rmn->n", gi4, cov), np.max(np.abs(cov))
 
@@ -878,9 +885,10 @@ def test_effective_stress_tensor_obeys_bianchi(spacetime, kind):
     tol = 1e-9 * max(1.0, scale)
     np.testing.assert_allclose(div, rhs, atol=tol)
     # discrimination: the same identity fails by far more than the tolerance when the
-    # Gauss-Bonnet term carries half, or minus, its coefficient
-    for wrong in (0.5, -1.0):
-        div_w, _ = divergence(wrong)
+    # Gauss-Bonnet term carries half, or minus, its coefficient (or the cubic term half of its)
+    wrongs = [(0.5, 1.0), (-1.0, 1.0)] + ([(1.0, 0.5)] if g3 else [])
+    for gbf, cf in wrongs:
+        div_w, _ = divergence(gbf, cf)
         assert np.max(np.abs(div_w - rhs)) > 1e3 * tol
 
 
@@ -1388,3 +1396,45 @@ def test_effective_metric_of_the_scalar_equation(orc, conformal_generic, g2):
         got = (orc.point_rhs(p, v, d1, dd)[0][26] - base) / 1e-3
         want = al * geff[i, j] / D * (1.0 if i == j else 2.0)
         assert got == pytest.approx(want, rel=1e-8, abs=1e-11), (i, j)
+
+
+@pytest.mark.parametrize("g3,lam,g2", [(0.6, 0.0, 0.0), (-0.9, 0.5, 0.2)])
+def test_cubic_effective_metric_against_brute_force(orc, z4_point, g3, lam, g2):
+    """With the cubic term the scalar equation's principal symbol g_eff^ab = dE/d(nabla_a nabla_b phi)
+    depends on the second derivatives of phi themselves: 2 g3 (box(phi) g^ab - nabla^a nabla^b phi)
+    joins the X and X^2 terms. The covariant Z4 solution at the generic point gives the 4D second
+    derivatives of the metric and of phi; central differences of the brute-force E (quadratic in
+    nabla nabla phi, so exact) give g_eff there, and its invariants det(g_eff)/det(g) and
+    -g_eff(n, n) must equal the oracle's second and third diagnostics (which evaluate the symbol at
+    the oracle's own solution of the 7x7 system)."""
+    D = z4_point
+    kw = dict(b=0.4, k1=0.25, k2=0.5, lam=lam, g2=g2, kind=1, g3=g3)
+    unk = an.z4_unknowns(D, **kw)
+    ddg = D["ddg"].copy()
+    for m, (i, j) in enumerate(an.SYM_PAIRS):
+        ddg[0, 0, i + 1, j + 1] += unk[m]
+        if i != j:
+            ddg[0, 0, j + 1, i + 1] += unk[m]
+    ddphi = D["ddphi"].copy()
+    ddphi[0, 0] += unk[10]
+    g = D["g4"]
+    gi4, Gam, Rdn, Ric, Rs = an.geometry4(g, D["dg"], ddg)
+
+    def E_of(dd):
+        return an.stress_and_scalar(g, gi4, Gam, Rdn, Ric, Rs, D["dphi"], dd, D["phi"], lam, g2, 1, g3=g3)[1]
+    geff = np.zeros((4, 4))
+    eps = 1e-3
+    for a in range(4):
+        for b in range(a, 4):
+            e = np.zeros((4, 4))
+            e[a, b] += 0.5 * eps
+            e[b, a] += 0.5 * eps
+            geff[a, b] = geff[b, a] = (E_of(ddphi + e) - E_of(ddphi - e)) / (2 * eps)
+    al = 1.0 / math.sqrt(-gi4[0, 0])
+    ratio = np.linalg.det(geff) / np.linalg.det(gi4)
+    dnn = -al * al * geff[0, 0]
+    h = orc.point_hyperbolicity(P(kappa1=0.25, kappa2=0.5, kappa3=1.0, a0=0.2, b0=0.4, lam=lam, g2=g2,
+                                  beta_kind=1, g3=g3), D["v"], D["d1"], D["d2"])
+    assert abs(ratio - 1.0) > 1e-3 and abs(dnn - 1.0) > 1e-3  # the cubic term changes both
+    assert h[1] == pytest.approx(ratio, rel=1e-9)
+    assert h[2] == pytest.approx(dnn, rel=1e-9)
