@@ -114,6 +114,9 @@ def parse():
                          "grids are for profiling captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-sub-records", action="store_true",
+                    help="skip the short same-process runs of the batched, differentiated and split-box workloads "
+                         "that the default line carries under sub_records")
     ap.add_argument("--decoupled", action="store_true",
                     help="4dST without backreaction onto the metric (bl_pair workloads)")
     ap.add_argument("--order", type=int, default=4, choices=[4, 6],
@@ -324,7 +327,7 @@ def run_tangent(args, rank, world, local_rank):
                        "peak": fp64_issue_ceiling(2070.0), "frac": issue,
                        "peak_source": "2 FP64 instructions per SM per clock x 152 SMs x 2070 MHz",
                        "fp64_instr_per_point_stage": TLM_FP64_INSTR_PER_POINT_STAGE, "traffic": None}
-    print(json.dumps(out), flush=True)
+    return out
 
 
 def run_adjoint(args, rank, world, local_rank):
@@ -408,7 +411,7 @@ def run_adjoint(args, rank, world, local_rank):
                        "workspace_bytes": grf.grf_adjoint_workspace_bytes(b, ce)},
            "signal": float(loss.cpu()[0]), "gradient": grad, "clocks": clk, "roofline": None, "e2e": None,
            "cpu_baseline": None}
-    print(json.dumps(out), flush=True)
+    return out
 
 
 def run_batched(args, rank, world, local_rank):
@@ -501,7 +504,7 @@ def run_batched(args, rank, world, local_rank):
            "e2e": {"value": npts * args.steps / (ems * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                    "d2h_bytes_per_step": nbytes, "ms_per_step": ems / args.steps},
            "cpu_baseline": None}
-    print(json.dumps(out), flush=True)
+    return out
 
 
 def run_patches(args, rank, world, local_rank):
@@ -586,7 +589,7 @@ def run_patches(args, rank, world, local_rank):
            "e2e": {"value": npts * args.steps / (ems * 1e-3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                    "d2h_bytes_per_step": nbytes, "ms_per_step": ems / args.steps},
            "cpu_baseline": None}
-    print(json.dumps(out), flush=True)
+    return out
 
 
 # ------------------------------------------------------------------------------ clocks
@@ -738,6 +741,40 @@ def run_reference(args, rank):
 
 
 # ------------------------------------------------------------------------------ GPU arm
+SUB_RECORD_DROP = ("n_gpus", "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "cpu_baseline")
+
+
+def sub_records(args, local_rank):
+    """Short runs of the other workloads in this process, after the headline measurement: the 96
+    AMR-like boxes in one batched launch (with the single-box path beside it), the tangent-linear
+    and the reverse-mode differentiated 96^3 evolutions (each against the plain step), and the
+    256^3 box split into 2 x 2 x 2 patches (with the halo exchange timed alone). Each keeps its
+    own timing rules (CUDA events, warm-up, clocks) with fewer steps than its own workload line."""
+    import argparse
+    import torch
+    recs = {}
+    plan = [("batched_amr_boxes_96", run_batched, "amr_boxes_96", 5, 3),
+            ("tangent_sphere_signal_96", run_tangent, "sphere_signal_96", 8, 3),
+            ("adjoint_96", run_adjoint, "adjoint_96", 4, 3),
+            ("patches_256", run_patches, "patches_256", 4, 3)]
+    for name, fn, wl, steps, warmup in plan:
+        a = argparse.Namespace(**vars(args))
+        a.workload, a.steps, a.warmup = wl, steps, warmup
+        t0 = time.time()
+        try:
+            r = fn(a, 0, 1, local_rank)
+        except (RuntimeError, OSError, ValueError) as e:  # reported in the line, the headline stands
+            recs[name] = {"error": f"{type(e).__name__}: {e}"}
+            continue
+        finally:
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+        rec = {k: v for k, v in r.items() if k not in SUB_RECORD_DROP}
+        rec["wall_s"] = time.time() - t0
+        recs[name] = rec
+    return recs
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -891,6 +928,11 @@ def run_ours(args, rank, world, local_rank):
            "status": {"solve": status, "finite": finite}}
     if box.bc in (2, 5):  # an octant with mirror planes evolves the symmetric full box on 1/8 of its points
         out["config"]["full_box_equivalent_point_updates_per_s"] = 8 * value
+    if world == 1 and not args.no_sub_records and args.workload == "bl_pair_256" and default_scheme \
+            and box.bc == 0 and not args.decoupled:
+        del state, init, ws
+        torch.cuda.empty_cache()
+        out["sub_records"] = sub_records(args, local_rank)
     print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -904,20 +946,15 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank)
         return
-    if args.workload == "sphere_signal_96":
-        run_tangent(args, rank, world, local_rank)
-        return
-    if args.workload == "adjoint_96":
-        run_adjoint(args, rank, world, local_rank)
-        return
     if args.workload in ("calls_256", "calls_96"):
         run_calls(args, rank, world, local_rank)
         return
-    if args.workload == "patches_256":
-        run_patches(args, rank, world, local_rank)
-        return
-    if args.workload in ("amr_boxes_96", "coupling_sweep_32"):
-        run_batched(args, rank, world, local_rank)
+    runs = {"sphere_signal_96": run_tangent, "adjoint_96": run_adjoint, "patches_256": run_patches,
+            "amr_boxes_96": run_batched, "coupling_sweep_32": run_batched}
+    if args.workload in runs:
+        out = runs[args.workload](args, rank, world, local_rank)
+        if out is not None and rank == 0:
+            print(json.dumps(out), flush=True)
         return
     run_ours(args, rank, world, local_rank)
 
