@@ -14,11 +14,13 @@
 //   u_s = E(u_n + c_s dt k_s)  (s = 1..3, c = 1/2, 1/2, 1),  u_{n+1} = E(u_n + dt/6 (acc + k_4)),
 //   k_s = F(u_{s-1}) = f(u, D u, D^2 u; lambda, g2) + KO(u),   acc = k_1 + 2 k_2 + 2 k_3,
 // with E the algebraic enforcement. Reversing stage s at a point p:
-//   * adj_stage_kernel re-evaluates the pointwise map (f, the stage update and E) on the
-//     reverse-mode scalar grf_rev::Rev, seeds the adjoints of the outputs (u_s, and the stage's
-//     contribution to acc), sweeps the tape backwards and obtains the adjoints of its inputs:
-//     the values of u_{s-1}, u_n and acc at p, the first and second derivatives and the KO sum
-//     of u_{s-1} at p, and lambda, g2;
+//   * adj_tape_kernel re-evaluates the pointwise map (f, the stage update and E) on the
+//     reverse-mode scalar grf_rev::Rev, recording one tape per point, and seeds the adjoints of
+//     the outputs (u_s, and the stage's contribution to acc);
+//   * adj_sweep_kernel, a light kernel run at high occupancy, sweeps each tape backwards and
+//     obtains the adjoints of the map's inputs: the values of u_{s-1}, u_n and acc at p, the
+//     first and second derivatives and the KO sum of u_{s-1} at p, and lambda, g2. The two run
+//     in waves of kAdjCols points, one tape column per point;
 //   * adj_transpose_kernel applies the transposed stencils to the derivative and KO adjoints:
 //     the first-difference stencil is antisymmetric (its transpose is -D), the second and mixed
 //     ones and KO are symmetric, so u_{s-1}'s adjoint at q collects -D(G_d1) + D2(G_d2) + KO(G_ko)
@@ -48,7 +50,10 @@ enum : int { kLV = 0, kLD1 = 27, kLD2 = 99, kLKO = 171, kLUN = 198, kLACC = 225,
 // enforcement about 130 more; an overflow is detected and reported
 constexpr int kTapeCap = 5120;
 constexpr int kAdjThreads = 128;
-constexpr long long kAdjCols = 152LL * 2 * kAdjThreads;  // tape columns: 2 blocks of 128 per SM of a GB300
+// tape columns (points per wave): 512 per SM of a GB300, so that the sweep has 16 warps per SM to
+// hide its dependent memory operations (the taping kernel, at 255 registers, holds 8)
+constexpr long long kAdjCols = 152LL * 512;
+constexpr int kSweepThreads = 256;
 // derivative and dissipation adjoints per point (slots of the G buffer): d1 72, d2 72, KO 27
 constexpr int kGD2 = 72, kGKO = 144, kGSlots = 171;
 
@@ -62,6 +67,7 @@ struct AdjArgs {
     double* unbar;        // adjoint of u_n (stage 3 writes it, stages 2..0 add)
     double* G;            // kGSlots derivative / KO adjoints, with periodic images
     double* pbar;         // per-column sums of the lambda and g2 adjoints
+    int* count;           // tape entries of each column (written by the taping kernel)
     double dt, ko, min_chi, min_lapse;
     int enforce;
     int* status;
@@ -84,120 +90,141 @@ __device__ __forceinline__ void enforce_point_t(T u[NFIELDS], double min_chi, do
 
 // Reverse sweep of this column's tape: node adjoints are consumed (reset to zero) as they are
 // propagated, so the column is clean for its next point.
+// The tape entries do not depend on the adjoints, so the next entry is loaded while the current
+// one is applied.
 __device__ __forceinline__ void rev_sweep(int entries, long long col) {
     const long long S = grf_rev::c_tape.stride;
     double* __restrict__ adj = grf_rev::c_tape.adj;
     const double2* __restrict__ w = grf_rev::c_tape.w;
     const ushort4* __restrict__ ix = grf_rev::c_tape.ix;
+    if (entries <= 0) return;
+    double2 pw = __ldcs(&w[(long long)(entries - 1) * S + col]);
+    ushort4 o = __ldcs(&ix[(long long)(entries - 1) * S + col]);
 #pragma unroll 1
     for (int n = entries - 1; n >= 0; --n) {
+        const double2 pc = pw;
+        const ushort4 oc = o;
+        if (n > 0) {
+            pw = __ldcs(&w[(long long)(n - 1) * S + col]);
+            o = __ldcs(&ix[(long long)(n - 1) * S + col]);
+        }
         const long long node = (long long)(kNLeaf + n) * S + col;
         const double g = adj[node];
         if (g == 0.0) continue;
         adj[node] = 0.0;
-        const long long off = (long long)n * S + col;
-        const double2 pw = w[off];
-        const ushort4 o = ix[off];
-        if (o.x != grf_rev::kNone) adj[(long long)o.x * S + col] += pw.x * g;
-        if (o.y != grf_rev::kNone) adj[(long long)o.y * S + col] += pw.y * g;
-        if (o.z != grf_rev::kNone) adj[(long long)o.z * S + col] += g;
+        if (oc.x != grf_rev::kNone) adj[(long long)oc.x * S + col] += pc.x * g;
+        if (oc.y != grf_rev::kNone) adj[(long long)oc.y * S + col] += pc.y * g;
+        if (oc.z != grf_rev::kNone) adj[(long long)oc.z * S + col] += g;
     }
 }
 
 // STAGE (0..3) is a run-time argument: one instantiation of the large pointwise map keeps the
 // library's build time down (its four stage variants differ only in a few scalars and leaves).
-__global__ void __launch_bounds__(kAdjThreads) adj_stage_kernel(Geom g, Coeffs c, AdjArgs a, int STAGE) {
+// Thread col tapes point q0 + col of the wave into tape column col.
+__global__ void __launch_bounds__(kAdjThreads) adj_tape_kernel(Geom g, Coeffs c, AdjArgs a, int STAGE, long long q0) {
     const long long col = grf_rev::rev_col();
-    const long long ncol = (long long)gridDim.x * blockDim.x;
+    const long long q = q0 + col;
+    if (col >= grf_rev::c_tape.stride || q >= a.npts) return;
     const long long S = grf_rev::c_tape.stride;
     double* adj = grf_rev::c_tape.adj;
     const double cs = (STAGE == 0 || STAGE == 1) ? 0.5 * a.dt : (STAGE == 2 ? a.dt : a.dt * (1.0 / 6.0));
     const double wacc = (STAGE == 0) ? 1.0 : 2.0;  // weight of k_s in the accumulator (stages 0..2)
     const long long nxy = (long long)g.nx * g.ny;
-    double lam_bar = 0.0, g2_bar = 0.0;
+    const int k = (int)(q / nxy);
+    const long long rem = q - (long long)k * nxy;
+    const int j = (int)(rem / g.nx), i = (int)(rem - (long long)j * g.nx);
+    const long long p = gidx(g, i + NG, j + NG, k + NG);
+    PointIn in;
+    double kos[NFIELDS];
+    gather<0>(g, a.src, p, in, kos, nullptr, nullptr, 0);
+    grf_rev::s_count[threadIdx.x] = 0;
+    PointInT<Rev> ir;
+#pragma unroll 1
+    for (int f = 0; f < NFIELDS; ++f) ir.v[f] = Rev(in.v[f], kLV + f);
+#pragma unroll 1
+    for (int m = 0; m < 24; ++m)
+        for (int d = 0; d < 3; ++d) ir.d1[m][d] = Rev(in.d1[m][d], kLD1 + 3 * m + d);
+#pragma unroll 1
+    for (int b = 0; b < 12; ++b)
+        for (int m = 0; m < 6; ++m) ir.d2[b][m] = Rev(in.d2[b][m], kLD2 + 6 * b + m);
+    CoeffsT<Rev> cr;
+    cr.kappa1 = c.kappa1; cr.kappa2 = c.kappa2; cr.kappa3 = c.kappa3; cr.shift_F = c.shift_F; cr.eta = c.eta;
+    cr.lam = Rev(c.lam, kLLAM);
+    cr.g3 = c.g3;
+    cr.g2 = Rev(c.g2, kLG2);
+    cr.inv_1pa = c.inv_1pa; cr.a_1pa = c.a_1pa; cr.bK = c.bK; cr.bTh = c.bTh;
+    cr.beta_kind = c.beta_kind; cr.beta_kappa = c.beta_kappa; cr.decoupled = c.decoupled; cr.advection = 0;
+    Rev r[NFIELDS];
+    bool ok = true;
+    point_rhs<Rev, Rev, -1, 0, 1>(cr, ir, r, nullptr, ok);
+    if (!ok) atomicOr(a.status, 1);
+    Rev out[NFIELDS];
+    int knode[NFIELDS];
+#pragma unroll 1
+    for (int f = 0; f < NFIELDS; ++f) {
+        const long long o = f * g.fstride + p;
+        const Rev kf = r[f] + a.ko * Rev(kos[f], kLKO + f);
+        knode[f] = kf.i;
+        const Rev unf = (STAGE == 0) ? ir.v[f] : Rev(a.un[o], kLUN + f);
+        out[f] = (STAGE == 3) ? fma(Rev(cs), Rev(a.acc[o], kLACC + f) + kf, unf) : fma(Rev(cs), kf, unf);
+    }
+    if (a.enforce) enforce_point_t(out, a.min_chi, a.min_lapse);
+    // seeds: the adjoint of the stage output, and (stages 0..2) of k_s through the accumulator
+#pragma unroll 1
+    for (int f = 0; f < NFIELDS; ++f) {
+        const long long o = f * g.fstride + p;
+        const double sb = a.ubar[o];
+        if (out[f].i >= 0 && sb != 0.0) adj[(long long)out[f].i * S + col] += sb;
+        if (STAGE < 3) {
+            const double ab = a.abar[o];
+            if (knode[f] >= 0 && ab != 0.0) adj[(long long)knode[f] * S + col] += wacc * ab;
+        }
+    }
+    a.count[col] = min(grf_rev::s_count[threadIdx.x], grf_rev::c_tape.cap);
+}
+
+// Sweeps tape column col (point q0 + col) and hands the leaves' adjoints to the stage's outputs:
+// the values' to vbar / unbar / abar, the derivative and KO sums' to G (with periodic images),
+// lambda's and g2's to the column's sums.
+__global__ void __launch_bounds__(kSweepThreads) adj_sweep_kernel(Geom g, AdjArgs a, int STAGE, long long q0) {
+    const long long col = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long q = q0 + col;
+    if (col >= grf_rev::c_tape.stride || q >= a.npts) return;
+    const long long S = grf_rev::c_tape.stride;
+    double* adj = grf_rev::c_tape.adj;
     auto take = [&](int leaf) {
         const long long o = (long long)leaf * S + col;
         const double x = adj[o];
         adj[o] = 0.0;
         return x;
     };
+    rev_sweep(a.count[col], col);
+    const long long nxy = (long long)g.nx * g.ny;
+    const int k = (int)(q / nxy);
+    const long long rem = q - (long long)k * nxy;
+    const int j = (int)(rem / g.nx), i = (int)(rem - (long long)j * g.nx);
+    const long long p = gidx(g, i + NG, j + NG, k + NG);
 #pragma unroll 1
-    for (long long q = col; q < a.npts; q += ncol) {
-        const int k = (int)(q / nxy);
-        const long long rem = q - (long long)k * nxy;
-        const int j = (int)(rem / g.nx), i = (int)(rem - (long long)j * g.nx);
-        const long long p = gidx(g, i + NG, j + NG, k + NG);
-        PointIn in;
-        double kos[NFIELDS];
-        gather<0>(g, a.src, p, in, kos, nullptr, nullptr, 0);
-        grf_rev::s_count[threadIdx.x] = 0;
-        PointInT<Rev> ir;
-#pragma unroll 1
-        for (int f = 0; f < NFIELDS; ++f) ir.v[f] = Rev(in.v[f], kLV + f);
-#pragma unroll 1
-        for (int m = 0; m < 24; ++m)
-            for (int d = 0; d < 3; ++d) ir.d1[m][d] = Rev(in.d1[m][d], kLD1 + 3 * m + d);
-#pragma unroll 1
-        for (int b = 0; b < 12; ++b)
-            for (int m = 0; m < 6; ++m) ir.d2[b][m] = Rev(in.d2[b][m], kLD2 + 6 * b + m);
-        CoeffsT<Rev> cr;
-        cr.kappa1 = c.kappa1; cr.kappa2 = c.kappa2; cr.kappa3 = c.kappa3; cr.shift_F = c.shift_F; cr.eta = c.eta;
-        cr.lam = Rev(c.lam, kLLAM);
-        cr.g3 = c.g3;
-        cr.g2 = Rev(c.g2, kLG2);
-        cr.inv_1pa = c.inv_1pa; cr.a_1pa = c.a_1pa; cr.bK = c.bK; cr.bTh = c.bTh;
-        cr.beta_kind = c.beta_kind; cr.beta_kappa = c.beta_kappa; cr.decoupled = c.decoupled; cr.advection = 0;
-        Rev r[NFIELDS];
-        bool ok = true;
-        point_rhs<Rev, Rev, -1, 0, 1>(cr, ir, r, nullptr, ok);
-        if (!ok) atomicOr(a.status, 1);
-        Rev out[NFIELDS];
-        int knode[NFIELDS];
-#pragma unroll 1
-        for (int f = 0; f < NFIELDS; ++f) {
-            const long long o = f * g.fstride + p;
-            const Rev kf = r[f] + a.ko * Rev(kos[f], kLKO + f);
-            knode[f] = kf.i;
-            const Rev unf = (STAGE == 0) ? ir.v[f] : Rev(a.un[o], kLUN + f);
-            out[f] = (STAGE == 3) ? fma(Rev(cs), Rev(a.acc[o], kLACC + f) + kf, unf) : fma(Rev(cs), kf, unf);
+    for (int f = 0; f < NFIELDS; ++f) {
+        const long long o = f * g.fstride + p;
+        const double vb = take(kLV + f);
+        if (STAGE == 0) {
+            a.unbar[o] += vb;
+        } else {
+            a.vbar[o] = vb;
+            const double ub = take(kLUN + f);
+            if (STAGE == 3) a.unbar[o] = ub;
+            else a.unbar[o] += ub;
         }
-        if (a.enforce) enforce_point_t(out, a.min_chi, a.min_lapse);
-        // seeds: the adjoint of the stage output, and (stages 0..2) of k_s through the accumulator
-#pragma unroll 1
-        for (int f = 0; f < NFIELDS; ++f) {
-            const long long o = f * g.fstride + p;
-            const double sb = a.ubar[o];
-            if (out[f].i >= 0 && sb != 0.0) adj[(long long)out[f].i * S + col] += sb;
-            if (STAGE < 3) {
-                const double ab = a.abar[o];
-                if (knode[f] >= 0 && ab != 0.0) adj[(long long)knode[f] * S + col] += wacc * ab;
-            }
-        }
-        rev_sweep(min(grf_rev::s_count[threadIdx.x], grf_rev::c_tape.cap), col);
-#pragma unroll 1
-        for (int f = 0; f < NFIELDS; ++f) {
-            const long long o = f * g.fstride + p;
-            const double vb = take(kLV + f);
-            if (STAGE == 0) {
-                a.unbar[o] += vb;
-            } else {
-                a.vbar[o] = vb;
-                const double ub = take(kLUN + f);
-                if (STAGE == 3) a.unbar[o] = ub;
-                else a.unbar[o] += ub;
-            }
-            if (STAGE == 3) a.abar[o] = take(kLACC + f);
-            store_with_images(g, a.G, kGKO + f, i, j, k, take(kLKO + f));
-        }
-#pragma unroll 1
-        for (int m = 0; m < 72; ++m) store_with_images(g, a.G, m, i, j, k, take(kLD1 + m));
-#pragma unroll 1
-        for (int m = 0; m < 72; ++m) store_with_images(g, a.G, kGD2 + m, i, j, k, take(kLD2 + m));
-        lam_bar += take(kLLAM);
-        g2_bar += take(kLG2);
+        if (STAGE == 3) a.abar[o] = take(kLACC + f);
+        store_with_images(g, a.G, kGKO + f, i, j, k, take(kLKO + f));
     }
-    a.pbar[2 * col] += lam_bar;
-    a.pbar[2 * col + 1] += g2_bar;
+#pragma unroll 1
+    for (int m = 0; m < 72; ++m) store_with_images(g, a.G, m, i, j, k, take(kLD1 + m));
+#pragma unroll 1
+    for (int m = 0; m < 72; ++m) store_with_images(g, a.G, kGD2 + m, i, j, k, take(kLD2 + m));
+    a.pbar[2 * col] += take(kLLAM);
+    a.pbar[2 * col + 1] += take(kLG2);
 }
 
 // X(q) += transposed stencils of the derivative / KO adjoints at interior q:
@@ -386,7 +413,7 @@ size_t sbytes(const Geom& g) { return sizeof(double) * (size_t)NFIELDS * (size_t
 
 long long adj_cols(const Geom& g) {
     const long long npts = (long long)g.nx * g.ny * g.nz;
-    const long long want = (npts + kAdjThreads - 1) / kAdjThreads * kAdjThreads;
+    const long long want = (npts + kSweepThreads - 1) / kSweepThreads * kSweepThreads;
     return want < kAdjCols ? want : kAdjCols;
 }
 
@@ -395,9 +422,9 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // Workspace layout (every region 256-byte aligned):
 //   status | stage region [U1 | U2 | ACC | U3] | adjoint states [W | UBn | Va | Vb | Abar] |
 //   G (171 slots) | segment states (checkpoint_every) | tape partials | tape operands |
-//   node adjoints | per-column parameter sums | dot-product partials
+//   node adjoints | per-column parameter sums | per-column tape lengths | dot-product partials
 struct Layout {
-    size_t status, stage, adjs, G, seg, w, ix, adj, pbar, part, total;
+    size_t status, stage, adjs, G, seg, w, ix, adj, pbar, count, part, total;
 };
 
 Layout layout(const Geom& g, int ce) {
@@ -414,6 +441,7 @@ Layout layout(const Geom& g, int ce) {
     L.ix = o; o += align256(sizeof(ushort4) * (size_t)kTapeCap * (size_t)cols);
     L.adj = o; o += align256(sizeof(double) * (size_t)(kNLeaf + kTapeCap) * (size_t)cols);
     L.pbar = o; o += align256(sizeof(double) * 2 * (size_t)cols);
+    L.count = o; o += align256(sizeof(int) * (size_t)cols);
     L.part = o; o += align256(sizeof(double) * kDotBlocks);
     L.total = o;
     return L;
@@ -569,8 +597,17 @@ int grf_adjoint_rk4(const grf_box* box, const grf_params* params, const double* 
     a.G = G;
     a.pbar = pbar;
     a.abar = Abar;
+    a.count = (int*)(base + L.count);
     const dim3 tgrd((g.nx + 31) / 32, (g.ny + 3) / 4, g.nz), tblk(32, 4, 1);
-    const int ablocks = (int)(cols / kAdjThreads);
+    const int tblocks = (int)((cols + kAdjThreads - 1) / kAdjThreads);
+    const int sblocks = (int)((cols + kSweepThreads - 1) / kSweepThreads);
+    // one reversed stage: waves of `cols` points, each taped, then swept
+    auto reverse_stage = [&](int stage) {
+        for (long long q0 = 0; q0 < a.npts; q0 += cols) {
+            adj_tape_kernel<<<tblocks, kAdjThreads, 0, st>>>(g, c, a, stage, q0);
+            adj_sweep_kernel<<<sblocks, kSweepThreads, 0, st>>>(g, a, stage, q0);
+        }
+    };
     const double sx0 = box->x0, sy0 = box->y0, sz0 = box->z0;
     auto seed_signal = [&](double* ub) {
         if (loss_bar != 0.0)
@@ -600,19 +637,19 @@ int grf_adjoint_rk4(const grf_box* box, const grf_params* params, const double* 
             a.acc = ACC;
             // stage 3: u_{n+1} = E(u_n + dt/6 (acc + k_4)), k_4 = F(u_3)
             a.src = U3; a.ubar = W; a.vbar = Va; a.unbar = UBn;
-            adj_stage_kernel<<<ablocks, kAdjThreads, 0, st>>>(g, c, a, 3);
+            reverse_stage(3);
             adj_transpose_kernel<<<tgrd, tblk, 0, st>>>(g, G, Va);
             // stage 2: u_3 = E(u_n + dt k_3), k_3 = F(u_2)
             a.src = U2; a.ubar = Va; a.vbar = Vb;
-            adj_stage_kernel<<<ablocks, kAdjThreads, 0, st>>>(g, c, a, 2);
+            reverse_stage(2);
             adj_transpose_kernel<<<tgrd, tblk, 0, st>>>(g, G, Vb);
             // stage 1: u_2 = E(u_n + dt/2 k_2), k_2 = F(u_1)
             a.src = U1; a.ubar = Vb; a.vbar = Va;
-            adj_stage_kernel<<<ablocks, kAdjThreads, 0, st>>>(g, c, a, 1);
+            reverse_stage(1);
             adj_transpose_kernel<<<tgrd, tblk, 0, st>>>(g, G, Va);
             // stage 0: u_1 = E(u_n + dt/2 k_1), k_1 = F(u_n)
             a.src = un; a.ubar = Va; a.vbar = nullptr;
-            adj_stage_kernel<<<ablocks, kAdjThreads, 0, st>>>(g, c, a, 0);
+            reverse_stage(0);
             adj_transpose_kernel<<<tgrd, tblk, 0, st>>>(g, G, UBn);
             if (n >= 1) seed_signal(UBn);  // the signal at t_n
             e = cudaGetLastError();
