@@ -117,6 +117,9 @@ def parse():
     ap.add_argument("--no-sub-records", action="store_true",
                     help="skip the short same-process runs of the batched, differentiated and split-box workloads "
                          "that the default line carries under sub_records")
+    ap.add_argument("--g3", type=float, default=0.0,
+                    help="cubic Horndeski coupling g3 of the bl_pair workloads (0: 4dST alone); a non-zero value "
+                         "runs the general stage instantiation with the cubic terms")
     ap.add_argument("--decoupled", action="store_true",
                     help="4dST without backreaction onto the metric (bl_pair workloads)")
     ap.add_argument("--order", type=int, default=4, choices=[4, 6],
@@ -336,7 +339,11 @@ def run_adjoint(args, rank, world, local_rank):
     RK4 step of the forward pass (grf_signal_forward, a checkpoint every 20 steps) plus its share
     of the reverse sweep (grf_adjoint_rk4: segment recomputation, stage recomputation, four
     reverse-mode stage kernels and four transposed-stencil kernels). --steps is the number of
-    RK4 steps differentiated; the gradient is with respect to (lambda, g2, A)."""
+    RK4 steps differentiated; the gradient is with respect to (lambda, g2, A). The adjoint is
+    seeded at the sphere after every step and spreads 12 points per reversed step, so the first
+    reversed steps touch little of the box (the sweep skips entries whose adjoint is zero); from
+    about 10 steps on they are dense, as in the 400-step run, so the per-step figure wants
+    --steps of 24 or more."""
     import numpy as np
     import torch
     import grf_inputs as gi
@@ -755,7 +762,7 @@ def sub_records(args, local_rank):
     recs = {}
     plan = [("batched_amr_boxes_96", run_batched, "amr_boxes_96", 5, 3),
             ("tangent_sphere_signal_96", run_tangent, "sphere_signal_96", 8, 3),
-            ("adjoint_96", run_adjoint, "adjoint_96", 4, 3),
+            ("adjoint_96", run_adjoint, "adjoint_96", 24, 3),
             ("patches_256", run_patches, "patches_256", 4, 3)]
     for name, fn, wl, steps, warmup in plan:
         a = argparse.Namespace(**vars(args))
@@ -786,6 +793,7 @@ def run_ours(args, rank, world, local_rank):
     params, dt = cfg["params"], cfg["dt"]
     if args.decoupled:
         params.decoupled = 1
+    params.g3 = args.g3
 
     # CPU oracle baseline first (rank 0, N = 1), before any CUDA work in this process
     cpu = None
@@ -881,7 +889,7 @@ def run_ours(args, rank, world, local_rank):
     launch_ms = ms / (4 * args.steps)  # the timed region is 4 stage kernels + 1 small ghost fill per step
     achieved = flop_ps * npts / (launch_ms * 1e-3) / 1e12
     scheme = {"order": box.ng * 2 - 2, "advection": "lopsided" if params.advection else "centred"}
-    default_scheme = scheme == {"order": 4, "advection": "centred"}
+    default_scheme = scheme == {"order": 4, "advection": "centred"} and params.g3 == 0.0
     roof = {"bound": "alu", "unit": "TFLOP/s",
             "kernel": "rk4_stage_kernel" if box.ng == 3 else "rk4_stage6_kernel", "achieved": achieved,
             "peak": FP64_PEAK_TFLOPS, "frac": achieved / FP64_PEAK_TFLOPS,
@@ -889,12 +897,14 @@ def run_ours(args, rank, world, local_rank):
             "peak_dfma_microbenchmark": peak, "flop_per_point_stage": flop_ps,
             "flop_convention": "FLOP_alg frozen: counted once from this formulation with an operation-counting scalar (add/sub/mul 1, fma 2, div 1)",
             "traffic": TRAFFIC_BYTES_PER_POINT_STAGE * npts if TRAFFIC_BYTES_PER_POINT_STAGE and default_scheme else None}
-    sixth_centred = scheme == {"order": 6, "advection": "centred"}
+    sixth_centred = scheme == {"order": 6, "advection": "centred"} and params.g3 == 0.0
     if sixth_centred:
         roof["traffic"] = TRAFFIC_BYTES_PER_POINT_STAGE_6 * npts
     if not default_scheme:
-        roof["note"] = ("flop_per_point_stage is the count of the 4th-order centred scheme; this scheme does more "
-                        "work per point, so achieved and frac are lower bounds")
+        roof["note"] = ("flop_per_point_stage is the count of the 4th-order centred scheme without the cubic term; "
+                        "this configuration does more work per point, so achieved and frac are lower bounds")
+    if params.g3 != 0.0 and box.ng == 3:
+        roof["kernel"] = "rk4_stage_kernel (general instantiation, cubic terms)"
     hbm_gbs, hbm_src = measured_hbm_gbs()
     roof["hbm_frac"] = BYTES_PER_POINT_UPDATE * value / (hbm_gbs * 1e9)
     roof["hbm_peak_source"] = f"{hbm_src} {hbm_gbs:.1f} GB/s"
@@ -913,7 +923,7 @@ def run_ours(args, rank, world, local_rank):
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": cfg["name"], "grid": [box.nx, box.ny, box.nz], "ghosts": box.ng, "dx": box.dx,
                       "fd_order": scheme["order"], "advection": scheme["advection"],
-                      "dt": dt, "beta": "lambda phi^2/2", "lambda": params.lam, "g2": params.g2,
+                      "dt": dt, "beta": "lambda phi^2/2", "lambda": params.lam, "g2": params.g2, "g3": params.g3,
                       "backreaction": not args.decoupled,
                       "boundary": {0: "periodic", 1: "frozen", 2: "mirror planes at the low faces, analytic high-face ghosts",
                                    3: "extrapolating", 4: "Sommerfeld",

@@ -50,9 +50,10 @@ enum : int { kLV = 0, kLD1 = 27, kLD2 = 99, kLKO = 171, kLUN = 198, kLACC = 225,
 // enforcement about 130 more; an overflow is detected and reported
 constexpr int kTapeCap = 5120;
 constexpr int kAdjThreads = 128;
-// tape columns (points per wave): 512 per SM of a GB300, so that the sweep has 16 warps per SM to
-// hide its dependent memory operations (the taping kernel, at 255 registers, holds 8)
-constexpr long long kAdjCols = 152LL * 512;
+// tape columns (points per wave): 1024 per SM of a GB300, so that the sweep (at most 64 registers)
+// has 32 warps per SM to hide its dependent memory operations; the taping kernel is held to 128
+// registers for 16 warps per SM (more spills, but it ran faster than at 255 registers with 8)
+constexpr long long kAdjCols = 152LL * 1024;
 constexpr int kSweepThreads = 256;
 // derivative and dissipation adjoints per point (slots of the G buffer): d1 72, d2 72, KO 27
 constexpr int kGD2 = 72, kGKO = 144, kGSlots = 171;
@@ -121,7 +122,7 @@ __device__ __forceinline__ void rev_sweep(int entries, long long col) {
 // STAGE (0..3) is a run-time argument: one instantiation of the large pointwise map keeps the
 // library's build time down (its four stage variants differ only in a few scalars and leaves).
 // Thread col tapes point q0 + col of the wave into tape column col.
-__global__ void __launch_bounds__(kAdjThreads) adj_tape_kernel(Geom g, Coeffs c, AdjArgs a, int STAGE, long long q0) {
+__global__ void __launch_bounds__(kAdjThreads, 4) adj_tape_kernel(Geom g, Coeffs c, AdjArgs a, int STAGE, long long q0) {
     const long long col = grf_rev::rev_col();
     const long long q = q0 + col;
     if (col >= grf_rev::c_tape.stride || q >= a.npts) return;
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_tape_kernel(Geom g, Coeffs c,
 // Sweeps tape column col (point q0 + col) and hands the leaves' adjoints to the stage's outputs:
 // the values' to vbar / unbar / abar, the derivative and KO sums' to G (with periodic images),
 // lambda's and g2's to the column's sums.
-__global__ void __launch_bounds__(kSweepThreads) adj_sweep_kernel(Geom g, AdjArgs a, int STAGE, long long q0) {
+__global__ void __launch_bounds__(kSweepThreads, 4) adj_sweep_kernel(Geom g, AdjArgs a, int STAGE, long long q0) {
     const long long col = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long q = q0 + col;
     if (col >= grf_rev::c_tape.stride || q >= a.npts) return;
