@@ -9,7 +9,8 @@ sphere-averaged scalar signal:
     than the run;
   * the gradient in (lambda, g2, A) against the GPU tangent-linear evolution (grf_tlm_rk4);
   * the 96^3 differentiation workload (dx = 0.2, periodic, R = 6) for 40 steps with a checkpoint
-    every 20: against central finite differences (h = 1e-6) to 1e-5 and against the tangents;
+    every 20, and for its stated 400 steps through the torch.autograd.Function: against central
+    finite differences (h = 1e-6) to 1e-5 and against the tangents;
   * determinism, and the torch.autograd.Function whose backward runs the sweep.
 """
 import numpy as np
@@ -161,6 +162,52 @@ def test_full_size_96_gradient_against_finite_differences_and_tangents(g, worklo
     state = g.to_device(s0, b)
     tang = g.alloc_state(b, 81)
     tang.view(3, -1)[2].copy_(g.to_device(dphi, b).reshape(-1))
+    loss = torch.zeros(4, dtype=torch.float64, device="cuda")
+    g.grf_tlm_rk4(b, p, [1.0, 0.0, 0.0, 1.0, 0.0, 0.0], state, tang, dt, n, sph, loss)
+    tlm = loss.cpu().numpy()
+    assert L == tlm[0]
+    np.testing.assert_allclose(grad, tlm[1:], rtol=1e-9)
+
+
+def test_config_96_400_steps_through_the_autograd_function(g, workload96):
+    """The differentiation workload as stated: 96^3 (dx = 0.2, periodic), 400 RK4 steps, a
+    checkpoint every 20 with recomputation, the sphere signal at r = 6. The gradient in
+    (lambda, g2, A) from SignalAdjoint's backward (the reverse sweep, 20 segments) against central
+    differences of the GPU evolution (h = 1e-6, relative 1e-5) and against the forward-mode
+    tangents of the same evolution (1e-9). About six minutes on a GB300."""
+    import torch
+    from paper_2309_06225_gb300 import diff
+    box, params, amp, dphi, dt = workload96
+    n, ce, R = 400, 20, 6.0
+    b, p = g.box_like(box), g.params_like(params)
+    s0 = g.to_device(gi.single_puncture(box, amp=amp), b)
+    dA = g.to_device(dphi, b)
+    sph = diff.sphere(R)
+    theta = torch.tensor([params.lam, params.g2, amp], dtype=torch.float64, requires_grad=True)
+    L = diff.SignalAdjoint.apply(theta, b, p, s0, dA, dt, n, sph, ce)
+    L.backward()
+    grad = theta.grad.numpy().copy()
+    L = float(L.detach())
+    ws = g.alloc_workspace(g.grf_adjoint_workspace_bytes(b, ce))
+    ck = torch.empty((g.checkpoint_count(n, ce),) + tuple(s0.shape), dtype=torch.float64, device="cuda")
+
+    def signal(lam, g2, A):
+        st = g.to_device(gi.single_puncture(box, amp=A), b)
+        loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        g.grf_signal_forward(b, g.params_like(gi.Params(lam=lam, g2=g2)), st, dt, n, sph, ce, ck, loss, ws=ws)
+        return float(loss.cpu()[0])
+
+    h = 1e-6
+    fd = np.array([(signal(params.lam + h, params.g2, amp) - signal(params.lam - h, params.g2, amp)) / (2 * h),
+                   (signal(params.lam, params.g2 + h, amp) - signal(params.lam, params.g2 - h, amp)) / (2 * h),
+                   (signal(params.lam, params.g2, amp + h) - signal(params.lam, params.g2, amp - h)) / (2 * h)])
+    floor = 20 * np.finfo(float).eps * abs(L) / h
+    for k in range(3):
+        assert abs(fd[k] - grad[k]) <= max(1e-5 * abs(grad[k]), floor), (k, fd, grad, floor)
+    del ws, ck
+    state = g.to_device(gi.single_puncture(box, amp=amp), b)
+    tang = g.alloc_state(b, 81)
+    tang.view(3, -1)[2].copy_(dA.reshape(-1))
     loss = torch.zeros(4, dtype=torch.float64, device="cuda")
     g.grf_tlm_rk4(b, p, [1.0, 0.0, 0.0, 1.0, 0.0, 0.0], state, tang, dt, n, sph, loss)
     tlm = loss.cpu().numpy()
