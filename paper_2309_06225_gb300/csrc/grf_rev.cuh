@@ -56,9 +56,11 @@ __device__ __noinline__ int rev_record(int a, double pa, int b, double pb, int c
         n = c_tape.cap - 1;
     }
     const long long off = (long long)n * c_tape.stride + rev_col();
-    c_tape.w[off] = make_double2(pa, pb);
-    c_tape.ix[off] = make_ushort4(a < 0 ? kNone : (unsigned short)a, b < 0 ? kNone : (unsigned short)b,
-                                  c < 0 ? kNone : (unsigned short)c, 0);
+    // streaming (evict-first) stores: a wave's tapes are far larger than L2 and are read back only
+    // by the sweep, so they should not push the taping kernel's own spilled registers out of L2
+    __stcs(&c_tape.w[off], make_double2(pa, pb));
+    __stcs(&c_tape.ix[off], make_ushort4(a < 0 ? kNone : (unsigned short)a, b < 0 ? kNone : (unsigned short)b,
+                                         c < 0 ? kNone : (unsigned short)c, 0));
     return c_tape.nleaf + n;
 }
 #define GRF_REV_RECORD(a, pa, b, pb, c) rev_record(a, pa, b, pb, c)
