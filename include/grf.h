@@ -418,7 +418,8 @@ int grf_tlm_rk4(const grf_box* box, const grf_params* params, const double* dpar
 
 /* Scratch bytes of grf_signal_forward and grf_adjoint_rk4 (0 for an unsupported box):
  * 9 + checkpoint_every state-sized buffers, 171 derivative-adjoint fields, and the reverse-mode
- * tapes of 38,912 threads (about 6.5 GB). */
+ * tapes of one wave of points: min(interior points, 155,648) tape columns of about 166 KB each
+ * (25.8 GB at full width; 34.1 GB in all for the 96^3 box with a checkpoint every 20 steps). */
 size_t grf_adjoint_workspace_bytes(const grf_box* box, int checkpoint_every);
 
 /* Evolves `state` (device, in place, ghosts filled first) by nsteps RK4 steps exactly as

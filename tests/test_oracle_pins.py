@@ -1030,8 +1030,8 @@ def test_solve_matrix_is_identity_at_zero_coupling(orc, conformal_generic):
     assert diag1[18] < 1e-12  # residual of the coupled equations after the solve
 
 
-@pytest.mark.parametrize("kind", [0, 1])
-def test_decoupled_metric_is_vacuum_and_blind_to_the_scalar(orc, conformal_generic, kind):
+@pytest.mark.parametrize("kind,g3", [(0, 0.0), (1, 0.0), (1, 0.6)])
+def test_decoupled_metric_is_vacuum_and_blind_to_the_scalar(orc, conformal_generic, kind, g3):
     """4dST without backreaction onto the metric ("Key features"): with decoupled = 1 the metric
     and gauge right-hand sides (fields 0..24) do not see the scalar at all. For any scalar data
     they equal the full theory's with the scalar switched off (phi = Pi = 0 with zero derivatives,
@@ -1039,10 +1039,12 @@ def test_decoupled_metric_is_vacuum_and_blind_to_the_scalar(orc, conformal_gener
     same scalar data does move the metric, and the decoupled scalar still evolves. Catches a
     stress-energy term left in a metric equation, or a mode switch that does nothing.
     The vacuum reference also switches the couplings off: with beta = lambda phi a zero scalar is
-    still sourced by L_GB (d_t Pi != 0), and its Gauss-Bonnet stress does not vanish."""
+    still sourced by L_GB (d_t Pi != 0), and its Gauss-Bonnet stress does not vanish. With the
+    cubic term (g3 != 0) its stress tensor is left out too, while the scalar equation keeps it:
+    the decoupled d_t Pi differs from the one without it."""
     v, d1, d2, ph = conformal_generic
     gauge = dict(a0=0.3, b0=0.5)
-    kw = dict(lam=0.4, g2=0.3, beta_kind=kind, **gauge)
+    kw = dict(lam=0.4, g2=0.3, beta_kind=kind, g3=g3, **gauge)
     r_dec, diag_dec, st = orc.point_rhs(P(decoupled=1, **kw), v, d1, d2)
     assert st == 0
     v0, d10, d20 = v.copy(), d1.copy(), d2.copy()
@@ -1057,6 +1059,10 @@ def test_decoupled_metric_is_vacuum_and_blind_to_the_scalar(orc, conformal_gener
     assert np.max(np.abs(r_full[:25] - r_vac[:25])) > 1e-4
     assert abs(r_dec[26]) > 1e-4 and abs(r_dec[26] - r_full[26]) > 1e-8
     assert diag_dec[18] < 1e-12                   # residual of the scalar equation after the solve
+    if g3:
+        r_nocub, _, _ = orc.point_rhs(P(decoupled=1, **dict(kw, g3=0.0)), v, d1, d2)
+        np.testing.assert_array_equal(r_dec[:25], r_nocub[:25])
+        assert abs(r_dec[26] - r_nocub[26]) > 1e-4
 
 
 def test_decoupled_scalar_at_zero_coupling_is_klein_gordon(orc, conformal_generic):
