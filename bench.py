@@ -44,9 +44,12 @@ TRAFFIC_BYTES_PER_POINT_STAGE = 12773
 FP64_INSTR_PER_POINT_STAGE = 4196
 # the tangent-linear (dual-number) stage kernel's FP64 instructions per point-stage (same kind of capture)
 TLM_FP64_INSTR_PER_POINT_STAGE = 28826
-# the 6th-order stage kernel with centred advection (same kind of capture)
+# the 6th-order stage kernel with centred advection, and the general 4th-order instantiation with
+# the cubic term (g3 = 0.1), from the same kind of capture
 FP64_INSTR_PER_POINT_STAGE_6 = None
 TRAFFIC_BYTES_PER_POINT_STAGE_6 = None
+FP64_INSTR_PER_POINT_STAGE_G3 = None
+TRAFFIC_BYTES_PER_POINT_STAGE_G3 = None
 # nominal FP64 (non-tensor) peak of GB300: 152 SMs x 2 FP64 FMA lanes/clk x 2 flop x ~2.06 GHz;
 # used only when no measured figure is stored
 FP64_NOMINAL_TFLOPS = 1.25
@@ -896,10 +899,19 @@ def run_ours(args, rank, world, local_rank):
             "peak_source": FP64_PEAK_SOURCE,
             "peak_dfma_microbenchmark": peak, "flop_per_point_stage": flop_ps,
             "flop_convention": "FLOP_alg frozen: counted once from this formulation with an operation-counting scalar (add/sub/mul 1, fma 2, div 1)",
-            "traffic": TRAFFIC_BYTES_PER_POINT_STAGE * npts if TRAFFIC_BYTES_PER_POINT_STAGE and default_scheme else None}
+            "traffic": None}
+    # per-point FP64 instructions and DRAM bytes of the stage kernel that runs, where captured
     sixth_centred = scheme == {"order": 6, "advection": "centred"} and params.g3 == 0.0
-    if sixth_centred:
-        roof["traffic"] = TRAFFIC_BYTES_PER_POINT_STAGE_6 * npts
+    cubic_centred = scheme == {"order": 4, "advection": "centred"} and params.g3 != 0.0
+    instr, traffic = None, None
+    if default_scheme:
+        instr, traffic = FP64_INSTR_PER_POINT_STAGE, TRAFFIC_BYTES_PER_POINT_STAGE
+    elif sixth_centred:
+        instr, traffic = FP64_INSTR_PER_POINT_STAGE_6, TRAFFIC_BYTES_PER_POINT_STAGE_6
+    elif cubic_centred:
+        instr, traffic = FP64_INSTR_PER_POINT_STAGE_G3, TRAFFIC_BYTES_PER_POINT_STAGE_G3
+    if traffic:
+        roof["traffic"] = traffic * npts
     if not default_scheme:
         roof["note"] = ("flop_per_point_stage is the count of the 4th-order centred scheme without the cubic term; "
                         "this configuration does more work per point, so achieved and frac are lower bounds")
@@ -908,9 +920,8 @@ def run_ours(args, rank, world, local_rank):
     hbm_gbs, hbm_src = measured_hbm_gbs()
     roof["hbm_frac"] = BYTES_PER_POINT_UPDATE * value / (hbm_gbs * 1e9)
     roof["hbm_peak_source"] = f"{hbm_src} {hbm_gbs:.1f} GB/s"
-    if FP64_INSTR_PER_POINT_STAGE and (default_scheme or sixth_centred):
+    if instr:
         # how full the FP64 pipe is: adds and multiplies take an issue slot but count one flop
-        instr = FP64_INSTR_PER_POINT_STAGE if default_scheme else FP64_INSTR_PER_POINT_STAGE_6
         rate = instr * npts / (launch_ms * 1e-3)
         sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
         roof["fp64_issue_frac"] = rate / fp64_issue_ceiling(sm_mhz)
