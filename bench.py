@@ -751,6 +751,53 @@ def run_reference(args, rank):
 
 
 # ------------------------------------------------------------------------------ GPU arm
+def roofline_record(ng, params, npts, launch_ms, value, clk, peak):
+    """The roofline object of a bl_pair line: the stage kernel's achieved FLOP_alg rate against the
+    measured FP64 peak, its DRAM bytes and FP64 issue fraction where a capture of that kernel is
+    stored, and the HBM fraction of the algorithmic bytes. Returns (roofline, scheme, default)."""
+    flop_ps = FLOP_ALG_PER_POINT_STAGE
+    achieved = flop_ps * npts / (launch_ms * 1e-3) / 1e12
+    scheme = {"order": ng * 2 - 2, "advection": "lopsided" if params.advection else "centred"}
+    default_scheme = scheme == {"order": 4, "advection": "centred"} and params.g3 == 0.0
+    roof = {"bound": "alu", "unit": "TFLOP/s",
+            "kernel": "rk4_stage_kernel" if ng == 3 else "rk4_stage6_kernel", "achieved": achieved,
+            "peak": FP64_PEAK_TFLOPS, "frac": achieved / FP64_PEAK_TFLOPS,
+            "peak_source": FP64_PEAK_SOURCE,
+            "peak_dfma_microbenchmark": peak, "flop_per_point_stage": flop_ps,
+            "flop_convention": "FLOP_alg frozen: counted once from this formulation with an operation-counting scalar (add/sub/mul 1, fma 2, div 1)",
+            "traffic": None}
+    # per-point FP64 instructions and DRAM bytes of the stage kernel that runs, where captured
+    sixth_centred = scheme == {"order": 6, "advection": "centred"} and params.g3 == 0.0
+    cubic_centred = scheme == {"order": 4, "advection": "centred"} and params.g3 != 0.0
+    instr, traffic = None, None
+    if default_scheme:
+        instr, traffic = FP64_INSTR_PER_POINT_STAGE, TRAFFIC_BYTES_PER_POINT_STAGE
+    elif sixth_centred:
+        instr, traffic = FP64_INSTR_PER_POINT_STAGE_6, TRAFFIC_BYTES_PER_POINT_STAGE_6
+    elif cubic_centred:
+        instr, traffic = FP64_INSTR_PER_POINT_STAGE_G3, TRAFFIC_BYTES_PER_POINT_STAGE_G3
+    if traffic:
+        roof["traffic"] = traffic * npts
+    if not default_scheme:
+        roof["note"] = ("flop_per_point_stage is the count of the 4th-order centred scheme without the cubic term; "
+                        "this configuration does more work per point, so achieved and frac are lower bounds")
+    if params.g3 != 0.0 and ng == 3:
+        roof["kernel"] = "rk4_stage_kernel (general instantiation, cubic terms)"
+    hbm_gbs, hbm_src = measured_hbm_gbs()
+    roof["hbm_frac"] = BYTES_PER_POINT_UPDATE * value / (hbm_gbs * 1e9)
+    roof["hbm_peak_source"] = f"{hbm_src} {hbm_gbs:.1f} GB/s"
+    if instr:
+        # how full the FP64 pipe is: adds and multiplies take an issue slot but count one flop
+        rate = instr * npts / (launch_ms * 1e-3)
+        sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
+        roof["fp64_issue_frac"] = rate / fp64_issue_ceiling(sm_mhz)
+        roof["fp64_issue"] = {"instr_per_point_stage": instr, "instr_per_s": rate,
+                              "ceiling": fp64_issue_ceiling(sm_mhz),
+                              "ceiling_source": f"2 per SM per clock x 152 SMs x {sm_mhz:.0f} MHz (sampled)",
+                              "vs_measured_chains": rate / FP64_PEAK_INSTR}
+    return roof, scheme, default_scheme
+
+
 SUB_RECORD_DROP = ("n_gpus", "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "cpu_baseline")
 
 
@@ -888,47 +935,8 @@ def run_ours(args, rank, world, local_rank):
         if dist is not None:
             dist.destroy_process_group()
         return
-    flop_ps = FLOP_ALG_PER_POINT_STAGE
     launch_ms = ms / (4 * args.steps)  # the timed region is 4 stage kernels + 1 small ghost fill per step
-    achieved = flop_ps * npts / (launch_ms * 1e-3) / 1e12
-    scheme = {"order": box.ng * 2 - 2, "advection": "lopsided" if params.advection else "centred"}
-    default_scheme = scheme == {"order": 4, "advection": "centred"} and params.g3 == 0.0
-    roof = {"bound": "alu", "unit": "TFLOP/s",
-            "kernel": "rk4_stage_kernel" if box.ng == 3 else "rk4_stage6_kernel", "achieved": achieved,
-            "peak": FP64_PEAK_TFLOPS, "frac": achieved / FP64_PEAK_TFLOPS,
-            "peak_source": FP64_PEAK_SOURCE,
-            "peak_dfma_microbenchmark": peak, "flop_per_point_stage": flop_ps,
-            "flop_convention": "FLOP_alg frozen: counted once from this formulation with an operation-counting scalar (add/sub/mul 1, fma 2, div 1)",
-            "traffic": None}
-    # per-point FP64 instructions and DRAM bytes of the stage kernel that runs, where captured
-    sixth_centred = scheme == {"order": 6, "advection": "centred"} and params.g3 == 0.0
-    cubic_centred = scheme == {"order": 4, "advection": "centred"} and params.g3 != 0.0
-    instr, traffic = None, None
-    if default_scheme:
-        instr, traffic = FP64_INSTR_PER_POINT_STAGE, TRAFFIC_BYTES_PER_POINT_STAGE
-    elif sixth_centred:
-        instr, traffic = FP64_INSTR_PER_POINT_STAGE_6, TRAFFIC_BYTES_PER_POINT_STAGE_6
-    elif cubic_centred:
-        instr, traffic = FP64_INSTR_PER_POINT_STAGE_G3, TRAFFIC_BYTES_PER_POINT_STAGE_G3
-    if traffic:
-        roof["traffic"] = traffic * npts
-    if not default_scheme:
-        roof["note"] = ("flop_per_point_stage is the count of the 4th-order centred scheme without the cubic term; "
-                        "this configuration does more work per point, so achieved and frac are lower bounds")
-    if params.g3 != 0.0 and box.ng == 3:
-        roof["kernel"] = "rk4_stage_kernel (general instantiation, cubic terms)"
-    hbm_gbs, hbm_src = measured_hbm_gbs()
-    roof["hbm_frac"] = BYTES_PER_POINT_UPDATE * value / (hbm_gbs * 1e9)
-    roof["hbm_peak_source"] = f"{hbm_src} {hbm_gbs:.1f} GB/s"
-    if instr:
-        # how full the FP64 pipe is: adds and multiplies take an issue slot but count one flop
-        rate = instr * npts / (launch_ms * 1e-3)
-        sm_mhz = (clk or {}).get("sm_mhz") or 2070.0
-        roof["fp64_issue_frac"] = rate / fp64_issue_ceiling(sm_mhz)
-        roof["fp64_issue"] = {"instr_per_point_stage": instr, "instr_per_s": rate,
-                              "ceiling": fp64_issue_ceiling(sm_mhz),
-                              "ceiling_source": f"2 per SM per clock x 152 SMs x {sm_mhz:.0f} MHz (sampled)",
-                              "vs_measured_chains": rate / FP64_PEAK_INSTR}
+    roof, scheme, default_scheme = roofline_record(box.ng, params, npts, launch_ms, value, clk, peak)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
