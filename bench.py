@@ -46,10 +46,10 @@ FP64_INSTR_PER_POINT_STAGE = 4196
 TLM_FP64_INSTR_PER_POINT_STAGE = 28826
 # the 6th-order stage kernel with centred advection, and the general 4th-order instantiation with
 # the cubic term (g3 = 0.1), from the same kind of capture
-FP64_INSTR_PER_POINT_STAGE_6 = None
-TRAFFIC_BYTES_PER_POINT_STAGE_6 = None
-FP64_INSTR_PER_POINT_STAGE_G3 = None
-TRAFFIC_BYTES_PER_POINT_STAGE_G3 = None
+FP64_INSTR_PER_POINT_STAGE_6 = 4846.5
+TRAFFIC_BYTES_PER_POINT_STAGE_6 = 11629
+FP64_INSTR_PER_POINT_STAGE_G3 = 4464
+TRAFFIC_BYTES_PER_POINT_STAGE_G3 = 13769
 # nominal FP64 (non-tensor) peak of GB300: 152 SMs x 2 FP64 FMA lanes/clk x 2 flop x ~2.06 GHz;
 # used only when no measured figure is stored
 FP64_NOMINAL_TFLOPS = 1.25
