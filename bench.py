@@ -37,19 +37,20 @@ FLOP_ALG_PER_POINT_STAGE = 6615.25
 # stage 1: read u_n, write u_1 and acc (3 x 216 B); stages 2-3: read u_s, u_n, acc, write u_s, acc
 # (5 x 216 B each); stage 4: read u_3, u_n, acc, write u_n (4 x 216 B)
 BYTES_PER_POINT_UPDATE = 216 * (3 + 5 + 5 + 4)
-# Per interior point and stage launch, from an ncu capture of the stage kernel on the 96^3 box
-# (mean of stages 0 and 1): dram__bytes_read.sum + dram__bytes_write.sum, and the FP64 thread
-# instructions (dadd + dmul + dfma). None when the kernel changed since the capture.
-TRAFFIC_BYTES_PER_POINT_STAGE = 12773
-FP64_INSTR_PER_POINT_STAGE = 4196
+# Per interior point and stage launch, from an ncu capture of each stage kernel on the 96^3 box
+# (mean of stages 0 and 1): the FP64 thread instructions (dadd + dmul + dfma) and
+# dram__bytes_read.sum + dram__bytes_write.sum. Keyed by (order, advection, cubic term); a scheme
+# absent here (or whose kernel changed since its capture) reports neither.
+STAGE_CAPTURES = {
+    (4, "centred", False): (4196, 12773),     # the default kernel, no cubic code
+    (4, "centred", True): (4464, 13769),      # general instantiation, g3 = 0.1
+    (4, "lopsided", False): (4523, 13515),
+    (6, "centred", False): (4846.5, 11629),
+    (6, "lopsided", False): (5381.5, 11256),
+}
+FP64_INSTR_PER_POINT_STAGE, TRAFFIC_BYTES_PER_POINT_STAGE = STAGE_CAPTURES[(4, "centred", False)]
 # the tangent-linear (dual-number) stage kernel's FP64 instructions per point-stage (same kind of capture)
 TLM_FP64_INSTR_PER_POINT_STAGE = 28826
-# the 6th-order stage kernel with centred advection, and the general 4th-order instantiation with
-# the cubic term (g3 = 0.1), from the same kind of capture
-FP64_INSTR_PER_POINT_STAGE_6 = 4846.5
-TRAFFIC_BYTES_PER_POINT_STAGE_6 = 11629
-FP64_INSTR_PER_POINT_STAGE_G3 = 4464
-TRAFFIC_BYTES_PER_POINT_STAGE_G3 = 13769
 # nominal FP64 (non-tensor) peak of GB300: 152 SMs x 2 FP64 FMA lanes/clk x 2 flop x ~2.06 GHz;
 # used only when no measured figure is stored
 FP64_NOMINAL_TFLOPS = 1.25
@@ -767,15 +768,7 @@ def roofline_record(ng, params, npts, launch_ms, value, clk, peak):
             "flop_convention": "FLOP_alg frozen: counted once from this formulation with an operation-counting scalar (add/sub/mul 1, fma 2, div 1)",
             "traffic": None}
     # per-point FP64 instructions and DRAM bytes of the stage kernel that runs, where captured
-    sixth_centred = scheme == {"order": 6, "advection": "centred"} and params.g3 == 0.0
-    cubic_centred = scheme == {"order": 4, "advection": "centred"} and params.g3 != 0.0
-    instr, traffic = None, None
-    if default_scheme:
-        instr, traffic = FP64_INSTR_PER_POINT_STAGE, TRAFFIC_BYTES_PER_POINT_STAGE
-    elif sixth_centred:
-        instr, traffic = FP64_INSTR_PER_POINT_STAGE_6, TRAFFIC_BYTES_PER_POINT_STAGE_6
-    elif cubic_centred:
-        instr, traffic = FP64_INSTR_PER_POINT_STAGE_G3, TRAFFIC_BYTES_PER_POINT_STAGE_G3
+    instr, traffic = STAGE_CAPTURES.get((scheme["order"], scheme["advection"], params.g3 != 0.0), (None, None))
     if traffic:
         roof["traffic"] = traffic * npts
     if not default_scheme:

@@ -37,15 +37,10 @@ def test_roofline_record_builds_for_every_scheme(bench, ng, advection, g3):
     if not default:
         assert "lower bounds" in roof["note"]
     # capture constants only for the kernel they were taken from
-    if default:
-        want = bench.TRAFFIC_BYTES_PER_POINT_STAGE
-    elif ng == 4 and advection == 0 and g3 == 0.0:
-        want = bench.TRAFFIC_BYTES_PER_POINT_STAGE_6
-    elif ng == 3 and advection == 0:
-        want = bench.TRAFFIC_BYTES_PER_POINT_STAGE_G3
-    else:
-        want = None
+    key = (2 * ng - 2, "lopsided" if advection else "centred", g3 != 0.0)
+    instr, want = bench.STAGE_CAPTURES.get(key, (None, None))
     assert roof["traffic"] == (want * npts if want else None)
+    assert (roof.get("fp64_issue") or {}).get("instr_per_point_stage") == instr
     if "fp64_issue" in roof:
         f = roof["fp64_issue"]
         assert roof["fp64_issue_frac"] == pytest.approx(f["instr_per_s"] / f["ceiling"])
