@@ -39,8 +39,9 @@ FLOP_ALG_PER_POINT_STAGE = 6615.25
 BYTES_PER_POINT_UPDATE = 216 * (3 + 5 + 5 + 4)
 # Per interior point and stage launch, from an ncu capture of each stage kernel on the 96^3 box
 # (mean of stages 0 and 1): the FP64 thread instructions (dadd + dmul + dfma) and
-# dram__bytes_read.sum + dram__bytes_write.sum. Keyed by (order, advection, cubic term); a scheme
-# absent here (or whose kernel changed since its capture) reports neither.
+# dram__bytes_read.sum + dram__bytes_write.sum. Keyed by (order, advection, cubic term), with
+# backreaction; a scheme absent here (the decoupled kernels, or one whose kernel changed since its
+# capture) reports neither.
 STAGE_CAPTURES = {
     (4, "centred", False): (4196, 12773),     # the default kernel, no cubic code
     (4, "centred", True): (4464, 13769),      # general instantiation, g3 = 0.1
@@ -759,7 +760,7 @@ def roofline_record(ng, params, npts, launch_ms, value, clk, peak):
     flop_ps = FLOP_ALG_PER_POINT_STAGE
     achieved = flop_ps * npts / (launch_ms * 1e-3) / 1e12
     scheme = {"order": ng * 2 - 2, "advection": "lopsided" if params.advection else "centred"}
-    default_scheme = scheme == {"order": 4, "advection": "centred"} and params.g3 == 0.0
+    default_scheme = scheme == {"order": 4, "advection": "centred"} and params.g3 == 0.0 and not params.decoupled
     roof = {"bound": "alu", "unit": "TFLOP/s",
             "kernel": "rk4_stage_kernel" if ng == 3 else "rk4_stage6_kernel", "achieved": achieved,
             "peak": FP64_PEAK_TFLOPS, "frac": achieved / FP64_PEAK_TFLOPS,
@@ -768,10 +769,14 @@ def roofline_record(ng, params, npts, launch_ms, value, clk, peak):
             "flop_convention": "FLOP_alg frozen: counted once from this formulation with an operation-counting scalar (add/sub/mul 1, fma 2, div 1)",
             "traffic": None}
     # per-point FP64 instructions and DRAM bytes of the stage kernel that runs, where captured
-    instr, traffic = STAGE_CAPTURES.get((scheme["order"], scheme["advection"], params.g3 != 0.0), (None, None))
+    instr, traffic = (None, None) if params.decoupled else \
+        STAGE_CAPTURES.get((scheme["order"], scheme["advection"], params.g3 != 0.0), (None, None))
     if traffic:
         roof["traffic"] = traffic * npts
-    if not default_scheme:
+    if params.decoupled:
+        roof["note"] = ("flop_per_point_stage is the count of the coupled 4th-order scheme; without backreaction the "
+                        "solve and the stress terms are compiled away, so achieved and frac overstate this kernel's work")
+    elif not default_scheme:
         roof["note"] = ("flop_per_point_stage is the count of the 4th-order centred scheme without the cubic term; "
                         "this configuration does more work per point, so achieved and frac are lower bounds")
     if params.g3 != 0.0 and ng == 3:
