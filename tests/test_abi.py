@@ -175,3 +175,27 @@ def test_adjoint_validation_without_gpu(grf):
                                 None) == grf.GRF_EINVAL
     assert L.grf_adjoint_rk4(C.byref(b), C.byref(ok), fake, 0.1, 4, C.byref(sph), 2, 1.0, fake, fake, None, 0,
                              None) == grf.GRF_EWORKSPACE
+
+
+def test_empty_and_degenerate_calls_without_gpu(grf):
+    """Empty boxes and negative step counts are rejected, and zero steps is a successful no-op, all
+    before any CUDA call (so these run without a GPU). A 1 x 1 x 1 frozen box is a valid box."""
+    L = grf.lib()
+    p = grf.grf_params()
+    fake_state = C.c_void_p(0x1000)
+    fake_ws = C.c_void_p(0x10000)  # 256-byte aligned, never touched
+    for n in ((0, 8, 8), (8, 0, 8), (8, 8, 0)):
+        b = grf.make_box(*n, 0.25)
+        assert grf.grf_workspace_bytes(b, grf.GRF_OP_RK4) == 0
+        assert L.grf_rk4_step(C.byref(b), C.byref(p), fake_state, 0.1, 1, fake_ws, 1 << 40, None) == grf.GRF_EINVAL
+        assert L.grf_rhs(C.byref(b), C.byref(p), fake_state, fake_state, None, 0, None) == grf.GRF_EINVAL
+    b = grf.make_box(8, 8, 8, 0.25)
+    nbytes = grf.grf_workspace_bytes(b, grf.GRF_OP_RK4)
+    assert L.grf_rk4_step(C.byref(b), C.byref(p), fake_state, 0.1, -1, fake_ws, nbytes, None) == grf.GRF_EINVAL
+    assert L.grf_rk4_step(C.byref(b), C.byref(p), fake_state, 0.1, 0, fake_ws, nbytes, None) == grf.GRF_OK
+    one = grf.make_box(1, 1, 1, 0.25, bc=grf.GRF_BC_FROZEN)
+    assert grf.grf_workspace_bytes(one, grf.GRF_OP_RK4) > 0
+    assert L.grf_rk4_step(C.byref(one), C.byref(p), fake_state, 0.1, 0, fake_ws, 1 << 40, None) == grf.GRF_OK
+    # a periodic box needs at least the ghost width of points per axis
+    two = grf.make_box(2, 8, 8, 0.25)
+    assert grf.grf_workspace_bytes(two, grf.GRF_OP_RK4) == 0
