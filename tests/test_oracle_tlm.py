@@ -15,10 +15,13 @@ import grf_inputs as gi
 EPS = np.finfo(np.float64).eps
 
 
-@pytest.fixture(scope="module")
-def setup():
+@pytest.fixture(scope="module", params=["quadratic", "linear_cubic"])
+def setup(request):
     box = gi.cube_box(12, -3.0, 3.0)   # dx 0.5, periodic
-    P = gi.Params(lam=0.05, g2=0.02, beta_kind=gi.BETA_QUADRATIC)
+    if request.param == "quadratic":
+        P = gi.Params(lam=0.05, g2=0.02, beta_kind=gi.BETA_QUADRATIC)
+    else:  # the cubic Horndeski term in the differentiated evolution (its coupling g3 held fixed)
+        P = gi.Params(lam=0.05, g2=0.02, beta_kind=gi.BETA_LINEAR, g3=0.4)
     s0 = gi.random_perturbed_state(box, 3, base=gi.single_puncture(box, amp=0.05), eps=1e-2)
     rng = np.random.default_rng(1)
     ds0 = rng.normal(size=s0.shape) * 1e-2
@@ -69,7 +72,7 @@ def test_tlm_matches_richardson_differences_of_the_plain_oracle(orc, setup, dp, 
     def sig(e):
         s = s0 + e * scale_ds * ds0
         orc.fill_ghosts(box, s)
-        p = gi.Params(lam=P.lam + e * dp[0], g2=P.g2 + e * dp[1], beta_kind=P.beta_kind)
+        p = gi.Params(lam=P.lam + e * dp[0], g2=P.g2 + e * dp[1], beta_kind=P.beta_kind, g3=P.g3)
         return orc.rk4_signal(box, p, s, dt, n, sphere)[1]
 
     h = 1e-3
