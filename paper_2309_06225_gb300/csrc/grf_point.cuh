@@ -950,8 +950,8 @@ GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS]
             if (!dec) {
                 // 8 pi S3_ij without its d_t Pi part, and that part's coefficient in the metric rows:
                 // S3_ij = S3_0 + g3 w / (2 alpha) (Pi^2 gamma_ij - d_i phi d_j phi)
-                const T pcoef = 0.5 * (trH3 - Hnn0);  // coefficients of d_i phi d_j phi and of gamma_ij
-                const T gcoef = fma(0.5 * Hnn0, Pi2, fma(0.5, Hdd3, -Pi * Hnd3));
+                const T pcoef = 0.5 * (trH3 - Hnn0);                               // of d_i phi d_j phi
+                const T gcoef = fma(0.5 * Hnn0, Pi2, fma(0.5, Hdd3, -Pi * Hnd3));  // of gamma_ij
 #pragma unroll
                 for (int i = 0; i < 3; ++i)
 #pragma unroll
