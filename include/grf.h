@@ -393,7 +393,8 @@ size_t grf_tlm_workspace_bytes(const grf_box* box);
 /* state: device, advanced in place (as grf_rk4_step). tangents: device, 3 consecutive states in
  * the same layout holding d state / d theta_k (the caller seeds them, e.g. d(initial state)/d
  * amplitude), advanced in place. dparams: host, 6 doubles {d lambda/d theta_k, d g2/d theta_k}
- * for k = 0, 1, 2. loss: device, 4 doubles {L, dL/dtheta_0..2}, ACCUMULATED (zero it first).
+ * for k = 0, 1, 2 (g3, when non-zero, is held fixed). loss: device, 4 doubles {L, dL/dtheta_0..2},
+ * ACCUMULATED (zero it first).
  * Synchronises `stream`; GRF_EINVAL if the sphere leaves the interior, GRF_ESINGULAR if a
  * coupled system was singular. */
 int grf_tlm_rk4(const grf_box* box, const grf_params* params, const double* dparams, double* state, double* tangents,
@@ -412,7 +413,8 @@ int grf_tlm_rk4(const grf_box* box, const grf_params* params, const double* dpar
  *     J = loss_bar * L + <state_bar_in, state_N>   (interior points, all 27 fields)
  * with respect to the initial state's interior values and to (lambda, g2).
  * Accepted boxes: 3 ghost layers, periodic or frozen ghosts; params: centred advection, any
- * coupling kind, with or without backreaction. Calls on one device must not overlap in time:
+ * coupling kind, with or without backreaction, with or without the cubic term (g3 is held fixed:
+ * no derivative is taken with respect to it). Calls on one device must not overlap in time:
  * the tape's device pointers are held in one constant of the library, set by each call.
  * ------------------------------------------------------------------------------------- */
 
