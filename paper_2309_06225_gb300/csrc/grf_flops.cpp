@@ -83,6 +83,34 @@ inline void opaque(double&) {}
 #include "grf_point.cuh"
 #include "grf.h"
 
+namespace {
+
+// The launch coefficients of grf_params as the library builds them, for the centred-advection
+// instance (the counts and the host checks use that one).
+grf::Coeffs host_coeffs(const grf_params* p) {
+    grf::Coeffs c;
+    c.kappa1 = p->kappa1; c.kappa2 = p->kappa2; c.kappa3 = p->kappa3; c.shift_F = p->shift_F; c.eta = p->eta;
+    c.lam = p->lambda; c.g2 = p->g2; c.g3 = p->g3;
+    c.inv_1pa = 1.0 / (1.0 + p->a0); c.a_1pa = p->a0 / (1.0 + p->a0);
+    c.bK = 3.0 * p->b0 / (4.0 * (1.0 + p->b0)); c.bTh = 1.0 / (2.0 * (1.0 + p->b0));
+    c.beta_kind = p->beta_kind; c.beta_kappa = p->beta_kappa; c.decoupled = p->decoupled;
+    c.advection = 0;
+    return c;
+}
+
+// Point data in the kernel's slot order (v: 27 values, d1: 24 x 3, d2: 12 x 6).
+grf::PointInT<double> host_point(const double* v, const double* d1, const double* d2) {
+    grf::PointInT<double> in;
+    for (int f = 0; f < grf::NFIELDS; ++f) in.v[f] = v[f];
+    for (int a = 0; a < 24; ++a)
+        for (int d = 0; d < 3; ++d) in.d1[a][d] = d1[a * 3 + d];
+    for (int b = 0; b < 12; ++b)
+        for (int m = 0; m < 6; ++m) in.d2[b][m] = d2[b * 6 + m];
+    return in;
+}
+
+}  // namespace
+
 extern "C" {
 
 // Counts the FP64 operations of one pointwise RHS evaluation on the given point data
@@ -98,12 +126,7 @@ int grf_count_point_ops(const grf_params* p, const double* v, const double* d1, 
         for (int d = 0; d < 3; ++d) in.d1[a][d] = CD::var(d1[a * 3 + d]);
     for (int b = 0; b < 12; ++b)
         for (int m = 0; m < 6; ++m) in.d2[b][m] = CD::var(d2[b * 6 + m]);
-    grf::Coeffs c;
-    c.kappa1 = p->kappa1; c.kappa2 = p->kappa2; c.kappa3 = p->kappa3; c.shift_F = p->shift_F; c.eta = p->eta;
-    c.lam = p->lambda; c.g2 = p->g2; c.g3 = p->g3; c.inv_1pa = 1.0 / (1.0 + p->a0); c.a_1pa = p->a0 / (1.0 + p->a0);
-    c.bK = 3.0 * p->b0 / (4.0 * (1.0 + p->b0)); c.bTh = 1.0 / (2.0 * (1.0 + p->b0)); c.beta_kind = p->beta_kind; c.decoupled = p->decoupled;
-    c.beta_kappa = p->beta_kappa;
-    c.advection = 0;  // operation counts of the centred-advection instance
+    const grf::Coeffs c = host_coeffs(p);
     CD rhs[grf::NFIELDS];
     grf::PointExtraT<CD> ex;
     bool ok = true;
@@ -120,18 +143,8 @@ int grf_count_point_ops(const grf_params* p, const double* v, const double* d1, 
 // the kernel formulas against the oracle). Slots as above; extra (may be NULL): H, M_1..3.
 int grf_host_point_rhs(const grf_params* p, const double* v, const double* d1, const double* d2, double* rhs,
                        double* extra) {
-    grf::PointInT<double> in;
-    for (int f = 0; f < grf::NFIELDS; ++f) in.v[f] = v[f];
-    for (int a = 0; a < 24; ++a)
-        for (int d = 0; d < 3; ++d) in.d1[a][d] = d1[a * 3 + d];
-    for (int b = 0; b < 12; ++b)
-        for (int m = 0; m < 6; ++m) in.d2[b][m] = d2[b * 6 + m];
-    grf::Coeffs c;
-    c.kappa1 = p->kappa1; c.kappa2 = p->kappa2; c.kappa3 = p->kappa3; c.shift_F = p->shift_F; c.eta = p->eta;
-    c.lam = p->lambda; c.g2 = p->g2; c.g3 = p->g3; c.inv_1pa = 1.0 / (1.0 + p->a0); c.a_1pa = p->a0 / (1.0 + p->a0);
-    c.bK = 3.0 * p->b0 / (4.0 * (1.0 + p->b0)); c.bTh = 1.0 / (2.0 * (1.0 + p->b0)); c.beta_kind = p->beta_kind; c.decoupled = p->decoupled;
-    c.beta_kappa = p->beta_kappa;
-    c.advection = 0;  // operation counts of the centred-advection instance
+    const grf::PointInT<double> in = host_point(v, d1, d2);
+    const grf::Coeffs c = host_coeffs(p);
     grf::PointExtraT<double> ex;
     bool ok = true;
     grf::point_rhs(c, in, rhs, &ex, ok);
@@ -146,19 +159,8 @@ int grf_host_point_rhs(const grf_params* p, const double* v, const double* d1, c
 // coordinates relative to the triad's origin; out2 = (re, im).
 int grf_host_point_psi4(const grf_params* p, const double* v, const double* d1, const double* d2, const double* xyz,
                         double* out2) {
-    grf::PointInT<double> in;
-    for (int f = 0; f < grf::NFIELDS; ++f) in.v[f] = v[f];
-    for (int a = 0; a < 24; ++a)
-        for (int d = 0; d < 3; ++d) in.d1[a][d] = d1[a * 3 + d];
-    for (int b = 0; b < 12; ++b)
-        for (int m = 0; m < 6; ++m) in.d2[b][m] = d2[b * 6 + m];
-    grf::Coeffs c;
-    c.kappa1 = p->kappa1; c.kappa2 = p->kappa2; c.kappa3 = p->kappa3; c.shift_F = p->shift_F; c.eta = p->eta;
-    c.lam = p->lambda; c.g2 = p->g2; c.g3 = p->g3; c.inv_1pa = 1.0 / (1.0 + p->a0); c.a_1pa = p->a0 / (1.0 + p->a0);
-    c.bK = 3.0 * p->b0 / (4.0 * (1.0 + p->b0)); c.bTh = 1.0 / (2.0 * (1.0 + p->b0)); c.beta_kind = p->beta_kind;
-    c.decoupled = p->decoupled;
-    c.beta_kappa = p->beta_kappa;
-    c.advection = 0;
+    const grf::PointInT<double> in = host_point(v, d1, d2);
+    const grf::Coeffs c = host_coeffs(p);
     grf::PointExtraT<double> ex;
     ex.want_psi4 = 1;
     for (int d = 0; d < 3; ++d) ex.xyz[d] = xyz[d];
@@ -173,19 +175,8 @@ int grf_host_point_psi4(const grf_params* p, const double* v, const double* d1, 
 // The kernel's hyperbolicity diagnostics (det M, det g_eff / det g, -g_eff^nn) of the same host
 // instance; out3 receives the three.
 int grf_host_point_hyp(const grf_params* p, const double* v, const double* d1, const double* d2, double* out3) {
-    grf::PointInT<double> in;
-    for (int f = 0; f < grf::NFIELDS; ++f) in.v[f] = v[f];
-    for (int a = 0; a < 24; ++a)
-        for (int d = 0; d < 3; ++d) in.d1[a][d] = d1[a * 3 + d];
-    for (int b = 0; b < 12; ++b)
-        for (int m = 0; m < 6; ++m) in.d2[b][m] = d2[b * 6 + m];
-    grf::Coeffs c;
-    c.kappa1 = p->kappa1; c.kappa2 = p->kappa2; c.kappa3 = p->kappa3; c.shift_F = p->shift_F; c.eta = p->eta;
-    c.lam = p->lambda; c.g2 = p->g2; c.g3 = p->g3; c.inv_1pa = 1.0 / (1.0 + p->a0); c.a_1pa = p->a0 / (1.0 + p->a0);
-    c.bK = 3.0 * p->b0 / (4.0 * (1.0 + p->b0)); c.bTh = 1.0 / (2.0 * (1.0 + p->b0)); c.beta_kind = p->beta_kind;
-    c.decoupled = p->decoupled;
-    c.beta_kappa = p->beta_kappa;
-    c.advection = 0;
+    const grf::PointInT<double> in = host_point(v, d1, d2);
+    const grf::Coeffs c = host_coeffs(p);
     grf::PointExtraT<double> ex;
     ex.want_hyp = 1;
     double rhs[grf::NFIELDS];
