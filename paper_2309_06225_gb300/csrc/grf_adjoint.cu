@@ -396,17 +396,8 @@ Geom adj_geom(const grf_box* b) {
 }
 
 Coeffs adj_coeffs(const grf_params* p) {
-    Coeffs c;
-    c.kappa1 = p->kappa1; c.kappa2 = p->kappa2; c.kappa3 = p->kappa3;
-    c.shift_F = p->shift_F; c.eta = p->eta; c.lam = p->lambda; c.g2 = p->g2; c.g3 = p->g3;
-    c.inv_1pa = 1.0 / (1.0 + p->a0);
-    c.a_1pa = p->a0 / (1.0 + p->a0);
-    c.bK = 3.0 * p->b0 / (4.0 * (1.0 + p->b0));
-    c.bTh = 1.0 / (2.0 * (1.0 + p->b0));
-    c.beta_kind = p->beta_kind;
-    c.beta_kappa = p->beta_kappa;
-    c.decoupled = p->decoupled;
-    c.advection = 0;
+    Coeffs c = make_coeffs(p);
+    c.advection = 0;  // centred advection only (checked by adj_params_ok)
     return c;
 }
 

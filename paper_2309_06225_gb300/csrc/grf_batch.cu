@@ -75,14 +75,7 @@ void batch_box_desc(BoxDesc& d, const grf_box* b, const grf_params* p, double dt
     g.dx = b->dx;
     g.periodic = (b->bc == GRF_BC_PERIODIC);
     g.reflect = 0;  // mirror boxes are not accepted here
-    d.c.kappa1 = p->kappa1; d.c.kappa2 = p->kappa2; d.c.kappa3 = p->kappa3;
-    d.c.shift_F = p->shift_F; d.c.eta = p->eta; d.c.lam = p->lambda; d.c.g2 = p->g2; d.c.g3 = p->g3;
-    d.c.inv_1pa = 1.0 / (1.0 + p->a0); d.c.a_1pa = p->a0 / (1.0 + p->a0);
-    d.c.bK = 3.0 * p->b0 / (4.0 * (1.0 + p->b0)); d.c.bTh = 1.0 / (2.0 * (1.0 + p->b0));
-    d.c.beta_kind = p->beta_kind;
-    d.c.beta_kappa = p->beta_kappa;
-    d.c.decoupled = p->decoupled;
-    d.c.advection = p->advection;
+    d.c = make_coeffs(p);
     d.dt = dt;
     d.ko = p->sigma_ko / (64.0 * b->dx);
     d.min_chi = p->min_chi;

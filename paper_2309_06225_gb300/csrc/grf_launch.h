@@ -10,6 +10,23 @@
 namespace grf {
 struct Geom;
 struct StageArgs;
+
+// The per-launch coefficients of a parameter set (every entry point builds them this way).
+inline Coeffs make_coeffs(const grf_params* p) {
+    Coeffs c;
+    c.kappa1 = p->kappa1; c.kappa2 = p->kappa2; c.kappa3 = p->kappa3;
+    c.shift_F = p->shift_F; c.eta = p->eta; c.lam = p->lambda; c.g2 = p->g2; c.g3 = p->g3;
+    c.inv_1pa = 1.0 / (1.0 + p->a0);
+    c.a_1pa = p->a0 / (1.0 + p->a0);
+    c.bK = 3.0 * p->b0 / (4.0 * (1.0 + p->b0));
+    c.bTh = 1.0 / (2.0 * (1.0 + p->b0));
+    c.beta_kind = p->beta_kind;
+    c.beta_kappa = p->beta_kappa;
+    c.decoupled = p->decoupled;
+    c.advection = p->advection;
+    return c;
+}
+
 void launch_stage(int stage, dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c, const StageArgs& a);
 void launch_stage_decoupled(int stage, dim3 grid, dim3 block, cudaStream_t st, const Geom& g, const Coeffs& c,
                             const StageArgs& a);
