@@ -225,6 +225,18 @@ def test_reverse_sweep_is_deterministic(g):
     assert np.array_equal(r1[2], r2[2]) and np.array_equal(r1[3], r2[3])
 
 
+def test_reverse_sweep_is_deterministic_across_waves(g, workload96):
+    """At 96^3 a reversed stage runs in six waves of tape columns, each taped then swept, the
+    columns' parameter sums accumulating across the waves. Two runs give the same bits."""
+    box, params, amp, dphi, dt = workload96
+    s0 = gi.single_puncture(box, amp=amp)
+    ubar = interior_random(box, np.random.default_rng(9), 1.0)
+    r1 = forward_and_adjoint(g, box, params, s0, dt, 2, (6.0, 0.0, 0.0, 0.0), 20, 0.5, ubar)
+    r2 = forward_and_adjoint(g, box, params, s0, dt, 2, (6.0, 0.0, 0.0, 0.0), 20, 0.5, ubar)
+    assert np.array_equal(r1[2], r2[2]) and np.array_equal(r1[3], r2[3])
+    assert np.any(r1[2] != 0.0)
+
+
 def test_autograd_backward_runs_the_reverse_sweep(g):
     """SignalAdjoint.backward returns grad_out * dL/dtheta from the sweep; the forward-mode
     SphereSignal agrees and keeps theta's device."""
