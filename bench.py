@@ -203,6 +203,7 @@ def run_calls(args, rank, world, local_rank):
     rhs = grf.alloc_state(b)
     out4 = grf.alloc_state(b, 4)
     out3 = grf.alloc_state(b, 3)
+    out4 = grf.alloc_state(b, 4)
     out2 = grf.alloc_state(b, 2)
     ews = grf.alloc_workspace(grf.grf_extract_workspace_bytes(32, 8))
     npts = box.nx * box.ny * box.nz
@@ -213,7 +214,7 @@ def run_calls(args, rank, world, local_rank):
         "grf_constraints": lambda: grf.grf_constraints(b, p, state, out4, norms=False),
         "grf_energy_densities": lambda: grf.grf_energy_densities(b, p, state, out3),
         "grf_weyl_psi4": lambda: grf.grf_weyl_psi4(b, p, state, out2),
-        "grf_hyperbolicity": lambda: grf.grf_hyperbolicity(b, p, state, out3),
+        "grf_hyperbolicity": lambda: grf.grf_hyperbolicity(b, p, state, out4),
         # the scalar waveform: spin-0 modes of phi up to l = 8 on a sphere of radius 0.75 L/2
         "grf_extract_modes": lambda: grf.grf_extract_modes(b, state[25], None, 0, 0.375 * box.nx * box.dx,
                                                            (0.0, 0.0, 0.0), 32, 64, 8, ws=ews),

@@ -465,18 +465,21 @@ int grf_state_dot(const grf_box* box, const double* x, const double* y, int fiel
  * ------------------------------------------------------------------------------------- */
 
 /* Hyperbolicity diagnostics of the 4dST equations ("Research projects": the loss of
- * hyperbolicity of the theory; "Key features": diagnostics) at the interior points, 3 fields in the
- * state's layout (device, out3):
+ * hyperbolicity of the theory; "Key features": diagnostics) at the interior points, 4 fields in the
+ * state's layout (device, out4):
  *   0  det M, the determinant of the per-point linear system for (d_t K_ij, d_t Pi) with each
  *      unknown's own coefficient normalised to 1 (1 without coupling). Where it vanishes the
  *      equations do not determine the time derivatives (the solve reports GRF_ESINGULAR);
  *   1  det(g_eff^ab) / det(g^ab) for the principal symbol of the scalar equation,
- *      g_eff^ab = (1 + 2 g2 X) g^ab - 2 g2 nabla^a phi nabla^b phi: (1 + 2 g2 X)^3 (1 + 6 g2 X);
- *   2  -g_eff^nn = 1 + 2 g2 X + 2 g2 Pi^2 (positive while the slice normal is timelike for the
- *      scalar's characteristic cone).
+ *      g_eff^ab = (1 + 2 g2 X) g^ab - 2 g2 nabla^a phi nabla^b phi + 2 g3 (box(phi) g^ab - nabla^a
+ *      nabla^b phi); without the cubic term (1 + 2 g2 X)^3 (1 + 6 g2 X);
+ *   2  -g_eff^nn = 1 + 2 g2 X + 2 g2 Pi^2 + 2 g3 tr(nabla_i nabla_j phi) (positive while the slice
+ *      normal is timelike for the scalar's characteristic cone);
+ *   3  the smallest pivot of Gaussian elimination with partial pivoting of that normalised system,
+ *      over its largest entry (1 without coupling; small where the solve nears a lost pivot).
  * The state's ghosts are refilled as for grf_rhs. Asynchronous. GRF_EINVAL for a bad box, params or
  * pointer. */
-int grf_hyperbolicity(const grf_box* box, const grf_params* params, double* state, double* out3, grf_stream_t stream);
+int grf_hyperbolicity(const grf_box* box, const grf_params* params, double* state, double* out4, grf_stream_t stream);
 
 /* Weyl scalar Psi_4, the source of the tensor waveforms: Psi_4 = C_abcd n^a mbar^b n^c mbar^d
  * with n = (u - e_r)/sqrt2, m = (e_theta + i e_phi)/sqrt2, u the slice normal and (e_r, e_theta,

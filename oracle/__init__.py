@@ -69,6 +69,7 @@ def lib():
         L.orc_psi4.argtypes = [C.POINTER(OrcBox), C.POINTER(OrcParams), _P, _P]
         L.orc_phys_sources_psi4.argtypes = [C.POINTER(OrcParams), _P, _P, C.c_double, _P, _P]
         L.orc_point_hyperbolicity.argtypes = [C.POINTER(OrcParams), _P, _P, _P, _P]
+        L.orc_point_system.argtypes = [C.POINTER(OrcParams), _P, _P, _P, _P]
         L.orc_hyperbolicity.argtypes = [C.POINTER(OrcBox), C.POINTER(OrcParams), _P, _P]
         L.orc_rk4_signal.argtypes = [C.POINTER(OrcBox), C.POINTER(OrcParams), _P, C.c_double, C.c_int, _P, _P]
         L.orc_rk4_signal.restype = C.c_int
@@ -279,18 +280,30 @@ def phys_psi4(p, phys, u6, w, xyz):
 
 
 def point_hyperbolicity(p, v, d1, d2):
-    """(det M of the coupled system, det(g_eff)/det(g), -g_eff^nn) at one point."""
+    """(det M of the coupled system, det(g_eff)/det(g), -g_eff^nn, smallest pivot ratio of M) at
+    one point."""
     v = np.ascontiguousarray(v, dtype=np.float64)
     d1 = np.ascontiguousarray(d1, dtype=np.float64)
     d2 = np.ascontiguousarray(d2, dtype=np.float64)
-    out = np.zeros(3)
+    out = np.zeros(4)
     lib().orc_point_hyperbolicity(C.byref(params(p)), _ptr(v), _ptr(d1), _ptr(d2), _ptr(out))
     return out
 
 
+def point_system(p, v, d1, d2):
+    """The coupled system's normalised 7 x 7 matrix at one point (rows 0..5: the d_t K_ij rows,
+    row 6: the scalar equation over its d_t Pi coefficient)."""
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    d1 = np.ascontiguousarray(d1, dtype=np.float64)
+    d2 = np.ascontiguousarray(d2, dtype=np.float64)
+    out = np.zeros(49)
+    lib().orc_point_system(C.byref(params(p)), _ptr(v), _ptr(d1), _ptr(d2), _ptr(out))
+    return out.reshape(7, 7)
+
+
 def hyperbolicity(b, p, s):
-    """The three hyperbolicity diagnostics at every interior point: [3, nz, ny, nx]."""
-    out = np.zeros((3, b.nz, b.ny, b.nx))
+    """The four hyperbolicity diagnostics at every interior point: [4, nz, ny, nx]."""
+    out = np.zeros((4, b.nz, b.ny, b.nx))
     lib().orc_hyperbolicity(C.byref(box(b)), C.byref(params(p)), _ptr(np.ascontiguousarray(s)), _ptr(out))
     return out
 

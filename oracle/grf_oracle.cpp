@@ -417,9 +417,14 @@ void orc_energy_densities(const orc_box* b, const orc_params* P, const double* s
 }
 
 // Hyperbolicity diagnostics at one point (point_hyperbolicity) and at every interior point:
-// out[3][nz][ny][nx] (the ghosts of s must be valid).
-void orc_point_hyperbolicity(const orc_params* P, const double* v, const double* d1, const double* d2, double* out3) {
-    point_hyperbolicity(prm_of(*P), v, d1, d2, out3);
+// out[4][nz][ny][nx] (the ghosts of s must be valid).
+void orc_point_hyperbolicity(const orc_params* P, const double* v, const double* d1, const double* d2, double* out4) {
+    point_hyperbolicity(prm_of(*P), v, d1, d2, out4);
+}
+
+// The normalised 7 x 7 matrix of the coupled system at one point (row-major, 49 doubles).
+void orc_point_system(const orc_params* P, const double* v, const double* d1, const double* d2, double* out49) {
+    point_system(prm_of(*P), v, d1, d2, out49);
 }
 
 void orc_hyperbolicity(const orc_box* b, const orc_params* P, const double* s, double* out) {
@@ -429,11 +434,11 @@ void orc_hyperbolicity(const orc_box* b, const orc_params* P, const double* s, d
     for (int k = 0; k < b->nz; ++k)
         for (int j = 0; j < b->ny; ++j)
             for (int i = 0; i < b->nx; ++i) {
-                double v[NF], d1[NF * 3], d2[NF * 6], o[3];
+                double v[NF], d1[NF * 3], d2[NF * 6], o[4];
                 point_derivs(g, s, b->dx, i + g.ng, j + g.ng, k + g.ng, v, d1, d2);
                 point_hyperbolicity(prm_of(*P), v, d1, d2, o);
                 long long p = ((long long)k * b->ny + j) * b->nx + i;
-                for (int m = 0; m < 3; ++m) out[m * npt + p] = o[m];
+                for (int m = 0; m < 4; ++m) out[m * npt + p] = o[m];
             }
 }
 

@@ -306,10 +306,12 @@ def grf_energy_densities(box: grf_box, params: grf_params, state, out3, stream=N
                                              _stream(stream)), "grf_energy_densities")
 
 
-def grf_hyperbolicity(box: grf_box, params: grf_params, state, out3, stream=None):
-    """det M of the coupled system, det(g_eff)/det(g) and -g_eff^nn at the interior points
-    (out3: device, 3 fields in the state's layout). See include/grf.h."""
-    return _check(lib().grf_hyperbolicity(C.byref(box), C.byref(params), _dev(state), _dev(out3), _stream(stream)),
+def grf_hyperbolicity(box: grf_box, params: grf_params, state, out4, stream=None):
+    """det M of the coupled system, det(g_eff)/det(g), -g_eff^nn and the system's smallest pivot
+    ratio at the interior points (out4: device, 4 fields in the state's layout). See include/grf.h."""
+    if hasattr(out4, "shape") and tuple(out4.shape) != state_shape(box, 4):
+        raise ValueError(f"grf_hyperbolicity writes 4 fields: out4 must have shape {state_shape(box, 4)}")
+    return _check(lib().grf_hyperbolicity(C.byref(box), C.byref(params), _dev(state), _dev(out4), _stream(stream)),
                   "grf_hyperbolicity")
 
 

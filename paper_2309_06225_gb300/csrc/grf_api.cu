@@ -722,14 +722,14 @@ int grf_weyl_psi4(const grf_box* box, const grf_params* params, double* state, d
     return check_launch();
 }
 
-int grf_hyperbolicity(const grf_box* box, const grf_params* params, double* state, double* out3, grf_stream_t stream) {
-    if (!box_ok(box) || !params_ok(params) || !state || !out3) return GRF_EINVAL;
+int grf_hyperbolicity(const grf_box* box, const grf_params* params, double* state, double* out4, grf_stream_t stream) {
+    if (!box_ok(box) || !params_ok(params) || !state || !out4) return GRF_EINVAL;
     Geom g = make_geom(box);
     cudaStream_t st = (cudaStream_t)stream;
     int r = fill_ghosts(g, box->bc, state, st);
     if (r) return r;
     launch_constraints(interior_grid(g), kBlock, st, g, make_coeffs(params), state, nullptr, nullptr, nullptr, nullptr,
-                       make_double3(0.0, 0.0, 0.0), out3);
+                       make_double3(0.0, 0.0, 0.0), out4);
     return check_launch();
 }
 

@@ -11,7 +11,7 @@ namespace grf {
 // three scalar terms) are each written when non-null.
 // ORD = 4: block gather mode (as rhs_kernel); ORD = 6: the 6th-order per-thread gather.
 // psi4 (2 fields, re and im) receives the Weyl scalar with the triad about the origin; o = the
-// coordinates of interior point (0, 0, 0); hyp (3 fields) the hyperbolicity diagnostics of the
+// coordinates of interior point (0, 0, 0); hyp (4 fields) the hyperbolicity diagnostics of the
 // coupled system (PointExtraT::hyp). PSI4 = 1 compiles those outputs in (they need the assembled
 // or solved coupled system); with PSI4 = 0 the compiler drops the coupled solve, which H, M_i and
 // the densities do not use.
@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(128) constraints_kernel(Geom g, Coeffs c, cons
             psi4[g.fstride + p] = ex.psi4[1];
         }
         if (PSI4 && hyp)
-            for (int m = 0; m < 3; ++m) hyp[m * g.fstride + p] = ex.hyp[m];
+            for (int m = 0; m < 4; ++m) hyp[m * g.fstride + p] = ex.hyp[m];
     }
     const int t = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
     for (int m = 0; m < 4; ++m) {

@@ -172,9 +172,9 @@ int grf_host_point_psi4(const grf_params* p, const double* v, const double* d1, 
     return ok ? 0 : -5;
 }
 
-// The kernel's hyperbolicity diagnostics (det M, det g_eff / det g, -g_eff^nn) of the same host
-// instance; out3 receives the three.
-int grf_host_point_hyp(const grf_params* p, const double* v, const double* d1, const double* d2, double* out3) {
+// The kernel's hyperbolicity diagnostics (det M, det g_eff / det g, -g_eff^nn, smallest pivot
+// ratio) of the same host instance; out4 receives the four.
+int grf_host_point_hyp(const grf_params* p, const double* v, const double* d1, const double* d2, double* out4) {
     const grf::PointInT<double> in = host_point(v, d1, d2);
     const grf::Coeffs c = host_coeffs(p);
     grf::PointExtraT<double> ex;
@@ -182,7 +182,7 @@ int grf_host_point_hyp(const grf_params* p, const double* v, const double* d1, c
     double rhs[grf::NFIELDS];
     bool ok = true;
     grf::point_rhs(c, in, rhs, &ex, ok);
-    for (int m = 0; m < 3; ++m) out3[m] = ex.hyp[m];
+    for (int m = 0; m < 4; ++m) out4[m] = ex.hyp[m];
     return ok ? 0 : -5;
 }
 

@@ -113,9 +113,10 @@ struct PointExtraT {
     //            g_eff^ab = (1 + 2 g2 X) g^ab - 2 g2 d^a phi d^b phi + 2 g3 (box(phi) g^ab - H^ab);
     //            for g3 = 0, by the matrix determinant lemma, (1 + 2 g2 X)^3 (1 + 6 g2 X);
     //   hyp[2] = -g_eff^nn = 1 + 2 g2 X + 2 g2 Pi^2 + 2 g3 tr H (the coefficient of d_t Pi; the
-    //            normal is timelike for the scalar's characteristic cone while it is positive).
+    //            normal is timelike for the scalar's characteristic cone while it is positive);
+    //   hyp[3] = the smallest pivot of partial-pivoting elimination of M over its largest entry.
     int want_hyp = 0;
-    double hyp[3];
+    double hyp[4];
 };
 using PointExtra = PointExtraT<double>;
 
@@ -170,16 +171,20 @@ __device__ __forceinline__ double abs_max7(const double M[7][8]) {
 #endif
 
 // Determinant of the 7x7 block of M (a copy, Gaussian elimination with partial pivoting and the
-// sign of each row exchange). Diagnostics only.
-GRF_HD double det7(const double M[7][8]) {
-    double A[7][7];
+// sign of each row exchange), and in *ratio the smallest pivot magnitude over the block's largest
+// entry magnitude. Diagnostics only.
+GRF_HD double det7(const double M[7][8], double* ratio) {
+    double A[7][7], mx = 0.0, mn = -1.0;
     for (int i = 0; i < 7; ++i)
-        for (int j = 0; j < 7; ++j) A[i][j] = M[i][j];
+        for (int j = 0; j < 7; ++j) { A[i][j] = M[i][j]; mx = fmax(mx, fabs(A[i][j])); }
+    *ratio = 0.0;
     double det = 1.0;
     for (int k = 0; k < 7; ++k) {
         int piv = k;
         for (int i = k + 1; i < 7; ++i)
             if (fabs(A[i][k]) > fabs(A[piv][k])) piv = i;
+        const double pm = fabs(A[piv][k]);
+        mn = (mn < 0.0 || pm < mn) ? pm : mn;
         if (A[piv][k] == 0.0) return 0.0;
         if (piv != k) {
             for (int j = 0; j < 7; ++j) {
@@ -195,6 +200,7 @@ GRF_HD double det7(const double M[7][8]) {
             for (int j = k + 1; j < 7; ++j) A[i][j] -= f * A[k][j];
         }
     }
+    *ratio = mx > 0.0 ? mn / mx : 0.0;
     return det;
 }
 
@@ -997,7 +1003,7 @@ GRF_HD void point_rhs(const CoeffsT<P>& c, const PointInT<T>& in, T rhs[NFIELDS]
         Msys[6][7] = fma(al * iD, src, bdPi + dadp);
         if constexpr (std::is_same<T, double>::value) {
             if (extra && extra->want_hyp) {
-                extra->hyp[0] = det7(Msys);
+                extra->hyp[0] = det7(Msys, &extra->hyp[3]);
                 extra->hyp[1] = fX * fX * fX * fma(6.0 * g2, X, 1.0);  // g3 = 0; the cubic case below
                 extra->hyp[2] = Dphi;
             }

@@ -101,9 +101,10 @@ def host_point_psi4(params, v, d1, d2, xyz):
 
 
 def host_point_hyp(params, v, d1, d2):
-    """The kernel's hyperbolicity diagnostics (det M, det g_eff / det g, -g_eff^nn) on the host."""
+    """The kernel's hyperbolicity diagnostics (det M, det g_eff / det g, -g_eff^nn, smallest pivot
+    ratio) on the host."""
     P = C.POINTER(C.c_double)
     arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (v, d1, d2)]
-    out = np.zeros(3)
+    out = np.zeros(4)
     st = _lib().grf_host_point_hyp(C.byref(params), *[a.ctypes.data_as(P) for a in arrs], out.ctypes.data_as(P))
     return out, st

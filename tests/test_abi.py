@@ -199,3 +199,13 @@ def test_empty_and_degenerate_calls_without_gpu(grf):
     # a periodic box needs at least the ghost width of points per axis
     two = grf.make_box(2, 8, 8, 0.25)
     assert grf.grf_workspace_bytes(two, grf.GRF_OP_RK4) == 0
+
+
+def test_hyperbolicity_output_shape_is_checked_without_gpu(grf):
+    """grf_hyperbolicity writes 4 fields: an output tensor of another shape is refused before
+    anything reaches the library."""
+    import torch
+    b = grf.make_box(8, 8, 8, 0.25)
+    state = torch.zeros(grf.state_shape(b), dtype=torch.float64)
+    with pytest.raises(ValueError):
+        grf.grf_hyperbolicity(b, grf.grf_params(), state, torch.zeros(grf.state_shape(b, 3), dtype=torch.float64))

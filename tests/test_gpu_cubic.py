@@ -148,10 +148,10 @@ def test_cubic_hyperbolicity_parity(g, orc, decoupled):
     ref = orc.hyperbolicity(box, params, filled)
     b = g.box_like(box)
     t = g.to_device(s, b)
-    out = g.alloc_state(b, 3)
+    out = g.alloc_state(b, 4)
     g.grf_hyperbolicity(b, g.params_like(params), t, out)
-    got = box.interior(g.to_host(out, b)[:3])
-    for m in range(3):
+    got = box.interior(g.to_host(out, b)[:4])
+    for m in range(4):
         den = max(np.max(np.abs(ref[m])), 1e-300)
         assert np.max(np.abs(got[m] - ref[m])) <= 1e-11 * den, (m, np.max(np.abs(got[m] - ref[m])) / den)
     no_cubic = orc.hyperbolicity(box, P(lam=0.3, g2=0.2, beta_kind=1, decoupled=decoupled), filled)

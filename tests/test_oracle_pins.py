@@ -1334,14 +1334,27 @@ def test_coupled_system_determinant_on_schwarzschild(orc, schwarzschild_points, 
         det M = 1 - 32 lambda^2 G_S^ij L(G_S)_ij = 1 - 32 lambda^2 R_ij R^ij = 1 - 192 lambda^2 M^2 / R^6,
     R the areal radius (R_ij = diag(-2, 1, 1) M / R^3 in an orthonormal frame). The oracle's
     determinant comes from its covariant residual; the closed form is independent of it. The
-    quadratic coupling has beta'(0) = 0 and det M = 1."""
+    quadratic coupling has beta'(0) = 0 and det M = 1.
+    The same structure fixes the smallest pivot ratio: with the 6x6 block the identity and the
+    scalar row's couplings below 1 in magnitude, partial pivoting exchanges no rows, the pivots are
+    1, ..., 1 and the Schur complement det M, and the ratio is min(1, |det M|) / max |M_ij|."""
     rs, data = schwarzschild_points
+    p = P(lam=lam, g2=0.3, beta_kind=gi.BETA_LINEAR)
+    closed = 0
     for r, (v, d1, d2) in zip(rs, data):
         R = an.areal_radius_isotropic(r, 1.0)
-        det = orc.point_hyperbolicity(P(lam=lam, g2=0.3, beta_kind=gi.BETA_LINEAR), v, d1, d2)[0]
+        h = orc.point_hyperbolicity(p, v, d1, d2)
+        det = h[0]
         assert det == pytest.approx(1.0 - 192.0 * lam ** 2 / R ** 6, rel=1e-12, abs=1e-13)
         detq = orc.point_hyperbolicity(P(lam=lam, g2=0.3, beta_kind=gi.BETA_QUADRATIC), v, d1, d2)[0]
         assert detq == pytest.approx(1.0, abs=1e-14)
+        M = orc.point_system(p, v, d1, d2)
+        np.testing.assert_allclose(M[:6, :6], np.eye(6), rtol=0, atol=1e-14)
+        assert M[6, 6] == 1.0
+        if np.max(np.abs(M[6, :6])) < 1.0:
+            assert h[3] == pytest.approx(min(1.0, abs(det)) / np.max(np.abs(M)), rel=1e-12)
+            closed += 1
+    assert closed >= 10
 
 
 def test_loss_of_solvability_radius_on_schwarzschild(orc, schwarzschild_points):
@@ -1365,10 +1378,10 @@ def test_loss_of_solvability_radius_on_schwarzschild(orc, schwarzschild_points):
 
 
 def test_hyperbolicity_diagnostics_without_coupling(orc, conformal_generic):
-    """lambda = g2 = 0: the coupled system is the identity and g_eff = g."""
+    """lambda = g2 = 0: the coupled system is the identity (all pivots 1) and g_eff = g."""
     v, d1, d2, ph = conformal_generic
     h = orc.point_hyperbolicity(P(lam=0.0, g2=0.0), v, d1, d2)
-    np.testing.assert_allclose(h, [1.0, 1.0, 1.0], rtol=0, atol=1e-14)
+    np.testing.assert_allclose(h, [1.0, 1.0, 1.0, 1.0], rtol=0, atol=1e-14)
 
 
 @pytest.mark.parametrize("g2", [0.3, -0.8])
