@@ -51,7 +51,7 @@ STAGE_CAPTURES = {
 }
 FP64_INSTR_PER_POINT_STAGE, TRAFFIC_BYTES_PER_POINT_STAGE = STAGE_CAPTURES[(4, "centred", False)]
 # the tangent-linear (dual-number) stage kernel's FP64 instructions per point-stage (same kind of capture)
-TLM_FP64_INSTR_PER_POINT_STAGE = 28826
+TLM_FP64_INSTR_PER_POINT_STAGE = 29130
 # nominal FP64 (non-tensor) peak of GB300: 152 SMs x 2 FP64 FMA lanes/clk x 2 flop x ~2.06 GHz;
 # used only when no measured figure is stored
 FP64_NOMINAL_TFLOPS = 1.25
