@@ -280,17 +280,19 @@ def test_energy_densities_parity(g, orc, bc, decoupled):
         assert np.max(np.abs(got[m] - ref[m])) <= 1e-11 * den, m
 
 
-@pytest.mark.parametrize("g3", [0.0, 0.1])
-def test_bl_pair_256_sampled_outputs(g, orc, g3):
+@pytest.mark.parametrize("g3,decoupled", [(0.0, 0), (0.1, 0), (0.0, 1)])
+def test_bl_pair_256_sampled_outputs(g, orc, g3, decoupled):
     """Full-size 256^3 Brill-Lindquist workload, one RK4 step in the production launch
     configuration; sampled points are recomputed by the oracle on 19^3 frozen-ghost sub-boxes
     centred on them (one RK4 step has a domain of dependence of 12 points, so the centre of
     such a sub-box is exact). Each field agrees to 1e-11 of its scale, or to 64 times the
     oracle's own rounding noise at the point where that is larger. g3 = 0.1 is the cubic
-    workload's launch (`bench.py --g3 0.1`: the general instantiation with the cubic branch)."""
+    workload's launch (`bench.py --g3 0.1`: the general instantiation with the cubic branch),
+    decoupled = 1 that of `bench.py --decoupled` (the stage kernel without backreaction)."""
     cfg = gi.config_bl_pair_256()
     box, params, dt = cfg["box"], cfg["params"], cfg["dt"]
     params.g3 = g3
+    params.decoupled = decoupled
     s0 = cfg["make_state"]()
     gpu = gpu_rk4(g, box, params, s0, dt, 1)
     assert np.all(np.isfinite(box.interior(gpu)))
